@@ -1,0 +1,288 @@
+"""FP64 CPU oracle for the MH3D portrait model (arXiv 2503.13802).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; never by the product package.
+It shares no code with the CUDA path.  The arithmetic lives in
+``mh3d_oracle.c`` (plain C, FP64, OpenMP); this module compiles it with gcc on
+first use and wraps it with numpy arrays.
+
+Functions and the passages they follow:
+
+* ``langevin_deriv(k, x)``: L^(k)(x), L(x) = coth x - 1/x (Sec. 2).
+* ``ck(k, gammaA)``: (gamma A)^k / (k-1)! (Theorem 1).
+* ``psf_tables(geom)``: separable harmonic PSF samples h_k ~ c_k L^(k)(gamma x)
+  (Sec. 3.3, Eq. hkapprox) on the drive axis, 3 L'(gamma_t y) across it.
+* ``forward / forward_full3d``: d = A rho, A = P H B (Eq. portz, Eq. dN), with
+  the phase e^{i theta_k} of Sec. 4.4.
+* ``adjoint``: A^T for the real inner product.
+* ``reg_apply``: R = I, or T^T T + alpha P_a^T P_a (Sec. 4.3, Eq. finalR).
+* ``normal_apply``: (A^T A + lambda R) p.
+* ``cg``: conjugate gradients on the normal equations.
+* ``apg``: the paper's accelerated projected gradient (Sec. 4.3, runtime
+  subsection).
+* ``mhad``: the multi-harmonic anti-differentiation native image (appendix
+  MHAD, Eq. mhadM); numpy's FFT is the library step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mh3d_oracle.c")
+_LIB = os.path.join(_HERE, "libmh3d_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (FP64, no fast-math, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    d, i, P = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    lib.orc_langevin_deriv.restype = d
+    lib.orc_langevin_deriv.argtypes = [i, d]
+    lib.orc_ck.restype = d
+    lib.orc_ck.argtypes = [i, d]
+    lib.orc_psf_tables.restype = None
+    lib.orc_psf_tables.argtypes = [i, i, i, d, d, d, i, i, d, d, d, P, P, P]
+    op_args = [i, i, i, i, i, i, P, P, P, P, P, P, P]
+    lib.orc_forward.restype = None
+    lib.orc_forward.argtypes = op_args
+    lib.orc_forward_full3d.restype = None
+    lib.orc_forward_full3d.argtypes = op_args
+    lib.orc_adjoint.restype = None
+    lib.orc_adjoint.argtypes = op_args
+    lib.orc_reg_apply.restype = None
+    lib.orc_reg_apply.argtypes = [i, i, i, i, d, i, P, P]
+    lib.orc_normal_apply.restype = None
+    lib.orc_normal_apply.argtypes = [i, i, i, i, i, i, P, P, P, P, P, d, i, d, i, P, P]
+    lib.orc_cg.restype = i
+    lib.orc_cg.argtypes = [i, i, i, i, i, i, P, P, P, P, P, d, i, d, i, P, d, i, P, P]
+    lib.orc_apg.restype = None
+    lib.orc_apg.argtypes = [i, i, i, i, i, i, P, P, P, P, P, d, i, d, i, P, d, i, P]
+    lib.orc_num_threads.restype = i
+    lib.orc_set_threads.argtypes = [i]
+    _lib = lib
+    return lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return _load().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    _load().orc_set_threads(int(n))
+
+
+@dataclass
+class Geometry:
+    """Grid and model parameters.  n = (nx, ny, nz); arrays are [nz][ny][nx]."""
+
+    n: Sequence[int]
+    voxel_mm: Sequence[float] = (1.0, 1.0, 1.0)
+    ds_factor: int = 1
+    ds_offset: int = 0
+    k_min: int = 2
+    k_max: int = 5
+    gamma_per_mm: float = 1.387016
+    gammaA: float = 2.0
+    transverse_ratio: float = 0.5
+    theta: Optional[Sequence[float]] = None
+
+    @property
+    def K(self) -> int:
+        return self.k_max - self.k_min + 1
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.n
+        return (nz, ny, nx)
+
+    @property
+    def portrait_shape(self):
+        nx, ny, nz = self.n
+        return (self.K, nz, ny, nx // self.ds_factor)
+
+    def theta_array(self) -> np.ndarray:
+        if self.theta is None:
+            return np.zeros(self.K)
+        t = _f64(self.theta)
+        assert t.shape == (self.K,)
+        return t
+
+
+def langevin_deriv(k: int, x) -> np.ndarray:
+    lib = _load()
+    xs = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    out = np.array([lib.orc_langevin_deriv(int(k), float(v)) for v in xs.ravel()])
+    return out.reshape(np.shape(x)) if np.ndim(x) else out[0]
+
+
+def ck(k: int, gammaA: float) -> float:
+    return _load().orc_ck(int(k), float(gammaA))
+
+
+def psf_tables(g: Geometry):
+    """Return (X [K, nx], Y [ny], Z [nz]) PSF sample tables (FP64)."""
+    nx, ny, nz = g.n
+    X = np.zeros((g.K, nx))
+    Y = np.zeros(ny)
+    Z = np.zeros(nz)
+    dx, dy, dz = g.voxel_mm
+    _load().orc_psf_tables(nx, ny, nz, dx, dy, dz, g.k_min, g.k_max, g.gamma_per_mm, g.gammaA,
+                           g.transverse_ratio, _ptr(X), _ptr(Y), _ptr(Z))
+    return X, Y, Z
+
+
+def _op(fn, g: Geometry, tables, b, src, out):
+    nx, ny, nz = g.n
+    X, Y, Z = tables
+    th = g.theta_array()
+    fn(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z), _ptr(th),
+       _ptr(b), _ptr(src), _ptr(out))
+    return out
+
+
+def forward(g: Geometry, rho, b=None, tables=None) -> np.ndarray:
+    """d = A rho as complex128 [K, nz, ny, nx/s]."""
+    tables = tables or psf_tables(g)
+    rho = _f64(rho).reshape(g.shape)
+    b = None if b is None else _f64(b).reshape(g.shape)
+    out = np.zeros(g.portrait_shape + (2,))
+    _op(_load().orc_forward, g, tables, b, rho, out)
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def forward_full3d(g: Geometry, rho, b=None, tables=None) -> np.ndarray:
+    tables = tables or psf_tables(g)
+    rho = _f64(rho).reshape(g.shape)
+    b = None if b is None else _f64(b).reshape(g.shape)
+    out = np.zeros(g.portrait_shape + (2,))
+    _op(_load().orc_forward_full3d, g, tables, b, rho, out)
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def _complex_in(g: Geometry, d) -> np.ndarray:
+    d = np.asarray(d).reshape(g.portrait_shape)
+    return np.ascontiguousarray(np.stack([d.real, d.imag], axis=-1), dtype=np.float64)
+
+
+def adjoint(g: Geometry, d, b=None, tables=None) -> np.ndarray:
+    """rho = A^T d (real inner product), float64 [nz, ny, nx]."""
+    tables = tables or psf_tables(g)
+    b = None if b is None else _f64(b).reshape(g.shape)
+    out = np.zeros(g.shape)
+    _op(_load().orc_adjoint, g, tables, b, _complex_in(g, d), out)
+    return out
+
+
+def reg_apply(g: Geometry, p, kind: int = 0, alpha: float = 0.0, shell: int = 2) -> np.ndarray:
+    nx, ny, nz = g.n
+    p = _f64(p).reshape(g.shape)
+    out = np.zeros(g.shape)
+    _load().orc_reg_apply(nx, ny, nz, int(kind), float(alpha), int(shell), _ptr(p), _ptr(out))
+    return out
+
+
+@dataclass
+class SolveOpts:
+    lam: float = 1e-3
+    reg_kind: int = 0
+    alpha: float = 0.0
+    shell: int = 2
+    rel_tol: float = 1e-4
+    max_iter: int = 1000
+
+
+def normal_apply(g: Geometry, p, b=None, opts: SolveOpts = SolveOpts(), tables=None) -> np.ndarray:
+    tables = tables or psf_tables(g)
+    nx, ny, nz = g.n
+    X, Y, Z = tables
+    th = g.theta_array()
+    b = None if b is None else _f64(b).reshape(g.shape)
+    p = _f64(p).reshape(g.shape)
+    out = np.zeros(g.shape)
+    _load().orc_normal_apply(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z),
+                             _ptr(th), _ptr(b), opts.lam, opts.reg_kind, opts.alpha, opts.shell,
+                             _ptr(p), _ptr(out))
+    return out
+
+
+def cg(g: Geometry, d, b=None, opts: SolveOpts = SolveOpts(), x0=None, tables=None):
+    """Returns (x, iters, history) for CG on (A^T A + lambda R) x = A^T d."""
+    tables = tables or psf_tables(g)
+    nx, ny, nz = g.n
+    X, Y, Z = tables
+    th = g.theta_array()
+    b = None if b is None else _f64(b).reshape(g.shape)
+    x = np.zeros(g.shape) if x0 is None else _f64(x0).reshape(g.shape).copy()
+    hist = np.zeros(opts.max_iter + 1)
+    it = _load().orc_cg(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z),
+                        _ptr(th), _ptr(b), opts.lam, opts.reg_kind, opts.alpha, opts.shell,
+                        _ptr(_complex_in(g, d)), opts.rel_tol, opts.max_iter, _ptr(x), _ptr(hist))
+    return x, it, hist[: it + 1]
+
+
+def apg(g: Geometry, d, tau: float, iters: int, b=None, opts: SolveOpts = SolveOpts(), x0=None,
+        tables=None) -> np.ndarray:
+    """The paper's accelerated projected gradient, fixed iteration count."""
+    tables = tables or psf_tables(g)
+    nx, ny, nz = g.n
+    X, Y, Z = tables
+    th = g.theta_array()
+    b = None if b is None else _f64(b).reshape(g.shape)
+    x = np.zeros(g.shape) if x0 is None else _f64(x0).reshape(g.shape).copy()
+    _load().orc_apg(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z),
+                    _ptr(th), _ptr(b), opts.lam, opts.reg_kind, opts.alpha, opts.shell,
+                    _ptr(_complex_in(g, d)), float(tau), int(iters), _ptr(x))
+    return x
+
+
+def mhad(d_list, ck_list, lam: float, axis: int = -1) -> np.ndarray:
+    """MHAD native image (appendix MHAD, Eq. mhadM) along one axis.
+
+    d_list[k'] is the portrait of harmonic k = k'+2 (real), ck_list[k'] its
+    coefficient c_k.  With f = [0, -1, 0, ..., 0, 1] (so (f*u)[j] =
+    u[j+1] - u[j-1]) and f^{m} its m-fold self-convolution,
+    rho_N = F^{-1}[ sum_k c_k^{-1} conj(F f^{k-1}) F d_k / (sum_k |F f^{k-1}|^2 + lambda) ].
+    """
+    d0 = np.asarray(d_list[0])
+    n = d0.shape[axis]
+    f = np.zeros(n)
+    f[1 % n] += -1.0
+    f[(n - 1) % n] += 1.0
+    fh = np.fft.fft(f)
+    shape = [1] * d0.ndim
+    shape[axis] = n
+    num = 0.0
+    den = lam
+    for j, (dk, c) in enumerate(zip(d_list, ck_list)):
+        k = j + 2
+        fk = (fh ** (k - 1)).reshape(shape)
+        num = num + np.conj(fk) * np.fft.fft(np.asarray(dk, dtype=np.float64), axis=axis) / c
+        den = den + np.abs(fk) ** 2
+    return np.real(np.fft.ifft(num / den, axis=axis))
