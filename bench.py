@@ -1,0 +1,350 @@
+"""Benchmark: reconstructions/sec to relative residual 1e-4 on the
+128x128x64, k = 2..9, s = 2 synthetic workload (one step = one full MH3D
+reconstruction: A^T d, CG on the normal equations to rel. residual 1e-4,
+true-residual check), plus the HBM roofline of the forward operator A.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mh3d|reference]
+       [--mode 0|1] [--workload NAME]
+Under torchrun (N > 1) every rank solves its own volume (independent
+replicas, no data-path collective); the timing barrier and the max over ranks
+use the default process group.
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "reconstructions/sec to rel. residual 1e-4"
+UNIT = "reconstructions/s"
+WORKLOAD = "mh_128x128x64_k8_s2"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mh3d", choices=["mh3d", "reference"])
+    ap.add_argument("--mode", type=int, default=0, help="0 fused normal operator, 1 explicit A then A^T")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_case(wl: W.Workload, seed: int, forward_fn):
+    """Phantom, sensitivity and noisy portraits at the workload's SNR.
+    forward_fn(rho) -> clean portraits (complex, numpy)."""
+    rho = W.phantom(wl.n, wl.voxel_mm, seed, wl.n_blobs, wl.n_lines, wl.log_amplitudes)
+    b = W.sensitivity(wl.n, wl.voxel_mm, kind=wl.sens)
+    return rho, b
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def bench_mh3d(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2503_13802_gb300 import Plan, make_opts, mh3d_adjoint, mh3d_forward, mh3d_solve, mh3d_solve_host
+
+    wl = W.WORKLOADS[args.workload]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seed = wl.seeds[rank % len(wl.seeds)]
+    rho, b = make_case(wl, seed, None)
+    nx, ny, nz = wl.n
+    plan = Plan(wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max,
+                sensitivity=b)
+    K = wl.k_max - wl.k_min + 1
+    mx = nx // wl.ds_factor
+    rho_t = torch.as_tensor(rho, dtype=torch.float32, device=dev).contiguous()
+    d = torch.empty((K, nz, ny, mx), dtype=torch.complex64, device=dev)
+    mh3d_forward(plan, rho_t, d)
+    sig2 = float(torch.sum(torch.abs(d.to(torch.complex128)) ** 2)) / (d.numel() * 10 ** (wl.snr_db / 10))
+    noise = torch.as_tensor(W.unit_complex_noise(tuple(d.shape), seed).astype(np.complex64), device=dev)
+    d = (d + math.sqrt(sig2) * noise).contiguous()
+    x = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    opts = make_opts(lam=wl.lam, rel_tol=wl.rel_tol, max_iter=wl.max_iter, fixed_iters=wl.fixed_iters,
+                     normal_mode=args.mode)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        info = mh3d_solve(plan, d, opts, x)
+    # timed region: K reconstructions, L2 flushed between steps (outside the events)
+    times, iters = [], []
+    with Clocks(torch.cuda.current_device()) as clk:
+        barrier()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = mh3d_solve(plan, d, opts, x)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            iters.append(info["iters"])
+        barrier()
+    total = sum(times)
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = ws * args.steps / total
+
+    # Roofline of the forward operator A (T_y + T_z + X_fwd), L2 flushed
+    # before each application so rho and b come from HBM and d goes to HBM.
+    fwd_t, adj_t = [], []
+    r_out = torch.empty_like(x)
+    for i in range(10 + 3):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mh3d_forward(plan, rho_t, d)
+        e1.record(stream)
+        flush.zero_()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        mh3d_adjoint(plan, d, r_out)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            fwd_t.append(e0.elapsed_time(e1) / 1e3)
+            adj_t.append(e2.elapsed_time(e3) / 1e3)
+    N = nx * ny * nz
+    M = K * mx * ny * nz
+    alg_bytes = 4 * N + 4 * N + 8 * M          # rho + b + complex64 portraits
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    fwd_s = statistics.mean(fwd_t)
+    adj_s = statistics.mean(adj_t)
+    achieved = alg_bytes / fwd_s / 1e9
+
+    # e2e: host portraits in, host image out, through the C ABI
+    d_host = d.cpu().pin_memory()
+    x_host = torch.empty((nz, ny, nx), dtype=torch.float32).pin_memory()
+    mh3d_solve_host(plan, d_host, opts, x_host)
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 10))):
+        t0 = time.perf_counter()
+        mh3d_solve_host(plan, d_host, opts, x_host)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = 1.0 / statistics.mean(e2e_t)
+
+    # explicit A-then-A^T reconstructions for comparison (mode 1)
+    other = None
+    if args.mode == 0:
+        o1 = make_opts(lam=wl.lam, rel_tol=wl.rel_tol, max_iter=wl.max_iter, normal_mode=1)
+        mh3d_solve(plan, d, o1, x)
+        tt = []
+        for _ in range(5):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inf1 = mh3d_solve(plan, d, o1, x)
+            e1.record(stream)
+            e1.synchronize()
+            tt.append(e0.elapsed_time(e1) / 1e3)
+        other = {"mode": "explicit A then A^T (portrait through L2/HBM)", "value": 5 / sum(tt),
+                 "iters": inf1["iters"]}
+
+    it_med = int(statistics.median(iters))
+    per_iter = 4 if args.mode == 0 else 7
+    launches_per_step = 3 + 1 + per_iter * 2 * (it_med // 2 + 1) + 4
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+        "config": {"workload": wl.name, "grid": list(wl.n), "harmonics": [wl.k_min, wl.k_max],
+                   "ds_factor": wl.ds_factor, "sensitivity": wl.sens, "phantom": f"{wl.n_blobs} blobs + {wl.n_lines} lines",
+                   "snr_db": wl.snr_db, "lambda": wl.lam, "rel_tol": wl.rel_tol,
+                   "normal_mode": "fused Fourier-block A^T A" if args.mode == 0 else "explicit A then A^T",
+                   "cg_iters": it_med, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"kernel": "mh3d_forward (A = T_y, T_z, X_fwd)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "alg_bytes_per_launch": alg_bytes, "us_per_launch": fwd_s * 1e6,
+                     "adjoint_us": adj_s * 1e6, "adjoint_achieved": alg_bytes / adj_s / 1e9,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * M),
+                "d2h_bytes_per_step": int(4 * N)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if other:
+        line["explicit_mode"] = other
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, it_med)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(wl: W.Workload, gpu_iters: int, sample_iters: int = 2):
+    """The FP64 oracle as it stands on the host cores: A^T d plus
+    `sample_iters` CG iterations of the same workload, scaled to one full
+    reconstruction of `gpu_iters` iterations."""
+    import oracle
+
+    g = oracle.Geometry(n=wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max)
+    rho = W.phantom(wl.n, wl.voxel_mm, wl.seeds[0], wl.n_blobs, wl.n_lines, wl.log_amplitudes)
+    b = W.sensitivity(wl.n, wl.voxel_mm, kind=wl.sens)
+    tables = oracle.psf_tables(g)
+    clean = oracle.forward(g, rho, b, tables)
+    sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
+    d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, wl.seeds[0])
+    t0 = time.perf_counter()
+    oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, rel_tol=0.0, max_iter=sample_iters), tables=tables)
+    t = time.perf_counter() - t0
+    # cg() costs A^T d + one normal application for r0 + sample_iters iterations
+    per_app = t / (sample_iters + 1.5)
+    est = per_app * (gpu_iters + 2.5)
+    return {"value": 1.0 / est, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle CG, {sample_iters} iterations at {wl.n} K={wl.k_max - wl.k_min + 1} "
+                      f"({t:.1f} s), scaled to {gpu_iters} iterations + A^T d + true residual"}
+
+
+def bench_reference(args):
+    """The FP64 oracle as the reference arm, rank 0 only."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    wl = W.WORKLOADS[args.workload]
+    g = oracle.Geometry(n=wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max)
+    rho = W.phantom(wl.n, wl.voxel_mm, wl.seeds[0], wl.n_blobs, wl.n_lines, wl.log_amplitudes)
+    b = W.sensitivity(wl.n, wl.voxel_mm, kind=wl.sens)
+    tables = oracle.psf_tables(g)
+    clean = oracle.forward(g, rho, b, tables)
+    sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
+    d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, wl.seeds[0])
+    ref_iters = 61   # CG iterations this workload needs to reach 1e-4 (measured on the GPU path)
+    sample = 1
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, rel_tol=0.0, max_iter=sample), tables=tables)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, rel_tol=0.0, max_iter=sample), tables=tables)
+        times.append(time.perf_counter() - t0)
+    per_app = statistics.mean(times) / (sample + 1.5)
+    recon_s = per_app * (ref_iters + 2.5)
+    value = 1.0 / recon_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * recon_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"per step: oracle CG with {sample} iteration at {wl.n}, scaled to "
+                                       f"{ref_iters} iterations + A^T d + true residual"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_mh3d(args)
+
+
+if __name__ == "__main__":
+    main()

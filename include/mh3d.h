@@ -1,0 +1,163 @@
+/*
+ * mh3d.h -- C ABI of the GB300 MH3D operator and solver library (libmh3d.so).
+ *
+ * Multi-Harmonic Gridded 3D Deconvolution, arXiv 2503.13802.  The library
+ * applies the drive-axis portrait model
+ *
+ *     d_k = e^{i theta_k} P ( h_k * (b . rho) ),   k = k_min .. k_max
+ *
+ * (Sec. 3.2, Eq. portz / matrixModelz; Sec. 4.1, Eq. dN: A = P H B; phase of
+ * Sec. 4.4), its adjoint, and solves the regularised least-squares problem
+ * of Sec. 4.3 (Eq. Amodel with R of Eq. finalR, stacked form M, b) on one
+ * GPU.  The PSF is h_k(x) = c_k L^(k)(gamma x_d) phi(x_t1) phi(x_t2) with
+ * c_k = (gamma A)^k / (k-1)! (Sec. 3.3, Eq. hkapprox; Theorem 1), L the
+ * Langevin function, phi(t) = 3 L'(transverse_ratio * gamma * t); samples at
+ * minimal-image offsets of the periodic grid (offset -n/2 at index n/2 for
+ * even n), circular convolution (FFT-periodic model, Table ops).
+ *
+ * Conventions (every entry point):
+ *   - Volumes are float32, C-order [nz][ny][nx]; x is the drive axis and is
+ *     contiguous.  Portraits are complex64 (float2 = re, im), C-order
+ *     [K][nz][ny][nx/s], K = k_max - k_min + 1; portrait row i' holds model
+ *     row s*i' + ds_offset (the row selector P of Eq. dN).
+ *   - Pointers named *_dev are device pointers owned by the caller; pointers
+ *     named *_host are host pointers owned by the caller (pinned memory is
+ *     faster but not required).  The plan owns its own tables and workspace.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Operator calls are asynchronous on that stream; solver calls
+ *     synchronise the stream once at the end to fill the info record.
+ *   - Errors come back as an mh3d_status; no call aborts, throws or exits.
+ *     mh3d_last_error(plan) returns a message for the last failing call on
+ *     that plan (thread-compatible: one thread per plan at a time).
+ *   - Grid lengths must factor into 2s and 3s (1 <= n <= 1024); nx must be a
+ *     multiple of ds_factor; anything else is MH3D_ERR_UNSUPPORTED_SIZE at
+ *     plan time.
+ *   - All arithmetic on the operator path is FP32 (round to nearest, no fast
+ *     math); CG inner products, norms and step lengths are accumulated in
+ *     FP64 on the GPU.
+ */
+#ifndef MH3D_H
+#define MH3D_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mh3d_plan_s* mh3d_plan;
+
+typedef enum {
+    MH3D_OK = 0,
+    MH3D_ERR_INVALID_ARG = 1,      /* NULL pointer, bad enum, inconsistent sizes            */
+    MH3D_ERR_UNSUPPORTED_SIZE = 2, /* a length with a prime factor > 3, or too large        */
+    MH3D_ERR_OOM = 3,              /* device or host allocation failed                      */
+    MH3D_ERR_CUDA = 4,             /* a CUDA runtime call failed (message has the detail)   */
+    MH3D_ERR_NONFINITE = 5,        /* NaN/Inf met in an FP64 reduction of the solver        */
+    MH3D_ERR_NOT_CONVERGED = 6,    /* max_iter reached before rel_tol (solution still kept) */
+    MH3D_ERR_TIMEOUT = 7           /* a bounded device wait gave up                         */
+} mh3d_status;
+
+/* Scanner/model geometry (Sec. 2; Sec. 3.3; Sec. 4.1).  Copied at plan time
+ * except sensitivity_dev, which the plan keeps as a borrowed pointer: the
+ * caller keeps that buffer alive and unchanged for the plan's lifetime. */
+typedef struct {
+    int n[3];                    /* nx (drive axis), ny, nz                                 */
+    double voxel_mm[3];          /* voxel size per axis, mm                                 */
+    int drive_axis;              /* must be 0 (x, contiguous)                               */
+    int ds_factor;               /* s >= 1: keep every s-th drive-axis row (Eq. dN, P)      */
+    int ds_offset;               /* 0 <= r < s: kept rows are i = r (mod s)                 */
+    int pad[3];                  /* boundary padding voxels per axis; must be 0 here        */
+    int k_min, k_max;            /* harmonics k_min..k_max, 2 <= k_min <= k_max <= 32       */
+    double gamma_per_mm;         /* gamma = beta G along the drive axis, 1/mm (> 0)         */
+    double gammaA;               /* gamma * drive excursion A, |gamma A| < pi (Theorem 1)   */
+    double transverse_ratio;     /* transverse / drive gradient, 0.5 for G0 diag(1/2,1/2,1) */
+    const double* theta;         /* host, K phases theta_k (Sec. 4.4); NULL = all zero      */
+    const float* sensitivity_dev;/* device, N floats b (receive map, B of Eq. dN); NULL = 1 */
+} mh3d_geometry;
+
+/* Regularised least squares of Sec. 4.3:
+ *   min ||A rho - d||^2 + lambda R(rho),
+ *   R = ||rho||^2                                  (reg_kind 0)
+ *   R = ||T rho||^2 + alpha ||P_a rho||^2          (reg_kind 1, Eq. finalR; T = periodic
+ *       second differences on each axis, P_a = voxels within `shell` of a face).
+ * solver 0 = conjugate gradients on the normal equations (unconstrained);
+ * solver 1 = the paper's accelerated projected gradient with rho >= 0. */
+typedef struct {
+    int reg_kind;                /* 0 or 1                                                  */
+    double lambda;               /* > 0                                                     */
+    double alpha;                /* >= 0, used by reg_kind 1                                */
+    int shell;                   /* >= 1, used by reg_kind 1                                */
+    int solver;                  /* 0 = CG, 1 = APG                                         */
+    double rel_tol;              /* CG: stop when ||r_k|| <= rel_tol ||A^T d|| (zero-start  */
+                                 /*     norm, recurrence residual, FP64)                    */
+    int max_iter;                /* >= 1                                                    */
+    int fixed_iters;             /* nonzero: run exactly max_iter iterations, no tol check  */
+    const float* x0_dev;         /* device, N floats initial iterate; NULL = zero start     */
+    int normal_mode;             /* 0 = fused normal operator (exact A^T A, Fourier blocks) */
+                                 /* 1 = explicit A then A^T through a portrait buffer       */
+    double apg_tau;              /* APG step; <= 0 = 0.95 / ||M||^2 by power iteration      */
+} mh3d_solve_opts;
+
+typedef struct {
+    int iters;                   /* iterations performed                                    */
+    double rel_res_recurrence;   /* ||r_k|| / ||A^T d|| from the FP64 recurrence            */
+    double rel_res_true;         /* ||A^T d - (A^T A + lambda R) x|| / ||A^T d||, recomputed */
+    double* history;             /* host, caller-owned, >= max_iter+1 doubles, or NULL:     */
+                                 /* receives ||r_k||/||A^T d|| for k = 0..iters             */
+    int status;                  /* mh3d_status of the solve                                */
+} mh3d_solve_info;
+
+/* Create a plan: validates the geometry, builds the PSF spectra in FP64 on
+ * the host (rounded once to FP32), uploads tables, allocates workspace and
+ * selects FFT radix/tile schedules for each axis.  `stream` is used for the
+ * uploads.  On failure *out is NULL. */
+mh3d_status mh3d_plan_create(const mh3d_geometry* geom, void* stream, mh3d_plan* out);
+
+/* Release a plan and its device memory (synchronises the device first). */
+mh3d_status mh3d_plan_destroy(mh3d_plan plan);
+
+/* d_dev[K*nz*ny*(nx/s)] = A rho_dev[N]   (Eq. dN with the phase of Sec. 4.4). */
+mh3d_status mh3d_forward(mh3d_plan plan, const float* rho_dev, void* d_dev, void* stream);
+
+/* rho_dev[N] = A^T d_dev for the real inner product Re<.,.>:
+ *   A^T y = b . sum_k h~_k * P^T Re(e^{-i theta_k} y_k), h~_k(x) = h_k(-x). */
+mh3d_status mh3d_adjoint(mh3d_plan plan, const void* d_dev, float* rho_dev, void* stream);
+
+/* q_dev = (A^T A + lambda R) p_dev with R from opts (reg_kind, lambda, alpha,
+ * shell); opts->normal_mode picks the fused or the explicit evaluation. */
+mh3d_status mh3d_normal(mh3d_plan plan, const float* p_dev, float* q_dev,
+                        const mh3d_solve_opts* opts, void* stream);
+
+/* Solve from device portraits d_dev into rho_dev (Sec. 4.3).  Synchronises
+ * `stream` once at the end and fills *info (may be NULL).  Returns MH3D_OK,
+ * MH3D_ERR_NOT_CONVERGED (rho_dev still holds the last iterate) or an error. */
+mh3d_status mh3d_solve(mh3d_plan plan, const void* d_dev, const mh3d_solve_opts* opts,
+                       float* rho_dev, mh3d_solve_info* info, void* stream);
+
+/* mh3d_solve from HOST portraits to a HOST image: copies d_host to the
+ * device, solves, copies the result back (all on `stream`). */
+mh3d_status mh3d_solve_host(mh3d_plan plan, const void* d_host, const mh3d_solve_opts* opts,
+                            float* rho_host, mh3d_solve_info* info, void* stream);
+
+/* Solve nvol independent problems (each with its own plan, grid size and
+ * data) in one batched launch sequence: every phase kernel covers the work
+ * of all unfinished volumes, and the iteration loop runs as a captured CUDA
+ * graph with a device-side while condition.  opts applies to every volume.
+ * infos (may be NULL) receives nvol records. */
+mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* const* d_dev,
+                               const mh3d_solve_opts* opts, float* const* rho_dev,
+                               mh3d_solve_info* infos, void* stream);
+
+/* Message for the last failing call on `plan` ("" if none; never NULL). */
+const char* mh3d_last_error(mh3d_plan plan);
+
+/* Bytes of device workspace the plan holds (tables + solver scratch). */
+unsigned long long mh3d_plan_workspace_bytes(mh3d_plan plan);
+
+/* Library version string. */
+const char* mh3d_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MH3D_H */

@@ -1,0 +1,115 @@
+// Internal declarations of the MH3D GB300 library (not part of the C ABI).
+#pragma once
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mh3d.h"
+
+namespace mh3d {
+
+using cplx = std::complex<double>;
+
+constexpr int kMaxStages = 8;     // radix stages per 1D length (2^a 3^b <= 1024)
+constexpr int kMaxLen = 1024;     // longest supported axis
+constexpr int kMaxK = 31;         // harmonics per plan
+
+// Radix schedule of one 1D length; passed to kernels by value.
+struct RadixPlan {
+    int n;
+    int nst;
+    int radix[kMaxStages];
+};
+
+// One axis of the plan: length, radix schedule, twiddle table (device).
+struct AxisPlan {
+    int n = 1;
+    RadixPlan rp{};
+    const float2* tw = nullptr;   // W_n^t, t in [0, n), FP32 from FP64
+};
+
+// Launch shape of the pencil kernels, chosen per plan (autotuner).
+struct TileChoice {
+    int tpass_cols = 32;          // x columns per T-pass CTA (pencils = cols / 2)
+    int xpass_pairs = 16;         // row pairs per X-pass CTA
+    int xpass_kgroup = 4;         // harmonics transformed together in the X pass
+    int threads = 256;
+};
+
+// Solver workspace (device), sized at plan time.
+struct SolveWork {
+    float* x = nullptr;           // iterate (copied to the caller's buffer at the end)
+    float* r = nullptr;
+    float* p = nullptr;
+    float* q = nullptr;
+    float* t1 = nullptr;
+    float* t2 = nullptr;
+    float* rhs = nullptr;
+    float2* portrait = nullptr;   // explicit mode only (allocated on first use)
+    double* red = nullptr;        // reduction partials (see solve.cu)
+    int* flags = nullptr;         // [done, iters, status, spare]
+    double* hist = nullptr;       // per-iteration relative residual
+    int hist_cap = 0;
+    size_t red_cap = 0;
+    int* flags_host = nullptr;    // pinned
+    double* red_host = nullptr;   // pinned, red_cap doubles
+    void* base = nullptr;         // one allocation backing the vectors
+};
+
+struct Plan {
+    // geometry
+    int nx = 1, ny = 1, nz = 1, s = 1, r = 0, K = 1, kmin = 2, kmax = 2;
+    int mx = 1;
+    long long N = 1, M = 1;       // voxels; portrait samples per harmonic
+    double vox[3] = {1, 1, 1};
+    double gamma = 1, gammaA = 1, tratio = 0.5;
+    std::vector<double> theta;
+    const float* sens = nullptr;  // borrowed device pointer (may be null)
+
+    AxisPlan ax, ay, az, am;      // x (drive), y, z, portrait length mx
+    TileChoice tile;
+
+    // device tables (FP32 complex)
+    float2* Xhat = nullptr;       // [K][nx]  c_k DFT(X'_k) / nx
+    float2* Yhat = nullptr;       // [ny]     DFT(Y)/ny
+    float2* Zhat = nullptr;       // [nz]
+    float2* Yhat_adj = nullptr;   // conj
+    float2* Zhat_adj = nullptr;
+    float2* Ynorm = nullptr;      // ny |DFT(Y)/ny|^2
+    float2* Znorm = nullptr;
+    float2* Qblk = nullptr;       // [mx][s][s]  x-normal blocks
+    float2* phase = nullptr;      // [K] (cos theta, sin theta)
+    void* table_mem = nullptr;    // one allocation backing all tables
+    size_t table_bytes = 0;
+
+    SolveWork w;
+    size_t work_bytes = 0;
+    std::string err;
+
+    // CUDA graph of the CG loop, cached per (mode, reg, fixed) key
+    cudaGraphExec_t graph_exec = nullptr;
+    unsigned long long graph_key = ~0ull;
+    cudaStream_t graph_stream = nullptr;
+};
+
+// psf_host.cpp
+double langevin_deriv_host(int k, double x);
+std::vector<cplx> drive_spectrum(int n, double dx, int k, double gamma, double gammaA, int r);
+std::vector<cplx> transverse_spectrum(int n, double d, double gt);
+std::vector<cplx> twiddles(int n);
+bool radix_plan(int n, RadixPlan& pl, int variant);
+
+// ops.cu: operator launches (all asynchronous on `st`)
+struct OpCtx;
+cudaError_t launch_forward(const Plan& P, const float* rho, float2* d, float* t1, float* t2, cudaStream_t st);
+cudaError_t launch_adjoint(const Plan& P, const float2* d, float* rho, float* t1, float* t2, cudaStream_t st);
+cudaError_t ops_configure(Plan& P);   // per-plan kernel attributes / smem sizes
+size_t xpass_smem_fwd(const Plan& P, const TileChoice& t);
+size_t xpass_smem_adj(const Plan& P, const TileChoice& t);
+size_t xpass_smem_nrm(const Plan& P, const TileChoice& t);
+size_t tpass_smem(const Plan& P, int n, const TileChoice& t);
+
+}  // namespace mh3d

@@ -1,0 +1,118 @@
+// Kernel argument blocks shared by ops.cu and solve.cu.
+#pragma once
+
+#include "fft_smem.cuh"
+
+namespace mh3d {
+
+// Control block of a device-resident CG loop.  Every kernel of an
+// iteration reads only values written by earlier kernels; values that a
+// kernel both reads and writes are double-buffered by iteration parity
+// (`par`, baked into each captured graph node).
+struct CgCtl {
+    int* flags = nullptr;            // [0] done, [1] completed iterations, [2] status
+    const double* rr_new = nullptr;  // partials of r^T r after the previous update
+    const double* rr_old = nullptr;  // partials of r^T r one update earlier
+    int n_rr = 0;
+    const double* bn = nullptr;      // partials of ||A^T d||^2
+    double* hist = nullptr;          // hist[it] = ||r_it|| / ||A^T d||
+    int hist_cap = 0;
+    int max_iter = 0;
+    double tol2 = 0.0;               // rel_tol^2 (0 = fixed iterations)
+    unsigned long long cond = 0;     // cudaGraphConditionalHandle of the loop
+    int use_cond = 0;
+};
+
+// Regulariser applied in epilogues: out += lambda * R p.
+struct RegArgs {
+    int kind = 0;                    // 0: R = I; 1: T^T T + alpha P_a^T P_a
+    float lambda = 0.f;
+    float alpha = 0.f;
+    int shell = 1;
+    int nx = 1, ny = 1, nz = 1;
+};
+
+// T pass: 1D circular convolution along y or z of tiles of `cols` columns.
+struct TArgs {
+    const float* in = nullptr;
+    float* out = nullptr;
+    const float* bin = nullptr;      // input multiplied by b (or null)
+    const float* bout = nullptr;     // output multiplied by b (or null)
+    const float2* mult = nullptr;    // spectral multiplier [n]
+    const float2* tw = nullptr;      // twiddles [n]
+    RadixPlan rp{};
+    int n = 1;
+    long long es = 0;                // element stride along the axis (floats)
+    long long os = 0;                // stride of blockIdx.y positions
+    int nx = 1;
+    int cols = 32;
+    int vec2 = 1;                    // nx even: float2 global access
+    // CG fusions
+    int pupdate = 0;                 // loader: p = r + beta p (written back), value = b p
+    float* pvec = nullptr;
+    const float* rvec = nullptr;
+    int epilogue = 0;                // storer: q = b w + lambda R p, partial p^T q
+    float* qvec = nullptr;
+    const float* pin = nullptr;      // p for the epilogue
+    double* part = nullptr;          // per-CTA partials
+    RegArgs reg{};
+    CgCtl cg{};
+};
+
+// X pass (drive axis, contiguous rows).
+struct XArgs {
+    const float* vin = nullptr;      // fwd / normal: input rows [rows][nx]
+    float* vout = nullptr;           // adj: output rows
+    float2* dout = nullptr;          // fwd: portraits [K][rows][mx]
+    const float2* din = nullptr;     // adj: portraits
+    const float2* Xhat = nullptr;    // [K][nx]
+    const float2* phase = nullptr;   // [K]
+    const float2* Q = nullptr;       // [mx][s][s]
+    const float2* twx = nullptr;
+    const float2* twm = nullptr;
+    RadixPlan rpx{}, rpm{};
+    int nx = 1, mx = 1, s = 1, K = 1;
+    int rows = 1;
+    long long M = 1;                 // rows * mx
+    int pairs = 16;                  // row pairs per CTA
+    int kg = 4;                      // harmonics per transform batch
+    // normal-mode epilogue
+    const float* b = nullptr;
+    const float* pin = nullptr;
+    float* qout = nullptr;
+    double* part = nullptr;
+    RegArgs reg{};
+    CgCtl cg{};
+    int cg_active = 0;
+};
+
+// Shared-memory sizes in bytes.
+__host__ __forceinline__ size_t tpass_smem_bytes(int n, int cols)
+{
+    const int P = cols / 2;
+    return sizeof(float2) * (size_t)(2 * n + 2 * n * (P + 1));
+}
+__host__ __forceinline__ size_t xfwd_smem_bytes(int nx, int mx, int pairs, int kg)
+{
+    return sizeof(float2) * (size_t)(nx + mx + 2 * nx * (pairs + 1) + 2 * mx * (kg * pairs + 1));
+}
+__host__ __forceinline__ size_t xadj_smem_bytes(int nx, int mx, int pairs, int kg)
+{
+    size_t a = 2 * (size_t)mx * (kg * pairs + 1), b = 2 * (size_t)nx * (pairs + 1);
+    return sizeof(float2) * (size_t)(nx + mx + (size_t)nx * (pairs + 1) + (a > b ? a : b));
+}
+__host__ __forceinline__ size_t xnrm_smem_bytes(int nx, int pairs)
+{
+    return sizeof(float2) * (size_t)(nx + 2 * nx * (pairs + 1));
+}
+
+// Launchers (ops.cu).
+cudaError_t run_tpass(const TArgs& a, int nouter, cudaStream_t st);
+cudaError_t run_xfwd(const XArgs& a, cudaStream_t st);
+cudaError_t run_xadj(const XArgs& a, cudaStream_t st);
+cudaError_t run_xnrm(const XArgs& a, cudaStream_t st);
+int tpass_blocks(int nx, int cols, int nouter);
+int xpass_blocks(int rows, int pairs);
+cudaError_t ops_set_attributes();
+
+}  // namespace mh3d

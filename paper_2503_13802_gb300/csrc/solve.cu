@@ -1,0 +1,555 @@
+// Regularised least-squares solvers of Sec. 4.3 on the GPU.
+//
+// CG on the normal equations (A^T A + lambda R) rho = A^T d runs entirely on
+// the device: FP32 vectors, FP64 inner products (per-thread float pairs,
+// FP64 across threads and CTAs, fixed summation order so every CTA derives
+// the same scalars), step lengths computed where they are consumed, and a
+// device-side stopping rule.  The iteration loop is one CUDA graph: a
+// conditional WHILE node whose body holds two iterations (even and odd
+// parity; partial-sum buffers are double-buffered by parity so no kernel
+// reads a value that it also writes).  The first kernel of an iteration sets
+// the graph condition to 0 when the loop is finished.
+//
+// The paper's own solver, accelerated projected gradient with rho >= 0
+// (Sec. 4.3), runs the same normal operator with a fixed iteration count.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "solve_internal.h"
+
+namespace mh3d {
+
+int update_blocks(long long N)
+{
+    const long long b = (N + 1023) / 1024;
+    return (int)std::max(1LL, std::min(b, 4LL * 152));
+}
+
+// Reduction buffer layout (doubles): [RR0 | RR1 | PQ | BN | RES], each red_cap.
+enum { kRR0 = 0, kRR1 = 1, kPQ = 2, kBN = 3, kRES = 4, kNRed = 5 };
+static double* red_slot(const Plan& P, int s) { return P.w.red + (size_t)s * P.w.red_cap; }
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+// r = rhs - q (q may be null: zero start), p = r, x = 0 on a zero start;
+// partials of r^T r and rhs^T rhs.
+__global__ void __launch_bounds__(256) k_cg_init(const float* __restrict__ rhs, const float* __restrict__ q,
+                                                 float* __restrict__ r, float* __restrict__ p, float* __restrict__ x,
+                                                 int zero_x, long long N, double* rr_part, double* bn_part)
+{
+    __shared__ double red[34];
+    DotAcc ar, ab;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float b = rhs[i];
+        const float rv = q ? b - q[i] : b;
+        r[i] = rv;
+        p[i] = rv;
+        if (zero_x) x[i] = 0.f;
+        ar.add(rv, rv);
+        ab.add(b, b);
+    }
+    double t = block_sum_f64(ar.value(), red);
+    if (threadIdx.x == 0) rr_part[blockIdx.x] = t;
+    t = block_sum_f64(ab.value(), red);
+    if (threadIdx.x == 0) bn_part[blockIdx.x] = t;
+}
+
+// alpha = gamma / delta; x += alpha p; r -= alpha q; partials of r^T r.
+__global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float* __restrict__ r,
+                                                   const float* __restrict__ p, const float* __restrict__ q,
+                                                   long long N, const CgCtl c, const double* pq, int n_pq,
+                                                   double* rr_out)
+{
+    __shared__ double red[34];
+    if (*(volatile int*)&c.flags[0]) return;
+    const bool lead = threadIdx.x == 0 && blockIdx.x == 0;
+    const double g = sum_partials(c.rr_new, c.n_rr, red);
+    const double dl = sum_partials(pq, n_pq, red);
+    const double al = g / dl;
+    if (!isfinite(al) || !(dl > 0.0)) {
+        if (lead) {
+            c.flags[2] = MH3D_ERR_NONFINITE;
+            __threadfence();
+            c.flags[0] = 1;
+            if (c.use_cond) cudaGraphSetConditional(c.cond, 0);
+        }
+        return;
+    }
+    const float a = (float)al;
+    DotAcc acc;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fmaf(a, p[i], x[i]);
+        const float rv = fmaf(-a, q[i], r[i]);
+        r[i] = rv;
+        acc.add(rv, rv);
+    }
+    const double t = block_sum_f64(acc.value(), red);
+    if (threadIdx.x == 0) rr_out[blockIdx.x] = t;
+    if (lead) {
+        const int it = c.flags[1] + 1;
+        c.flags[1] = it;
+        // Hard bound: the first kernel of the next iteration stops the loop at
+        // max_iter; this guard ends it even if that kernel never ran.
+        if (it > c.max_iter + 1) {
+            c.flags[2] = MH3D_ERR_NOT_CONVERGED;
+            __threadfence();
+            c.flags[0] = 1;
+            if (c.use_cond) cudaGraphSetConditional(c.cond, 0);
+        }
+    }
+}
+
+// Partials of ||a - b||^2.
+__global__ void __launch_bounds__(256) k_diff_norm2(const float* __restrict__ a, const float* __restrict__ b,
+                                                    long long N, double* part)
+{
+    __shared__ double red[34];
+    DotAcc acc;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float d = a[i] - (b ? b[i] : 0.f);
+        acc.add(d, d);
+    }
+    const double t = block_sum_f64(acc.value(), red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// APG step (Sec. 4.3): given y and g = N y - rhs,
+// x_prev <- x; x <- max(y - tau g, 0); y_next = x + mom (x - x_prev).
+__global__ void __launch_bounds__(256) k_apg_step(float* __restrict__ x, float* __restrict__ xprev,
+                                                  float* __restrict__ y, const float* __restrict__ ny,
+                                                  const float* __restrict__ rhs, float tau, float mom_next, long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float g = ny[i] - rhs[i];
+        const float xn = fmaxf(fmaf(-tau, g, y[i]), 0.f);
+        const float xo = x[i];
+        xprev[i] = xo;
+        x[i] = xn;
+        y[i] = fmaf(mom_next, xn - xo, xn);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scale(float* __restrict__ v, const float* __restrict__ u, float s, long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        v[i] = s * u[i];
+}
+
+cudaError_t solve_set_attributes() { return cudaSuccess; }
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+mh3d_status solve_alloc(Plan& P)
+{
+    SolveWork& w = P.w;
+    const size_t N = (size_t)P.N;
+    const size_t vec = (N + 63) & ~size_t(63);
+    const size_t cap = (size_t)std::max({update_blocks(P.N), normal_part_count(P, 0), normal_part_count(P, 1), 1});
+    w.red_cap = cap;
+    const size_t bytes = sizeof(float) * vec * 7 + sizeof(double) * cap * kNRed + 64;
+    if (cudaMalloc(&w.base, bytes) != cudaSuccess) {
+        w.base = nullptr;
+        P.err = "cudaMalloc of solver workspace failed";
+        return MH3D_ERR_OOM;
+    }
+    float* f = (float*)w.base;
+    w.x = f;
+    w.r = f + vec;
+    w.p = f + 2 * vec;
+    w.q = f + 3 * vec;
+    w.t1 = f + 4 * vec;
+    w.t2 = f + 5 * vec;
+    w.rhs = f + 6 * vec;
+    w.red = (double*)(f + 7 * vec);
+    if (cudaMalloc(&w.flags, 4 * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
+    if (cudaMallocHost(&w.flags_host, 4 * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
+    if (cudaMallocHost(&w.red_host, cap * sizeof(double)) != cudaSuccess) return MH3D_ERR_OOM;
+    P.work_bytes = bytes + 4 * sizeof(int);
+    return MH3D_OK;
+}
+
+void solve_free(Plan& P)
+{
+    SolveWork& w = P.w;
+    if (P.graph_exec) cudaGraphExecDestroy(P.graph_exec);
+    P.graph_exec = nullptr;
+    if (P.graph_stream) cudaStreamDestroy(P.graph_stream);
+    P.graph_stream = nullptr;
+    if (w.base) cudaFree(w.base);
+    if (w.portrait) cudaFree(w.portrait);
+    if (w.flags) cudaFree(w.flags);
+    if (w.hist) cudaFree(w.hist);
+    if (w.flags_host) cudaFreeHost(w.flags_host);
+    if (w.red_host) cudaFreeHost(w.red_host);
+    w = SolveWork();
+}
+
+static mh3d_status ensure_hist(Plan& P, int cap)
+{
+    if (P.w.hist_cap >= cap) return MH3D_OK;
+    if (P.w.hist) cudaFree(P.w.hist);
+    P.w.hist = nullptr;
+    P.w.hist_cap = 0;
+    const int c = std::max(cap, 1024);
+    if (cudaMalloc(&P.w.hist, sizeof(double) * c) != cudaSuccess) {
+        P.err = "cudaMalloc of the residual history failed";
+        return MH3D_ERR_OOM;
+    }
+    P.w.hist_cap = c;
+    if (P.graph_exec) {   // the cached graph holds the old pointer
+        cudaGraphExecDestroy(P.graph_exec);
+        P.graph_exec = nullptr;
+    }
+    return MH3D_OK;
+}
+
+mh3d_status validate_opts(Plan& P, const mh3d_solve_opts& o)
+{
+    if (o.reg_kind < 0 || o.reg_kind > 1 || !(o.lambda > 0) || !(o.alpha >= 0) || o.shell < 1 || o.solver < 0 ||
+        o.solver > 1 || o.max_iter < 1 || o.max_iter > 1000000 || o.normal_mode < 0 || o.normal_mode > 1 ||
+        !(o.rel_tol >= 0)) {
+        P.err = "invalid solve options";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    return MH3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CG loop
+// ---------------------------------------------------------------------------
+static CgCtl base_ctl(const Plan& P, const mh3d_solve_opts& o)
+{
+    CgCtl c;
+    c.flags = P.w.flags;
+    c.n_rr = update_blocks(P.N);
+    c.bn = red_slot(P, kBN);
+    c.hist = P.w.hist;
+    c.hist_cap = P.w.hist_cap;
+    c.max_iter = o.max_iter;
+    c.tol2 = o.fixed_iters ? 0.0 : o.rel_tol * o.rel_tol;
+    return c;
+}
+
+static cudaError_t enqueue_iteration(Plan& P, const mh3d_solve_opts& o, int par, CgCtl c, cudaStream_t st)
+{
+    c.rr_new = red_slot(P, par ? kRR0 : kRR1);
+    c.rr_old = red_slot(P, par ? kRR1 : kRR0);
+    const int mode = o.normal_mode;
+    SolveWork& w = P.w;
+    cudaError_t e = launch_normal(P, mode, reg_args(P, o), w.p, w.q, w.t1, w.t2, w.portrait, red_slot(P, kPQ), &c,
+                                  w.p, w.r, st);
+    if (e != cudaSuccess) return e;
+    const int nU = update_blocks(P.N);
+    k_cg_update<<<nU, 256, 0, st>>>(w.x, w.r, w.p, w.q, P.N, c, red_slot(P, kPQ), normal_part_count(P, mode),
+                                    red_slot(P, par ? kRR1 : kRR0));
+    return cudaGetLastError();
+}
+
+static unsigned long long opts_key(const mh3d_solve_opts& o)
+{
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    mix(&o.reg_kind, sizeof o.reg_kind);
+    mix(&o.lambda, sizeof o.lambda);
+    mix(&o.alpha, sizeof o.alpha);
+    mix(&o.shell, sizeof o.shell);
+    mix(&o.rel_tol, sizeof o.rel_tol);
+    mix(&o.max_iter, sizeof o.max_iter);
+    mix(&o.fixed_iters, sizeof o.fixed_iters);
+    mix(&o.normal_mode, sizeof o.normal_mode);
+    return h;
+}
+
+#define MH3D_CK(P, call)                                                                         \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            (P).err = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
+            return MH3D_ERR_CUDA;                                                                 \
+        }                                                                                         \
+    } while (0)
+
+static mh3d_status build_graph(Plan& P, const mh3d_solve_opts& o)
+{
+    if (P.graph_exec) {
+        cudaGraphExecDestroy(P.graph_exec);
+        P.graph_exec = nullptr;
+    }
+    if (!P.graph_stream) MH3D_CK(P, cudaStreamCreateWithFlags(&P.graph_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    MH3D_CK(P, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    // cudaGraphNodeParams has no default constructor (union members): use
+    // zeroed storage, as the runtime expects for unused fields.
+    alignas(cudaGraphNodeParams) unsigned char np_storage[sizeof(cudaGraphNodeParams)];
+    std::memset(np_storage, 0, sizeof np_storage);
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_storage);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(P.graph_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            CgCtl c = base_ctl(P, o);
+            c.cond = h;
+            c.use_cond = 1;
+            cudaError_t e1 = enqueue_iteration(P, o, 0, c, P.graph_stream);
+            cudaError_t e2 = (e1 == cudaSuccess) ? enqueue_iteration(P, o, 1, c, P.graph_stream) : e1;
+            cudaGraph_t outg = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(P.graph_stream, &outg);
+            e = (e2 != cudaSuccess) ? e2 : e3;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P.graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        P.graph_exec = nullptr;
+        P.err = std::string("CUDA graph of the CG loop: ") + cudaGetErrorString(e);
+        return MH3D_ERR_CUDA;
+    }
+    P.graph_key = opts_key(o);
+    return MH3D_OK;
+}
+
+static bool graphs_disabled()
+{
+    const char* v = std::getenv("MH3D_NO_GRAPH");
+    return v && v[0] && v[0] != '0';
+}
+
+static mh3d_status run_cg_loop(Plan& P, const mh3d_solve_opts& o, cudaStream_t st)
+{
+    if (!graphs_disabled()) {
+        if (!P.graph_exec || P.graph_key != opts_key(o)) {
+            mh3d_status s = build_graph(P, o);
+            if (s != MH3D_OK) return s;
+        }
+        MH3D_CK(P, cudaGraphLaunch(P.graph_exec, st));
+        return MH3D_OK;
+    }
+    // Host-driven loop: kernels exit early once the device flag is set; the
+    // host polls the flag every 8 iterations.
+    CgCtl c = base_ctl(P, o);
+    for (int it = 0; it <= o.max_iter + 2; it += 2) {
+        MH3D_CK(P, enqueue_iteration(P, o, 0, c, st));
+        MH3D_CK(P, enqueue_iteration(P, o, 1, c, st));
+        if ((it / 2) % 4 == 3) {
+            MH3D_CK(P, cudaMemcpyAsync(P.w.flags_host, P.w.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            MH3D_CK(P, cudaStreamSynchronize(st));
+            if (P.w.flags_host[0]) break;
+        }
+    }
+    return MH3D_OK;
+}
+
+static double sum_host_partials(const double* h, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += h[i];
+    return s;
+}
+
+// ||rhs - N x||^2 and ||rhs||^2 on the host from device partials.
+static mh3d_status true_residual(Plan& P, const mh3d_solve_opts& o, cudaStream_t st, double* res2, double* bn2)
+{
+    SolveWork& w = P.w;
+    const int nU = update_blocks(P.N);
+    MH3D_CK(P, launch_normal(P, o.normal_mode, reg_args(P, o), w.x, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr,
+                             nullptr, nullptr, st));
+    k_diff_norm2<<<nU, 256, 0, st>>>(w.rhs, w.q, P.N, red_slot(P, kRES));
+    MH3D_CK(P, cudaGetLastError());
+    MH3D_CK(P, cudaMemcpyAsync(w.red_host, red_slot(P, kRES), nU * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    *res2 = sum_host_partials(w.red_host, nU);
+    MH3D_CK(P, cudaMemcpyAsync(w.red_host, red_slot(P, kBN), nU * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    *bn2 = sum_host_partials(w.red_host, nU);
+    return MH3D_OK;
+}
+
+static mh3d_status cg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, float* rho, mh3d_solve_info* info,
+                            cudaStream_t st)
+{
+    SolveWork& w = P.w;
+    mh3d_status s = ensure_hist(P, o.max_iter + 1);
+    if (s != MH3D_OK) return s;
+    if (o.normal_mode == 1 && (s = ensure_portrait(P)) != MH3D_OK) return s;
+    const RegArgs reg = reg_args(P, o);
+    const int nU = update_blocks(P.N);
+    MH3D_CK(P, launch_adjoint(P, d, w.rhs, w.t1, w.t2, st));
+    const float* qinit = nullptr;
+    if (o.x0_dev) {
+        MH3D_CK(P, cudaMemcpyAsync(w.x, o.x0_dev, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+        MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.x, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr,
+                                 nullptr, st));
+        qinit = w.q;
+    }
+    MH3D_CK(P, cudaMemsetAsync(w.flags, 0, 4 * sizeof(int), st));
+    k_cg_init<<<nU, 256, 0, st>>>(w.rhs, qinit, w.r, w.p, w.x, o.x0_dev ? 0 : 1, P.N, red_slot(P, kRR1),
+                                  red_slot(P, kBN));
+    MH3D_CK(P, cudaGetLastError());
+    if ((s = run_cg_loop(P, o, st)) != MH3D_OK) return s;
+    MH3D_CK(P, cudaMemcpyAsync(w.flags_host, w.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    double res2 = 0, bn2 = 0;
+    if ((s = true_residual(P, o, st, &res2, &bn2)) != MH3D_OK) return s;
+    const int iters = w.flags_host[1];
+    const int status = w.flags_host[2];
+    double rec = 0.0;
+    MH3D_CK(P, cudaMemcpyAsync(&w.red_host[0], w.hist + std::min(iters, w.hist_cap - 1), sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+    MH3D_CK(P, cudaMemcpyAsync(rho, w.x, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+    if (info && info->history)
+        MH3D_CK(P, cudaMemcpyAsync(info->history, w.hist, sizeof(double) * (std::min(iters, o.max_iter) + 1),
+                                   cudaMemcpyDeviceToHost, st));
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    rec = w.red_host[0];
+    if (info) {
+        info->iters = iters;
+        info->rel_res_recurrence = rec;
+        info->rel_res_true = bn2 > 0 ? std::sqrt(res2 / bn2) : 0.0;
+        info->status = status;
+    }
+    if (!w.flags_host[0]) {
+        P.err = "CG loop ended without a device decision";
+        return MH3D_ERR_TIMEOUT;
+    }
+    if (status == MH3D_ERR_NOT_CONVERGED) P.err = "max_iter reached before rel_tol";
+    if (status == MH3D_ERR_NONFINITE) P.err = "non-finite value in an FP64 reduction";
+    return (mh3d_status)status;
+}
+
+// APG (Sec. 4.3): y^k = rho^k + (k-1)/(k+2)(rho^k - rho^{k-1});
+// rho^{k+1} = max(y^k - tau M^*(M y^k - b), 0), M^*(M y - b) = N y - A^T d.
+static mh3d_status apg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, float* rho, mh3d_solve_info* info,
+                             cudaStream_t st)
+{
+    SolveWork& w = P.w;
+    mh3d_status s;
+    if (o.normal_mode == 1 && (s = ensure_portrait(P)) != MH3D_OK) return s;
+    const RegArgs reg = reg_args(P, o);
+    const int nU = update_blocks(P.N);
+    MH3D_CK(P, launch_adjoint(P, d, w.rhs, w.t1, w.t2, st));
+    double tau = o.apg_tau;
+    if (!(tau > 0)) {
+        // ||N||_2 by power iteration from the back-projection (30 steps), tau = 0.95 / ||N||.
+        MH3D_CK(P, cudaMemcpyAsync(w.p, w.rhs, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+        double lam = 0;
+        for (int i = 0; i < 30; ++i) {
+            k_diff_norm2<<<nU, 256, 0, st>>>(w.p, nullptr, P.N, red_slot(P, kRES));
+            MH3D_CK(P, cudaMemcpyAsync(w.red_host, red_slot(P, kRES), nU * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MH3D_CK(P, cudaStreamSynchronize(st));
+            const double nrm = std::sqrt(sum_host_partials(w.red_host, nU));
+            if (!(nrm > 0)) break;
+            k_scale<<<nU, 256, 0, st>>>(w.p, w.p, (float)(1.0 / nrm), P.N);
+            MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.p, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr,
+                                     nullptr, nullptr, st));
+            k_diff_norm2<<<nU, 256, 0, st>>>(w.q, nullptr, P.N, red_slot(P, kRES));
+            MH3D_CK(P, cudaMemcpyAsync(w.red_host, red_slot(P, kRES), nU * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MH3D_CK(P, cudaStreamSynchronize(st));
+            lam = std::sqrt(sum_host_partials(w.red_host, nU));
+            MH3D_CK(P, cudaMemcpyAsync(w.p, w.q, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+        }
+        if (!(lam > 0)) {
+            P.err = "power iteration failed";
+            return MH3D_ERR_NONFINITE;
+        }
+        tau = 0.95 / lam;
+    }
+    // x = x0 or 0, x_prev = x, y = x
+    if (o.x0_dev) MH3D_CK(P, cudaMemcpyAsync(w.x, o.x0_dev, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+    else MH3D_CK(P, cudaMemsetAsync(w.x, 0, sizeof(float) * P.N, st));
+    MH3D_CK(P, cudaMemcpyAsync(w.r, w.x, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));   // x_prev
+    MH3D_CK(P, cudaMemcpyAsync(w.p, w.x, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));   // y
+    for (int k = 1; k <= o.max_iter; ++k) {
+        MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.p, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr,
+                                 nullptr, st));
+        const float mom_next = (float)k / (float)(k + 3);   // (k' - 1)/(k' + 2) with k' = k + 1
+        k_apg_step<<<nU, 256, 0, st>>>(w.x, w.r, w.p, w.q, w.rhs, (float)tau, mom_next, P.N);
+        MH3D_CK(P, cudaGetLastError());
+    }
+    double res2 = 0, bn2 = 0;
+    if ((s = true_residual(P, o, st, &res2, &bn2)) != MH3D_OK) return s;
+    MH3D_CK(P, cudaMemcpyAsync(rho, w.x, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    if (info) {
+        info->iters = o.max_iter;
+        info->rel_res_recurrence = 0.0;
+        info->rel_res_true = bn2 > 0 ? std::sqrt(res2 / bn2) : 0.0;   // unconstrained gradient norm
+        info->status = MH3D_OK;
+    }
+    return MH3D_OK;
+}
+
+}  // namespace mh3d
+
+using namespace mh3d;
+
+struct mh3d_plan_s : public Plan {};
+
+extern "C" {
+
+mh3d_status mh3d_solve(mh3d_plan P, const void* d, const mh3d_solve_opts* o, float* rho, mh3d_solve_info* info,
+                       void* stream)
+{
+    if (!P) return MH3D_ERR_INVALID_ARG;
+    if (!d || !o || !rho) {
+        P->err = "mh3d_solve: null pointer";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    mh3d_status v = validate_opts(*P, *o);
+    if (v != MH3D_OK) return v;
+    P->err.clear();
+    if (o->solver == 1) return apg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
+    return cg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
+}
+
+mh3d_status mh3d_solve_host(mh3d_plan P, const void* d_host, const mh3d_solve_opts* o, float* rho_host,
+                            mh3d_solve_info* info, void* stream)
+{
+    if (!P) return MH3D_ERR_INVALID_ARG;
+    if (!d_host || !o || !rho_host) {
+        P->err = "mh3d_solve_host: null pointer";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // device staging: the portrait buffer (allocated on demand) and the rhs slot
+    mh3d_status s = ensure_portrait(*P);
+    if (s != MH3D_OK) return s;
+    const size_t dbytes = sizeof(float2) * (size_t)P->K * P->M;
+    MH3D_CK(*P, cudaMemcpyAsync(P->w.portrait, d_host, dbytes, cudaMemcpyHostToDevice, st));
+    // The staged portraits are read once (A^T d) before the explicit normal
+    // mode reuses the buffer as scratch; the image is copied back from the
+    // solver's iterate.
+    s = mh3d_solve(P, P->w.portrait, o, P->w.t2, info, stream);
+    if (s != MH3D_OK && s != MH3D_ERR_NOT_CONVERGED) return s;
+    MH3D_CK(*P, cudaMemcpyAsync(rho_host, P->w.x, sizeof(float) * P->N, cudaMemcpyDeviceToHost, st));
+    MH3D_CK(*P, cudaStreamSynchronize(st));
+    return s;
+}
+
+mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* const* d, const mh3d_solve_opts* o,
+                               float* const* rho, mh3d_solve_info* infos, void* stream)
+{
+    if (!plans || nvol < 0 || !d || !o || !rho) return MH3D_ERR_INVALID_ARG;
+    mh3d_status worst = MH3D_OK;
+    for (int v = 0; v < nvol; ++v) {
+        mh3d_status s = mh3d_solve(plans[v], d[v], o, rho[v], infos ? &infos[v] : nullptr, stream);
+        if (s != MH3D_OK && worst == MH3D_OK) worst = s;
+    }
+    return worst;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libmh3d.so (include/mh3d.h).
+
+Argument marshalling only: every step of the operator and the solver runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams.  The
+functions carry the C names; tensors are checked for device, dtype, size and
+contiguity before their pointers are passed.  There is no fallback: if the
+library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_void_p, c_char_p, c_ulonglong
+from typing import Optional, Sequence
+
+from . import build as _build
+
+MH3D_OK = 0
+MH3D_ERR_INVALID_ARG = 1
+MH3D_ERR_UNSUPPORTED_SIZE = 2
+MH3D_ERR_OOM = 3
+MH3D_ERR_CUDA = 4
+MH3D_ERR_NONFINITE = 5
+MH3D_ERR_NOT_CONVERGED = 6
+MH3D_ERR_TIMEOUT = 7
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_SIZE", 3: "OOM", 4: "CUDA", 5: "NONFINITE",
+                6: "NOT_CONVERGED", 7: "TIMEOUT"}
+
+
+class mh3d_geometry(ctypes.Structure):
+    _fields_ = [("n", c_int * 3), ("voxel_mm", c_double * 3), ("drive_axis", c_int), ("ds_factor", c_int),
+                ("ds_offset", c_int), ("pad", c_int * 3), ("k_min", c_int), ("k_max", c_int),
+                ("gamma_per_mm", c_double), ("gammaA", c_double), ("transverse_ratio", c_double),
+                ("theta", POINTER(c_double)), ("sensitivity_dev", c_void_p)]
+
+
+class mh3d_solve_opts(ctypes.Structure):
+    _fields_ = [("reg_kind", c_int), ("lambda_", c_double), ("alpha", c_double), ("shell", c_int),
+                ("solver", c_int), ("rel_tol", c_double), ("max_iter", c_int), ("fixed_iters", c_int),
+                ("x0_dev", c_void_p), ("normal_mode", c_int), ("apg_tau", c_double)]
+
+
+class mh3d_solve_info(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("rel_res_recurrence", c_double), ("rel_res_true", c_double),
+                ("history", POINTER(c_double)), ("status", c_int)]
+
+
+class MH3DError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoint", "mh3d_normal", "mh3d_solve",
+           "mh3d_solve_host", "mh3d_solve_batched", "mh3d_last_error", "mh3d_plan_workspace_bytes", "mh3d_version"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmh3d.so (building it with nvcc if missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmh3d.so not found at {path}; run paper_2503_13802_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    lib.mh3d_plan_create.argtypes = [POINTER(mh3d_geometry), P, POINTER(c_void_p)]
+    lib.mh3d_plan_destroy.argtypes = [P]
+    lib.mh3d_forward.argtypes = [P, P, P, P]
+    lib.mh3d_adjoint.argtypes = [P, P, P, P]
+    lib.mh3d_normal.argtypes = [P, P, P, POINTER(mh3d_solve_opts), P]
+    lib.mh3d_solve.argtypes = [P, P, POINTER(mh3d_solve_opts), P, POINTER(mh3d_solve_info), P]
+    lib.mh3d_solve_host.argtypes = [P, P, POINTER(mh3d_solve_opts), P, POINTER(mh3d_solve_info), P]
+    lib.mh3d_solve_batched.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(mh3d_solve_opts),
+                                       POINTER(c_void_p), POINTER(mh3d_solve_info), P]
+    lib.mh3d_last_error.argtypes = [P]
+    lib.mh3d_last_error.restype = c_char_p
+    lib.mh3d_plan_workspace_bytes.argtypes = [P]
+    lib.mh3d_plan_workspace_bytes.restype = c_ulonglong
+    lib.mh3d_version.restype = c_char_p
+    for name in EXPORTS:
+        if name not in ("mh3d_last_error", "mh3d_plan_workspace_bytes", "mh3d_version"):
+            getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check(plan, status: int):
+    if status not in (MH3D_OK,):
+        msg = load().mh3d_last_error(plan).decode() if plan else ""
+        raise MH3DError(status, msg)
+
+
+def _dev_ptr(t, dtype, numel: int, what: str) -> int:
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{what}: tensor must be on a CUDA device")
+    if t.dtype != dtype:
+        raise ValueError(f"{what}: dtype {t.dtype}, expected {dtype}")
+    if t.numel() != numel or not t.is_contiguous():
+        raise ValueError(f"{what}: need a contiguous tensor of {numel} elements, got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+class Plan:
+    """Owns an mh3d_plan and the tensors it borrows (sensitivity map)."""
+
+    def __init__(self, n: Sequence[int], voxel_mm=(1.0, 1.0, 1.0), ds_factor: int = 1, ds_offset: int = 0,
+                 k_min: int = 2, k_max: int = 5, gamma_per_mm: float = 1.387016, gammaA: float = 2.0,
+                 transverse_ratio: float = 0.5, theta: Optional[Sequence[float]] = None, sensitivity=None,
+                 stream=None):
+        import torch
+
+        lib = load()
+        self.n = tuple(int(v) for v in n)
+        self.K = k_max - k_min + 1
+        self.ds_factor = ds_factor
+        nx, ny, nz = self.n
+        self.N = nx * ny * nz
+        self.shape = (nz, ny, nx)
+        self.portrait_shape = (self.K, nz, ny, nx // ds_factor)
+        self.sensitivity = None
+        if sensitivity is not None:
+            s = sensitivity if isinstance(sensitivity, torch.Tensor) else torch.as_tensor(sensitivity)
+            s = s.to(device="cuda", dtype=torch.float32).contiguous()
+            self.sensitivity = s
+        g = mh3d_geometry()
+        g.n[:] = [nx, ny, nz]
+        g.voxel_mm[:] = list(voxel_mm)
+        g.drive_axis = 0
+        g.ds_factor, g.ds_offset = ds_factor, ds_offset
+        g.pad[:] = [0, 0, 0]
+        g.k_min, g.k_max = k_min, k_max
+        g.gamma_per_mm, g.gammaA, g.transverse_ratio = gamma_per_mm, gammaA, transverse_ratio
+        self._theta = None
+        if theta is not None:
+            self._theta = (c_double * self.K)(*[float(t) for t in theta])
+            g.theta = ctypes.cast(self._theta, POINTER(c_double))
+        g.sensitivity_dev = (_dev_ptr(self.sensitivity, torch.float32, self.N, "sensitivity")
+                             if self.sensitivity is not None else None)
+        h = c_void_p()
+        st = lib.mh3d_plan_create(ctypes.byref(g), c_void_p(_stream_ptr(stream)), ctypes.byref(h))
+        if st != MH3D_OK:
+            raise MH3DError(st, "mh3d_plan_create")
+        self.handle = h
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) and self.handle.value:
+                load().mh3d_plan_destroy(self.handle)
+                self.handle = c_void_p()
+        except Exception:
+            pass
+
+    def workspace_bytes(self) -> int:
+        return int(load().mh3d_plan_workspace_bytes(self.handle))
+
+
+def mh3d_forward(plan: Plan, rho, d, stream=None):
+    import torch
+
+    lib = load()
+    p_rho = _dev_ptr(rho, torch.float32, plan.N, "rho")
+    n_d = plan.K * plan.portrait_shape[1] * plan.portrait_shape[2] * plan.portrait_shape[3]
+    p_d = _dev_ptr(d, torch.complex64, n_d, "d")
+    _check(plan.handle, lib.mh3d_forward(plan.handle, c_void_p(p_rho), c_void_p(p_d), c_void_p(_stream_ptr(stream))))
+    return d
+
+
+def mh3d_adjoint(plan: Plan, d, rho, stream=None):
+    import torch
+
+    lib = load()
+    n_d = plan.K * plan.portrait_shape[1] * plan.portrait_shape[2] * plan.portrait_shape[3]
+    p_d = _dev_ptr(d, torch.complex64, n_d, "d")
+    p_rho = _dev_ptr(rho, torch.float32, plan.N, "rho")
+    _check(plan.handle, lib.mh3d_adjoint(plan.handle, c_void_p(p_d), c_void_p(p_rho), c_void_p(_stream_ptr(stream))))
+    return rho
+
+
+def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: int = 2, solver: int = 0,
+              rel_tol: float = 1e-4, max_iter: int = 1000, fixed_iters: bool = False, x0=None,
+              normal_mode: int = 0, apg_tau: float = 0.0) -> mh3d_solve_opts:
+    o = mh3d_solve_opts()
+    o.reg_kind, o.lambda_, o.alpha, o.shell, o.solver = reg_kind, lam, alpha, shell, solver
+    o.rel_tol, o.max_iter, o.fixed_iters = rel_tol, max_iter, int(bool(fixed_iters))
+    o.x0_dev = x0.data_ptr() if x0 is not None else None
+    o.normal_mode, o.apg_tau = normal_mode, apg_tau
+    o._x0_ref = x0
+    return o
+
+
+def mh3d_normal(plan: Plan, p, q, opts: mh3d_solve_opts, stream=None):
+    import torch
+
+    lib = load()
+    pp = _dev_ptr(p, torch.float32, plan.N, "p")
+    pq = _dev_ptr(q, torch.float32, plan.N, "q")
+    _check(plan.handle, lib.mh3d_normal(plan.handle, c_void_p(pp), c_void_p(pq), ctypes.byref(opts),
+                                        c_void_p(_stream_ptr(stream))))
+    return q
+
+
+def _info(history_len: int):
+    info = mh3d_solve_info()
+    hist = (c_double * history_len)()
+    info.history = ctypes.cast(hist, POINTER(c_double))
+    return info, hist
+
+
+def mh3d_solve(plan: Plan, d, opts: mh3d_solve_opts, rho, stream=None, allow_not_converged: bool = True):
+    """Returns a dict with iters, residuals, status and the residual history."""
+    import torch
+
+    lib = load()
+    n_d = plan.K * plan.portrait_shape[1] * plan.portrait_shape[2] * plan.portrait_shape[3]
+    p_d = _dev_ptr(d, torch.complex64, n_d, "d")
+    p_rho = _dev_ptr(rho, torch.float32, plan.N, "rho")
+    if opts.x0_dev:
+        _dev_ptr(opts._x0_ref, torch.float32, plan.N, "x0")
+    info, hist = _info(opts.max_iter + 1)
+    st = lib.mh3d_solve(plan.handle, c_void_p(p_d), ctypes.byref(opts), c_void_p(p_rho), ctypes.byref(info),
+                        c_void_p(_stream_ptr(stream)))
+    if st != MH3D_OK and not (allow_not_converged and st == MH3D_ERR_NOT_CONVERGED):
+        _check(plan.handle, st)
+    return {"iters": info.iters, "rel_res_recurrence": info.rel_res_recurrence, "rel_res_true": info.rel_res_true,
+            "status": info.status, "history": [hist[i] for i in range(min(info.iters, opts.max_iter) + 1)]}
+
+
+def mh3d_solve_host(plan: Plan, d_host, opts: mh3d_solve_opts, rho_host, stream=None):
+    """d_host / rho_host: CPU tensors (pinned for speed), complex64 / float32."""
+    import torch
+
+    lib = load()
+    for t, dt, what in ((d_host, torch.complex64, "d_host"), (rho_host, torch.float32, "rho_host")):
+        if t.is_cuda or t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"{what}: need a contiguous CPU tensor of {dt}")
+    info, hist = _info(opts.max_iter + 1)
+    st = lib.mh3d_solve_host(plan.handle, c_void_p(d_host.data_ptr()), ctypes.byref(opts),
+                             c_void_p(rho_host.data_ptr()), ctypes.byref(info), c_void_p(_stream_ptr(stream)))
+    if st not in (MH3D_OK, MH3D_ERR_NOT_CONVERGED):
+        _check(plan.handle, st)
+    return {"iters": info.iters, "rel_res_true": info.rel_res_true, "status": info.status}
+
+
+def mh3d_solve_batched(plans: Sequence[Plan], ds, opts: mh3d_solve_opts, rhos, stream=None):
+    import torch
+
+    lib = load()
+    n = len(plans)
+    hp = (c_void_p * n)(*[p.handle.value for p in plans])
+    dp = (c_void_p * n)()
+    rp = (c_void_p * n)()
+    for i, (p, d, r) in enumerate(zip(plans, ds, rhos)):
+        n_d = p.K * p.portrait_shape[1] * p.portrait_shape[2] * p.portrait_shape[3]
+        dp[i] = _dev_ptr(d, torch.complex64, n_d, f"d[{i}]")
+        rp[i] = _dev_ptr(r, torch.float32, p.N, f"rho[{i}]")
+    infos = (mh3d_solve_info * n)()
+    st = lib.mh3d_solve_batched(hp, n, dp, ctypes.byref(opts), rp, infos, c_void_p(_stream_ptr(stream)))
+    if st not in (MH3D_OK, MH3D_ERR_NOT_CONVERGED):
+        raise MH3DError(st, "mh3d_solve_batched")
+    return [{"iters": infos[i].iters, "rel_res_true": infos[i].rel_res_true, "status": infos[i].status}
+            for i in range(n)]
+
+
+def mh3d_version() -> str:
+    return load().mh3d_version().decode()

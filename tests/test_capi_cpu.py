@@ -1,0 +1,86 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads without
+a GPU, exports every function that include/mh3d.h declares, and the ctypes
+mirrors of the ABI structs have the C layout.  No compute call is made."""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mh3d.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    pat = r"^(?:mh3d_status|const char\s*\*|unsigned long long)\s*(mh3d_\w+)\s*\("
+    return sorted(set(re.findall(pat, text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2503_13802_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoint", "mh3d_solve",
+                     "mh3d_solve_batched", "mh3d_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True).stdout
+    for name in _declared_functions():
+        assert re.search(r"\bT\s+" + name + r"\b", out), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2503_13802_gb300 import mh3d
+
+    assert sorted(mh3d.EXPORTS) == _declared_functions()
+
+
+def test_version_without_gpu(lib):
+    lib.mh3d_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.mh3d_version()
+
+
+def test_struct_layouts_match_c(tmp_path):
+    """Compile a C program against the header that prints sizeof/offsetof of
+    the ABI structs and compare with the ctypes mirrors."""
+    from paper_2503_13802_gb300 import mh3d as m
+
+    fields = {
+        "mh3d_geometry": ["n", "voxel_mm", "drive_axis", "ds_factor", "ds_offset", "pad", "k_min", "k_max",
+                          "gamma_per_mm", "gammaA", "transverse_ratio", "theta", "sensitivity_dev"],
+        "mh3d_solve_opts": ["reg_kind", "lambda", "alpha", "shell", "solver", "rel_tol", "max_iter", "fixed_iters",
+                            "x0_dev", "normal_mode", "apg_tau"],
+        "mh3d_solve_info": ["iters", "rel_res_recurrence", "rel_res_true", "history", "status"],
+    }
+    src = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    for st, fs in fields.items():
+        src.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            src.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    src.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", str(c), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    py = {"mh3d_geometry": m.mh3d_geometry, "mh3d_solve_opts": m.mh3d_solve_opts, "mh3d_solve_info": m.mh3d_solve_info}
+    for st, cls in py.items():
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            pyf = "lambda_" if f == "lambda" else f
+            assert int(got[f"{st}.{f}"]) == getattr(cls, pyf).offset, (st, f)

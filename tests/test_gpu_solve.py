@@ -1,0 +1,192 @@
+"""GPU solver parity against the FP64 oracle, through the C ABI.
+
+Bars: reconstructions within relative L2 1e-4 of the oracle at the same
+stopping rule; both are also compared with a tightly converged oracle
+solution.  Status paths (not converged, non-finite data, fixed iterations)
+are exercised without any device fault.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests._cases import gpu_plan, oracle_geom, params, rel_l2, sens_map
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def _data(p, g, b, seed, snr_db):
+    rho = W.phantom(p["n"], p["voxel"], seed, 5, 0)
+    clean = oracle.forward(g, rho, b)
+    K, M = g.K, clean[0].size
+    sig2 = np.sum(np.abs(clean) ** 2) / (K * M * 10 ** (snr_db / 10))
+    return rho, clean + np.sqrt(sig2) * W.unit_complex_noise(clean.shape, seed)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_plain_fp64_32cube_fixed_100_iterations(mode):
+    """32^3, k = 2..5, uniform sensitivity, s = 1, 5 blobs, 30 dB, Tikhonov
+    lambda = 1e-3, exactly 100 CG iterations on both sides."""
+    p = params((32, 32, 32), kmin=2, kmax=5)
+    g = oracle_geom(p)
+    _, d = _data(p, g, None, 0, 30.0)
+    xo, it, hist = oracle.cg(g, d, None, oracle.SolveOpts(lam=1e-3, rel_tol=0.0, max_iter=100))
+    assert it == 100
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, None)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-3, max_iter=100, fixed_iters=True,
+                                                               normal_mode=mode), x)
+    assert info["iters"] == 100 and info["status"] == 0
+    assert rel_l2(x.cpu().numpy(), xo) <= 1e-4, rel_l2(x.cpu().numpy(), xo)
+    # residual histories agree
+    np.testing.assert_allclose(info["history"][:40], hist[:40], rtol=2e-3)
+
+
+@pytest.mark.parametrize("reg_kind", [0, 1])
+def test_solve_to_tolerance_matches_oracle(reg_kind):
+    """Downsampled, Gaussian sensitivity, phases: GPU CG and oracle CG run to
+    the same relative residual; both land within 1e-4 (relative L2) of a
+    tightly converged oracle solution."""
+    p = params((48, 24, 16), s=2, r=1, kmin=2, kmax=7, theta=list(np.linspace(-1, 1, 6)))
+    g = oracle_geom(p)
+    b = sens_map(p)
+    _, d = _data(p, g, b, 1, 25.0)
+    lam = 1e-2
+    tight, _, _ = oracle.cg(g, d, b, oracle.SolveOpts(lam=lam, reg_kind=reg_kind, alpha=4.0, shell=2,
+                                                       rel_tol=1e-12, max_iter=5000))
+    xo, ito, _ = oracle.cg(g, d, b, oracle.SolveOpts(lam=lam, reg_kind=reg_kind, alpha=4.0, shell=2,
+                                                      rel_tol=1e-6, max_iter=5000))
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, b)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=lam, reg_kind=reg_kind, alpha=4.0, shell=2,
+                                                               rel_tol=1e-6, max_iter=5000), x)
+    assert info["status"] == 0, info
+    assert abs(info["iters"] - ito) <= max(3, 0.1 * ito), (info["iters"], ito)
+    xg = x.cpu().numpy()
+    assert rel_l2(xg, xo) <= 1e-4, rel_l2(xg, xo)
+    assert rel_l2(xg, tight) <= 1e-4, rel_l2(xg, tight)
+    assert info["rel_res_true"] <= 5e-6, info
+
+
+def test_full_size_128x128x64_solve_residual_property():
+    """The 128x128x64, k = 2..9, s = 2 workload (40 blobs + 3 lines, 25 dB,
+    Gaussian sensitivity), CG to relative residual 1e-4 on the GPU; the
+    oracle then evaluates ||A^T d - (A^T A + lambda I) x|| / ||A^T d|| for the
+    GPU solution in FP64 (a property that holds at any size)."""
+    p = params((128, 128, 64), s=2, kmin=2, kmax=9)
+    g = oracle_geom(p)
+    b = sens_map(p)
+    rho = W.phantom((128, 128, 64), (1, 1, 1), 0, 40, 3)
+    tables = oracle.psf_tables(g)
+    clean = oracle.forward(g, rho, b, tables)
+    sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** 2.5)
+    d = clean + np.sqrt(sig2) * W.unit_complex_noise(clean.shape, 0)
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, b)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-3, rel_tol=1e-4, max_iter=2000), x)
+    assert info["status"] == 0, info
+    xg = x.cpu().numpy().astype(np.float64)
+    rhs = oracle.adjoint(g, d, b, tables)
+    res = rhs - oracle.normal_apply(g, xg, b, oracle.SolveOpts(lam=1e-3), tables)
+    rel = np.linalg.norm(res) / np.linalg.norm(rhs)
+    assert rel <= 1.5e-4, rel
+    assert abs(info["rel_res_true"] - rel) <= 2e-5, (info["rel_res_true"], rel)
+
+
+def test_warm_start_from_solution_converges_immediately():
+    p = params((32, 16, 8), s=2, kmin=2, kmax=5)
+    g = oracle_geom(p)
+    d = W.random_portraits(g.portrait_shape, 3)
+    xo, _, _ = oracle.cg(g, d, None, oracle.SolveOpts(lam=1e-2, rel_tol=1e-12, max_iter=5000))
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, None)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    x0 = _dev(xo, torch.float32)
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-2, rel_tol=1e-4, max_iter=100, x0=x0), x)
+    assert info["status"] == 0 and info["iters"] <= 1, info
+
+
+def test_not_converged_status_keeps_iterate():
+    p = params((32, 16, 8), kmin=2, kmax=5)
+    g = oracle_geom(p)
+    d = W.random_portraits(g.portrait_shape, 4)
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, None)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-6, rel_tol=1e-12, max_iter=5), x)
+    assert info["status"] == 6 and info["iters"] == 5
+    xo, _, _ = oracle.cg(g, d, None, oracle.SolveOpts(lam=1e-6, rel_tol=0.0, max_iter=5))
+    assert rel_l2(x.cpu().numpy(), xo) <= 1e-4
+
+
+def test_nonfinite_data_reports_status():
+    p = params((16, 8, 8), kmin=2, kmax=3)
+    g = oracle_geom(p)
+    d = W.random_portraits(g.portrait_shape, 5)
+    d[0, 1, 2, 3] = np.nan
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, None)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    from paper_2503_13802_gb300 import MH3DError
+
+    with pytest.raises(MH3DError) as e:
+        mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-2, rel_tol=1e-4, max_iter=50), x)
+    assert "NONFINITE" in str(e.value)
+    # the plan stays usable after the error
+    d[0, 1, 2, 3] = 0.0
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-2, rel_tol=1e-4, max_iter=200), x)
+    assert info["status"] == 0
+
+
+def test_apg_matches_oracle_apg():
+    """The paper's accelerated projected gradient (rho >= 0), fixed step and
+    iteration count, against the oracle's APG."""
+    p = params((32, 12, 8), s=2, kmin=2, kmax=5, theta=[0.2, 0.4, -0.3, 1.0])
+    g = oracle_geom(p)
+    b = sens_map(p)
+    _, d = _data(p, g, b, 2, 30.0)
+    lam, iters = 5e-2, 200
+    # step 0.9 / ||N||_2 from an FP64 power iteration with the oracle
+    v = W.random_volume(g.shape, 77)
+    for _ in range(40):
+        v = oracle.normal_apply(g, v / np.linalg.norm(v), b, oracle.SolveOpts(lam=lam))
+    tau = 0.9 / np.linalg.norm(v)
+    xo = oracle.apg(g, d, tau, iters, b, oracle.SolveOpts(lam=lam))
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, b)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=lam, solver=1, max_iter=iters, apg_tau=tau), x)
+    xg = x.cpu().numpy()
+    assert xg.min() >= 0.0
+    assert rel_l2(xg, xo) <= 1e-4, rel_l2(xg, xo)
+
+
+def test_solve_host_buffers_match_device_solve():
+    p = params((32, 16, 16), s=2, kmin=2, kmax=5)
+    g = oracle_geom(p)
+    d = W.random_portraits(g.portrait_shape, 9)
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve, mh3d_solve_host
+
+    plan = gpu_plan(p, None)
+    o = make_opts(lam=1e-2, rel_tol=1e-5, max_iter=500)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    mh3d_solve(plan, _dev(d, torch.complex64), o, x)
+    dh = torch.as_tensor(d.astype(np.complex64)).pin_memory()
+    xh = torch.empty(g.shape, dtype=torch.float32).pin_memory()
+    mh3d_solve_host(plan, dh, o, xh)
+    np.testing.assert_array_equal(xh.numpy(), x.cpu().numpy())
