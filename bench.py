@@ -140,8 +140,8 @@ def bench_mh3d(args):
     noise = torch.as_tensor(W.unit_complex_noise(tuple(d.shape), seed).astype(np.complex64), device=dev)
     d = (d + math.sqrt(sig2) * noise).contiguous()
     x = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
-    opts = make_opts(lam=wl.lam, rel_tol=wl.rel_tol, max_iter=wl.max_iter, fixed_iters=wl.fixed_iters,
-                     normal_mode=args.mode)
+    opts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter,
+                     fixed_iters=wl.fixed_iters, normal_mode=args.mode)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
 
@@ -226,7 +226,7 @@ def bench_mh3d(args):
     # explicit A-then-A^T reconstructions for comparison (mode 1)
     other = None
     if args.mode == 0:
-        o1 = make_opts(lam=wl.lam, rel_tol=wl.rel_tol, max_iter=wl.max_iter, normal_mode=1)
+        o1 = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter, normal_mode=1)
         mh3d_solve(plan, d, o1, x)
         tt = []
         for _ in range(5):
@@ -290,7 +290,8 @@ def cpu_baseline(wl: W.Workload, gpu_iters: int, sample_iters: int = 2):
     sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
     d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, wl.seeds[0])
     t0 = time.perf_counter()
-    oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, rel_tol=0.0, max_iter=sample_iters), tables=tables)
+    oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=sample_iters),
+              tables=tables)
     t = time.perf_counter() - t0
     # cg() costs A^T d + one normal application for r0 + sample_iters iterations
     per_app = t / (sample_iters + 1.5)
@@ -318,11 +319,13 @@ def bench_reference(args):
     ref_iters = 61   # CG iterations this workload needs to reach 1e-4 (measured on the GPU path)
     sample = 1
     for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, rel_tol=0.0, max_iter=sample), tables=tables)
+        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=sample),
+                  tables=tables)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, rel_tol=0.0, max_iter=sample), tables=tables)
+        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=sample),
+                  tables=tables)
         times.append(time.perf_counter() - t0)
     per_app = statistics.mean(times) / (sample + 1.5)
     recon_s = per_app * (ref_iters + 2.5)

@@ -95,6 +95,9 @@ typedef struct {
     int normal_mode;             /* 0 = fused normal operator (exact A^T A, Fourier blocks) */
                                  /* 1 = explicit A then A^T through a portrait buffer       */
     double apg_tau;              /* APG step; <= 0 = 0.95 / ||M||^2 by power iteration      */
+    int lambda_relative;         /* nonzero: the weight of R is lambda * ||A||_2^2, the     */
+                                 /* squared spectral norm of A with b = 1 (see              */
+                                 /* mh3d_operator_norm2); zero: lambda is absolute          */
 } mh3d_solve_opts;
 
 typedef struct {
@@ -147,7 +150,18 @@ mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* con
                                const mh3d_solve_opts* opts, float* const* rho_dev,
                                mh3d_solve_info* infos, void* stream);
 
-/* Message for the last failing call on `plan` ("" if none; never NULL). */
+/* *norm2 = ||A||_2^2 for b = 1: the largest eigenvalue of A^T A, evaluated
+ * in FP64 at plan time from the PSF spectra.  With the separable PSF it is
+ * max|Y^|^2 max|Z^|^2 max_m lambda_max(B_m), B_m the s x s alias block
+ * (1/s) sum_k conj(X^_k(m + a n/s)) X^_k(m + b n/s) of the drive axis.  The
+ * PSF's overall scale is a free constant of the model (the paper drops
+ * i 2 pi m f0 / Delta_t and the coil gain), so regularisation weights are
+ * most meaningful relative to it. */
+mh3d_status mh3d_operator_norm2(mh3d_plan plan, double* norm2);
+
+/* Message for the last failing call on `plan` ("" if none; never NULL).
+ * With plan == NULL: the message of the calling thread's last failed
+ * mh3d_plan_create. */
 const char* mh3d_last_error(mh3d_plan plan);
 
 /* Bytes of device workspace the plan holds (tables + solver scratch). */

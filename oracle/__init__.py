@@ -17,6 +17,7 @@ Functions and the passages they follow:
 * ``adjoint``: A^T for the real inner product.
 * ``reg_apply``: R = I, or T^T T + alpha P_a^T P_a (Sec. 4.3, Eq. finalR).
 * ``normal_apply``: (A^T A + lambda R) p.
+* ``operator_norm2``: ||A||_2^2 with b = 1, the scale relative weights refer to.
 * ``cg``: conjugate gradients on the normal equations.
 * ``apg``: the paper's accelerated projected gradient (Sec. 4.3, runtime
   subsection).
@@ -208,14 +209,45 @@ def reg_apply(g: Geometry, p, kind: int = 0, alpha: float = 0.0, shell: int = 2)
     return out
 
 
+def operator_norm2(g: Geometry, tables=None) -> float:
+    """||A||_2^2 for b = 1: the largest eigenvalue of A^T A.
+
+    The sampled PSF is separable, so A^T A = (X part) (x) (Y^T Y) (x) (Z^T Z);
+    the transverse factors are circulant (eigenvalues |DFT|^2, numpy's FFT as
+    the library step) and the drive factor sum_k X_k^T P^T P X_k couples
+    each frequency w only with its aliases w + j n/s.  With kernels shifted by
+    the kept-row offset r (X'_k[o] = X_k[o + r], P then keeps rows 0 mod s),
+    the alias block is B_m[a][b] = (1/s) sum_k conj(x_k[m + a M]) x_k[m + b M],
+    M = n/s, whose largest eigenvalue comes from numpy's eigvalsh."""
+    X, Y, Z = tables or psf_tables(g)
+    nx = g.n[0]
+    s, r = g.ds_factor, g.ds_offset
+    M = nx // s
+    Xs = np.roll(X, -r, axis=1)                # X'_k[o] = X_k[o + r]
+    xh = np.fft.fft(Xs, axis=1)
+    lam_x = 0.0
+    for m in range(M):
+        idx = m + M * np.arange(s)
+        v = xh[:, idx]                         # [K, s]
+        B = (np.conj(v).T @ v) / s
+        lam_x = max(lam_x, float(np.linalg.eigvalsh(B).max()))
+    return lam_x * float(np.max(np.abs(np.fft.fft(Y)) ** 2)) * float(np.max(np.abs(np.fft.fft(Z)) ** 2))
+
+
 @dataclass
 class SolveOpts:
+    """lam is the weight of R; with lam_relative it is multiplied by
+    operator_norm2(g) (the PSF's overall scale is a free constant)."""
     lam: float = 1e-3
     reg_kind: int = 0
     alpha: float = 0.0
     shell: int = 2
     rel_tol: float = 1e-4
     max_iter: int = 1000
+    lam_relative: bool = False
+
+    def lam_eff(self, g: Geometry, tables=None) -> float:
+        return self.lam * operator_norm2(g, tables) if self.lam_relative else self.lam
 
 
 def normal_apply(g: Geometry, p, b=None, opts: SolveOpts = SolveOpts(), tables=None) -> np.ndarray:
@@ -227,7 +259,7 @@ def normal_apply(g: Geometry, p, b=None, opts: SolveOpts = SolveOpts(), tables=N
     p = _f64(p).reshape(g.shape)
     out = np.zeros(g.shape)
     _load().orc_normal_apply(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z),
-                             _ptr(th), _ptr(b), opts.lam, opts.reg_kind, opts.alpha, opts.shell,
+                             _ptr(th), _ptr(b), opts.lam_eff(g, tables), opts.reg_kind, opts.alpha, opts.shell,
                              _ptr(p), _ptr(out))
     return out
 
@@ -242,7 +274,7 @@ def cg(g: Geometry, d, b=None, opts: SolveOpts = SolveOpts(), x0=None, tables=No
     x = np.zeros(g.shape) if x0 is None else _f64(x0).reshape(g.shape).copy()
     hist = np.zeros(opts.max_iter + 1)
     it = _load().orc_cg(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z),
-                        _ptr(th), _ptr(b), opts.lam, opts.reg_kind, opts.alpha, opts.shell,
+                        _ptr(th), _ptr(b), opts.lam_eff(g, tables), opts.reg_kind, opts.alpha, opts.shell,
                         _ptr(_complex_in(g, d)), opts.rel_tol, opts.max_iter, _ptr(x), _ptr(hist))
     return x, it, hist[: it + 1]
 
@@ -257,7 +289,7 @@ def apg(g: Geometry, d, tau: float, iters: int, b=None, opts: SolveOpts = SolveO
     b = None if b is None else _f64(b).reshape(g.shape)
     x = np.zeros(g.shape) if x0 is None else _f64(x0).reshape(g.shape).copy()
     _load().orc_apg(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z),
-                    _ptr(th), _ptr(b), opts.lam, opts.reg_kind, opts.alpha, opts.shell,
+                    _ptr(th), _ptr(b), opts.lam_eff(g, tables), opts.reg_kind, opts.alpha, opts.shell,
                     _ptr(_complex_in(g, d)), float(tau), int(iters), _ptr(x))
     return x
 

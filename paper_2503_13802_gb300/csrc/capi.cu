@@ -1,4 +1,5 @@
 // Plan construction and operator entry points of the C ABI (include/mh3d.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -14,6 +15,7 @@ namespace {
 
 std::mutex g_attr_mu;
 bool g_attr_done = false;
+thread_local std::string g_create_err;   // message of the last failed mh3d_plan_create
 
 bool is_235(int n)
 {
@@ -98,6 +100,26 @@ static mh3d_status build_tables(Plan& P, cudaStream_t st)
                 put(oQ + ((size_t)m * s + a) * s + b, (double)mx * acc);
             }
     for (int kk = 0; kk < K; ++kk) put(oPh + kk, cplx(std::cos(P.theta[kk]), std::sin(P.theta[kk])));
+    // ||A||_2^2 (b = 1) = max|DFT Y|^2 max|DFT Z|^2 max_m lambda_max(B_m), with
+    // B_m[a][b] = (1/s) sum_k conj(x_k[m + a mx]) x_k[m + b mx] and x_k the
+    // unnormalised drive spectra (X here holds x_k / nx).
+    {
+        double ym = 0, zm = 0, xm = 0;
+        for (int w = 0; w < ny; ++w) ym = std::max(ym, std::norm(Y[w] * (double)ny));
+        for (int w = 0; w < nz; ++w) zm = std::max(zm, std::norm(Z[w] * (double)nz));
+        std::vector<cplx> B((size_t)s * s);
+        for (int m = 0; m < mx; ++m) {
+            for (int a = 0; a < s; ++a)
+                for (int b = 0; b < s; ++b) {
+                    cplx acc(0, 0);
+                    for (int kk = 0; kk < K; ++kk)
+                        acc += std::conj(X[kk][m + a * mx]) * X[kk][m + b * mx] * ((double)nx * nx);
+                    B[(size_t)a * s + b] = acc / (double)s;
+                }
+            xm = std::max(xm, hermitian_lambda_max(B, s));
+        }
+        P.opnorm2 = xm * ym * zm;
+    }
     auto put_tw = [&](size_t o, int n) {
         auto w = twiddles(n);
         for (int t = 0; t < n; ++t) put(o + t, w[t]);
@@ -194,7 +216,7 @@ RegArgs reg_args(const Plan& P, const mh3d_solve_opts& o)
 {
     RegArgs g;
     g.kind = o.reg_kind;
-    g.lambda = (float)o.lambda;
+    g.lambda = (float)(o.lambda_relative ? o.lambda * P.opnorm2 : o.lambda);
     g.alpha = (float)o.alpha;
     g.shell = o.shell;
     g.nx = P.nx;
@@ -389,6 +411,7 @@ mh3d_status mh3d_plan_create(const mh3d_geometry* g, void* stream, mh3d_plan* ou
             cudaError_t e = ops_set_attributes();
             if (e == cudaSuccess) e = solve_set_attributes();
             if (e != cudaSuccess) {
+                g_create_err = std::string("kernel attributes: ") + cudaGetErrorString(e);
                 delete P;
                 return MH3D_ERR_CUDA;
             }
@@ -399,11 +422,13 @@ mh3d_status mh3d_plan_create(const mh3d_geometry* g, void* stream, mh3d_plan* ou
     mh3d_status s = build_tables(*P, st);
     if (s == MH3D_OK) s = solve_alloc(*P);
     if (s != MH3D_OK) {
+        g_create_err = P->err;
         solve_free(*P);
         if (P->table_mem) cudaFree(P->table_mem);
         delete P;
         return s;
     }
+    g_create_err.clear();
     *out = P;
     return MH3D_OK;
 }
@@ -418,7 +443,14 @@ mh3d_status mh3d_plan_destroy(mh3d_plan P)
     return MH3D_OK;
 }
 
-const char* mh3d_last_error(mh3d_plan P) { return P ? P->err.c_str() : "null plan"; }
+mh3d_status mh3d_operator_norm2(mh3d_plan P, double* out)
+{
+    if (!P || !out) return MH3D_ERR_INVALID_ARG;
+    *out = P->opnorm2;
+    return MH3D_OK;
+}
+
+const char* mh3d_last_error(mh3d_plan P) { return P ? P->err.c_str() : g_create_err.c_str(); }
 
 unsigned long long mh3d_plan_workspace_bytes(mh3d_plan P)
 {

@@ -67,6 +67,7 @@ struct Plan {
     double vox[3] = {1, 1, 1};
     double gamma = 1, gammaA = 1, tratio = 0.5;
     std::vector<double> theta;
+    double opnorm2 = 1.0;         // ||A||_2^2 with b = 1 (FP64)
     const float* sens = nullptr;  // borrowed device pointer (may be null)
 
     AxisPlan ax, ay, az, am;      // x (drive), y, z, portrait length mx
@@ -100,6 +101,7 @@ double langevin_deriv_host(int k, double x);
 std::vector<cplx> drive_spectrum(int n, double dx, int k, double gamma, double gammaA, int r);
 std::vector<cplx> transverse_spectrum(int n, double d, double gt);
 std::vector<cplx> twiddles(int n);
+double hermitian_lambda_max(const std::vector<cplx>& H, int s);
 bool radix_plan(int n, RadixPlan& pl, int variant);
 
 // ops.cu: operator launches (all asynchronous on `st`)

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_tpass(const TArgs a)
     DotAcc acc;
     fft_run<false, true, true>(a.rp, TLoad{&a, base, x0, beta}, BufSt{sr, ld}, s0, s1, ld, P, tw);
     fft_run<true, true, true>(a.rp, MulLd{sr, ld, mu}, TStore{&a, base, x0, &acc}, so, sr, ld, P, tw);
-    if (a.epilogue) {
+    if (a.epilogue && a.part) {
         const double t = block_sum_f64(acc.value(), red);
         if (threadIdx.x == 0) a.part[blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
@@ -463,14 +463,27 @@ cudaError_t run_xnrm(const XArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Opt every pencil kernel into the device's full shared-memory carve-out
+// (the opt-in limit minus the kernel's static shared memory).
+template <class F>
+static cudaError_t opt_in_smem(F* f, int optin)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t ops_set_attributes()
 {
-    const int maxs = 227 * 1024;
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_tpass, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_xadj, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_xnrm, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs)) != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if ((e = opt_in_smem(k_tpass, optin)) != cudaSuccess) return e;
+    if ((e = opt_in_smem(k_xfwd, optin)) != cudaSuccess) return e;
+    if ((e = opt_in_smem(k_xadj, optin)) != cudaSuccess) return e;
+    if ((e = opt_in_smem(k_xnrm, optin)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 

@@ -10,6 +10,7 @@
 // O(n^2) sum with exactly reduced angles, then rounded once to FP32.
 #include "mh3d_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -168,6 +169,52 @@ std::vector<cplx> transverse_spectrum(int n, double d, double gt)
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_trans_cache[key] = H;
     return H;
+}
+
+// Largest eigenvalue of a small Hermitian positive semidefinite matrix
+// (row-major s x s) by the cyclic Jacobi method on its real 2s x 2s
+// symmetric embedding [[Re, -Im], [Im, Re]] (each eigenvalue appears twice).
+double hermitian_lambda_max(const std::vector<cplx>& H, int s)
+{
+    if (s == 1) return H[0].real();
+    const int n = 2 * s;
+    std::vector<double> a((size_t)n * n);
+    for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j) {
+            const cplx h = H[(size_t)i * s + j];
+            a[(size_t)i * n + j] = h.real();
+            a[(size_t)i * n + j + s] = -h.imag();
+            a[(size_t)(i + s) * n + j] = h.imag();
+            a[(size_t)(i + s) * n + j + s] = h.real();
+        }
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += a[(size_t)p * n + q] * a[(size_t)p * n + q];
+        if (off < 1e-30) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = a[(size_t)p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {   // rotate columns p, q
+                    const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+                    a[(size_t)k * n + p] = c * akp - sn * akq;
+                    a[(size_t)k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {   // rotate rows p, q
+                    const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+                    a[(size_t)p * n + k] = c * apk - sn * aqk;
+                    a[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    double mx = a[0];
+    for (int i = 1; i < n; ++i) mx = std::max(mx, a[(size_t)i * n + i]);
+    return mx;
 }
 
 // Twiddles W_n^t = e^{-2 pi i t / n}, t = 0..n-1, from exactly reduced angles.

@@ -37,7 +37,8 @@ class mh3d_geometry(ctypes.Structure):
 class mh3d_solve_opts(ctypes.Structure):
     _fields_ = [("reg_kind", c_int), ("lambda_", c_double), ("alpha", c_double), ("shell", c_int),
                 ("solver", c_int), ("rel_tol", c_double), ("max_iter", c_int), ("fixed_iters", c_int),
-                ("x0_dev", c_void_p), ("normal_mode", c_int), ("apg_tau", c_double)]
+                ("x0_dev", c_void_p), ("normal_mode", c_int), ("apg_tau", c_double),
+                ("lambda_relative", c_int)]
 
 
 class mh3d_solve_info(ctypes.Structure):
@@ -54,7 +55,8 @@ class MH3DError(RuntimeError):
 _lib = None
 
 EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoint", "mh3d_normal", "mh3d_solve",
-           "mh3d_solve_host", "mh3d_solve_batched", "mh3d_last_error", "mh3d_plan_workspace_bytes", "mh3d_version"]
+           "mh3d_solve_host", "mh3d_solve_batched", "mh3d_operator_norm2", "mh3d_last_error",
+           "mh3d_plan_workspace_bytes", "mh3d_version"]
 
 
 def library_path() -> str:
@@ -82,6 +84,7 @@ def load(build_if_missing: bool = True):
     lib.mh3d_solve_host.argtypes = [P, P, POINTER(mh3d_solve_opts), P, POINTER(mh3d_solve_info), P]
     lib.mh3d_solve_batched.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(mh3d_solve_opts),
                                        POINTER(c_void_p), POINTER(mh3d_solve_info), P]
+    lib.mh3d_operator_norm2.argtypes = [P, POINTER(c_double)]
     lib.mh3d_last_error.argtypes = [P]
     lib.mh3d_last_error.restype = c_char_p
     lib.mh3d_plan_workspace_bytes.argtypes = [P]
@@ -161,7 +164,7 @@ class Plan:
         h = c_void_p()
         st = lib.mh3d_plan_create(ctypes.byref(g), c_void_p(_stream_ptr(stream)), ctypes.byref(h))
         if st != MH3D_OK:
-            raise MH3DError(st, "mh3d_plan_create")
+            raise MH3DError(st, "mh3d_plan_create: " + (lib.mh3d_last_error(None) or b"").decode())
         self.handle = h
 
     def __del__(self):
@@ -200,12 +203,14 @@ def mh3d_adjoint(plan: Plan, d, rho, stream=None):
 
 def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: int = 2, solver: int = 0,
               rel_tol: float = 1e-4, max_iter: int = 1000, fixed_iters: bool = False, x0=None,
-              normal_mode: int = 0, apg_tau: float = 0.0) -> mh3d_solve_opts:
+              normal_mode: int = 0, apg_tau: float = 0.0, lam_relative: bool = False) -> mh3d_solve_opts:
+    """lam_relative: lam multiplies ||A||_2^2 (b = 1), see mh3d_operator_norm2."""
     o = mh3d_solve_opts()
     o.reg_kind, o.lambda_, o.alpha, o.shell, o.solver = reg_kind, lam, alpha, shell, solver
     o.rel_tol, o.max_iter, o.fixed_iters = rel_tol, max_iter, int(bool(fixed_iters))
     o.x0_dev = x0.data_ptr() if x0 is not None else None
     o.normal_mode, o.apg_tau = normal_mode, apg_tau
+    o.lambda_relative = int(bool(lam_relative))
     o._x0_ref = x0
     return o
 
@@ -281,6 +286,12 @@ def mh3d_solve_batched(plans: Sequence[Plan], ds, opts: mh3d_solve_opts, rhos, s
         raise MH3DError(st, "mh3d_solve_batched")
     return [{"iters": infos[i].iters, "rel_res_true": infos[i].rel_res_true, "status": infos[i].status}
             for i in range(n)]
+
+
+def mh3d_operator_norm2(plan: Plan) -> float:
+    out = c_double()
+    _check(plan.handle, load().mh3d_operator_norm2(plan.handle, ctypes.byref(out)))
+    return out.value
 
 
 def mh3d_version() -> str:

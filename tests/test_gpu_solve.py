@@ -31,50 +31,67 @@ def _data(p, g, b, seed, snr_db):
 @pytest.mark.parametrize("mode", [0, 1])
 def test_plain_fp64_32cube_fixed_100_iterations(mode):
     """32^3, k = 2..5, uniform sensitivity, s = 1, 5 blobs, 30 dB, Tikhonov
-    lambda = 1e-3, exactly 100 CG iterations on both sides."""
+    lambda = 1e-3 (relative to ||A||^2), exactly 100 CG iterations on both
+    sides: the FP32 GPU iterate is within 1e-4 of the FP64 oracle iterate."""
     p = params((32, 32, 32), kmin=2, kmax=5)
     g = oracle_geom(p)
     _, d = _data(p, g, None, 0, 30.0)
-    xo, it, hist = oracle.cg(g, d, None, oracle.SolveOpts(lam=1e-3, rel_tol=0.0, max_iter=100))
+    xo, it, hist = oracle.cg(g, d, None, oracle.SolveOpts(lam=1e-3, rel_tol=0.0, max_iter=100, lam_relative=True))
     assert it == 100
-    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+    from paper_2503_13802_gb300 import make_opts, mh3d_operator_norm2, mh3d_solve
 
     plan = gpu_plan(p, None)
+    assert mh3d_operator_norm2(plan) == pytest.approx(oracle.operator_norm2(g), rel=1e-8)
     x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
-    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-3, max_iter=100, fixed_iters=True,
-                                                               normal_mode=mode), x)
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-3, lam_relative=True, max_iter=100,
+                                                               fixed_iters=True, normal_mode=mode), x)
     assert info["iters"] == 100 and info["status"] == 0
     assert rel_l2(x.cpu().numpy(), xo) <= 1e-4, rel_l2(x.cpu().numpy(), xo)
     # residual histories agree
-    np.testing.assert_allclose(info["history"][:40], hist[:40], rtol=2e-3)
+    np.testing.assert_allclose(info["history"][:40], hist[:40], rtol=1e-3)
 
 
 @pytest.mark.parametrize("reg_kind", [0, 1])
-def test_solve_to_tolerance_matches_oracle(reg_kind):
-    """Downsampled, Gaussian sensitivity, phases: GPU CG and oracle CG run to
-    the same relative residual; both land within 1e-4 (relative L2) of a
-    tightly converged oracle solution."""
+@pytest.mark.parametrize("mode", [0, 1])
+def test_solve_to_tolerance_matches_oracle(reg_kind, mode):
+    """Downsampled, Gaussian sensitivity, phases, relative lambda 1e-3.
+    (a) At a common relative residual of 1e-6 the GPU and oracle
+    reconstructions agree within 1e-4 and both sit within 1e-4 of a tightly
+    converged oracle solution.  (b) At the 1e-4 stopping rule the GPU
+    solution is as close to the exact solution as the oracle's own is at that
+    rule (the rule itself leaves ~kappa * 1e-4 of slack)."""
     p = params((48, 24, 16), s=2, r=1, kmin=2, kmax=7, theta=list(np.linspace(-1, 1, 6)))
     g = oracle_geom(p)
     b = sens_map(p)
     _, d = _data(p, g, b, 1, 25.0)
-    lam = 1e-2
-    tight, _, _ = oracle.cg(g, d, b, oracle.SolveOpts(lam=lam, reg_kind=reg_kind, alpha=4.0, shell=2,
-                                                       rel_tol=1e-12, max_iter=5000))
-    xo, ito, _ = oracle.cg(g, d, b, oracle.SolveOpts(lam=lam, reg_kind=reg_kind, alpha=4.0, shell=2,
-                                                      rel_tol=1e-6, max_iter=5000))
+    mk = lambda tol: oracle.SolveOpts(lam=1e-3, lam_relative=True, reg_kind=reg_kind, alpha=4.0, shell=2,
+                                      rel_tol=tol, max_iter=20000)
+    tight, _, _ = oracle.cg(g, d, b, mk(1e-12))
     from paper_2503_13802_gb300 import make_opts, mh3d_solve
 
     plan = gpu_plan(p, b)
     x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
-    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=lam, reg_kind=reg_kind, alpha=4.0, shell=2,
-                                                               rel_tol=1e-6, max_iter=5000), x)
+    dd = _dev(d, torch.complex64)
+    # (a)
+    xo6, it6, _ = oracle.cg(g, d, b, mk(1e-6))
+    info = mh3d_solve(plan, dd, make_opts(lam=1e-3, lam_relative=True, reg_kind=reg_kind, alpha=4.0, shell=2,
+                                          rel_tol=1e-6, max_iter=20000, normal_mode=mode), x)
     assert info["status"] == 0, info
-    assert abs(info["iters"] - ito) <= max(3, 0.1 * ito), (info["iters"], ito)
     xg = x.cpu().numpy()
-    assert rel_l2(xg, xo) <= 1e-4, rel_l2(xg, xo)
+    assert rel_l2(xg, xo6) <= 1e-4, rel_l2(xg, xo6)
     assert rel_l2(xg, tight) <= 1e-4, rel_l2(xg, tight)
-    assert info["rel_res_true"] <= 5e-6, info
+    assert rel_l2(xo6, tight) <= 1e-4
+    # (b)
+    xo4, it4, _ = oracle.cg(g, d, b, mk(1e-4))
+    info = mh3d_solve(plan, dd, make_opts(lam=1e-3, lam_relative=True, reg_kind=reg_kind, alpha=4.0, shell=2,
+                                          rel_tol=1e-4, max_iter=20000, normal_mode=mode), x)
+    assert info["status"] == 0 and info["rel_res_true"] <= 1.2e-4, info
+    xg = x.cpu().numpy()
+    assert rel_l2(xg, tight) <= 2.0 * rel_l2(xo4, tight) + 1e-4, (rel_l2(xg, tight), rel_l2(xo4, tight))
+    # same Krylov iterates: the oracle run for the GPU's iteration count
+    xo_same, _, _ = oracle.cg(g, d, b, oracle.SolveOpts(lam=1e-3, lam_relative=True, reg_kind=reg_kind, alpha=4.0,
+                                                          shell=2, rel_tol=0.0, max_iter=info["iters"]))
+    assert rel_l2(xg, xo_same) <= 1e-3, rel_l2(xg, xo_same)
 
 
 def test_full_size_128x128x64_solve_residual_property():
@@ -94,11 +111,12 @@ def test_full_size_128x128x64_solve_residual_property():
 
     plan = gpu_plan(p, b)
     x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
-    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-3, rel_tol=1e-4, max_iter=2000), x)
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-3, lam_relative=True, rel_tol=1e-4,
+                                                               max_iter=2000), x)
     assert info["status"] == 0, info
     xg = x.cpu().numpy().astype(np.float64)
     rhs = oracle.adjoint(g, d, b, tables)
-    res = rhs - oracle.normal_apply(g, xg, b, oracle.SolveOpts(lam=1e-3), tables)
+    res = rhs - oracle.normal_apply(g, xg, b, oracle.SolveOpts(lam=1e-3, lam_relative=True), tables)
     rel = np.linalg.norm(res) / np.linalg.norm(rhs)
     assert rel <= 1.5e-4, rel
     assert abs(info["rel_res_true"] - rel) <= 2e-5, (info["rel_res_true"], rel)
@@ -148,7 +166,8 @@ def test_nonfinite_data_reports_status():
     assert "NONFINITE" in str(e.value)
     # the plan stays usable after the error
     d[0, 1, 2, 3] = 0.0
-    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-2, rel_tol=1e-4, max_iter=200), x)
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-2, lam_relative=True, rel_tol=1e-4,
+                                                               max_iter=2000), x)
     assert info["status"] == 0
 
 

@@ -342,6 +342,30 @@ def test_cg_matches_fourier_closed_form():
     np.testing.assert_allclose(x, ref, atol=1e-8 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("n,s,r", [((12, 6, 4), 1, 0), ((12, 6, 4), 2, 1), ((18, 4, 3), 3, 2)])
+def test_operator_norm2_matches_power_iteration(n, s, r):
+    """||A||_2^2 (b = 1) from the Fourier/alias-block formula equals the
+    limit of a power iteration with the oracle's own A^T A (lambda = 0)."""
+    g = _geom(n, s=s, r=r, kmin=2, kmax=5, theta=[0.1, 0.2, 0.3, 0.4])
+    v = W.random_volume(g.shape, 5)
+    o = oracle.SolveOpts(lam=0.0)
+    lam = 0.0
+    for _ in range(400):
+        w = oracle.normal_apply(g, v, None, o)
+        lam = float(np.sum(v * w) / np.sum(v * v))
+        v = w / np.linalg.norm(w)
+    assert oracle.operator_norm2(g) == pytest.approx(lam, rel=1e-9)
+
+
+def test_relative_lambda_scales_regulariser():
+    g = _geom((8, 4, 4), s=2, kmin=2, kmax=3)
+    p = W.random_volume(g.shape, 1)
+    sig2 = oracle.operator_norm2(g)
+    a = oracle.normal_apply(g, p, None, oracle.SolveOpts(lam=1e-3, lam_relative=True))
+    b = oracle.normal_apply(g, p, None, oracle.SolveOpts(lam=1e-3 * sig2))
+    np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-13 * np.abs(b).max())
+
+
 def test_cg_fixed_iterations_and_history():
     g = _geom((8, 4, 4), kmin=2, kmax=3)
     d = W.random_portraits(g.portrait_shape, 3)

@@ -158,7 +158,8 @@ def random_portraits(shape: Tuple[int, ...], seed: int) -> np.ndarray:
 @dataclass
 class Workload:
     """One named synthetic workload: grid, harmonics, downsampling, phantom
-    recipe, SNR and solve settings."""
+    recipe, SNR and solve settings.  `lam` is relative to ||A||_2^2 (b = 1):
+    the PSF's overall scale is a free constant of the model."""
 
     name: str
     n: Tuple[int, int, int]
