@@ -150,6 +150,28 @@ mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* con
                                const mh3d_solve_opts* opts, float* const* rho_dev,
                                mh3d_solve_info* infos, void* stream);
 
+/* d_dev = A rho_dev like mh3d_forward, for callers that cannot allocate
+ * device memory (a fixed device-memory budget owned by another framework's
+ * pool, a frozen real-time memory plan, or code that must not risk the
+ * implicit synchronisation of an allocation), and therefore cannot create a
+ * plan.  No plan and no allocation: the PSF tables (built in FP64 on the host
+ * from `geom`, rounded to FP32) and the two intermediate volumes live in one
+ * fixed __device__ array that every GPU loading this library holds until
+ * exit (512 KiB of tables + 16 MiB of volumes).  The paper has no
+ * counterpart; this is a deployment variant of the forward operator.
+ *   Limits: nx*ny*nz <= 2,097,152 voxels and tables within 512 KiB, else
+ *   MH3D_ERR_UNSUPPORTED_SIZE before any work is issued; other arguments as
+ *   for mh3d_plan_create / mh3d_forward (geom->sensitivity_dev is read during
+ *   the call only).
+ *   Set-up: the first call on each device (with that device current)
+ *   resolves the array's address; make it before any stream capture.
+ *   Sharing: all calls on a device share the array; calls whose GPU work
+ *   overlaps (other streams, other threads) race and corrupt each other's
+ *   results -- serialise them.  Nothing in the array needs to start at zero.
+ *   The host table build makes this call far slower than mh3d_forward on a
+ *   plan; it is for callers that have no other option. */
+mh3d_status mh3d_forward_noalloc(const mh3d_geometry* geom, const float* rho_dev, void* d_dev, void* stream);
+
 /* *norm2 = ||A||_2^2 for b = 1: the largest eigenvalue of A^T A, evaluated
  * in FP64 at plan time from the PSF spectra.  With the separable PSF it is
  * max|Y^|^2 max|Z^|^2 max_m lambda_max(B_m), B_m the s x s alias block

@@ -55,7 +55,7 @@ class MH3DError(RuntimeError):
 _lib = None
 
 EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoint", "mh3d_normal", "mh3d_solve",
-           "mh3d_solve_host", "mh3d_solve_batched", "mh3d_operator_norm2", "mh3d_last_error",
+           "mh3d_solve_host", "mh3d_solve_batched", "mh3d_forward_noalloc", "mh3d_operator_norm2", "mh3d_last_error",
            "mh3d_plan_workspace_bytes", "mh3d_version"]
 
 
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
     lib.mh3d_solve_batched.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(mh3d_solve_opts),
                                        POINTER(c_void_p), POINTER(mh3d_solve_info), P]
     lib.mh3d_operator_norm2.argtypes = [P, POINTER(c_double)]
+    lib.mh3d_forward_noalloc.argtypes = [POINTER(mh3d_geometry), P, P, P]
     lib.mh3d_last_error.argtypes = [P]
     lib.mh3d_last_error.restype = c_char_p
     lib.mh3d_plan_workspace_bytes.argtypes = [P]
@@ -286,6 +287,47 @@ def mh3d_solve_batched(plans: Sequence[Plan], ds, opts: mh3d_solve_opts, rhos, s
         raise MH3DError(st, "mh3d_solve_batched")
     return [{"iters": infos[i].iters, "rel_res_true": infos[i].rel_res_true, "status": infos[i].status}
             for i in range(n)]
+
+
+def mh3d_forward_noalloc(n, rho, d, voxel_mm=(1.0, 1.0, 1.0), ds_factor: int = 1, ds_offset: int = 0,
+                         k_min: int = 2, k_max: int = 5, gamma_per_mm: float = 1.387016, gammaA: float = 2.0,
+                         transverse_ratio: float = 0.5, theta=None, sensitivity=None, stream=None):
+    """d = A rho without a plan and without any device allocation.
+
+    For callers that cannot allocate device memory when they need the
+    operator (a fixed memory budget owned by another pool, a frozen
+    real-time memory plan): the library keeps the tables and intermediate
+    volumes in one fixed device array (grids up to 2,097,152 voxels).  Calls
+    share that array, so calls that overlap on the GPU race; issue them on
+    one stream.  The first call on a device resolves the array's address and
+    should come before any stream capture.  `sensitivity` must already be a
+    float32 CUDA tensor (this call does not copy it to the device).
+    """
+    import torch
+
+    lib = load()
+    nx, ny, nz = (int(v) for v in n)
+    K = k_max - k_min + 1
+    g = mh3d_geometry()
+    g.n[:] = [nx, ny, nz]
+    g.voxel_mm[:] = list(voxel_mm)
+    g.drive_axis = 0
+    g.ds_factor, g.ds_offset = ds_factor, ds_offset
+    g.pad[:] = [0, 0, 0]
+    g.k_min, g.k_max = k_min, k_max
+    g.gamma_per_mm, g.gammaA, g.transverse_ratio = gamma_per_mm, gammaA, transverse_ratio
+    th = None
+    if theta is not None:
+        th = (c_double * K)(*[float(t) for t in theta])
+        g.theta = ctypes.cast(th, POINTER(c_double))
+    N = nx * ny * nz
+    g.sensitivity_dev = _dev_ptr(sensitivity, torch.float32, N, "sensitivity") if sensitivity is not None else None
+    p_rho = _dev_ptr(rho, torch.float32, N, "rho")
+    p_d = _dev_ptr(d, torch.complex64, K * nz * ny * (nx // ds_factor), "d")
+    st = lib.mh3d_forward_noalloc(ctypes.byref(g), c_void_p(p_rho), c_void_p(p_d), c_void_p(_stream_ptr(stream)))
+    if st != MH3D_OK:
+        raise MH3DError(st, "mh3d_forward_noalloc")
+    return d
 
 
 def mh3d_operator_norm2(plan: Plan) -> float:
