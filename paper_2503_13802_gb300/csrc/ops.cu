@@ -27,166 +27,9 @@
 #include <cstdio>
 
 #include "ops_kernels.cuh"
+#include "ops_functors.cuh"
 
 namespace mh3d {
-
-// ---------------------------------------------------------------------------
-// Small helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 ld2(const float* __restrict__ p, long long i, bool has2, int vec2)
-{
-    if (vec2 && has2) return *reinterpret_cast<const float2*>(p + i);
-    return make_float2(p[i], has2 ? p[i + 1] : 0.f);
-}
-__device__ __forceinline__ void st2(float* __restrict__ p, long long i, bool has2, int vec2, float2 v)
-{
-    if (vec2 && has2) {
-        *reinterpret_cast<float2*>(p + i) = v;
-    } else {
-        p[i] = v.x;
-        if (has2) p[i + 1] = v.y;
-    }
-}
-
-__device__ __forceinline__ int wrap(int a, int n) { a %= n; return a < 0 ? a + n : a; }
-
-// lambda * (R p)[i] at voxel (x, y, z).
-__device__ __forceinline__ float reg_term(const RegArgs& g, const float* __restrict__ p, long long i, int x, int y,
-                                          int z)
-{
-    const float pc = p[i];
-    if (g.kind == 0) return g.lambda * pc;
-    // T^T T = sum_a D_a^2, D_a the periodic second difference: stencil
-    // (1, -4, 6, -4, 1) along each axis.
-    const long long sy = g.nx, sz = (long long)g.nx * g.ny;
-    const long long base = i - x - (long long)y * sy - (long long)z * sz;
-    float acc = 0.f;
-    {
-        const long long r = base + (long long)y * sy + (long long)z * sz;
-        acc += p[r + wrap(x - 2, g.nx)] - 4.f * p[r + wrap(x - 1, g.nx)] + 6.f * pc
-             - 4.f * p[r + wrap(x + 1, g.nx)] + p[r + wrap(x + 2, g.nx)];
-    }
-    {
-        const long long r = base + x + (long long)z * sz;
-        acc += p[r + wrap(y - 2, g.ny) * sy] - 4.f * p[r + wrap(y - 1, g.ny) * sy] + 6.f * pc
-             - 4.f * p[r + wrap(y + 1, g.ny) * sy] + p[r + wrap(y + 2, g.ny) * sy];
-    }
-    {
-        const long long r = base + x + (long long)y * sy;
-        acc += p[r + wrap(z - 2, g.nz) * sz] - 4.f * p[r + wrap(z - 1, g.nz) * sz] + 6.f * pc
-             - 4.f * p[r + wrap(z + 1, g.nz) * sz] + p[r + wrap(z + 2, g.nz) * sz];
-    }
-    const bool shell = x < g.shell || y < g.shell || z < g.shell || x >= g.nx - g.shell || y >= g.ny - g.shell ||
-                       z >= g.nz - g.shell;
-    if (shell) acc += g.alpha * pc;
-    return g.lambda * acc;
-}
-
-// CG loop control at the start of an iteration's kernels.  Returns false
-// when the loop is finished (every CTA of the kernel returns).  The first
-// kernel of an iteration also evaluates the stopping rule and the CG beta.
-__device__ bool cg_enter(const CgCtl& c, bool first_kernel, float* beta, double* sh)
-{
-    if (*(volatile int*)&c.flags[0]) return false;
-    if (!first_kernel) return true;
-    const int it = *(volatile int*)&c.flags[1];
-    const double g_new = sum_partials(c.rr_new, c.n_rr, sh);
-    const double bn = sum_partials(c.bn, c.n_rr, sh);
-    const double rel2 = (bn > 0.0) ? g_new / bn : 0.0;
-    int status = -1;
-    if (!isfinite(g_new) || !isfinite(bn)) status = MH3D_ERR_NONFINITE;
-    else if (g_new == 0.0 || bn == 0.0) status = MH3D_OK;
-    else if (c.tol2 > 0.0 && rel2 <= c.tol2) status = MH3D_OK;
-    else if (it >= c.max_iter) status = (c.tol2 > 0.0) ? MH3D_ERR_NOT_CONVERGED : MH3D_OK;
-    const bool lead = threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0;
-    if (lead && it < c.hist_cap) c.hist[it] = sqrt(rel2);
-    if (status >= 0) {
-        if (lead) {
-            c.flags[2] = status;
-            __threadfence();
-            c.flags[0] = 1;
-            if (c.use_cond) cudaGraphSetConditional(c.cond, 0);
-        }
-        return false;
-    }
-    if (it == 0) {
-        *beta = 0.f;
-    } else {
-        const double g_old = sum_partials(c.rr_old, c.n_rr, sh);
-        *beta = (float)(g_new / g_old);
-    }
-    return true;
-}
-
-// ---------------------------------------------------------------------------
-// T pass
-// ---------------------------------------------------------------------------
-struct TLoad {
-    const TArgs* a;
-    long long base;
-    int x0;
-    float beta;
-    __device__ __forceinline__ float2 operator()(int e, int p) const
-    {
-        const int x = x0 + 2 * p;
-        if (x >= a->nx) return make_float2(0.f, 0.f);
-        const long long i = base + (long long)e * a->es + x;
-        const bool has2 = x + 1 < a->nx;
-        float2 v;
-        if (a->pupdate) {
-            const float2 rr = ld2(a->rvec, i, has2, a->vec2);
-            const float2 pp = ld2(a->pvec, i, has2, a->vec2);
-            v = make_float2(fmaf(beta, pp.x, rr.x), fmaf(beta, pp.y, rr.y));
-            st2(a->pvec, i, has2, a->vec2, v);
-        } else {
-            v = ld2(a->in, i, has2, a->vec2);
-        }
-        if (a->bin) {
-            const float2 bb = ld2(a->bin, i, has2, a->vec2);
-            v.x *= bb.x;
-            v.y *= bb.y;
-        }
-        return v;
-    }
-};
-
-struct MulLd {
-    const float2* b;
-    int ld;
-    const float2* mu;
-    __device__ __forceinline__ float2 operator()(int e, int p) const { return c_mul(b[e * ld + p], mu[e]); }
-};
-
-struct TStore {
-    const TArgs* a;
-    long long base;
-    int x0;
-    DotAcc* acc;
-    __device__ __forceinline__ void operator()(int e, int p, float2 v) const
-    {
-        const int x = x0 + 2 * p;
-        if (x >= a->nx) return;
-        const long long i = base + (long long)e * a->es + x;
-        const bool has2 = x + 1 < a->nx;
-        if (a->bout) {
-            const float2 bb = ld2(a->bout, i, has2, a->vec2);
-            v.x *= bb.x;
-            v.y *= bb.y;
-        }
-        if (a->epilogue) {
-            const RegArgs& g = a->reg;
-            const long long sz = (long long)g.nx * g.ny;
-            const int z = (int)(i / sz), y = (int)((i - (long long)z * sz) / g.nx);
-            v.x += reg_term(g, a->pin, i, x, y, z);
-            if (has2) v.y += reg_term(g, a->pin, i + 1, x + 1, y, z);
-            st2(a->qvec, i, has2, a->vec2, v);
-            acc->add(a->pin[i], v.x);
-            if (has2) acc->add(a->pin[i + 1], v.y);
-        } else {
-            st2(a->out, i, has2, a->vec2, v);
-        }
-    }
-};
 
 __global__ void __launch_bounds__(256) k_tpass(const TArgs a)
 {
@@ -222,138 +65,12 @@ int tpass_blocks(int nx, int cols, int nouter) { return ((nx + cols - 1) / cols)
 
 cudaError_t run_tpass(const TArgs& a, int nouter, cudaStream_t st)
 {
+    if (ct_tpass_available(a.n, a.cols)) return run_tpass_ct(a, nouter, st);
     dim3 grid((a.nx + a.cols - 1) / a.cols, nouter);
     const size_t smem = tpass_smem_bytes(a.n, a.cols);
     k_tpass<<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
-
-// ---------------------------------------------------------------------------
-// X pass: loaders and storers
-// ---------------------------------------------------------------------------
-// Pencil p of a row-pair batch = rows (row0 + 2p, row0 + 2p + 1) as re/im.
-struct RowPairLd {
-    const float* v;
-    int nx, row0, rows;
-    __device__ __forceinline__ float2 operator()(int e, int p) const
-    {
-        const int r = row0 + 2 * p;
-        float2 o = make_float2(0.f, 0.f);
-        if (r < rows) o.x = v[(long long)r * nx + e];
-        if (r + 1 < rows) o.y = v[(long long)(r + 1) * nx + e];
-        return o;
-    }
-};
-struct RowPairSt {
-    float* v;
-    int nx, row0, rows;
-    __device__ __forceinline__ void operator()(int e, int p, float2 val) const
-    {
-        const int r = row0 + 2 * p;
-        if (r < rows) v[(long long)r * nx + e] = val.x;
-        if (r + 1 < rows) v[(long long)(r + 1) * nx + e] = val.y;
-    }
-};
-
-// Forward: portrait spectrum of harmonic k0 + q / P at bin m =
-// sum_{j < s} A[m + j mx] Xhat_k[m + j mx]   (the fold that realises P).
-struct FoldLd {
-    const float2* A;
-    int ldA;
-    const float2* __restrict__ Xh;   // Xhat + k0 * nx
-    int nx, mx, s, P;
-    __device__ __forceinline__ float2 operator()(int m, int q) const
-    {
-        const int kk = q / P, p = q - kk * P;
-        const float2* xk = Xh + (long long)kk * nx;
-        float2 acc = c_mul(A[m * ldA + p], __ldg(xk + m));
-        for (int j = 1; j < s; ++j) {
-            const int w = m + j * mx;
-            acc = c_add(acc, c_mul(A[w * ldA + p], __ldg(xk + w)));
-        }
-        return acc;
-    }
-};
-
-struct PortraitSt {
-    float2* d;
-    const float2* __restrict__ phase;   // phase + k0
-    long long M;
-    int mx, row0, rows, P;
-    __device__ __forceinline__ void operator()(int m, int q, float2 val) const
-    {
-        const int kk = q / P, p = q - kk * P;
-        const float2 ph = __ldg(phase + kk);
-        const int r = row0 + 2 * p;
-        float2* dk = d + (long long)kk * M;
-        if (r < rows) dk[(long long)r * mx + m] = make_float2(ph.x * val.x, ph.y * val.x);
-        if (r + 1 < rows) dk[(long long)(r + 1) * mx + m] = make_float2(ph.x * val.y, ph.y * val.y);
-    }
-};
-
-// Adjoint: (Re(e^{-i theta} y[row]), Re(e^{-i theta} y[row+1])) at sample m.
-struct PortraitLd {
-    const float2* __restrict__ d;
-    const float2* __restrict__ phase;
-    long long M;
-    int mx, row0, rows, P;
-    __device__ __forceinline__ float2 operator()(int m, int q) const
-    {
-        const int kk = q / P, p = q - kk * P;
-        const float2 ph = __ldg(phase + kk);
-        const int r = row0 + 2 * p;
-        const float2* dk = d + (long long)kk * M;
-        float2 o = make_float2(0.f, 0.f);
-        if (r < rows) {
-            const float2 y = dk[(long long)r * mx + m];
-            o.x = fmaf(ph.x, y.x, ph.y * y.y);
-        }
-        if (r + 1 < rows) {
-            const float2 y = dk[(long long)(r + 1) * mx + m];
-            o.y = fmaf(ph.x, y.x, ph.y * y.y);
-        }
-        return o;
-    }
-};
-
-// Normal: out[m + a mx] = sum_b Q[m][a][b] A[m + b mx].
-struct QLd {
-    const float2* A;
-    int ldA;
-    const float2* __restrict__ Q;
-    int mx, s;
-    __device__ __forceinline__ float2 operator()(int w, int p) const
-    {
-        const int a = w / mx, m = w - a * mx;
-        const float2* qm = Q + ((long long)m * s + a) * s;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int b = 0; b < s; ++b) acc = c_add(acc, c_mul(__ldg(qm + b), A[(m + b * mx) * ldA + p]));
-        return acc;
-    }
-};
-
-// Normal epilogue: q = b w + lambda R p, accumulating p^T q.
-struct NrmEpiSt {
-    const XArgs* a;
-    int row0;
-    DotAcc* acc;
-    __device__ __forceinline__ void one(int r, int x, float w) const
-    {
-        const long long i = (long long)r * a->nx + x;
-        float q = a->b ? a->b[i] * w : w;
-        const RegArgs& g = a->reg;
-        const int z = r / g.ny, y = r - z * g.ny;
-        q += reg_term(g, a->pin, i, x, y, z);
-        a->qout[i] = q;
-        acc->add(a->pin[i], q);
-    }
-    __device__ __forceinline__ void operator()(int x, int p, float2 val) const
-    {
-        const int r = row0 + 2 * p;
-        if (r < a->rows) one(r, x, val.x);
-        if (r + 1 < a->rows) one(r + 1, x, val.y);
-    }
-};
 
 // ---------------------------------------------------------------------------
 // X pass kernels
@@ -449,16 +166,19 @@ int xpass_blocks(int rows, int pairs) { return (rows + 2 * pairs - 1) / (2 * pai
 
 cudaError_t run_xfwd(const XArgs& a, cudaStream_t st)
 {
+    if (ct_xpass_available(a.nx, a.s, a.pairs)) return run_xfwd_ct(a, st);
     k_xfwd<<<xpass_blocks(a.rows, a.pairs), 256, xfwd_smem_bytes(a.nx, a.mx, a.pairs, a.kg), st>>>(a);
     return cudaGetLastError();
 }
 cudaError_t run_xadj(const XArgs& a, cudaStream_t st)
 {
+    if (ct_xpass_available(a.nx, a.s, a.pairs)) return run_xadj_ct(a, st);
     k_xadj<<<xpass_blocks(a.rows, a.pairs), 256, xadj_smem_bytes(a.nx, a.mx, a.pairs, a.kg), st>>>(a);
     return cudaGetLastError();
 }
 cudaError_t run_xnrm(const XArgs& a, cudaStream_t st)
 {
+    if (ct_xpass_available(a.nx, a.s, a.pairs)) return run_xnrm_ct(a, st);
     k_xnrm<<<xpass_blocks(a.rows, a.pairs), 256, xnrm_smem_bytes(a.nx, a.pairs), st>>>(a);
     return cudaGetLastError();
 }
@@ -484,7 +204,7 @@ cudaError_t ops_set_attributes()
     if ((e = opt_in_smem(k_xfwd, optin)) != cudaSuccess) return e;
     if ((e = opt_in_smem(k_xadj, optin)) != cudaSuccess) return e;
     if ((e = opt_in_smem(k_xnrm, optin)) != cudaSuccess) return e;
-    return cudaSuccess;
+    return ct_set_attributes(optin);
 }
 
 }  // namespace mh3d

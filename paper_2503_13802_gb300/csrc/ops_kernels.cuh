@@ -112,6 +112,15 @@ cudaError_t run_xfwd(const XArgs& a, cudaStream_t st);
 cudaError_t run_xadj(const XArgs& a, cudaStream_t st);
 cudaError_t run_xnrm(const XArgs& a, cudaStream_t st);
 int tpass_blocks(int nx, int cols, int nouter);
+
+// Compile-time specialised kernels (ops_ct.cu) for the common lengths.
+bool ct_tpass_available(int n, int cols);
+bool ct_xpass_available(int nx, int s, int pairs);
+cudaError_t ct_set_attributes(int optin);
+cudaError_t run_tpass_ct(const TArgs& a, int nouter, cudaStream_t st);
+cudaError_t run_xfwd_ct(const XArgs& a, cudaStream_t st);
+cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st);
+cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st);
 int xpass_blocks(int rows, int pairs);
 cudaError_t ops_set_attributes();
 

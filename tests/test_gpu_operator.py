@@ -17,12 +17,24 @@ torch = pytest.importorskip("torch")
 TOL = 1e-5
 
 
+@pytest.fixture(params=["specialised", "generic"])
+def kernel_path(request, monkeypatch):
+    """Run each operator test on the compile-time specialised kernels (the
+    default for the common lengths) and again with MH3D_GENERIC=1, which
+    forces the runtime-general kernels for every size."""
+    if request.param == "generic":
+        monkeypatch.setenv("MH3D_GENERIC", "1")
+    else:
+        monkeypatch.delenv("MH3D_GENERIC", raising=False)
+    return request.param
+
+
 def _dev(a, dtype):
     return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
 
 
 @pytest.mark.parametrize("name", list(OP_CASES))
-def test_forward_matches_oracle(name):
+def test_forward_matches_oracle(name, kernel_path):
     p = OP_CASES[name]
     g = oracle_geom(p)
     b = sens_map(p)
@@ -40,7 +52,7 @@ def test_forward_matches_oracle(name):
 
 
 @pytest.mark.parametrize("name", list(OP_CASES))
-def test_adjoint_matches_oracle(name):
+def test_adjoint_matches_oracle(name, kernel_path):
     p = OP_CASES[name]
     g = oracle_geom(p)
     b = sens_map(p)
@@ -57,7 +69,7 @@ def test_adjoint_matches_oracle(name):
 @pytest.mark.parametrize("name", ["cube32_k4", "ds2_theta", "ds3_radix3", "odd_nx27", "tall_z"])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("reg_kind", [0, 1])
-def test_normal_matches_oracle(name, mode, reg_kind):
+def test_normal_matches_oracle(name, mode, reg_kind, kernel_path):
     p = OP_CASES[name]
     g = oracle_geom(p)
     b = sens_map(p)
@@ -112,7 +124,7 @@ def test_gpu_adjoint_identity_fp64_dots():
     assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(x) * np.linalg.norm(y) * 0.1
 
 
-def test_full_size_128x128x64_forward_adjoint():
+def test_full_size_128x128x64_forward_adjoint(kernel_path):
     """The 128x128x64, K = 8 (k = 2..9), s = 2 workload with a Gaussian
     sensitivity map, at full size in the launch configuration the benchmark
     uses: whole-array comparison with the oracle."""
