@@ -98,6 +98,12 @@ typedef struct {
     int lambda_relative;         /* nonzero: the weight of R is lambda * ||A||_2^2, the     */
                                  /* squared spectral norm of A with b = 1 (see              */
                                  /* mh3d_operator_norm2); zero: lambda is absolute          */
+    int cg_variant;              /* 0 = single-reduction CG (Chronopoulos-Gear): the vector */
+                                 /*     update runs inside the operator's first pass, one   */
+                                 /*     grid reduction per iteration;                       */
+                                 /* 1 = classic CG (Hestenes-Stiefel), two reductions and a */
+                                 /*     separate update pass.  Same iterates in exact       */
+                                 /*     arithmetic.                                         */
 } mh3d_solve_opts;
 
 typedef struct {
@@ -126,7 +132,8 @@ mh3d_status mh3d_forward(mh3d_plan plan, const float* rho_dev, void* d_dev, void
 mh3d_status mh3d_adjoint(mh3d_plan plan, const void* d_dev, float* rho_dev, void* stream);
 
 /* q_dev = (A^T A + lambda R) p_dev with R from opts (reg_kind, lambda, alpha,
- * shell); opts->normal_mode picks the fused or the explicit evaluation. */
+ * shell); opts->normal_mode picks the fused or the explicit evaluation.
+ * p_dev and q_dev must not overlap. */
 mh3d_status mh3d_normal(mh3d_plan plan, const float* p_dev, float* q_dev,
                         const mh3d_solve_opts* opts, void* stream);
 

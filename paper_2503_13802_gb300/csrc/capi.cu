@@ -1,5 +1,6 @@
 // Plan construction and operator entry points of the C ABI (include/mh3d.h).
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -167,6 +168,7 @@ TArgs tpass_args(const Plan& P, int axis /*1 = y, 2 = z*/, const float* in, floa
     a.nx = P.nx;
     a.cols = P.tile.tpass_cols;
     a.vec2 = (P.nx % 2 == 0) ? 1 : 0;
+    a.vec4 = (P.nx % 4 == 0 && ((uintptr_t)P.sens % 16) == 0) ? 1 : 0;
     if (axis == 1) {
         a.rp = P.ay.rp;
         a.tw = P.ay.tw;
@@ -206,6 +208,7 @@ XArgs xpass_args(const Plan& P)
     a.M = (long long)a.rows * P.mx;
     a.pairs = P.tile.xpass_pairs;
     a.kg = P.tile.xpass_kgroup;
+    a.vec4 = (P.nx % 4 == 0 && ((uintptr_t)P.sens % 16) == 0) ? 1 : 0;
     a.reg.nx = P.nx;
     a.reg.ny = P.ny;
     a.reg.nz = P.nz;
@@ -253,29 +256,32 @@ cudaError_t launch_adjoint(const Plan& P, const float2* d, float* rho, float* t1
     return run_tpass(ty, tpass_outer(P, 1), st);
 }
 
-// q = (A^T A + lambda R) p.  mode 0: fused Fourier-block normal operator;
-// mode 1: explicit A then A^T through the portrait buffer.  `part` (may be
-// null) receives per-CTA partials of p^T q; cg (may be null) is the loop
-// control of a CG iteration.
-cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const float* p, float* q, float* t1,
-                          float* t2, float2* portrait, double* part, const CgCtl* cg, float* pupd_p,
-                          const float* pupd_r, cudaStream_t st)
+// out = (A^T A + lambda R) in.  mode 0: fused Fourier-block normal operator;
+// mode 1: explicit A then A^T through the portrait buffer.  `dots` (may be
+// null) receives in^T out (and in^T in when dots->part2 is set) as grid
+// totals; `cg` (may be null) is the loop control of a CG iteration; `upd`
+// (may be null) fuses a CG vector update into the first pass's loader, in
+// which case `in` is the vector that update produces.
+cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const float* in, float* out, float* t1,
+                          float* t2, float2* portrait, const RedSink* dots, const CgCtl* cg, const LoaderUpdate* upd,
+                          cudaStream_t st)
 {
     cudaError_t e;
-    const bool upd = pupd_p != nullptr;
-    TArgs ty = tpass_args(P, 1, p, t1, mode == 0 ? P.Ynorm : P.Yhat);
+    TArgs ty = tpass_args(P, 1, in, t1, mode == 0 ? P.Ynorm : P.Yhat);
     ty.bin = P.sens;
-    if (upd) {
-        ty.pupdate = 1;
-        ty.pvec = pupd_p;
-        ty.rvec = pupd_r;
+    if (upd && upd->mode) {
+        ty.pupdate = upd->mode;
+        ty.pvec = upd->p;
+        ty.rvec = upd->r;
+        ty.rvec_w = upd->r_w;
+        ty.qdir = upd->q;
+        ty.svec = upd->s;
+        ty.xvec = upd->x;
     }
     if (cg) ty.cg = *cg;
     if ((e = run_tpass(ty, tpass_outer(P, 1), st)) != cudaSuccess) return e;
     CgCtl cgp;
-    if (cg) {
-        cgp = *cg;   // later kernels only check the done flag
-    }
+    if (cg) cgp = *cg;   // later kernels only check the done flag
     TArgs tz = tpass_args(P, 2, t1, t2, mode == 0 ? P.Znorm : P.Zhat);
     if (cg) tz.cg = cgp;
     if ((e = run_tpass(tz, tpass_outer(P, 2), st)) != cudaSuccess) return e;
@@ -283,25 +289,29 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
         XArgs x = xpass_args(P);
         x.vin = t2;
         x.b = P.sens;
-        x.pin = p;
-        x.qout = q;
-        x.part = part;
+        x.pin = in;
+        x.qout = out;
+        if (dots) {
+            x.part = dots->part;
+            x.ticket = dots->ticket;
+            x.sum_out = dots->out;
+            x.part2 = dots->part2;
+            x.sum_out2 = dots->out2;
+        }
         x.reg = reg;
         if (cg) {
             x.cg = cgp;
             x.cg_active = 1;
+            x.count_iter = cg->cgcg;
         }
         return run_xnrm(x, st);
     }
+    // Explicit mode.  The drive-axis kernels carry no loop control: once the
+    // loop has finished, the first pass returns early and leaves t2 as it
+    // was, so recomputing them is harmless (the epilogue pass checks the flag).
     XArgs xf = xpass_args(P);
     xf.vin = t2;
     xf.dout = portrait;
-    if (cg) {
-        // the forward/adjoint X kernels carry no CG control: a finished loop
-        // is detected by the T pass before them, which leaves t2 unchanged;
-        // recomputing on stale inputs is harmless because the update kernel
-        // checks the flag.
-    }
     if ((e = run_xfwd(xf, st)) != cudaSuccess) return e;
     XArgs xa = xpass_args(P);
     xa.din = portrait;
@@ -313,11 +323,20 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
     TArgs ty2 = tpass_args(P, 1, t2, nullptr, P.Yhat_adj);
     ty2.bout = P.sens;
     ty2.epilogue = 1;
-    ty2.qvec = q;
-    ty2.pin = p;
-    ty2.part = part;
+    ty2.qvec = out;
+    ty2.pin = in;
+    if (dots) {
+        ty2.part = dots->part;
+        ty2.ticket = dots->ticket;
+        ty2.sum_out = dots->out;
+        ty2.part2 = dots->part2;
+        ty2.sum_out2 = dots->out2;
+    }
     ty2.reg = reg;
-    if (cg) ty2.cg = cgp;
+    if (cg) {
+        ty2.cg = cgp;
+        ty2.count_iter = cg->cgcg;
+    }
     return run_tpass(ty2, tpass_outer(P, 1), st);
 }
 
@@ -496,7 +515,7 @@ mh3d_status mh3d_normal(mh3d_plan P, const float* p, float* q, const mh3d_solve_
         if (s != MH3D_OK) return s;
     }
     MH3D_TRY(P, launch_normal(*P, o->normal_mode, reg_args(*P, *o), p, q, P->w.t1, P->w.t2, P->w.portrait,
-                              nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream));
+                              nullptr, nullptr, nullptr, (cudaStream_t)stream));
     return MH3D_OK;
 }
 

@@ -294,4 +294,65 @@ __device__ __forceinline__ double sum_partials(const double* __restrict__ part, 
     return r;
 }
 
+// Grid-wide deterministic FP64 reduction.  Each block stores its partial
+// (v valid in thread 0) at part[bid]; the last block to arrive (atomic
+// ticket) sums part[0..nparts) in index order and stores the total in *out,
+// then re-arms the ticket counter for the next launch.  Consumers read the
+// single scalar.
+__device__ __forceinline__ void grid_sum_finalize(double v, double* part, int bid, int nparts, unsigned int* counter,
+                                                  double* out, double* sh)
+{
+    __shared__ int am_last;
+    if (threadIdx.x == 0) {
+        part[bid] = v;
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        am_last = (t == (unsigned int)nparts - 1u);
+    }
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += __ldcg(part + i);
+        acc = block_sum_f64(acc, sh);
+        if (threadIdx.x == 0) {
+            *out = acc;
+            *counter = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// Two totals with one ticket: the last block sums both partial arrays.
+__device__ __forceinline__ void grid_sum_finalize2(double v0, double v1, double* part0, double* part1, int bid,
+                                                   int nparts, unsigned int* counter, double* out0, double* out1,
+                                                   double* sh)
+{
+    __shared__ int am_last2;
+    if (threadIdx.x == 0) {
+        part0[bid] = v0;
+        part1[bid] = v1;
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        am_last2 = (t == (unsigned int)nparts - 1u);
+    }
+    __syncthreads();
+    if (am_last2) {
+        __threadfence();
+        double a0 = 0.0, a1 = 0.0;
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+            a0 += __ldcg(part0 + i);
+            a1 += __ldcg(part1 + i);
+        }
+        a0 = block_sum_f64(a0, sh);
+        a1 = block_sum_f64(a1, sh);
+        if (threadIdx.x == 0) {
+            *out0 = a0;
+            *out1 = a1;
+            *counter = 0u;
+            __threadfence();
+        }
+    }
+}
+
 }  // namespace mh3d

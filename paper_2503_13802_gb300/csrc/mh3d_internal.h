@@ -48,6 +48,7 @@ struct SolveWork {
     float* t1 = nullptr;
     float* t2 = nullptr;
     float* rhs = nullptr;
+    float* s = nullptr;           // A r (single-reduction CG)
     float2* portrait = nullptr;   // explicit mode only (allocated on first use)
     double* red = nullptr;        // reduction partials (see solve.cu)
     int* flags = nullptr;         // [done, iters, status, spare]

@@ -35,8 +35,8 @@ __global__ void __launch_bounds__(256) k_tpass(const TArgs a)
 {
     extern __shared__ float2 sm[];
     __shared__ double red[34];
-    float beta = 0.f;
-    if (a.cg.flags && !cg_enter(a.cg, a.pupdate != 0, &beta, red)) return;
+    float beta = 0.f, alpha = 0.f;
+    if (a.cg.flags && !cg_enter(a.cg, a.pupdate != 0, &beta, red, &alpha)) return;
     const int n = a.n, P = a.cols / 2, ld = P + 1;
     float2* tw = sm;
     float2* mu = tw + n;
@@ -52,13 +52,21 @@ __global__ void __launch_bounds__(256) k_tpass(const TArgs a)
     const int res = fft_result_index(a.rp.nst);
     float2* sr = res ? s1 : s0;
     float2* so = res ? s0 : s1;
-    DotAcc acc;
-    fft_run<false, true, true>(a.rp, TLoad{&a, base, x0, beta}, BufSt{sr, ld}, s0, s1, ld, P, tw);
-    fft_run<true, true, true>(a.rp, MulLd{sr, ld, mu}, TStore{&a, base, x0, &acc}, so, sr, ld, P, tw);
+    DotAcc acc, acc2;
+    fft_run<false, true, true>(a.rp, TLoad{&a, base, x0, beta, alpha}, BufSt{sr, ld}, s0, s1, ld, P, tw);
+    fft_run<true, true, true>(a.rp, MulLd{sr, ld, mu}, TStore{&a, base, x0, &acc, a.part2 ? &acc2 : nullptr}, so,
+                              sr, ld, P, tw);
     if (a.epilogue && a.part) {
         const double t = block_sum_f64(acc.value(), red);
-        if (threadIdx.x == 0) a.part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+        const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+        if (a.part2) {
+            const double t2 = block_sum_f64(acc2.value(), red);
+            grid_sum_finalize2(t, t2, a.part, a.part2, bid, nb, a.ticket, a.sum_out, a.sum_out2, red);
+        } else {
+            grid_sum_finalize(t, a.part, bid, nb, a.ticket, a.sum_out, red);
+        }
     }
+    if (a.count_iter) cg_count_iteration(a.cg);
 }
 
 int tpass_blocks(int nx, int cols, int nouter) { return ((nx + cols - 1) / cols) * nouter; }
@@ -153,13 +161,20 @@ __global__ void __launch_bounds__(256) k_xnrm(const XArgs a)
     const int res = fft_result_index(a.rpx.nst);
     float2* Ar = res ? A1 : A0;
     float2* Ao = res ? A0 : A1;
-    DotAcc dacc;
+    DotAcc dacc, dacc2;
     fft_run<false, false, true>(a.rpx, RowPairLd{a.vin, nx, row0, a.rows}, BufSt{Ar, ldA}, A0, A1, ldA, P, twx);
-    fft_run<true, true, false>(a.rpx, QLd{Ar, ldA, a.Q, a.mx, a.s}, NrmEpiSt{&a, row0, &dacc}, Ao, Ar, ldA, P, twx);
+    fft_run<true, true, false>(a.rpx, QLd{Ar, ldA, a.Q, a.mx, a.s},
+                               NrmEpiSt{&a, row0, &dacc, a.part2 ? &dacc2 : nullptr}, Ao, Ar, ldA, P, twx);
     if (a.part) {
         const double t = block_sum_f64(dacc.value(), red);
-        if (threadIdx.x == 0) a.part[blockIdx.x] = t;
+        if (a.part2) {
+            const double t2 = block_sum_f64(dacc2.value(), red);
+            grid_sum_finalize2(t, t2, a.part, a.part2, blockIdx.x, gridDim.x, a.ticket, a.sum_out, a.sum_out2, red);
+        } else {
+            grid_sum_finalize(t, a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out, red);
+        }
     }
+    if (a.count_iter) cg_count_iteration(a.cg);
 }
 
 int xpass_blocks(int rows, int pairs) { return (rows + 2 * pairs - 1) / (2 * pairs); }

@@ -55,6 +55,87 @@ __device__ __forceinline__ void fused_conv_stage(const LD& ld, const ST& st, con
     }
 }
 
+// Elementwise pre-pass of a T-pass tile (n elements x 2P columns): the CG
+// update of the loader modes 1/2, with every global load of a thread issued
+// before any of its stores (the updated vectors are read and written in
+// place, which the compiler cannot reorder across), float4 along x.  The
+// operator input b * (p or r) goes to shared memory in the pencil layout
+// (element e of column pair p at buf[e * P + p]).
+template <int N, int P, int T>
+__device__ __forceinline__ void tpass_cg_prepass(const TArgs& a, long long base, int x0, float beta, float alpha,
+                                                 float2* __restrict__ buf)
+{
+    constexpr int V = 2 * P / 4;              // float4 per tile row
+    constexpr int TOTAL = N * V;
+    constexpr int ITER = (TOTAL + T - 1) / T;
+    const bool vec4 = a.vec4 && (x0 + 2 * P <= a.nx);
+    if (!vec4) {                              // ragged tile: scalar through the loader functor
+        const TLoad ld{&a, base, x0, beta, alpha};
+        for (int idx = threadIdx.x; idx < N * P; idx += T) {
+            const int p = idx % P, e = idx / P;
+            buf[e * P + p] = ld(e, p);
+        }
+        return;
+    }
+    float* __restrict__ pv = a.pvec;
+    const float* __restrict__ rv = a.rvec;
+    const float* __restrict__ bv = a.bin;
+    constexpr int CH = ITER < 4 ? ITER : 4;   // iterations whose loads are in flight together
+    for (int it0 = 0; it0 < ITER; it0 += CH) {
+        float4 R[CH], Pp[CH], B[CH], S[CH], Q[CH], X[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int idx = (int)threadIdx.x + (it0 + u) * T;
+            if (it0 + u >= ITER || ((TOTAL % T) != 0 && idx >= TOTAL)) break;
+            const int c = idx % V, e = idx / V;
+            const long long i = base + (long long)e * a.es + x0 + 4 * c;
+            R[u] = __ldcg(reinterpret_cast<const float4*>(rv + i));
+            Pp[u] = __ldcg(reinterpret_cast<const float4*>(pv + i));
+            B[u] = bv ? __ldg(reinterpret_cast<const float4*>(bv + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
+            if (a.pupdate == 2) {
+                S[u] = __ldcg(reinterpret_cast<const float4*>(a.svec + i));
+                Q[u] = __ldcg(reinterpret_cast<const float4*>(a.qdir + i));
+                X[u] = __ldcg(reinterpret_cast<const float4*>(a.xvec + i));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int idx = (int)threadIdx.x + (it0 + u) * T;
+            if (it0 + u >= ITER || ((TOTAL % T) != 0 && idx >= TOTAL)) break;
+            const int c = idx % V, e = idx / V;
+            const long long i = base + (long long)e * a.es + x0 + 4 * c;
+            float4 pn, out;
+            pn.x = fmaf(beta, Pp[u].x, R[u].x);
+            pn.y = fmaf(beta, Pp[u].y, R[u].y);
+            pn.z = fmaf(beta, Pp[u].z, R[u].z);
+            pn.w = fmaf(beta, Pp[u].w, R[u].w);
+            *reinterpret_cast<float4*>(pv + i) = pn;
+            if (a.pupdate == 2) {
+                float4 qn, xn;
+                qn.x = fmaf(beta, Q[u].x, S[u].x);
+                qn.y = fmaf(beta, Q[u].y, S[u].y);
+                qn.z = fmaf(beta, Q[u].z, S[u].z);
+                qn.w = fmaf(beta, Q[u].w, S[u].w);
+                xn.x = fmaf(alpha, pn.x, X[u].x);
+                xn.y = fmaf(alpha, pn.y, X[u].y);
+                xn.z = fmaf(alpha, pn.z, X[u].z);
+                xn.w = fmaf(alpha, pn.w, X[u].w);
+                out.x = fmaf(-alpha, qn.x, R[u].x);
+                out.y = fmaf(-alpha, qn.y, R[u].y);
+                out.z = fmaf(-alpha, qn.z, R[u].z);
+                out.w = fmaf(-alpha, qn.w, R[u].w);
+                *reinterpret_cast<float4*>(a.qdir + i) = qn;
+                *reinterpret_cast<float4*>(a.xvec + i) = xn;
+                *reinterpret_cast<float4*>(a.rvec_w + i) = out;
+            } else {
+                out = pn;
+            }
+            buf[e * P + 2 * c] = make_float2(out.x * B[u].x, out.y * B[u].y);
+            buf[e * P + 2 * c + 1] = make_float2(out.z * B[u].z, out.w * B[u].w);
+        }
+    }
+}
+
 // T pass along y or z: TArgs as in ops.cu with cols = 2 kP.
 template <class L>
 __global__ void __launch_bounds__(kT) k_tpass_ct(const TArgs a)
@@ -63,10 +144,11 @@ __global__ void __launch_bounds__(kT) k_tpass_ct(const TArgs a)
     constexpr int N = I::n(), NST = I::nst, RL = I::last();
     using LI = Reverse<L>;
     constexpr int P = kP, T = kT;
+    static_assert(NST >= 2, "the specialised T pass has at least two stages");
     extern __shared__ float2 sm[];
     __shared__ double red[34];
-    float beta = 0.f;
-    if (a.cg.flags && !cg_enter(a.cg, a.pupdate != 0, &beta, red)) return;
+    float beta = 0.f, alpha = 0.f;
+    if (a.cg.flags && !cg_enter(a.cg, a.pupdate != 0, &beta, red, &alpha)) return;
     float2* tw = sm;
     float2* mu = tw + N;
     float2* b0 = mu + N;
@@ -75,27 +157,37 @@ __global__ void __launch_bounds__(kT) k_tpass_ct(const TArgs a)
         tw[i] = a.tw[i];
         mu[i] = a.mult[i];
     }
-    __syncthreads();
     const int x0 = blockIdx.x * 2 * P;
     const long long base = (long long)blockIdx.y * a.os;
-    DotAcc acc;
-    const TLoad ld{&a, base, x0, beta};
-    const TStore st{&a, base, x0, &acc};
-    if constexpr (NST == 1) {
-        fused_conv_stage<N, RL, P, T>(ld, st, mu, tw);
-    } else {
-        constexpr int pf = result_parity<0, NST - 1>();
-        float2* fo = pf ? b1 : b0;   // output of forward stage NST-2
-        float2* fx = pf ? b0 : b1;
-        run_stages<L, 0, NST - 1, P, T, 1, false, true, true>(ld, BufSt{fo, P}, b0, b1, P, tw);
-        fused_conv_stage<N, RL, P, T>(BufLd{fo, P}, BufSt{fx, P}, mu, tw);
+    DotAcc acc, acc2;
+    const TLoad ld{&a, base, x0, beta, alpha};
+    const TStore st{&a, base, x0, &acc, a.part2 ? &acc2 : nullptr};
+    constexpr int pf = result_parity<0, NST - 1>();
+    float2* fo = pf ? b1 : b0;   // output of forward stage NST-2
+    float2* fx = pf ? b0 : b1;
+    if (a.pupdate) {
+        // stage 0 then reads b1 and writes b0 (or fo), so b1 is free here
+        tpass_cg_prepass<N, P, T>(a, base, x0, beta, alpha, b1);
         __syncthreads();
-        run_stages<LI, 1, NST, P, T, 1, true, true, true>(BufLd{fx, P}, st, fo, fx, P, tw);
+        run_stages<L, 0, NST - 1, P, T, 1, false, true, true>(BufLd{b1, P}, BufSt{fo, P}, b0, b1, P, tw);
+    } else {
+        __syncthreads();
+        run_stages<L, 0, NST - 1, P, T, 1, false, true, true>(ld, BufSt{fo, P}, b0, b1, P, tw);
     }
+    fused_conv_stage<N, RL, P, T>(BufLd{fo, P}, BufSt{fx, P}, mu, tw);
+    __syncthreads();
+    run_stages<LI, 1, NST, P, T, 1, true, true, true>(BufLd{fx, P}, st, fo, fx, P, tw);
     if (a.epilogue && a.part) {
         const double t = block_sum_f64(acc.value(), red);
-        if (threadIdx.x == 0) a.part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+        const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+        if (a.part2) {
+            const double t2 = block_sum_f64(acc2.value(), red);
+            grid_sum_finalize2(t, t2, a.part, a.part2, bid, nb, a.ticket, a.sum_out, a.sum_out2, red);
+        } else {
+            grid_sum_finalize(t, a.part, bid, nb, a.ticket, a.sum_out, red);
+        }
     }
+    if (a.count_iter) cg_count_iteration(a.cg);
 }
 
 template <class L>
@@ -278,6 +370,87 @@ constexpr size_t xadj_ct_smem()
     return sizeof(float2) * (nx + 2 * nx * kP);
 }
 
+// Storer into a row-major staging tile: pencil p's real part is tile row
+// 2p, its imaginary part row 2p + 1.
+struct RowStageSt {
+    float* stg;
+    int nx;
+    __device__ __forceinline__ void operator()(int e, int p, float2 v) const
+    {
+        stg[(2 * p) * nx + e] = v.x;
+        stg[(2 * p + 1) * nx + e] = v.y;
+    }
+};
+
+// Normal-operator epilogue over a staged tile of ROWS rows:
+// q = b w + lambda R p, with p^T q (and p^T p) accumulated.
+template <int NX, int ROWS, int T>
+__device__ __forceinline__ void nrm_epilogue(const XArgs& a, int row0, const float* __restrict__ stg, DotAcc* acc,
+                                             DotAcc* acc2)
+{
+    constexpr int V = NX / 4;
+    constexpr int TOTAL = ROWS * V;
+    constexpr int ITER = (TOTAL + T - 1) / T;
+    static_assert(NX % 4 == 0, "tile rows are read as float4");
+    const float* __restrict__ bp = a.b;
+    const float* __restrict__ pp = a.pin;
+    float* __restrict__ qp = a.qout;
+    if (!a.vec4 || a.reg.kind != 0) {
+        for (int idx = threadIdx.x; idx < ROWS * NX; idx += T) {
+            const int rr = idx / NX, x = idx - rr * NX;
+            const int r = row0 + rr;
+            if (r >= a.rows) continue;
+            const long long i = (long long)r * NX + x;
+            const float w = stg[rr * NX + x];
+            float q = bp ? bp[i] * w : w;
+            const int z = r / a.reg.ny, y = r - z * a.reg.ny;
+            q += reg_term(a.reg, pp, i, x, y, z);
+            qp[i] = q;
+            const float pv = pp[i];
+            acc->add(pv, q);
+            if (acc2) acc2->add(pv, pv);
+        }
+        return;
+    }
+    float4 W[ITER], B[ITER], Pv[ITER];
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int idx = (int)threadIdx.x + it * T;
+        const int rr = idx / V, c = idx - rr * V;
+        const int r = row0 + rr;
+        if (((TOTAL % T) != 0 && idx >= TOTAL) || r >= a.rows) continue;
+        const long long i = (long long)r * NX + 4 * c;
+        W[it] = *reinterpret_cast<const float4*>(stg + rr * NX + 4 * c);
+        B[it] = bp ? __ldg(reinterpret_cast<const float4*>(bp + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
+        Pv[it] = __ldg(reinterpret_cast<const float4*>(pp + i));
+    }
+    const float lam = a.reg.lambda;
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int idx = (int)threadIdx.x + it * T;
+        const int rr = idx / V, c = idx - rr * V;
+        const int r = row0 + rr;
+        if (((TOTAL % T) != 0 && idx >= TOTAL) || r >= a.rows) continue;
+        const long long i = (long long)r * NX + 4 * c;
+        float4 q;
+        q.x = fmaf(B[it].x, W[it].x, lam * Pv[it].x);
+        q.y = fmaf(B[it].y, W[it].y, lam * Pv[it].y);
+        q.z = fmaf(B[it].z, W[it].z, lam * Pv[it].z);
+        q.w = fmaf(B[it].w, W[it].w, lam * Pv[it].w);
+        *reinterpret_cast<float4*>(qp + i) = q;
+        acc->add(Pv[it].x, q.x);
+        acc->add(Pv[it].y, q.y);
+        acc->add(Pv[it].z, q.z);
+        acc->add(Pv[it].w, q.w);
+        if (acc2) {
+            acc2->add(Pv[it].x, Pv[it].x);
+            acc2->add(Pv[it].y, Pv[it].y);
+            acc2->add(Pv[it].z, Pv[it].z);
+            acc2->add(Pv[it].w, Pv[it].w);
+        }
+    }
+}
+
 // X normal: LF = schedule of length nx whose last radix is divisible by S;
 // the inverse runs the reversed schedule.
 template <class LF, int S>
@@ -301,8 +474,7 @@ __global__ void __launch_bounds__(kT) k_xnrm_ct(const XArgs a)
     __syncthreads();
     const int row0 = blockIdx.x * 2 * P;
     const RowPairLd ld{a.vin, NX, row0, a.rows};
-    DotAcc dacc;
-    const NrmEpiSt st{&a, row0, &dacc};
+    DotAcc dacc, dacc2;
     constexpr int pf = result_parity<0, NST - 1>();
     float2* fo = pf ? b1 : b0;
     float2* fx = pf ? b0 : b1;
@@ -333,17 +505,25 @@ __global__ void __launch_bounds__(kT) k_xnrm_ct(const XArgs a)
         }
         dft<R, true>(g);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if constexpr (NST > 1) fx[(j * R + r) * P + p] = g[r];
-            else st(j * R + r, p, g[r]);
-        }
+        for (int r = 0; r < R; ++r) fx[(j * R + r) * P + p] = g[r];
     }
     __syncthreads();
-    if constexpr (NST > 1) run_stages<LI, 1, NST, P, T, 1, true, true, false>(BufLd{fx, P}, st, fo, fx, P, tw);
+    // Last inverse stage into a row-major staging tile (2P rows x NX floats)
+    // in the buffer that stage does not read, then the epilogue over the tile
+    // with all of a thread's loads issued before its stores.
+    float* stg = reinterpret_cast<float*>((NST % 2 == 0) ? fo : fx);
+    run_stages<LI, 1, NST, P, T, 1, true, true, false>(BufLd{fx, P}, RowStageSt{stg, NX}, fo, fx, P, tw);
+    nrm_epilogue<NX, 2 * P, T>(a, row0, stg, &dacc, a.part2 ? &dacc2 : nullptr);
     if (a.part) {
         const double t = block_sum_f64(dacc.value(), red);
-        if (threadIdx.x == 0) a.part[blockIdx.x] = t;
+        if (a.part2) {
+            const double t2 = block_sum_f64(dacc2.value(), red);
+            grid_sum_finalize2(t, t2, a.part, a.part2, blockIdx.x, gridDim.x, a.ticket, a.sum_out, a.sum_out2, red);
+        } else {
+            grid_sum_finalize(t, a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out, red);
+        }
     }
+    if (a.count_iter) cg_count_iteration(a.cg);
     (void)MX;
 }
 

@@ -61,13 +61,14 @@ __device__ __forceinline__ float reg_term(const RegArgs& g, const float* __restr
 // CG loop control at the start of an iteration's kernels.  Returns false
 // when the loop is finished (every CTA of the kernel returns).  The first
 // kernel of an iteration also evaluates the stopping rule and the CG beta.
-__device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, float* beta, double* sh)
+__device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, float* beta, double* sh,
+                                         float* alpha = nullptr)
 {
     if (*(volatile int*)&c.flags[0]) return false;
     if (!first_kernel) return true;
     const int it = *(volatile int*)&c.flags[1];
-    const double g_new = sum_partials(c.rr_new, c.n_rr, sh);
-    const double bn = sum_partials(c.bn, c.n_rr, sh);
+    const double g_new = __ldcg(c.rr_new);
+    const double bn = __ldcg(c.bn);
     const double rel2 = (bn > 0.0) ? g_new / bn : 0.0;
     int status = -1;
     if (!isfinite(g_new) || !isfinite(bn)) status = MH3D_ERR_NONFINITE;
@@ -85,13 +86,42 @@ __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, floa
         }
         return false;
     }
-    if (it == 0) {
-        *beta = 0.f;
-    } else {
-        const double g_old = sum_partials(c.rr_old, c.n_rr, sh);
-        *beta = (float)(g_new / g_old);
+    double b = 0.0;
+    if (it > 0) b = g_new / __ldcg(c.rr_old);
+    *beta = (float)b;
+    if (c.cgcg) {
+        // alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
+        const double dl = __ldcg(c.delta);
+        const double a = (it == 0) ? g_new / dl : g_new / (dl - b * g_new / __ldcg(c.alpha_prev));
+        if (!isfinite(a) || !(a > 0.0)) {
+            if (lead) {
+                c.flags[2] = MH3D_ERR_NONFINITE;
+                __threadfence();
+                c.flags[0] = 1;
+                if (c.use_cond) cudaGraphSetConditional(c.cond, 0);
+            }
+            return false;
+        }
+        if (lead) *c.alpha_out = a;
+        if (alpha) *alpha = (float)a;
     }
     return true;
+}
+
+// End of a CG iteration whose last pass is this kernel: the lead thread
+// advances the completed-iteration counter (read only by later kernels).
+// The hard bound ends the graph loop even if the first kernel of the next
+// iteration, which normally stops it at max_iter, never ran.
+__device__ __forceinline__ void cg_count_iteration(const CgCtl& c)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
+        const int it = c.flags[1] + 1;
+        c.flags[1] = it;
+        if (it > c.max_iter + 1) {
+            c.flags[2] = MH3D_ERR_NOT_CONVERGED;
+            if (c.use_cond) cudaGraphSetConditional(c.cond, 0);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -102,6 +132,7 @@ struct TLoad {
     long long base;
     int x0;
     float beta;
+    float alpha = 0.f;
     __device__ __forceinline__ float2 operator()(int e, int p) const
     {
         const int x = x0 + 2 * p;
@@ -109,7 +140,20 @@ struct TLoad {
         const long long i = base + (long long)e * a->es + x;
         const bool has2 = x + 1 < a->nx;
         float2 v;
-        if (a->pupdate) {
+        if (a->pupdate == 2) {
+            const float2 rr = ld2(a->rvec, i, has2, a->vec2);
+            const float2 ss = ld2(a->svec, i, has2, a->vec2);
+            const float2 pp = ld2(a->pvec, i, has2, a->vec2);
+            const float2 qq = ld2(a->qdir, i, has2, a->vec2);
+            const float2 xx = ld2(a->xvec, i, has2, a->vec2);
+            const float2 pn = make_float2(fmaf(beta, pp.x, rr.x), fmaf(beta, pp.y, rr.y));
+            const float2 qn = make_float2(fmaf(beta, qq.x, ss.x), fmaf(beta, qq.y, ss.y));
+            st2(a->pvec, i, has2, a->vec2, pn);
+            st2(a->qdir, i, has2, a->vec2, qn);
+            st2(a->xvec, i, has2, a->vec2, make_float2(fmaf(alpha, pn.x, xx.x), fmaf(alpha, pn.y, xx.y)));
+            v = make_float2(fmaf(-alpha, qn.x, rr.x), fmaf(-alpha, qn.y, rr.y));
+            st2(a->rvec_w, i, has2, a->vec2, v);
+        } else if (a->pupdate) {
             const float2 rr = ld2(a->rvec, i, has2, a->vec2);
             const float2 pp = ld2(a->pvec, i, has2, a->vec2);
             v = make_float2(fmaf(beta, pp.x, rr.x), fmaf(beta, pp.y, rr.y));
@@ -138,6 +182,7 @@ struct TStore {
     long long base;
     int x0;
     DotAcc* acc;
+    DotAcc* acc2 = nullptr;   // input . input (single-reduction CG)
     __device__ __forceinline__ void operator()(int e, int p, float2 v) const
     {
         const int x = x0 + 2 * p;
@@ -156,8 +201,14 @@ struct TStore {
             v.x += reg_term(g, a->pin, i, x, y, z);
             if (has2) v.y += reg_term(g, a->pin, i + 1, x + 1, y, z);
             st2(a->qvec, i, has2, a->vec2, v);
-            acc->add(a->pin[i], v.x);
-            if (has2) acc->add(a->pin[i + 1], v.y);
+            const float p0 = a->pin[i];
+            acc->add(p0, v.x);
+            if (acc2) acc2->add(p0, p0);
+            if (has2) {
+                const float p1 = a->pin[i + 1];
+                acc->add(p1, v.y);
+                if (acc2) acc2->add(p1, p1);
+            }
         } else {
             st2(a->out, i, has2, a->vec2, v);
         }
@@ -273,6 +324,7 @@ struct NrmEpiSt {
     const XArgs* a;
     int row0;
     DotAcc* acc;
+    DotAcc* acc2 = nullptr;   // input . input (single-reduction CG)
     __device__ __forceinline__ void one(int r, int x, float w) const
     {
         const long long i = (long long)r * a->nx + x;
@@ -281,7 +333,9 @@ struct NrmEpiSt {
         const int z = r / g.ny, y = r - z * g.ny;
         q += reg_term(g, a->pin, i, x, y, z);
         a->qout[i] = q;
-        acc->add(a->pin[i], q);
+        const float pv = a->pin[i];
+        acc->add(pv, q);
+        if (acc2) acc2->add(pv, pv);
     }
     __device__ __forceinline__ void operator()(int x, int p, float2 val) const
     {

@@ -11,16 +11,31 @@ namespace mh3d {
 // (`par`, baked into each captured graph node).
 struct CgCtl {
     int* flags = nullptr;            // [0] done, [1] completed iterations, [2] status
-    const double* rr_new = nullptr;  // partials of r^T r after the previous update
-    const double* rr_old = nullptr;  // partials of r^T r one update earlier
-    int n_rr = 0;
-    const double* bn = nullptr;      // partials of ||A^T d||^2
+    const double* rr_new = nullptr;  // r^T r after the previous update (scalar)
+    const double* rr_old = nullptr;  // r^T r one update earlier (scalar)
+    const double* bn = nullptr;      // ||A^T d||^2 (scalar)
     double* hist = nullptr;          // hist[it] = ||r_it|| / ||A^T d||
     int hist_cap = 0;
     int max_iter = 0;
     double tol2 = 0.0;               // rel_tol^2 (0 = fixed iterations)
     unsigned long long cond = 0;     // cudaGraphConditionalHandle of the loop
     int use_cond = 0;
+    // single-reduction (Chronopoulos-Gear) form: delta = r^T A r of the
+    // current residual, the previous step length, and where to store the new one
+    int cgcg = 0;
+    const double* delta = nullptr;
+    const double* alpha_prev = nullptr;
+    double* alpha_out = nullptr;
+};
+
+// Destination of a grid-wide FP64 reduction: per-CTA partials, the ticket
+// counter of the last-CTA finalisation, and the scalar total.
+struct RedSink {
+    double* part = nullptr;
+    unsigned int* ticket = nullptr;
+    double* out = nullptr;
+    double* part2 = nullptr;         // optional second total (input . input)
+    double* out2 = nullptr;
 };
 
 // Regulariser applied in epilogues: out += lambda * R p.
@@ -47,14 +62,26 @@ struct TArgs {
     int nx = 1;
     int cols = 32;
     int vec2 = 1;                    // nx even: float2 global access
+    int vec4 = 0;                    // nx % 4 == 0 and every vector 16-byte aligned: float4 access
     // CG fusions
-    int pupdate = 0;                 // loader: p = r + beta p (written back), value = b p
+    int pupdate = 0;                 // loader: 1 = p = r + beta p (written back), value = b p;
+                                     //         2 = p = r + beta p, q = s + beta q, x += alpha p,
+                                     //             r -= alpha q (all written back), value = b r
     float* pvec = nullptr;
     const float* rvec = nullptr;
+    float* rvec_w = nullptr;         // r written back (mode 2)
+    float* qdir = nullptr;           // q = A p recurrence (mode 2)
+    const float* svec = nullptr;     // s = A r (mode 2)
+    float* xvec = nullptr;           // iterate (mode 2)
     int epilogue = 0;                // storer: q = b w + lambda R p, partial p^T q
     float* qvec = nullptr;
     const float* pin = nullptr;      // p for the epilogue
-    double* part = nullptr;          // per-CTA partials
+    double* part = nullptr;          // per-CTA partials of p^T q (null: none)
+    unsigned int* ticket = nullptr;  // grid reduction counter
+    double* sum_out = nullptr;       // p^T q total
+    double* part2 = nullptr;         // optional second total p^T p (same ticket)
+    double* sum_out2 = nullptr;
+    int count_iter = 0;              // last pass of a CG iteration: advance the counter
     RegArgs reg{};
     CgCtl cg{};
 };
@@ -76,11 +103,17 @@ struct XArgs {
     long long M = 1;                 // rows * mx
     int pairs = 16;                  // row pairs per CTA
     int kg = 4;                      // harmonics per transform batch
+    int vec4 = 0;                    // nx % 4 == 0 and every vector 16-byte aligned
     // normal-mode epilogue
     const float* b = nullptr;
     const float* pin = nullptr;
     float* qout = nullptr;
-    double* part = nullptr;
+    double* part = nullptr;          // per-CTA partials of p^T q (null: none)
+    unsigned int* ticket = nullptr;
+    double* sum_out = nullptr;
+    double* part2 = nullptr;         // optional second total p^T p (same ticket)
+    double* sum_out2 = nullptr;
+    int count_iter = 0;              // last pass of a CG iteration: advance the counter
     RegArgs reg{};
     CgCtl cg{};
     int cg_active = 0;

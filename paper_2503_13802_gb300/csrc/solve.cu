@@ -27,18 +27,31 @@ int update_blocks(long long N)
     return (int)std::max(1LL, std::min(b, 4LL * 152));
 }
 
-// Reduction buffer layout (doubles): [RR0 | RR1 | PQ | BN | RES], each red_cap.
-enum { kRR0 = 0, kRR1 = 1, kPQ = 2, kBN = 3, kRES = 4, kNRed = 5 };
-static double* red_slot(const Plan& P, int s) { return P.w.red + (size_t)s * P.w.red_cap; }
+// Reduction memory (doubles): per-CTA partial arrays [RR | PQ | BN | RES],
+// each red_cap long, then the scalars [RR0, RR1, PQ, BN, RES] written by the
+// last CTA of each producer, then four ticket counters (unsigned int).
+enum { kPartRR = 0, kPartPQ = 1, kPartBN = 2, kPartRES = 3, kNPart = 4 };
+enum { kRR0 = 0, kRR1 = 1, kPQ = 2, kBN = 3, kRES = 4, kDL0 = 5, kDL1 = 6, kAL0 = 7, kAL1 = 8, kNScal = 9 };
+enum { kTkRR = 0, kTkPQ = 1, kTkBN = 2, kTkRES = 3, kNTk = 4 };
+static double* part_slot(const Plan& P, int s) { return P.w.red + (size_t)s * P.w.red_cap; }
+static double* scal(const Plan& P, int s) { return P.w.red + (size_t)kNPart * P.w.red_cap + s; }
+static unsigned int* ticket(const Plan& P, int s)
+{
+    return reinterpret_cast<unsigned int*>(P.w.red + (size_t)kNPart * P.w.red_cap + 16) + s;
+}
+static size_t red_bytes(size_t cap) { return sizeof(double) * (cap * kNPart + 16) + sizeof(unsigned int) * 8; }
 
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-// r = rhs - q (q may be null: zero start), p = r, x = 0 on a zero start;
-// partials of r^T r and rhs^T rhs.
+// r = rhs - q (q may be null: zero start), x = 0 on a zero start; the
+// search direction starts as p = r (classic CG) or p = qd = 0 (single-
+// reduction CG, whose first update forms p = r); totals r^T r, rhs^T rhs.
 __global__ void __launch_bounds__(256) k_cg_init(const float* __restrict__ rhs, const float* __restrict__ q,
-                                                 float* __restrict__ r, float* __restrict__ p, float* __restrict__ x,
-                                                 int zero_x, long long N, double* rr_part, double* bn_part)
+                                                 float* __restrict__ r, float* __restrict__ p, float* __restrict__ qd,
+                                                 float* __restrict__ x, int zero_x, long long N, double* rr_part,
+                                                 unsigned int* rr_tk, double* rr_out, double* bn_part,
+                                                 unsigned int* bn_tk, double* bn_out)
 {
     __shared__ double red[34];
     DotAcc ar, ab;
@@ -46,28 +59,33 @@ __global__ void __launch_bounds__(256) k_cg_init(const float* __restrict__ rhs, 
         const float b = rhs[i];
         const float rv = q ? b - q[i] : b;
         r[i] = rv;
-        p[i] = rv;
+        if (qd) {
+            p[i] = 0.f;
+            qd[i] = 0.f;
+        } else {
+            p[i] = rv;
+        }
         if (zero_x) x[i] = 0.f;
         ar.add(rv, rv);
         ab.add(b, b);
     }
     double t = block_sum_f64(ar.value(), red);
-    if (threadIdx.x == 0) rr_part[blockIdx.x] = t;
+    grid_sum_finalize(t, rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out, red);
     t = block_sum_f64(ab.value(), red);
-    if (threadIdx.x == 0) bn_part[blockIdx.x] = t;
+    grid_sum_finalize(t, bn_part, blockIdx.x, gridDim.x, bn_tk, bn_out, red);
 }
 
 // alpha = gamma / delta; x += alpha p; r -= alpha q; partials of r^T r.
 __global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float* __restrict__ r,
                                                    const float* __restrict__ p, const float* __restrict__ q,
-                                                   long long N, const CgCtl c, const double* pq, int n_pq,
-                                                   double* rr_out)
+                                                   long long N, const CgCtl c, const double* pq, double* rr_part,
+                                                   unsigned int* rr_tk, double* rr_out)
 {
     __shared__ double red[34];
     if (*(volatile int*)&c.flags[0]) return;
     const bool lead = threadIdx.x == 0 && blockIdx.x == 0;
-    const double g = sum_partials(c.rr_new, c.n_rr, red);
-    const double dl = sum_partials(pq, n_pq, red);
+    const double g = __ldcg(c.rr_new);
+    const double dl = __ldcg(pq);
     const double al = g / dl;
     if (!isfinite(al) || !(dl > 0.0)) {
         if (lead) {
@@ -80,23 +98,40 @@ __global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float*
     }
     const float a = (float)al;
     DotAcc acc;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    // float4 body (vector buffers are 256-byte aligned), scalar tail
+    const long long N4 = N >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N4; i += stride) {
+        const float4 pv = reinterpret_cast<const float4*>(p)[i];
+        const float4 qv = reinterpret_cast<const float4*>(q)[i];
+        float4 xv = reinterpret_cast<float4*>(x)[i];
+        float4 rv = reinterpret_cast<float4*>(r)[i];
+        xv.x = fmaf(a, pv.x, xv.x); xv.y = fmaf(a, pv.y, xv.y); xv.z = fmaf(a, pv.z, xv.z); xv.w = fmaf(a, pv.w, xv.w);
+        rv.x = fmaf(-a, qv.x, rv.x); rv.y = fmaf(-a, qv.y, rv.y); rv.z = fmaf(-a, qv.z, rv.z); rv.w = fmaf(-a, qv.w, rv.w);
+        reinterpret_cast<float4*>(x)[i] = xv;
+        reinterpret_cast<float4*>(r)[i] = rv;
+        acc.add(rv.x, rv.x);
+        acc.add(rv.y, rv.y);
+        acc.add(rv.z, rv.z);
+        acc.add(rv.w, rv.w);
+    }
+    for (long long i = 4 * N4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         x[i] = fmaf(a, p[i], x[i]);
         const float rv = fmaf(-a, q[i], r[i]);
         r[i] = rv;
         acc.add(rv, rv);
     }
     const double t = block_sum_f64(acc.value(), red);
-    if (threadIdx.x == 0) rr_out[blockIdx.x] = t;
+    grid_sum_finalize(t, rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out, red);
     if (lead) {
         const int it = c.flags[1] + 1;
         c.flags[1] = it;
         // Hard bound: the first kernel of the next iteration stops the loop at
-        // max_iter; this guard ends it even if that kernel never ran.
+        // max_iter; this guard ends the graph loop even if that kernel never
+        // ran.  It does not set the done flag (other CTAs of this kernel may
+        // not have started yet); the host reports the missing decision.
         if (it > c.max_iter + 1) {
             c.flags[2] = MH3D_ERR_NOT_CONVERGED;
-            __threadfence();
-            c.flags[0] = 1;
             if (c.use_cond) cudaGraphSetConditional(c.cond, 0);
         }
     }
@@ -104,7 +139,7 @@ __global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float*
 
 // Partials of ||a - b||^2.
 __global__ void __launch_bounds__(256) k_diff_norm2(const float* __restrict__ a, const float* __restrict__ b,
-                                                    long long N, double* part)
+                                                    long long N, double* part, unsigned int* tk, double* out)
 {
     __shared__ double red[34];
     DotAcc acc;
@@ -113,7 +148,7 @@ __global__ void __launch_bounds__(256) k_diff_norm2(const float* __restrict__ a,
         acc.add(d, d);
     }
     const double t = block_sum_f64(acc.value(), red);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    grid_sum_finalize(t, part, blockIdx.x, gridDim.x, tk, out, red);
 }
 
 // APG step (Sec. 4.3): given y and g = N y - rhs,
@@ -150,7 +185,7 @@ mh3d_status solve_alloc(Plan& P)
     const size_t vec = (N + 63) & ~size_t(63);
     const size_t cap = (size_t)std::max({update_blocks(P.N), normal_part_count(P, 0), normal_part_count(P, 1), 1});
     w.red_cap = cap;
-    const size_t bytes = sizeof(float) * vec * 7 + sizeof(double) * cap * kNRed + 64;
+    const size_t bytes = sizeof(float) * vec * 8 + red_bytes(cap) + 64;
     if (cudaMalloc(&w.base, bytes) != cudaSuccess) {
         w.base = nullptr;
         P.err = "cudaMalloc of solver workspace failed";
@@ -164,10 +199,12 @@ mh3d_status solve_alloc(Plan& P)
     w.t1 = f + 4 * vec;
     w.t2 = f + 5 * vec;
     w.rhs = f + 6 * vec;
-    w.red = (double*)(f + 7 * vec);
+    w.s = f + 7 * vec;
+    w.red = (double*)(f + 8 * vec);
+    if (cudaMemset(w.red, 0, red_bytes(cap)) != cudaSuccess) return MH3D_ERR_CUDA;
     if (cudaMalloc(&w.flags, 4 * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
     if (cudaMallocHost(&w.flags_host, 4 * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
-    if (cudaMallocHost(&w.red_host, cap * sizeof(double)) != cudaSuccess) return MH3D_ERR_OOM;
+    if (cudaMallocHost(&w.red_host, std::max(cap, (size_t)16) * sizeof(double)) != cudaSuccess) return MH3D_ERR_OOM;
     P.work_bytes = bytes + 4 * sizeof(int);
     return MH3D_OK;
 }
@@ -211,7 +248,7 @@ mh3d_status validate_opts(Plan& P, const mh3d_solve_opts& o)
 {
     if (o.reg_kind < 0 || o.reg_kind > 1 || !(o.lambda > 0) || !(o.alpha >= 0) || o.shell < 1 || o.solver < 0 ||
         o.solver > 1 || o.max_iter < 1 || o.max_iter > 1000000 || o.normal_mode < 0 || o.normal_mode > 1 ||
-        !(o.rel_tol >= 0)) {
+        !(o.rel_tol >= 0) || o.cg_variant < 0 || o.cg_variant > 1) {
         P.err = "invalid solve options";
         return MH3D_ERR_INVALID_ARG;
     }
@@ -225,8 +262,7 @@ static CgCtl base_ctl(const Plan& P, const mh3d_solve_opts& o)
 {
     CgCtl c;
     c.flags = P.w.flags;
-    c.n_rr = update_blocks(P.N);
-    c.bn = red_slot(P, kBN);
+    c.bn = scal(P, kBN);
     c.hist = P.w.hist;
     c.hist_cap = P.w.hist_cap;
     c.max_iter = o.max_iter;
@@ -236,16 +272,47 @@ static CgCtl base_ctl(const Plan& P, const mh3d_solve_opts& o)
 
 static cudaError_t enqueue_iteration(Plan& P, const mh3d_solve_opts& o, int par, CgCtl c, cudaStream_t st)
 {
-    c.rr_new = red_slot(P, par ? kRR0 : kRR1);
-    c.rr_old = red_slot(P, par ? kRR1 : kRR0);
+    c.rr_new = scal(P, par ? kRR0 : kRR1);
+    c.rr_old = scal(P, par ? kRR1 : kRR0);
     const int mode = o.normal_mode;
     SolveWork& w = P.w;
-    cudaError_t e = launch_normal(P, mode, reg_args(P, o), w.p, w.q, w.t1, w.t2, w.portrait, red_slot(P, kPQ), &c,
-                                  w.p, w.r, st);
+    if (o.cg_variant == 0) {
+        // single-reduction CG: the first pass updates p, q, x, r and applies
+        // the operator to the new r; the last pass produces s = A r with
+        // delta = r^T s and gamma = r^T r (one grid reduction per iteration)
+        c.cgcg = 1;
+        c.delta = scal(P, par ? kDL0 : kDL1);
+        c.alpha_prev = scal(P, par ? kAL0 : kAL1);
+        c.alpha_out = scal(P, par ? kAL1 : kAL0);
+        LoaderUpdate u;
+        u.mode = 2;
+        u.p = w.p;
+        u.r = w.r;
+        u.r_w = w.r;
+        u.q = w.q;
+        u.s = w.s;
+        u.x = w.x;
+        RedSink dots;
+        dots.part = part_slot(P, kPartPQ);
+        dots.ticket = ticket(P, kTkPQ);
+        dots.out = scal(P, par ? kDL1 : kDL0);
+        dots.part2 = part_slot(P, kPartRR);
+        dots.out2 = scal(P, par ? kRR1 : kRR0);
+        return launch_normal(P, mode, reg_args(P, o), w.r, w.s, w.t1, w.t2, w.portrait, &dots, &c, &u, st);
+    }
+    RedSink pq;
+    pq.part = part_slot(P, kPartPQ);
+    pq.ticket = ticket(P, kTkPQ);
+    pq.out = scal(P, kPQ);
+    LoaderUpdate u;
+    u.mode = 1;
+    u.p = w.p;
+    u.r = w.r;
+    cudaError_t e = launch_normal(P, mode, reg_args(P, o), w.p, w.q, w.t1, w.t2, w.portrait, &pq, &c, &u, st);
     if (e != cudaSuccess) return e;
     const int nU = update_blocks(P.N);
-    k_cg_update<<<nU, 256, 0, st>>>(w.x, w.r, w.p, w.q, P.N, c, red_slot(P, kPQ), normal_part_count(P, mode),
-                                    red_slot(P, par ? kRR1 : kRR0));
+    k_cg_update<<<nU, 256, 0, st>>>(w.x, w.r, w.p, w.q, P.N, c, scal(P, kPQ), part_slot(P, kPartRR),
+                                    ticket(P, kTkRR), scal(P, par ? kRR1 : kRR0));
     return cudaGetLastError();
 }
 
@@ -264,6 +331,8 @@ static unsigned long long opts_key(const mh3d_solve_opts& o)
     mix(&o.max_iter, sizeof o.max_iter);
     mix(&o.fixed_iters, sizeof o.fixed_iters);
     mix(&o.normal_mode, sizeof o.normal_mode);
+    mix(&o.cg_variant, sizeof o.cg_variant);
+    mix(&o.lambda_relative, sizeof o.lambda_relative);
     return h;
 }
 
@@ -355,12 +424,6 @@ static mh3d_status run_cg_loop(Plan& P, const mh3d_solve_opts& o, cudaStream_t s
     return MH3D_OK;
 }
 
-static double sum_host_partials(const double* h, int n)
-{
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += h[i];
-    return s;
-}
 
 // ||rhs - N x||^2 and ||rhs||^2 on the host from device partials.
 static mh3d_status true_residual(Plan& P, const mh3d_solve_opts& o, cudaStream_t st, double* res2, double* bn2)
@@ -368,15 +431,13 @@ static mh3d_status true_residual(Plan& P, const mh3d_solve_opts& o, cudaStream_t
     SolveWork& w = P.w;
     const int nU = update_blocks(P.N);
     MH3D_CK(P, launch_normal(P, o.normal_mode, reg_args(P, o), w.x, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr,
-                             nullptr, nullptr, st));
-    k_diff_norm2<<<nU, 256, 0, st>>>(w.rhs, w.q, P.N, red_slot(P, kRES));
+                             nullptr, st));
+    k_diff_norm2<<<nU, 256, 0, st>>>(w.rhs, w.q, P.N, part_slot(P, kPartRES), ticket(P, kTkRES), scal(P, kRES));
     MH3D_CK(P, cudaGetLastError());
-    MH3D_CK(P, cudaMemcpyAsync(w.red_host, red_slot(P, kRES), nU * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, 0), kNScal * sizeof(double), cudaMemcpyDeviceToHost, st));
     MH3D_CK(P, cudaStreamSynchronize(st));
-    *res2 = sum_host_partials(w.red_host, nU);
-    MH3D_CK(P, cudaMemcpyAsync(w.red_host, red_slot(P, kBN), nU * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MH3D_CK(P, cudaStreamSynchronize(st));
-    *bn2 = sum_host_partials(w.red_host, nU);
+    *res2 = w.red_host[kRES];
+    *bn2 = w.red_host[kBN];
     return MH3D_OK;
 }
 
@@ -394,13 +455,26 @@ static mh3d_status cg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, 
     if (o.x0_dev) {
         MH3D_CK(P, cudaMemcpyAsync(w.x, o.x0_dev, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
         MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.x, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr,
-                                 nullptr, st));
+                                 st));
         qinit = w.q;
     }
     MH3D_CK(P, cudaMemsetAsync(w.flags, 0, 4 * sizeof(int), st));
-    k_cg_init<<<nU, 256, 0, st>>>(w.rhs, qinit, w.r, w.p, w.x, o.x0_dev ? 0 : 1, P.N, red_slot(P, kRR1),
-                                  red_slot(P, kBN));
+    MH3D_CK(P, cudaMemsetAsync(ticket(P, 0), 0, kNTk * sizeof(unsigned int), st));
+    const bool cgcg = (o.cg_variant == 0);
+    k_cg_init<<<nU, 256, 0, st>>>(w.rhs, qinit, w.r, w.p, cgcg ? w.q : nullptr, w.x, o.x0_dev ? 0 : 1, P.N,
+                                  part_slot(P, kPartRR), ticket(P, kTkRR), scal(P, kRR1), part_slot(P, kPartBN),
+                                  ticket(P, kTkBN), scal(P, kBN));
     MH3D_CK(P, cudaGetLastError());
+    if (cgcg) {   // s0 = A r0 with delta0 = r0^T s0 and gamma0 = r0^T r0 (parity-1 slots)
+        RedSink dots;
+        dots.part = part_slot(P, kPartPQ);
+        dots.ticket = ticket(P, kTkPQ);
+        dots.out = scal(P, kDL1);
+        dots.part2 = part_slot(P, kPartRR);
+        dots.out2 = scal(P, kRR1);
+        MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.r, w.s, w.t1, w.t2, w.portrait, &dots, nullptr, nullptr,
+                                 st));
+    }
     if ((s = run_cg_loop(P, o, st)) != MH3D_OK) return s;
     MH3D_CK(P, cudaMemcpyAsync(w.flags_host, w.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     double res2 = 0, bn2 = 0;
@@ -447,19 +521,22 @@ static mh3d_status apg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o,
         // ||N||_2 by power iteration from the back-projection (30 steps), tau = 0.95 / ||N||.
         MH3D_CK(P, cudaMemcpyAsync(w.p, w.rhs, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
         double lam = 0;
+        MH3D_CK(P, cudaMemsetAsync(ticket(P, 0), 0, kNTk * sizeof(unsigned int), st));
         for (int i = 0; i < 30; ++i) {
-            k_diff_norm2<<<nU, 256, 0, st>>>(w.p, nullptr, P.N, red_slot(P, kRES));
-            MH3D_CK(P, cudaMemcpyAsync(w.red_host, red_slot(P, kRES), nU * sizeof(double), cudaMemcpyDeviceToHost, st));
+            k_diff_norm2<<<nU, 256, 0, st>>>(w.p, nullptr, P.N, part_slot(P, kPartRES), ticket(P, kTkRES),
+                                             scal(P, kRES));
+            MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, kRES), sizeof(double), cudaMemcpyDeviceToHost, st));
             MH3D_CK(P, cudaStreamSynchronize(st));
-            const double nrm = std::sqrt(sum_host_partials(w.red_host, nU));
+            const double nrm = std::sqrt(w.red_host[0]);
             if (!(nrm > 0)) break;
             k_scale<<<nU, 256, 0, st>>>(w.p, w.p, (float)(1.0 / nrm), P.N);
             MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.p, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr,
-                                     nullptr, nullptr, st));
-            k_diff_norm2<<<nU, 256, 0, st>>>(w.q, nullptr, P.N, red_slot(P, kRES));
-            MH3D_CK(P, cudaMemcpyAsync(w.red_host, red_slot(P, kRES), nU * sizeof(double), cudaMemcpyDeviceToHost, st));
+                                     nullptr, st));
+            k_diff_norm2<<<nU, 256, 0, st>>>(w.q, nullptr, P.N, part_slot(P, kPartRES), ticket(P, kTkRES),
+                                             scal(P, kRES));
+            MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, kRES), sizeof(double), cudaMemcpyDeviceToHost, st));
             MH3D_CK(P, cudaStreamSynchronize(st));
-            lam = std::sqrt(sum_host_partials(w.red_host, nU));
+            lam = std::sqrt(w.red_host[0]);
             MH3D_CK(P, cudaMemcpyAsync(w.p, w.q, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
         }
         if (!(lam > 0)) {
@@ -475,12 +552,15 @@ static mh3d_status apg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o,
     MH3D_CK(P, cudaMemcpyAsync(w.p, w.x, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));   // y
     for (int k = 1; k <= o.max_iter; ++k) {
         MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.p, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr,
-                                 nullptr, st));
+                                 st));
         const float mom_next = (float)k / (float)(k + 3);   // (k' - 1)/(k' + 2) with k' = k + 1
         k_apg_step<<<nU, 256, 0, st>>>(w.x, w.r, w.p, w.q, w.rhs, (float)tau, mom_next, P.N);
         MH3D_CK(P, cudaGetLastError());
     }
     double res2 = 0, bn2 = 0;
+    // ||A^T d||^2 for the relative true residual
+    k_diff_norm2<<<nU, 256, 0, st>>>(w.rhs, nullptr, P.N, part_slot(P, kPartBN), ticket(P, kTkBN), scal(P, kBN));
+    MH3D_CK(P, cudaGetLastError());
     if ((s = true_residual(P, o, st, &res2, &bn2)) != MH3D_OK) return s;
     MH3D_CK(P, cudaMemcpyAsync(rho, w.x, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
     MH3D_CK(P, cudaStreamSynchronize(st));

@@ -9,9 +9,19 @@ TArgs tpass_args(const Plan& P, int axis, const float* in, float* out, const flo
 int tpass_outer(const Plan& P, int axis);
 XArgs xpass_args(const Plan& P);
 RegArgs reg_args(const Plan& P, const mh3d_solve_opts& o);
-cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const float* p, float* q, float* t1,
-                          float* t2, float2* portrait, double* part, const CgCtl* cg, float* pupd_p,
-                          const float* pupd_r, cudaStream_t st);
+// CG vector update fused into the first pass of the normal operator.
+struct LoaderUpdate {
+    int mode = 0;                 // 1: p = r + beta p; 2: single-reduction CG update (see TArgs)
+    float* p = nullptr;
+    const float* r = nullptr;
+    float* r_w = nullptr;
+    float* q = nullptr;
+    const float* s = nullptr;
+    float* x = nullptr;
+};
+cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const float* in, float* out, float* t1,
+                          float* t2, float2* portrait, const RedSink* dots, const CgCtl* cg, const LoaderUpdate* upd,
+                          cudaStream_t st);
 int normal_part_count(const Plan& P, int mode);
 mh3d_status ensure_portrait(Plan& P);
 

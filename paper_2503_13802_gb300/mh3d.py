@@ -38,7 +38,7 @@ class mh3d_solve_opts(ctypes.Structure):
     _fields_ = [("reg_kind", c_int), ("lambda_", c_double), ("alpha", c_double), ("shell", c_int),
                 ("solver", c_int), ("rel_tol", c_double), ("max_iter", c_int), ("fixed_iters", c_int),
                 ("x0_dev", c_void_p), ("normal_mode", c_int), ("apg_tau", c_double),
-                ("lambda_relative", c_int)]
+                ("lambda_relative", c_int), ("cg_variant", c_int)]
 
 
 class mh3d_solve_info(ctypes.Structure):
@@ -204,7 +204,8 @@ def mh3d_adjoint(plan: Plan, d, rho, stream=None):
 
 def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: int = 2, solver: int = 0,
               rel_tol: float = 1e-4, max_iter: int = 1000, fixed_iters: bool = False, x0=None,
-              normal_mode: int = 0, apg_tau: float = 0.0, lam_relative: bool = False) -> mh3d_solve_opts:
+              normal_mode: int = 0, apg_tau: float = 0.0, lam_relative: bool = False,
+              cg_variant: int = 0) -> mh3d_solve_opts:
     """lam_relative: lam multiplies ||A||_2^2 (b = 1), see mh3d_operator_norm2."""
     o = mh3d_solve_opts()
     o.reg_kind, o.lambda_, o.alpha, o.shell, o.solver = reg_kind, lam, alpha, shell, solver
@@ -212,6 +213,7 @@ def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: i
     o.x0_dev = x0.data_ptr() if x0 is not None else None
     o.normal_mode, o.apg_tau = normal_mode, apg_tau
     o.lambda_relative = int(bool(lam_relative))
+    o.cg_variant = int(cg_variant)
     o._x0_ref = x0
     return o
 

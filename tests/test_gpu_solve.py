@@ -28,8 +28,9 @@ def _data(p, g, b, seed, snr_db):
     return rho, clean + np.sqrt(sig2) * W.unit_complex_noise(clean.shape, seed)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_plain_fp64_32cube_fixed_100_iterations(mode):
+def test_plain_fp64_32cube_fixed_100_iterations(mode, variant):
     """32^3, k = 2..5, uniform sensitivity, s = 1, 5 blobs, 30 dB, Tikhonov
     lambda = 1e-3 (relative to ||A||^2), exactly 100 CG iterations on both
     sides: the FP32 GPU iterate is within 1e-4 of the FP64 oracle iterate."""
@@ -44,7 +45,8 @@ def test_plain_fp64_32cube_fixed_100_iterations(mode):
     assert mh3d_operator_norm2(plan) == pytest.approx(oracle.operator_norm2(g), rel=1e-8)
     x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
     info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-3, lam_relative=True, max_iter=100,
-                                                               fixed_iters=True, normal_mode=mode), x)
+                                                               fixed_iters=True, normal_mode=mode,
+                                                               cg_variant=variant), x)
     assert info["iters"] == 100 and info["status"] == 0
     assert rel_l2(x.cpu().numpy(), xo) <= 1e-4, rel_l2(x.cpu().numpy(), xo)
     # residual histories agree while the residual is well above FP32
@@ -52,9 +54,10 @@ def test_plain_fp64_32cube_fixed_100_iterations(mode):
     np.testing.assert_allclose(info["history"][:15], hist[:15], rtol=1e-3)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("reg_kind", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_solve_to_tolerance_matches_oracle(reg_kind, mode):
+def test_solve_to_tolerance_matches_oracle(reg_kind, mode, variant):
     """Downsampled, Gaussian sensitivity, phases, relative lambda 1e-3.
     (a) At a common relative residual of 1e-6 the GPU and oracle
     reconstructions agree within 1e-4 and both sit within 1e-4 of a tightly
@@ -76,7 +79,7 @@ def test_solve_to_tolerance_matches_oracle(reg_kind, mode):
     # (a)
     xo6, it6, _ = oracle.cg(g, d, b, mk(1e-6))
     info = mh3d_solve(plan, dd, make_opts(lam=1e-3, lam_relative=True, reg_kind=reg_kind, alpha=4.0, shell=2,
-                                          rel_tol=1e-6, max_iter=20000, normal_mode=mode), x)
+                                          rel_tol=1e-6, max_iter=20000, normal_mode=mode, cg_variant=variant), x)
     assert info["status"] == 0, info
     xg = x.cpu().numpy()
     assert rel_l2(xg, xo6) <= 1e-4, rel_l2(xg, xo6)
@@ -85,7 +88,7 @@ def test_solve_to_tolerance_matches_oracle(reg_kind, mode):
     # (b)
     xo4, it4, _ = oracle.cg(g, d, b, mk(1e-4))
     info = mh3d_solve(plan, dd, make_opts(lam=1e-3, lam_relative=True, reg_kind=reg_kind, alpha=4.0, shell=2,
-                                          rel_tol=1e-4, max_iter=20000, normal_mode=mode), x)
+                                          rel_tol=1e-4, max_iter=20000, normal_mode=mode, cg_variant=variant), x)
     assert info["status"] == 0 and info["rel_res_true"] <= 1.2e-4, info
     xg = x.cpu().numpy()
     assert rel_l2(xg, tight) <= 2.0 * rel_l2(xo4, tight) + 1e-4, (rel_l2(xg, tight), rel_l2(xo4, tight))
@@ -137,7 +140,8 @@ def test_warm_start_from_solution_converges_immediately():
     assert info["status"] == 0 and info["iters"] <= 1, info
 
 
-def test_not_converged_status_keeps_iterate():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_not_converged_status_keeps_iterate(variant):
     p = params((32, 16, 8), kmin=2, kmax=5)
     g = oracle_geom(p)
     d = W.random_portraits(g.portrait_shape, 4)
@@ -145,7 +149,8 @@ def test_not_converged_status_keeps_iterate():
 
     plan = gpu_plan(p, None)
     x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
-    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-6, rel_tol=1e-12, max_iter=5), x)
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-6, rel_tol=1e-12, max_iter=5,
+                                                               cg_variant=variant), x)
     assert info["status"] == 6 and info["iters"] == 5
     xo, _, _ = oracle.cg(g, d, None, oracle.SolveOpts(lam=1e-6, rel_tol=0.0, max_iter=5))
     assert rel_l2(x.cpu().numpy(), xo) <= 1e-4
