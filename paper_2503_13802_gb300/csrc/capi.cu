@@ -44,7 +44,7 @@ static void choose_tiles(Plan& P)
 {
     TileChoice t;
     const int nt = std::max(P.ny, P.nz);
-    t.tpass_cols = 32;
+    t.tpass_cols = 16;
     while (t.tpass_cols > 4 && tpass_smem_bytes(nt, t.tpass_cols) > kSmemBudget) t.tpass_cols /= 2;
     t.xpass_pairs = 16;
     t.xpass_kgroup = std::min(4, P.K);
@@ -169,6 +169,8 @@ TArgs tpass_args(const Plan& P, int axis /*1 = y, 2 = z*/, const float* in, floa
     a.cols = P.tile.tpass_cols;
     a.vec2 = (P.nx % 2 == 0) ? 1 : 0;
     a.vec4 = (P.nx % 4 == 0 && ((uintptr_t)P.sens % 16) == 0) ? 1 : 0;
+    a.status = P.w.flags ? P.w.flags + 3 : nullptr;
+    a.axis = axis;
     if (axis == 1) {
         a.rp = P.ay.rp;
         a.tw = P.ay.tw;

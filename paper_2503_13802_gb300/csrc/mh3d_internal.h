@@ -33,7 +33,7 @@ struct AxisPlan {
 
 // Launch shape of the pencil kernels, chosen per plan (autotuner).
 struct TileChoice {
-    int tpass_cols = 32;          // x columns per T-pass CTA (pencils = cols / 2)
+    int tpass_cols = 16;          // x columns per T-pass CTA (pencils = cols / 2)
     int xpass_pairs = 16;         // row pairs per X-pass CTA
     int xpass_kgroup = 4;         // harmonics transformed together in the X pass
     int threads = 256;

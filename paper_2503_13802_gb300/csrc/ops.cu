@@ -73,7 +73,7 @@ int tpass_blocks(int nx, int cols, int nouter) { return ((nx + cols - 1) / cols)
 
 cudaError_t run_tpass(const TArgs& a, int nouter, cudaStream_t st)
 {
-    if (ct_tpass_available(a.n, a.cols)) return run_tpass_ct(a, nouter, st);
+    if (ct_tpass_available(a)) return run_tpass_ct(a, nouter, st);
     dim3 grid((a.nx + a.cols - 1) / a.cols, nouter);
     const size_t smem = tpass_smem_bytes(a.n, a.cols);
     k_tpass<<<grid, 256, smem, st>>>(a);

@@ -6,7 +6,11 @@
 // transform's last radix feeds the inverse's first one (see fft_ct.cuh).
 // Every other size runs the runtime-general kernels of ops.cu; setting
 // MH3D_GENERIC=1 forces those for every size (A/B checks).
+#include <cstdint>
 #include <cstdlib>
+#include <mutex>
+
+#include <cudaTypedefs.h>
 
 #include "ops_ct.cuh"
 
@@ -34,7 +38,7 @@ struct XDesc {
 template <class L>
 TDesc tdesc()
 {
-    return TDesc{k_tpass_ct<L>, tpass_ct_smem<L>()};
+    return TDesc{k_tpass_ct<L, kPT>, tpass_ct_smem<L, kPT>()};
 }
 
 TDesc tpass_desc(int n)
@@ -94,7 +98,56 @@ cudaError_t opt_in(F* f, size_t need, int optin)
 
 }  // namespace
 
-bool ct_tpass_available(int n, int cols) { return !force_generic() && cols == 2 * kP && tpass_desc(n).fn; }
+static bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime
+// (no link-time dependency on libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Map of a float32 volume [nz][ny][nx] whose box is one T-pass tile:
+// (box_x, n, 1) along y or (box_x, 1, n) along z.
+static bool encode_tile_map(CUtensorMap* m, const void* base, int nx, int ny, int nz, int axis, int n, int box_x)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, axis == 1 ? (cuuint32_t)n : 1u, axis == 1 ? 1u : (cuuint32_t)n};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// The bulk-copy T pass needs whole 16-float tiles and 16-byte aligned rows.
+bool ct_tpass_available(const TArgs& a)
+{
+    if (force_generic() || a.cols != 2 * kPT || !tpass_desc(a.n).fn) return false;
+    if (a.nx % (2 * kPT) != 0 || (a.es % 4) != 0 || (a.os % 4) != 0) return false;
+    const void* ptrs[] = {a.in, a.out, a.bin, a.bout, a.pvec, a.rvec, a.rvec_w, a.qdir, a.svec, a.xvec, a.qvec, a.pin};
+    for (const void* p : ptrs)
+        if (p && !al16(p)) return false;
+    if (a.epilogue && a.reg.kind != 0) return false;
+    if (a.pupdate == 2 && a.rvec_w != a.rvec) return false;   // r is updated in place
+    if (a.n > 256 || !tensor_map_encoder()) return false;     // TMA box limit
+    return true;
+}
 bool ct_xpass_available(int nx, int s, int pairs) { return !force_generic() && pairs == kP && xpass_desc(nx, s, 0).fn; }
 
 cudaError_t ct_set_attributes(int optin)
@@ -115,10 +168,19 @@ cudaError_t ct_set_attributes(int optin)
     return cudaSuccess;
 }
 
-cudaError_t run_tpass_ct(const TArgs& a, int nouter, cudaStream_t st)
+cudaError_t run_tpass_ct(const TArgs& a0, int nouter, cudaStream_t st)
 {
+    TArgs a = a0;
+    const int ny = (a.axis == 1) ? a.n : nouter, nz = (a.axis == 1) ? nouter : a.n;
+    auto enc = [&](int slot, const void* ptr) {
+        return !ptr || encode_tile_map(&a.tm.m[slot], ptr, a.nx, ny, nz, a.axis, a.n, 2 * kPT);
+    };
+    const bool ok = enc(kTmIn, a.in) && enc(kTmB, a.bin ? a.bin : a.bout) && enc(kTmR, a.rvec) &&
+                    enc(kTmS, a.svec) && enc(kTmP, a.pvec) && enc(kTmQ, a.qdir) && enc(kTmX, a.xvec) &&
+                    enc(kTmOut, a.epilogue ? a.qvec : a.out) && enc(kTmPin, a.pin);
+    if (!ok) return cudaErrorInvalidValue;
     const TDesc d = tpass_desc(a.n);
-    dim3 grid((a.nx + 2 * kP - 1) / (2 * kP), nouter);
+    dim3 grid((a.nx + 2 * kPT - 1) / (2 * kPT), nouter);
     d.fn<<<grid, kT, d.smem, st>>>(a);
     return cudaGetLastError();
 }

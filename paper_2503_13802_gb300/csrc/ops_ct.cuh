@@ -17,13 +17,15 @@
 //              and the inverse's first stage, in registers.
 #pragma once
 
+#include "bulk.cuh"
 #include "fft_ct.cuh"
 #include "ops_functors.cuh"
 
 namespace mh3d {
 namespace ct {
 
-constexpr int kP = 16;    // pencils per CTA: 16 column pairs (T pass) or 16 row pairs (X pass)
+constexpr int kP = 16;    // pencils per CTA of the X passes: 16 row pairs
+constexpr int kPT = 8;    // pencils per CTA of the T pass: 8 column pairs (16 floats)
 constexpr int kT = 128;   // threads per CTA
 constexpr int kKG = 2;    // harmonics per inverse batch in the X forward kernel
 
@@ -55,129 +57,200 @@ __device__ __forceinline__ void fused_conv_stage(const LD& ld, const ST& st, con
     }
 }
 
-// Elementwise pre-pass of a T-pass tile (n elements x 2P columns): the CG
-// update of the loader modes 1/2, with every global load of a thread issued
-// before any of its stores (the updated vectors are read and written in
-// place, which the compiler cannot reorder across), float4 along x.  The
-// operator input b * (p or r) goes to shared memory in the pencil layout
-// (element e of column pair p at buf[e * P + p]).
-template <int N, int P, int T>
-__device__ __forceinline__ void tpass_cg_prepass(const TArgs& a, long long base, int x0, float beta, float alpha,
-                                                 float2* __restrict__ buf)
-{
-    constexpr int V = 2 * P / 4;              // float4 per tile row
-    constexpr int TOTAL = N * V;
-    constexpr int ITER = (TOTAL + T - 1) / T;
-    const bool vec4 = a.vec4 && (x0 + 2 * P <= a.nx);
-    if (!vec4) {                              // ragged tile: scalar through the loader functor
-        const TLoad ld{&a, base, x0, beta, alpha};
-        for (int idx = threadIdx.x; idx < N * P; idx += T) {
-            const int p = idx % P, e = idx / P;
-            buf[e * P + p] = ld(e, p);
-        }
-        return;
-    }
-    float* __restrict__ pv = a.pvec;
-    const float* __restrict__ rv = a.rvec;
-    const float* __restrict__ bv = a.bin;
-    constexpr int CH = ITER < 4 ? ITER : 4;   // iterations whose loads are in flight together
-    for (int it0 = 0; it0 < ITER; it0 += CH) {
-        float4 R[CH], Pp[CH], B[CH], S[CH], Q[CH], X[CH];
-#pragma unroll
-        for (int u = 0; u < CH; ++u) {
-            const int idx = (int)threadIdx.x + (it0 + u) * T;
-            if (it0 + u >= ITER || ((TOTAL % T) != 0 && idx >= TOTAL)) break;
-            const int c = idx % V, e = idx / V;
-            const long long i = base + (long long)e * a.es + x0 + 4 * c;
-            R[u] = __ldcg(reinterpret_cast<const float4*>(rv + i));
-            Pp[u] = __ldcg(reinterpret_cast<const float4*>(pv + i));
-            B[u] = bv ? __ldg(reinterpret_cast<const float4*>(bv + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
-            if (a.pupdate == 2) {
-                S[u] = __ldcg(reinterpret_cast<const float4*>(a.svec + i));
-                Q[u] = __ldcg(reinterpret_cast<const float4*>(a.qdir + i));
-                X[u] = __ldcg(reinterpret_cast<const float4*>(a.xvec + i));
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < CH; ++u) {
-            const int idx = (int)threadIdx.x + (it0 + u) * T;
-            if (it0 + u >= ITER || ((TOTAL % T) != 0 && idx >= TOTAL)) break;
-            const int c = idx % V, e = idx / V;
-            const long long i = base + (long long)e * a.es + x0 + 4 * c;
-            float4 pn, out;
-            pn.x = fmaf(beta, Pp[u].x, R[u].x);
-            pn.y = fmaf(beta, Pp[u].y, R[u].y);
-            pn.z = fmaf(beta, Pp[u].z, R[u].z);
-            pn.w = fmaf(beta, Pp[u].w, R[u].w);
-            *reinterpret_cast<float4*>(pv + i) = pn;
-            if (a.pupdate == 2) {
-                float4 qn, xn;
-                qn.x = fmaf(beta, Q[u].x, S[u].x);
-                qn.y = fmaf(beta, Q[u].y, S[u].y);
-                qn.z = fmaf(beta, Q[u].z, S[u].z);
-                qn.w = fmaf(beta, Q[u].w, S[u].w);
-                xn.x = fmaf(alpha, pn.x, X[u].x);
-                xn.y = fmaf(alpha, pn.y, X[u].y);
-                xn.z = fmaf(alpha, pn.z, X[u].z);
-                xn.w = fmaf(alpha, pn.w, X[u].w);
-                out.x = fmaf(-alpha, qn.x, R[u].x);
-                out.y = fmaf(-alpha, qn.y, R[u].y);
-                out.z = fmaf(-alpha, qn.z, R[u].z);
-                out.w = fmaf(-alpha, qn.w, R[u].w);
-                *reinterpret_cast<float4*>(a.qdir + i) = qn;
-                *reinterpret_cast<float4*>(a.xvec + i) = xn;
-                *reinterpret_cast<float4*>(a.rvec_w + i) = out;
-            } else {
-                out = pn;
-            }
-            buf[e * P + 2 * c] = make_float2(out.x * B[u].x, out.y * B[u].y);
-            buf[e * P + 2 * c + 1] = make_float2(out.z * B[u].z, out.w * B[u].w);
-        }
-    }
-}
+// T pass with bulk (copy-engine) tile I/O.  A tile is N rows (the axis
+// elements, stride es) x 2P contiguous floats (P column pairs); row e of a
+// tile lands in shared memory as the P float2 of pencil layout row e, so
+// the FFT stages read it directly.  Tiles loaded, by loader mode:
+//   plain      : in (and b when the input or output is weighted by b)
+//   pupdate 1  : r, p, b            (p = r + beta p, input b p)
+//   pupdate 2  : r, s, p, q, x, b   (single-reduction CG update, input b r)
+//   epilogue   : in, p, b           (q = b w + lambda p, p^T q [, p^T p])
+// Updated vectors are written back by bulk stores that overlap the FFT; the
+// output leaves through a staging tile.  Host conditions: nx % 2P == 0,
+// every pointer 16-byte aligned, regulariser R = I for the epilogue.
+template <int N, int P>
+struct TTiles {
+    static constexpr int kTile = N * P;   // float2 per tile
+};
 
-// T pass along y or z: TArgs as in ops.cu with cols = 2 kP.
-template <class L>
-__global__ void __launch_bounds__(kT) k_tpass_ct(const TArgs a)
+template <class L, int P>
+__global__ void __launch_bounds__(kT) k_tpass_ct(const __grid_constant__ TArgs a)
 {
     using I = RInfo<L>;
     constexpr int N = I::n(), NST = I::nst, RL = I::last();
     using LI = Reverse<L>;
-    constexpr int P = kP, T = kT;
+    constexpr int T = kT, TILE = N * P;
     static_assert(NST >= 2, "the specialised T pass has at least two stages");
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(128) float2 sm_raw[];
     __shared__ double red[34];
+    __shared__ __align__(8) uint64_t bar;
     float beta = 0.f, alpha = 0.f;
     if (a.cg.flags && !cg_enter(a.cg, a.pupdate != 0, &beta, red, &alpha)) return;
+    // 128-byte aligned start for the TMA boxes (the launcher adds the slack)
+    float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
     float2* tw = sm;
     float2* mu = tw + N;
-    float2* b0 = mu + N;
-    float2* b1 = b0 + N * P;
+    float2* tiles = mu + N;   // six tile slots
+    const int x0 = blockIdx.x * 2 * P;
+    // tiles by loader mode (tensor-map slot of each)
+    int tmap[6] = {0, 0, 0, 0, 0, 0};
+    int nt = 0;
+    const int mode = a.pupdate ? a.pupdate : (a.epilogue ? 3 : 0);
+    const bool bw = (a.bin || a.bout);
+    if (mode == 0) {
+        tmap[nt++] = kTmIn;
+    } else if (mode == 1) {
+        tmap[nt++] = kTmR;
+        tmap[nt++] = kTmP;
+    } else if (mode == 2) {
+        tmap[nt++] = kTmR;
+        tmap[nt++] = kTmS;
+        tmap[nt++] = kTmP;
+        tmap[nt++] = kTmQ;
+        tmap[nt++] = kTmX;
+    } else {
+        tmap[nt++] = kTmIn;
+        tmap[nt++] = kTmPin;
+    }
+    if (bw) tmap[nt++] = kTmB;
+    // box coordinates (x, y, z) of this tile
+    const int cy = (a.axis == 1) ? 0 : (int)blockIdx.y;
+    const int cz = (a.axis == 1) ? (int)blockIdx.y : 0;
+    constexpr uint32_t TILEB = (uint32_t)(N * P * sizeof(float2));
+    // The barrier must be initialised (and the initialisation fenced) before
+    // any thread waits on it: the word may hold a previous CTA's state.
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, TILEB * nt);
+        for (int t = 0; t < nt; ++t) tma_load_3d(tiles + t * TILE, &a.tm.m[tmap[t]], x0, cy, cz, &bar);
+    }
     for (int i = threadIdx.x; i < N; i += T) {
         tw[i] = a.tw[i];
         mu[i] = a.mult[i];
     }
-    const int x0 = blockIdx.x * 2 * P;
-    const long long base = (long long)blockIdx.y * a.os;
-    DotAcc acc, acc2;
-    const TLoad ld{&a, base, x0, beta, alpha};
-    const TStore st{&a, base, x0, &acc, a.part2 ? &acc2 : nullptr};
+    // A copy that never completes would be a hardware fault; the bounded wait
+    // records MH3D_ERR_TIMEOUT and the CTA skips its work instead of hanging.
+    const bool ok = mbar_wait(&bar, 0, a.status);
+    if (!__syncthreads_and(ok)) return;
+
+    // ---- input to the first stage (tin), CG updates in place in the tiles.
+    // tin overwrites, element by element, a tile that only its own thread
+    // reads (in, r or s); the FFT's second buffer b0 is a free slot, or in
+    // the CG update the b tile, which is dead once tin is formed.  Tiles being
+    // written back (r, p, q, x) are never reused before the final wait.
+    const float2* tb = bw ? tiles + (nt - 1) * TILE : nullptr;   // b is the last tile
+    float2* tin = (mode == 2) ? tiles + TILE : tiles;
+    float2* b1 = tin;
+    float2* b0 = (mode == 2) ? tiles + 5 * TILE : tiles + nt * TILE;
+    if (mode == 0 || mode == 3) {
+        const float2* t0 = tiles;
+        for (int i = threadIdx.x; i < TILE; i += T) {
+            float2 v = t0[i];
+            if (a.bin) {
+                const float2 bb = tb[i];
+                v.x *= bb.x;
+                v.y *= bb.y;
+            }
+            tin[i] = v;
+        }
+    } else if (mode == 1) {
+        float2* tr = tiles;
+        float2* tp = tiles + TILE;
+        for (int i = threadIdx.x; i < TILE; i += T) {
+            const float2 r = tr[i], pp = tp[i];
+            const float2 pn = make_float2(fmaf(beta, pp.x, r.x), fmaf(beta, pp.y, r.y));
+            tp[i] = pn;
+            const float2 bb = tb ? tb[i] : make_float2(1.f, 1.f);
+            tin[i] = make_float2(pn.x * bb.x, pn.y * bb.y);
+        }
+    } else {
+        float2* tr = tiles;
+        const float2* ts = tiles + TILE;
+        float2* tp = tiles + 2 * TILE;
+        float2* tq = tiles + 3 * TILE;
+        float2* tx = tiles + 4 * TILE;
+        for (int i = threadIdx.x; i < TILE; i += T) {
+            const float2 r = tr[i], sv = ts[i], pp = tp[i], qq = tq[i], xx = tx[i];
+            const float2 pn = make_float2(fmaf(beta, pp.x, r.x), fmaf(beta, pp.y, r.y));
+            const float2 qn = make_float2(fmaf(beta, qq.x, sv.x), fmaf(beta, qq.y, sv.y));
+            const float2 rn = make_float2(fmaf(-alpha, qn.x, r.x), fmaf(-alpha, qn.y, r.y));
+            tp[i] = pn;
+            tq[i] = qn;
+            tx[i] = make_float2(fmaf(alpha, pn.x, xx.x), fmaf(alpha, pn.y, xx.y));
+            tr[i] = rn;
+            const float2 bb = tb ? tb[i] : make_float2(1.f, 1.f);
+            tin[i] = make_float2(rn.x * bb.x, rn.y * bb.y);
+        }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    // write the updated vectors back while the transform runs
+    if ((mode == 1 || mode == 2) && threadIdx.x == 0) {
+        if (mode == 1) {
+            tma_store_3d(&a.tm.m[kTmP], x0, cy, cz, tiles + TILE);
+        } else {
+            tma_store_3d(&a.tm.m[kTmR], x0, cy, cz, tiles);
+            tma_store_3d(&a.tm.m[kTmP], x0, cy, cz, tiles + 2 * TILE);
+            tma_store_3d(&a.tm.m[kTmQ], x0, cy, cz, tiles + 3 * TILE);
+            tma_store_3d(&a.tm.m[kTmX], x0, cy, cz, tiles + 4 * TILE);
+        }
+        bulk_commit();
+    }
+
+    // ---- convolution: forward stages, fused spectral step, inverse stages
     constexpr int pf = result_parity<0, NST - 1>();
     float2* fo = pf ? b1 : b0;   // output of forward stage NST-2
     float2* fx = pf ? b0 : b1;
-    if (a.pupdate) {
-        // stage 0 then reads b1 and writes b0 (or fo), so b1 is free here
-        tpass_cg_prepass<N, P, T>(a, base, x0, beta, alpha, b1);
-        __syncthreads();
-        run_stages<L, 0, NST - 1, P, T, 1, false, true, true>(BufLd{b1, P}, BufSt{fo, P}, b0, b1, P, tw);
-    } else {
-        __syncthreads();
-        run_stages<L, 0, NST - 1, P, T, 1, false, true, true>(ld, BufSt{fo, P}, b0, b1, P, tw);
-    }
+    run_stages<L, 0, NST - 1, P, T, 1, false, true, true>(BufLd{tin, P}, BufSt{fo, P}, b0, b1, P, tw);
     fused_conv_stage<N, RL, P, T>(BufLd{fo, P}, BufSt{fx, P}, mu, tw);
     __syncthreads();
-    run_stages<LI, 1, NST, P, T, 1, true, true, true>(BufLd{fx, P}, st, fo, fx, P, tw);
-    if (a.epilogue && a.part) {
+    // the last inverse stage writes the buffer it does not read
+    float2* stg = (NST % 2 == 0) ? fo : fx;
+    run_stages<LI, 1, NST, P, T, 1, true, true, true>(BufLd{fx, P}, BufSt{stg, P}, fo, fx, P, tw);
+
+    // ---- output: b weighting / CG epilogue in the staging tile, bulk store
+    DotAcc acc, acc2;
+    if (mode == 3) {
+        const float2* tpin = tiles + TILE;
+        const float lam = a.reg.lambda;
+        for (int i = threadIdx.x; i < TILE; i += T) {
+            float2 w = stg[i];
+            const float2 pv = tpin[i];
+            if (a.bout) {
+                const float2 bb = tb[i];
+                w.x *= bb.x;
+                w.y *= bb.y;
+            }
+            w.x = fmaf(lam, pv.x, w.x);
+            w.y = fmaf(lam, pv.y, w.y);
+            stg[i] = w;
+            acc.add(pv.x, w.x);
+            acc.add(pv.y, w.y);
+            if (a.part2) {
+                acc2.add(pv.x, pv.x);
+                acc2.add(pv.y, pv.y);
+            }
+        }
+    } else if (a.bout) {
+        for (int i = threadIdx.x; i < TILE; i += T) {
+            float2 w = stg[i];
+            const float2 bb = tb[i];
+            stg[i] = make_float2(w.x * bb.x, w.y * bb.y);
+        }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tma_store_3d(&a.tm.m[kTmOut], x0, cy, cz, stg);
+        bulk_commit();
+        bulk_wait_all();   // the copies read shared memory and must land before the kernel ends
+    }
+
+    if (mode == 3 && a.part) {
         const double t = block_sum_f64(acc.value(), red);
         const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
         if (a.part2) {
@@ -190,8 +263,12 @@ __global__ void __launch_bounds__(kT) k_tpass_ct(const TArgs a)
     if (a.count_iter) cg_count_iteration(a.cg);
 }
 
-template <class L>
-constexpr size_t tpass_ct_smem() { return sizeof(float2) * (size_t)(2 * RInfo<L>::n() + 2 * RInfo<L>::n() * kP); }
+template <class L, int P>
+constexpr size_t tpass_ct_smem()
+{
+    // tables, 6 tile slots, and 128 bytes of alignment slack
+    return sizeof(float2) * (size_t)(2 * RInfo<L>::n() + 6 * RInfo<L>::n() * P) + 128;
+}
 
 // Portrait store of one inverse batch (pencil q = kk * P + p), skipping
 // harmonics beyond the last one of the batch.

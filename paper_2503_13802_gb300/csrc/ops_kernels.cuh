@@ -1,6 +1,8 @@
 // Kernel argument blocks shared by ops.cu and solve.cu.
 #pragma once
 
+#include <cuda.h>
+
 #include "fft_smem.cuh"
 
 namespace mh3d {
@@ -47,8 +49,17 @@ struct RegArgs {
     int nx = 1, ny = 1, nz = 1;
 };
 
+// Tensor maps of the T-pass tiles (one per vector), encoded on the host for
+// the box (cols x n x 1) along y or (cols x 1 x n) along z.
+enum { kTmIn = 0, kTmB, kTmR, kTmS, kTmP, kTmQ, kTmX, kTmOut, kTmPin, kTmCount };
+struct TMaps {
+    CUtensorMap m[kTmCount];
+};
+
 // T pass: 1D circular convolution along y or z of tiles of `cols` columns.
 struct TArgs {
+    TMaps tm;                        // filled by the bulk-copy launcher
+    int axis = 1;                    // 1 = y, 2 = z
     const float* in = nullptr;
     float* out = nullptr;
     const float* bin = nullptr;      // input multiplied by b (or null)
@@ -63,6 +74,7 @@ struct TArgs {
     int cols = 32;
     int vec2 = 1;                    // nx even: float2 global access
     int vec4 = 0;                    // nx % 4 == 0 and every vector 16-byte aligned: float4 access
+    int* status = nullptr;           // device status word (bounded waits record timeouts here)
     // CG fusions
     int pupdate = 0;                 // loader: 1 = p = r + beta p (written back), value = b p;
                                      //         2 = p = r + beta p, q = s + beta q, x += alpha p,
@@ -147,7 +159,7 @@ cudaError_t run_xnrm(const XArgs& a, cudaStream_t st);
 int tpass_blocks(int nx, int cols, int nouter);
 
 // Compile-time specialised kernels (ops_ct.cu) for the common lengths.
-bool ct_tpass_available(int n, int cols);
+bool ct_tpass_available(const TArgs& a);
 bool ct_xpass_available(int nx, int s, int pairs);
 cudaError_t ct_set_attributes(int optin);
 cudaError_t run_tpass_ct(const TArgs& a, int nouter, cudaStream_t st);

@@ -496,6 +496,10 @@ static mh3d_status cg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, 
         info->rel_res_true = bn2 > 0 ? std::sqrt(res2 / bn2) : 0.0;
         info->status = status;
     }
+    if (w.flags_host[3] == MH3D_ERR_TIMEOUT) {
+        P.err = "a bounded device wait (bulk copy) timed out";
+        return MH3D_ERR_TIMEOUT;
+    }
     if (!w.flags_host[0]) {
         P.err = "CG loop ended without a device decision";
         return MH3D_ERR_TIMEOUT;
