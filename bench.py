@@ -1,7 +1,8 @@
 """Benchmark: reconstructions/sec to relative residual 1e-4 on the
 128x128x64, k = 2..9, s = 2 synthetic workload (one step = one full MH3D
 reconstruction: A^T d, CG on the normal equations to rel. residual 1e-4,
-true-residual check), plus the HBM roofline of the forward operator A.
+true-residual check), plus the HBM roofline of one CG iteration (the
+unit that dominates a step) and of the forward operator A.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mh3d|reference]
        [--mode 0|1] [--workload NAME]
@@ -31,17 +32,25 @@ import workloads as W  # noqa: E402
 METRIC = "reconstructions/sec to rel. residual 1e-4"
 UNIT = "reconstructions/s"
 WORKLOAD = "mh_128x128x64_k8_s2"
+# Iterations the FP64 oracle's CG takes to reach rel. residual 1e-4 on this
+# workload (seed 0); `python bench.py --impl reference --count-iters` recounts.
+ORACLE_CG_ITERS = 83
+# DRAM bytes (read + write) of one CG iteration's three kernels, summed from
+# one ncu capture with cold L2 (ncu's default cache flush between kernels).
+TRAFFIC_PER_ITER = 42115840   # 25.22 MB T_y + 4.24 MB T_z + 12.65 MB X normal, writes stay in L2
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mh3d", choices=["mh3d", "reference"])
     ap.add_argument("--mode", type=int, default=0, help="0 fused normal operator, 1 explicit A then A^T")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count-iters", action="store_true",
+                    help="reference arm: run the oracle's CG to the tolerance once and print its iteration count")
     return ap.parse_args()
 
 
@@ -76,8 +85,9 @@ class Clocks:
                 ["nvidia-smi", "-i", str(self.gpu),
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)   # nvidia-smi's start-up, so that sampling covers the timed region
         except Exception:
             self.proc = None
         return self
@@ -178,6 +188,40 @@ def bench_mh3d(args):
         total = float(t.item())
     value = ws * args.steps / total
 
+    it_med = int(statistics.median(iters))
+    N = nx * ny * nz
+    M = K * mx * ny * nz
+
+    # Roofline of one CG iteration, the unit that dominates a step: the loop
+    # body's three kernels (T_y with the fused CG vector update, T_z, and the
+    # drive-axis normal pass with b, lambda p and the two dot products).  The
+    # loop runs inside a CUDA graph, so its per-iteration duration is measured
+    # live with events on this stream as the difference of two solves with a
+    # fixed iteration count (it_med and 2): set-up and exit work cancel.
+    def fixed_solve_seconds(n_it, reps=5):
+        of = make_opts(lam=wl.lam, lam_relative=True, max_iter=n_it, fixed_iters=1, normal_mode=args.mode)
+        mh3d_solve(plan, d, of, x)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            mh3d_solve(plan, d, of, x)
+            a1.record(stream)
+            a1.synchronize()
+            ts.append(a0.elapsed_time(a1) / 1e3)
+        return statistics.median(ts)
+
+    it_lo = 2
+    it_s = (fixed_solve_seconds(it_med) - fixed_solve_seconds(it_lo)) / (it_med - it_lo)
+    # Algorithmic bytes of one single-reduction CG iteration with the fused
+    # normal operator: read r, s, p, q, x and b, write r, p, q, x and the new
+    # s = (A^T A + lambda I) r: 11 float32 vectors of N.  (The two
+    # intermediate volumes between the passes and the second reads of b and r
+    # are traffic of this design, not of the algorithm: 17 vectors in all.)
+    it_alg = 11 * 4 * N if args.mode == 0 else 11 * 4 * N + 2 * 8 * M
+
     # Roofline of the forward operator A (T_y + T_z + X_fwd), L2 flushed
     # before each application so rho and b come from HBM and d goes to HBM.
     fwd_t, adj_t = [], []
@@ -199,8 +243,6 @@ def bench_mh3d(args):
         if i >= 3:
             fwd_t.append(e0.elapsed_time(e1) / 1e3)
             adj_t.append(e2.elapsed_time(e3) / 1e3)
-    N = nx * ny * nz
-    M = K * mx * ny * nz
     alg_bytes = 4 * N + 4 * N + 8 * M          # rho + b + complex64 portraits
     peaks = {}
     try:
@@ -210,7 +252,7 @@ def bench_mh3d(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     fwd_s = statistics.mean(fwd_t)
     adj_s = statistics.mean(adj_t)
-    achieved = alg_bytes / fwd_s / 1e9
+    achieved = it_alg / it_s / 1e9
 
     # e2e: host portraits in, host image out, through the C ABI
     d_host = d.cpu().pin_memory()
@@ -241,9 +283,11 @@ def bench_mh3d(args):
         other = {"mode": "explicit A then A^T (portrait through L2/HBM)", "value": 5 / sum(tt),
                  "iters": inf1["iters"]}
 
-    it_med = int(statistics.median(iters))
-    per_iter = 4 if args.mode == 0 else 7
-    launches_per_step = 3 + 1 + per_iter * 2 * (it_med // 2 + 1) + 4
+    # kernels per solve: A^T d (3), CG init (1), s0 = N r0 (per_iter), the
+    # graph loop (two iterations per body, every body launches all its
+    # kernels), the true residual (per_iter + 1)
+    per_iter = 3 if args.mode == 0 else 6
+    launches_per_step = 3 + 1 + per_iter + per_iter * 2 * ((it_med + 1) // 2) + per_iter + 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -254,10 +298,16 @@ def bench_mh3d(args):
                    "normal_mode": "fused Fourier-block A^T A" if args.mode == 0 else "explicit A then A^T",
                    "cg_iters": it_med, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"kernel": "mh3d_forward (A = T_y, T_z, X_fwd)", "bound": "hbm", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "alg_bytes_per_launch": alg_bytes, "us_per_launch": fwd_s * 1e6,
-                     "adjoint_us": adj_s * 1e6, "adjoint_achieved": alg_bytes / adj_s / 1e9,
+        "roofline": {"kernel": "CG iteration = graph body (k_tpass_ct T_y + CG update, k_tpass_ct T_z, "
+                               "k_xnrm_ct)" if args.mode == 0 else "CG iteration, explicit A then A^T",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": TRAFFIC_PER_ITER if args.mode == 0 else None,
+                     "alg_bytes_per_launch": it_alg, "us_per_launch": it_s * 1e6,
+                     "design_bytes_per_iter": 17 * 4 * N,
+                     "forward_A": {"us": fwd_s * 1e6, "alg_bytes": alg_bytes, "achieved_gbs": alg_bytes / fwd_s / 1e9,
+                                   "frac": alg_bytes / fwd_s / 1e9 / peak},
+                     "adjoint_AT": {"us": adj_s * 1e6, "alg_bytes": alg_bytes,
+                                    "achieved_gbs": alg_bytes / adj_s / 1e9, "frac": alg_bytes / adj_s / 1e9 / peak},
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * M),
                 "d2h_bytes_per_step": int(4 * N)},
@@ -316,7 +366,14 @@ def bench_reference(args):
     clean = oracle.forward(g, rho, b, tables)
     sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
     d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, wl.seeds[0])
-    ref_iters = 61   # CG iterations this workload needs to reach 1e-4 (measured on the GPU path)
+    if args.count_iters:
+        t0 = time.perf_counter()
+        _, n_it, _ = oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol,
+                                                         max_iter=wl.max_iter), tables=tables)
+        print(json.dumps({"oracle_cg_iters": int(n_it), "seconds": time.perf_counter() - t0,
+                          "cores": oracle.num_threads()}), flush=True)
+        return
+    ref_iters = ORACLE_CG_ITERS
     sample = 1
     for _ in range(args.warmup if args.warmup < 1 else 1):
         oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=sample),

@@ -452,3 +452,36 @@ def test_generator_statistics_and_determinism():
     assert p1.min() >= 0 and p1.max() > 0.1
     b = W.sensitivity((32, 24, 16))
     assert b.max() <= 1.0 and b.min() > 0.3   # corners: exp(-3 (0.5/0.6)^2 / 2) = 0.35
+
+
+# --------------------------------------------------------------------------
+# Golden fixtures (tests/golden/): values fixed by the paper's printed
+# formulas and by the Taylor series of the Langevin function
+# --------------------------------------------------------------------------
+
+def _golden_rows(name):
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append([int(v) for v in line.split()])
+    return rows
+
+
+def test_golden_ck_theorem1():
+    """c_k = (gamma A)^k / (k-1)! at gamma A = 2 (Theorem 1), k = 1..17."""
+    rows = _golden_rows("ck_theorem1.txt")
+    assert len(rows) == 17
+    for k, num, den in rows:
+        assert oracle.ck(k, 2.0) == pytest.approx(num / den, rel=1e-15), k
+
+
+def test_golden_langevin_taylor_at_zero():
+    """L^(k)(0) for odd k from the Taylor series of coth x - 1/x."""
+    rows = _golden_rows("langevin_taylor_at_zero.txt")
+    assert [r[0] for r in rows] == [1, 3, 5, 7, 9, 11]
+    for k, num, den in rows:
+        assert oracle.langevin_deriv(k, 0.0) == pytest.approx(num / den, rel=1e-13), k
