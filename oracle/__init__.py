@@ -69,6 +69,11 @@ def _load():
     lib.orc_forward_full3d.argtypes = op_args
     lib.orc_adjoint.restype = None
     lib.orc_adjoint.argtypes = op_args
+    crop_args = [i, i, i, i, i, i, P, P, P, P, P, P, P, P]
+    lib.orc_forward_crop.restype = None
+    lib.orc_forward_crop.argtypes = crop_args
+    lib.orc_adjoint_crop.restype = None
+    lib.orc_adjoint_crop.argtypes = crop_args
     lib.orc_reg_apply.restype = None
     lib.orc_reg_apply.argtypes = [i, i, i, i, d, i, P, P]
     lib.orc_normal_apply.restype = None
@@ -198,6 +203,47 @@ def adjoint(g: Geometry, d, b=None, tables=None) -> np.ndarray:
     b = None if b is None else _f64(b).reshape(g.shape)
     out = np.zeros(g.shape)
     _op(_load().orc_adjoint, g, tables, b, _complex_in(g, d), out)
+    return out
+
+
+def _crop_arg(crop):
+    """crop = ((a0, na), (y0, ny), (z0, nz)) along (drive, y, z)."""
+    (a0, na), (y0, ny), (z0, nz) = crop
+    return np.ascontiguousarray([a0, na, y0, ny, z0, nz], dtype=np.int32)
+
+
+def _op_crop(fn, g: Geometry, tables, b, src, crop, out):
+    nx, ny, nz = g.n
+    X, Y, Z = tables
+    th = g.theta_array()
+    c = _crop_arg(crop)
+    fn(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z), _ptr(th),
+       _ptr(b), _ptr(src), _ptr(c), _ptr(out))
+    return out
+
+
+def forward_crop(g: Geometry, rho, crop, b=None, tables=None) -> np.ndarray:
+    """d = A rho on an output crop ((i0, ni), (y0, ny_c), (z0, nz_c)) of the
+    portrait mesh (i along the downsampled drive axis): complex128
+    [K, nz_c, ny_c, ni].  Only the crop's outputs are evaluated, so large
+    grids stay tractable."""
+    tables = tables or psf_tables(g)
+    rho = _f64(rho).reshape(g.shape)
+    b = None if b is None else _f64(b).reshape(g.shape)
+    (_, ni), (_, nyc), (_, nzc) = crop
+    out = np.zeros((g.K, nzc, nyc, ni, 2))
+    _op_crop(_load().orc_forward_crop, g, tables, b, rho, crop, out)
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def adjoint_crop(g: Geometry, d, crop, b=None, tables=None) -> np.ndarray:
+    """rho = A^T d on an image crop ((x0, nx_c), (y0, ny_c), (z0, nz_c)):
+    float64 [nz_c, ny_c, nx_c]."""
+    tables = tables or psf_tables(g)
+    b = None if b is None else _f64(b).reshape(g.shape)
+    (_, nxc), (_, nyc), (_, nzc) = crop
+    out = np.zeros((nzc, nyc, nxc))
+    _op_crop(_load().orc_adjoint_crop, g, tables, b, _complex_in(g, d), crop, out)
     return out
 
 

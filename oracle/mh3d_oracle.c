@@ -320,6 +320,114 @@ void orc_adjoint(int nx, int ny, int nz, int s, int r, int K,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Output crops of the forward and adjoint operators (large grids)          */
+/* ------------------------------------------------------------------------ */
+
+/* The forward model of orc_forward, evaluated only on the output crop
+ * z in [c[4], c[4]+c[5]), y in [c[2], c[2]+c[3]), i' in [c[0], c[0]+c[1])
+ * (c = {i0, ni, y0, ny_c, z0, nz_c}); d_crop is [K][nz_c][ny_c][ni] complex.
+ * Same definition, the circular sums restricted to the outputs asked for:
+ *   v[z][y'][x'] = sum_z' Z[z - z'] b rho[z'][y'][x']      (z in the crop)
+ *   w[z][y][x']  = sum_y' Y[y - y'] v[z][y'][x']           (y in the crop)
+ *   d_k[z][y][i'] = e^{i theta_k} sum_x' X_k[s i' + r - x'] w[z][y][x']. */
+void orc_forward_crop(int nx, int ny, int nz, int s, int r, int K,
+                      const double* X, const double* Y, const double* Z, const double* theta,
+                      const double* b, const double* rho, const int* c, double* d)
+{
+    const int i0 = c[0], ni = c[1], y0 = c[2], nyc = c[3], z0 = c[4], nzc = c[5];
+    double* v = (double*)malloc((size_t)nzc * ny * nx * sizeof(double));
+    double* w = (double*)malloc((size_t)nzc * nyc * nx * sizeof(double));
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int zc = 0; zc < nzc; ++zc)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                double acc = 0.0;
+                for (int zp = 0; zp < nz; ++zp) {
+                    const size_t j = ((size_t)zp * ny + y) * nx + x;
+                    acc += Z[orc_mod((long)(z0 + zc) - zp, nz)] * (b ? b[j] : 1.0) * rho[j];
+                }
+                v[((size_t)zc * ny + y) * nx + x] = acc;
+            }
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int zc = 0; zc < nzc; ++zc)
+        for (int yc = 0; yc < nyc; ++yc)
+            for (int x = 0; x < nx; ++x) {
+                double acc = 0.0;
+                for (int yp = 0; yp < ny; ++yp)
+                    acc += Y[orc_mod((long)(y0 + yc) - yp, ny)] * v[((size_t)zc * ny + yp) * nx + x];
+                w[((size_t)zc * nyc + yc) * nx + x] = acc;
+            }
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int kk = 0; kk < K; ++kk)
+        for (int zy = 0; zy < nzc * nyc; ++zy) {
+            const double cs = cos(theta ? theta[kk] : 0.0), sn = sin(theta ? theta[kk] : 0.0);
+            const double* row = w + (size_t)zy * nx;
+            const double* Xk = X + (size_t)kk * nx;
+            for (int ic = 0; ic < ni; ++ic) {
+                const long ip = i0 + ic;
+                double acc = 0.0;
+                for (int xp = 0; xp < nx; ++xp) acc += Xk[orc_mod((long)s * ip + r - xp, nx)] * row[xp];
+                double* o = d + 2 * (((size_t)kk * nzc * nyc + zy) * ni + ic);
+                o[0] = cs * acc;
+                o[1] = sn * acc;
+            }
+        }
+    free(v);
+    free(w);
+}
+
+/* The adjoint of orc_adjoint, evaluated only on the image crop
+ * z in [c[4], c[4]+c[5]), y in [c[2], c[2]+c[3]), x in [c[0], c[0]+c[1]);
+ * rho_crop is [nz_c][ny_c][nx_c]:
+ *   g[z'][y'][x] = sum_k sum_i' X_k[s i' + r - x] Re(e^{-i theta_k} d_k[z'][y'][i'])   (x in the crop)
+ *   v[z][y'][x]  = sum_z' Z[z' - z] g[z'][y'][x]                                        (z in the crop)
+ *   rho[z][y][x] = b sum_y' Y[y' - y] v[z][y'][x]                                       (y in the crop) */
+void orc_adjoint_crop(int nx, int ny, int nz, int s, int r, int K,
+                      const double* X, const double* Y, const double* Z, const double* theta,
+                      const double* b, const double* d, const int* c, double* rho)
+{
+    const int x0 = c[0], nxc = c[1], y0 = c[2], nyc = c[3], z0 = c[4], nzc = c[5];
+    const int mx = nx / s;
+    double* g = (double*)malloc((size_t)nz * ny * nxc * sizeof(double));
+    double* v = (double*)malloc((size_t)nzc * ny * nxc * sizeof(double));
+    #pragma omp parallel for schedule(static)
+    for (int zy = 0; zy < nz * ny; ++zy)
+        for (int xc = 0; xc < nxc; ++xc) {
+            double acc = 0.0;
+            for (int kk = 0; kk < K; ++kk) {
+                const double cs = cos(theta ? theta[kk] : 0.0), sn = sin(theta ? theta[kk] : 0.0);
+                const double* Xk = X + (size_t)kk * nx;
+                for (int ip = 0; ip < mx; ++ip) {
+                    const double* dv = d + 2 * (((size_t)kk * nz * ny + zy) * mx + ip);
+                    acc += Xk[orc_mod((long)s * ip + r - (x0 + xc), nx)] * (cs * dv[0] + sn * dv[1]);
+                }
+            }
+            g[(size_t)zy * nxc + xc] = acc;
+        }
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int zc = 0; zc < nzc; ++zc)
+        for (int y = 0; y < ny; ++y)
+            for (int xc = 0; xc < nxc; ++xc) {
+                double acc = 0.0;
+                for (int zp = 0; zp < nz; ++zp)
+                    acc += Z[orc_mod((long)zp - (z0 + zc), nz)] * g[((size_t)zp * ny + y) * nxc + xc];
+                v[((size_t)zc * ny + y) * nxc + xc] = acc;
+            }
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int zc = 0; zc < nzc; ++zc)
+        for (int yc = 0; yc < nyc; ++yc)
+            for (int xc = 0; xc < nxc; ++xc) {
+                double acc = 0.0;
+                for (int yp = 0; yp < ny; ++yp)
+                    acc += Y[orc_mod((long)yp - (y0 + yc), ny)] * v[((size_t)zc * ny + yp) * nxc + xc];
+                const size_t j = ((size_t)(z0 + zc) * ny + (y0 + yc)) * nx + (x0 + xc);
+                rho[((size_t)zc * nyc + yc) * nxc + xc] = (b ? b[j] : 1.0) * acc;
+            }
+    free(g);
+    free(v);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Regulariser and normal operator                                          */
 /* ------------------------------------------------------------------------ */
 

@@ -485,3 +485,35 @@ def test_golden_langevin_taylor_at_zero():
     assert [r[0] for r in rows] == [1, 3, 5, 7, 9, 11]
     for k, num, den in rows:
         assert oracle.langevin_deriv(k, 0.0) == pytest.approx(num / den, rel=1e-13), k
+
+
+# --------------------------------------------------------------------------
+# Output crops (for grids too large for the whole-volume oracle)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,s,r", [((12, 10, 8), 1, 0), ((16, 6, 9), 2, 1), ((18, 7, 6), 3, 2)])
+def test_forward_crop_equals_window_of_full_forward(n, s, r):
+    """The crop evaluation is the same circular sum restricted to the outputs
+    asked for: it must equal the matching window of the whole forward model
+    (itself pinned against numpy's FFT convolution and the triple sum)."""
+    g = _geom(n, s=s, r=r, kmin=2, kmax=5, theta=[0.2, -1.0, 2.5, 0.7])
+    rho = W.random_volume(g.shape, 11)
+    b = W.sensitivity(n, (1.0, 1.0, 1.0))
+    full = oracle.forward(g, rho, b)
+    mx = n[0] // s
+    crop = ((1, mx - 2), (2, n[1] - 3), (1, n[2] - 2))
+    got = oracle.forward_crop(g, rho, crop, b)
+    ref = full[:, 1:1 + n[2] - 2, 2:2 + n[1] - 3, 1:1 + mx - 2]
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(full).max()
+
+
+@pytest.mark.parametrize("n,s,r", [((12, 10, 8), 1, 0), ((16, 6, 9), 2, 1), ((18, 7, 6), 3, 2)])
+def test_adjoint_crop_equals_window_of_full_adjoint(n, s, r):
+    g = _geom(n, s=s, r=r, kmin=2, kmax=5, theta=[0.2, -1.0, 2.5, 0.7])
+    y = W.random_portraits(g.portrait_shape, 12)
+    b = W.sensitivity(n, (1.0, 1.0, 1.0))
+    full = oracle.adjoint(g, y, b)
+    crop = ((3, n[0] - 5), (1, n[1] - 2), (2, n[2] - 4))
+    got = oracle.adjoint_crop(g, y, crop, b)
+    ref = full[2:2 + n[2] - 4, 1:1 + n[1] - 2, 3:3 + n[0] - 5]
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(full).max()
