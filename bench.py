@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--mode", type=int, default=0, help="0 fused normal operator, 1 explicit A then A^T")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="the 64-volume batched workload (one JSON line of its own)")
     ap.add_argument("--count-iters", action="store_true",
                     help="reference arm: run the oracle's CG to the tolerance once and print its iteration count")
     return ap.parse_args()
@@ -351,6 +353,87 @@ def cpu_baseline(wl: W.Workload, gpu_iters: int, sample_iters: int = 2):
                       f"({t:.1f} s), scaled to {gpu_iters} iterations + A^T d + true residual"}
 
 
+def bench_batched(args):
+    """The 64-volume workload: sizes drawn (seed 777) from 64^3, 96x96x64,
+    128x128x64 and 192x192x96; volume i has phantom and noise seed 1000 + i;
+    K = 8, s = 2, Gaussian b, 25 dB, CG to rel. residual 1e-4.  One step =
+    one mh3d_solve_batched call over all 64 volumes (one CUDA graph);
+    value = volumes / second.  The same volumes solved one after another by
+    mh3d_solve are reported beside it."""
+    import torch
+
+    from paper_2503_13802_gb300 import Plan, make_opts, mh3d_forward, mh3d_solve, mh3d_solve_batched
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = W.WORKLOADS[WORKLOAD]
+    sizes = W.batch_sizes(64, 777)
+    plans, ds, xs = [], [], []
+    for i, n in enumerate(sizes):
+        rho = W.phantom(n, (1.0, 1.0, 1.0), 1000 + i, wl.n_blobs, wl.n_lines)
+        b = W.sensitivity(n, (1.0, 1.0, 1.0), kind="gaussian")
+        pl = Plan(n, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max, sensitivity=b)
+        d = torch.empty(pl.portrait_shape, dtype=torch.complex64, device=dev)
+        mh3d_forward(pl, torch.as_tensor(rho, dtype=torch.float32, device=dev).contiguous(), d)
+        sig2 = float(torch.sum(torch.abs(d.to(torch.complex128)) ** 2)) / (d.numel() * 10 ** (wl.snr_db / 10))
+        noise = torch.as_tensor(W.unit_complex_noise(tuple(d.shape), 1000 + i).astype(np.complex64), device=dev)
+        plans.append(pl)
+        ds.append((d + math.sqrt(sig2) * noise).contiguous())
+        xs.append(torch.empty(pl.shape, dtype=torch.float32, device=dev))
+    opts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        infos = mh3d_solve_batched(plans, ds, opts, xs)
+    times = []
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos = mh3d_solve_batched(plans, ds, opts, xs)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+    total = sum(times)
+    value = len(plans) * args.steps / total
+    # one after another, for comparison
+    seq = []
+    for _ in range(2):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for pl, d, x in zip(plans, ds, xs):
+            mh3d_solve(pl, d, opts, x)
+        e1.record(stream)
+        e1.synchronize()
+        seq.append(e0.elapsed_time(e1) / 1e3)
+    iters = [inf["iters"] for inf in infos]
+    worst = max(inf["rel_res_true"] for inf in infos)
+    line = {
+        "metric": "batched reconstructions/sec to rel. residual 1e-4", "value": value, "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)",
+        "data": "synthetic",
+        "config": {"workload": "batch64_mixed_k8_s2", "volumes": len(plans),
+                   "size_classes": [list(c) for c in W.BATCH_SIZE_CLASSES],
+                   "count_per_class": [sizes.count(c) for c in W.BATCH_SIZE_CLASSES],
+                   "voxels_total": int(sum(p.N for p in plans)), "harmonics": [wl.k_min, wl.k_max],
+                   "ds_factor": wl.ds_factor, "snr_db": wl.snr_db, "lambda": wl.lam, "rel_tol": wl.rel_tol,
+                   "launch": "one CUDA graph, one branch per volume", "l2": "flushed between steps (256 MB write)"},
+        "cg_iters": {"min": min(iters), "max": max(iters), "mean": statistics.mean(iters)},
+        "worst_rel_res_true": worst,
+        "one_after_another": {"value": len(plans) / statistics.mean(seq), "unit": UNIT,
+                              "ms": 1e3 * statistics.mean(seq)},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def bench_reference(args):
     """The FP64 oracle as the reference arm, rank 0 only."""
     ws, rank, _ = dist_env()
@@ -402,6 +485,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.batched:
+        bench_batched(args)
     else:
         bench_mh3d(args)
 

@@ -148,11 +148,22 @@ mh3d_status mh3d_solve(mh3d_plan plan, const void* d_dev, const mh3d_solve_opts*
 mh3d_status mh3d_solve_host(mh3d_plan plan, const void* d_host, const mh3d_solve_opts* opts,
                             float* rho_host, mh3d_solve_info* info, void* stream);
 
-/* Solve nvol independent problems (each with its own plan, grid size and
- * data) in one batched launch sequence: every phase kernel covers the work
- * of all unfinished volumes, and the iteration loop runs as a captured CUDA
- * graph with a device-side while condition.  opts applies to every volume.
- * infos (may be NULL) receives nvol records. */
+/* Solve nvol independent problems, each with its own plan (grid sizes may
+ * differ) and data, in one launch: for CG (opts->solver == 0) the call
+ * stages every volume's portraits into its plan, then launches ONE CUDA graph
+ * that holds one independent branch per volume (A^T d, set-up, a
+ * device-driven conditional while loop, true residual), so the GPU runs the
+ * volumes concurrently; it synchronises twice and fills infos.  The graph
+ * is cached for the same plans and options.  APG (solver 1), or
+ * MH3D_NO_GRAPH=1, solves the volumes one after another.
+ *   plans[v], d_dev[v] (K*M complex64 on the device), rho_dev[v] (N floats
+ *   on the device) for v < nvol; each plan at most once (the branches use
+ *   the plans' workspaces); opts applies to every volume and opts->x0_dev
+ *   must be NULL; infos (may be NULL) receives nvol records, and their
+ *   history pointers (may be NULL) are honoured.
+ *   Returns the first non-OK volume status (MH3D_ERR_NOT_CONVERGED keeps
+ *   the iterates); mh3d_last_error(plans[0]) names the volume.  Plans must
+ *   not be destroyed while a call that uses them runs. */
 mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* const* d_dev,
                                const mh3d_solve_opts* opts, float* const* rho_dev,
                                mh3d_solve_info* infos, void* stream);

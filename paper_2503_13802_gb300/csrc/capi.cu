@@ -458,6 +458,7 @@ mh3d_status mh3d_plan_destroy(mh3d_plan P)
 {
     if (!P) return MH3D_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
+    batch_forget(*P);
     solve_free(*P);
     if (P->table_mem) cudaFree(P->table_mem);
     delete P;

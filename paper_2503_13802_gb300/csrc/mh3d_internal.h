@@ -1,6 +1,7 @@
 // Internal declarations of the MH3D GB300 library (not part of the C ABI).
 #pragma once
 
+#include <atomic>
 #include <complex>
 #include <string>
 #include <vector>
@@ -60,7 +61,15 @@ struct SolveWork {
     void* base = nullptr;         // one allocation backing the vectors
 };
 
+inline unsigned long long next_plan_serial()
+{
+    static std::atomic<unsigned long long> n{0};
+    return ++n;
+}
+
 struct Plan {
+    // unique for the process's lifetime (caches key on it, never on addresses)
+    unsigned long long serial = next_plan_serial();
     // geometry
     int nx = 1, ny = 1, nz = 1, s = 1, r = 0, K = 1, kmin = 2, kmax = 2;
     int mx = 1;

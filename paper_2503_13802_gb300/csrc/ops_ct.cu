@@ -152,6 +152,9 @@ bool ct_xpass_available(int nx, int s, int pairs) { return !force_generic() && p
 
 cudaError_t ct_set_attributes(int optin)
 {
+    // resolve the driver's encoder now: a first call inside a stream capture
+    // would query the driver while the capture is open
+    tensor_map_encoder();
     static const int tn[] = {32, 64, 96, 128, 192, 256};
     for (int n : tn) {
         const TDesc d = tpass_desc(n);

@@ -16,6 +16,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "solve_internal.h"
 
@@ -345,17 +347,15 @@ static unsigned long long opts_key(const mh3d_solve_opts& o)
         }                                                                                         \
     } while (0)
 
-static mh3d_status build_graph(Plan& P, const mh3d_solve_opts& o)
+// Adds to graph g, after deps, a conditional WHILE node whose body holds
+// two CG iterations of plan P (captured on cap, which must not be
+// capturing); the kernels set the condition from the device.
+static cudaError_t add_cg_loop_node(Plan& P, const mh3d_solve_opts& o, cudaGraph_t g, const cudaGraphNode_t* deps,
+                                    size_t ndeps, cudaStream_t cap, cudaGraphNode_t* node)
 {
-    if (P.graph_exec) {
-        cudaGraphExecDestroy(P.graph_exec);
-        P.graph_exec = nullptr;
-    }
-    if (!P.graph_stream) MH3D_CK(P, cudaStreamCreateWithFlags(&P.graph_stream, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    MH3D_CK(P, cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
     cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
     // cudaGraphNodeParams has no default constructor (union members): use
     // zeroed storage, as the runtime expects for unused fields.
     alignas(cudaGraphNodeParams) unsigned char np_storage[sizeof(cudaGraphNodeParams)];
@@ -365,22 +365,32 @@ static mh3d_status build_graph(Plan& P, const mh3d_solve_opts& o)
     np.conditional.handle = h;
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
-    cudaGraphNode_t node;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
-    if (e == cudaSuccess) {
-        cudaGraph_t body = np.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(P.graph_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            CgCtl c = base_ctl(P, o);
-            c.cond = h;
-            c.use_cond = 1;
-            cudaError_t e1 = enqueue_iteration(P, o, 0, c, P.graph_stream);
-            cudaError_t e2 = (e1 == cudaSuccess) ? enqueue_iteration(P, o, 1, c, P.graph_stream) : e1;
-            cudaGraph_t outg = nullptr;
-            cudaError_t e3 = cudaStreamEndCapture(P.graph_stream, &outg);
-            e = (e2 != cudaSuccess) ? e2 : e3;
-        }
+    e = cudaGraphAddNode(node, g, deps, nullptr, ndeps, &np);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    CgCtl c = base_ctl(P, o);
+    c.cond = h;
+    c.use_cond = 1;
+    cudaError_t e1 = enqueue_iteration(P, o, 0, c, cap);
+    cudaError_t e2 = (e1 == cudaSuccess) ? enqueue_iteration(P, o, 1, c, cap) : e1;
+    cudaGraph_t outg = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(cap, &outg);
+    return (e2 != cudaSuccess) ? e2 : e3;
+}
+
+static mh3d_status build_graph(Plan& P, const mh3d_solve_opts& o)
+{
+    if (P.graph_exec) {
+        cudaGraphExecDestroy(P.graph_exec);
+        P.graph_exec = nullptr;
     }
+    if (!P.graph_stream) MH3D_CK(P, cudaStreamCreateWithFlags(&P.graph_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    MH3D_CK(P, cudaGraphCreate(&g, 0));
+    cudaGraphNode_t node;
+    cudaError_t e = add_cg_loop_node(P, o, g, nullptr, 0, P.graph_stream, &node);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&P.graph_exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -425,29 +435,12 @@ static mh3d_status run_cg_loop(Plan& P, const mh3d_solve_opts& o, cudaStream_t s
 }
 
 
-// ||rhs - N x||^2 and ||rhs||^2 on the host from device partials.
-static mh3d_status true_residual(Plan& P, const mh3d_solve_opts& o, cudaStream_t st, double* res2, double* bn2)
+// What a CG solve enqueues before its loop: A^T d, zeroed flags and tickets,
+// the initial residual and, for single-reduction CG, s0 = N r0 with its two
+// dot products.
+static mh3d_status cg_prefix(Plan& P, const float2* d, const mh3d_solve_opts& o, cudaStream_t st)
 {
     SolveWork& w = P.w;
-    const int nU = update_blocks(P.N);
-    MH3D_CK(P, launch_normal(P, o.normal_mode, reg_args(P, o), w.x, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr,
-                             nullptr, st));
-    k_diff_norm2<<<nU, 256, 0, st>>>(w.rhs, w.q, P.N, part_slot(P, kPartRES), ticket(P, kTkRES), scal(P, kRES));
-    MH3D_CK(P, cudaGetLastError());
-    MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, 0), kNScal * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MH3D_CK(P, cudaStreamSynchronize(st));
-    *res2 = w.red_host[kRES];
-    *bn2 = w.red_host[kBN];
-    return MH3D_OK;
-}
-
-static mh3d_status cg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, float* rho, mh3d_solve_info* info,
-                            cudaStream_t st)
-{
-    SolveWork& w = P.w;
-    mh3d_status s = ensure_hist(P, o.max_iter + 1);
-    if (s != MH3D_OK) return s;
-    if (o.normal_mode == 1 && (s = ensure_portrait(P)) != MH3D_OK) return s;
     const RegArgs reg = reg_args(P, o);
     const int nU = update_blocks(P.N);
     MH3D_CK(P, launch_adjoint(P, d, w.rhs, w.t1, w.t2, st));
@@ -475,24 +468,60 @@ static mh3d_status cg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, 
         MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.r, w.s, w.t1, w.t2, w.portrait, &dots, nullptr, nullptr,
                                  st));
     }
-    if ((s = run_cg_loop(P, o, st)) != MH3D_OK) return s;
+    return MH3D_OK;
+}
+
+// What a CG solve enqueues after its loop: the loop's flags to the host, the
+// true residual ||rhs - N x||^2 and the scalars (||rhs||^2 among them).
+static mh3d_status cg_suffix(Plan& P, const mh3d_solve_opts& o, cudaStream_t st)
+{
+    SolveWork& w = P.w;
+    const int nU = update_blocks(P.N);
     MH3D_CK(P, cudaMemcpyAsync(w.flags_host, w.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    double res2 = 0, bn2 = 0;
-    if ((s = true_residual(P, o, st, &res2, &bn2)) != MH3D_OK) return s;
+    MH3D_CK(P, launch_normal(P, o.normal_mode, reg_args(P, o), w.x, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr,
+                             nullptr, st));
+    k_diff_norm2<<<nU, 256, 0, st>>>(w.rhs, w.q, P.N, part_slot(P, kPartRES), ticket(P, kTkRES), scal(P, kRES));
+    MH3D_CK(P, cudaGetLastError());
+    MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, 0), kNScal * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return MH3D_OK;
+}
+
+// ||rhs - N x||^2 and ||rhs||^2 on the host (synchronises).
+static mh3d_status true_residual(Plan& P, const mh3d_solve_opts& o, cudaStream_t st, double* res2, double* bn2)
+{
+    mh3d_status s = cg_suffix(P, o, st);
+    if (s != MH3D_OK) return s;
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    *res2 = P.w.red_host[kRES];
+    *bn2 = P.w.red_host[kBN];
+    return MH3D_OK;
+}
+
+constexpr int kRecSlot = 12;   // host slot of the final recurrence residual (after the scalars)
+
+// Once the suffix's copies have landed: the recurrence residual of the last
+// iteration, the image and the residual history.
+static mh3d_status cg_tail(Plan& P, const mh3d_solve_opts& o, float* rho, mh3d_solve_info* info, cudaStream_t st)
+{
+    SolveWork& w = P.w;
     const int iters = w.flags_host[1];
-    const int status = w.flags_host[2];
-    double rec = 0.0;
-    MH3D_CK(P, cudaMemcpyAsync(&w.red_host[0], w.hist + std::min(iters, w.hist_cap - 1), sizeof(double),
+    MH3D_CK(P, cudaMemcpyAsync(&w.red_host[kRecSlot], w.hist + std::min(iters, w.hist_cap - 1), sizeof(double),
                                cudaMemcpyDeviceToHost, st));
-    MH3D_CK(P, cudaMemcpyAsync(rho, w.x, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+    if (rho) MH3D_CK(P, cudaMemcpyAsync(rho, w.x, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
     if (info && info->history)
         MH3D_CK(P, cudaMemcpyAsync(info->history, w.hist, sizeof(double) * (std::min(iters, o.max_iter) + 1),
                                    cudaMemcpyDeviceToHost, st));
-    MH3D_CK(P, cudaStreamSynchronize(st));
-    rec = w.red_host[0];
+    return MH3D_OK;
+}
+
+// Fills info from the host copies; returns the solve's status.
+static mh3d_status cg_report(Plan& P, double res2, double bn2, mh3d_solve_info* info)
+{
+    SolveWork& w = P.w;
+    const int status = w.flags_host[2];
     if (info) {
-        info->iters = iters;
-        info->rel_res_recurrence = rec;
+        info->iters = w.flags_host[1];
+        info->rel_res_recurrence = w.red_host[kRecSlot];
         info->rel_res_true = bn2 > 0 ? std::sqrt(res2 / bn2) : 0.0;
         info->status = status;
     }
@@ -507,6 +536,191 @@ static mh3d_status cg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, 
     if (status == MH3D_ERR_NOT_CONVERGED) P.err = "max_iter reached before rel_tol";
     if (status == MH3D_ERR_NONFINITE) P.err = "non-finite value in an FP64 reduction";
     return (mh3d_status)status;
+}
+
+static mh3d_status cg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, float* rho, mh3d_solve_info* info,
+                            cudaStream_t st)
+{
+    mh3d_status s = ensure_hist(P, o.max_iter + 1);
+    if (s != MH3D_OK) return s;
+    if (o.normal_mode == 1 && (s = ensure_portrait(P)) != MH3D_OK) return s;
+    if ((s = cg_prefix(P, d, o, st)) != MH3D_OK) return s;
+    if ((s = run_cg_loop(P, o, st)) != MH3D_OK) return s;
+    if ((s = cg_suffix(P, o, st)) != MH3D_OK) return s;
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    const double res2 = P.w.red_host[kRES], bn2 = P.w.red_host[kBN];
+    if ((s = cg_tail(P, o, rho, info, st)) != MH3D_OK) return s;
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    return cg_report(P, res2, bn2, info);
+}
+
+// ---------------------------------------------------------------------------
+// Batched CG: one CUDA graph, one independent branch per volume
+// ---------------------------------------------------------------------------
+// Each branch is a volume's whole solve: A^T d from the plan's staged
+// portraits, the CG set-up, its own conditional WHILE loop driven by its own
+// device flags, the true residual and the copies of its flags and scalars to
+// pinned host memory.  Branches share nothing, so the GPU runs them
+// concurrently and small volumes fill the SMs that one volume leaves idle.
+// The graph is cached per (plans, options, plan buffers); portraits and
+// images pass through plan-owned buffers, so a call with new pointers reuses
+// it.
+namespace {
+
+struct BatchGraph {
+    std::vector<unsigned long long> serials;
+    unsigned long long key = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batches;   // most recent last
+constexpr size_t kMaxBatchGraphs = 4;
+
+unsigned long long batch_key(const std::vector<Plan*>& ps, const mh3d_solve_opts& o)
+{
+    unsigned long long h = opts_key(o);
+    auto mix = [&](unsigned long long v) {
+        for (int i = 0; i < 8; ++i) h = (h ^ ((v >> (8 * i)) & 0xff)) * 1099511628211ull;
+    };
+    for (const Plan* P : ps) {
+        mix(P->serial);
+        mix((unsigned long long)(uintptr_t)P->w.hist);
+        mix((unsigned long long)(uintptr_t)P->w.portrait);
+    }
+    return h;
+}
+
+}  // namespace
+
+void batch_forget(const Plan& P)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batches.size();) {
+        const auto& v = g_batches[i].serials;
+        if (std::find(v.begin(), v.end(), P.serial) != v.end()) {
+            cudaGraphExecDestroy(g_batches[i].exec);
+            g_batches.erase(g_batches.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+static mh3d_status build_batch_graph(const std::vector<Plan*>& ps, const mh3d_solve_opts& o, cudaGraphExec_t* out)
+{
+    Plan& P0 = *ps[0];
+    cudaStream_t cs = nullptr, cb = nullptr;
+    MH3D_CK(P0, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamCreateWithFlags(&cb, cudaStreamNonBlocking);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+    mh3d_status st = MH3D_OK;
+    for (size_t v = 0; v < ps.size() && e == cudaSuccess && st == MH3D_OK; ++v) {
+        Plan& P = *ps[v];
+        e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        st = cg_prefix(P, P.w.portrait, o, cs);
+        if (st == MH3D_OK) {
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+            cudaGraphNode_t loop = nullptr;
+            if (e == cudaSuccess) {
+                std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+                e = add_cg_loop_node(P, o, g, dv.data(), dv.size(), cb, &loop);
+            }
+            if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1,
+                                                                          cudaStreamSetCaptureDependencies);
+            if (e == cudaSuccess) st = cg_suffix(P, o, cs);
+        }
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+        if (e == cudaSuccess) e = e2;
+        if (st != MH3D_OK && P0.err.empty()) P0.err = P.err;
+    }
+    if (e == cudaSuccess && st == MH3D_OK) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (cb) cudaStreamDestroy(cb);
+    cudaStreamDestroy(cs);
+    if (st != MH3D_OK) return st;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        P0.err = std::string("CUDA graph of the batched solve: ") + cudaGetErrorString(e);
+        return MH3D_ERR_CUDA;
+    }
+    return MH3D_OK;
+}
+
+static mh3d_status batch_graph(const std::vector<Plan*>& ps, const mh3d_solve_opts& o, cudaGraphExec_t* exec)
+{
+    std::vector<unsigned long long> serials;
+    for (const Plan* P : ps) serials.push_back(P->serial);
+    const unsigned long long key = batch_key(ps, o);
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batches.size(); ++i)
+        if (g_batches[i].key == key && g_batches[i].serials == serials) {
+            BatchGraph b = g_batches[i];
+            g_batches.erase(g_batches.begin() + i);
+            g_batches.push_back(b);
+            *exec = b.exec;
+            return MH3D_OK;
+        }
+    BatchGraph b;
+    b.serials = serials;
+    b.key = key;
+    mh3d_status s = build_batch_graph(ps, o, &b.exec);
+    if (s != MH3D_OK) return s;
+    if (g_batches.size() >= kMaxBatchGraphs) {
+        cudaGraphExecDestroy(g_batches.front().exec);
+        g_batches.erase(g_batches.begin());
+    }
+    g_batches.push_back(b);
+    *exec = b.exec;
+    return MH3D_OK;
+}
+
+static mh3d_status cg_solve_batched(const std::vector<Plan*>& ps, const float2* const* d, const mh3d_solve_opts& o,
+                                    float* const* rho, mh3d_solve_info* infos, cudaStream_t st)
+{
+    Plan& P0 = *ps[0];
+    for (Plan* P : ps) {
+        mh3d_status s = ensure_hist(*P, o.max_iter + 1);
+        if (s == MH3D_OK) s = ensure_portrait(*P);
+        if (s != MH3D_OK) {
+            P0.err = P->err;
+            return s;
+        }
+    }
+    // stage the portraits in the plans' own buffers (the graph reads those)
+    for (size_t v = 0; v < ps.size(); ++v)
+        MH3D_CK(P0, cudaMemcpyAsync(ps[v]->w.portrait, d[v], sizeof(float2) * (size_t)ps[v]->K * ps[v]->M,
+                                    cudaMemcpyDeviceToDevice, st));
+    cudaGraphExec_t exec = nullptr;
+    mh3d_status s = batch_graph(ps, o, &exec);
+    if (s != MH3D_OK) return s;
+    MH3D_CK(P0, cudaGraphLaunch(exec, st));
+    MH3D_CK(P0, cudaStreamSynchronize(st));
+    std::vector<double> res2(ps.size()), bn2(ps.size());
+    for (size_t v = 0; v < ps.size(); ++v) {
+        res2[v] = ps[v]->w.red_host[kRES];
+        bn2[v] = ps[v]->w.red_host[kBN];
+        if ((s = cg_tail(*ps[v], o, rho[v], infos ? &infos[v] : nullptr, st)) != MH3D_OK) {
+            P0.err = ps[v]->err;
+            return s;
+        }
+    }
+    MH3D_CK(P0, cudaStreamSynchronize(st));
+    mh3d_status worst = MH3D_OK;
+    for (size_t v = 0; v < ps.size(); ++v) {
+        const mh3d_status sv = cg_report(*ps[v], res2[v], bn2[v], infos ? &infos[v] : nullptr);
+        if (sv != MH3D_OK && worst == MH3D_OK) {
+            worst = sv;
+            if (ps[v] != &P0) P0.err = "volume " + std::to_string(v) + ": " + ps[v]->err;
+        }
+    }
+    return worst;
 }
 
 // APG (Sec. 4.3): y^k = rho^k + (k-1)/(k+2)(rho^k - rho^{k-1});
@@ -628,6 +842,38 @@ mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* con
                                float* const* rho, mh3d_solve_info* infos, void* stream)
 {
     if (!plans || nvol < 0 || !d || !o || !rho) return MH3D_ERR_INVALID_ARG;
+    if (nvol == 0) return MH3D_OK;
+    std::vector<Plan*> ps(nvol);
+    for (int v = 0; v < nvol; ++v) {
+        if (!plans[v]) return MH3D_ERR_INVALID_ARG;
+        ps[v] = plans[v];
+    }
+    Plan& P0 = *ps[0];
+    P0.err.clear();
+    for (int v = 0; v < nvol; ++v) {
+        if (!d[v] || !rho[v]) {
+            P0.err = "mh3d_solve_batched: null pointer for volume " + std::to_string(v);
+            return MH3D_ERR_INVALID_ARG;
+        }
+        for (int u = 0; u < v; ++u)
+            if (ps[u] == ps[v]) {
+                P0.err = "mh3d_solve_batched: a plan appears twice (each volume needs its own plan)";
+                return MH3D_ERR_INVALID_ARG;
+            }
+        mh3d_status s = validate_opts(*ps[v], *o);
+        if (s != MH3D_OK) return s;
+    }
+    if (o->x0_dev) {
+        P0.err = "mh3d_solve_batched: x0_dev must be NULL (one warm start cannot serve several volumes)";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (o->solver == 0 && !graphs_disabled()) {
+        std::vector<const float2*> dv(nvol);
+        for (int v = 0; v < nvol; ++v) dv[v] = (const float2*)d[v];
+        return cg_solve_batched(ps, dv.data(), *o, rho, infos, st);
+    }
+    // APG, or graphs switched off: one volume after another
     mh3d_status worst = MH3D_OK;
     for (int v = 0; v < nvol; ++v) {
         mh3d_status s = mh3d_solve(plans[v], d[v], o, rho[v], infos ? &infos[v] : nullptr, stream);

@@ -26,6 +26,8 @@ int normal_part_count(const Plan& P, int mode);
 mh3d_status ensure_portrait(Plan& P);
 
 mh3d_status solve_alloc(Plan& P);
+// Drops every cached batch graph that holds this plan's buffers.
+void batch_forget(const Plan& P);
 void solve_free(Plan& P);
 cudaError_t solve_set_attributes();
 mh3d_status validate_opts(Plan& P, const mh3d_solve_opts& o);

@@ -272,6 +272,9 @@ def mh3d_solve_host(plan: Plan, d_host, opts: mh3d_solve_opts, rho_host, stream=
 
 
 def mh3d_solve_batched(plans: Sequence[Plan], ds, opts: mh3d_solve_opts, rhos, stream=None):
+    """Solves every volume (its own plan, portraits ds[i], image rhos[i]) in
+    one call: for CG, one CUDA graph with an independent branch per volume.
+    Returns one info dict per volume."""
     import torch
 
     lib = load()
@@ -286,9 +289,9 @@ def mh3d_solve_batched(plans: Sequence[Plan], ds, opts: mh3d_solve_opts, rhos, s
     infos = (mh3d_solve_info * n)()
     st = lib.mh3d_solve_batched(hp, n, dp, ctypes.byref(opts), rp, infos, c_void_p(_stream_ptr(stream)))
     if st not in (MH3D_OK, MH3D_ERR_NOT_CONVERGED):
-        raise MH3DError(st, "mh3d_solve_batched")
-    return [{"iters": infos[i].iters, "rel_res_true": infos[i].rel_res_true, "status": infos[i].status}
-            for i in range(n)]
+        _check(plans[0].handle if n else None, st)
+    return [{"iters": infos[i].iters, "rel_res_recurrence": infos[i].rel_res_recurrence,
+             "rel_res_true": infos[i].rel_res_true, "status": infos[i].status} for i in range(n)]
 
 
 def mh3d_forward_noalloc(n, rho, d, voxel_mm=(1.0, 1.0, 1.0), ds_factor: int = 1, ds_offset: int = 0,

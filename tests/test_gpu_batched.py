@@ -1,0 +1,166 @@
+"""Batched CG (mh3d_solve_batched): one CUDA graph with an independent branch
+per volume, volumes of different sizes.
+
+* Every volume of a batch must equal, bit for bit, the same volume solved
+  alone by mh3d_solve: the branches launch the same kernels with the same
+  launch shapes, and every reduction has a fixed order.
+* One volume is compared with the FP64 oracle's CG at a fixed iteration
+  count (rel. L2 <= 1e-4, as for single solves).
+* At the full size classes of the 64-volume workload (64^3, 96x96x64,
+  128x128x64, 192x192x96; K = 8, s = 2, Gaussian b, 25 dB), each volume's
+  true residual meets the stopping rule.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests._cases import gpu_plan, oracle_geom, params, rel_l2, sens_map
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SMALL = [
+    params((64, 64, 32), s=2, kmin=2, kmax=9),
+    params((32, 32, 32), s=1, kmin=2, kmax=5),
+    params((96, 96, 64), s=2, kmin=2, kmax=9),
+    params((64, 64, 32), s=2, kmin=2, kmax=9),
+    params((48, 32, 32), s=2, kmin=2, kmax=5),    # drive length 48: runtime-general X kernels
+]
+
+
+def _case(p, seed, snr_db=25.0):
+    """Oracle-made noisy portraits of a seeded phantom (small grids)."""
+    g = oracle_geom(p)
+    b = sens_map(p)
+    rho = W.phantom(p["n"], p["voxel"], seed, 12, 1)
+    clean = oracle.forward(g, rho, b)
+    sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (snr_db / 10))
+    d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, seed)
+    return g, b, d
+
+
+def _dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def _opts(**kw):
+    from paper_2503_13802_gb300 import make_opts
+
+    base = dict(lam=1e-3, lam_relative=True, rel_tol=1e-4, max_iter=400)
+    base.update(kw)
+    return make_opts(**base)
+
+
+def _small_batch(seed0=500):
+    plans, ds, cases = [], [], []
+    for i, p in enumerate(SMALL):
+        g, b, d = _case(p, seed0 + i)
+        plans.append(gpu_plan(p, b))
+        ds.append(_dev(d, torch.complex64))
+        cases.append((g, b, d))
+    return plans, ds, cases
+
+
+def _solve_each(plans, ds, opts):
+    from paper_2503_13802_gb300 import mh3d_solve
+
+    out = []
+    for pl, d in zip(plans, ds):
+        x = torch.empty(pl.shape, dtype=torch.float32, device="cuda")
+        info = mh3d_solve(pl, d, opts, x)
+        out.append((x.cpu().numpy(), info))
+    return out
+
+
+def _solve_batch(plans, ds, opts):
+    from paper_2503_13802_gb300 import mh3d_solve_batched
+
+    xs = [torch.empty(pl.shape, dtype=torch.float32, device="cuda") for pl in plans]
+    infos = mh3d_solve_batched(plans, ds, opts, xs)
+    return [x.cpu().numpy() for x in xs], infos
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_batched_equals_single_solves_bit_for_bit(variant):
+    plans, ds, _ = _small_batch()
+    opts = _opts(cg_variant=variant)
+    alone = _solve_each(plans, ds, opts)
+    xs, infos = _solve_batch(plans, ds, opts)
+    for v, ((xa, ia), xb, ib) in enumerate(zip(alone, xs, infos)):
+        assert ib["iters"] == ia["iters"], (v, ib, ia)
+        assert ib["status"] == ia["status"] == 0, (v, ib, ia)
+        assert np.array_equal(xa, xb), (v, float(np.abs(xa - xb).max()))
+        assert ib["rel_res_true"] == ia["rel_res_true"]
+        assert ib["rel_res_true"] <= 1.5e-4, (v, ib)
+
+
+def test_batched_graph_reuse_with_new_data():
+    """A second call with other portraits (other device pointers) reuses the
+    cached graph: the portraits are staged into the plans' own buffers."""
+    plans, ds, _ = _small_batch(600)
+    opts = _opts()
+    _solve_batch(plans, ds, opts)
+    ds2 = [torch.flip(d, dims=[1]).contiguous() for d in ds]
+    xs, infos = _solve_batch(plans, ds2, opts)
+    alone = _solve_each(plans, ds2, opts)
+    for (xa, ia), xb, ib in zip(alone, xs, infos):
+        assert ib["iters"] == ia["iters"]
+        assert np.array_equal(xa, xb)
+
+
+def test_batched_volume_matches_oracle_at_fixed_iterations():
+    plans, ds, cases = _small_batch(700)
+    opts = _opts(fixed_iters=1, max_iter=30)
+    xs, infos = _solve_batch(plans, ds, opts)
+    v = 1                                           # 32^3, K = 4, s = 1
+    g, b, d = cases[v]
+    xo, it, _ = oracle.cg(g, d, b, oracle.SolveOpts(lam=1e-3, lam_relative=True, rel_tol=0.0, max_iter=30))
+    assert infos[v]["iters"] == 30 and it == 30
+    assert rel_l2(xs[v], xo) <= 1e-4, rel_l2(xs[v], xo)
+
+
+def test_batched_rejects_warm_start_and_repeated_plans():
+    from paper_2503_13802_gb300 import MH3DError, make_opts, mh3d_solve_batched
+
+    plans, ds, _ = _small_batch(800)
+    xs = [torch.empty(pl.shape, dtype=torch.float32, device="cuda") for pl in plans]
+    with pytest.raises(MH3DError) as e:
+        mh3d_solve_batched([plans[0], plans[0]], [ds[0], ds[0]], _opts(), [xs[0], xs[0]])
+    assert "INVALID_ARG" in str(e.value)
+    x0 = torch.zeros(plans[0].shape, dtype=torch.float32, device="cuda")
+    with pytest.raises(MH3DError) as e:
+        mh3d_solve_batched(plans[:1], ds[:1], make_opts(lam=1e-3, lam_relative=True, x0=x0), xs[:1])
+    assert "INVALID_ARG" in str(e.value)
+
+
+def test_batched_full_size_classes_residual_property():
+    """Two volumes of each size class of the 64-volume workload, data made
+    by the GPU forward operator (the oracle cannot run these sizes whole):
+    every volume reaches rel. residual 1e-4 by its true residual, and one
+    of each class equals its single solve bit for bit."""
+    from paper_2503_13802_gb300 import Plan, mh3d_forward
+
+    wl = W.WORKLOADS["mh_128x128x64_k8_s2"]
+    plans, ds = [], []
+    for i, n in enumerate([c for c in W.BATCH_SIZE_CLASSES for _ in range(2)]):
+        rho = W.phantom(n, (1.0, 1.0, 1.0), 1000 + i, wl.n_blobs, wl.n_lines)
+        b = W.sensitivity(n, (1.0, 1.0, 1.0), kind="gaussian")
+        pl = Plan(n, ds_factor=2, k_min=2, k_max=9, sensitivity=b)
+        d = torch.empty(pl.portrait_shape, dtype=torch.complex64, device="cuda")
+        mh3d_forward(pl, _dev(rho, torch.float32), d)
+        sig2 = float(torch.sum(torch.abs(d.to(torch.complex128)) ** 2)) / (d.numel() * 10 ** (wl.snr_db / 10))
+        noise = _dev(W.unit_complex_noise(tuple(d.shape), 1000 + i), torch.complex64)
+        plans.append(pl)
+        ds.append((d + math.sqrt(sig2) * noise).contiguous())
+    opts = _opts(max_iter=wl.max_iter)
+    xs, infos = _solve_batch(plans, ds, opts)
+    for v, inf in enumerate(infos):
+        assert inf["status"] == 0, (v, inf)
+        assert inf["rel_res_true"] <= 1.5e-4, (v, inf)
+    alone = _solve_each(plans[::2], ds[::2], opts)
+    for (xa, ia), xb, ib in zip(alone, xs[::2], infos[::2]):
+        assert ia["iters"] == ib["iters"]
+        assert np.array_equal(xa, xb)
