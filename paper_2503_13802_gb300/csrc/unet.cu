@@ -1,0 +1,561 @@
+// The learned warm-start network behind the C ABI of include/mh3d_unet.h:
+// parameters (FP32 master copy, Adam state), bfloat16 weight matrices laid
+// out for the implicit-GEMM kernels, every stored activation of the last
+// forward pass, and the gradient buffers of the backward pass.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/mh3d_unet.h"
+#include "unet_kernels.cuh"
+
+namespace mh3d {
+namespace unet {
+
+namespace {
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+int tile_n(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : 64); }
+unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct Layer {
+    int cin = 0, cout = 0;
+    long long woff = 0, boff = 0;   // offsets of W [cout][27][cin] and b [cout] in theta
+    int Kf = 0, Nf = 0;             // forward matrix [Kf][Nf]
+    int Kb = 0, Nb = 0;             // input-gradient matrix [Kb][Nb]
+    __nv_bfloat16* Wf = nullptr;
+    __nv_bfloat16* Wb = nullptr;
+};
+
+}  // namespace
+
+struct Net {
+    int D = 0, H = 0, W = 0, c0 = 0, c1 = 0, c2 = 0;
+    long long V0 = 0, V1 = 0, V2 = 0;
+    long long nparam = 0;
+    int adam_t = 0;
+    Layer L[11];
+    std::vector<void*> allocs;
+    float *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
+    // forward activations (bfloat16, channels last) and the FP32 output
+    __nv_bfloat16 *e0a = nullptr, *e0 = nullptr, *p0 = nullptr, *e1a = nullptr, *e1 = nullptr, *p1 = nullptr;
+    __nv_bfloat16 *ba = nullptr, *b = nullptr, *u1 = nullptr, *d1 = nullptr, *u0 = nullptr, *d0 = nullptr;
+    float* out = nullptr;
+    const float* in = nullptr;   // the last forward's input (borrowed)
+    // gradients
+    __nv_bfloat16 *gout = nullptr, *gd0 = nullptr, *gs0 = nullptr, *gup = nullptr, *ge0 = nullptr, *ge0a = nullptr;
+    __nv_bfloat16 *gd1 = nullptr, *gs1 = nullptr, *gupb = nullptr, *ge1 = nullptr, *ge1a = nullptr, *gp0 = nullptr;
+    __nv_bfloat16 *gb = nullptr, *gba = nullptr, *gp1 = nullptr, *scratch = nullptr;
+    float *wpart = nullptr, *bpart = nullptr;
+    double* lpart = nullptr;
+    double* lhost = nullptr;
+    size_t wpart_n = 0, bpart_n = 0;
+    int lblocks = 0;
+    bool weights_ready = false;
+    std::string err;
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(Net& n, T** p, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        n.allocs.push_back(q);
+        *p = (T*)q;
+    }
+    return e;
+}
+
+void free_net(Net& n)
+{
+    for (void* p : n.allocs) cudaFree(p);
+    n.allocs.clear();
+    if (n.lhost) cudaFreeHost(n.lhost);
+    n.lhost = nullptr;
+}
+
+ConvSrc src_of(const __nv_bfloat16* a, int D, int H, int W, int C, const __nv_bfloat16* skip = nullptr, int up = 0)
+{
+    ConvSrc s;
+    s.a = a;
+    s.b = skip;
+    s.D = D;
+    s.H = H;
+    s.W = W;
+    s.C = C;
+    s.up = up;
+    return s;
+}
+
+template <class OutT>
+cudaError_t launch_conv(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, int N, const float* bias,
+                        int relu, OutT* out, cudaStream_t st)
+{
+    const long long V = (long long)s.D * s.H * s.W;
+    const int bn = tile_n(N);
+    dim3 grid(blocks_for(V, kBM), (unsigned)(Npad / bn));
+    if (bn == 16)
+        k_conv<16, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, out);
+    else if (bn == 32)
+        k_conv<32, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, out);
+    else
+        k_conv<64, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, out);
+    return cudaGetLastError();
+}
+
+size_t wpart_floats(long long V, int Kpad, int N) { return (size_t)blocks_for(V, kWChunk) * Kpad * N; }
+
+// gW [N][27 C] and gb [N] of a convolution with input s and output gradient
+// g ([V][N] bfloat16), through the partial buffers.
+cudaError_t launch_wgrad(const ConvSrc& s, const __nv_bfloat16* g, int N, float* wpart, float* bpart, float* gW,
+                         float* gbias, cudaStream_t st)
+{
+    const long long V = (long long)s.D * s.H * s.W;
+    const int Kpad = round_up(27 * s.C, kBK);
+    const unsigned chunks = blocks_for(V, kWChunk);
+    dim3 grid(blocks_for(Kpad, kBM), chunks);
+    const int bn = tile_n(N);
+    if (bn == 16)
+        k_conv_wgrad<16><<<grid, kThreads, 0, st>>>(s, g, N, Kpad, wpart);
+    else if (bn == 32)
+        k_conv_wgrad<32><<<grid, kThreads, 0, st>>>(s, g, N, Kpad, wpart);
+    else
+        k_conv_wgrad<64><<<grid, kThreads, 0, st>>>(s, g, N, Kpad, wpart);
+    const int Kvalid = 27 * s.C;
+    k_wgrad_reduce<<<blocks_for((long long)Kvalid * N, 256), 256, 0, st>>>(wpart, (int)chunks, Kpad, Kvalid, N, gW);
+    k_bias_part<<<chunks, 64, 0, st>>>(g, V, N, bpart);
+    k_bias_reduce<<<blocks_for(N, 64), 64, 0, st>>>(bpart, (int)chunks, N, gbias);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace unet
+}  // namespace mh3d
+
+namespace mh3d {
+namespace unet {
+namespace {
+
+#define UN_CK(n, call)                                                                            \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            (n).err = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
+            return e_ == cudaErrorMemoryAllocation ? MH3D_ERR_OOM : MH3D_ERR_CUDA;                \
+        }                                                                                         \
+    } while (0)
+
+mh3d_status prep_weights(Net& n, cudaStream_t st)
+{
+    for (Layer& l : n.L) {
+        k_prep_weights<<<blocks_for((long long)l.Kf * l.Nf, 256), 256, 0, st>>>(n.theta + l.woff, l.cin, l.cout,
+                                                                                l.Kf, l.Nf, 0, l.Wf);
+        k_prep_weights<<<blocks_for((long long)l.Kb * l.Nb, 256), 256, 0, st>>>(n.theta + l.woff, l.cin, l.cout,
+                                                                                l.Kb, l.Nb, 1, l.Wb);
+    }
+    UN_CK(n, cudaGetLastError());
+    n.weights_ready = true;
+    return MH3D_OK;
+}
+
+template <class OutT>
+cudaError_t fwd(const Net& n, int li, const ConvSrc& s, int relu, OutT* out, cudaStream_t st)
+{
+    const Layer& l = n.L[li];
+    return launch_conv(s, l.Wf, l.Kf, l.Nf, l.cout, n.theta + l.boff, relu, out, st);
+}
+
+mh3d_status forward_pass(Net& n, const float* in, cudaStream_t st)
+{
+    const int D = n.D, H = n.H, W = n.W, D1 = D / 2, H1 = H / 2, W1 = W / 2, D2 = D / 4, H2 = H / 4, W2 = W / 4;
+    ConvSrc s0;
+    s0.f32 = in;
+    s0.D = D;
+    s0.H = H;
+    s0.W = W;
+    s0.C = 1;
+    n.in = in;
+    UN_CK(n, fwd(n, 0, s0, 1, n.e0a, st));
+    UN_CK(n, fwd(n, 1, src_of(n.e0a, D, H, W, n.c0), 1, n.e0, st));
+    k_pool<<<blocks_for(n.V1 * n.c0, 256), 256, 0, st>>>(n.e0, D, H, W, n.c0, n.p0);
+    UN_CK(n, fwd(n, 2, src_of(n.p0, D1, H1, W1, n.c0), 1, n.e1a, st));
+    UN_CK(n, fwd(n, 3, src_of(n.e1a, D1, H1, W1, n.c1), 1, n.e1, st));
+    k_pool<<<blocks_for(n.V2 * n.c1, 256), 256, 0, st>>>(n.e1, D1, H1, W1, n.c1, n.p1);
+    UN_CK(n, fwd(n, 4, src_of(n.p1, D2, H2, W2, n.c1), 1, n.ba, st));
+    UN_CK(n, fwd(n, 5, src_of(n.ba, D2, H2, W2, n.c2), 1, n.b, st));
+    UN_CK(n, fwd(n, 6, src_of(n.b, D1, H1, W1, n.c2, nullptr, 1), 1, n.u1, st));
+    UN_CK(n, fwd(n, 7, src_of(n.u1, D1, H1, W1, n.c1, n.e1), 1, n.d1, st));
+    UN_CK(n, fwd(n, 8, src_of(n.d1, D, H, W, n.c1, nullptr, 1), 1, n.u0, st));
+    UN_CK(n, fwd(n, 9, src_of(n.u0, D, H, W, n.c0, n.e0), 1, n.d0, st));
+    UN_CK(n, fwd(n, 10, src_of(n.d0, D, H, W, n.c0), 0, n.out, st));
+    return MH3D_OK;
+}
+
+// Backward through layer li: g is the gradient w.r.t. the layer's output
+// (before the ReLU mask when y != null: masked into the scratch buffer);
+// parameter gradients go to n.grad; the input gradient, when gin != null,
+// is written at the convolution's resolution.
+mh3d_status back_layer(Net& n, int li, const ConvSrc& s, const __nv_bfloat16* g, const __nv_bfloat16* y,
+                       __nv_bfloat16* gin, cudaStream_t st)
+{
+    const Layer& l = n.L[li];
+    const long long V = (long long)s.D * s.H * s.W;
+    if (y) {
+        k_relu_grad<<<blocks_for(V * l.cout, 256), 256, 0, st>>>(n.scratch, g, y, V * l.cout);
+        g = n.scratch;
+    }
+    UN_CK(n, launch_wgrad(s, g, l.cout, n.wpart, n.bpart, n.grad + l.woff, n.grad + l.boff, st));
+    if (gin) {
+        ConvSrc sg = src_of(g, s.D, s.H, s.W, l.cout);
+        sg.flip = 1;
+        UN_CK(n, launch_conv(sg, l.Wb, l.Kb, l.Nb, l.cin, (const float*)nullptr, 0, gin, st));
+    }
+    return MH3D_OK;
+}
+
+mh3d_status backward_pass(Net& n, cudaStream_t st)
+{
+    const int D = n.D, H = n.H, W = n.W, D1 = D / 2, H1 = H / 2, W1 = W / 2, D2 = D / 4, H2 = H / 4, W2 = W / 4;
+    mh3d_status s;
+#define UN_BACK(...)                                             \
+    if ((s = back_layer(n, __VA_ARGS__, st)) != MH3D_OK) return s
+    UN_BACK(10, src_of(n.d0, D, H, W, n.c0), n.gout, nullptr, n.gd0);
+    UN_BACK(9, src_of(n.u0, D, H, W, n.c0, n.e0), n.gd0, n.d0, n.gs0);
+    UN_BACK(8, src_of(n.d1, D, H, W, n.c1, nullptr, 1), n.gs0, n.u0, n.gup);
+    k_up_grad<<<blocks_for(n.V1 * n.c1, 256), 256, 0, st>>>(n.gup, D1, H1, W1, n.c1, n.gd1);
+    UN_BACK(7, src_of(n.u1, D1, H1, W1, n.c1, n.e1), n.gd1, n.d1, n.gs1);
+    UN_BACK(6, src_of(n.b, D1, H1, W1, n.c2, nullptr, 1), n.gs1, n.u1, n.gupb);
+    k_up_grad<<<blocks_for(n.V2 * n.c2, 256), 256, 0, st>>>(n.gupb, D2, H2, W2, n.c2, n.gb);
+    UN_BACK(5, src_of(n.ba, D2, H2, W2, n.c2), n.gb, n.b, n.gba);
+    UN_BACK(4, src_of(n.p1, D2, H2, W2, n.c1), n.gba, n.ba, n.gp1);
+    k_pool_grad_add<<<blocks_for(n.V1 * n.c1, 256), 256, 0, st>>>(n.gs1, n.gp1, D1, H1, W1, n.c1, n.ge1);
+    UN_BACK(3, src_of(n.e1a, D1, H1, W1, n.c1), n.ge1, n.e1, n.ge1a);
+    UN_BACK(2, src_of(n.p0, D1, H1, W1, n.c0), n.ge1a, n.e1a, n.gp0);
+    k_pool_grad_add<<<blocks_for(n.V0 * n.c0, 256), 256, 0, st>>>(n.gs0, n.gp0, D, H, W, n.c0, n.ge0);
+    UN_BACK(1, src_of(n.e0a, D, H, W, n.c0), n.ge0, n.e0, n.ge0a);
+    ConvSrc s0;
+    s0.f32 = n.in;
+    s0.D = D;
+    s0.H = H;
+    s0.W = W;
+    s0.C = 1;
+    UN_BACK(0, s0, n.ge0a, n.e0a, nullptr);
+#undef UN_BACK
+    UN_CK(n, cudaGetLastError());
+    return MH3D_OK;
+}
+
+const int kLayerIO[11][2] = {{-1, 0}, {0, 0}, {0, 1}, {1, 1}, {1, 2}, {2, 2}, {2, 1}, {1, 1}, {1, 0}, {0, 0}, {0, -1}};
+
+}  // namespace
+}  // namespace unet
+}  // namespace mh3d
+
+using mh3d::unet::Net;
+struct mh3d_unet_s : public Net {};
+
+extern "C" {
+
+long long mh3d_unet_param_count(int c0, int c1, int c2)
+{
+    const int ch[3] = {c0, c1, c2};
+    long long n = 0;
+    for (const auto& io : mh3d::unet::kLayerIO) {
+        const int ci = io[0] < 0 ? 1 : ch[io[0]], co = io[1] < 0 ? 1 : ch[io[1]];
+        n += (long long)co * 27 * ci + co;
+    }
+    return n;
+}
+
+mh3d_status mh3d_unet_create(int nx, int ny, int nz, int c0, int c1, int c2, mh3d_unet* out)
+{
+    using namespace mh3d::unet;
+    if (!out) return MH3D_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nx < 4 || ny < 4 || nz < 4 || nx % 4 || ny % 4 || nz % 4 || c0 < 1 || c1 < 1 || c2 < 1 || c0 > 64 ||
+        c1 > 64 || c2 > 64)
+        return MH3D_ERR_INVALID_ARG;
+    mh3d_unet n = new mh3d_unet_s();
+    n->W = nx;
+    n->H = ny;
+    n->D = nz;
+    n->c0 = c0;
+    n->c1 = c1;
+    n->c2 = c2;
+    n->V0 = (long long)nx * ny * nz;
+    n->V1 = n->V0 / 8;
+    n->V2 = n->V1 / 8;
+    const int ch[3] = {c0, c1, c2};
+    long long off = 0;
+    size_t wp = 0, bp = 0;
+    const long long Vl[11] = {n->V0, n->V0, n->V1, n->V1, n->V2, n->V2, n->V1, n->V1, n->V0, n->V0, n->V0};
+    for (int i = 0; i < 11; ++i) {
+        Layer& l = n->L[i];
+        l.cin = kLayerIO[i][0] < 0 ? 1 : ch[kLayerIO[i][0]];
+        l.cout = kLayerIO[i][1] < 0 ? 1 : ch[kLayerIO[i][1]];
+        l.woff = off;
+        off += (long long)l.cout * 27 * l.cin;
+        l.boff = off;
+        off += l.cout;
+        l.Kf = round_up(27 * l.cin, kBK);
+        l.Nf = round_up(l.cout, tile_n(l.cout));
+        l.Kb = round_up(27 * l.cout, kBK);
+        l.Nb = round_up(l.cin, tile_n(l.cin));
+        wp = std::max(wp, wpart_floats(Vl[i], l.Kf, l.cout));
+        bp = std::max(bp, (size_t)blocks_for(Vl[i], kWChunk) * l.cout);
+    }
+    n->nparam = off;
+    n->wpart_n = wp;
+    n->bpart_n = bp;
+    n->lblocks = (int)blocks_for(n->V0, kThreads);
+    const int cm = std::max(c0, std::max(c1, c2));
+    bool ok = true;
+    auto A = [&](auto** p, size_t count) { ok = ok && dalloc(*n, p, count) == cudaSuccess; };
+    A(&n->theta, off);
+    A(&n->grad, off);
+    A(&n->am, off);
+    A(&n->av, off);
+    for (Layer& l : n->L) {
+        A(&l.Wf, (size_t)l.Kf * l.Nf);
+        A(&l.Wb, (size_t)l.Kb * l.Nb);
+    }
+    const size_t V0 = n->V0, V1 = n->V1, V2 = n->V2;
+    A(&n->e0a, V0 * c0);
+    A(&n->e0, V0 * c0);
+    A(&n->p0, V1 * c0);
+    A(&n->e1a, V1 * c1);
+    A(&n->e1, V1 * c1);
+    A(&n->p1, V2 * c1);
+    A(&n->ba, V2 * c2);
+    A(&n->b, V2 * c2);
+    A(&n->u1, V1 * c1);
+    A(&n->d1, V1 * c1);
+    A(&n->u0, V0 * c0);
+    A(&n->d0, V0 * c0);
+    A(&n->out, V0);
+    A(&n->gout, V0);
+    A(&n->gd0, V0 * c0);
+    A(&n->gs0, V0 * c0);
+    A(&n->gup, V0 * c1);
+    A(&n->ge0, V0 * c0);
+    A(&n->ge0a, V0 * c0);
+    A(&n->gd1, V1 * c1);
+    A(&n->gs1, V1 * c1);
+    A(&n->gupb, V1 * c2);
+    A(&n->ge1, V1 * c1);
+    A(&n->ge1a, V1 * c1);
+    A(&n->gp0, V1 * c0);
+    A(&n->gb, V2 * c2);
+    A(&n->gba, V2 * c2);
+    A(&n->gp1, V2 * c1);
+    A(&n->scratch, V0 * cm);
+    A(&n->wpart, wp);
+    A(&n->bpart, bp);
+    A(&n->lpart, (size_t)n->lblocks);
+    if (ok && cudaMallocHost(&n->lhost, sizeof(double) * n->lblocks) != cudaSuccess) {
+        n->lhost = nullptr;
+        ok = false;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        free_net(*n);
+        delete n;
+        return MH3D_ERR_OOM;
+    }
+    *out = n;
+    return MH3D_OK;
+}
+
+mh3d_status mh3d_unet_destroy(mh3d_unet n)
+{
+    if (!n) return MH3D_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    mh3d::unet::free_net(*n);
+    delete n;
+    return MH3D_OK;
+}
+
+mh3d_status mh3d_unet_set_params(mh3d_unet n, const float* theta, void* stream)
+{
+    if (!n || !theta) return MH3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    UN_CK(*n, cudaMemcpyAsync(n->theta, theta, sizeof(float) * n->nparam, cudaMemcpyDeviceToDevice, st));
+    UN_CK(*n, cudaMemsetAsync(n->am, 0, sizeof(float) * n->nparam, st));
+    UN_CK(*n, cudaMemsetAsync(n->av, 0, sizeof(float) * n->nparam, st));
+    n->adam_t = 0;
+    return mh3d::unet::prep_weights(*n, st);
+}
+
+mh3d_status mh3d_unet_get_params(mh3d_unet n, float* theta, void* stream)
+{
+    if (!n || !theta) return MH3D_ERR_INVALID_ARG;
+    UN_CK(*n, cudaMemcpyAsync(theta, n->theta, sizeof(float) * n->nparam, cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+    return MH3D_OK;
+}
+
+mh3d_status mh3d_unet_forward(mh3d_unet n, const float* in, float* out, void* stream)
+{
+    if (!n || !in || !out) return MH3D_ERR_INVALID_ARG;
+    if (!n->weights_ready) {
+        n->err = "parameters not set";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    mh3d_status s = mh3d::unet::forward_pass(*n, in, st);
+    if (s != MH3D_OK) return s;
+    UN_CK(*n, cudaMemcpyAsync(out, n->out, sizeof(float) * n->V0, cudaMemcpyDeviceToDevice, st));
+    return MH3D_OK;
+}
+
+mh3d_status mh3d_unet_loss_grad(mh3d_unet n, const float* in, const float* target, float* grad, double* loss,
+                                void* stream)
+{
+    using namespace mh3d::unet;
+    if (!n || !in || !target) return MH3D_ERR_INVALID_ARG;
+    if (!n->weights_ready) {
+        n->err = "parameters not set";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    mh3d_status s = forward_pass(*n, in, st);
+    if (s != MH3D_OK) return s;
+    k_mse<<<n->lblocks, kThreads, 0, st>>>(n->out, target, n->V0, n->gout, n->lpart);
+    if ((s = backward_pass(*n, st)) != MH3D_OK) return s;
+    if (grad) UN_CK(*n, cudaMemcpyAsync(grad, n->grad, sizeof(float) * n->nparam, cudaMemcpyDeviceToDevice, st));
+    if (loss) {
+        UN_CK(*n, cudaMemcpyAsync(n->lhost, n->lpart, sizeof(double) * n->lblocks, cudaMemcpyDeviceToHost, st));
+        UN_CK(*n, cudaStreamSynchronize(st));
+        double L = 0.0;
+        for (int i = 0; i < n->lblocks; ++i) L += n->lhost[i];
+        *loss = L;
+    }
+    return MH3D_OK;
+}
+
+mh3d_status mh3d_unet_adam_step(mh3d_unet n, float lr, void* stream)
+{
+    using namespace mh3d::unet;
+    if (!n || !(lr > 0.f)) return MH3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    n->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - (float)std::pow(0.9, n->adam_t), c2 = 1.f - (float)std::pow(0.999, n->adam_t);
+    k_adam<<<blocks_for(n->nparam, 256), 256, 0, st>>>(n->theta, n->am, n->av, n->grad, n->nparam, lr, b1, b2, 1e-8f,
+                                                       c1, c2);
+    UN_CK(*n, cudaGetLastError());
+    return prep_weights(*n, st);
+}
+
+const char* mh3d_unet_last_error(mh3d_unet n) { return n ? n->err.c_str() : ""; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Single-layer primitives (temporaries allocated per call)
+// ---------------------------------------------------------------------------
+namespace {
+
+using namespace mh3d::unet;
+
+bool desc_ok(const mh3d_unet_conv_desc* c)
+{
+    if (!c || c->nx < 1 || c->ny < 1 || c->nz < 1 || c->cin < 1 || c->cout < 1 || c->cin > 64 || c->cout > 64)
+        return false;
+    if (c->up && (c->nx % 2 || c->ny % 2 || c->nz % 2)) return false;
+    if (c->src_f32) return c->cin == 1 && !c->up && !c->skip_bf16;
+    return c->src_bf16 != nullptr;
+}
+
+ConvSrc src_from(const mh3d_unet_conv_desc* c)
+{
+    ConvSrc s;
+    s.a = (const __nv_bfloat16*)c->src_bf16;
+    s.b = (const __nv_bfloat16*)c->skip_bf16;
+    s.f32 = c->src_f32;
+    s.D = c->nz;
+    s.H = c->ny;
+    s.W = c->nx;
+    s.C = c->cin;
+    s.up = c->up;
+    return s;
+}
+
+// RAII device buffer for the primitives.
+struct Tmp {
+    void* p = nullptr;
+    explicit Tmp(size_t bytes) { if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr; }
+    ~Tmp() { if (p) cudaFree(p); }
+};
+
+mh3d_status finish(cudaStream_t st)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? MH3D_OK : MH3D_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+mh3d_status mh3d_unet_conv_forward(const mh3d_unet_conv_desc* c, const float* W, const float* b, int relu,
+                                   float* out, void* stream)
+{
+    if (!desc_ok(c) || !W || !out) return MH3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = round_up(27 * c->cin, kBK), Np = round_up(c->cout, tile_n(c->cout));
+    Tmp wt(sizeof(__nv_bfloat16) * K * Np);
+    if (!wt.p) return MH3D_ERR_OOM;
+    k_prep_weights<<<blocks_for((long long)K * Np, 256), 256, 0, st>>>(W, c->cin, c->cout, K, Np, 0,
+                                                                       (__nv_bfloat16*)wt.p);
+    if (launch_conv(src_from(c), (const __nv_bfloat16*)wt.p, K, Np, c->cout, b, relu, out, st) != cudaSuccess)
+        return MH3D_ERR_CUDA;
+    return finish(st);
+}
+
+mh3d_status mh3d_unet_conv_input_grad(const mh3d_unet_conv_desc* c, const void* g, const float* W, float* gin,
+                                      void* stream)
+{
+    if (!c || !g || !W || !gin || c->nx < 1 || c->ny < 1 || c->nz < 1 || c->cin < 1 || c->cout < 1 ||
+        c->cin > 64 || c->cout > 64)
+        return MH3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = round_up(27 * c->cout, kBK), Np = round_up(c->cin, tile_n(c->cin));
+    Tmp wt(sizeof(__nv_bfloat16) * K * Np);
+    if (!wt.p) return MH3D_ERR_OOM;
+    k_prep_weights<<<blocks_for((long long)K * Np, 256), 256, 0, st>>>(W, c->cin, c->cout, K, Np, 1,
+                                                                       (__nv_bfloat16*)wt.p);
+    ConvSrc s;
+    s.a = (const __nv_bfloat16*)g;
+    s.D = c->nz;
+    s.H = c->ny;
+    s.W = c->nx;
+    s.C = c->cout;
+    s.flip = 1;
+    if (launch_conv(s, (const __nv_bfloat16*)wt.p, K, Np, c->cin, (const float*)nullptr, 0, gin, st) != cudaSuccess)
+        return MH3D_ERR_CUDA;
+    return finish(st);
+}
+
+mh3d_status mh3d_unet_conv_weight_grad(const mh3d_unet_conv_desc* c, const void* g, float* gW, float* gb,
+                                       void* stream)
+{
+    if (!desc_ok(c) || !g || !gW || !gb) return MH3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long V = (long long)c->nx * c->ny * c->nz;
+    const int K = round_up(27 * c->cin, kBK);
+    Tmp wp(sizeof(float) * wpart_floats(V, K, c->cout));
+    Tmp bp(sizeof(float) * (size_t)blocks_for(V, kWChunk) * c->cout);
+    if (!wp.p || !bp.p) return MH3D_ERR_OOM;
+    if (launch_wgrad(src_from(c), (const __nv_bfloat16*)g, c->cout, (float*)wp.p, (float*)bp.p, gW, gb, st) !=
+        cudaSuccess)
+        return MH3D_ERR_CUDA;
+    return finish(st);
+}
+
+}  // extern "C"

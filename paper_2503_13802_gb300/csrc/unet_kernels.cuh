@@ -1,0 +1,490 @@
+// Kernels of the learned warm-start network: a small 3D U-Net with additive
+// skips whose 3x3x3 convolutions run as implicit GEMMs on the tensor cores
+// (bfloat16 operands, FP32 accumulation, mma.sync m16n8k16).
+//
+// Activations are channels-last bfloat16 volumes [D][H][W][C].  A
+// convolution "same" (zero padding) with weights W[co][tap][ci] (tap =
+// 9 (dz+1) + 3 (dy+1) + (dx+1)) is the GEMM
+//     out[v][co] = sum_k A[v][k] Wt[k][co],   k = tap * Cin + ci,
+// where A[v][k] = in[v + tap][ci] is gathered on the fly (never stored).
+// The gather also forms the two special inputs of the decoder: a nearest x2
+// upsampling of a half-resolution source, and the sum of two sources (the
+// additive skip), rounded to bfloat16 as a stored sum would be.  The same
+// kernel with negated taps and re-laid-out weights computes the gradient
+// with respect to the input; the weight gradient is the GEMM
+//     dW^T[k][co] = sum_v A[v][k] dY[v][co]
+// split over voxel chunks into FP32 partials that a second kernel adds in a
+// fixed order.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace mh3d {
+namespace unet {
+
+constexpr int kBM = 128;   // GEMM rows per CTA (voxels, or weight rows in wgrad)
+constexpr int kBK = 32;    // reduction depth per shared-memory stage
+constexpr int kThreads = 256;
+constexpr int kWChunk = 4096;   // voxels per CTA in the weight gradient
+
+// Source of a convolution's input (the GEMM's gathered operand).
+struct ConvSrc {
+    const __nv_bfloat16* a = nullptr;   // [.][.][.][C] bfloat16
+    const __nv_bfloat16* b = nullptr;   // second addend (skip), same shape as a, or null
+    const float* f32 = nullptr;         // single-channel FP32 source instead of a (network input)
+    int D = 0, H = 0, W = 0;            // resolution of the convolution (output)
+    int C = 0;                          // source channels
+    int up = 0;                         // 1: a is at half resolution (nearest x2 upsampling)
+    int flip = 0;                       // 1: taps negated (gradient w.r.t. the input)
+};
+
+__device__ __forceinline__ float bf2f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// A[v][k] for one voxel (z, y, x) and k = tap * C + ci; 0 outside the volume.
+__device__ __forceinline__ float gather1(const ConvSrc& s, int z, int y, int x, int k)
+{
+    const int tap = k / s.C, ci = k - tap * s.C;
+    int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    if (s.flip) {
+        dz = -dz;
+        dy = -dy;
+        dx = -dx;
+    }
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    if (zz < 0 || zz >= s.D || yy < 0 || yy >= s.H || xx < 0 || xx >= s.W) return 0.f;
+    if (s.f32) return s.f32[((size_t)zz * s.H + yy) * s.W + xx];
+    size_t off;
+    if (s.up)
+        off = (((size_t)(zz >> 1) * (s.H >> 1) + (yy >> 1)) * (s.W >> 1) + (xx >> 1)) * s.C + ci;
+    else
+        off = (((size_t)zz * s.H + yy) * s.W + xx) * s.C + ci;
+    float v = bf2f(s.a[off]);
+    if (s.b) v = bf2f(__float2bfloat16(v + bf2f(s.b[off])));
+    return v;
+}
+
+// Eight consecutive k (one tap, ci .. ci+7; needs C % 8 == 0) as 16 bytes.
+__device__ __forceinline__ uint4 gather8(const ConvSrc& s, int z, int y, int x, int k)
+{
+    const int tap = k / s.C, ci = k - tap * s.C;
+    int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    if (s.flip) {
+        dz = -dz;
+        dy = -dy;
+        dx = -dx;
+    }
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (zz < 0 || zz >= s.D || yy < 0 || yy >= s.H || xx < 0 || xx >= s.W) return r;
+    size_t off;
+    if (s.up)
+        off = (((size_t)(zz >> 1) * (s.H >> 1) + (yy >> 1)) * (s.W >> 1) + (xx >> 1)) * s.C + ci;
+    else
+        off = (((size_t)zz * s.H + yy) * s.W + xx) * s.C + ci;
+    r = *reinterpret_cast<const uint4*>(s.a + off);
+    if (s.b) {
+        const uint4 q = *reinterpret_cast<const uint4*>(s.b + off);
+        __nv_bfloat162* pr = reinterpret_cast<__nv_bfloat162*>(&r);
+        const __nv_bfloat162* pq = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 u = __bfloat1622float2(pr[i]), w = __bfloat1622float2(pq[i]);
+            pr[i] = __floats2bfloat162_rn(u.x + w.x, u.y + w.y);
+        }
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One kBK-deep stage: warp w owns GEMM rows [16 w, 16 w + 16) and every
+// column of the BN-wide tile.  sA is [kBM][kBK + 8] (row-major, m by k) or,
+// with A_KMAJOR, [kBK][kBM + 8] (k by m); sB is [kBK][BN + 8] (k by n).
+template <int BN, bool A_KMAJOR>
+__device__ __forceinline__ void mma_stage(const __nv_bfloat16* sA, const __nv_bfloat16* sB, float (&acc)[BN / 8][4],
+                                          int warp, int lane)
+{
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 16) {
+        uint32_t a[4];
+        if (A_KMAJOR) {
+            const int row = kk + (lane & 7) + (lane >> 4) * 8;
+            const int col = 16 * warp + ((lane >> 3) & 1) * 8;
+            ldsm_x4_t(a, sA + row * (kBM + 8) + col);
+        } else {
+            const int row = 16 * warp + (lane & 15);
+            const int col = kk + (lane >> 4) * 8;
+            ldsm_x4(a, sA + row * (kBK + 8) + col);
+        }
+#pragma unroll
+        for (int j = 0; j < BN / 16; ++j) {
+            uint32_t b[4];
+            const int row = kk + (lane & 7) + ((lane >> 3) & 1) * 8;
+            const int col = j * 16 + (lane >> 4) * 8;
+            ldsm_x4_t(b, sB + row * (BN + 8) + col);
+            mma_bf16(acc[2 * j], a, b[0], b[1]);
+            mma_bf16(acc[2 * j + 1], a, b[2], b[3]);
+        }
+    }
+}
+
+// Loads rows [k0, k0 + kBK) x columns [n0, n0 + BN) of a [Kpad][Npad] bfloat16
+// weight matrix (Kpad a multiple of kBK, Npad a multiple of BN).
+template <int BN>
+__device__ __forceinline__ void load_weights(__nv_bfloat16* sB, const __nv_bfloat16* Wt, int Npad, int k0, int n0)
+{
+    constexpr int CH = BN / 8;
+    for (int i = threadIdx.x; i < kBK * CH; i += kThreads) {
+        const int r = i / CH, c = i % CH;
+        *reinterpret_cast<uint4*>(sB + r * (BN + 8) + c * 8) =
+            *reinterpret_cast<const uint4*>(Wt + (size_t)(k0 + r) * Npad + n0 + c * 8);
+    }
+}
+
+// Convolution as GEMM: out[v][n] (n < N) = sum_k A[v][k] Wt[k][n] (+ bias,
+// ReLU).  Kvalid = 27 C; Wt is [Kpad][Npad] with zero rows k >= Kvalid.
+// OutT = __nv_bfloat16 (stored activations) or float.
+template <int BN, class OutT>
+__global__ void __launch_bounds__(kThreads) k_conv(ConvSrc src, const __nv_bfloat16* __restrict__ Wt, int Kpad,
+                                                   int Npad, int N, const float* __restrict__ bias, int relu,
+                                                   OutT* __restrict__ out)
+{
+    __shared__ __align__(16) __nv_bfloat16 sA[kBM * (kBK + 8)];
+    __shared__ __align__(16) __nv_bfloat16 sB[kBK * (BN + 8)];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long V = (long long)src.D * src.H * src.W;
+    const long long m0 = (long long)blockIdx.x * kBM;
+    const int n0 = blockIdx.y * BN;
+    const int Kvalid = 27 * src.C;
+    const bool vec = (src.C % 8) == 0 && !src.f32;
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int t = 0; t < BN / 8; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+    for (int k0 = 0; k0 < Kpad; k0 += kBK) {
+        if (vec) {
+            for (int i = threadIdx.x; i < kBM * (kBK / 8); i += kThreads) {
+                const int r = i / (kBK / 8), c = i % (kBK / 8);
+                const long long v = m0 + r;
+                const int k = k0 + c * 8;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (v < V && k < Kvalid) {
+                    const int x = (int)(v % src.W), y = (int)((v / src.W) % src.H), z = (int)(v / ((long long)src.W * src.H));
+                    val = gather8(src, z, y, x, k);
+                }
+                *reinterpret_cast<uint4*>(sA + r * (kBK + 8) + c * 8) = val;
+            }
+        } else {
+            for (int i = threadIdx.x; i < kBM * kBK; i += kThreads) {
+                const int r = i / kBK, c = i % kBK;
+                const long long v = m0 + r;
+                const int k = k0 + c;
+                float val = 0.f;
+                if (v < V && k < Kvalid) {
+                    const int x = (int)(v % src.W), y = (int)((v / src.W) % src.H), z = (int)(v / ((long long)src.W * src.H));
+                    val = gather1(src, z, y, x, k);
+                }
+                sA[r * (kBK + 8) + c] = __float2bfloat16(val);
+            }
+        }
+        load_weights<BN>(sB, Wt, Npad, k0, n0);
+        __syncthreads();
+        mma_stage<BN, false>(sA, sB, acc, warp, lane);
+        __syncthreads();
+    }
+    // epilogue: fragment (row lane/4 [+8], columns 2 (lane%4) + {0, 1})
+#pragma unroll
+    for (int t = 0; t < BN / 8; ++t) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long v = m0 + 16 * warp + (lane >> 2) + 8 * h;
+            if (v >= V) continue;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int n = n0 + t * 8 + 2 * (lane & 3) + e;
+                if (n >= N) continue;
+                float val = acc[t][2 * h + e] + (bias ? bias[n] : 0.f);
+                if (relu) val = fmaxf(val, 0.f);
+                if constexpr (sizeof(OutT) == 2)
+                    out[v * N + n] = __float2bfloat16(val);
+                else
+                    out[v * N + n] = val;
+            }
+        }
+    }
+}
+
+// Weight gradient, split over voxel chunks: part[chunk][k][n] =
+// sum over the chunk's voxels of A[v][k] dY[v][n] (k < Kpad, n < N, dY is
+// [V][N] bfloat16).  Grid (Kpad / kBM rounded up, chunks).
+template <int BN>
+__global__ void __launch_bounds__(kThreads) k_conv_wgrad(ConvSrc src, const __nv_bfloat16* __restrict__ dY, int N,
+                                                         int Kpad, float* __restrict__ part)
+{
+    __shared__ __align__(16) __nv_bfloat16 sA[kBK * (kBM + 8)];   // [v][k]
+    __shared__ __align__(16) __nv_bfloat16 sB[kBK * (BN + 8)];    // [v][n]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long V = (long long)src.D * src.H * src.W;
+    const int k0 = blockIdx.x * kBM;
+    const long long v0 = (long long)blockIdx.y * kWChunk;
+    const long long v1 = v0 + kWChunk < V ? v0 + kWChunk : V;
+    const int Kvalid = 27 * src.C;
+    const bool vec = (src.C % 8) == 0 && !src.f32;
+    const bool vecy = (N % 8) == 0;
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int t = 0; t < BN / 8; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+    for (long long vb = v0; vb < v1; vb += kBK) {
+        if (vec) {
+            for (int i = threadIdx.x; i < kBK * (kBM / 8); i += kThreads) {
+                const int r = i / (kBM / 8), c = i % (kBM / 8);
+                const long long v = vb + r;
+                const int k = k0 + c * 8;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (v < v1 && k < Kvalid) {
+                    const int x = (int)(v % src.W), y = (int)((v / src.W) % src.H), z = (int)(v / ((long long)src.W * src.H));
+                    val = gather8(src, z, y, x, k);
+                }
+                *reinterpret_cast<uint4*>(sA + r * (kBM + 8) + c * 8) = val;
+            }
+        } else {
+            for (int i = threadIdx.x; i < kBK * kBM; i += kThreads) {
+                const int r = i / kBM, c = i % kBM;
+                const long long v = vb + r;
+                const int k = k0 + c;
+                float val = 0.f;
+                if (v < v1 && k < Kvalid) {
+                    const int x = (int)(v % src.W), y = (int)((v / src.W) % src.H), z = (int)(v / ((long long)src.W * src.H));
+                    val = gather1(src, z, y, x, k);
+                }
+                sA[r * (kBM + 8) + c] = __float2bfloat16(val);
+            }
+        }
+        if (vecy) {
+            for (int i = threadIdx.x; i < kBK * (BN / 8); i += kThreads) {
+                const int r = i / (BN / 8), c = i % (BN / 8);
+                const long long v = vb + r;
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (v < v1 && c * 8 < N) val = *reinterpret_cast<const uint4*>(dY + v * N + c * 8);
+                *reinterpret_cast<uint4*>(sB + r * (BN + 8) + c * 8) = val;
+            }
+        } else {
+            for (int i = threadIdx.x; i < kBK * BN; i += kThreads) {
+                const int r = i / BN, c = i % BN;
+                const long long v = vb + r;
+                sB[r * (BN + 8) + c] = (v < v1 && c < N) ? dY[v * N + c] : __float2bfloat16(0.f);
+            }
+        }
+        __syncthreads();
+        mma_stage<BN, true>(sA, sB, acc, warp, lane);
+        __syncthreads();
+    }
+    float* P = part + (size_t)blockIdx.y * Kpad * N;
+#pragma unroll
+    for (int t = 0; t < BN / 8; ++t)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = k0 + 16 * warp + (lane >> 2) + 8 * h;
+            if (k >= Kpad) continue;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int n = t * 8 + 2 * (lane & 3) + e;
+                if (n < N) P[(size_t)k * N + n] = acc[t][2 * h + e];
+            }
+        }
+}
+
+// grad[n][k] (k < Kvalid: the parameter layout W[co][tap][ci]) = sum over
+// chunks, in chunk order, of part[chunk][k][n].
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int chunks, int Kpad, int Kvalid, int N,
+                               float* __restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Kvalid * N) return;
+    const int k = i / N, n = i % N;
+    float s = 0.f;
+    for (int c = 0; c < chunks; ++c) s += part[((size_t)c * Kpad + k) * N + n];
+    grad[(size_t)n * Kvalid + k] = s;
+}
+
+// Bias gradient: part[b][n] = sum over block b's voxels of dY[v][n]; then
+// grad[n] = sum over blocks in order.
+__global__ void k_bias_part(const __nv_bfloat16* __restrict__ dY, long long V, int N, float* __restrict__ part)
+{
+    const long long v0 = (long long)blockIdx.x * kWChunk;
+    const long long v1 = v0 + kWChunk < V ? v0 + kWChunk : V;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        float s = 0.f;
+        for (long long v = v0; v < v1; ++v) s += bf2f(dY[v * N + n]);
+        part[(size_t)blockIdx.x * N + n] = s;
+    }
+}
+
+__global__ void k_bias_reduce(const float* __restrict__ part, int blocks, int N, float* __restrict__ grad)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int b = 0; b < blocks; ++b) s += part[(size_t)b * N + n];
+    grad[n] = s;
+}
+
+// 2x2x2 mean pool of [D][H][W][C] (D, H, W even) into [D/2][H/2][W/2][C].
+__global__ void k_pool(const __nv_bfloat16* __restrict__ in, int D, int H, int W, int C,
+                       __nv_bfloat16* __restrict__ out)
+{
+    const long long n = (long long)(D / 2) * (H / 2) * (W / 2) * C;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    long long v = i / C;
+    const int x = (int)(v % (W / 2));
+    v /= (W / 2);
+    const int y = (int)(v % (H / 2));
+    const int z = (int)(v / (H / 2));
+    float s = 0.f;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 2; ++e)
+                s += bf2f(in[(((size_t)(2 * z + a) * H + (2 * y + b)) * W + (2 * x + e)) * C + c]);
+    out[i] = __float2bfloat16(s * 0.125f);
+}
+
+// g[v][c] = skip[v][c] + gp[parent(v)][c] / 8: gradient of a volume that
+// feeds both a 2x2x2 mean pool (gradient gp) and an additive skip (skip).
+__global__ void k_pool_grad_add(const __nv_bfloat16* __restrict__ skip, const __nv_bfloat16* __restrict__ gp, int D,
+                                int H, int W, int C, __nv_bfloat16* __restrict__ g)
+{
+    const long long n = (long long)D * H * W * C;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    long long v = i / C;
+    const int x = (int)(v % W);
+    v /= W;
+    const int y = (int)(v % H);
+    const int z = (int)(v / H);
+    const size_t pi = (((size_t)(z >> 1) * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1)) * C + c;
+    g[i] = __float2bfloat16(bf2f(skip[i]) + bf2f(gp[pi]) * 0.125f);
+}
+
+// Gradient of a nearest x2 upsampling: g[z][y][x][c] = sum of the 8 children
+// of fine-grid gradient gf ([2D][2H][2W][C]).
+__global__ void k_up_grad(const __nv_bfloat16* __restrict__ gf, int D, int H, int W, int C,
+                          __nv_bfloat16* __restrict__ g)
+{
+    const long long n = (long long)D * H * W * C;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    long long v = i / C;
+    const int x = (int)(v % W);
+    v /= W;
+    const int y = (int)(v % H);
+    const int z = (int)(v / H);
+    float s = 0.f;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 2; ++e)
+                s += bf2f(gf[(((size_t)(2 * z + a) * (2 * H) + (2 * y + b)) * (2 * W) + (2 * x + e)) * C + c]);
+    g[i] = __float2bfloat16(s);
+}
+
+// out = g where y > 0 else 0 (ReLU gradient; g itself is kept, a skip may
+// need it unmasked).
+__global__ void k_relu_grad(__nv_bfloat16* __restrict__ out, const __nv_bfloat16* __restrict__ g,
+                            const __nv_bfloat16* __restrict__ y, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = bf2f(y[i]) > 0.f ? g[i] : __float2bfloat16(0.f);
+}
+
+// Loss sum((out - t)^2) / (2 V) per block in FP64 partials; gradient
+// g = (out - t) / V as bfloat16.
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t, long long V,
+                      __nv_bfloat16* __restrict__ g, double* __restrict__ part)
+{
+    __shared__ double red[kThreads];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (i < V) {
+        const float d = out[i] - t[i];
+        g[i] = __float2bfloat16(d / (float)V);
+        s = (double)d * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0] / (2.0 * (double)V);
+}
+
+// Wt[k][n] (forward) = W[n][k] for k < 27 Cin, n < Cout; zero padding.
+// With transpose_io (gradient w.r.t. the input): k = tap * Cout + co,
+// n = ci, Wt[k][n] = W[co][tap][ci].
+__global__ void k_prep_weights(const float* __restrict__ W, int Cin, int Cout, int Kpad, int Npad, int transpose_io,
+                               __nv_bfloat16* __restrict__ Wt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Kpad * Npad) return;
+    const int k = i / Npad, n = i % Npad;
+    float v = 0.f;
+    if (!transpose_io) {
+        if (k < 27 * Cin && n < Cout) v = W[(size_t)n * 27 * Cin + k];
+    } else {
+        if (k < 27 * Cout && n < Cin) {
+            const int tap = k / Cout, co = k % Cout;
+            v = W[((size_t)co * 27 + tap) * Cin + n];
+        }
+    }
+    Wt[i] = __float2bfloat16(v);
+}
+
+// Adam (FP32 master weights): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+// theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+__global__ void k_adam(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps, float c1,
+                       float c2)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace unet
+}  // namespace mh3d

@@ -2,6 +2,7 @@
 a GPU, exports every function that include/mh3d.h declares, and the ctypes
 mirrors of the ABI structs have the C layout.  No compute call is made."""
 import ctypes
+import glob
 import os
 import re
 import shutil
@@ -11,11 +12,12 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "mh3d.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def _declared_functions():
-    text = open(HEADER).read()
-    pat = r"^(?:mh3d_status|const char\s*\*|unsigned long long)\s*(mh3d_\w+)\s*\("
+    text = "".join(open(h).read() for h in HEADERS)
+    pat = r"^(?:mh3d_status|const char\s*\*|unsigned long long|long long)\s*(mh3d_\w+)\s*\("
     return sorted(set(re.findall(pat, text, re.M)))
 
 
@@ -45,9 +47,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_binding_covers_every_declared_symbol():
-    from paper_2503_13802_gb300 import mh3d
+    from paper_2503_13802_gb300 import mh3d, unet
 
-    assert sorted(mh3d.EXPORTS) == _declared_functions()
+    assert sorted(mh3d.EXPORTS + unet.EXPORTS) == _declared_functions()
 
 
 def test_version_without_gpu(lib):
@@ -66,8 +68,9 @@ def test_struct_layouts_match_c(tmp_path):
         "mh3d_solve_opts": ["reg_kind", "lambda", "alpha", "shell", "solver", "rel_tol", "max_iter", "fixed_iters",
                             "x0_dev", "normal_mode", "apg_tau", "lambda_relative", "cg_variant"],
         "mh3d_solve_info": ["iters", "rel_res_recurrence", "rel_res_true", "history", "status"],
+        "mh3d_unet_conv_desc": ["nx", "ny", "nz", "cin", "cout", "src_bf16", "skip_bf16", "src_f32", "up"],
     }
-    src = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    src = ['#include <stdio.h>', '#include <stddef.h>'] + [f'#include "{h}"' for h in HEADERS] + ["int main(void){"]
     for st, fs in fields.items():
         src.append(f'printf("{st} %zu\\n", sizeof({st}));')
         for f in fs:
@@ -78,7 +81,10 @@ def test_struct_layouts_match_c(tmp_path):
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-std=c11", str(c), "-o", str(exe)])
     got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
-    py = {"mh3d_geometry": m.mh3d_geometry, "mh3d_solve_opts": m.mh3d_solve_opts, "mh3d_solve_info": m.mh3d_solve_info}
+    from paper_2503_13802_gb300 import unet as u
+
+    py = {"mh3d_geometry": m.mh3d_geometry, "mh3d_solve_opts": m.mh3d_solve_opts, "mh3d_solve_info": m.mh3d_solve_info,
+          "mh3d_unet_conv_desc": u.mh3d_unet_conv_desc}
     for st, cls in py.items():
         assert int(got[st]) == ctypes.sizeof(cls), st
         for f in fields[st]:

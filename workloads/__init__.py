@@ -136,6 +136,67 @@ def phantom(n: Sequence[int], voxel_mm: Sequence[float], seed: int, n_blobs: int
     return vol
 
 
+def _box(x, lo, hi):
+    """Index range of the sorted coordinates x that lie in [lo, hi]."""
+    return int(np.searchsorted(x, lo, "left")), int(np.searchsorted(x, hi, "right"))
+
+
+def learned_case(n: Sequence[int], voxel_mm: Sequence[float], seed: int, n_lines: int = 3):
+    """One volume of the learned-warm-start workload: (phantom, snr_db).
+
+    Blob count log-uniform in [5, 200], SNR U(15, 40) dB, then blobs as in
+    `phantom` (sigma ~ U(1.5, 4) mm, centres >= 3 sigma from the faces,
+    amplitude U(0.2, 1)) and `n_lines` line segments (FWHM U(1, 2) mm,
+    amplitude U(0.2, 1), endpoints inside a 3 mm margin).  Each blob and line
+    is evaluated only inside its box of +-4 sigma (where the Gaussian has
+    fallen below e^-8 of its peak) so that thousands of volumes stay cheap.
+    Draw order (stream = seed): count, SNR, then 5 uniforms per blob and 8
+    per line, as in `phantom`."""
+    st = Stream(seed)
+    u0 = st.uniform(2)
+    nb = int(round(math.exp(math.log(5.0) + (math.log(200.0) - math.log(5.0)) * u0[0])))
+    snr_db = 15.0 + 25.0 * u0[1]
+    xs = voxel_coords(n, voxel_mm)
+    half = [xs[a][-1] + 0.5 * voxel_mm[a] for a in range(3)]
+    vol = np.zeros((n[2], n[1], n[0]))
+    for _ in range(nb):
+        u = st.uniform(5)
+        sig = 1.5 + 2.5 * u[0]
+        c = []
+        for a in range(3):
+            lim = max(half[a] - 3.0 * sig, 0.0)
+            c.append(-lim + 2.0 * lim * u[1 + a])
+        amp = 0.2 + 0.8 * u[4]
+        r = [_box(xs[a], c[a] - 4.0 * sig, c[a] + 4.0 * sig) for a in range(3)]
+        gx, gy, gz = (_gauss1d(xs[a][r[a][0]:r[a][1]], c[a], sig) for a in range(3))
+        vol[r[2][0]:r[2][1], r[1][0]:r[1][1], r[0][0]:r[0][1]] += \
+            amp * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    for _ in range(n_lines):
+        u = st.uniform(8)
+        fwhm = 1.0 + u[0]
+        amp = 0.2 + 0.8 * u[1]
+        lim = [max(half[a] - 3.0, 0.0) for a in range(3)]
+        p0 = np.array([-lim[a] + 2 * lim[a] * u[2 + a] for a in range(3)])
+        p1 = np.array([-lim[a] + 2 * lim[a] * u[5 + a] for a in range(3)])
+        s = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+        r = [_box(xs[a], min(p0[a], p1[a]) - 4.0 * s, max(p0[a], p1[a]) + 4.0 * s) for a in range(3)]
+        Z, Yg, Xg = np.meshgrid(xs[2][r[2][0]:r[2][1]], xs[1][r[1][0]:r[1][1]], xs[0][r[0][0]:r[0][1]],
+                                indexing="ij")
+        dvec = p1 - p0
+        L2 = float(dvec @ dvec)
+        t = ((Xg - p0[0]) * dvec[0] + (Yg - p0[1]) * dvec[1] + (Z - p0[2]) * dvec[2])
+        t = np.clip(t / L2, 0.0, 1.0) if L2 > 0 else np.zeros_like(Xg)
+        dist2 = ((Xg - p0[0] - t * dvec[0]) ** 2 + (Yg - p0[1] - t * dvec[1]) ** 2
+                 + (Z - p0[2] - t * dvec[2]) ** 2)
+        vol[r[2][0]:r[2][1], r[1][0]:r[1][1], r[0][0]:r[0][1]] += amp * np.exp(-dist2 / (2.0 * s * s))
+    return vol, snr_db
+
+
+# Seeds of the learned-warm-start workload (128x128x64, K = 8, s = 2).
+LEARNED_TRAIN_SEEDS = tuple(range(10000, 12000))
+LEARNED_TEST_SEEDS = tuple(range(20000, 20200))
+
+
 def unit_complex_noise(shape: Tuple[int, ...], seed: int) -> np.ndarray:
     """Circular complex Gaussian noise with E|n|^2 = 1 (re, im ~ N(0, 1/2))."""
     st = Stream(int(seed) ^ NOISE_STREAM_XOR)
