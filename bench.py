@@ -51,6 +51,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", action="store_true",
                     help="the 64-volume batched workload (one JSON line of its own)")
+    ap.add_argument("--learned", action="store_true",
+                    help="train the warm-start network and compare warm and zero starts (own JSON line)")
+    ap.add_argument("--train-n", type=int, default=2000)
+    ap.add_argument("--test-n", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--channels", type=int, nargs=3, default=[16, 32, 64])
     ap.add_argument("--count-iters", action="store_true",
                     help="reference arm: run the oracle's CG to the tolerance once and print its iteration count")
     return ap.parse_args()
@@ -434,6 +442,101 @@ def bench_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_learned(args):
+    """Learned warm start on the 128x128x64, K = 8, s = 2 workload: phantoms
+    with 5-200 blobs (log-uniform) + 3 lines, SNR U(15, 40) dB, Gaussian b.
+    Trains the network on --train-n volumes (seeds 10000 + i; target: the
+    zero-start CG solution to 1e-4), then on the 200 test volumes (seeds
+    20000 + i) times zero-start CG against warm start (A^T d, network, CG
+    from x0 with the device-side fallback), each with CUDA events on the
+    stream.  Noise: torch's seeded CUDA generator (seed = volume seed)."""
+    import torch
+
+    from paper_2503_13802_gb300 import Plan, make_opts, mh3d_forward, mh3d_solve
+    from paper_2503_13802_gb300.warmstart import WarmStart
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = W.WORKLOADS[WORKLOAD]
+    b = W.sensitivity(wl.n, wl.voxel_mm, kind="gaussian")
+    plan = Plan(wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max, sensitivity=b)
+    opts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter)
+    stream = torch.cuda.current_stream()
+
+    def portraits(seed):
+        rho, snr = W.learned_case(wl.n, wl.voxel_mm, seed)
+        d = torch.empty(plan.portrait_shape, dtype=torch.complex64, device=dev)
+        mh3d_forward(plan, torch.as_tensor(rho, dtype=torch.float32, device=dev).contiguous(), d)
+        sig2 = float(torch.sum(torch.abs(d.to(torch.complex128)) ** 2)) / (d.numel() * 10 ** (snr / 10))
+        gen = torch.Generator(device=dev).manual_seed(int(seed))
+        noise = torch.randn(d.shape, generator=gen, dtype=torch.complex64, device=dev)
+        return (d + math.sqrt(sig2) * noise).contiguous()
+
+    ws = WarmStart(plan, channels=tuple(args.channels))
+    ws.init_params(args.seed)
+    t_gen = time.perf_counter()
+    rhs_list, tgt_list = [], []
+    x = torch.empty(plan.shape, dtype=torch.float32, device=dev)
+    for seed in W.LEARNED_TRAIN_SEEDS[:args.train_n]:
+        d = portraits(seed)
+        rhs_list.append(ws.back_projection(d, torch.empty_like(x)))
+        mh3d_solve(plan, d, opts, x)
+        tgt_list.append(x.clone())
+    t_gen = time.perf_counter() - t_gen
+    t_fit = time.perf_counter()
+    hist = ws.fit(rhs_list, tgt_list, epochs=args.epochs, lr_max=args.lr, lr_min=args.lr * 1e-2, seed=args.seed)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t_fit
+    del rhs_list, tgt_list
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    test = W.LEARNED_TEST_SEEDS[:args.test_n]
+    tests = [portraits(sd) for sd in test]
+    for d in tests[:3]:   # warm-up
+        mh3d_solve(plan, d, opts, x)
+        ws.solve(d, x, lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter)
+    n0, n1, t0, t1, tinf, fb, r0 = [], [], [], [], [], 0, []
+    for d in tests:
+        i0, s0 = timed(lambda: mh3d_solve(plan, d, opts, x))
+        i1, s1 = timed(lambda: ws.solve(d, x, lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol,
+                                        max_iter=wl.max_iter))
+        _, si = timed(lambda: ws.predict(d))
+        n0.append(i0["iters"])
+        n1.append(i1["iters"])
+        t0.append(s0)
+        t1.append(s1)
+        tinf.append(si)
+        fb += int(i1["x0_rejected"])
+        r0.append(i1["history"][0])
+    ratio = np.array(t0) / np.array(t1)
+    m, sd = float(ratio.mean()), float(ratio.std(ddof=1)) if len(ratio) > 1 else 0.0
+    half = 1.972 * sd / math.sqrt(len(ratio))
+    line = {
+        "metric": "reconstructions/sec to rel. residual 1e-4 with learned warm start", "value": len(t1) / sum(t1),
+        "unit": UNIT, "n_gpus": 1, "steps": len(t1), "warmup": 3, "ms_per_step": 1e3 * float(np.mean(t1)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 solve, bf16 network (f32 accumulation)", "data": "synthetic",
+        "config": {"workload": "learned_128x128x64_k8_s2", "train_volumes": args.train_n, "test_volumes": len(t1),
+                   "epochs": args.epochs, "channels": list(args.channels), "params": ws.net.nparam,
+                   "lr": args.lr, "seed": args.seed},
+        "zero_start": {"value": len(t0) / sum(t0), "mean_iters": float(np.mean(n0))},
+        "warm_start": {"mean_iters": float(np.mean(n1)), "inference_ms": 1e3 * float(np.mean(tinf)),
+                       "fallback_rate": fb / len(t1),
+                       "median_initial_rel_res": float(np.median(r0))},
+        "speedup": {"mean": m, "ci95": [m - half, m + half], "per": "volume, zero-start time / warm-start time"},
+        "train": {"loss_per_epoch": hist, "data_s": t_gen, "fit_s": t_fit},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def bench_reference(args):
     """The FP64 oracle as the reference arm, rank 0 only."""
     ws, rank, _ = dist_env()
@@ -487,6 +590,8 @@ def main():
         bench_reference(args)
     elif args.batched:
         bench_batched(args)
+    elif args.learned:
+        bench_learned(args)
     else:
         bench_mh3d(args)
 

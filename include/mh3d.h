@@ -104,6 +104,9 @@ typedef struct {
                                  /* 1 = classic CG (Hestenes-Stiefel), two reductions and a */
                                  /*     separate update pass.  Same iterates in exact       */
                                  /*     arithmetic.                                         */
+    int x0_fallback;             /* with x0_dev: if ||A^T d - N x0|| >= ||A^T d|| (the guess */
+                                 /* is no better than zero) the solve restarts from x = 0;   */
+                                 /* decided on the device, reported in info.x0_rejected      */
 } mh3d_solve_opts;
 
 typedef struct {
@@ -113,6 +116,7 @@ typedef struct {
     double* history;             /* host, caller-owned, >= max_iter+1 doubles, or NULL:     */
                                  /* receives ||r_k||/||A^T d|| for k = 0..iters             */
     int status;                  /* mh3d_status of the solve                                */
+    int x0_rejected;             /* 1 if x0_fallback replaced x0 by the zero start          */
 } mh3d_solve_info;
 
 /* Create a plan: validates the geometry, builds the PSF spectra in FP64 on

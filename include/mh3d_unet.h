@@ -65,6 +65,17 @@ mh3d_status mh3d_unet_forward(mh3d_unet net, const float* in, float* out, void* 
 mh3d_status mh3d_unet_loss_grad(mh3d_unet net, const float* in, const float* target, float* grad, double* loss,
                                 void* stream);
 
+/* Scale-free versions for back-projections of any magnitude.  With
+ * r = RMS(in) (computed on the device, r = 1 for a zero input):
+ *   forward_scaled:   out = (r gain) * network(in / r)
+ *   loss_grad_scaled: the loss and gradient of network(in / r) against
+ *                     target / (r gain)
+ * gain > 0 (the warm start uses 1 / ||A||_2^2).  No host synchronisation
+ * except for the loss, as above. */
+mh3d_status mh3d_unet_forward_scaled(mh3d_unet net, const float* in, float gain, float* out, void* stream);
+mh3d_status mh3d_unet_loss_grad_scaled(mh3d_unet net, const float* in, const float* target, float gain, float* grad,
+                                       double* loss, void* stream);
+
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on
  * the gradient of the last mh3d_unet_loss_grad. */
 mh3d_status mh3d_unet_adam_step(mh3d_unet net, float lr, void* stream);

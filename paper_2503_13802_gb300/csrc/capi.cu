@@ -1,5 +1,6 @@
 // Plan construction and operator entry points of the C ABI (include/mh3d.h).
 #include <algorithm>
+#include <cstdlib>
 #include <cstdint>
 #include <cmath>
 #include <cstdio>
@@ -45,6 +46,10 @@ static void choose_tiles(Plan& P)
     TileChoice t;
     const int nt = std::max(P.ny, P.nz);
     t.tpass_cols = 16;
+    if (const char* e = std::getenv("MH3D_TPASS_COLS")) {   // A/B override: 8 or 16
+        const int c = std::atoi(e);
+        if (c == 8 || c == 16) t.tpass_cols = c;
+    }
     while (t.tpass_cols > 4 && tpass_smem_bytes(nt, t.tpass_cols) > kSmemBudget) t.tpass_cols /= 2;
     t.xpass_pairs = 16;
     t.xpass_kgroup = std::min(4, P.K);

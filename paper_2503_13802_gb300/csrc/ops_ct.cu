@@ -35,21 +35,24 @@ struct XDesc {
     size_t smem = 0;
 };
 
+// P: column pairs (pencils) per CTA, 4 or 8 (tiles of 8 or 16 columns).
 template <class L>
-TDesc tdesc()
+TDesc tdesc(int P)
 {
-    return TDesc{k_tpass_ct<L, kPT>, tpass_ct_smem<L, kPT>()};
+    if (P == 4) return TDesc{k_tpass_ct<L, 4>, tpass_ct_smem<L, 4>()};
+    if (P == 8) return TDesc{k_tpass_ct<L, 8>, tpass_ct_smem<L, 8>()};
+    return TDesc{};
 }
 
-TDesc tpass_desc(int n)
+TDesc tpass_desc(int n, int P)
 {
     switch (n) {
-        case 32: return tdesc<RList<4, 8>>();
-        case 64: return tdesc<RList<8, 8>>();
-        case 96: return tdesc<RList<3, 4, 8>>();
-        case 128: return tdesc<RList<16, 8>>();
-        case 192: return tdesc<RList<3, 8, 8>>();
-        case 256: return tdesc<RList<16, 16>>();
+        case 32: return tdesc<RList<4, 8>>(P);
+        case 64: return tdesc<RList<8, 8>>(P);
+        case 96: return tdesc<RList<3, 4, 8>>(P);
+        case 128: return tdesc<RList<16, 8>>(P);
+        case 192: return tdesc<RList<3, 8, 8>>(P);
+        case 256: return tdesc<RList<16, 16>>(P);
         default: return TDesc{};
     }
 }
@@ -138,8 +141,8 @@ static bool encode_tile_map(CUtensorMap* m, const void* base, int nx, int ny, in
 // The bulk-copy T pass needs whole 16-float tiles and 16-byte aligned rows.
 bool ct_tpass_available(const TArgs& a)
 {
-    if (force_generic() || a.cols != 2 * kPT || !tpass_desc(a.n).fn) return false;
-    if (a.nx % (2 * kPT) != 0 || (a.es % 4) != 0 || (a.os % 4) != 0) return false;
+    if (force_generic() || (a.cols != 8 && a.cols != 16) || !tpass_desc(a.n, a.cols / 2).fn) return false;
+    if (a.nx % a.cols != 0 || (a.es % 4) != 0 || (a.os % 4) != 0) return false;
     const void* ptrs[] = {a.in, a.out, a.bin, a.bout, a.pvec, a.rvec, a.rvec_w, a.qdir, a.svec, a.xvec, a.qvec, a.pin};
     for (const void* p : ptrs)
         if (p && !al16(p)) return false;
@@ -156,11 +159,12 @@ cudaError_t ct_set_attributes(int optin)
     // would query the driver while the capture is open
     tensor_map_encoder();
     static const int tn[] = {32, 64, 96, 128, 192, 256};
-    for (int n : tn) {
-        const TDesc d = tpass_desc(n);
-        cudaError_t e = opt_in(d.fn, d.smem, optin);
-        if (e != cudaSuccess) return e;
-    }
+    for (int n : tn)
+        for (int P : {4, 8}) {
+            const TDesc d = tpass_desc(n, P);
+            cudaError_t e = opt_in(d.fn, d.smem, optin);
+            if (e != cudaSuccess) return e;
+        }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
         for (int w = 0; w < 3; ++w) {
@@ -176,14 +180,14 @@ cudaError_t run_tpass_ct(const TArgs& a0, int nouter, cudaStream_t st)
     TArgs a = a0;
     const int ny = (a.axis == 1) ? a.n : nouter, nz = (a.axis == 1) ? nouter : a.n;
     auto enc = [&](int slot, const void* ptr) {
-        return !ptr || encode_tile_map(&a.tm.m[slot], ptr, a.nx, ny, nz, a.axis, a.n, 2 * kPT);
+        return !ptr || encode_tile_map(&a.tm.m[slot], ptr, a.nx, ny, nz, a.axis, a.n, a.cols);
     };
     const bool ok = enc(kTmIn, a.in) && enc(kTmB, a.bin ? a.bin : a.bout) && enc(kTmR, a.rvec) &&
                     enc(kTmS, a.svec) && enc(kTmP, a.pvec) && enc(kTmQ, a.qdir) && enc(kTmX, a.xvec) &&
                     enc(kTmOut, a.epilogue ? a.qvec : a.out) && enc(kTmPin, a.pin);
     if (!ok) return cudaErrorInvalidValue;
-    const TDesc d = tpass_desc(a.n);
-    dim3 grid((a.nx + 2 * kPT - 1) / (2 * kPT), nouter);
+    const TDesc d = tpass_desc(a.n, a.cols / 2);
+    dim3 grid((a.nx + a.cols - 1) / a.cols, nouter);
     d.fn<<<grid, kT, d.smem, st>>>(a);
     return cudaGetLastError();
 }

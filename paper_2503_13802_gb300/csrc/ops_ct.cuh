@@ -25,7 +25,6 @@ namespace mh3d {
 namespace ct {
 
 constexpr int kP = 16;    // pencils per CTA of the X passes: 16 row pairs
-constexpr int kPT = 8;    // pencils per CTA of the T pass: 8 column pairs (16 floats)
 constexpr int kT = 128;   // threads per CTA
 constexpr int kKG = 2;    // harmonics per inverse batch in the X forward kernel
 

@@ -35,6 +35,9 @@ int update_blocks(long long N)
 enum { kPartRR = 0, kPartPQ = 1, kPartBN = 2, kPartRES = 3, kNPart = 4 };
 enum { kRR0 = 0, kRR1 = 1, kPQ = 2, kBN = 3, kRES = 4, kDL0 = 5, kDL1 = 6, kAL0 = 7, kAL1 = 8, kNScal = 9 };
 enum { kTkRR = 0, kTkPQ = 1, kTkBN = 2, kTkRES = 3, kNTk = 4 };
+// device flags: [0] loop decided, [1] iterations, [2] status, [3] timeout
+// status, [4] warm start rejected
+constexpr int kNFlags = 8;
 static double* part_slot(const Plan& P, int s) { return P.w.red + (size_t)s * P.w.red_cap; }
 static double* scal(const Plan& P, int s) { return P.w.red + (size_t)kNPart * P.w.red_cap + s; }
 static unsigned int* ticket(const Plan& P, int s)
@@ -75,6 +78,34 @@ __global__ void __launch_bounds__(256) k_cg_init(const float* __restrict__ rhs, 
     grid_sum_finalize(t, rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out, red);
     t = block_sum_f64(ab.value(), red);
     grid_sum_finalize(t, bn_part, blockIdx.x, gridDim.x, bn_tk, bn_out, red);
+}
+
+// Warm-start fallback: if r0^T r0 >= rhs^T rhs the initial iterate is no
+// better than zero, so restart from it: x = 0, r = rhs, the search state as
+// k_cg_init leaves it for a zero start, r^T r = rhs^T rhs.  Every block
+// reads the same two totals, so all take the same decision.
+__global__ void __launch_bounds__(256) k_cg_fallback(const float* __restrict__ rhs, float* __restrict__ r,
+                                                     float* __restrict__ p, float* __restrict__ qd,
+                                                     float* __restrict__ x, long long N, double* rr, const double* bn,
+                                                     int* flags)
+{
+    const double b = *bn;
+    if (!(*rr >= b)) return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float v = rhs[i];
+        r[i] = v;
+        x[i] = 0.f;
+        if (qd) {
+            p[i] = 0.f;
+            qd[i] = 0.f;
+        } else {
+            p[i] = v;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *rr = b;
+        flags[4] = 1;
+    }
 }
 
 // alpha = gamma / delta; x += alpha p; r -= alpha q; partials of r^T r.
@@ -204,10 +235,10 @@ mh3d_status solve_alloc(Plan& P)
     w.s = f + 7 * vec;
     w.red = (double*)(f + 8 * vec);
     if (cudaMemset(w.red, 0, red_bytes(cap)) != cudaSuccess) return MH3D_ERR_CUDA;
-    if (cudaMalloc(&w.flags, 4 * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
-    if (cudaMallocHost(&w.flags_host, 4 * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
+    if (cudaMalloc(&w.flags, kNFlags * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
+    if (cudaMallocHost(&w.flags_host, kNFlags * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
     if (cudaMallocHost(&w.red_host, std::max(cap, (size_t)16) * sizeof(double)) != cudaSuccess) return MH3D_ERR_OOM;
-    P.work_bytes = bytes + 4 * sizeof(int);
+    P.work_bytes = bytes + kNFlags * sizeof(int);
     return MH3D_OK;
 }
 
@@ -335,6 +366,7 @@ static unsigned long long opts_key(const mh3d_solve_opts& o)
     mix(&o.normal_mode, sizeof o.normal_mode);
     mix(&o.cg_variant, sizeof o.cg_variant);
     mix(&o.lambda_relative, sizeof o.lambda_relative);
+    mix(&o.x0_fallback, sizeof o.x0_fallback);
     return h;
 }
 
@@ -426,7 +458,7 @@ static mh3d_status run_cg_loop(Plan& P, const mh3d_solve_opts& o, cudaStream_t s
         MH3D_CK(P, enqueue_iteration(P, o, 0, c, st));
         MH3D_CK(P, enqueue_iteration(P, o, 1, c, st));
         if ((it / 2) % 4 == 3) {
-            MH3D_CK(P, cudaMemcpyAsync(P.w.flags_host, P.w.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            MH3D_CK(P, cudaMemcpyAsync(P.w.flags_host, P.w.flags, kNFlags * sizeof(int), cudaMemcpyDeviceToHost, st));
             MH3D_CK(P, cudaStreamSynchronize(st));
             if (P.w.flags_host[0]) break;
         }
@@ -451,13 +483,18 @@ static mh3d_status cg_prefix(Plan& P, const float2* d, const mh3d_solve_opts& o,
                                  st));
         qinit = w.q;
     }
-    MH3D_CK(P, cudaMemsetAsync(w.flags, 0, 4 * sizeof(int), st));
+    MH3D_CK(P, cudaMemsetAsync(w.flags, 0, kNFlags * sizeof(int), st));
     MH3D_CK(P, cudaMemsetAsync(ticket(P, 0), 0, kNTk * sizeof(unsigned int), st));
     const bool cgcg = (o.cg_variant == 0);
     k_cg_init<<<nU, 256, 0, st>>>(w.rhs, qinit, w.r, w.p, cgcg ? w.q : nullptr, w.x, o.x0_dev ? 0 : 1, P.N,
                                   part_slot(P, kPartRR), ticket(P, kTkRR), scal(P, kRR1), part_slot(P, kPartBN),
                                   ticket(P, kTkBN), scal(P, kBN));
     MH3D_CK(P, cudaGetLastError());
+    if (o.x0_dev && o.x0_fallback) {
+        k_cg_fallback<<<nU, 256, 0, st>>>(w.rhs, w.r, w.p, cgcg ? w.q : nullptr, w.x, P.N, scal(P, kRR1), scal(P, kBN),
+                                          w.flags);
+        MH3D_CK(P, cudaGetLastError());
+    }
     if (cgcg) {   // s0 = A r0 with delta0 = r0^T s0 and gamma0 = r0^T r0 (parity-1 slots)
         RedSink dots;
         dots.part = part_slot(P, kPartPQ);
@@ -477,7 +514,7 @@ static mh3d_status cg_suffix(Plan& P, const mh3d_solve_opts& o, cudaStream_t st)
 {
     SolveWork& w = P.w;
     const int nU = update_blocks(P.N);
-    MH3D_CK(P, cudaMemcpyAsync(w.flags_host, w.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    MH3D_CK(P, cudaMemcpyAsync(w.flags_host, w.flags, kNFlags * sizeof(int), cudaMemcpyDeviceToHost, st));
     MH3D_CK(P, launch_normal(P, o.normal_mode, reg_args(P, o), w.x, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr,
                              nullptr, st));
     k_diff_norm2<<<nU, 256, 0, st>>>(w.rhs, w.q, P.N, part_slot(P, kPartRES), ticket(P, kTkRES), scal(P, kRES));
@@ -524,6 +561,7 @@ static mh3d_status cg_report(Plan& P, double res2, double bn2, mh3d_solve_info* 
         info->rel_res_recurrence = w.red_host[kRecSlot];
         info->rel_res_true = bn2 > 0 ? std::sqrt(res2 / bn2) : 0.0;
         info->status = status;
+        info->x0_rejected = w.flags_host[4];
     }
     if (w.flags_host[3] == MH3D_ERR_TIMEOUT) {
         P.err = "a bounded device wait (bulk copy) timed out";

@@ -4,6 +4,7 @@
 // forward pass, and the gradient buffers of the backward pass.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -16,6 +17,13 @@ namespace unet {
 namespace {
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// MH3D_UNET_GATHER=1 forces the gather kernel for every convolution (A/B checks).
+bool tiles_disabled()
+{
+    const char* e = std::getenv("MH3D_UNET_GATHER");
+    return e && e[0] && e[0] != '0';
+}
 int tile_n(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : 64); }
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -42,7 +50,10 @@ struct Net {
     __nv_bfloat16 *e0a = nullptr, *e0 = nullptr, *p0 = nullptr, *e1a = nullptr, *e1 = nullptr, *p1 = nullptr;
     __nv_bfloat16 *ba = nullptr, *b = nullptr, *u1 = nullptr, *d1 = nullptr, *u0 = nullptr, *d0 = nullptr;
     float* out = nullptr;
-    const float* in = nullptr;   // the last forward's input (borrowed)
+    const float* in = nullptr;       // the last forward's input (borrowed)
+    const float* iscale = nullptr;   // the last forward's input scale (device scalar) or null
+    float* scales = nullptr;         // {1 / r, r gain, 1 / (r gain)} of the scaled calls
+    double* spart = nullptr;
     // gradients
     __nv_bfloat16 *gout = nullptr, *gd0 = nullptr, *gs0 = nullptr, *gup = nullptr, *ge0 = nullptr, *ge0a = nullptr;
     __nv_bfloat16 *gd1 = nullptr, *gs1 = nullptr, *gupb = nullptr, *ge1 = nullptr, *ge1a = nullptr, *gp0 = nullptr;
@@ -91,19 +102,98 @@ ConvSrc src_of(const __nv_bfloat16* a, int D, int H, int W, int C, const __nv_bf
     return s;
 }
 
+int num_sms()
+{
+    static int v = -1;
+    if (v < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    }
+    return v;
+}
+
+int smem_optin()
+{
+    static int v = -1;
+    if (v < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 48 * 1024;
+    }
+    return v;
+}
+
+// The halo-tiled kernel when its shared memory fits; false otherwise.
+template <int C, int BN, class OutT>
+bool tile_conv(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, int N, const float* bias, int relu,
+               const float* oscale, OutT* out, cudaStream_t st, cudaError_t* err)
+{
+    const size_t smem = tile_smem<C, BN>(Kpad);
+    if (smem > (size_t)smem_optin()) return false;
+    static bool attr = false;
+    if (!attr && smem > 48 * 1024) {
+        if ((*err = cudaFuncSetAttribute(k_conv_tile<C, BN, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_optin())) != cudaSuccess)
+            return true;
+        attr = true;
+    }
+    // persistent grid: resident CTAs per SM (cached per shared-memory size) x SMs
+    static size_t occ_smem = 0;
+    static int occ = 0;
+    if (occ_smem != smem) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_tile<C, BN, OutT>, kThreads, smem) !=
+            cudaSuccess)
+            occ = 1;
+        occ = std::max(occ, 1);
+        occ_smem = smem;
+    }
+    const int tiles = ((s.W + kTX - 1) / kTX) * ((s.H + kTY - 1) / kTY) * ((s.D + kTZ - 1) / kTZ);
+    const int grid = std::min(tiles, num_sms() * occ);
+    k_conv_tile<C, BN, OutT><<<dim3((unsigned)grid, (unsigned)(Npad / BN)), kThreads, smem, st>>>(
+        s, Wt, Kpad, Npad, N, bias, relu, oscale, out, tiles);
+    *err = cudaGetLastError();
+    return true;
+}
+
+template <int C, class OutT>
+bool tile_conv_n(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, int N, const float* bias, int relu,
+                 const float* oscale, OutT* out, cudaStream_t st, cudaError_t* err)
+{
+    const int bn = tile_n(N);
+    if (bn == 16) return tile_conv<C, 16>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, err);
+    if (bn == 32) return tile_conv<C, 32>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, err);
+    return tile_conv<C, 64>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, err);
+}
+
 template <class OutT>
 cudaError_t launch_conv(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, int N, const float* bias,
-                        int relu, OutT* out, cudaStream_t st)
+                        int relu, OutT* out, cudaStream_t st, const float* oscale = nullptr)
 {
+    cudaError_t e = cudaSuccess;
+    bool done = false;
+    if (!tiles_disabled()) {
+        if (s.C == 1)
+            done = tile_conv_n<1>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, &e);
+        else if (s.C == 8 && !s.f32)
+            done = tile_conv_n<8>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, &e);
+        else if (s.C == 16 && !s.f32)
+            done = tile_conv_n<16>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, &e);
+        else if (s.C == 32 && !s.f32)
+            done = tile_conv_n<32>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, &e);
+        else if (s.C == 64 && !s.f32)
+            done = tile_conv_n<64>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, &e);
+    }
+    if (done) return e;
     const long long V = (long long)s.D * s.H * s.W;
     const int bn = tile_n(N);
     dim3 grid(blocks_for(V, kBM), (unsigned)(Npad / bn));
     if (bn == 16)
-        k_conv<16, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, out);
+        k_conv<16, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out);
     else if (bn == 32)
-        k_conv<32, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, out);
+        k_conv<32, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out);
     else
-        k_conv<64, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, out);
+        k_conv<64, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out);
     return cudaGetLastError();
 }
 
@@ -127,7 +217,7 @@ cudaError_t launch_wgrad(const ConvSrc& s, const __nv_bfloat16* g, int N, float*
         k_conv_wgrad<64><<<grid, kThreads, 0, st>>>(s, g, N, Kpad, wpart);
     const int Kvalid = 27 * s.C;
     k_wgrad_reduce<<<blocks_for((long long)Kvalid * N, 256), 256, 0, st>>>(wpart, (int)chunks, Kpad, Kvalid, N, gW);
-    k_bias_part<<<chunks, 64, 0, st>>>(g, V, N, bpart);
+    k_bias_part<<<chunks, kThreads, 0, st>>>(g, V, N, bpart);
     k_bias_reduce<<<blocks_for(N, 64), 64, 0, st>>>(bpart, (int)chunks, N, gbias);
     return cudaGetLastError();
 }
@@ -163,13 +253,17 @@ mh3d_status prep_weights(Net& n, cudaStream_t st)
 }
 
 template <class OutT>
-cudaError_t fwd(const Net& n, int li, const ConvSrc& s, int relu, OutT* out, cudaStream_t st)
+cudaError_t fwd(const Net& n, int li, const ConvSrc& s, int relu, OutT* out, cudaStream_t st,
+                const float* oscale = nullptr)
 {
     const Layer& l = n.L[li];
-    return launch_conv(s, l.Wf, l.Kf, l.Nf, l.cout, n.theta + l.boff, relu, out, st);
+    return launch_conv(s, l.Wf, l.Kf, l.Nf, l.cout, n.theta + l.boff, relu, out, st, oscale);
 }
 
-mh3d_status forward_pass(Net& n, const float* in, cudaStream_t st)
+// iscale / oscale: device scalars multiplying the input and the output
+// (null: 1).
+mh3d_status forward_pass(Net& n, const float* in, cudaStream_t st, const float* iscale = nullptr,
+                         const float* oscale = nullptr)
 {
     const int D = n.D, H = n.H, W = n.W, D1 = D / 2, H1 = H / 2, W1 = W / 2, D2 = D / 4, H2 = H / 4, W2 = W / 4;
     ConvSrc s0;
@@ -178,7 +272,9 @@ mh3d_status forward_pass(Net& n, const float* in, cudaStream_t st)
     s0.H = H;
     s0.W = W;
     s0.C = 1;
+    s0.f32_scale = iscale;
     n.in = in;
+    n.iscale = iscale;
     UN_CK(n, fwd(n, 0, s0, 1, n.e0a, st));
     UN_CK(n, fwd(n, 1, src_of(n.e0a, D, H, W, n.c0), 1, n.e0, st));
     k_pool<<<blocks_for(n.V1 * n.c0, 256), 256, 0, st>>>(n.e0, D, H, W, n.c0, n.p0);
@@ -191,7 +287,7 @@ mh3d_status forward_pass(Net& n, const float* in, cudaStream_t st)
     UN_CK(n, fwd(n, 7, src_of(n.u1, D1, H1, W1, n.c1, n.e1), 1, n.d1, st));
     UN_CK(n, fwd(n, 8, src_of(n.d1, D, H, W, n.c1, nullptr, 1), 1, n.u0, st));
     UN_CK(n, fwd(n, 9, src_of(n.u0, D, H, W, n.c0, n.e0), 1, n.d0, st));
-    UN_CK(n, fwd(n, 10, src_of(n.d0, D, H, W, n.c0), 0, n.out, st));
+    UN_CK(n, fwd(n, 10, src_of(n.d0, D, H, W, n.c0), 0, n.out, st, oscale));
     return MH3D_OK;
 }
 
@@ -239,6 +335,7 @@ mh3d_status backward_pass(Net& n, cudaStream_t st)
     UN_BACK(1, src_of(n.e0a, D, H, W, n.c0), n.ge0, n.e0, n.ge0a);
     ConvSrc s0;
     s0.f32 = n.in;
+    s0.f32_scale = n.iscale;
     s0.D = D;
     s0.H = H;
     s0.W = W;
@@ -248,6 +345,8 @@ mh3d_status backward_pass(Net& n, cudaStream_t st)
     UN_CK(n, cudaGetLastError());
     return MH3D_OK;
 }
+
+constexpr int kScaleBlocks = 304;   // partial sums of the RMS (2 per SM)
 
 const int kLayerIO[11][2] = {{-1, 0}, {0, 0}, {0, 1}, {1, 1}, {1, 2}, {2, 2}, {2, 1}, {1, 1}, {1, 0}, {0, 0}, {0, -1}};
 
@@ -356,6 +455,8 @@ mh3d_status mh3d_unet_create(int nx, int ny, int nz, int c0, int c1, int c2, mh3
     A(&n->wpart, wp);
     A(&n->bpart, bp);
     A(&n->lpart, (size_t)n->lblocks);
+    A(&n->spart, (size_t)kScaleBlocks);
+    A(&n->scales, 4);
     if (ok && cudaMallocHost(&n->lhost, sizeof(double) * n->lblocks) != cudaSuccess) {
         n->lhost = nullptr;
         ok = false;
@@ -412,19 +513,13 @@ mh3d_status mh3d_unet_forward(mh3d_unet n, const float* in, float* out, void* st
     return MH3D_OK;
 }
 
-mh3d_status mh3d_unet_loss_grad(mh3d_unet n, const float* in, const float* target, float* grad, double* loss,
-                                void* stream)
+static mh3d_status loss_grad_impl(mh3d_unet n, const float* in, const float* target, float* grad, double* loss,
+                                  const float* iscale, const float* tscale, cudaStream_t st)
 {
     using namespace mh3d::unet;
-    if (!n || !in || !target) return MH3D_ERR_INVALID_ARG;
-    if (!n->weights_ready) {
-        n->err = "parameters not set";
-        return MH3D_ERR_INVALID_ARG;
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    mh3d_status s = forward_pass(*n, in, st);
+    mh3d_status s = forward_pass(*n, in, st, iscale, nullptr);
     if (s != MH3D_OK) return s;
-    k_mse<<<n->lblocks, kThreads, 0, st>>>(n->out, target, n->V0, n->gout, n->lpart);
+    k_mse<<<n->lblocks, kThreads, 0, st>>>(n->out, target, tscale, n->V0, n->gout, n->lpart);
     if ((s = backward_pass(*n, st)) != MH3D_OK) return s;
     if (grad) UN_CK(*n, cudaMemcpyAsync(grad, n->grad, sizeof(float) * n->nparam, cudaMemcpyDeviceToDevice, st));
     if (loss) {
@@ -435,6 +530,50 @@ mh3d_status mh3d_unet_loss_grad(mh3d_unet n, const float* in, const float* targe
         *loss = L;
     }
     return MH3D_OK;
+}
+
+static bool ready(mh3d_unet n)
+{
+    if (n->weights_ready) return true;
+    n->err = "parameters not set";
+    return false;
+}
+
+static void launch_scales(mh3d_unet n, const float* in, float gain, cudaStream_t st)
+{
+    using namespace mh3d::unet;
+    k_sumsq_part<<<kScaleBlocks, kThreads, 0, st>>>(in, n->V0, n->spart);
+    k_scales<<<1, 32, 0, st>>>(n->spart, kScaleBlocks, n->V0, gain, n->scales);
+}
+
+mh3d_status mh3d_unet_loss_grad(mh3d_unet n, const float* in, const float* target, float* grad, double* loss,
+                                void* stream)
+{
+    if (!n || !in || !target) return MH3D_ERR_INVALID_ARG;
+    if (!ready(n)) return MH3D_ERR_INVALID_ARG;
+    return loss_grad_impl(n, in, target, grad, loss, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+mh3d_status mh3d_unet_forward_scaled(mh3d_unet n, const float* in, float gain, float* out, void* stream)
+{
+    if (!n || !in || !out || !(gain > 0.f)) return MH3D_ERR_INVALID_ARG;
+    if (!ready(n)) return MH3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_scales(n, in, gain, st);
+    mh3d_status s = mh3d::unet::forward_pass(*n, in, st, n->scales, n->scales + 1);
+    if (s != MH3D_OK) return s;
+    UN_CK(*n, cudaMemcpyAsync(out, n->out, sizeof(float) * n->V0, cudaMemcpyDeviceToDevice, st));
+    return MH3D_OK;
+}
+
+mh3d_status mh3d_unet_loss_grad_scaled(mh3d_unet n, const float* in, const float* target, float gain, float* grad,
+                                       double* loss, void* stream)
+{
+    if (!n || !in || !target || !(gain > 0.f)) return MH3D_ERR_INVALID_ARG;
+    if (!ready(n)) return MH3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_scales(n, in, gain, st);
+    return loss_grad_impl(n, in, target, grad, loss, n->scales, n->scales + 2, st);
 }
 
 mh3d_status mh3d_unet_adam_step(mh3d_unet n, float lr, void* stream)

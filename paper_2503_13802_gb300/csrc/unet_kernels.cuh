@@ -35,6 +35,7 @@ struct ConvSrc {
     const __nv_bfloat16* a = nullptr;   // [.][.][.][C] bfloat16
     const __nv_bfloat16* b = nullptr;   // second addend (skip), same shape as a, or null
     const float* f32 = nullptr;         // single-channel FP32 source instead of a (network input)
+    const float* f32_scale = nullptr;   // device scalar multiplying the FP32 source (null: 1)
     int D = 0, H = 0, W = 0;            // resolution of the convolution (output)
     int C = 0;                          // source channels
     int up = 0;                         // 1: a is at half resolution (nearest x2 upsampling)
@@ -55,7 +56,7 @@ __device__ __forceinline__ float gather1(const ConvSrc& s, int z, int y, int x, 
     }
     const int zz = z + dz, yy = y + dy, xx = x + dx;
     if (zz < 0 || zz >= s.D || yy < 0 || yy >= s.H || xx < 0 || xx >= s.W) return 0.f;
-    if (s.f32) return s.f32[((size_t)zz * s.H + yy) * s.W + xx];
+    if (s.f32) return s.f32[((size_t)zz * s.H + yy) * s.W + xx] * (s.f32_scale ? *s.f32_scale : 1.f);
     size_t off;
     if (s.up)
         off = (((size_t)(zz >> 1) * (s.H >> 1) + (yy >> 1)) * (s.W >> 1) + (xx >> 1)) * s.C + ci;
@@ -171,12 +172,13 @@ __device__ __forceinline__ void load_weights(__nv_bfloat16* sB, const __nv_bfloa
 }
 
 // Convolution as GEMM: out[v][n] (n < N) = sum_k A[v][k] Wt[k][n] (+ bias,
-// ReLU).  Kvalid = 27 C; Wt is [Kpad][Npad] with zero rows k >= Kvalid.
-// OutT = __nv_bfloat16 (stored activations) or float.
+// times the device scalar *oscale when given, ReLU).  Kvalid = 27 C; Wt is
+// [Kpad][Npad] with zero rows k >= Kvalid.  OutT = __nv_bfloat16 (stored
+// activations) or float.
 template <int BN, class OutT>
 __global__ void __launch_bounds__(kThreads) k_conv(ConvSrc src, const __nv_bfloat16* __restrict__ Wt, int Kpad,
                                                    int Npad, int N, const float* __restrict__ bias, int relu,
-                                                   OutT* __restrict__ out)
+                                                   const float* __restrict__ oscale, OutT* __restrict__ out)
 {
     __shared__ __align__(16) __nv_bfloat16 sA[kBM * (kBK + 8)];
     __shared__ __align__(16) __nv_bfloat16 sB[kBK * (BN + 8)];
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvSrc src, const __nv_bfloa
         __syncthreads();
     }
     // epilogue: fragment (row lane/4 [+8], columns 2 (lane%4) + {0, 1})
+    const float osc = oscale ? *oscale : 1.f;
 #pragma unroll
     for (int t = 0; t < BN / 8; ++t) {
 #pragma unroll
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvSrc src, const __nv_bfloa
             for (int e = 0; e < 2; ++e) {
                 const int n = n0 + t * 8 + 2 * (lane & 3) + e;
                 if (n >= N) continue;
-                float val = acc[t][2 * h + e] + (bias ? bias[n] : 0.f);
+                float val = (acc[t][2 * h + e] + (bias ? bias[n] : 0.f)) * osc;
                 if (relu) val = fmaxf(val, 0.f);
                 if constexpr (sizeof(OutT) == 2)
                     out[v * N + n] = __float2bfloat16(val);
@@ -239,6 +242,233 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvSrc src, const __nv_bfloa
                     out[v * N + n] = val;
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled convolution: one CTA per 8 x 4 x 4 output block.  The block's input
+// halo (10 x 6 x 6 voxels, all C channels) and the whole weight matrix are
+// staged in shared memory once; the GEMM operand for tap t is then the halo
+// shifted by t, read by ldmatrix with one row address per lane, so each
+// input voxel leaves global memory about 2.8 times per block instead of 27.
+// Halo voxels are padded to C + 8 elements (16 bytes) so that the eight
+// rows an ldmatrix reads fall in distinct banks.  C = 1 (the network input,
+// or a one-channel gradient) builds the 128 x 32 operand explicitly instead.
+constexpr int kTX = 8, kTY = 4, kTZ = 4;
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2, kHV = kHX * kHY * kHZ;
+
+template <int C>
+__host__ __device__ constexpr int halo_stride() { return C == 1 ? 1 : C + 8; }
+
+// Shared-memory bytes of k_conv_tile<C, BN> for a weight matrix of Kpad rows
+// (weights, two halo buffers, a zero row, and for C == 1 the explicit
+// operand tile).
+template <int C, int BN>
+constexpr size_t tile_smem(int Kpad)
+{
+    return sizeof(__nv_bfloat16) * ((size_t)Kpad * (BN + 8) + 2 * (((kHV * halo_stride<C>() + 7) / 8) * 8) + 8 +
+                                    (C == 1 ? kBM * (kBK + 8) : 0));
+}
+
+// Halo elements a thread carries between tiles: uint4 (8 channels) for
+// C >= 8, one value for C == 1.
+template <int C>
+struct HaloRegs {
+    static constexpr int kItems = (C == 1) ? kHV : kHV * (C / 8);
+    static constexpr int kPer = (kItems + kThreads - 1) / kThreads;
+    uint4 v[kPer];
+};
+
+__device__ __forceinline__ void tile_origin(const ConvSrc& s, int t, int& x0, int& y0, int& z0)
+{
+    const int tilesX = (s.W + kTX - 1) / kTX, tilesY = (s.H + kTY - 1) / kTY;
+    x0 = (t % tilesX) * kTX;
+    t /= tilesX;
+    y0 = (t % tilesY) * kTY;
+    z0 = (t / tilesY) * kTZ;
+}
+
+// Global -> registers: the halo of the tile at (x0, y0, z0), zero outside,
+// the skip addend summed and rounded as a stored sum would be.
+template <int C>
+__device__ __forceinline__ void halo_fetch(const ConvSrc& src, int x0, int y0, int z0, HaloRegs<C>& h)
+{
+    const int Hs = src.up ? (src.H >> 1) : src.H, Ws = src.up ? (src.W >> 1) : src.W;
+#pragma unroll
+    for (int j = 0; j < HaloRegs<C>::kPer; ++j) {
+        const int i = threadIdx.x + j * kThreads;
+        uint4 r = make_uint4(0, 0, 0, 0);
+        if (i < HaloRegs<C>::kItems) {
+            const int hv = (C == 1) ? i : i / (C / 8), c8 = (C == 1) ? 0 : i % (C / 8);
+            const int hx = hv % kHX, hy = (hv / kHX) % kHY, hz = hv / (kHX * kHY);
+            const int z = z0 - 1 + hz, y = y0 - 1 + hy, x = x0 - 1 + hx;
+            if (z >= 0 && z < src.D && y >= 0 && y < src.H && x >= 0 && x < src.W) {
+                const size_t vox = src.up ? ((size_t)(z >> 1) * Hs + (y >> 1)) * Ws + (x >> 1)
+                                          : ((size_t)z * src.H + y) * src.W + x;
+                if constexpr (C == 1) {
+                    float v;
+                    if (src.f32) {
+                        v = src.f32[((size_t)z * src.H + y) * src.W + x] * (src.f32_scale ? *src.f32_scale : 1.f);
+                    } else {
+                        v = bf2f(src.a[vox]);
+                        if (src.b) v = bf2f(__float2bfloat16(v + bf2f(src.b[vox])));
+                    }
+                    r.x = __float_as_uint(v);
+                } else {
+                    const size_t off = vox * C + c8 * 8;
+                    r = *reinterpret_cast<const uint4*>(src.a + off);
+                    if (src.b) {
+                        const uint4 q = *reinterpret_cast<const uint4*>(src.b + off);
+                        __nv_bfloat162* pr = reinterpret_cast<__nv_bfloat162*>(&r);
+                        const __nv_bfloat162* pq = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 u = __bfloat1622float2(pr[e]), w = __bfloat1622float2(pq[e]);
+                            pr[e] = __floats2bfloat162_rn(u.x + w.x, u.y + w.y);
+                        }
+                    }
+                }
+            }
+        }
+        h.v[j] = r;
+    }
+}
+
+// Registers -> one halo buffer.
+template <int C>
+__device__ __forceinline__ void halo_store(__nv_bfloat16* sH, const HaloRegs<C>& h)
+{
+    constexpr int CS = halo_stride<C>();
+#pragma unroll
+    for (int j = 0; j < HaloRegs<C>::kPer; ++j) {
+        const int i = threadIdx.x + j * kThreads;
+        if (i >= HaloRegs<C>::kItems) continue;
+        if constexpr (C == 1) {
+            sH[i] = __float2bfloat16(__uint_as_float(h.v[j].x));
+        } else {
+            const int hv = i / (C / 8), c8 = i % (C / 8);
+            *reinterpret_cast<uint4*>(sH + hv * CS + c8 * 8) = h.v[j];
+        }
+    }
+}
+
+// Persistent: each CTA stages the weight matrix once and walks output
+// blocks blockIdx.x, blockIdx.x + gridDim.x, ...; while it multiplies one
+// block, the next block's halo is in flight to registers, and lands in the
+// other halo buffer afterwards.
+template <int C, int BN, class OutT>
+__global__ void __launch_bounds__(kThreads, 2) k_conv_tile(ConvSrc src, const __nv_bfloat16* __restrict__ Wt, int Kpad,
+                                                        int Npad, int N, const float* __restrict__ bias, int relu,
+                                                        const float* __restrict__ oscale, OutT* __restrict__ out,
+                                                        int ntiles)
+{
+    extern __shared__ __align__(16) unsigned char tile_raw[];
+    constexpr int CS = halo_stride<C>();
+    constexpr int HB = ((kHV * CS + 7) / 8) * 8;
+    __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(tile_raw);   // [Kpad][BN + 8]
+    __nv_bfloat16* sH0 = sW + (size_t)Kpad * (BN + 8);                 // two [kHV][CS] buffers
+    __nv_bfloat16* sZ = sH0 + 2 * HB;                                  // 8 zeros
+    __nv_bfloat16* sA = sZ + 8;                                        // C == 1: [kBM][kBK + 8]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.y * BN;
+    const int sgn = src.flip ? -1 : 1;
+    const float osc = oscale ? *oscale : 1.f;
+
+    for (int i = threadIdx.x; i < Kpad * (BN / 8); i += kThreads) {
+        const int r = i / (BN / 8), c = i % (BN / 8);
+        *reinterpret_cast<uint4*>(sW + r * (BN + 8) + c * 8) =
+            *reinterpret_cast<const uint4*>(Wt + (size_t)r * Npad + n0 + c * 8);
+    }
+    if (threadIdx.x < 8) sZ[threadIdx.x] = __float2bfloat16(0.f);
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    HaloRegs<C> h;
+    int x0, y0, z0;
+    tile_origin(src, tile, x0, y0, z0);
+    halo_fetch<C>(src, x0, y0, z0, h);
+    halo_store<C>(sH0, h);
+    __syncthreads();
+    int cur = 0;
+    // this thread's fragment row
+    const int m = 16 * warp + (lane & 15);
+    const int hc = ((m / (kTX * kTY) + 1) * kHY + ((m / kTX) % kTY + 1)) * kHX + (m % kTX + 1);
+    for (;;) {
+        const int next = tile + gridDim.x;
+        int nx0 = 0, ny0 = 0, nz0 = 0;
+        if (next < ntiles) {
+            tile_origin(src, next, nx0, ny0, nz0);
+            halo_fetch<C>(src, nx0, ny0, nz0, h);
+        }
+        const __nv_bfloat16* sH = sH0 + cur * HB;
+        float acc[BN / 8][4];
+#pragma unroll
+        for (int q = 0; q < BN / 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+        if constexpr (C == 1) {
+            for (int i = threadIdx.x; i < kBM * kBK; i += kThreads) {
+                const int mm = i / kBK, k = i % kBK;
+                __nv_bfloat16 v = __float2bfloat16(0.f);
+                if (k < 27) {
+                    const int tx = mm % kTX, ty = (mm / kTX) % kTY, tz = mm / (kTX * kTY);
+                    const int dz = sgn * (k / 9 - 1), dy = sgn * ((k / 3) % 3 - 1), dx = sgn * (k % 3 - 1);
+                    v = sH[((tz + 1 + dz) * kHY + (ty + 1 + dy)) * kHX + (tx + 1 + dx)];
+                }
+                sA[mm * (kBK + 8) + k] = v;
+            }
+            __syncthreads();
+            mma_stage<BN, false>(sA, sW, acc, warp, lane);
+        } else {
+            const int KS = Kpad / 16;
+            for (int ks = 0; ks < KS; ++ks) {
+                const int k = ks * 16 + (lane >> 4) * 8;
+                const int tap = k / C, ch = k % C;
+                const __nv_bfloat16* pa = sZ;
+                if (tap < 27) {
+                    const int dz = sgn * (tap / 9 - 1), dy = sgn * ((tap / 3) % 3 - 1), dx = sgn * (tap % 3 - 1);
+                    pa = sH + (hc + (dz * kHY + dy) * kHX + dx) * CS + ch;
+                }
+                uint32_t a[4];
+                ldsm_x4(a, pa);
+#pragma unroll
+                for (int j = 0; j < BN / 16; ++j) {
+                    uint32_t b[4];
+                    const int row = ks * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+                    const int col = j * 16 + (lane >> 4) * 8;
+                    ldsm_x4_t(b, sW + row * (BN + 8) + col);
+                    mma_bf16(acc[2 * j], a, b[0], b[1]);
+                    mma_bf16(acc[2 * j + 1], a, b[2], b[3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < BN / 8; ++q) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int mm = 16 * warp + (lane >> 2) + 8 * hh;
+                const int x = x0 + mm % kTX, y = y0 + (mm / kTX) % kTY, z = z0 + mm / (kTX * kTY);
+                if (x >= src.W || y >= src.H || z >= src.D) continue;
+                const long long v = ((long long)z * src.H + y) * src.W + x;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int n = n0 + q * 8 + 2 * (lane & 3) + e;
+                    if (n >= N) continue;
+                    float val = (acc[q][2 * hh + e] + (bias ? bias[n] : 0.f)) * osc;
+                    if (relu) val = fmaxf(val, 0.f);
+                    if constexpr (sizeof(OutT) == 2)
+                        out[v * N + n] = __float2bfloat16(val);
+                    else
+                        out[v * N + n] = val;
+                }
+            }
+        }
+        if (next >= ntiles) break;
+        // the other buffer was last read two tiles ago, before the previous barrier
+        halo_store<C>(sH0 + (cur ^ 1) * HB, h);
+        __syncthreads();
+        cur ^= 1;
+        tile = next;
+        x0 = nx0;
+        y0 = ny0;
+        z0 = nz0;
     }
 }
 
@@ -336,15 +566,25 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, int chunks, int K
 }
 
 // Bias gradient: part[b][n] = sum over block b's voxels of dY[v][n]; then
-// grad[n] = sum over blocks in order.
+// grad[n] = sum over blocks in order.  The block reads its chunk of dY as one
+// contiguous run: thread t (t < per, per the largest multiple of N within
+// the block) always lands on channel t % N, and the threads of a channel are
+// combined in thread order.
 __global__ void k_bias_part(const __nv_bfloat16* __restrict__ dY, long long V, int N, float* __restrict__ part)
 {
+    __shared__ float red[kThreads];
     const long long v0 = (long long)blockIdx.x * kWChunk;
     const long long v1 = v0 + kWChunk < V ? v0 + kWChunk : V;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        float s = 0.f;
-        for (long long v = v0; v < v1; ++v) s += bf2f(dY[v * N + n]);
-        part[(size_t)blockIdx.x * N + n] = s;
+    const int per = (kThreads / N) * N;
+    float s = 0.f;
+    if ((int)threadIdx.x < per)
+        for (long long i = v0 * N + threadIdx.x; i < v1 * N; i += per) s += bf2f(dY[i]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if ((int)threadIdx.x < N) {
+        float t = 0.f;
+        for (int j = threadIdx.x; j < per; j += N) t += red[j];
+        part[(size_t)blockIdx.x * N + threadIdx.x] = t;
     }
 }
 
@@ -428,15 +668,16 @@ __global__ void k_relu_grad(__nv_bfloat16* __restrict__ out, const __nv_bfloat16
 }
 
 // Loss sum((out - t)^2) / (2 V) per block in FP64 partials; gradient
-// g = (out - t) / V as bfloat16.
-__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t, long long V,
-                      __nv_bfloat16* __restrict__ g, double* __restrict__ part)
+// g = (out - t) / V as bfloat16.  The target is multiplied by the device
+// scalar *tscale when given.
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t, const float* __restrict__ tscale,
+                      long long V, __nv_bfloat16* __restrict__ g, double* __restrict__ part)
 {
     __shared__ double red[kThreads];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double s = 0.0;
     if (i < V) {
-        const float d = out[i] - t[i];
+        const float d = out[i] - t[i] * (tscale ? *tscale : 1.f);
         g[i] = __float2bfloat16(d / (float)V);
         s = (double)d * d;
     }
@@ -447,6 +688,38 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t
         __syncthreads();
     }
     if (threadIdx.x == 0) part[blockIdx.x] = red[0] / (2.0 * (double)V);
+}
+
+// Per-block FP64 partial sums of in[i]^2.
+__global__ void k_sumsq_part(const float* __restrict__ in, long long V, double* __restrict__ part)
+{
+    __shared__ double red[kThreads];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+        const double v = in[i];
+        s += v * v;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// r = RMS of the input from the partials (in block order); scales =
+// {1 / r, r gain, 1 / (r gain)} (r = 1 for an all-zero input).
+__global__ void k_scales(const double* __restrict__ part, int nb, long long V, float gain, float* __restrict__ scales)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    double r = sqrt(s / (double)V);
+    if (!(r > 0.0)) r = 1.0;
+    scales[0] = (float)(1.0 / r);
+    scales[1] = (float)(r * gain);
+    scales[2] = (float)(1.0 / (r * gain));
 }
 
 // Wt[k][n] (forward) = W[n][k] for k < 27 Cin, n < Cout; zero padding.

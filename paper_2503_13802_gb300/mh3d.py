@@ -38,12 +38,12 @@ class mh3d_solve_opts(ctypes.Structure):
     _fields_ = [("reg_kind", c_int), ("lambda_", c_double), ("alpha", c_double), ("shell", c_int),
                 ("solver", c_int), ("rel_tol", c_double), ("max_iter", c_int), ("fixed_iters", c_int),
                 ("x0_dev", c_void_p), ("normal_mode", c_int), ("apg_tau", c_double),
-                ("lambda_relative", c_int), ("cg_variant", c_int)]
+                ("lambda_relative", c_int), ("cg_variant", c_int), ("x0_fallback", c_int)]
 
 
 class mh3d_solve_info(ctypes.Structure):
     _fields_ = [("iters", c_int), ("rel_res_recurrence", c_double), ("rel_res_true", c_double),
-                ("history", POINTER(c_double)), ("status", c_int)]
+                ("history", POINTER(c_double)), ("status", c_int), ("x0_rejected", c_int)]
 
 
 class MH3DError(RuntimeError):
@@ -205,7 +205,7 @@ def mh3d_adjoint(plan: Plan, d, rho, stream=None):
 def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: int = 2, solver: int = 0,
               rel_tol: float = 1e-4, max_iter: int = 1000, fixed_iters: bool = False, x0=None,
               normal_mode: int = 0, apg_tau: float = 0.0, lam_relative: bool = False,
-              cg_variant: int = 0) -> mh3d_solve_opts:
+              cg_variant: int = 0, x0_fallback: bool = False) -> mh3d_solve_opts:
     """lam_relative: lam multiplies ||A||_2^2 (b = 1), see mh3d_operator_norm2."""
     o = mh3d_solve_opts()
     o.reg_kind, o.lambda_, o.alpha, o.shell, o.solver = reg_kind, lam, alpha, shell, solver
@@ -214,6 +214,7 @@ def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: i
     o.normal_mode, o.apg_tau = normal_mode, apg_tau
     o.lambda_relative = int(bool(lam_relative))
     o.cg_variant = int(cg_variant)
+    o.x0_fallback = int(bool(x0_fallback))
     o._x0_ref = x0
     return o
 
@@ -252,7 +253,8 @@ def mh3d_solve(plan: Plan, d, opts: mh3d_solve_opts, rho, stream=None, allow_not
     if st != MH3D_OK and not (allow_not_converged and st == MH3D_ERR_NOT_CONVERGED):
         _check(plan.handle, st)
     return {"iters": info.iters, "rel_res_recurrence": info.rel_res_recurrence, "rel_res_true": info.rel_res_true,
-            "status": info.status, "history": [hist[i] for i in range(min(info.iters, opts.max_iter) + 1)]}
+            "status": info.status, "x0_rejected": info.x0_rejected,
+            "history": [hist[i] for i in range(min(info.iters, opts.max_iter) + 1)]}
 
 
 def mh3d_solve_host(plan: Plan, d_host, opts: mh3d_solve_opts, rho_host, stream=None):

@@ -13,7 +13,8 @@ from typing import Sequence
 from .mh3d import MH3DError, _dev_ptr, _stream_ptr, load as _load_base
 
 EXPORTS = ["mh3d_unet_param_count", "mh3d_unet_create", "mh3d_unet_destroy", "mh3d_unet_set_params",
-           "mh3d_unet_get_params", "mh3d_unet_forward", "mh3d_unet_loss_grad", "mh3d_unet_adam_step",
+           "mh3d_unet_get_params", "mh3d_unet_forward", "mh3d_unet_loss_grad", "mh3d_unet_forward_scaled",
+           "mh3d_unet_loss_grad_scaled", "mh3d_unet_adam_step",
            "mh3d_unet_conv_forward", "mh3d_unet_conv_input_grad", "mh3d_unet_conv_weight_grad",
            "mh3d_unet_last_error"]
 
@@ -40,6 +41,8 @@ def load():
     lib.mh3d_unet_get_params.argtypes = [P, P, P]
     lib.mh3d_unet_forward.argtypes = [P, P, P, P]
     lib.mh3d_unet_loss_grad.argtypes = [P, P, P, P, POINTER(c_double), P]
+    lib.mh3d_unet_forward_scaled.argtypes = [P, P, c_float, P, P]
+    lib.mh3d_unet_loss_grad_scaled.argtypes = [P, P, P, c_float, P, POINTER(c_double), P]
     lib.mh3d_unet_adam_step.argtypes = [P, c_float, P]
     lib.mh3d_unet_conv_forward.argtypes = [POINTER(mh3d_unet_conv_desc), P, P, c_int, P, P]
     lib.mh3d_unet_conv_input_grad.argtypes = [POINTER(mh3d_unet_conv_desc), P, P, P, P]
@@ -119,6 +122,27 @@ class UNet:
         self._check(load().mh3d_unet_loss_grad(self.handle, c_void_p(pi), c_void_p(pt), c_void_p(pg),
                                                ctypes.byref(loss) if want_loss else None,
                                                c_void_p(_stream_ptr(stream))), "loss_grad")
+        return loss.value if want_loss else None
+
+    def forward_scaled(self, inp, gain: float, out, stream=None):
+        """out = (r gain) network(inp / r), r = RMS(inp) on the device."""
+        import torch
+
+        pi = _dev_ptr(inp, torch.float32, self.V, "in")
+        po = _dev_ptr(out, torch.float32, self.V, "out")
+        self._check(load().mh3d_unet_forward_scaled(self.handle, c_void_p(pi), c_float(gain), c_void_p(po),
+                                                    c_void_p(_stream_ptr(stream))), "forward_scaled")
+
+    def loss_grad_scaled(self, inp, target, gain: float, grad=None, want_loss: bool = True, stream=None):
+        import torch
+
+        pi = _dev_ptr(inp, torch.float32, self.V, "in")
+        pt = _dev_ptr(target, torch.float32, self.V, "target")
+        pg = _dev_ptr(grad, torch.float32, self.nparam, "grad") if grad is not None else None
+        loss = c_double(0.0)
+        self._check(load().mh3d_unet_loss_grad_scaled(self.handle, c_void_p(pi), c_void_p(pt), c_float(gain),
+                                                      c_void_p(pg), ctypes.byref(loss) if want_loss else None,
+                                                      c_void_p(_stream_ptr(stream))), "loss_grad_scaled")
         return loss.value if want_loss else None
 
     def adam_step(self, lr: float, stream=None):

@@ -141,6 +141,32 @@ def test_warm_start_from_solution_converges_immediately():
 
 
 @pytest.mark.parametrize("variant", [0, 1])
+def test_warm_start_fallback_rejects_a_bad_guess(variant):
+    """x0_fallback: a guess no better than zero (||A^T d - N x0|| >= ||A^T d||)
+    is replaced by the zero start on the device, and the result then equals
+    the zero-start solve bit for bit; a good guess is kept."""
+    p = params((32, 16, 8), s=2, kmin=2, kmax=5)
+    g = oracle_geom(p)
+    d = W.random_portraits(g.portrait_shape, 5)
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, None)
+    dd = _dev(d, torch.complex64)
+    x_zero = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    base = dict(lam=1e-2, lam_relative=True, rel_tol=1e-4, max_iter=400, cg_variant=variant)
+    i0 = mh3d_solve(plan, dd, make_opts(**base), x_zero)
+    bad = _dev(W.random_volume(g.shape, 6) * 1e3, torch.float32)
+    x = torch.empty_like(x_zero)
+    ib = mh3d_solve(plan, dd, make_opts(x0=bad, x0_fallback=True, **base), x)
+    assert ib["x0_rejected"] == 1 and ib["iters"] == i0["iters"], (ib, i0)
+    assert torch.equal(x, x_zero)
+    good = (x_zero * 0.9).contiguous()
+    ig = mh3d_solve(plan, dd, make_opts(x0=good, x0_fallback=True, **base), x)
+    assert ig["x0_rejected"] == 0 and ig["iters"] < i0["iters"], (ig, i0)
+    assert ig["history"][0] < 1.0
+
+
+@pytest.mark.parametrize("variant", [0, 1])
 def test_not_converged_status_keeps_iterate(variant):
     p = params((32, 16, 8), kmin=2, kmax=5)
     g = oracle_geom(p)

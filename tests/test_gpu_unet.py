@@ -24,7 +24,18 @@ from tests._cases import rel_l2
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-N_SMALL = (14, 10, 6)   # nx, ny, nz: V = 840, not a multiple of the 128-voxel tile
+N_SMALL = (14, 10, 6)   # nx, ny, nz: V = 840, not a multiple of the 128-voxel tile; partial 8x4x4 blocks
+
+
+@pytest.fixture(params=["tiled", "gather"], autouse=True)
+def conv_path(request, monkeypatch):
+    """Every test runs on the halo-tiled convolution (the default) and again
+    with MH3D_UNET_GATHER=1, which forces the gather kernel."""
+    if request.param == "gather":
+        monkeypatch.setenv("MH3D_UNET_GATHER", "1")
+    else:
+        monkeypatch.delenv("MH3D_UNET_GATHER", raising=False)
+    return request.param
 
 
 def _bf(shape, seed, scale=1.0):
@@ -54,6 +65,8 @@ CONV_CASES = [
     (16, 1, "plain"),
     (8, 24, "plain"),
     (12, 16, "plain"),    # channels not a multiple of 8: scalar gathers
+    (8, 16, "skip"),
+    (64, 64, "plain"),    # weights beyond the tiled kernel's shared memory: gather kernel
 ]
 
 
