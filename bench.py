@@ -253,6 +253,28 @@ def bench_mh3d(args):
         if i >= 3:
             fwd_t.append(e0.elapsed_time(e1) / 1e3)
             adj_t.append(e2.elapsed_time(e3) / 1e3)
+    # the same operators through cuFFT (torch.fft) and torch's elementwise kernels
+    cf = CufftOperators(plan, torch.as_tensor(b, dtype=torch.float32, device=dev).contiguous())
+    cf_f, cf_a = [], []
+    d_cf = torch.empty_like(d)
+    r_cf = torch.empty_like(x)
+    for i in range(6 + 2):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cf.forward(rho_t, d_cf)
+        e1.record(stream)
+        flush.zero_()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        cf.adjoint(d, r_cf)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        if i >= 2:
+            cf_f.append(e0.elapsed_time(e1) / 1e3)
+            cf_a.append(e2.elapsed_time(e3) / 1e3)
     alg_bytes = 4 * N + 4 * N + 8 * M          # rho + b + complex64 portraits
     peaks = {}
     try:
@@ -319,6 +341,10 @@ def bench_mh3d(args):
                      "adjoint_AT": {"us": adj_s * 1e6, "alg_bytes": alg_bytes,
                                     "achieved_gbs": alg_bytes / adj_s / 1e9, "frac": alg_bytes / adj_s / 1e9 / peak},
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "cufft_comparison": {"what": "A and A^T with cuFFT (torch.fft) + torch elementwise kernels, same spectra",
+                             "forward_us": 1e6 * statistics.mean(cf_f), "adjoint_us": 1e6 * statistics.mean(cf_a),
+                             "forward_speedup_of_mh3d": statistics.mean(cf_f) / fwd_s,
+                             "adjoint_speedup_of_mh3d": statistics.mean(cf_a) / adj_s},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * M),
                 "d2h_bytes_per_step": int(4 * N)},
         "gpu_launches": launches_per_step * args.steps,
@@ -359,6 +385,52 @@ def cpu_baseline(wl: W.Workload, gpu_iters: int, sample_iters: int = 2):
     return {"value": 1.0 / est, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"oracle CG, {sample_iters} iterations at {wl.n} K={wl.k_max - wl.k_min + 1} "
                       f"({t:.1f} s), scaled to {gpu_iters} iterations + A^T d + true residual"}
+
+
+class CufftOperators:
+    """The forward and adjoint operators written with cuFFT (torch.fft) and
+    torch's elementwise kernels, from the plan's own spectra: the comparison
+    arm for the hand-written passes (same model, same inputs, same GPU).
+    Forward: U = DFT3(b rho) (nz Z)(ny Y); per harmonic, fold the drive-axis
+    spectrum of U nx X_k by s (the row selector), inverse DFT on the portrait
+    mesh, times e^{i theta_k}.  Adjoint: per harmonic, DFT3 of
+    Re(e^{-i theta_k} y_k), periodised s times (zero insertion), times
+    conj(nx X_k); the sum times conj((nz Z)(ny Y)), inverse DFT3, times b."""
+
+    def __init__(self, plan, b_t):
+        import torch
+
+        from paper_2503_13802_gb300 import mh3d_plan_spectra
+
+        X, Y, Z, ph = mh3d_plan_spectra(plan)
+        self.nz, self.ny, self.nx = plan.shape
+        self.K = plan.K
+        self.mx = plan.portrait_shape[3]
+        self.s = self.nx // self.mx
+        self.Xt = X * self.nx
+        self.Hyz = (Z * self.nz)[:, None, None] * (Y * self.ny)[None, :, None]
+        self.ph = ph
+        self.b = b_t
+        self.torch = torch
+
+    def forward(self, rho, d):
+        torch = self.torch
+        u = rho * self.b if self.b is not None else rho
+        U = torch.fft.fftn(u.to(torch.complex64), dim=(0, 1, 2)) * self.Hyz
+        for k in range(self.K):
+            V = (U * self.Xt[k][None, None, :]).reshape(self.nz, self.ny, self.s, self.mx).sum(dim=2)
+            d[k] = torch.fft.ifftn(V, dim=(0, 1, 2)).real * (self.ph[k] / self.s)
+
+    def adjoint(self, d, rho):
+        torch = self.torch
+        acc = None
+        for k in range(self.K):
+            v = (d[k] * self.ph[k].conj()).real
+            Vn = torch.fft.fftn(v.to(torch.complex64), dim=(0, 1, 2)).repeat(1, 1, self.s)
+            t = Vn * self.Xt[k].conj()[None, None, :]
+            acc = t if acc is None else acc + t
+        r = torch.fft.ifftn(acc * self.Hyz.conj(), dim=(0, 1, 2)).real
+        rho.copy_(r * self.b if self.b is not None else r)
 
 
 def bench_batched(args):

@@ -172,6 +172,23 @@ mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* con
                                const mh3d_solve_opts* opts, float* const* rho_dev,
                                mh3d_solve_info* infos, void* stream);
 
+/* Copies the plan's FP32 spectral tables (device -> device, any pointer may
+ * be NULL): X [K][nx] complex = c_k DFT_nx(L^(k)(gamma o dx) at o + ds_offset)
+ * / nx (the drive-axis spectra, Eq. hkapprox and Theorem 1, shifted so that
+ * portrait row i' is model row s i' + ds_offset), Y [ny] = DFT of the
+ * transverse samples / ny, Z [nz] likewise, phase [K] = e^{i theta_k}.  With
+ * these, d_k = e^{i theta_k} S_s IDFT(DFT(b rho) nx X_k ny Y nz Z) (the
+ * forward model, Sec. 3.2 and 4.1).  Asynchronous on `stream`. */
+mh3d_status mh3d_plan_spectra(mh3d_plan plan, void* X, void* Y, void* Z, void* phase, void* stream);
+
+/* Tile autotuning: times the fused normal operator (the CG loop's kernels)
+ * for each transverse-pass tile width (16 and 8 columns) on the plan's
+ * workspace and keeps the fastest for this plan.  The choice is remembered
+ * for the process per (grid, ds_factor, K, weighted or not), so later plans
+ * of a tuned size take it without timing.  Synchronises `stream`; drops the
+ * plan's cached graphs.  tpass_cols (may be NULL) receives the width. */
+mh3d_status mh3d_plan_autotune(mh3d_plan plan, void* stream, int* tpass_cols);
+
 /* d_dev = A rho_dev like mh3d_forward, for callers that cannot allocate
  * device memory (a fixed device-memory budget owned by another framework's
  * pool, a frozen real-time memory plan, or code that must not risk the

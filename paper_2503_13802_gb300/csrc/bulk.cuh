@@ -136,4 +136,13 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int
                  : "memory");
 }
 
+// Programmatic dependent launch.  pdl_trigger lets the next kernel in the
+// stream (launched with the programmatic-serialization attribute) be
+// scheduled once every CTA of this grid has triggered or exited; pdl_wait
+// blocks until the previous grid has completed and its memory is visible.
+// Both are no-ops for kernels launched without the attribute.  Everything a
+// kernel reads that an earlier kernel writes must come after pdl_wait.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace mh3d

@@ -219,6 +219,7 @@ XArgs xpass_args(const Plan& P)
     a.reg.nx = P.nx;
     a.reg.ny = P.ny;
     a.reg.nz = P.nz;
+    a.status = P.w.flags ? P.w.flags + 3 : nullptr;
     return a;
 }
 
@@ -456,6 +457,24 @@ mh3d_status mh3d_plan_create(const mh3d_geometry* g, void* stream, mh3d_plan* ou
     }
     g_create_err.clear();
     *out = P;
+    return MH3D_OK;
+}
+
+mh3d_status mh3d_plan_spectra(mh3d_plan P, void* X, void* Y, void* Z, void* phase, void* stream)
+{
+    if (!P) return MH3D_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto cp = [&](void* dst, const float2* src, size_t n) {
+        return dst ? cudaMemcpyAsync(dst, src, sizeof(float2) * n, cudaMemcpyDeviceToDevice, st) : cudaSuccess;
+    };
+    cudaError_t e = cp(X, P->Xhat, (size_t)P->K * P->nx);
+    if (e == cudaSuccess) e = cp(Y, P->Yhat, (size_t)P->ny);
+    if (e == cudaSuccess) e = cp(Z, P->Zhat, (size_t)P->nz);
+    if (e == cudaSuccess) e = cp(phase, P->phase, (size_t)P->K);
+    if (e != cudaSuccess) {
+        P->err = std::string("mh3d_plan_spectra: ") + cudaGetErrorString(e);
+        return MH3D_ERR_CUDA;
+    }
     return MH3D_OK;
 }
 

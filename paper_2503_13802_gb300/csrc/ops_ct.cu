@@ -33,6 +33,7 @@ struct TDesc {
 struct XDesc {
     void (*fn)(XArgs) = nullptr;
     size_t smem = 0;
+    int threads = kT;
 };
 
 // P: column pairs (pencils) per CTA, 4 or 8 (tiles of 8 or 16 columns).
@@ -65,10 +66,11 @@ XDesc xdesc(int which)
 {
     if (which == 0) return XDesc{k_xfwd_ct<LFF, LIF, S>, xfwd_ct_smem<LFF, LIF, S>()};
     if (which == 1) return XDesc{k_xadj_ct<LFA, LIA, S>, xadj_ct_smem<LFA, LIA, S>()};
-    return XDesc{k_xnrm_ct<LFN, S>, xnrm_ct_smem<LFN, S>()};
+    if (which == 3) return XDesc{k_xnrm_ct<LFN, S, true>, xnrm_ct_smem<LFN, S, true>(), kTN};
+    return XDesc{k_xnrm_ct<LFN, S, false>, xnrm_ct_smem<LFN, S, false>(), kTN};
 }
 
-XDesc xpass_desc(int nx, int s, int which /*0 forward, 1 adjoint, 2 normal*/)
+XDesc xpass_desc(int nx, int s, int which /*0 forward, 1 adjoint, 2 normal, 3 normal with bulk copies*/)
 {
     if (nx == 32 && s == 1)
         return xdesc<1, RList<4, 8>, RList<8, 4>, RList<4, 8>, RList<8, 4>, RList<4, 8>>(which);
@@ -102,6 +104,38 @@ cudaError_t opt_in(F* f, size_t need, int optin)
 }  // namespace
 
 static bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// MH3D_PDL=1 (opt-in): launch the CG loop's kernels (T passes, drive-axis
+// normal pass) with programmatic stream serialization, so each may be
+// scheduled while its predecessor finishes; the kernels wait for it before
+// reading its output.  Measured at 128x128x64 inside the CG graph: 40.9 us
+// per iteration with it, 35.7 us without (the early-scheduled CTAs hold SM
+// slots the running pass needs), hence off by default.
+static bool pdl_enabled()
+{
+    const char* e = std::getenv("MH3D_PDL");
+    return e && e[0] == '1';
+}
+
+template <class Args>
+static cudaError_t launch_pdl(void (*fn)(Args), dim3 grid, int threads, size_t smem, cudaStream_t st, const Args& a)
+{
+    if (!pdl_enabled()) {
+        fn<<<grid, threads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, a);
+}
 
 // cuTensorMapEncodeTiled from the driver, resolved once through the runtime
 // (no link-time dependency on libcuda).
@@ -167,7 +201,7 @@ cudaError_t ct_set_attributes(int optin)
         }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
-        for (int w = 0; w < 3; ++w) {
+        for (int w = 0; w < 4; ++w) {
             const XDesc d = xpass_desc(p[0], p[1], w);
             cudaError_t e = opt_in(d.fn, d.smem, optin);
             if (e != cudaSuccess) return e;
@@ -188,19 +222,31 @@ cudaError_t run_tpass_ct(const TArgs& a0, int nouter, cudaStream_t st)
     if (!ok) return cudaErrorInvalidValue;
     const TDesc d = tpass_desc(a.n, a.cols / 2);
     dim3 grid((a.nx + a.cols - 1) / a.cols, nouter);
-    d.fn<<<grid, kT, d.smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(d.fn, grid, kT, d.smem, st, a);
 }
 
 static cudaError_t run_x_ct(const XArgs& a, int which, cudaStream_t st)
 {
     const XDesc d = xpass_desc(a.nx, a.s, which);
-    d.fn<<<xpass_blocks(a.rows, kP), kT, d.smem, st>>>(a);
+    if (which >= 2) return launch_pdl(d.fn, dim3(xpass_blocks(a.rows, kP)), d.threads, d.smem, st, a);
+    d.fn<<<xpass_blocks(a.rows, kP), d.threads, d.smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t run_xfwd_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, 0, st); }
 cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, 1, st); }
-cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, 2, st); }
+// The bulk-copy normal pass (opt-in: MH3D_XNRM_BULK=1; measured 3 % slower
+// per CG iteration than the register-loading pass at 128x128x64) needs
+// 16-byte aligned vectors (rows of nx floats are then 16-byte aligned too,
+// nx % 4 == 0) and R = I.
+static bool xnrm_bulk_ok(const XArgs& a)
+{
+    const char* e = std::getenv("MH3D_XNRM_BULK");
+    if (!e || e[0] != '1') return false;
+    return a.vec4 && a.reg.kind == 0 && (a.nx % 4) == 0 && al16(a.vin) && al16(a.pin) && al16(a.qout) &&
+           (!a.b || al16(a.b));
+}
+
+cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, xnrm_bulk_ok(a) ? 3 : 2, st); }
 
 }  // namespace mh3d

@@ -26,6 +26,7 @@ namespace ct {
 
 constexpr int kP = 16;    // pencils per CTA of the X passes: 16 row pairs
 constexpr int kT = 128;   // threads per CTA
+constexpr int kTN = 256;  // threads per CTA of the X normal pass (one butterfly each per stage)
 constexpr int kKG = 2;    // harmonics per inverse batch in the X forward kernel
 
 // Forward last stage (radix R, Ns = N/R) -> per-element spectral multiplier
@@ -84,6 +85,8 @@ __global__ void __launch_bounds__(kT) k_tpass_ct(const __grid_constant__ TArgs a
     __shared__ double red[34];
     __shared__ __align__(8) uint64_t bar;
     float beta = 0.f, alpha = 0.f;
+    pdl_trigger();
+    pdl_wait();   // no-ops unless launched with programmatic serialization
     if (a.cg.flags && !cg_enter(a.cg, a.pupdate != 0, &beta, red, &alpha)) return;
     // 128-byte aligned start for the TMA boxes (the launcher adds the slack)
     float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(kT) k_tpass_ct(const __grid_constant__ TArgs a
         mbar_arrive_expect_tx(&bar, TILEB * nt);
         for (int t = 0; t < nt; ++t) tma_load_3d(tiles + t * TILE, &a.tm.m[tmap[t]], x0, cy, cz, &bar);
     }
+    // tables while the tile copies are in flight
     for (int i = threadIdx.x; i < N; i += T) {
         tw[i] = a.tw[i];
         mu[i] = a.mult[i];
@@ -529,27 +533,100 @@ __device__ __forceinline__ void nrm_epilogue(const XArgs& a, int row0, const flo
 
 // X normal: LF = schedule of length nx whose last radix is divisible by S;
 // the inverse runs the reversed schedule.
-template <class LF, int S>
-__global__ void __launch_bounds__(kT) k_xnrm_ct(const XArgs a)
+// The epilogue of the bulk-copy variant: q = b w + lambda p for the tile's
+// nrow rows, with w, b and p read from shared memory and q written in place
+// over w (each thread reads and then writes the same float4); dots p^T q
+// (and p^T p) accumulate in the same order as nrm_epilogue's.
+template <int NX, int ROWS, int T>
+__device__ __forceinline__ void nrm_epilogue_tile(const XArgs& a, int nrow, float* stg, const float* tb,
+                                                  const float* tp, DotAcc* acc, DotAcc* acc2)
+{
+    constexpr int V = NX / 4;
+    constexpr int TOTAL = ROWS * V;
+    constexpr int ITER = (TOTAL + T - 1) / T;
+    const float lam = a.reg.lambda;
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int idx = (int)threadIdx.x + it * T;
+        const int rr = idx / V, c = idx - rr * V;
+        if (((TOTAL % T) != 0 && idx >= TOTAL) || rr >= nrow) continue;
+        const int o = rr * NX + 4 * c;
+        const float4 W = *reinterpret_cast<const float4*>(stg + o);
+        const float4 B = tb ? *reinterpret_cast<const float4*>(tb + o) : make_float4(1.f, 1.f, 1.f, 1.f);
+        const float4 Pv = *reinterpret_cast<const float4*>(tp + o);
+        float4 q;
+        q.x = fmaf(B.x, W.x, lam * Pv.x);
+        q.y = fmaf(B.y, W.y, lam * Pv.y);
+        q.z = fmaf(B.z, W.z, lam * Pv.z);
+        q.w = fmaf(B.w, W.w, lam * Pv.w);
+        *reinterpret_cast<float4*>(stg + o) = q;
+        acc->add(Pv.x, q.x);
+        acc->add(Pv.y, q.y);
+        acc->add(Pv.z, q.z);
+        acc->add(Pv.w, q.w);
+        if (acc2) {
+            acc2->add(Pv.x, Pv.x);
+            acc2->add(Pv.y, Pv.y);
+            acc2->add(Pv.z, Pv.z);
+            acc2->add(Pv.w, Pv.w);
+        }
+    }
+}
+
+// BULK: the CTA's 2P consecutive rows of the input, b and p are one
+// contiguous block each, brought in by three 1D bulk copies on one
+// mbarrier while the twiddles load; q leaves the same way from the staging
+// tile.  Host conditions: 16-byte aligned vectors, R = I.
+template <class LF, int S, bool BULK>
+__global__ void __launch_bounds__(kTN) k_xnrm_ct(const XArgs a)
 {
     using IF = RInfo<LF>;
     using LI = Reverse<LF>;
     constexpr int NX = IF::n(), NST = IF::nst, R = IF::last(), R2 = R / S, MX = NX / S;
     static_assert(R % S == 0, "alias blocks must sit in one butterfly");
-    constexpr int P = kP, T = kT;
+    constexpr int P = kP, T = kTN;
     constexpr int NBL = NX / R;
     constexpr int ITERL = (NBL * P + T - 1) / T;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
     __shared__ double red[34];
+    __shared__ __align__(8) uint64_t bar;
     float dummy;
+    pdl_trigger();
+    pdl_wait();   // no-ops unless launched with programmatic serialization
     if (a.cg_active && !cg_enter(a.cg, false, &dummy, red)) return;
     float2* tw = sm;
     float2* b0 = tw + NX;
     float2* b1 = b0 + NX * P;
-    for (int i = threadIdx.x; i < NX; i += T) tw[i] = a.twx[i];
-    __syncthreads();
+    float* tin = reinterpret_cast<float*>(b1 + NX * P);   // BULK: [2P][NX] tiles of v, b, p
+    float* tb = tin + 2 * P * NX;
+    float* tp = tb + 2 * P * NX;
     const int row0 = blockIdx.x * 2 * P;
-    const RowPairLd ld{a.vin, NX, row0, a.rows};
+    const int nrow = min(2 * P, a.rows - row0);
+    const uint32_t tbytes = (uint32_t)(nrow * NX * sizeof(float));
+    if constexpr (BULK) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&bar, tbytes * (a.b ? 3u : 2u));
+            const size_t off = (size_t)row0 * NX;
+            bulk_g2s(tin, a.vin + off, tbytes, &bar);
+            if (a.b) bulk_g2s(tb, a.b + off, tbytes, &bar);
+            bulk_g2s(tp, a.pin + off, tbytes, &bar);
+        }
+    }
+    for (int i = threadIdx.x; i < NX; i += T) tw[i] = a.twx[i];
+    if constexpr (BULK) {
+        // a copy that never lands would be a hardware fault: give up after
+        // the bounded wait, record MH3D_ERR_TIMEOUT and skip the work
+        const bool ok = mbar_wait(&bar, 0, a.status);
+        if (!__syncthreads_and(ok)) return;
+    } else {
+        __syncthreads();
+    }
+    const RowPairLd ld{BULK ? tin : a.vin, NX, BULK ? 0 : row0, BULK ? nrow : a.rows};
     DotAcc dacc, dacc2;
     constexpr int pf = result_parity<0, NST - 1>();
     float2* fo = pf ? b1 : b0;
@@ -589,7 +666,18 @@ __global__ void __launch_bounds__(kT) k_xnrm_ct(const XArgs a)
     // with all of a thread's loads issued before its stores.
     float* stg = reinterpret_cast<float*>((NST % 2 == 0) ? fo : fx);
     run_stages<LI, 1, NST, P, T, 1, true, true, false>(BufLd{fx, P}, RowStageSt{stg, NX}, fo, fx, P, tw);
-    nrm_epilogue<NX, 2 * P, T>(a, row0, stg, &dacc, a.part2 ? &dacc2 : nullptr);
+    if constexpr (BULK) {
+        nrm_epilogue_tile<NX, 2 * P, T>(a, nrow, stg, a.b ? tb : nullptr, tp, &dacc, a.part2 ? &dacc2 : nullptr);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bulk_s2g(a.qout + (size_t)row0 * NX, stg, tbytes);
+            bulk_commit();
+            bulk_wait_all();   // the copy reads shared memory and must land before the CTA ends
+        }
+    } else {
+        nrm_epilogue<NX, 2 * P, T>(a, row0, stg, &dacc, a.part2 ? &dacc2 : nullptr);
+    }
     if (a.part) {
         const double t = block_sum_f64(dacc.value(), red);
         if (a.part2) {
@@ -603,11 +691,11 @@ __global__ void __launch_bounds__(kT) k_xnrm_ct(const XArgs a)
     (void)MX;
 }
 
-template <class LF, int S>
+template <class LF, int S, bool BULK = false>
 constexpr size_t xnrm_ct_smem()
 {
     constexpr size_t nx = RInfo<LF>::n();
-    return sizeof(float2) * (nx + 2 * nx * kP);
+    return sizeof(float2) * (nx + 2 * nx * kP) + (BULK ? sizeof(float) * 3 * 2 * kP * nx : 0);
 }
 
 }  // namespace ct

@@ -129,6 +129,7 @@ struct XArgs {
     RegArgs reg{};
     CgCtl cg{};
     int cg_active = 0;
+    int* status = nullptr;           // device status word for bounded-wait timeouts
 };
 
 // Shared-memory sizes in bytes.

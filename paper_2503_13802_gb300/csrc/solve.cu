@@ -216,7 +216,9 @@ mh3d_status solve_alloc(Plan& P)
     SolveWork& w = P.w;
     const size_t N = (size_t)P.N;
     const size_t vec = (N + 63) & ~size_t(63);
-    const size_t cap = (size_t)std::max({update_blocks(P.N), normal_part_count(P, 0), normal_part_count(P, 1), 1});
+    // partial-sum slots for the widest grid any tile choice (8-column T pass) can launch
+    const size_t cap = (size_t)std::max({update_blocks(P.N), normal_part_count(P, 0), normal_part_count(P, 1),
+                                         tpass_blocks(P.nx, 8, tpass_outer(P, 1)), 1});
     w.red_cap = cap;
     const size_t bytes = sizeof(float) * vec * 8 + red_bytes(cap) + 64;
     if (cudaMalloc(&w.base, bytes) != cudaSuccess) {
@@ -761,6 +763,89 @@ static mh3d_status cg_solve_batched(const std::vector<Plan*>& ps, const float2* 
     return worst;
 }
 
+// ---------------------------------------------------------------------------
+// Tile autotuning
+// ---------------------------------------------------------------------------
+// Times the fused normal operator (the kernels of the CG loop) for each
+// transverse-pass tile width on the plan's own workspace and keeps the
+// fastest; the choice is remembered per (grid, s, K, weighting) for the
+// process, so plans of an already tuned size take it without timing.
+namespace {
+std::mutex g_tune_mu;
+std::vector<std::pair<std::vector<long long>, int>> g_tuned;
+}  // namespace
+
+static void drop_graphs(Plan& P)
+{
+    if (P.graph_exec) {
+        cudaGraphExecDestroy(P.graph_exec);
+        P.graph_exec = nullptr;
+    }
+    batch_forget(P);
+}
+
+static mh3d_status autotune(Plan& P, cudaStream_t st, int* chosen)
+{
+    const std::vector<long long> key = {P.nx, P.ny, P.nz, P.s, P.K, P.sens ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto& e : g_tuned)
+            if (e.first == key) {
+                if (P.tile.tpass_cols != e.second) {
+                    P.tile.tpass_cols = e.second;
+                    drop_graphs(P);
+                }
+                *chosen = e.second;
+                return MH3D_OK;
+            }
+    }
+    mh3d_solve_opts o{};
+    o.lambda = 1e-3;
+    o.lambda_relative = 1;
+    const RegArgs reg = reg_args(P, o);
+    SolveWork& w = P.w;
+    cudaEvent_t e0, e1;
+    MH3D_CK(P, cudaEventCreate(&e0));
+    MH3D_CK(P, cudaEventCreate(&e1));
+    MH3D_CK(P, cudaMemsetAsync(w.r, 0, sizeof(float) * P.N, st));
+    const int cand[2] = {16, 8};
+    float best = 1e30f;
+    int pick = P.tile.tpass_cols;
+    for (int c : cand) {
+        P.tile.tpass_cols = c;
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            e = launch_normal(P, 0, reg, w.r, w.s, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int i = 0; i < 20 && e == cudaSuccess; ++i)
+            e = launch_normal(P, 0, reg, w.r, w.s, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            P.err = std::string("autotune: ") + cudaGetErrorString(e);
+            return MH3D_ERR_CUDA;
+        }
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P.tile.tpass_cols = pick;
+    drop_graphs(P);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned.push_back({key, pick});
+    }
+    *chosen = pick;
+    return MH3D_OK;
+}
+
 // APG (Sec. 4.3): y^k = rho^k + (k-1)/(k+2)(rho^k - rho^{k-1});
 // rho^{k+1} = max(y^k - tau M^*(M y^k - b), 0), M^*(M y - b) = N y - A^T d.
 static mh3d_status apg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o, float* rho, mh3d_solve_info* info,
@@ -850,6 +935,15 @@ mh3d_status mh3d_solve(mh3d_plan P, const void* d, const mh3d_solve_opts* o, flo
     P->err.clear();
     if (o->solver == 1) return apg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
     return cg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
+}
+
+mh3d_status mh3d_plan_autotune(mh3d_plan P, void* stream, int* tpass_cols)
+{
+    if (!P) return MH3D_ERR_INVALID_ARG;
+    int c = 0;
+    mh3d_status s = autotune(*P, (cudaStream_t)stream, &c);
+    if (s == MH3D_OK && tpass_cols) *tpass_cols = c;
+    return s;
 }
 
 mh3d_status mh3d_solve_host(mh3d_plan P, const void* d_host, const mh3d_solve_opts* o, float* rho_host,

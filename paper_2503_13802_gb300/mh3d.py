@@ -56,7 +56,7 @@ _lib = None
 
 EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoint", "mh3d_normal", "mh3d_solve",
            "mh3d_solve_host", "mh3d_solve_batched", "mh3d_forward_noalloc", "mh3d_operator_norm2", "mh3d_last_error",
-           "mh3d_plan_workspace_bytes", "mh3d_version"]
+           "mh3d_plan_workspace_bytes", "mh3d_version", "mh3d_plan_autotune", "mh3d_plan_spectra"]
 
 
 def library_path() -> str:
@@ -85,6 +85,8 @@ def load(build_if_missing: bool = True):
     lib.mh3d_solve_batched.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(mh3d_solve_opts),
                                        POINTER(c_void_p), POINTER(mh3d_solve_info), P]
     lib.mh3d_operator_norm2.argtypes = [P, POINTER(c_double)]
+    lib.mh3d_plan_autotune.argtypes = [P, P, POINTER(c_int)]
+    lib.mh3d_plan_spectra.argtypes = [P, P, P, P, P, P]
     lib.mh3d_forward_noalloc.argtypes = [POINTER(mh3d_geometry), P, P, P]
     lib.mh3d_last_error.argtypes = [P]
     lib.mh3d_last_error.restype = c_char_p
@@ -341,6 +343,29 @@ def mh3d_operator_norm2(plan: Plan) -> float:
     out = c_double()
     _check(plan.handle, load().mh3d_operator_norm2(plan.handle, ctypes.byref(out)))
     return out.value
+
+
+def mh3d_plan_autotune(plan: Plan, stream=None) -> int:
+    """Picks the transverse-pass tile width by timing; returns it."""
+    c = c_int(0)
+    _check(plan.handle, load().mh3d_plan_autotune(plan.handle, c_void_p(_stream_ptr(stream)), ctypes.byref(c)))
+    return c.value
+
+
+def mh3d_plan_spectra(plan: Plan, stream=None):
+    """(X [K, nx], Y [ny], Z [nz], phase [K]) complex64 device tensors: the
+    plan's spectral tables (see include/mh3d.h)."""
+    import torch
+
+    nz, ny, nx = plan.shape
+    X = torch.empty((plan.K, nx), dtype=torch.complex64, device="cuda")
+    Y = torch.empty(ny, dtype=torch.complex64, device="cuda")
+    Z = torch.empty(nz, dtype=torch.complex64, device="cuda")
+    ph = torch.empty(plan.K, dtype=torch.complex64, device="cuda")
+    _check(plan.handle, load().mh3d_plan_spectra(plan.handle, c_void_p(X.data_ptr()), c_void_p(Y.data_ptr()),
+                                                 c_void_p(Z.data_ptr()), c_void_p(ph.data_ptr()),
+                                                 c_void_p(_stream_ptr(stream))))
+    return X, Y, Z, ph
 
 
 def mh3d_version() -> str:

@@ -17,15 +17,18 @@ torch = pytest.importorskip("torch")
 TOL = 1e-5
 
 
-@pytest.fixture(params=["specialised", "generic"])
+@pytest.fixture(params=["specialised", "generic", "bulk"])
 def kernel_path(request, monkeypatch):
     """Run each operator test on the compile-time specialised kernels (the
-    default for the common lengths) and again with MH3D_GENERIC=1, which
-    forces the runtime-general kernels for every size."""
+    default for the common lengths), again with MH3D_GENERIC=1, which forces
+    the runtime-general kernels for every size, and with MH3D_XNRM_BULK=1,
+    the bulk-copy variant of the drive-axis normal pass."""
+    monkeypatch.delenv("MH3D_GENERIC", raising=False)
+    monkeypatch.delenv("MH3D_XNRM_BULK", raising=False)
     if request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
-    else:
-        monkeypatch.delenv("MH3D_GENERIC", raising=False)
+    elif request.param == "bulk":
+        monkeypatch.setenv("MH3D_XNRM_BULK", "1")
     return request.param
 
 

@@ -241,3 +241,31 @@ def test_solve_host_buffers_match_device_solve():
     xh = torch.empty(g.shape, dtype=torch.float32).pin_memory()
     mh3d_solve_host(plan, dh, o, xh)
     np.testing.assert_array_equal(xh.numpy(), x.cpu().numpy())
+
+
+def test_tile_width_and_autotune_keep_results_bit_identical(monkeypatch):
+    """The transverse-pass tile width (8 or 16 columns per CTA) only groups
+    columns into CTAs: every column's transform and every reduction is the
+    same, so solves agree bit for bit, before and after autotuning."""
+    from paper_2503_13802_gb300 import make_opts, mh3d_plan_autotune, mh3d_solve
+
+    p = params((64, 32, 32), s=2, kmin=2, kmax=9)
+    g = oracle_geom(p)
+    b = sens_map(p)
+    d = _dev(W.random_portraits(g.portrait_shape, 17), torch.complex64)
+    opts = make_opts(lam=1e-3, lam_relative=True, rel_tol=1e-4, max_iter=300)
+    monkeypatch.delenv("MH3D_TPASS_COLS", raising=False)
+    plan16 = gpu_plan(p, b)
+    monkeypatch.setenv("MH3D_TPASS_COLS", "8")
+    plan8 = gpu_plan(p, b)
+    monkeypatch.delenv("MH3D_TPASS_COLS")
+    x16 = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    x8 = torch.empty_like(x16)
+    i16 = mh3d_solve(plan16, d, opts, x16)
+    i8 = mh3d_solve(plan8, d, opts, x8)
+    assert i16["iters"] == i8["iters"] and torch.equal(x16, x8)
+    cols = mh3d_plan_autotune(plan16)
+    assert cols in (8, 16)
+    xt = torch.empty_like(x16)
+    mh3d_solve(plan16, d, opts, xt)
+    assert torch.equal(xt, x16)
