@@ -71,6 +71,23 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_throughput(local_total_s: float, steps: int, device):
+    """Whole-job throughput of independent replicas (one volume per rank, no
+    data-path collective): the job time is the slowest rank's (one MAX
+    all-reduce of the timing only) and the value counts every rank's steps.
+    Returns (value, job_seconds)."""
+    import torch
+    import torch.distributed as dist
+
+    ws, total = 1, float(local_total_s)
+    if dist.is_available() and dist.is_initialized():
+        ws = dist.get_world_size()
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return ws * steps / total, total
+
+
 def make_case(wl: W.Workload, seed: int, forward_fn):
     """Phantom, sensitivity and noisy portraits at the workload's SNR.
     forward_fn(rho) -> clean portraits (complex, numpy)."""
@@ -189,14 +206,7 @@ def bench_mh3d(args):
             times.append(e0.elapsed_time(e1) / 1e3)
             iters.append(info["iters"])
         barrier()
-    total = sum(times)
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = ws * args.steps / total
+    value, total = replica_throughput(sum(times), args.steps, dev)
 
     it_med = int(statistics.median(iters))
     N = nx * ny * nz

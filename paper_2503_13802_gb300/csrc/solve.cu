@@ -973,8 +973,8 @@ mh3d_status mh3d_solve_host(mh3d_plan P, const void* d_host, const mh3d_solve_op
 mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* const* d, const mh3d_solve_opts* o,
                                float* const* rho, mh3d_solve_info* infos, void* stream)
 {
+    if (nvol == 0) return MH3D_OK;   // nothing to do; the arrays may be NULL
     if (!plans || nvol < 0 || !d || !o || !rho) return MH3D_ERR_INVALID_ARG;
-    if (nvol == 0) return MH3D_OK;
     std::vector<Plan*> ps(nvol);
     for (int v = 0; v < nvol; ++v) {
         if (!plans[v]) return MH3D_ERR_INVALID_ARG;

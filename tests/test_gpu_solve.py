@@ -269,3 +269,35 @@ def test_tile_width_and_autotune_keep_results_bit_identical(monkeypatch):
     xt = torch.empty_like(x16)
     mh3d_solve(plan16, d, opts, xt)
     assert torch.equal(xt, x16)
+
+
+def test_zero_data_converges_at_once_to_zero():
+    """A^T d = 0: the zero start is the solution; the loop stops before the
+    first iteration with status OK and x = 0 (degenerate case)."""
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    p = params((32, 16, 8), s=2, kmin=2, kmax=5)
+    g = oracle_geom(p)
+    plan = gpu_plan(p, None)
+    d = torch.zeros(g.portrait_shape, dtype=torch.complex64, device="cuda")
+    x = torch.full(g.shape, 7.0, dtype=torch.float32, device="cuda")
+    for variant in (0, 1):
+        info = mh3d_solve(plan, d, make_opts(lam=1e-3, lam_relative=True, cg_variant=variant), x)
+        assert info["status"] == 0 and info["iters"] == 0, info
+        assert float(torch.abs(x).max()) == 0.0
+
+
+def test_batched_empty_and_single():
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve, mh3d_solve_batched
+
+    assert mh3d_solve_batched([], [], make_opts(lam=1e-3, lam_relative=True), []) == []
+    p = params((32, 16, 8), s=2, kmin=2, kmax=5)
+    g = oracle_geom(p)
+    plan = gpu_plan(p, sens_map(p))
+    d = _dev(W.random_portraits(g.portrait_shape, 21), torch.complex64)
+    o = make_opts(lam=1e-3, lam_relative=True, rel_tol=1e-4, max_iter=300)
+    xa = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    xb = torch.empty_like(xa)
+    ia = mh3d_solve(plan, d, o, xa)
+    ib = mh3d_solve_batched([plan], [d], o, [xb])[0]
+    assert ia["iters"] == ib["iters"] and torch.equal(xa, xb)
