@@ -137,7 +137,7 @@ static mh3d_status build_tables(Plan& P, cudaStream_t st)
 
     void* mem = nullptr;
     P.table_bytes = off * sizeof(float2);
-    if (cudaMalloc(&mem, P.table_bytes) != cudaSuccess) {
+    if (dev_malloc(&mem, P.table_bytes) != cudaSuccess) {
         P.err = "cudaMalloc of tables failed";
         return MH3D_ERR_OOM;
     }
@@ -175,6 +175,11 @@ TArgs tpass_args(const Plan& P, int axis /*1 = y, 2 = z*/, const float* in, floa
     a.vec2 = (P.nx % 2 == 0) ? 1 : 0;
     a.vec4 = (P.nx % 4 == 0 && ((uintptr_t)P.sens % 16) == 0) ? 1 : 0;
     a.status = P.w.flags ? P.w.flags + 3 : nullptr;
+    // Fault test (MH3D_DEBUG_WAIT_TIMEOUT=1): the tile barrier expects 16 bytes
+    // that no copy delivers, so its bounded wait runs out and records
+    // MH3D_ERR_TIMEOUT; every real copy has landed by then.
+    if (const char* e = std::getenv("MH3D_DEBUG_WAIT_TIMEOUT"))
+        if (e[0] == '1') a.debug_extra_tx = 16;
     a.axis = axis;
     if (axis == 1) {
         a.rp = P.ay.rp;
@@ -358,7 +363,7 @@ mh3d_status ensure_portrait(Plan& P)
 {
     if (P.w.portrait) return MH3D_OK;
     const size_t bytes = sizeof(float2) * (size_t)P.K * P.M;
-    if (cudaMalloc(&P.w.portrait, bytes) != cudaSuccess) {
+    if (dev_malloc(&P.w.portrait, bytes) != cudaSuccess) {
         P.w.portrait = nullptr;
         P.err = "cudaMalloc of the portrait buffer failed";
         return MH3D_ERR_OOM;
@@ -379,6 +384,7 @@ const char* mh3d_version(void) { return "mh3d-gb300 0.1 (sm_103a)"; }
 
 mh3d_status mh3d_plan_create(const mh3d_geometry* g, void* stream, mh3d_plan* out)
 {
+    alloc_counter() = 0;   // fault-test hook: count this creation's allocations
     if (!out) return MH3D_ERR_INVALID_ARG;
     *out = nullptr;
     if (!g) return MH3D_ERR_INVALID_ARG;

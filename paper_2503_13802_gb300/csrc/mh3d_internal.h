@@ -2,6 +2,7 @@
 #pragma once
 
 #include <atomic>
+#include <cstdlib>
 #include <complex>
 #include <string>
 #include <vector>
@@ -60,6 +61,35 @@ struct SolveWork {
     double* red_host = nullptr;   // pinned, red_cap doubles
     void* base = nullptr;         // one allocation backing the vectors
 };
+
+// Allocation hook for fault tests: with MH3D_DEBUG_FAIL_ALLOC=k the k-th
+// device or pinned-host allocation after the counter was last reset (at the
+// start of each plan creation, per thread) fails as out of memory, so every
+// clean-up path of plan creation can be exercised on the host side.
+inline int& alloc_counter()
+{
+    static thread_local int c = 0;
+    return c;
+}
+inline bool alloc_should_fail()
+{
+    const char* e = std::getenv("MH3D_DEBUG_FAIL_ALLOC");
+    if (!e) return false;
+    const int k = std::atoi(e);
+    return k > 0 && ++alloc_counter() == k;
+}
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes)
+{
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t host_malloc(T** p, size_t bytes)
+{
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+    return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
+}
 
 inline unsigned long long next_plan_serial()
 {

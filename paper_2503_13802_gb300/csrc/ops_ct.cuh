@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kT) k_tpass_ct(const __grid_constant__ TArgs a
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, TILEB * nt);
+        mbar_arrive_expect_tx(&bar, TILEB * nt + a.debug_extra_tx);
         for (int t = 0; t < nt; ++t) tma_load_3d(tiles + t * TILE, &a.tm.m[tmap[t]], x0, cy, cz, &bar);
     }
     // tables while the tile copies are in flight

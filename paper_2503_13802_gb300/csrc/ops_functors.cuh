@@ -67,6 +67,15 @@ __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, floa
     if (*(volatile int*)&c.flags[0]) return false;
     if (!first_kernel) return true;
     const int it = *(volatile int*)&c.flags[1];
+    if (*(volatile int*)&c.flags[3]) {   // a bounded wait gave up earlier: stop the loop
+        if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
+            c.flags[2] = MH3D_ERR_TIMEOUT;
+            __threadfence();
+            c.flags[0] = 1;
+            if (c.use_cond) cudaGraphSetConditional(c.cond, 0);
+        }
+        return false;
+    }
     const double g_new = __ldcg(c.rr_new);
     const double bn = __ldcg(c.bn);
     const double rel2 = (bn > 0.0) ? g_new / bn : 0.0;

@@ -75,6 +75,7 @@ struct TArgs {
     int vec2 = 1;                    // nx even: float2 global access
     int vec4 = 0;                    // nx % 4 == 0 and every vector 16-byte aligned: float4 access
     int* status = nullptr;           // device status word (bounded waits record timeouts here)
+    unsigned debug_extra_tx = 0;     // fault test only: bytes the tile barrier waits for that never arrive
     // CG fusions
     int pupdate = 0;                 // loader: 1 = p = r + beta p (written back), value = b p;
                                      //         2 = p = r + beta p, q = s + beta q, x += alpha p,

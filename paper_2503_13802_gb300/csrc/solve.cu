@@ -221,7 +221,7 @@ mh3d_status solve_alloc(Plan& P)
                                          tpass_blocks(P.nx, 8, tpass_outer(P, 1)), 1});
     w.red_cap = cap;
     const size_t bytes = sizeof(float) * vec * 8 + red_bytes(cap) + 64;
-    if (cudaMalloc(&w.base, bytes) != cudaSuccess) {
+    if (dev_malloc(&w.base, bytes) != cudaSuccess) {
         w.base = nullptr;
         P.err = "cudaMalloc of solver workspace failed";
         return MH3D_ERR_OOM;
@@ -237,9 +237,13 @@ mh3d_status solve_alloc(Plan& P)
     w.s = f + 7 * vec;
     w.red = (double*)(f + 8 * vec);
     if (cudaMemset(w.red, 0, red_bytes(cap)) != cudaSuccess) return MH3D_ERR_CUDA;
-    if (cudaMalloc(&w.flags, kNFlags * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
-    if (cudaMallocHost(&w.flags_host, kNFlags * sizeof(int)) != cudaSuccess) return MH3D_ERR_OOM;
-    if (cudaMallocHost(&w.red_host, std::max(cap, (size_t)16) * sizeof(double)) != cudaSuccess) return MH3D_ERR_OOM;
+    if (dev_malloc(&w.flags, kNFlags * sizeof(int)) != cudaSuccess ||
+        host_malloc(&w.flags_host, kNFlags * sizeof(int)) != cudaSuccess ||
+        host_malloc(&w.red_host, std::max(cap, (size_t)16) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        P.err = "allocation of the solver's flags or pinned scalars failed";
+        return MH3D_ERR_OOM;
+    }
     P.work_bytes = bytes + kNFlags * sizeof(int);
     return MH3D_OK;
 }
@@ -267,7 +271,7 @@ static mh3d_status ensure_hist(Plan& P, int cap)
     P.w.hist = nullptr;
     P.w.hist_cap = 0;
     const int c = std::max(cap, 1024);
-    if (cudaMalloc(&P.w.hist, sizeof(double) * c) != cudaSuccess) {
+    if (dev_malloc(&P.w.hist, sizeof(double) * c) != cudaSuccess) {
         P.err = "cudaMalloc of the residual history failed";
         return MH3D_ERR_OOM;
     }

@@ -63,6 +63,24 @@ class WarmStart:
     def get_params(self):
         return self.net.get_params()
 
+    def save(self, path: str):
+        """Writes the parameters (FP32), the channels and the grid to an .npz
+        file.  The Adam state is not kept: a reloaded network resumes
+        training with fresh moments."""
+        import numpy as np
+
+        np.savez(path, theta=self.get_params().cpu().numpy(), channels=np.array(self.channels),
+                 n=np.array(self.plan.n))
+
+    def load(self, path: str):
+        import numpy as np
+        import torch
+
+        z = np.load(path)
+        if tuple(int(c) for c in z["channels"]) != self.channels or tuple(int(v) for v in z["n"]) != tuple(self.plan.n):
+            raise ValueError(f"{path}: saved for channels {tuple(z['channels'])} and grid {tuple(z['n'])}")
+        self.set_params(torch.as_tensor(z["theta"], dtype=torch.float32).cuda())
+
     # -- training -----------------------------------------------------------
     def back_projection(self, d, out=None):
         out = self.rhs if out is None else out

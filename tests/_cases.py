@@ -51,4 +51,9 @@ OP_CASES = {
     "plane_2d": params((48, 36, 1), s=1, kmin=2, kmax=3, voxel=(0.5, 1.5, 1.0)),
     "tall_z": params((8, 3, 192), s=4, r=3, kmin=2, kmax=3),
     "long_x256": params((256, 4, 6), s=1, kmin=2, kmax=17, gammaA=1.0),
+    # the specialised lengths of the batched size classes (96 and 192 on
+    # every axis kind: drive with s = 2, transverse y and z)
+    "spec96": params((96, 96, 32), s=2, kmin=2, kmax=9),
+    "spec192": params((192, 192, 16), s=2, kmin=2, kmax=5, theta=[0.4, -0.9, 1.7, 2.2]),
+    "spec192_z": params((64, 32, 192), s=2, kmin=2, kmax=5),
 }

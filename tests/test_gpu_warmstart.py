@@ -82,3 +82,18 @@ def test_untrained_guess_is_rejected_or_helps():
         assert iw["iters"] == i0["iters"]
     else:
         assert iw["history"][0] < 1.0
+
+
+def test_save_and_load_reproduce_the_prediction(tmp_path):
+    from paper_2503_13802_gb300.warmstart import WarmStart
+
+    plan, opts, ws, portraits, rhs, tgt = _setup(n_train=2)
+    ws.fit(rhs, tgt, epochs=2, seed=1)
+    d = portraits(20002)
+    a = ws.predict(d).clone()
+    path = str(tmp_path / "ws.npz")
+    ws.save(path)
+    ws2 = WarmStart(plan, channels=ws.channels)
+    ws2.load(path)
+    b = ws2.predict(d)
+    assert torch.equal(a, b)
