@@ -34,6 +34,7 @@ struct XDesc {
     void (*fn)(XArgs) = nullptr;
     size_t smem = 0;
     int threads = kT;
+    int pairs = kP;
 };
 
 // P: column pairs (pencils) per CTA, 4 or 8 (tiles of 8 or 16 columns).
@@ -66,8 +67,10 @@ XDesc xdesc(int which)
 {
     if (which == 0) return XDesc{k_xfwd_ct<LFF, LIF, S>, xfwd_ct_smem<LFF, LIF, S>()};
     if (which == 1) return XDesc{k_xadj_ct<LFA, LIA, S>, xadj_ct_smem<LFA, LIA, S>()};
-    if (which == 3) return XDesc{k_xnrm_ct<LFN, S, true>, xnrm_ct_smem<LFN, S, true>(), kTN};
-    return XDesc{k_xnrm_ct<LFN, S, false>, xnrm_ct_smem<LFN, S, false>(), kTN};
+    if (which == 5) return XDesc{k_xadj_ct<LFA, LIA, S, true>, xadj_ct_smem<LFA, LIA, S, true>()};
+    if (which == 3) return XDesc{k_xnrm_ct<LFN, S, true>, xnrm_ct_smem<LFN, S, true>(), kTN, kP};
+    if (which == 4) return XDesc{k_xnrm_ct<LFN, S, false, 8, 128>, xnrm_ct_smem<LFN, S, false, 8>(), 128, 8};
+    return XDesc{k_xnrm_ct<LFN, S, false>, xnrm_ct_smem<LFN, S, false>(), kTN, kP};
 }
 
 XDesc xpass_desc(int nx, int s, int which /*0 forward, 1 adjoint, 2 normal, 3 normal with bulk copies*/)
@@ -201,7 +204,7 @@ cudaError_t ct_set_attributes(int optin)
         }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < 6; ++w) {
             const XDesc d = xpass_desc(p[0], p[1], w);
             cudaError_t e = opt_in(d.fn, d.smem, optin);
             if (e != cudaSuccess) return e;
@@ -228,13 +231,24 @@ cudaError_t run_tpass_ct(const TArgs& a0, int nouter, cudaStream_t st)
 static cudaError_t run_x_ct(const XArgs& a, int which, cudaStream_t st)
 {
     const XDesc d = xpass_desc(a.nx, a.s, which);
-    if (which >= 2) return launch_pdl(d.fn, dim3(xpass_blocks(a.rows, kP)), d.threads, d.smem, st, a);
-    d.fn<<<xpass_blocks(a.rows, kP), d.threads, d.smem, st>>>(a);
+    if (which >= 2 && which <= 4)
+        return launch_pdl(d.fn, dim3(xpass_blocks(a.rows, d.pairs)), d.threads, d.smem, st, a);
+    d.fn<<<xpass_blocks(a.rows, d.pairs), d.threads, d.smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t run_xfwd_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, 0, st); }
-cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, 1, st); }
+// The pipelined adjoint needs 16-byte aligned portrait blocks: an aligned
+// base, an even mx (rows of mx complex are then 16-byte multiples) and an
+// even M; MH3D_XADJ_BULK=0 turns it off (A/B checks).
+static bool xadj_bulk_ok(const XArgs& a)
+{
+    const char* e = std::getenv("MH3D_XADJ_BULK");
+    if (e && e[0] == '0') return false;
+    return al16(a.din) && (a.mx % 2) == 0 && (a.M % 2) == 0;
+}
+
+cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, xadj_bulk_ok(a) ? 5 : 1, st); }
 // The bulk-copy normal pass (opt-in: MH3D_XNRM_BULK=1; measured 3 % slower
 // per CG iteration than the register-loading pass at 128x128x64) needs
 // 16-byte aligned vectors (rows of nx floats are then 16-byte aligned too,
@@ -247,6 +261,18 @@ static bool xnrm_bulk_ok(const XArgs& a)
            (!a.b || al16(a.b));
 }
 
-cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, xnrm_bulk_ok(a) ? 3 : 2, st); }
+// 16 rows per CTA (512 CTAs at 128x128x64, 128 threads) by default: 35.3 us
+// per CG iteration against 35.7 us with 32 rows and 256 threads;
+// MH3D_XNRM_PAIRS=16 selects the latter (A/B checks).
+static bool xnrm_small()
+{
+    const char* e = std::getenv("MH3D_XNRM_PAIRS");
+    return !(e && e[0] == '1' && e[1] == '6');
+}
+
+cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st)
+{
+    return run_x_ct(a, xnrm_bulk_ok(a) ? 3 : (xnrm_small() ? 4 : 2), st);
+}
 
 }  // namespace mh3d

@@ -17,6 +17,8 @@
 //              and the inverse's first stage, in registers.
 #pragma once
 
+#include <type_traits>
+
 #include "bulk.cuh"
 #include "fft_ct.cuh"
 #include "ops_functors.cuh"
@@ -380,7 +382,34 @@ constexpr size_t xfwd_ct_smem()
 // X adjoint: LF2 = schedule of the length-mx forward transforms (one per
 // harmonic), LI = schedule of the length-nx inverse, first radix = LF2's
 // last times S.
-template <class LF2, class LI, int S>
+// Loader of the adjoint's first stage from a staged block of 2P portrait
+// rows [2P][mx] (one harmonic): pencil p packs Re(e^{-i theta} y) of rows
+// 2p and 2p + 1; rows at or beyond nrow read as zero.
+struct PortraitTileLd {
+    const float2* blk;
+    float2 ph;
+    int mx, nrow;
+    __device__ __forceinline__ float2 operator()(int m, int p) const
+    {
+        float2 o = make_float2(0.f, 0.f);
+        if (2 * p < nrow) {
+            const float2 y = blk[(2 * p) * mx + m];
+            o.x = fmaf(ph.x, y.x, ph.y * y.y);
+        }
+        if (2 * p + 1 < nrow) {
+            const float2 y = blk[(2 * p + 1) * mx + m];
+            o.y = fmaf(ph.x, y.x, ph.y * y.y);
+        }
+        return o;
+    }
+};
+
+// BULK: each harmonic's 2P portrait rows are one contiguous block; two
+// shared-memory buffers with one mbarrier each take the blocks of
+// harmonics k and k + 1 by 1D bulk copies, and a buffer is refilled with
+// harmonic k + 2 as soon as harmonic k's first stage has read it, so the
+// copies run under the transforms.
+template <class LF2, class LI, int S, bool BULK = false>
 __global__ void __launch_bounds__(kT) k_xadj_ct(const XArgs a)
 {
     using IF = RInfo<LF2>;
@@ -390,13 +419,30 @@ __global__ void __launch_bounds__(kT) k_xadj_ct(const XArgs a)
     constexpr int P = kP, T = kT;
     constexpr int NBL = MX / R;    // = NX / RI
     constexpr int ITERL = (NBL * P + T - 1) / T;
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ __align__(8) uint64_t bars[2];
     float2* tw = sm;               // W_NX^t; W_MX^t = tw[t S]
     float2* b0 = tw + NX;
     float2* b1 = b0 + NX * P;
+    float2* pb = b1 + NX * P;      // BULK: two [2P][MX] portrait blocks
+    const int row0 = blockIdx.x * 2 * P;
+    const int nrow = min(2 * P, a.rows - row0);
+    const uint32_t pbytes = (uint32_t)(nrow * MX * sizeof(float2));
+    if constexpr (BULK) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < a.K && k < 2; ++k) {
+                mbar_arrive_expect_tx(&bars[k], pbytes);
+                bulk_g2s(pb + k * 2 * P * MX, a.din + (long long)k * a.M + (long long)row0 * MX, pbytes, &bars[k]);
+            }
+    }
     for (int i = threadIdx.x; i < NX; i += T) tw[i] = a.twx[i];
     __syncthreads();
-    const int row0 = blockIdx.x * 2 * P;
     float2 acc[ITERL][RI];
 #pragma unroll
     for (int it = 0; it < ITERL; ++it)
@@ -405,7 +451,18 @@ __global__ void __launch_bounds__(kT) k_xadj_ct(const XArgs a)
     constexpr int pf = result_parity<0, NST2 - 1>();
     float2* fo = pf ? b1 : b0;
     for (int k = 0; k < a.K; ++k) {
-        const PortraitLd ld{a.din + (long long)k * a.M, a.phase + k, a.M, MX, row0, a.rows, P};
+        const int buf = k & 1;
+        if constexpr (BULK) {
+            // a copy that never lands would be a hardware fault: bounded wait
+            const bool ok = mbar_wait(&bars[buf], (uint32_t)((k >> 1) & 1), a.status);
+            if (!__syncthreads_and(ok)) return;
+        }
+        using LdT = typename std::conditional<BULK, PortraitTileLd, PortraitLd>::type;
+        LdT ld;
+        if constexpr (BULK)
+            ld = PortraitTileLd{pb + buf * 2 * P * MX, __ldg(a.phase + k), MX, nrow};
+        else
+            ld = PortraitLd{a.din + (long long)k * a.M, a.phase + k, a.M, MX, row0, a.rows, P};
         if constexpr (NST2 > 1) run_stages<LF2, 0, NST2 - 1, P, T, S, false, false, true>(ld, BufSt{fo, P}, b0, b1, P, tw);
         const float2* __restrict__ xk = a.Xhat + (long long)k * NX;
 #pragma unroll
@@ -425,6 +482,15 @@ __global__ void __launch_bounds__(kT) k_xadj_ct(const XArgs a)
             for (int r = 0; r < RI; ++r) acc[it][r] = c_add(acc[it][r], c_mulc(v[r % R], __ldg(xk + j + r * NBL)));
         }
         __syncthreads();
+        if constexpr (BULK) {
+            // harmonic k's block has been read (barrier above): refill it with k + 2
+            if (threadIdx.x == 0 && k + 2 < a.K) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[buf], pbytes);
+                bulk_g2s(pb + buf * 2 * P * MX, a.din + (long long)(k + 2) * a.M + (long long)row0 * MX, pbytes,
+                         &bars[buf]);
+            }
+        }
     }
     const RowPairSt st{a.vout, NX, row0, a.rows};
 #pragma unroll
@@ -443,11 +509,11 @@ __global__ void __launch_bounds__(kT) k_xadj_ct(const XArgs a)
     if constexpr (NSTI > 1) run_stages<LI, 1, NSTI, P, T, 1, true, true, false>(BufLd{b0, P}, st, b1, b0, P, tw);
 }
 
-template <class LF2, class LI, int S>
+template <class LF2, class LI, int S, bool BULK = false>
 constexpr size_t xadj_ct_smem()
 {
-    constexpr size_t nx = RInfo<LI>::n();
-    return sizeof(float2) * (nx + 2 * nx * kP);
+    constexpr size_t nx = RInfo<LI>::n(), mx = RInfo<LF2>::n();
+    return sizeof(float2) * (nx + 2 * nx * kP + (BULK ? 2 * 2 * kP * mx : 0));
 }
 
 // Storer into a row-major staging tile: pencil p's real part is tile row
@@ -577,14 +643,15 @@ __device__ __forceinline__ void nrm_epilogue_tile(const XArgs& a, int nrow, floa
 // contiguous block each, brought in by three 1D bulk copies on one
 // mbarrier while the twiddles load; q leaves the same way from the staging
 // tile.  Host conditions: 16-byte aligned vectors, R = I.
-template <class LF, int S, bool BULK>
-__global__ void __launch_bounds__(kTN) k_xnrm_ct(const XArgs a)
+// PP row pairs per CTA (2 PP rows), TT threads.
+template <class LF, int S, bool BULK, int PP = kP, int TT = kTN>
+__global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
 {
     using IF = RInfo<LF>;
     using LI = Reverse<LF>;
     constexpr int NX = IF::n(), NST = IF::nst, R = IF::last(), R2 = R / S, MX = NX / S;
     static_assert(R % S == 0, "alias blocks must sit in one butterfly");
-    constexpr int P = kP, T = kTN;
+    constexpr int P = PP, T = TT;
     constexpr int NBL = NX / R;
     constexpr int ITERL = (NBL * P + T - 1) / T;
     extern __shared__ __align__(16) float2 sm[];
@@ -691,11 +758,11 @@ __global__ void __launch_bounds__(kTN) k_xnrm_ct(const XArgs a)
     (void)MX;
 }
 
-template <class LF, int S, bool BULK = false>
+template <class LF, int S, bool BULK = false, int PP = kP>
 constexpr size_t xnrm_ct_smem()
 {
     constexpr size_t nx = RInfo<LF>::n();
-    return sizeof(float2) * (nx + 2 * nx * kP) + (BULK ? sizeof(float) * 3 * 2 * kP * nx : 0);
+    return sizeof(float2) * (nx + 2 * nx * PP) + (BULK ? sizeof(float) * 3 * 2 * PP * nx : 0);
 }
 
 }  // namespace ct

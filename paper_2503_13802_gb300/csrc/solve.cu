@@ -218,7 +218,8 @@ mh3d_status solve_alloc(Plan& P)
     const size_t vec = (N + 63) & ~size_t(63);
     // partial-sum slots for the widest grid any tile choice (8-column T pass) can launch
     const size_t cap = (size_t)std::max({update_blocks(P.N), normal_part_count(P, 0), normal_part_count(P, 1),
-                                         tpass_blocks(P.nx, 8, tpass_outer(P, 1)), 1});
+                                         tpass_blocks(P.nx, 8, tpass_outer(P, 1)),
+                                         xpass_blocks(P.ny * P.nz, 8), 1});
     w.red_cap = cap;
     const size_t bytes = sizeof(float) * vec * 8 + red_bytes(cap) + 64;
     if (dev_malloc(&w.base, bytes) != cudaSuccess) {

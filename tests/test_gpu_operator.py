@@ -17,19 +17,41 @@ torch = pytest.importorskip("torch")
 TOL = 1e-5
 
 
-@pytest.fixture(params=["specialised", "generic", "bulk"])
+@pytest.fixture(params=["specialised", "generic", "alternatives"])
 def kernel_path(request, monkeypatch):
     """Run each operator test on the compile-time specialised kernels (the
-    default for the common lengths), again with MH3D_GENERIC=1, which forces
-    the runtime-general kernels for every size, and with MH3D_XNRM_BULK=1,
-    the bulk-copy variant of the drive-axis normal pass."""
-    monkeypatch.delenv("MH3D_GENERIC", raising=False)
-    monkeypatch.delenv("MH3D_XNRM_BULK", raising=False)
+    default for the common lengths: pipelined drive-axis adjoint, 16-row
+    normal pass), again with MH3D_GENERIC=1, which forces the runtime-general
+    kernels for every size, and on the measured alternatives of the
+    specialised path: the bulk-copy normal pass, the 32-row normal pass and
+    the adjoint without copy pipelining."""
+    for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS"):
+        monkeypatch.delenv(v, raising=False)
     if request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
-    elif request.param == "bulk":
+    elif request.param == "alternatives":
         monkeypatch.setenv("MH3D_XNRM_BULK", "1")
+        monkeypatch.setenv("MH3D_XADJ_BULK", "0")
     return request.param
+
+
+@pytest.mark.parametrize("name", ["ds2_theta", "spec96", "cube32_k4"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_normal_32_row_pass_matches_oracle(name, mode, monkeypatch):
+    """The 32-row, 256-thread drive-axis normal pass (MH3D_XNRM_PAIRS=16)."""
+    monkeypatch.setenv("MH3D_XNRM_PAIRS", "16")
+    p = OP_CASES[name]
+    g = oracle_geom(p)
+    b = sens_map(p)
+    x = W.random_volume(g.shape, 301)
+    oo = oracle.SolveOpts(lam=2e-2, reg_kind=0)
+    ref = oracle.normal_apply(g, x, b, oo)
+    plan = gpu_plan(p, b)
+    from paper_2503_13802_gb300 import make_opts, mh3d_normal
+
+    q = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    mh3d_normal(plan, _dev(x, torch.float32), q, make_opts(lam=2e-2, normal_mode=mode))
+    assert rel_l2(q.cpu().numpy(), ref) <= TOL, rel_l2(q.cpu().numpy(), ref)
 
 
 def _dev(a, dtype):
