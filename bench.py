@@ -392,9 +392,21 @@ def cpu_baseline(wl: W.Workload, gpu_iters: int, sample_iters: int = 2):
     # cg() costs A^T d + one normal application for r0 + sample_iters iterations
     per_app = t / (sample_iters + 1.5)
     est = per_app * (gpu_iters + 2.5)
-    return {"value": 1.0 / est, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same on one host thread, one iteration (bounded sample)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=1), tables=tables)
+        t1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    est1 = t1 / 2.5 * (gpu_iters + 2.5)
+    return {"value": 1.0 / est, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"oracle CG, {sample_iters} iterations at {wl.n} K={wl.k_max - wl.k_min + 1} "
-                      f"({t:.1f} s), scaled to {gpu_iters} iterations + A^T d + true residual"}
+                      f"({t:.1f} s on {cores} threads), scaled to {gpu_iters} iterations + A^T d + true residual",
+            "one_thread": {"value": 1.0 / est1, "cores": 1,
+                           "sample": f"oracle CG, 1 iteration ({t1:.1f} s), scaled the same way"}}
 
 
 class CufftOperators:
