@@ -516,6 +516,7 @@ def bench_batched(args):
         seq.append(e0.elapsed_time(e1) / 1e3)
     iters = [inf["iters"] for inf in infos]
     worst = max(inf["rel_res_true"] for inf in infos)
+    cpu = None if args.no_cpu_baseline else batched_cpu_baseline(wl, sizes, iters)
     line = {
         "metric": "batched reconstructions/sec to rel. residual 1e-4", "value": value, "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -533,7 +534,41 @@ def bench_batched(args):
                               "ms": 1e3 * statistics.mean(seq)},
         "clocks": clk.summary(),
     }
+    if cpu:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
+
+
+def batched_cpu_baseline(wl, sizes, iters):
+    """The FP64 oracle on the host cores for the 64-volume workload: one
+    volume per size class (its first one), A^T d and one CG iteration,
+    scaled to that class's mean GPU iteration count; the batch estimate sums
+    the classes' per-volume times over their volume counts."""
+    import oracle
+
+    per_class, total = {}, 0.0
+    for c in W.BATCH_SIZE_CLASSES:
+        idx = [i for i, n in enumerate(sizes) if n == c]
+        if not idx:
+            continue
+        i = idx[0]
+        g = oracle.Geometry(n=c, voxel_mm=(1.0, 1.0, 1.0), ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max)
+        rho = W.phantom(c, (1.0, 1.0, 1.0), 1000 + i, wl.n_blobs, wl.n_lines)
+        b = W.sensitivity(c, (1.0, 1.0, 1.0), kind="gaussian")
+        tables = oracle.psf_tables(g)
+        clean = oracle.forward(g, rho, b, tables)
+        sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
+        d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, 1000 + i)
+        t0 = time.perf_counter()
+        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=1), tables=tables)
+        t = time.perf_counter() - t0
+        it = statistics.mean(iters[j] for j in idx)
+        vol_s = t / 2.5 * (it + 2.5)
+        per_class["x".join(map(str, c))] = {"seconds_per_volume": vol_s, "volumes": len(idx), "sample_s": t}
+        total += vol_s * len(idx)
+    return {"value": len(sizes) / total, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "one volume per size class, A^T d + 1 CG iteration, scaled to the class's mean "
+                      "GPU iteration count", "per_class": per_class}
 
 
 def bench_learned(args):
