@@ -68,6 +68,8 @@ XDesc xdesc(int which)
     if (which == 0) return XDesc{k_xfwd_ct<LFF, LIF, S>, xfwd_ct_smem<LFF, LIF, S>()};
     if (which == 1) return XDesc{k_xadj_ct<LFA, LIA, S>, xadj_ct_smem<LFA, LIA, S>()};
     if (which == 5) return XDesc{k_xadj_ct<LFA, LIA, S, true>, xadj_ct_smem<LFA, LIA, S, true>()};
+    if (which == 7)
+        return XDesc{k_xadj_ct<LFA, LIA, S, true, 8, 128>, xadj_ct_smem<LFA, LIA, S, true, 8>(), 128, 8};
     if (which == 3) return XDesc{k_xnrm_ct<LFN, S, true>, xnrm_ct_smem<LFN, S, true>(), kTN, kP};
     if (which == 4) return XDesc{k_xnrm_ct<LFN, S, false, 8, 128>, xnrm_ct_smem<LFN, S, false, 8>(), 128, 8};
     return XDesc{k_xnrm_ct<LFN, S, false>, xnrm_ct_smem<LFN, S, false>(), kTN, kP};
@@ -204,7 +206,8 @@ cudaError_t ct_set_attributes(int optin)
         }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
-        for (int w = 0; w < 6; ++w) {
+        for (int w = 0; w < 8; ++w) {
+            if (w == 6) continue;
             const XDesc d = xpass_desc(p[0], p[1], w);
             cudaError_t e = opt_in(d.fn, d.smem, optin);
             if (e != cudaSuccess) return e;
@@ -248,7 +251,17 @@ static bool xadj_bulk_ok(const XArgs& a)
     return al16(a.din) && (a.mx % 2) == 0 && (a.M % 2) == 0;
 }
 
-cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, xadj_bulk_ok(a) ? 5 : 1, st); }
+// MH3D_XADJ_PAIRS=8: 16 rows per CTA for the pipelined adjoint (A/B).
+static bool xadj_small()
+{
+    const char* e = std::getenv("MH3D_XADJ_PAIRS");
+    return e && e[0] == '8';
+}
+
+cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st)
+{
+    return run_x_ct(a, xadj_bulk_ok(a) ? (xadj_small() ? 7 : 5) : 1, st);
+}
 // The bulk-copy normal pass (opt-in: MH3D_XNRM_BULK=1; measured 3 % slower
 // per CG iteration than the register-loading pass at 128x128x64) needs
 // 16-byte aligned vectors (rows of nx floats are then 16-byte aligned too,

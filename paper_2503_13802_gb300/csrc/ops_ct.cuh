@@ -409,14 +409,14 @@ struct PortraitTileLd {
 // harmonics k and k + 1 by 1D bulk copies, and a buffer is refilled with
 // harmonic k + 2 as soon as harmonic k's first stage has read it, so the
 // copies run under the transforms.
-template <class LF2, class LI, int S, bool BULK = false>
-__global__ void __launch_bounds__(kT) k_xadj_ct(const XArgs a)
+template <class LF2, class LI, int S, bool BULK = false, int PP = kP, int TT = kT>
+__global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
 {
     using IF = RInfo<LF2>;
     using II = RInfo<LI>;
     constexpr int MX = IF::n(), NX = II::n(), NST2 = IF::nst, NSTI = II::nst, R = IF::last(), RI = II::first();
     static_assert(NX == MX * S && RI == R * S, "inconsistent X adjoint schedules");
-    constexpr int P = kP, T = kT;
+    constexpr int P = PP, T = TT;
     constexpr int NBL = MX / R;    // = NX / RI
     constexpr int ITERL = (NBL * P + T - 1) / T;
     extern __shared__ __align__(16) float2 sm[];
@@ -509,11 +509,11 @@ __global__ void __launch_bounds__(kT) k_xadj_ct(const XArgs a)
     if constexpr (NSTI > 1) run_stages<LI, 1, NSTI, P, T, 1, true, true, false>(BufLd{b0, P}, st, b1, b0, P, tw);
 }
 
-template <class LF2, class LI, int S, bool BULK = false>
+template <class LF2, class LI, int S, bool BULK = false, int PP = kP>
 constexpr size_t xadj_ct_smem()
 {
     constexpr size_t nx = RInfo<LI>::n(), mx = RInfo<LF2>::n();
-    return sizeof(float2) * (nx + 2 * nx * kP + (BULK ? 2 * 2 * kP * mx : 0));
+    return sizeof(float2) * (nx + 2 * nx * PP + (BULK ? 2 * 2 * PP * mx : 0));
 }
 
 // Storer into a row-major staging tile: pencil p's real part is tile row
