@@ -75,13 +75,13 @@ struct TTiles {
     static constexpr int kTile = N * P;   // float2 per tile
 };
 
-template <class L, int P>
-__global__ void __launch_bounds__(kT) k_tpass_ct(const __grid_constant__ TArgs a)
+template <class L, int P, int TT = kT>
+__global__ void __launch_bounds__(TT) k_tpass_ct(const __grid_constant__ TArgs a)
 {
     using I = RInfo<L>;
     constexpr int N = I::n(), NST = I::nst, RL = I::last();
     using LI = Reverse<L>;
-    constexpr int T = kT, TILE = N * P;
+    constexpr int T = TT, TILE = N * P;
     static_assert(NST >= 2, "the specialised T pass has at least two stages");
     extern __shared__ __align__(128) float2 sm_raw[];
     __shared__ double red[34];

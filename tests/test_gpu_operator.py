@@ -25,7 +25,7 @@ def kernel_path(request, monkeypatch):
     kernels for every size, and on the measured alternatives of the
     specialised path: the bulk-copy normal pass, the 32-row normal pass and
     the adjoint without copy pipelining."""
-    for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS"):
+    for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS"):
         monkeypatch.delenv(v, raising=False)
     if request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
@@ -33,6 +33,23 @@ def kernel_path(request, monkeypatch):
         monkeypatch.setenv("MH3D_XNRM_BULK", "1")
         monkeypatch.setenv("MH3D_XADJ_BULK", "0")
     return request.param
+
+
+@pytest.mark.parametrize("name", ["ds2_theta", "spec96", "spec192", "cube32_k4"])
+def test_adjoint_32_row_pipelined_pass_matches_oracle(name, monkeypatch):
+    """The 32-row pipelined drive-axis adjoint (MH3D_XADJ_PAIRS=16)."""
+    monkeypatch.setenv("MH3D_XADJ_PAIRS", "16")
+    p = OP_CASES[name]
+    g = oracle_geom(p)
+    b = sens_map(p)
+    y = W.random_portraits(g.portrait_shape, 202)
+    ref = oracle.adjoint(g, y, b)
+    plan = gpu_plan(p, b)
+    from paper_2503_13802_gb300 import mh3d_adjoint
+
+    rho = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    mh3d_adjoint(plan, _dev(y, torch.complex64), rho)
+    assert rel_l2(rho.cpu().numpy(), ref) <= TOL, rel_l2(rho.cpu().numpy(), ref)
 
 
 @pytest.mark.parametrize("name", ["ds2_theta", "spec96", "cube32_k4"])
