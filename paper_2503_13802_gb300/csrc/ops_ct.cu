@@ -75,6 +75,7 @@ template <int S, class LFF, class LIF, class LFA, class LIA, class LFN>
 XDesc xdesc(int which)
 {
     if (which == 0) return XDesc{k_xfwd_ct<LFF, LIF, S>, xfwd_ct_smem<LFF, LIF, S>()};
+    if (which == 6) return XDesc{k_xfwd_ct<LFF, LIF, S, 8, 128>, xfwd_ct_smem<LFF, LIF, S, 8>(), 128, 8};
     if (which == 1) return XDesc{k_xadj_ct<LFA, LIA, S>, xadj_ct_smem<LFA, LIA, S>()};
     if (which == 5) return XDesc{k_xadj_ct<LFA, LIA, S, true>, xadj_ct_smem<LFA, LIA, S, true>()};
     if (which == 7)
@@ -217,7 +218,6 @@ cudaError_t ct_set_attributes(int optin)
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
         for (int w = 0; w < 8; ++w) {
-            if (w == 6) continue;
             const XDesc d = xpass_desc(p[0], p[1], w);
             cudaError_t e = opt_in(d.fn, d.smem, optin);
             if (e != cudaSuccess) return e;
@@ -250,7 +250,14 @@ static cudaError_t run_x_ct(const XArgs& a, int which, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t run_xfwd_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, 0, st); }
+// MH3D_XFWD_PAIRS=8: 16 rows per CTA for the forward pass (A/B).
+static bool xfwd_small()
+{
+    const char* e = std::getenv("MH3D_XFWD_PAIRS");
+    return e && e[0] == '8';
+}
+
+cudaError_t run_xfwd_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, xfwd_small() ? 6 : 0, st); }
 // The pipelined adjoint needs 16-byte aligned portrait blocks: an aligned
 // base, an even mx (rows of mx complex are then 16-byte multiples) and an
 // even M; MH3D_XADJ_BULK=0 turns it off (A/B checks).

@@ -282,9 +282,10 @@ struct PortraitStK {
     const float2* __restrict__ phase;
     long long M;
     int mx, row0, rows, kn;
+    int P = kP;   // pencils per harmonic in the batch
     __device__ __forceinline__ void operator()(int m, int q, float2 val) const
     {
-        const int kk = q / kP, p = q - kk * kP;
+        const int kk = q / P, p = q - kk * P;
         if (kk >= kn) return;
         const float2 ph = __ldg(phase + kk);
         const int r = row0 + 2 * p;
@@ -296,14 +297,14 @@ struct PortraitStK {
 
 // X forward: LF = radix schedule of length nx, LI = schedule of the length
 // mx = nx / S inverse, whose first radix is LF's last divided by S.
-template <class LF, class LI, int S>
-__global__ void __launch_bounds__(kT) k_xfwd_ct(const XArgs a)
+template <class LF, class LI, int S, int PP = kP, int TT = kT>
+__global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
 {
     using IF = RInfo<LF>;
     using II = RInfo<LI>;
     constexpr int NX = IF::n(), MX = II::n(), NSTF = IF::nst, NSTI = II::nst, RL = IF::last(), R2 = II::first();
     static_assert(NX == MX * S && RL == R2 * S, "inconsistent X forward schedules");
-    constexpr int P = kP, T = kT, KG = kKG, PB = KG * P;
+    constexpr int P = PP, T = TT, KG = kKG, PB = KG * P;
     constexpr int NBL = NX / RL;   // = MX / R2
     constexpr int ITERL = (NBL * P + T - 1) / T;
     constexpr int BREG = 2 * NX * P, CREG = 2 * MX * PB;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(kT) k_xfwd_ct(const XArgs a)
     __syncthreads();   // the c buffers alias the forward scratch
     for (int k0 = 0; k0 < a.K; k0 += KG) {
         const int kn = min(KG, a.K - k0);
-        const PortraitStK pst{a.dout + (long long)k0 * a.M, a.phase + k0, a.M, MX, row0, a.rows, kn};
+        const PortraitStK pst{a.dout + (long long)k0 * a.M, a.phase + k0, a.M, MX, row0, a.rows, kn, P};
 #pragma unroll
         for (int kk = 0; kk < KG; ++kk) {
             const float2* __restrict__ xk = a.Xhat + (long long)(k0 + (kk < kn ? kk : 0)) * NX;
@@ -371,11 +372,11 @@ __global__ void __launch_bounds__(kT) k_xfwd_ct(const XArgs a)
     }
 }
 
-template <class LF, class LI, int S>
+template <class LF, class LI, int S, int PP = kP>
 constexpr size_t xfwd_ct_smem()
 {
     constexpr size_t nx = RInfo<LF>::n(), mx = RInfo<LI>::n();
-    constexpr size_t b = 2 * nx * kP, c = 2 * mx * kKG * kP;
+    constexpr size_t b = 2 * nx * PP, c = 2 * mx * kKG * PP;
     return sizeof(float2) * (nx + (b > c ? b : c));
 }
 
