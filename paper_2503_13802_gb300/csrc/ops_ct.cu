@@ -39,31 +39,25 @@ struct XDesc {
 };
 
 // P: column pairs (pencils) per CTA, 4 or 8 (tiles of 8 or 16 columns).
-// MH3D_TPASS_THREADS=256: 16-column tiles with 256 threads (A/B).
-static bool tpass_wide()
-{
-    const char* e = std::getenv("MH3D_TPASS_THREADS");
-    return e && e[0] == '2' && e[1] == '5' && e[2] == '6';
-}
-
+// (16-column tiles with 256 threads measured 41.8 us per CG iteration
+// against 35.1 us with 128 threads at 128x128x64; not instantiated.)
 template <class L>
-TDesc tdesc(int P, bool wide = false)
+TDesc tdesc(int P)
 {
     if (P == 4) return TDesc{k_tpass_ct<L, 4>, tpass_ct_smem<L, 4>()};
-    if (P == 8 && wide) return TDesc{k_tpass_ct<L, 8, 256>, tpass_ct_smem<L, 8>(), 256};
     if (P == 8) return TDesc{k_tpass_ct<L, 8>, tpass_ct_smem<L, 8>()};
     return TDesc{};
 }
 
-TDesc tpass_desc(int n, int P, bool wide = false)
+TDesc tpass_desc(int n, int P)
 {
     switch (n) {
-        case 32: return tdesc<RList<4, 8>>(P, wide);
-        case 64: return tdesc<RList<8, 8>>(P, wide);
-        case 96: return tdesc<RList<3, 4, 8>>(P, wide);
-        case 128: return tdesc<RList<16, 8>>(P, wide);
-        case 192: return tdesc<RList<3, 8, 8>>(P, wide);
-        case 256: return tdesc<RList<16, 16>>(P, wide);
+        case 32: return tdesc<RList<4, 8>>(P);
+        case 64: return tdesc<RList<8, 8>>(P);
+        case 96: return tdesc<RList<3, 4, 8>>(P);
+        case 128: return tdesc<RList<16, 8>>(P);
+        case 192: return tdesc<RList<3, 8, 8>>(P);
+        case 256: return tdesc<RList<16, 16>>(P);
         default: return TDesc{};
     }
 }
@@ -209,12 +203,11 @@ cudaError_t ct_set_attributes(int optin)
     tensor_map_encoder();
     static const int tn[] = {32, 64, 96, 128, 192, 256};
     for (int n : tn)
-        for (int P : {4, 8})
-            for (bool wide : {false, true}) {
-                const TDesc d = tpass_desc(n, P, wide);
-                cudaError_t e = opt_in(d.fn, d.smem, optin);
-                if (e != cudaSuccess) return e;
-            }
+        for (int P : {4, 8}) {
+            const TDesc d = tpass_desc(n, P);
+            cudaError_t e = opt_in(d.fn, d.smem, optin);
+            if (e != cudaSuccess) return e;
+        }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
         for (int w = 0; w < 8; ++w) {
@@ -236,7 +229,7 @@ cudaError_t run_tpass_ct(const TArgs& a0, int nouter, cudaStream_t st)
                     enc(kTmS, a.svec) && enc(kTmP, a.pvec) && enc(kTmQ, a.qdir) && enc(kTmX, a.xvec) &&
                     enc(kTmOut, a.epilogue ? a.qvec : a.out) && enc(kTmPin, a.pin);
     if (!ok) return cudaErrorInvalidValue;
-    const TDesc d = tpass_desc(a.n, a.cols / 2, tpass_wide());
+    const TDesc d = tpass_desc(a.n, a.cols / 2);
     dim3 grid((a.nx + a.cols - 1) / a.cols, nouter);
     return launch_pdl(d.fn, grid, d.threads, d.smem, st, a);
 }
