@@ -44,7 +44,7 @@ struct XDesc {
 template <class L>
 TDesc tdesc(int P)
 {
-    if (P == 4) return TDesc{k_tpass_ct<L, 4>, tpass_ct_smem<L, 4>()};
+    if (P == 4) return TDesc{k_tpass_ct<L, 4, 64>, tpass_ct_smem<L, 4>(), 64};   // 8-column tiles, 64 threads
     if (P == 8) return TDesc{k_tpass_ct<L, 8>, tpass_ct_smem<L, 8>()};
     return TDesc{};
 }
