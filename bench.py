@@ -53,6 +53,9 @@ def parse():
                     help="the 64-volume batched workload (one JSON line of its own)")
     ap.add_argument("--learned", action="store_true",
                     help="train the warm-start network and compare warm and zero starts (own JSON line)")
+    ap.add_argument("--mhad", action="store_true",
+                    help="MHAD image timing and the MHAD warm start against the zero start (own JSON line)")
+    ap.add_argument("--mhad-lambda", type=float, default=1e-2)
     ap.add_argument("--train-n", type=int, default=2000)
     ap.add_argument("--test-n", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=3)
@@ -666,6 +669,105 @@ def bench_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_mhad(args):
+    """MHAD (App. D, Eq. mhadM) on the 128x128x64, K = 8, s = 2 workload and
+    the test volumes of the learned warm start (seeds 20000 + i, same phantom
+    and noise recipe): (1) the native image alone, timed with CUDA events
+    over repeated calls with the L2 flushed between them (algorithmic bytes:
+    the K M complex64 portraits read, the N-float model-grid image written);
+    (2) per volume, zero-start CG against CG from the MHAD warm start
+    (image, / b, least-squares scale, then CG with the device-side
+    fallback), both to rel. residual 1e-4."""
+    import torch
+
+    from paper_2503_13802_gb300 import Plan, make_opts, mh3d_forward, mh3d_mhad, mh3d_mhad_warm_start, mh3d_solve
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = W.WORKLOADS[WORKLOAD]
+    b = W.sensitivity(wl.n, wl.voxel_mm, kind="gaussian")
+    plan = Plan(wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max, sensitivity=b)
+    opts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter)
+    stream = torch.cuda.current_stream()
+    lam_m = args.mhad_lambda
+
+    def portraits(seed):
+        rho, snr = W.learned_case(wl.n, wl.voxel_mm, seed)
+        d = torch.empty(plan.portrait_shape, dtype=torch.complex64, device=dev)
+        mh3d_forward(plan, torch.as_tensor(rho, dtype=torch.float32, device=dev).contiguous(), d)
+        sig2 = float(torch.sum(torch.abs(d.to(torch.complex128)) ** 2)) / (d.numel() * 10 ** (snr / 10))
+        gen = torch.Generator(device=dev).manual_seed(int(seed))
+        noise = torch.randn(d.shape, generator=gen, dtype=torch.complex64, device=dev)
+        return (d + math.sqrt(sig2) * noise).contiguous()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    test = W.LEARNED_TEST_SEEDS[:args.test_n]
+    tests = [portraits(sd) for sd in test]
+    x = torch.empty(plan.shape, dtype=torch.float32, device=dev)
+    x0 = torch.empty_like(x)
+    img = torch.empty(plan.N, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    for _ in range(5):
+        mh3d_mhad(plan, tests[0], lam_m, img, upsample=True)
+    us = []
+    for i in range(50):
+        flush.zero_()
+        _, t = timed(lambda: mh3d_mhad(plan, tests[i % len(tests)], lam_m, img, upsample=True))
+        us.append(1e6 * t)
+    us_img = float(np.median(us))
+    alg = plan.K * int(np.prod(plan.portrait_shape[1:])) * 8 + plan.N * 4
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+    except (OSError, ValueError):
+        peak = 6800.0
+
+    warm_opts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter, x0=x0,
+                          x0_fallback=True)
+
+    def warm(d):
+        mh3d_mhad_warm_start(plan, d, lam_m, x0)
+        return mh3d_solve(plan, d, warm_opts, x)
+
+    for d in tests[:3]:   # warm-up
+        mh3d_solve(plan, d, opts, x)
+        warm(d)
+    n0, n1, t0, t1, fb, r0 = [], [], [], [], 0, []
+    for d in tests:
+        i0, s0 = timed(lambda: mh3d_solve(plan, d, opts, x))
+        i1, s1 = timed(lambda: warm(d))
+        n0.append(i0["iters"])
+        n1.append(i1["iters"])
+        t0.append(s0)
+        t1.append(s1)
+        fb += int(i1["x0_rejected"])
+        r0.append(i1["history"][0])
+    ratio = np.array(t0) / np.array(t1)
+    m, sd = float(ratio.mean()), float(ratio.std(ddof=1)) if len(ratio) > 1 else 0.0
+    half = 1.972 * sd / math.sqrt(len(ratio))
+    line = {
+        "metric": "reconstructions/sec to rel. residual 1e-4 with MHAD warm start", "value": len(t1) / sum(t1),
+        "unit": UNIT, "n_gpus": 1, "steps": len(t1), "warmup": 3, "ms_per_step": 1e3 * float(np.mean(t1)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 tables, FP64 sums)",
+        "data": "synthetic", "config": {"workload": "learned_128x128x64_k8_s2 test volumes", "test_volumes": len(t1),
+                                        "mhad_lambda": lam_m},
+        "mhad_image": {"us": us_img, "alg_bytes": alg, "achieved_gbs": alg / us_img / 1e3,
+                       "frac": alg / us_img / 1e3 / peak, "l2": "flushed before each call"},
+        "zero_start": {"value": len(t0) / sum(t0), "mean_iters": float(np.mean(n0))},
+        "warm_start": {"mean_iters": float(np.mean(n1)), "fallback_rate": fb / len(t1),
+                       "median_initial_rel_res": float(np.median(r0))},
+        "speedup": {"mean": m, "ci95": [m - half, m + half], "per": "volume, zero-start time / warm-start time"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def bench_reference(args):
     """The FP64 oracle as the reference arm, rank 0 only."""
     ws, rank, _ = dist_env()
@@ -721,6 +823,8 @@ def main():
         bench_batched(args)
     elif args.learned:
         bench_learned(args)
+    elif args.mhad:
+        bench_mhad(args)
     else:
         bench_mh3d(args)
 

@@ -181,6 +181,44 @@ mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* con
  * forward model, Sec. 3.2 and 4.1).  Asynchronous on `stream`. */
 mh3d_status mh3d_plan_spectra(mh3d_plan plan, void* X, void* Y, void* Z, void* phase, void* stream);
 
+/* MHAD native image (App. D, Eq. mhadM), the paper's FFT-only closed-form
+ * reconstruction along the drive axis, computed for every portrait row:
+ *   rho_N = IDFT[ sum_k c_k^{-1} conj(DFT f^{k-1}) DFT(D_k) / (sum_k |DFT f^{k-1}|^2 + lambda) ]
+ * over the plan's harmonics k, with D_k = Re(e^{-i theta_k} d_k) (the
+ * portrait with its phase removed, Sec. 4.4), f the circular central
+ * difference of the portrait mesh ((f * u)[j] = u[j+1] - u[j-1]),
+ * c_k = (gamma A)^k / (k-1)! and DFTs of length mx = nx / ds_factor.
+ *   d_dev: K*nz*ny*mx complex64 portraits (device, the layout of
+ *   mh3d_forward).  lambda: the closed form's Tikhonov weight, finite and
+ *   > 0 (absolute; f is zero at DC and at the mesh's Nyquist bin, where
+ *   lambda alone keeps the quotient defined), else MH3D_ERR_INVALID_ARG.
+ *   upsample = 0: out_dev receives the image on the portrait mesh,
+ *   nz*ny*mx floats [nz][ny][mx].  upsample = 1: out_dev receives its
+ *   band-limited interpolation onto the model grid, N floats [nz][ny][nx]:
+ *   the drive-axis spectrum zero-padded from mx to nx bins (the mesh's
+ *   Nyquist bin split between +mx/2 and -mx/2), portrait row i' on model
+ *   row ds_factor i' + ds_offset, where it equals the upsample = 0 image.
+ *   The filter tables are built in FP64 on the host and cached in the plan
+ *   per (lambda, upsample); calls on one plan must be ordered on one stream.
+ *   Asynchronous on `stream` (the first call allocates K*max(nx, mx)
+ *   complex64 of tables). */
+mh3d_status mh3d_mhad(mh3d_plan plan, const void* d_dev, double lambda, int upsample, float* out_dev, void* stream);
+
+/* Warm start for mh3d_solve from the MHAD image: u = mh3d_mhad(upsample = 1)
+ * divided by the sensitivity b where b > 0 (0 where b <= 0; no division for
+ * a plan without b), then x0_dev = alpha u with alpha = Re<A u, d> /
+ * ||A u||^2, the least-squares scale of u on the data (A applied by the
+ * library, the two sums in FP64 on the device; alpha = 0 if A u = 0).
+ * The paper uses MHAD as an image, not as a starting point; this is the
+ * non-learned warm start compared with the learned one.
+ *   d_dev, lambda: as for mh3d_mhad; x0_dev: N floats (device), written.
+ *   alpha_dev: one double on the device receiving alpha, or NULL.
+ *   The first call allocates K*M complex64 of scratch portraits and 16 KiB
+ *   of partial sums, kept by the plan.  Uses the plan's workspace like
+ *   mh3d_forward.  Asynchronous on `stream`. */
+mh3d_status mh3d_mhad_warm_start(mh3d_plan plan, const void* d_dev, double lambda, float* x0_dev, double* alpha_dev,
+                                 void* stream);
+
 /* Tile autotuning: times the fused normal operator (the CG loop's kernels)
  * for each transverse-pass tile width (16 and 8 columns) on the plan's
  * workspace and keeps the fastest for this plan.  The choice is remembered

@@ -340,11 +340,11 @@ def apg(g: Geometry, d, tau: float, iters: int, b=None, opts: SolveOpts = SolveO
     return x
 
 
-def mhad(d_list, ck_list, lam: float, axis: int = -1) -> np.ndarray:
+def mhad(d_list, ck_list, lam: float, axis: int = -1, k_min: int = 2) -> np.ndarray:
     """MHAD native image (appendix MHAD, Eq. mhadM) along one axis.
 
-    d_list[k'] is the portrait of harmonic k = k'+2 (real), ck_list[k'] its
-    coefficient c_k.  With f = [0, -1, 0, ..., 0, 1] (so (f*u)[j] =
+    d_list[k'] is the portrait of harmonic k = k'+k_min (real), ck_list[k']
+    its coefficient c_k.  With f = [0, -1, 0, ..., 0, 1] (so (f*u)[j] =
     u[j+1] - u[j-1]) and f^{m} its m-fold self-convolution,
     rho_N = F^{-1}[ sum_k c_k^{-1} conj(F f^{k-1}) F d_k / (sum_k |F f^{k-1}|^2 + lambda) ].
     """
@@ -359,7 +359,7 @@ def mhad(d_list, ck_list, lam: float, axis: int = -1) -> np.ndarray:
     num = 0.0
     den = lam
     for j, (dk, c) in enumerate(zip(d_list, ck_list)):
-        k = j + 2
+        k = j + k_min
         fk = (fh ** (k - 1)).reshape(shape)
         num = num + np.conj(fk) * np.fft.fft(np.asarray(dk, dtype=np.float64), axis=axis) / c
         den = den + np.abs(fk) ** 2

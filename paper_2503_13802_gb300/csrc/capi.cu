@@ -490,6 +490,7 @@ mh3d_status mh3d_plan_destroy(mh3d_plan P)
     cudaDeviceSynchronize();
     batch_forget(*P);
     solve_free(*P);
+    mhad_free(*P);
     if (P->table_mem) cudaFree(P->table_mem);
     delete P;
     return MH3D_OK;

@@ -130,11 +130,22 @@ struct Plan {
     size_t work_bytes = 0;
     std::string err;
 
+    // MHAD native image (mhad.cu): filter tables cached per (lambda, upsample);
+    // warm-start scratch portraits and scale partials, allocated on first use
+    float2* mhad_tab = nullptr;
+    double mhad_lambda = -1.0;
+    int mhad_up = -1;
+    float2* mhad_scratch = nullptr;
+    double* mhad_red = nullptr;
+
     // CUDA graph of the CG loop, cached per (mode, reg, fixed) key
     cudaGraphExec_t graph_exec = nullptr;
     unsigned long long graph_key = ~0ull;
     cudaStream_t graph_stream = nullptr;
 };
+
+// mhad.cu
+void mhad_free(Plan& P);
 
 // psf_host.cpp
 double langevin_deriv_host(int k, double x);

@@ -250,7 +250,25 @@ static bool xfwd_small()
     return e && e[0] == '8';
 }
 
-cudaError_t run_xfwd_ct(const XArgs& a, cudaStream_t st) { return run_x_ct(a, xfwd_small() ? 6 : 0, st); }
+// Harmonics per CTA of the forward pass: all of them by default (13.5 us
+// per launch at 128x128x64, K = 8, against 15.4 us in groups of 4 and
+// 18.3 us in groups of 2 on grid.y); MH3D_XFWD_KPC=n sets groups of n.
+static int xfwd_kpc(int K)
+{
+    int kpc = 0;
+    if (const char* e = std::getenv("MH3D_XFWD_KPC")) kpc = std::atoi(e);
+    return (kpc <= 0 || kpc >= K) ? K : kpc;
+}
+
+cudaError_t run_xfwd_ct(const XArgs& a0, cudaStream_t st)
+{
+    XArgs a = a0;
+    a.kpc = xfwd_kpc(a.K);
+    const XDesc d = xpass_desc(a.nx, a.s, xfwd_small() ? 6 : 0);
+    const dim3 grid(xpass_blocks(a.rows, d.pairs), (a.K + a.kpc - 1) / a.kpc);
+    d.fn<<<grid, d.threads, d.smem, st>>>(a);
+    return cudaGetLastError();
+}
 // The pipelined adjoint needs 16-byte aligned portrait blocks: an aligned
 // base, an even mx (rows of mx complex are then 16-byte multiples) and an
 // even M; MH3D_XADJ_BULK=0 turns it off (A/B checks).

@@ -31,6 +31,22 @@ constexpr int kT = 128;   // threads per CTA
 constexpr int kTN = 256;  // threads per CTA of the X normal pass (one butterfly each per stage)
 constexpr int kKG = 2;    // harmonics per inverse batch in the X forward kernel
 
+// Pencil stride (float2) of a [element][pencil] shared buffer read or
+// written by a stage whose consecutive lanes take consecutive butterflies
+// j (NB per pencil) of a few pencils.  The 16 lanes of a half-warp then
+// span min(NB, 16) butterflies x 16 / min(NB, 16) pencils; with
+// ld = 16 / nb (mod 32 / nb) the butterflies' rows start 32 / nb banks
+// apart and every lane lands in its own bank.  Pencil-fast stages stay
+// conflict-free with any stride.
+constexpr int conflict_free_ld(int P, int NB)
+{
+    const int nb = NB < 16 ? NB : 16;
+    if (nb <= 1) return P;
+    int ld = P;
+    while (ld % (32 / nb) != 16 / nb) ++ld;
+    return ld;
+}
+
 // Forward last stage (radix R, Ns = N/R) -> per-element spectral multiplier
 // -> inverse first stage (radix R, Ns = 1), for P pencils.
 template <int N, int R, int P, int T, class LD, class ST>
@@ -295,8 +311,20 @@ struct PortraitStK {
     }
 };
 
+// Pencil stride of the X forward kernel's inverse buffers (KG * PP pencils;
+// the last inverse stage runs butterfly-fast).
+template <class LI, int PP>
+constexpr int xfwd_ldc()
+{
+    return conflict_free_ld(kKG * PP, RInfo<LI>::n() / RInfo<LI>::last());
+}
+
 // X forward: LF = radix schedule of length nx, LI = schedule of the length
 // mx = nx / S inverse, whose first radix is LF's last divided by S.
+// Harmonics split over grid.y in groups of a.kpc (0: one group); every
+// group recomputes the drive-axis spectrum of its rows, which costs one
+// more read of the (L2-resident) input per group and lets the portrait
+// stores of the groups run on more SMs at once.
 template <class LF, class LI, int S, int PP = kP, int TT = kT>
 __global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
 {
@@ -307,13 +335,14 @@ __global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
     constexpr int P = PP, T = TT, KG = kKG, PB = KG * P;
     constexpr int NBL = NX / RL;   // = MX / R2
     constexpr int ITERL = (NBL * P + T - 1) / T;
-    constexpr int BREG = 2 * NX * P, CREG = 2 * MX * PB;
+    constexpr int LDC = xfwd_ldc<LI, PP>();
+    constexpr int BREG = 2 * NX * P, CREG = 2 * MX * LDC;
     extern __shared__ float2 sm[];
     float2* tw = sm;                 // W_NX^t; W_MX^t = tw[t S]
     float2* b0 = tw + NX;
     float2* b1 = b0 + NX * P;
     float2* c0 = tw + NX;            // reused after the forward transform
-    float2* c1 = c0 + MX * PB;
+    float2* c1 = c0 + MX * LDC;
     (void)BREG;
     (void)CREG;
     for (int i = threadIdx.x; i < NX; i += T) tw[i] = a.twx[i];
@@ -339,8 +368,10 @@ __global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
         dft<RL, false>(F[it]);
     }
     __syncthreads();   // the c buffers alias the forward scratch
-    for (int k0 = 0; k0 < a.K; k0 += KG) {
-        const int kn = min(KG, a.K - k0);
+    const int kpc = a.kpc > 0 ? a.kpc : a.K;
+    const int kend = min(a.K, (int)blockIdx.y * kpc + kpc);
+    for (int k0 = (int)blockIdx.y * kpc; k0 < kend; k0 += KG) {
+        const int kn = min(KG, kend - k0);
         const PortraitStK pst{a.dout + (long long)k0 * a.M, a.phase + k0, a.M, MX, row0, a.rows, kn, P};
 #pragma unroll
         for (int kk = 0; kk < KG; ++kk) {
@@ -362,13 +393,13 @@ __global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
                 dft<R2, true>(G);
 #pragma unroll
                 for (int r2 = 0; r2 < R2; ++r2) {
-                    if constexpr (NSTI > 1) c0[(j * R2 + r2) * PB + kk * P + p] = G[r2];
+                    if constexpr (NSTI > 1) c0[(j * R2 + r2) * LDC + kk * P + p] = G[r2];
                     else pst(j * R2 + r2, kk * P + p, G[r2]);
                 }
             }
         }
         __syncthreads();
-        if constexpr (NSTI > 1) run_stages<LI, 1, NSTI, PB, T, S, true, true, false>(BufLd{c0, PB}, pst, c1, c0, PB, tw);
+        if constexpr (NSTI > 1) run_stages<LI, 1, NSTI, PB, T, S, true, true, false>(BufLd{c0, LDC}, pst, c1, c0, LDC, tw);
     }
 }
 
@@ -376,40 +407,68 @@ template <class LF, class LI, int S, int PP = kP>
 constexpr size_t xfwd_ct_smem()
 {
     constexpr size_t nx = RInfo<LF>::n(), mx = RInfo<LI>::n();
-    constexpr size_t b = 2 * nx * PP, c = 2 * mx * kKG * PP;
+    constexpr size_t b = 2 * nx * PP, c = 2 * mx * xfwd_ldc<LI, PP>();
     return sizeof(float2) * (nx + (b > c ? b : c));
 }
 
 // X adjoint: LF2 = schedule of the length-mx forward transforms (one per
 // harmonic), LI = schedule of the length-nx inverse, first radix = LF2's
 // last times S.
-// Loader of the adjoint's first stage from a staged block of 2P portrait
-// rows [2P][mx] (one harmonic): pencil p packs Re(e^{-i theta} y) of rows
-// 2p and 2p + 1; rows at or beyond nrow read as zero.
-struct PortraitTileLd {
+// Loader of the adjoint's first stage from a staged block of one harmonic's
+// portrait rows, mxs float2 apart: pencil p packs Re(e^{-i theta} y) of
+// rows p and p + P (rows at or beyond nrow read as zero).  With mxs = mx + 2
+// the rows of a half-warp's pencils start 4 banks apart, so the
+// pencil-fast first stage reads without bank conflicts.
+struct PortraitSplitLd {
     const float2* blk;
     float2 ph;
-    int mx, nrow;
+    int mxs, P, nrow;
     __device__ __forceinline__ float2 operator()(int m, int p) const
     {
         float2 o = make_float2(0.f, 0.f);
-        if (2 * p < nrow) {
-            const float2 y = blk[(2 * p) * mx + m];
+        if (p < nrow) {
+            const float2 y = blk[p * mxs + m];
             o.x = fmaf(ph.x, y.x, ph.y * y.y);
         }
-        if (2 * p + 1 < nrow) {
-            const float2 y = blk[(2 * p + 1) * mx + m];
+        if (p + P < nrow) {
+            const float2 y = blk[(p + P) * mxs + m];
             o.y = fmaf(ph.x, y.x, ph.y * y.y);
         }
         return o;
     }
 };
+// Output rows of that pairing: pencil p's real part is row row0 + p, its
+// imaginary part row row0 + p + P.
+struct RowSplitSt {
+    float* v;
+    int nx, row0, rows, P;
+    __device__ __forceinline__ void operator()(int e, int p, float2 val) const
+    {
+        const int r = row0 + p;
+        if (r < rows) v[(long long)r * nx + e] = val.x;
+        if (r + P < rows) v[(long long)(r + P) * nx + e] = val.y;
+    }
+};
 
-// BULK: each harmonic's 2P portrait rows are one contiguous block; two
-// shared-memory buffers with one mbarrier each take the blocks of
-// harmonics k and k + 1 by 1D bulk copies, and a buffer is refilled with
-// harmonic k + 2 as soon as harmonic k's first stage has read it, so the
-// copies run under the transforms.
+// Adjoint buffer geometry: pencil stride of the transform buffers (the last
+// inverse stage runs butterfly-fast) and row stride of the staged portrait
+// blocks.
+template <class LI, int PP>
+constexpr int xadj_ld()
+{
+    return conflict_free_ld(PP, RInfo<LI>::n() / RInfo<LI>::last());
+}
+template <class LF2>
+constexpr int xadj_mxs()
+{
+    return RInfo<LF2>::n() + 2;
+}
+
+// BULK: each harmonic's 2P portrait rows go to a shared-memory block, one
+// 1D bulk copy per row (rows padded to mx + 2 float2); two such buffers with
+// one mbarrier each take the blocks of harmonics k and k + 1, and a buffer
+// is refilled with harmonic k + 2 as soon as harmonic k's first stage has
+// read it, so the copies run under the transforms.
 template <class LF2, class LI, int S, bool BULK = false, int PP = kP, int TT = kT>
 __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
 {
@@ -420,15 +479,26 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
     constexpr int P = PP, T = TT;
     constexpr int NBL = MX / R;    // = NX / RI
     constexpr int ITERL = (NBL * P + T - 1) / T;
+    constexpr int LD = xadj_ld<LI, PP>();
+    constexpr int MXS = xadj_mxs<LF2>();
+    constexpr uint32_t ROWB = (uint32_t)(MX * sizeof(float2));
     extern __shared__ __align__(16) float2 sm[];
     __shared__ __align__(8) uint64_t bars[2];
     float2* tw = sm;               // W_NX^t; W_MX^t = tw[t S]
     float2* b0 = tw + NX;
-    float2* b1 = b0 + NX * P;
-    float2* pb = b1 + NX * P;      // BULK: two [2P][MX] portrait blocks
+    float2* b1 = b0 + NX * LD;
+    float2* pb = b1 + NX * LD;     // BULK: two [2P][MXS] portrait blocks
     const int row0 = blockIdx.x * 2 * P;
     const int nrow = min(2 * P, a.rows - row0);
-    const uint32_t pbytes = (uint32_t)(nrow * MX * sizeof(float2));
+    const uint32_t pbytes = (uint32_t)nrow * ROWB;
+    // warp 0 stages harmonic k's rows into buffer k & 1, one copy per row
+    auto stage_rows = [&](int k) {
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&bars[k & 1], pbytes);
+        __syncwarp();
+        const float2* src = a.din + (long long)k * a.M + (long long)row0 * MX;
+        for (int r = (int)threadIdx.x; r < nrow; r += 32)
+            bulk_g2s(pb + (k & 1) * 2 * P * MXS + r * MXS, src + (long long)r * MX, ROWB, &bars[k & 1]);
+    };
     if constexpr (BULK) {
         if (threadIdx.x == 0) {
             mbar_init(&bars[0], 1);
@@ -436,11 +506,8 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
             fence_barrier_init();
         }
         __syncthreads();
-        if (threadIdx.x == 0)
-            for (int k = 0; k < a.K && k < 2; ++k) {
-                mbar_arrive_expect_tx(&bars[k], pbytes);
-                bulk_g2s(pb + k * 2 * P * MX, a.din + (long long)k * a.M + (long long)row0 * MX, pbytes, &bars[k]);
-            }
+        if (threadIdx.x < 32)
+            for (int k = 0; k < a.K && k < 2; ++k) stage_rows(k);
     }
     for (int i = threadIdx.x; i < NX; i += T) tw[i] = a.twx[i];
     __syncthreads();
@@ -458,13 +525,14 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
             const bool ok = mbar_wait(&bars[buf], (uint32_t)((k >> 1) & 1), a.status);
             if (!__syncthreads_and(ok)) return;
         }
-        using LdT = typename std::conditional<BULK, PortraitTileLd, PortraitLd>::type;
+        using LdT = typename std::conditional<BULK, PortraitSplitLd, PortraitLd>::type;
         LdT ld;
         if constexpr (BULK)
-            ld = PortraitTileLd{pb + buf * 2 * P * MX, __ldg(a.phase + k), MX, nrow};
+            ld = PortraitSplitLd{pb + buf * 2 * P * MXS, __ldg(a.phase + k), MXS, P, nrow};
         else
             ld = PortraitLd{a.din + (long long)k * a.M, a.phase + k, a.M, MX, row0, a.rows, P};
-        if constexpr (NST2 > 1) run_stages<LF2, 0, NST2 - 1, P, T, S, false, false, true>(ld, BufSt{fo, P}, b0, b1, P, tw);
+        if constexpr (NST2 > 1)
+            run_stages<LF2, 0, NST2 - 1, P, T, S, false, false, true>(ld, BufSt{fo, LD}, b0, b1, LD, tw);
         const float2* __restrict__ xk = a.Xhat + (long long)k * NX;
 #pragma unroll
         for (int it = 0; it < ITERL; ++it) {
@@ -473,7 +541,7 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
             if ((NBL * P) % T != 0 && idx >= NBL * P) break;
             float2 v[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = (NST2 > 1) ? fo[(j + r * NBL) * P + p] : ld(j + r * NBL, p);
+            for (int r = 0; r < R; ++r) v[r] = (NST2 > 1) ? fo[(j + r * NBL) * LD + p] : ld(j + r * NBL, p);
             if (NBL > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw[r * j * S]);
@@ -484,16 +552,21 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
         }
         __syncthreads();
         if constexpr (BULK) {
-            // harmonic k's block has been read (barrier above): refill it with k + 2
-            if (threadIdx.x == 0 && k + 2 < a.K) {
+            // harmonic k's block has been read (barrier above): refill it
+            // with k + 2; each issuing lane orders the CTA's reads before
+            // its own async-proxy writes
+            if (threadIdx.x < 32 && k + 2 < a.K) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bars[buf], pbytes);
-                bulk_g2s(pb + buf * 2 * P * MX, a.din + (long long)(k + 2) * a.M + (long long)row0 * MX, pbytes,
-                         &bars[buf]);
+                stage_rows(k + 2);
             }
         }
     }
-    const RowPairSt st{a.vout, NX, row0, a.rows};
+    using StT = typename std::conditional<BULK, RowSplitSt, RowPairSt>::type;
+    StT st;
+    if constexpr (BULK)
+        st = RowSplitSt{a.vout, NX, row0, a.rows, P};
+    else
+        st = RowPairSt{a.vout, NX, row0, a.rows};
 #pragma unroll
     for (int it = 0; it < ITERL; ++it) {
         const int idx = (int)threadIdx.x + it * T;
@@ -502,19 +575,19 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
         dft<RI, true>(acc[it]);
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
-            if constexpr (NSTI > 1) b0[(j * RI + r) * P + p] = acc[it][r];
+            if constexpr (NSTI > 1) b0[(j * RI + r) * LD + p] = acc[it][r];
             else st(j * RI + r, p, acc[it][r]);
         }
     }
     __syncthreads();
-    if constexpr (NSTI > 1) run_stages<LI, 1, NSTI, P, T, 1, true, true, false>(BufLd{b0, P}, st, b1, b0, P, tw);
+    if constexpr (NSTI > 1) run_stages<LI, 1, NSTI, P, T, 1, true, true, false>(BufLd{b0, LD}, st, b1, b0, LD, tw);
 }
 
 template <class LF2, class LI, int S, bool BULK = false, int PP = kP>
 constexpr size_t xadj_ct_smem()
 {
-    constexpr size_t nx = RInfo<LI>::n(), mx = RInfo<LF2>::n();
-    return sizeof(float2) * (nx + 2 * nx * PP + (BULK ? 2 * 2 * PP * mx : 0));
+    constexpr size_t nx = RInfo<LI>::n();
+    return sizeof(float2) * (nx + 2 * nx * xadj_ld<LI, PP>() + (BULK ? 2 * 2 * PP * xadj_mxs<LF2>() : 0));
 }
 
 // Storer into a row-major staging tile: pencil p's real part is tile row
@@ -531,10 +604,11 @@ struct RowStageSt {
 
 // Normal-operator epilogue over a staged tile of ROWS rows:
 // q = b w + lambda R p, with p^T q (and p^T p) accumulated.
-template <int NX, int ROWS, int T>
+template <int NX, int ROWS, int T, int NXS = NX>
 __device__ __forceinline__ void nrm_epilogue(const XArgs& a, int row0, const float* __restrict__ stg, DotAcc* acc,
                                              DotAcc* acc2)
 {
+    static_assert(NXS % 4 == 0, "staged rows start on 16-byte boundaries");
     constexpr int V = NX / 4;
     constexpr int TOTAL = ROWS * V;
     constexpr int ITER = (TOTAL + T - 1) / T;
@@ -548,7 +622,7 @@ __device__ __forceinline__ void nrm_epilogue(const XArgs& a, int row0, const flo
             const int r = row0 + rr;
             if (r >= a.rows) continue;
             const long long i = (long long)r * NX + x;
-            const float w = stg[rr * NX + x];
+            const float w = stg[rr * NXS + x];
             float q = bp ? bp[i] * w : w;
             const int z = r / a.reg.ny, y = r - z * a.reg.ny;
             q += reg_term(a.reg, pp, i, x, y, z);
@@ -567,7 +641,7 @@ __device__ __forceinline__ void nrm_epilogue(const XArgs& a, int row0, const flo
         const int r = row0 + rr;
         if (((TOTAL % T) != 0 && idx >= TOTAL) || r >= a.rows) continue;
         const long long i = (long long)r * NX + 4 * c;
-        W[it] = *reinterpret_cast<const float4*>(stg + rr * NX + 4 * c);
+        W[it] = *reinterpret_cast<const float4*>(stg + rr * NXS + 4 * c);
         B[it] = bp ? __ldg(reinterpret_cast<const float4*>(bp + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
         Pv[it] = __ldg(reinterpret_cast<const float4*>(pp + i));
     }
@@ -596,6 +670,24 @@ __device__ __forceinline__ void nrm_epilogue(const XArgs& a, int row0, const flo
             acc2->add(Pv[it].w, Pv[it].w);
         }
     }
+}
+
+// X normal pass buffer geometry: the pencil stride of the transform
+// buffers (the last inverse stage runs butterfly-fast), and the row stride
+// of the staging tile, padded by 8 floats (rows 2p and 2p + 2 of one
+// half-warp's store then start 16 banks apart) where the padded tile still
+// fits in the buffer it overlays; the bulk-copy variant stores the tile
+// with one contiguous copy and keeps it unpadded.
+template <class LF, int PP>
+constexpr int xnrm_ld()
+{
+    return conflict_free_ld(PP, RInfo<LF>::n() / RInfo<LF>::first());
+}
+template <class LF, bool BULK, int PP>
+constexpr int xnrm_nxs()
+{
+    constexpr int nx = RInfo<LF>::n();
+    return (!BULK && PP * (nx + 8) <= nx * xnrm_ld<LF, PP>()) ? nx + 8 : nx;
 }
 
 // X normal: LF = schedule of length nx whose last radix is divisible by S;
@@ -655,6 +747,8 @@ __global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
     constexpr int P = PP, T = TT;
     constexpr int NBL = NX / R;
     constexpr int ITERL = (NBL * P + T - 1) / T;
+    constexpr int LD = xnrm_ld<LF, PP>();     // pencil stride of b0 / b1
+    constexpr int NXS = xnrm_nxs<LF, BULK, PP>();   // row stride of the staging tile
     extern __shared__ __align__(16) float2 sm[];
     __shared__ double red[34];
     __shared__ __align__(8) uint64_t bar;
@@ -664,8 +758,8 @@ __global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
     if (a.cg_active && !cg_enter(a.cg, false, &dummy, red)) return;
     float2* tw = sm;
     float2* b0 = tw + NX;
-    float2* b1 = b0 + NX * P;
-    float* tin = reinterpret_cast<float*>(b1 + NX * P);   // BULK: [2P][NX] tiles of v, b, p
+    float2* b1 = b0 + NX * LD;
+    float* tin = reinterpret_cast<float*>(b1 + NX * LD);   // BULK: [2P][NX] tiles of v, b, p
     float* tb = tin + 2 * P * NX;
     float* tp = tb + 2 * P * NX;
     const int row0 = blockIdx.x * 2 * P;
@@ -699,7 +793,7 @@ __global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
     constexpr int pf = result_parity<0, NST - 1>();
     float2* fo = pf ? b1 : b0;
     float2* fx = pf ? b0 : b1;
-    if constexpr (NST > 1) run_stages<LF, 0, NST - 1, P, T, 1, false, false, true>(ld, BufSt{fo, P}, b0, b1, P, tw);
+    if constexpr (NST > 1) run_stages<LF, 0, NST - 1, P, T, 1, false, false, true>(ld, BufSt{fo, LD}, b0, b1, LD, tw);
 #pragma unroll
     for (int it = 0; it < ITERL; ++it) {
         const int idx = (int)threadIdx.x + it * T;
@@ -707,7 +801,7 @@ __global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
         if ((NBL * P) % T != 0 && idx >= NBL * P) break;
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = (NST > 1) ? fo[(j + r * NBL) * P + p] : ld(j + r * NBL, p);
+        for (int r = 0; r < R; ++r) v[r] = (NST > 1) ? fo[(j + r * NBL) * LD + p] : ld(j + r * NBL, p);
         if (NBL > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw[r * j]);
@@ -726,14 +820,14 @@ __global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
         }
         dft<R, true>(g);
 #pragma unroll
-        for (int r = 0; r < R; ++r) fx[(j * R + r) * P + p] = g[r];
+        for (int r = 0; r < R; ++r) fx[(j * R + r) * LD + p] = g[r];
     }
     __syncthreads();
     // Last inverse stage into a row-major staging tile (2P rows x NX floats)
     // in the buffer that stage does not read, then the epilogue over the tile
     // with all of a thread's loads issued before its stores.
     float* stg = reinterpret_cast<float*>((NST % 2 == 0) ? fo : fx);
-    run_stages<LI, 1, NST, P, T, 1, true, true, false>(BufLd{fx, P}, RowStageSt{stg, NX}, fo, fx, P, tw);
+    run_stages<LI, 1, NST, P, T, 1, true, true, false>(BufLd{fx, LD}, RowStageSt{stg, NXS}, fo, fx, LD, tw);
     if constexpr (BULK) {
         nrm_epilogue_tile<NX, 2 * P, T>(a, nrow, stg, a.b ? tb : nullptr, tp, &dacc, a.part2 ? &dacc2 : nullptr);
         fence_proxy_async_smem();
@@ -744,7 +838,7 @@ __global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
             bulk_wait_all();   // the copy reads shared memory and must land before the CTA ends
         }
     } else {
-        nrm_epilogue<NX, 2 * P, T>(a, row0, stg, &dacc, a.part2 ? &dacc2 : nullptr);
+        nrm_epilogue<NX, 2 * P, T, NXS>(a, row0, stg, &dacc, a.part2 ? &dacc2 : nullptr);
     }
     if (a.part) {
         const double t = block_sum_f64(dacc.value(), red);
@@ -763,7 +857,7 @@ template <class LF, int S, bool BULK = false, int PP = kP>
 constexpr size_t xnrm_ct_smem()
 {
     constexpr size_t nx = RInfo<LF>::n();
-    return sizeof(float2) * (nx + 2 * nx * PP) + (BULK ? sizeof(float) * 3 * 2 * PP * nx : 0);
+    return sizeof(float2) * (nx + 2 * nx * xnrm_ld<LF, PP>()) + (BULK ? sizeof(float) * 3 * 2 * PP * nx : 0);
 }
 
 }  // namespace ct

@@ -116,6 +116,7 @@ struct XArgs {
     long long M = 1;                 // rows * mx
     int pairs = 16;                  // row pairs per CTA
     int kg = 4;                      // harmonics per transform batch
+    int kpc = 0;                     // specialised forward: harmonics per CTA (grid.y groups; 0: all)
     int vec4 = 0;                    // nx % 4 == 0 and every vector 16-byte aligned
     // normal-mode epilogue
     const float* b = nullptr;

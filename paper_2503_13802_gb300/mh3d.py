@@ -56,7 +56,8 @@ _lib = None
 
 EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoint", "mh3d_normal", "mh3d_solve",
            "mh3d_solve_host", "mh3d_solve_batched", "mh3d_forward_noalloc", "mh3d_operator_norm2", "mh3d_last_error",
-           "mh3d_plan_workspace_bytes", "mh3d_version", "mh3d_plan_autotune", "mh3d_plan_spectra"]
+           "mh3d_plan_workspace_bytes", "mh3d_version", "mh3d_plan_autotune", "mh3d_plan_spectra", "mh3d_mhad",
+           "mh3d_mhad_warm_start"]
 
 
 def library_path() -> str:
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = True):
     lib.mh3d_plan_autotune.argtypes = [P, P, POINTER(c_int)]
     lib.mh3d_plan_spectra.argtypes = [P, P, P, P, P, P]
     lib.mh3d_forward_noalloc.argtypes = [POINTER(mh3d_geometry), P, P, P]
+    lib.mh3d_mhad.argtypes = [P, P, c_double, c_int, P, P]
+    lib.mh3d_mhad_warm_start.argtypes = [P, P, c_double, P, P, P]
     lib.mh3d_last_error.argtypes = [P]
     lib.mh3d_last_error.restype = c_char_p
     lib.mh3d_plan_workspace_bytes.argtypes = [P]
@@ -337,6 +340,36 @@ def mh3d_forward_noalloc(n, rho, d, voxel_mm=(1.0, 1.0, 1.0), ds_factor: int = 1
     if st != MH3D_OK:
         raise MH3DError(st, "mh3d_forward_noalloc")
     return d
+
+
+def mh3d_mhad(plan: Plan, d, lam: float, out, upsample: bool = False, stream=None):
+    """MHAD native image of the portraits d (include/mh3d.h): out has
+    nz*ny*mx floats (upsample False) or N floats (True)."""
+    import torch
+
+    lib = load()
+    K, nz, ny, mx = plan.portrait_shape
+    p_d = _dev_ptr(d, torch.complex64, K * nz * ny * mx, "d")
+    p_o = _dev_ptr(out, torch.float32, plan.N if upsample else nz * ny * mx, "out")
+    _check(plan.handle, lib.mh3d_mhad(plan.handle, c_void_p(p_d), c_double(lam), c_int(1 if upsample else 0),
+                                      c_void_p(p_o), c_void_p(_stream_ptr(stream))))
+    return out
+
+
+def mh3d_mhad_warm_start(plan: Plan, d, lam: float, x0, alpha=None, stream=None):
+    """x0 = alpha * (upsampled MHAD image / b), alpha the least-squares
+    scale on the data; alpha (optional) is a float64 device tensor of one
+    element receiving it."""
+    import torch
+
+    lib = load()
+    K, nz, ny, mx = plan.portrait_shape
+    p_d = _dev_ptr(d, torch.complex64, K * nz * ny * mx, "d")
+    p_x = _dev_ptr(x0, torch.float32, plan.N, "x0")
+    p_a = _dev_ptr(alpha, torch.float64, 1, "alpha") if alpha is not None else None
+    _check(plan.handle, lib.mh3d_mhad_warm_start(plan.handle, c_void_p(p_d), c_double(lam), c_void_p(p_x),
+                                                 c_void_p(p_a), c_void_p(_stream_ptr(stream))))
+    return x0
 
 
 def mh3d_operator_norm2(plan: Plan) -> float:

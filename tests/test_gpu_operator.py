@@ -23,15 +23,19 @@ def kernel_path(request, monkeypatch):
     default for the common lengths: pipelined drive-axis adjoint, 16-row
     normal pass), again with MH3D_GENERIC=1, which forces the runtime-general
     kernels for every size, and on the measured alternatives of the
-    specialised path: the bulk-copy normal pass, the 32-row normal pass and
-    the adjoint without copy pipelining."""
-    for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS"):
+    specialised path: the bulk-copy normal pass, the adjoint without copy
+    pipelining, and the 16-row forward pass with uneven harmonic groups of
+    three per CTA."""
+    for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS",
+              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS"):
         monkeypatch.delenv(v, raising=False)
     if request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
     elif request.param == "alternatives":
         monkeypatch.setenv("MH3D_XNRM_BULK", "1")
         monkeypatch.setenv("MH3D_XADJ_BULK", "0")
+        monkeypatch.setenv("MH3D_XFWD_KPC", "3")
+        monkeypatch.setenv("MH3D_XFWD_PAIRS", "8")
     return request.param
 
 
