@@ -37,6 +37,7 @@ WORKLOAD = "mh_128x128x64_k8_s2"
 ORACLE_CG_ITERS = 83
 # DRAM bytes (read + write) of one CG iteration's three kernels, summed from
 # one ncu capture with cold L2 (ncu's default cache flush between kernels).
+TRAFFIC_PER_ITER_FUSED = None   # the fused T_z + normal pass: not yet captured
 TRAFFIC_PER_ITER = 42103808   # 25.22 MB T_y + 4.24 MB T_z + 12.64 MB X normal (mean of two iterations), writes stay in L2
 
 
@@ -65,6 +66,16 @@ def parse():
     ap.add_argument("--count-iters", action="store_true",
                     help="reference arm: run the oracle's CG to the tolerance once and print its iteration count")
     return ap.parse_args()
+
+
+def fused_zx(wl) -> bool:
+    """Whether the library runs T_z and the drive-axis normal pass as one
+    cluster launch for this workload (its instantiated (nx, nz, s) pairs,
+    unless MH3D_FUSE_ZX=0 or MH3D_GENERIC=1)."""
+    if os.environ.get("MH3D_FUSE_ZX", "1").startswith("0") or os.environ.get("MH3D_GENERIC", "0") not in ("", "0"):
+        return False
+    nx, _, nz = wl.n
+    return wl.ds_factor == 2 and (nx, nz) in ((128, 64), (64, 64), (96, 64), (192, 96))
 
 
 def dist_env():
@@ -331,7 +342,7 @@ def bench_mh3d(args):
     # kernels per solve: A^T d (3), CG init (1), s0 = N r0 (per_iter), the
     # graph loop (two iterations per body, every body launches all its
     # kernels), the true residual (per_iter + 1)
-    per_iter = 3 if args.mode == 0 else 6
+    per_iter = (2 if fused_zx(wl) else 3) if args.mode == 0 else 6
     launches_per_step = 3 + 1 + per_iter + per_iter * 2 * ((it_med + 1) // 2) + per_iter + 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -343,12 +354,15 @@ def bench_mh3d(args):
                    "normal_mode": "fused Fourier-block A^T A" if args.mode == 0 else "explicit A then A^T",
                    "cg_iters": it_med, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"kernel": "CG iteration = graph body (k_tpass_ct T_y + CG update, k_tpass_ct T_z, "
-                               "k_xnrm_ct)" if args.mode == 0 else "CG iteration, explicit A then A^T",
+        "roofline": {"kernel": ("CG iteration = graph body (k_tpass_ct T_y + CG update, k_zxnrm_ct T_z + "
+                                "drive-axis normal pass)" if fused_zx(wl) else
+                                "CG iteration = graph body (k_tpass_ct T_y + CG update, k_tpass_ct T_z, k_xnrm_ct)")
+                               if args.mode == 0 else "CG iteration, explicit A then A^T",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": TRAFFIC_PER_ITER if args.mode == 0 else None,
+                     "traffic": (TRAFFIC_PER_ITER_FUSED if fused_zx(wl) else TRAFFIC_PER_ITER)
+                                if args.mode == 0 else None,
                      "alg_bytes_per_launch": it_alg, "us_per_launch": it_s * 1e6,
-                     "design_bytes_per_iter": 17 * 4 * N,
+                     "design_bytes_per_iter": (15 if fused_zx(wl) else 17) * 4 * N,
                      "forward_A": {"us": fwd_s * 1e6, "alg_bytes": alg_bytes, "achieved_gbs": alg_bytes / fwd_s / 1e9,
                                    "frac": alg_bytes / fwd_s / 1e9 / peak},
                      "adjoint_AT": {"us": adj_s * 1e6, "alg_bytes": alg_bytes,

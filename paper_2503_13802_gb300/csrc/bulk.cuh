@@ -142,6 +142,31 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int
 // blocks until the previous grid has completed and its memory is visible.
 // Both are no-ops for kernels launched without the attribute.  Everything a
 // kernel reads that an earlier kernel writes must come after pdl_wait.
+// Thread-block clusters: this CTA's rank, a full cluster barrier (release /
+// acquire: shared-memory writes before it, local or remote, are visible to
+// every CTA of the cluster after it), and stores into another CTA's shared
+// memory through its shared::cluster address.
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_smem_addr(const void* p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 

@@ -295,6 +295,34 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
     if ((e = run_tpass(ty, tpass_outer(P, 1), st)) != cudaSuccess) return e;
     CgCtl cgp;
     if (cg) cgp = *cg;   // later kernels only check the done flag
+    auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+    if (mode == 0 && reg.kind == 0 && ct_zxnrm_available(P.nx, P.nz, P.s) && a16(t1) && a16(in) && a16(out) &&
+        (!P.sens || a16(P.sens))) {
+        // T_z and the drive-axis normal pass in one launch (clusters of two CTAs per y-slab)
+        ZXArgs z;
+        z.x = xpass_args(P);
+        z.x.b = P.sens;
+        z.x.pin = in;
+        z.x.qout = out;
+        if (dots) {
+            z.x.part = dots->part;
+            z.x.ticket = dots->ticket;
+            z.x.sum_out = dots->out;
+            z.x.part2 = dots->part2;
+            z.x.sum_out2 = dots->out2;
+        }
+        z.x.reg = reg;
+        if (cg) {
+            z.x.cg = cgp;
+            z.x.cg_active = 1;
+            z.x.count_iter = cg->cgcg;
+        }
+        z.twz = P.az.tw;
+        z.muz = P.Znorm;
+        z.ny = P.ny;
+        z.nz = P.nz;
+        return run_zxnrm_ct(z, t1, st);
+    }
     TArgs tz = tpass_args(P, 2, t1, t2, mode == 0 ? P.Znorm : P.Zhat);
     if (cg) tz.cg = cgp;
     if ((e = run_tpass(tz, tpass_outer(P, 2), st)) != cudaSuccess) return e;

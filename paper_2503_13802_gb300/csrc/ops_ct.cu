@@ -196,6 +196,28 @@ bool ct_tpass_available(const TArgs& a)
 }
 bool ct_xpass_available(int nx, int s, int pairs) { return !force_generic() && pairs == kP && xpass_desc(nx, s, 0).fn; }
 
+// Fused T_z + normal pass (k_zxnrm_ct), per (nx, nz, s): the z schedule
+// of the T pass and the drive-axis schedule of the normal pass.
+struct ZXDesc {
+    void (*fn)(ZXArgs) = nullptr;
+    size_t smem = 0;
+};
+template <class LZ, class LF, int S>
+ZXDesc zxdesc()
+{
+    constexpr int PZ = RInfo<LF>::n() / 4, PX = RInfo<LZ>::n() / 4;
+    return ZXDesc{k_zxnrm_ct<LZ, LF, S, PZ, PX, 256>, ZxGeom<LZ, LF, PZ, PX>::smem()};
+}
+ZXDesc zxnrm_desc(int nx, int nz, int s)
+{
+    if (s != 2) return ZXDesc{};
+    if (nx == 128 && nz == 64) return zxdesc<RList<8, 8>, RList<16, 8>, 2>();
+    if (nx == 64 && nz == 64) return zxdesc<RList<8, 8>, RList<8, 8>, 2>();
+    if (nx == 96 && nz == 64) return zxdesc<RList<8, 8>, RList<3, 4, 8>, 2>();
+    if (nx == 192 && nz == 96) return zxdesc<RList<3, 4, 8>, RList<3, 8, 8>, 2>();
+    return ZXDesc{};
+}
+
 cudaError_t ct_set_attributes(int optin)
 {
     // resolve the driver's encoder now: a first call inside a stream capture
@@ -208,6 +230,12 @@ cudaError_t ct_set_attributes(int optin)
             cudaError_t e = opt_in(d.fn, d.smem, optin);
             if (e != cudaSuccess) return e;
         }
+    static const int zx[][2] = {{128, 64}, {64, 64}, {96, 64}, {192, 96}};
+    for (const auto& p : zx) {
+        const ZXDesc d = zxnrm_desc(p[0], p[1], 2);
+        cudaError_t e = opt_in(d.fn, d.smem, optin);
+        if (e != cudaSuccess) return e;
+    }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
         for (int w = 0; w < 8; ++w) {
@@ -311,6 +339,29 @@ static bool xnrm_small()
 {
     const char* e = std::getenv("MH3D_XNRM_PAIRS");
     return !(e && e[0] == '1' && e[1] == '6');
+}
+
+// The fused T_z + normal pass for the instantiated (nx, nz, s);
+// MH3D_FUSE_ZX=0 keeps the separate T_z and normal passes (A/B checks).
+bool ct_zxnrm_available(int nx, int nz, int s)
+{
+    const char* e = std::getenv("MH3D_FUSE_ZX");
+    if (e && e[0] == '0') return false;
+    return !force_generic() && zxnrm_desc(nx, nz, s).fn && tensor_map_encoder();
+}
+
+// One cluster of two CTAs per y-slab; the z input's tensor map (box
+// nx/2 x 1 x nz, x coordinates 0 and nx/2: 16-byte multiples for nx % 8 == 0)
+// is encoded here.
+cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st)
+{
+    const int nx = a.x.nx;
+    if (nx % 8 != 0 || a.nz % 2 != 0 || !al16(zin)) return cudaErrorInvalidValue;
+    if (!encode_tile_map(&a.tz, zin, nx, a.ny, a.nz, 2, a.nz, nx / 2)) return cudaErrorInvalidValue;
+    const ZXDesc d = zxnrm_desc(nx, a.nz, a.x.s);
+    if (!d.fn) return cudaErrorInvalidValue;
+    d.fn<<<2 * a.ny, 256, d.smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st)

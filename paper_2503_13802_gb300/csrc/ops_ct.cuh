@@ -860,5 +860,226 @@ constexpr size_t xnrm_ct_smem()
     return sizeof(float2) * (nx + 2 * nx * xnrm_ld<LF, PP>()) + (BULK ? sizeof(float) * 3 * 2 * PP * nx : 0);
 }
 
+// ---------------------------------------------------------------------------
+// Fused T_z + drive-axis normal pass.  The normal operator's z and x steps
+// act on different axes, so one y-slab (nz rows of nx) carries all the data
+// both need.  A cluster of two CTAs takes one slab:
+//   phase 1: CTA c loads x-columns [c nx/2, (c+1) nx/2) of every z by one
+//            TMA box and runs the z-axis convolution on them (the T pass's
+//            stages, nx/4 column-pair pencils); the last inverse stage stores
+//            each row z straight into the exchange buffer of the CTA that owns
+//            it (rows [c' nz/2, (c'+1) nz/2) belong to CTA c'), locally or
+//            through distributed shared memory;
+//   cluster barrier;
+//   phase 2: CTA c runs the drive-axis normal pass (alias blocks, then
+//            q = b w + lambda p and the dot products) on its nz/2 full rows.
+// This removes the T_z launch and its round trip of the volume through L2.
+// Every CTA of a cluster passes both cluster barriers or neither (the
+// loop's done flag is the same for all), so no CTA waits on one that left.
+// Host conditions: R = I, 16-byte aligned vectors, nx % 8 == 0, nz even.
+
+// Stores of the z pass's last stage into the owners' exchange buffers:
+// element e = z, pencil p = columns x0 + 2p, x0 + 2p + 1.
+struct ZxExchangeSt {
+    float* xb;           // this CTA's exchange buffer [nz/2][nxp]
+    uint32_t peer;       // the other CTA's buffer (shared::cluster address)
+    int half, x0, rank, nxp;
+    __device__ __forceinline__ void operator()(int e, int p, float2 v) const
+    {
+        const int owner = e >= half ? 1 : 0;
+        const int o = (e - owner * half) * nxp + x0 + 2 * p;
+        if (owner == rank) {
+            xb[o] = v.x;
+            xb[o + 1] = v.y;
+        } else {
+            st_cluster_f32(peer + 4u * (uint32_t)o, v.x);
+            st_cluster_f32(peer + 4u * (uint32_t)(o + 1), v.y);
+        }
+    }
+};
+// Row pairs of the exchange buffer as the drive-axis pass's pencils.
+struct XbPairLd {
+    const float* xb;
+    int nxp;
+    __device__ __forceinline__ float2 operator()(int e, int p) const
+    {
+        return make_float2(xb[(2 * p) * nxp + e], xb[(2 * p + 1) * nxp + e]);
+    }
+};
+
+template <class LZ, class LF, int PZ, int PX>
+struct ZxGeom {
+    static constexpr int NZ = RInfo<LZ>::n(), NX = RInfo<LF>::n();
+    static constexpr int NXP = NX + 1;                  // exchange rows: odd stride, conflict-free pencil reads
+    static constexpr int LD = xnrm_ld<LF, PX>();        // drive-axis transform buffers
+    static constexpr int NXS = xnrm_nxs<LF, false, PX>();
+    static constexpr int TAB = 2 * NZ + NX;             // float2: W_nz, z multiplier, W_nx
+    static constexpr int XB = (NZ / 2) * NXP;           // floats
+    static constexpr int OFF = (TAB + (XB + 1) / 2 + 15) / 16 * 16;   // float2 offset of the union, 128-byte aligned
+    static constexpr int P1 = 2 * NZ * PZ;              // float2: tile + second buffer of the z pass
+    static constexpr int P2 = 2 * NX * LD;              // float2: the drive-axis buffers
+    static constexpr int UN = P1 > P2 ? P1 : P2;
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)(OFF + UN) + 128; }
+};
+
+template <class LZ, class LF, int S, int PZ, int PX, int TT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const __grid_constant__ ZXArgs a)
+{
+    using G = ZxGeom<LZ, LF, PZ, PX>;
+    constexpr int NZ = G::NZ, NX = G::NX, T = TT;
+    constexpr int NSTZ = RInfo<LZ>::nst, RLZ = RInfo<LZ>::last();
+    using LZI = Reverse<LZ>;
+    using IF = RInfo<LF>;
+    using LI = Reverse<LF>;
+    constexpr int NSTX = IF::nst, R = IF::last(), R2 = R / S;
+    constexpr int NBL = NX / R, ITERL = (NBL * PX + T - 1) / T;
+    constexpr int LD = G::LD, NXS = G::NXS, NXP = G::NXP, HALF = NZ / 2;
+    static_assert(R % S == 0, "alias blocks must sit in one butterfly");
+    static_assert(NX == 4 * PZ && NZ == 4 * PX, "pencil counts: nx/4 column pairs, nz/4 row pairs");
+    static_assert(NSTZ >= 2 && NSTX >= 2, "two stages at least on each axis");
+    extern __shared__ __align__(128) float2 zx_raw[];
+    __shared__ double red[34];
+    __shared__ __align__(8) uint64_t bar;
+    float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(zx_raw) + 127) & ~uintptr_t(127));
+    float2* twz = sm;
+    float2* muz = twz + NZ;
+    float2* twx = muz + NZ;
+    float* xb = reinterpret_cast<float*>(twx + NX);
+    float2* un = sm + G::OFF;           // 128-byte aligned: the TMA box lands at its start
+    const uint32_t rank = cluster_ctarank();
+    const int y = (int)blockIdx.x >> 1;
+    // every CTA of the cluster is running before any of them stores remotely
+    cluster_sync_all();
+    float dummy;
+    if (a.x.cg_active && !cg_enter(a.x.cg, false, &dummy, red)) return;
+
+    // ---- phase 1: z-axis convolution of this CTA's column half
+    float2* tile = un;
+    float2* zb = un + NZ * PZ;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (uint32_t)(NZ * PZ * sizeof(float2)));
+        tma_load_3d(tile, &a.tz, (int)rank * (NX / 2), y, 0, &bar);
+    }
+    for (int i = threadIdx.x; i < NZ; i += T) {
+        twz[i] = a.twz[i];
+        muz[i] = a.muz[i];
+    }
+    for (int i = threadIdx.x; i < NX; i += T) twx[i] = a.x.twx[i];
+    // a copy that never lands would be a hardware fault: the bounded wait
+    // records MH3D_ERR_TIMEOUT; the CTA still takes part in the cluster barrier
+    const bool ok = __syncthreads_and(mbar_wait(&bar, 0, a.x.status));
+    if (ok) {
+        constexpr int pf = result_parity<0, NSTZ - 1>();
+        float2* fo = pf ? tile : zb;
+        float2* fx = pf ? zb : tile;
+        run_stages<LZ, 0, NSTZ - 1, PZ, T, 1, false, true, true>(BufLd{tile, PZ}, BufSt{fo, PZ}, zb, tile, PZ, twz);
+        fused_conv_stage<NZ, RLZ, PZ, T>(BufLd{fo, PZ}, BufSt{fx, PZ}, muz, twz);
+        __syncthreads();
+        const ZxExchangeSt xs{xb, cluster_smem_addr(xb, rank ^ 1u), HALF, (int)rank * (NX / 2), (int)rank, NXP};
+        run_stages<LZI, 1, NSTZ, PZ, T, 1, true, true, true>(BufLd{fx, PZ}, xs, fo, fx, PZ, twz);
+    }
+    // both halves of every owned row have landed (local and remote stores)
+    cluster_sync_all();
+    if (!ok) return;
+
+    // ---- phase 2: drive-axis normal pass on rows z = rank nz/2 + rr
+    float2* b0 = un;
+    float2* b1 = b0 + NX * LD;
+    constexpr int pfx = result_parity<0, NSTX - 1>();
+    float2* fo = pfx ? b1 : b0;
+    float2* fx = pfx ? b0 : b1;
+    run_stages<LF, 0, NSTX - 1, PX, T, 1, false, false, true>(XbPairLd{xb, NXP}, BufSt{fo, LD}, b0, b1, LD, twx);
+#pragma unroll
+    for (int it = 0; it < ITERL; ++it) {
+        const int idx = (int)threadIdx.x + it * T;
+        const int p = idx % PX, j = idx / PX;
+        if ((NBL * PX) % T != 0 && idx >= NBL * PX) break;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = fo[(j + r * NBL) * LD + p];
+        if (NBL > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], twx[r * j]);
+        }
+        dft<R, false>(v);
+        float2 g[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int al = r / R2, rr = r - al * R2;
+            const int m = j + rr * NBL;
+            const float2* __restrict__ q = a.x.Q + ((long long)m * S + al) * S;
+            float2 sacc = c_mul(__ldg(q), v[rr]);
+#pragma unroll
+            for (int b = 1; b < S; ++b) sacc = c_add(sacc, c_mul(__ldg(q + b), v[rr + b * R2]));
+            g[r] = sacc;
+        }
+        dft<R, true>(g);
+#pragma unroll
+        for (int r = 0; r < R; ++r) fx[(j * R + r) * LD + p] = g[r];
+    }
+    __syncthreads();
+    float* stg = reinterpret_cast<float*>((NSTX % 2 == 0) ? fo : fx);
+    run_stages<LI, 1, NSTX, PX, T, 1, true, true, false>(BufLd{fx, LD}, RowStageSt{stg, NXS}, fo, fx, LD, twx);
+
+    // epilogue over the 2 PX staged rows; volume row of staged row rr:
+    // (rank nz/2 + rr) ny + y
+    constexpr int V = NX / 4, TOTAL = 2 * PX * V, ITER = (TOTAL + T - 1) / T;
+    const float* __restrict__ bp = a.x.b;
+    const float* __restrict__ pp = a.x.pin;
+    float* __restrict__ qp = a.x.qout;
+    const float lam = a.x.reg.lambda;
+    DotAcc dacc, dacc2;
+    float4 W[ITER], B[ITER], Pv[ITER];
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int idx = (int)threadIdx.x + it * T;
+        if ((TOTAL % T) != 0 && idx >= TOTAL) continue;
+        const int rr = idx / V, c = idx - rr * V;
+        const long long i = ((long long)((int)rank * HALF + rr) * a.ny + y) * NX + 4 * c;
+        W[it] = *reinterpret_cast<const float4*>(stg + rr * NXS + 4 * c);
+        B[it] = bp ? __ldg(reinterpret_cast<const float4*>(bp + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
+        Pv[it] = __ldg(reinterpret_cast<const float4*>(pp + i));
+    }
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int idx = (int)threadIdx.x + it * T;
+        if ((TOTAL % T) != 0 && idx >= TOTAL) continue;
+        const int rr = idx / V, c = idx - rr * V;
+        const long long i = ((long long)((int)rank * HALF + rr) * a.ny + y) * NX + 4 * c;
+        float4 q;
+        q.x = fmaf(B[it].x, W[it].x, lam * Pv[it].x);
+        q.y = fmaf(B[it].y, W[it].y, lam * Pv[it].y);
+        q.z = fmaf(B[it].z, W[it].z, lam * Pv[it].z);
+        q.w = fmaf(B[it].w, W[it].w, lam * Pv[it].w);
+        *reinterpret_cast<float4*>(qp + i) = q;
+        dacc.add(Pv[it].x, q.x);
+        dacc.add(Pv[it].y, q.y);
+        dacc.add(Pv[it].z, q.z);
+        dacc.add(Pv[it].w, q.w);
+        if (a.x.part2) {
+            dacc2.add(Pv[it].x, Pv[it].x);
+            dacc2.add(Pv[it].y, Pv[it].y);
+            dacc2.add(Pv[it].z, Pv[it].z);
+            dacc2.add(Pv[it].w, Pv[it].w);
+        }
+    }
+    if (a.x.part) {
+        const double t = block_sum_f64(dacc.value(), red);
+        if (a.x.part2) {
+            const double t2 = block_sum_f64(dacc2.value(), red);
+            grid_sum_finalize2(t, t2, a.x.part, a.x.part2, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out,
+                               a.x.sum_out2, red);
+        } else {
+            grid_sum_finalize(t, a.x.part, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out, red);
+        }
+    }
+    if (a.x.count_iter) cg_count_iteration(a.x.cg);
+}
+
 }  // namespace ct
 }  // namespace mh3d

@@ -134,6 +134,16 @@ struct XArgs {
     int* status = nullptr;           // device status word for bounded-wait timeouts
 };
 
+// Fused T_z + drive-axis normal pass: one y-slab per cluster of two CTAs
+// (ops_ct.cuh, k_zxnrm_ct).
+struct ZXArgs {
+    CUtensorMap tz;                  // the z-pass input (T_y output), box (nx/2 x 1 x nz)
+    XArgs x;                         // the normal pass; x.vin unused (rows come through the cluster)
+    const float2* twz = nullptr;     // W_nz^t
+    const float2* muz = nullptr;     // z-axis normal multiplier [nz]
+    int ny = 1, nz = 1;
+};
+
 // Shared-memory sizes in bytes.
 __host__ __forceinline__ size_t tpass_smem_bytes(int n, int cols)
 {
@@ -168,6 +178,9 @@ cudaError_t ct_set_attributes(int optin);
 cudaError_t run_tpass_ct(const TArgs& a, int nouter, cudaStream_t st);
 cudaError_t run_xfwd_ct(const XArgs& a, cudaStream_t st);
 cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st);
+// Fused T_z + normal pass where instantiated (false: use the two passes).
+bool ct_zxnrm_available(int nx, int nz, int s);
+cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st);
 cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st);
 int xpass_blocks(int rows, int pairs);
 cudaError_t ops_set_attributes();

@@ -56,4 +56,10 @@ OP_CASES = {
     "spec96": params((96, 96, 32), s=2, kmin=2, kmax=9),
     "spec192": params((192, 192, 16), s=2, kmin=2, kmax=5, theta=[0.4, -0.9, 1.7, 2.2]),
     "spec192_z": params((64, 32, 192), s=2, kmin=2, kmax=5),
+    # (nx, nz) pairs of the fused T_z + normal pass (one y-slab per cluster of
+    # two CTAs), with few y-slabs so the oracle stays fast
+    "zx128": params((128, 6, 64), s=2, kmin=2, kmax=9, theta=[0.2, -0.4, 0.9, 1.3, -2.0, 2.6, 0.0, -1.1]),
+    "zx64": params((64, 4, 64), s=2, kmin=2, kmax=5),
+    "zx96": params((96, 3, 64), s=2, r=1, kmin=2, kmax=9),
+    "zx192": params((192, 2, 96), s=2, kmin=2, kmax=5),
 }

@@ -24,10 +24,11 @@ def kernel_path(request, monkeypatch):
     normal pass), again with MH3D_GENERIC=1, which forces the runtime-general
     kernels for every size, and on the measured alternatives of the
     specialised path: the bulk-copy normal pass, the adjoint without copy
-    pipelining, and the 16-row forward pass with uneven harmonic groups of
-    three per CTA."""
+    pipelining, the 16-row forward pass with uneven harmonic groups of
+    three per CTA, and the separate T_z and normal passes instead of the
+    fused cluster pass."""
     for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS",
-              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS"):
+              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX"):
         monkeypatch.delenv(v, raising=False)
     if request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
@@ -36,6 +37,7 @@ def kernel_path(request, monkeypatch):
         monkeypatch.setenv("MH3D_XADJ_BULK", "0")
         monkeypatch.setenv("MH3D_XFWD_KPC", "3")
         monkeypatch.setenv("MH3D_XFWD_PAIRS", "8")
+        monkeypatch.setenv("MH3D_FUSE_ZX", "0")
     return request.param
 
 
