@@ -69,9 +69,10 @@ def parse():
 
 
 def fused_zx(wl) -> bool:
-    """Whether the library runs T_z and the drive-axis normal pass as one
-    cluster launch for this workload (its instantiated (nx, nz, s) pairs,
-    unless MH3D_FUSE_ZX=0 or MH3D_GENERIC=1)."""
+    """Whether the library runs T_z together with the drive-axis pass (normal,
+    forward and adjoint operators) as one cluster launch for this workload
+    (its instantiated (nx, nz, s) pairs, unless MH3D_FUSE_ZX=0 or
+    MH3D_GENERIC=1)."""
     if os.environ.get("MH3D_FUSE_ZX", "1").startswith("0") or os.environ.get("MH3D_GENERIC", "0") not in ("", "0"):
         return False
     nx, _, nz = wl.n
@@ -339,11 +340,12 @@ def bench_mh3d(args):
         other = {"mode": "explicit A then A^T (portrait through L2/HBM)", "value": 5 / sum(tt),
                  "iters": inf1["iters"]}
 
-    # kernels per solve: A^T d (3), CG init (1), s0 = N r0 (per_iter), the
-    # graph loop (two iterations per body, every body launches all its
-    # kernels), the true residual (per_iter + 1)
+    # kernels per solve: A^T d (3, or 2 with the fused adjoint pass), CG init
+    # (1), s0 = N r0 (per_iter), the graph loop (two iterations per body,
+    # every body launches all its kernels), the true residual (per_iter + 1)
     per_iter = (2 if fused_zx(wl) else 3) if args.mode == 0 else 6
-    launches_per_step = 3 + 1 + per_iter + per_iter * 2 * ((it_med + 1) // 2) + per_iter + 1
+    adj_launches = 2 if fused_zx(wl) else 3
+    launches_per_step = adj_launches + 1 + per_iter + per_iter * 2 * ((it_med + 1) // 2) + per_iter + 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",

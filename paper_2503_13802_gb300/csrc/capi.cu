@@ -247,6 +247,17 @@ cudaError_t launch_forward(const Plan& P, const float* rho, float2* d, float* t1
     TArgs ty = tpass_args(P, 1, rho, t1, P.Yhat);
     ty.bin = P.sens;
     if ((e = run_tpass(ty, tpass_outer(P, 1), st)) != cudaSuccess) return e;
+    if (ct_zxfwd_available(P.nx, P.nz, P.s) && ((uintptr_t)t1 & 15u) == 0) {
+        // T_z and the drive-axis forward in one launch (clusters of two CTAs per y-slab)
+        ZXArgs z;
+        z.x = xpass_args(P);
+        z.x.dout = d;
+        z.twz = P.az.tw;
+        z.muz = P.Zhat;
+        z.ny = P.ny;
+        z.nz = P.nz;
+        return run_zxfwd_ct(z, t1, st);
+    }
     TArgs tz = tpass_args(P, 2, t1, t2, P.Zhat);
     if ((e = run_tpass(tz, tpass_outer(P, 2), st)) != cudaSuccess) return e;
     XArgs x = xpass_args(P);
@@ -258,12 +269,26 @@ cudaError_t launch_forward(const Plan& P, const float* rho, float2* d, float* t1
 cudaError_t launch_adjoint(const Plan& P, const float2* d, float* rho, float* t1, float* t2, cudaStream_t st)
 {
     cudaError_t e;
-    XArgs x = xpass_args(P);
-    x.din = d;
-    x.vout = t1;
-    if ((e = run_xadj(x, st)) != cudaSuccess) return e;
-    TArgs tz = tpass_args(P, 2, t1, t2, P.Zhat_adj);
-    if ((e = run_tpass(tz, tpass_outer(P, 2), st)) != cudaSuccess) return e;
+    const bool fused = ct_xzadj_available(P.nx, P.nz, P.s) && ((uintptr_t)d & 15u) == 0 &&
+                       ((uintptr_t)t2 & 15u) == 0 && P.mx % 2 == 0 && P.M % 2 == 0;
+    if (fused) {
+        // the drive-axis adjoint and T_z^T in one launch (clusters of two CTAs per y-slab)
+        ZXArgs z;
+        z.x = xpass_args(P);
+        z.x.din = d;
+        z.twz = P.az.tw;
+        z.muz = P.Zhat_adj;
+        z.ny = P.ny;
+        z.nz = P.nz;
+        if ((e = run_xzadj_ct(z, t2, st)) != cudaSuccess) return e;
+    } else {
+        XArgs x = xpass_args(P);
+        x.din = d;
+        x.vout = t1;
+        if ((e = run_xadj(x, st)) != cudaSuccess) return e;
+        TArgs tz = tpass_args(P, 2, t1, t2, P.Zhat_adj);
+        if ((e = run_tpass(tz, tpass_outer(P, 2), st)) != cudaSuccess) return e;
+    }
     TArgs ty = tpass_args(P, 1, t2, rho, P.Yhat_adj);
     ty.bout = P.sens;
     return run_tpass(ty, tpass_outer(P, 1), st);

@@ -208,6 +208,42 @@ ZXDesc zxdesc()
     constexpr int PZ = RInfo<LF>::n() / 4, PX = RInfo<LZ>::n() / 4;
     return ZXDesc{k_zxnrm_ct<LZ, LF, S, PZ, PX, 256>, ZxGeom<LZ, LF, PZ, PX>::smem()};
 }
+// Fused T_z + drive-axis forward (k_zxfwd_ct): the z schedule, the forward
+// kernel's length-nx forward and length-nx/s inverse schedules.
+template <class LZ, class LF, class LI, int S>
+ZXDesc zxfdesc()
+{
+    constexpr int PZ = RInfo<LF>::n() / 4, PX = RInfo<LZ>::n() / 4;
+    return ZXDesc{k_zxfwd_ct<LZ, LF, LI, S, PZ, PX, 256>, ZxFwdGeom<LZ, LF, LI, PZ, PX>::smem()};
+}
+ZXDesc zxfwd_desc(int nx, int nz, int s)
+{
+    if (s != 2) return ZXDesc{};
+    if (nx == 128 && nz == 64) return zxfdesc<RList<8, 8>, RList<16, 8>, RList<4, 16>, 2>();
+    if (nx == 64 && nz == 64) return zxfdesc<RList<8, 8>, RList<8, 8>, RList<4, 8>, 2>();
+    if (nx == 96 && nz == 64) return zxfdesc<RList<8, 8>, RList<3, 4, 8>, RList<4, 4, 3>, 2>();
+    if (nx == 192 && nz == 96) return zxfdesc<RList<3, 4, 8>, RList<3, 8, 8>, RList<4, 8, 3>, 2>();
+    return ZXDesc{};
+}
+
+// Fused drive-axis adjoint + z correlation (k_xzadj_ct): the adjoint
+// kernel's length-nx/s forward and length-nx inverse schedules, the z one.
+template <class LF2, class LI, class LZ, int S>
+ZXDesc xzdesc()
+{
+    constexpr int PZ = RInfo<LI>::n() / 4, PX = RInfo<LZ>::n() / 4;
+    return ZXDesc{k_xzadj_ct<LF2, LI, LZ, S, PZ, PX, 256>, XzGeom<LF2, LI, LZ, PZ, PX>::smem()};
+}
+ZXDesc xzadj_desc(int nx, int nz, int s)
+{
+    if (s != 2) return ZXDesc{};
+    if (nx == 128 && nz == 64) return xzdesc<RList<8, 8>, RList<16, 8>, RList<8, 8>, 2>();
+    if (nx == 64 && nz == 64) return xzdesc<RList<4, 8>, RList<16, 4>, RList<8, 8>, 2>();
+    if (nx == 96 && nz == 64) return xzdesc<RList<3, 4, 4>, RList<8, 4, 3>, RList<8, 8>, 2>();
+    if (nx == 192 && nz == 96) return xzdesc<RList<3, 4, 8>, RList<16, 4, 3>, RList<3, 4, 8>, 2>();
+    return ZXDesc{};
+}
+
 ZXDesc zxnrm_desc(int nx, int nz, int s)
 {
     if (s != 2) return ZXDesc{};
@@ -235,6 +271,10 @@ cudaError_t ct_set_attributes(int optin)
         const ZXDesc d = zxnrm_desc(p[0], p[1], 2);
         cudaError_t e = opt_in(d.fn, d.smem, optin);
         if (e != cudaSuccess) return e;
+        const ZXDesc f = zxfwd_desc(p[0], p[1], 2);
+        if ((e = opt_in(f.fn, f.smem, optin)) != cudaSuccess) return e;
+        const ZXDesc g = xzadj_desc(p[0], p[1], 2);
+        if ((e = opt_in(g.fn, g.smem, optin)) != cudaSuccess) return e;
     }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
@@ -350,18 +390,45 @@ bool ct_zxnrm_available(int nx, int nz, int s)
     return !force_generic() && zxnrm_desc(nx, nz, s).fn && tensor_map_encoder();
 }
 
+bool ct_zxfwd_available(int nx, int nz, int s)
+{
+    const char* e = std::getenv("MH3D_FUSE_ZX");
+    if (e && e[0] == '0') return false;
+    return !force_generic() && zxfwd_desc(nx, nz, s).fn && tensor_map_encoder();
+}
+
 // One cluster of two CTAs per y-slab; the z input's tensor map (box
 // nx/2 x 1 x nz, x coordinates 0 and nx/2: 16-byte multiples for nx % 8 == 0)
 // is encoded here.
-cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st)
+static cudaError_t run_zx(ZXArgs& a, const float* zin, const ZXDesc& d, cudaStream_t st)
 {
     const int nx = a.x.nx;
-    if (nx % 8 != 0 || a.nz % 2 != 0 || !al16(zin)) return cudaErrorInvalidValue;
+    if (!d.fn || nx % 8 != 0 || a.nz % 2 != 0 || !al16(zin)) return cudaErrorInvalidValue;
     if (!encode_tile_map(&a.tz, zin, nx, a.ny, a.nz, 2, a.nz, nx / 2)) return cudaErrorInvalidValue;
-    const ZXDesc d = zxnrm_desc(nx, a.nz, a.x.s);
-    if (!d.fn) return cudaErrorInvalidValue;
     d.fn<<<2 * a.ny, 256, d.smem, st>>>(a);
     return cudaGetLastError();
+}
+cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st)
+{
+    return run_zx(a, zin, zxnrm_desc(a.x.nx, a.nz, a.x.s), st);
+}
+cudaError_t run_zxfwd_ct(ZXArgs& a, const float* zin, cudaStream_t st)
+{
+    return run_zx(a, zin, zxfwd_desc(a.x.nx, a.nz, a.x.s), st);
+}
+
+// The adjoint's fused pass needs the pipelined adjoint's conditions (16-byte
+// aligned portraits, even mx and M); its tensor map is that of the output.
+bool ct_xzadj_available(int nx, int nz, int s)
+{
+    const char* e = std::getenv("MH3D_FUSE_ZX");
+    if (e && e[0] == '0') return false;
+    return !force_generic() && xzadj_desc(nx, nz, s).fn && tensor_map_encoder();
+}
+cudaError_t run_xzadj_ct(ZXArgs& a, float* zout, cudaStream_t st)
+{
+    if (!al16(a.x.din) || (a.x.mx % 2) != 0 || (a.x.M % 2) != 0) return cudaErrorInvalidValue;
+    return run_zx(a, zout, xzadj_desc(a.x.nx, a.nz, a.x.s), st);
 }
 
 cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st)

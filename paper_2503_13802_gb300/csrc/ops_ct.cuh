@@ -298,16 +298,17 @@ struct PortraitStK {
     const float2* __restrict__ phase;
     long long M;
     int mx, row0, rows, kn;
-    int P = kP;   // pencils per harmonic in the batch
+    int P = kP;        // pencils per harmonic in the batch
+    int rstride = 1;   // portrait rows between a pencil's two rows (and between pencils: 2 rstride)
     __device__ __forceinline__ void operator()(int m, int q, float2 val) const
     {
         const int kk = q / P, p = q - kk * P;
         if (kk >= kn) return;
         const float2 ph = __ldg(phase + kk);
-        const int r = row0 + 2 * p;
+        const int r = row0 + 2 * p * rstride;
         float2* dk = d + (long long)kk * M;
         if (r < rows) dk[(long long)r * mx + m] = make_float2(ph.x * val.x, ph.y * val.x);
-        if (r + 1 < rows) dk[(long long)(r + 1) * mx + m] = make_float2(ph.x * val.y, ph.y * val.y);
+        if (r + rstride < rows) dk[(long long)(r + rstride) * mx + m] = make_float2(ph.x * val.y, ph.y * val.y);
     }
 };
 
@@ -319,36 +320,30 @@ constexpr int xfwd_ldc()
     return conflict_free_ld(kKG * PP, RInfo<LI>::n() / RInfo<LI>::last());
 }
 
-// X forward: LF = radix schedule of length nx, LI = schedule of the length
-// mx = nx / S inverse, whose first radix is LF's last divided by S.
-// Harmonics split over grid.y in groups of a.kpc (0: one group); every
-// group recomputes the drive-axis spectrum of its rows, which costs one
-// more read of the (L2-resident) input per group and lets the portrait
-// stores of the groups run on more SMs at once.
-template <class LF, class LI, int S, int PP = kP, int TT = kT>
-__global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
+// The drive-axis forward on 2P rows (LF = radix schedule of length nx, LI =
+// schedule of the length mx = nx / S inverse, whose first radix is LF's last
+// divided by S): the length-nx forward transform of the
+// rows (loader ld: pencil p packs rows 2p and 2p + 1), then per batch of kKG
+// harmonics in [kbeg, kend) the fold times X_k, the length-mx inverse, the
+// phase and the portrait store (pst: every field but d, phase and kn).
+// Shared memory: tw (W_nx, loaded) and a scratch region of
+// max(2 nx P, 2 mx ldc) float2.
+template <class LF, class LI, int S, int P, int T, class LD>
+__device__ __forceinline__ void xfwd_rows(const LD& ld, const XArgs& a, PortraitStK pst, int kbeg, int kend,
+                                          const float2* tw, float2* scratch)
 {
     using IF = RInfo<LF>;
     using II = RInfo<LI>;
     constexpr int NX = IF::n(), MX = II::n(), NSTF = IF::nst, NSTI = II::nst, RL = IF::last(), R2 = II::first();
     static_assert(NX == MX * S && RL == R2 * S, "inconsistent X forward schedules");
-    constexpr int P = PP, T = TT, KG = kKG, PB = KG * P;
+    constexpr int KG = kKG, PB = KG * P;
     constexpr int NBL = NX / RL;   // = MX / R2
     constexpr int ITERL = (NBL * P + T - 1) / T;
-    constexpr int LDC = xfwd_ldc<LI, PP>();
-    constexpr int BREG = 2 * NX * P, CREG = 2 * MX * LDC;
-    extern __shared__ float2 sm[];
-    float2* tw = sm;                 // W_NX^t; W_MX^t = tw[t S]
-    float2* b0 = tw + NX;
+    constexpr int LDC = xfwd_ldc<LI, P>();
+    float2* b0 = scratch;
     float2* b1 = b0 + NX * P;
-    float2* c0 = tw + NX;            // reused after the forward transform
+    float2* c0 = scratch;            // reused after the forward transform
     float2* c1 = c0 + MX * LDC;
-    (void)BREG;
-    (void)CREG;
-    for (int i = threadIdx.x; i < NX; i += T) tw[i] = a.twx[i];
-    __syncthreads();
-    const int row0 = blockIdx.x * 2 * P;
-    const RowPairLd ld{a.vin, NX, row0, a.rows};
     constexpr int pf = result_parity<0, NSTF - 1>();
     float2* fo = pf ? b1 : b0;
     if constexpr (NSTF > 1) run_stages<LF, 0, NSTF - 1, P, T, 1, false, false, true>(ld, BufSt{fo, P}, b0, b1, P, tw);
@@ -368,11 +363,11 @@ __global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
         dft<RL, false>(F[it]);
     }
     __syncthreads();   // the c buffers alias the forward scratch
-    const int kpc = a.kpc > 0 ? a.kpc : a.K;
-    const int kend = min(a.K, (int)blockIdx.y * kpc + kpc);
-    for (int k0 = (int)blockIdx.y * kpc; k0 < kend; k0 += KG) {
+    for (int k0 = kbeg; k0 < kend; k0 += KG) {
         const int kn = min(KG, kend - k0);
-        const PortraitStK pst{a.dout + (long long)k0 * a.M, a.phase + k0, a.M, MX, row0, a.rows, kn, P};
+        pst.d = a.dout + (long long)k0 * a.M;
+        pst.phase = a.phase + k0;
+        pst.kn = kn;
 #pragma unroll
         for (int kk = 0; kk < KG; ++kk) {
             const float2* __restrict__ xk = a.Xhat + (long long)(k0 + (kk < kn ? kk : 0)) * NX;
@@ -401,6 +396,24 @@ __global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
         __syncthreads();
         if constexpr (NSTI > 1) run_stages<LI, 1, NSTI, PB, T, S, true, true, false>(BufLd{c0, LDC}, pst, c1, c0, LDC, tw);
     }
+}
+
+// X forward over consecutive rows.  Harmonics split over grid.y in groups
+// of a.kpc (0: one group); every group recomputes the drive-axis spectrum of
+// its rows (one more read of the L2-resident input per group).
+template <class LF, class LI, int S, int PP = kP, int TT = kT>
+__global__ void __launch_bounds__(TT) k_xfwd_ct(const XArgs a)
+{
+    constexpr int NX = RInfo<LF>::n(), MX = RInfo<LI>::n(), P = PP, T = TT;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;                 // W_NX^t; W_MX^t = tw[t S]
+    for (int i = threadIdx.x; i < NX; i += T) tw[i] = a.twx[i];
+    __syncthreads();
+    const int row0 = blockIdx.x * 2 * P;
+    const int kpc = a.kpc > 0 ? a.kpc : a.K;
+    const int kbeg = (int)blockIdx.y * kpc, kend = min(a.K, kbeg + kpc);
+    const PortraitStK pst{nullptr, nullptr, a.M, MX, row0, a.rows, 0, P};
+    xfwd_rows<LF, LI, S, P, T>(RowPairLd{a.vin, NX, row0, a.rows}, a, pst, kbeg, kend, tw, tw + NX);
 }
 
 template <class LF, class LI, int S, int PP = kP>
@@ -469,35 +482,36 @@ constexpr int xadj_mxs()
 // one mbarrier each take the blocks of harmonics k and k + 1, and a buffer
 // is refilled with harmonic k + 2 as soon as harmonic k's first stage has
 // read it, so the copies run under the transforms.
-template <class LF2, class LI, int S, bool BULK = false, int PP = kP, int TT = kT>
-__global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
+// The drive-axis adjoint of 2P rows, portrait row rbase + r rstride for row
+// r of the CTA (r < nrow): per harmonic the length-mx forward transform of
+// Re(e^{-i theta_k} y_k), times conj(X_k) periodised to length nx, summed
+// over k in registers; then one length-nx inverse whose last stage goes to
+// `st` (element, pencil, value).  BULK pairs rows p and p + P in a pencil
+// (rows staged by 1D bulk copies); otherwise rows 2p and 2p + 1, read from
+// global memory (rstride 1).  Loads W_nx into tw.  Returns false if a bulk
+// copy's bounded wait gave up (MH3D_ERR_TIMEOUT recorded; the rest skipped).
+template <class LF2, class LI, int S, bool BULK, int P, int T, class ST>
+__device__ __forceinline__ bool xadj_rows(const XArgs& a, int rbase, int rstride, int nrow, const ST& st, float2* tw,
+                                          float2* b0, float2* b1, float2* pb, uint64_t* bars)
 {
     using IF = RInfo<LF2>;
     using II = RInfo<LI>;
     constexpr int MX = IF::n(), NX = II::n(), NST2 = IF::nst, NSTI = II::nst, R = IF::last(), RI = II::first();
     static_assert(NX == MX * S && RI == R * S, "inconsistent X adjoint schedules");
-    constexpr int P = PP, T = TT;
     constexpr int NBL = MX / R;    // = NX / RI
     constexpr int ITERL = (NBL * P + T - 1) / T;
-    constexpr int LD = xadj_ld<LI, PP>();
+    constexpr int LD = xadj_ld<LI, P>();
     constexpr int MXS = xadj_mxs<LF2>();
     constexpr uint32_t ROWB = (uint32_t)(MX * sizeof(float2));
-    extern __shared__ __align__(16) float2 sm[];
-    __shared__ __align__(8) uint64_t bars[2];
-    float2* tw = sm;               // W_NX^t; W_MX^t = tw[t S]
-    float2* b0 = tw + NX;
-    float2* b1 = b0 + NX * LD;
-    float2* pb = b1 + NX * LD;     // BULK: two [2P][MXS] portrait blocks
-    const int row0 = blockIdx.x * 2 * P;
-    const int nrow = min(2 * P, a.rows - row0);
     const uint32_t pbytes = (uint32_t)nrow * ROWB;
     // warp 0 stages harmonic k's rows into buffer k & 1, one copy per row
     auto stage_rows = [&](int k) {
         if (threadIdx.x == 0) mbar_arrive_expect_tx(&bars[k & 1], pbytes);
         __syncwarp();
-        const float2* src = a.din + (long long)k * a.M + (long long)row0 * MX;
+        const float2* src = a.din + (long long)k * a.M;
         for (int r = (int)threadIdx.x; r < nrow; r += 32)
-            bulk_g2s(pb + (k & 1) * 2 * P * MXS + r * MXS, src + (long long)r * MX, ROWB, &bars[k & 1]);
+            bulk_g2s(pb + (k & 1) * 2 * P * MXS + r * MXS, src + (long long)(rbase + r * rstride) * MX, ROWB,
+                     &bars[k & 1]);
     };
     if constexpr (BULK) {
         if (threadIdx.x == 0) {
@@ -523,14 +537,14 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
         if constexpr (BULK) {
             // a copy that never lands would be a hardware fault: bounded wait
             const bool ok = mbar_wait(&bars[buf], (uint32_t)((k >> 1) & 1), a.status);
-            if (!__syncthreads_and(ok)) return;
+            if (!__syncthreads_and(ok)) return false;
         }
         using LdT = typename std::conditional<BULK, PortraitSplitLd, PortraitLd>::type;
         LdT ld;
         if constexpr (BULK)
             ld = PortraitSplitLd{pb + buf * 2 * P * MXS, __ldg(a.phase + k), MXS, P, nrow};
         else
-            ld = PortraitLd{a.din + (long long)k * a.M, a.phase + k, a.M, MX, row0, a.rows, P};
+            ld = PortraitLd{a.din + (long long)k * a.M, a.phase + k, a.M, MX, rbase, a.rows, P};
         if constexpr (NST2 > 1)
             run_stages<LF2, 0, NST2 - 1, P, T, S, false, false, true>(ld, BufSt{fo, LD}, b0, b1, LD, tw);
         const float2* __restrict__ xk = a.Xhat + (long long)k * NX;
@@ -561,12 +575,6 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
             }
         }
     }
-    using StT = typename std::conditional<BULK, RowSplitSt, RowPairSt>::type;
-    StT st;
-    if constexpr (BULK)
-        st = RowSplitSt{a.vout, NX, row0, a.rows, P};
-    else
-        st = RowPairSt{a.vout, NX, row0, a.rows};
 #pragma unroll
     for (int it = 0; it < ITERL; ++it) {
         const int idx = (int)threadIdx.x + it * T;
@@ -581,6 +589,29 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
     }
     __syncthreads();
     if constexpr (NSTI > 1) run_stages<LI, 1, NSTI, P, T, 1, true, true, false>(BufLd{b0, LD}, st, b1, b0, LD, tw);
+    return true;
+}
+
+template <class LF2, class LI, int S, bool BULK = false, int PP = kP, int TT = kT>
+__global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
+{
+    constexpr int NX = RInfo<LI>::n(), P = PP;
+    constexpr int LD = xadj_ld<LI, PP>();
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ __align__(8) uint64_t bars[2];
+    float2* tw = sm;               // W_NX^t; W_MX^t = tw[t S]
+    float2* b0 = tw + NX;
+    float2* b1 = b0 + NX * LD;
+    float2* pb = b1 + NX * LD;     // BULK: two [2P][MXS] portrait blocks
+    const int row0 = blockIdx.x * 2 * P;
+    const int nrow = min(2 * P, a.rows - row0);
+    using StT = typename std::conditional<BULK, RowSplitSt, RowPairSt>::type;
+    StT st;
+    if constexpr (BULK)
+        st = RowSplitSt{a.vout, NX, row0, a.rows, P};
+    else
+        st = RowPairSt{a.vout, NX, row0, a.rows};
+    xadj_rows<LF2, LI, S, BULK, P, TT>(a, row0, 1, nrow, st, tw, b0, b1, pb, bars);
 }
 
 template <class LF2, class LI, int S, bool BULK = false, int PP = kP>
@@ -922,13 +953,54 @@ struct ZxGeom {
     static constexpr size_t smem() { return sizeof(float2) * (size_t)(OFF + UN) + 128; }
 };
 
+// Phase 1 of the y-slab cluster passes: the z-axis convolution (multiplier
+// mu) of this CTA's column half, every result row stored into its owner's
+// exchange buffer.  Loads the phase-2 twiddles (W_nx) while the TMA box is
+// in flight.  Returns whether the box landed; the caller takes the cluster
+// barrier either way.
+template <class LZ, int NX, int PZ, int T>
+__device__ __forceinline__ bool zx_zconv(const ZXArgs& a, const float2* __restrict__ mu_g, float2* twz, float2* muz,
+                                         float2* twx, float* xb, float2* un, uint64_t* bar, int y, uint32_t rank)
+{
+    constexpr int NZ = RInfo<LZ>::n(), NSTZ = RInfo<LZ>::nst, RLZ = RInfo<LZ>::last(), HALF = NZ / 2, NXP = NX + 1;
+    using LZI = Reverse<LZ>;
+    float2* tile = un;
+    float2* zb = un + NZ * PZ;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(NZ * PZ * sizeof(float2)));
+        tma_load_3d(tile, &a.tz, (int)rank * (NX / 2), y, 0, bar);
+    }
+    for (int i = threadIdx.x; i < NZ; i += T) {
+        twz[i] = a.twz[i];
+        muz[i] = mu_g[i];
+    }
+    for (int i = threadIdx.x; i < NX; i += T) twx[i] = a.x.twx[i];
+    // a copy that never lands would be a hardware fault: the bounded wait
+    // records MH3D_ERR_TIMEOUT
+    const bool ok = __syncthreads_and(mbar_wait(bar, 0, a.x.status));
+    if (ok) {
+        constexpr int pf = result_parity<0, NSTZ - 1>();
+        float2* fo = pf ? tile : zb;
+        float2* fx = pf ? zb : tile;
+        run_stages<LZ, 0, NSTZ - 1, PZ, T, 1, false, true, true>(BufLd{tile, PZ}, BufSt{fo, PZ}, zb, tile, PZ, twz);
+        fused_conv_stage<NZ, RLZ, PZ, T>(BufLd{fo, PZ}, BufSt{fx, PZ}, muz, twz);
+        __syncthreads();
+        const ZxExchangeSt xs{xb, cluster_smem_addr(xb, rank ^ 1u), HALF, (int)rank * (NX / 2), (int)rank, NXP};
+        run_stages<LZI, 1, NSTZ, PZ, T, 1, true, true, true>(BufLd{fx, PZ}, xs, fo, fx, PZ, twz);
+    }
+    return ok;
+}
+
 template <class LZ, class LF, int S, int PZ, int PX, int TT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const __grid_constant__ ZXArgs a)
 {
     using G = ZxGeom<LZ, LF, PZ, PX>;
     constexpr int NZ = G::NZ, NX = G::NX, T = TT;
-    constexpr int NSTZ = RInfo<LZ>::nst, RLZ = RInfo<LZ>::last();
-    using LZI = Reverse<LZ>;
     using IF = RInfo<LF>;
     using LI = Reverse<LF>;
     constexpr int NSTX = IF::nst, R = IF::last(), R2 = R / S;
@@ -936,7 +1008,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
     constexpr int LD = G::LD, NXS = G::NXS, NXP = G::NXP, HALF = NZ / 2;
     static_assert(R % S == 0, "alias blocks must sit in one butterfly");
     static_assert(NX == 4 * PZ && NZ == 4 * PX, "pencil counts: nx/4 column pairs, nz/4 row pairs");
-    static_assert(NSTZ >= 2 && NSTX >= 2, "two stages at least on each axis");
+    static_assert(RInfo<LZ>::nst >= 2 && NSTX >= 2, "two stages at least on each axis");
     extern __shared__ __align__(128) float2 zx_raw[];
     __shared__ double red[34];
     __shared__ __align__(8) uint64_t bar;
@@ -954,35 +1026,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
     if (a.x.cg_active && !cg_enter(a.x.cg, false, &dummy, red)) return;
 
     // ---- phase 1: z-axis convolution of this CTA's column half
-    float2* tile = un;
-    float2* zb = un + NZ * PZ;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, (uint32_t)(NZ * PZ * sizeof(float2)));
-        tma_load_3d(tile, &a.tz, (int)rank * (NX / 2), y, 0, &bar);
-    }
-    for (int i = threadIdx.x; i < NZ; i += T) {
-        twz[i] = a.twz[i];
-        muz[i] = a.muz[i];
-    }
-    for (int i = threadIdx.x; i < NX; i += T) twx[i] = a.x.twx[i];
-    // a copy that never lands would be a hardware fault: the bounded wait
-    // records MH3D_ERR_TIMEOUT; the CTA still takes part in the cluster barrier
-    const bool ok = __syncthreads_and(mbar_wait(&bar, 0, a.x.status));
-    if (ok) {
-        constexpr int pf = result_parity<0, NSTZ - 1>();
-        float2* fo = pf ? tile : zb;
-        float2* fx = pf ? zb : tile;
-        run_stages<LZ, 0, NSTZ - 1, PZ, T, 1, false, true, true>(BufLd{tile, PZ}, BufSt{fo, PZ}, zb, tile, PZ, twz);
-        fused_conv_stage<NZ, RLZ, PZ, T>(BufLd{fo, PZ}, BufSt{fx, PZ}, muz, twz);
-        __syncthreads();
-        const ZxExchangeSt xs{xb, cluster_smem_addr(xb, rank ^ 1u), HALF, (int)rank * (NX / 2), (int)rank, NXP};
-        run_stages<LZI, 1, NSTZ, PZ, T, 1, true, true, true>(BufLd{fx, PZ}, xs, fo, fx, PZ, twz);
-    }
+    const bool ok = zx_zconv<LZ, NX, PZ, T>(a, a.muz, twz, muz, twx, xb, un, &bar, y, rank);
     // both halves of every owned row have landed (local and remote stores)
     cluster_sync_all();
     if (!ok) return;
@@ -1079,6 +1123,140 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
         }
     }
     if (a.x.count_iter) cg_count_iteration(a.x.cg);
+}
+
+// The forward operator's last two steps, T_z then the drive-axis forward
+// (fold by s, phase, portrait store), for one y-slab per cluster of two
+// CTAs: phase 1 as in k_zxnrm_ct (multiplier Zhat), phase 2 the forward
+// pass on this CTA's nz/2 rows, whose portrait rows are ny apart.
+template <class LZ, class LF, class LI, int PZ, int PX>
+struct ZxFwdGeom {
+    using B = ZxGeom<LZ, LF, PZ, PX>;
+    static constexpr int NX = RInfo<LF>::n(), MX = RInfo<LI>::n();
+    static constexpr int F2 = 2 * NX * PX > 2 * MX * xfwd_ldc<LI, PX>() ? 2 * NX * PX : 2 * MX * xfwd_ldc<LI, PX>();
+    static constexpr int UN = B::P1 > F2 ? B::P1 : F2;
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)(B::OFF + UN) + 128; }
+};
+
+template <class LZ, class LF, class LI, int S, int PZ, int PX, int TT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxfwd_ct(const __grid_constant__ ZXArgs a)
+{
+    using G = ZxGeom<LZ, LF, PZ, PX>;
+    constexpr int NZ = G::NZ, NX = G::NX, MX = RInfo<LI>::n(), T = TT, HALF = NZ / 2;
+    static_assert(NX == 4 * PZ && NZ == 4 * PX, "pencil counts: nx/4 column pairs, nz/4 row pairs");
+    extern __shared__ __align__(128) float2 zf_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(zf_raw) + 127) & ~uintptr_t(127));
+    float2* twz = sm;
+    float2* muz = twz + NZ;
+    float2* twx = muz + NZ;
+    float* xb = reinterpret_cast<float*>(twx + NX);
+    float2* un = sm + G::OFF;
+    const uint32_t rank = cluster_ctarank();
+    const int y = (int)blockIdx.x >> 1;
+    cluster_sync_all();   // every CTA of the cluster runs before any remote store
+    const bool ok = zx_zconv<LZ, NX, PZ, T>(a, a.muz, twz, muz, twx, xb, un, &bar, y, rank);
+    cluster_sync_all();   // both halves of every owned row have landed
+    if (!ok) return;
+    const PortraitStK pst{nullptr, nullptr, a.x.M, MX, ((int)rank * HALF) * a.ny + y, a.x.rows, 0, PX, a.ny};
+    xfwd_rows<LF, LI, S, PX, T>(XbPairLd{xb, G::NXP}, a.x, pst, 0, a.x.K, twx, un);
+}
+
+// The adjoint operator's first two steps, the drive-axis adjoint then the
+// z-axis correlation (T_z^T), for one y-slab per cluster of two CTAs:
+//   phase 1: CTA c runs the drive-axis adjoint of rows z in
+//            [c nz/2, (c+1) nz/2) (portrait rows z ny + y, staged by per-row
+//            bulk copies); its last inverse stage stores each row's x-columns
+//            into the z-tile of the CTA that owns them (columns
+//            [c' nx/2, (c'+1) nx/2) belong to CTA c'), locally or through
+//            distributed shared memory;
+//   cluster barrier;
+//   phase 2: CTA c runs the z correlation on its nx/2 columns of every z and
+//            stores the result box with one TMA store.
+// Every CTA passes the cluster barrier, whether or not its copies landed.
+struct XzExchangeSt {
+    float* xt;           // this CTA's z-tile [nz][nx/2]
+    uint32_t peer;       // the other CTA's z-tile (shared::cluster address)
+    int half_x, z0, P, rank;
+    __device__ __forceinline__ void operator()(int e, int p, float2 v) const
+    {
+        const int owner = e >= half_x ? 1 : 0;
+        const int col = e - owner * half_x;
+        const int o1 = (z0 + p) * half_x + col, o2 = (z0 + p + P) * half_x + col;
+        if (owner == rank) {
+            xt[o1] = v.x;
+            xt[o2] = v.y;
+        } else {
+            st_cluster_f32(peer + 4u * (uint32_t)o1, v.x);
+            st_cluster_f32(peer + 4u * (uint32_t)o2, v.y);
+        }
+    }
+};
+
+template <class LF2, class LI, class LZ, int PZ, int PX>
+struct XzGeom {
+    static constexpr int NX = RInfo<LI>::n(), NZ = RInfo<LZ>::n();
+    static constexpr int TAB = NX + 2 * NZ;                       // float2: W_nx, W_nz, z multiplier
+    static constexpr int TABR = (TAB + 15) / 16 * 16;             // 128-byte aligned z-tile
+    static constexpr int XT = NZ * PZ;                            // float2: the z-tile
+    static constexpr int A1 = 2 * NX * xadj_ld<LI, PX>() + 2 * 2 * PX * xadj_mxs<LF2>();   // phase-1 buffers
+    static constexpr int UN = A1 > XT ? A1 : XT;                  // phase 2: the z pass's second buffer
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)(TABR + XT + UN) + 128; }
+};
+
+template <class LF2, class LI, class LZ, int S, int PZ, int PX, int TT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_xzadj_ct(const __grid_constant__ ZXArgs a)
+{
+    using G = XzGeom<LF2, LI, LZ, PZ, PX>;
+    constexpr int NX = G::NX, NZ = G::NZ, T = TT, HALF = NZ / 2;
+    constexpr int NSTZ = RInfo<LZ>::nst, RLZ = RInfo<LZ>::last();
+    using LZI = Reverse<LZ>;
+    constexpr int LD = xadj_ld<LI, PX>();
+    static_assert(NX == 4 * PZ && NZ == 4 * PX, "pencil counts: nx/4 column pairs, nz/4 row pairs");
+    static_assert(NSTZ >= 2, "two stages at least along z");
+    extern __shared__ __align__(128) float2 xz_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(xz_raw) + 127) & ~uintptr_t(127));
+    float2* tw = sm;
+    float2* twz = tw + NX;
+    float2* muz = twz + NZ;
+    float2* xt = sm + G::TABR;          // the z-tile [NZ][PZ], written by both CTAs of the cluster
+    float2* un = xt + G::XT;            // 128-byte aligned
+    const uint32_t rank = cluster_ctarank();
+    const int y = (int)blockIdx.x >> 1;
+    for (int i = threadIdx.x; i < NZ; i += T) {
+        twz[i] = a.twz[i];
+        muz[i] = a.muz[i];
+    }
+    cluster_sync_all();   // every CTA of the cluster runs before any remote store
+    // ---- phase 1: drive-axis adjoint of rows z = rank nz/2 + r
+    float2* b0 = un;
+    float2* b1 = b0 + NX * LD;
+    float2* pb = b1 + NX * LD;
+    float* xtf = reinterpret_cast<float*>(xt);
+    const XzExchangeSt st{xtf, cluster_smem_addr(xtf, rank ^ 1u), NX / 2, (int)rank * HALF, PX, (int)rank};
+    const bool ok = xadj_rows<LF2, LI, S, true, PX, T>(a.x, ((int)rank * HALF) * a.ny + y, a.ny, HALF, st, tw, b0,
+                                                       b1, pb, bars);
+    cluster_sync_all();   // every column of this CTA's z-tile has landed
+    if (!ok) return;
+    // ---- phase 2: z correlation of this CTA's columns, one TMA store
+    float2* tile = xt;
+    float2* zb = un;
+    constexpr int pf = result_parity<0, NSTZ - 1>();
+    float2* fo = pf ? tile : zb;
+    float2* fx = pf ? zb : tile;
+    run_stages<LZ, 0, NSTZ - 1, PZ, T, 1, false, true, true>(BufLd{tile, PZ}, BufSt{fo, PZ}, zb, tile, PZ, twz);
+    fused_conv_stage<NZ, RLZ, PZ, T>(BufLd{fo, PZ}, BufSt{fx, PZ}, muz, twz);
+    __syncthreads();
+    float2* stg = (NSTZ % 2 == 0) ? fo : fx;   // the buffer the last stage does not read
+    run_stages<LZI, 1, NSTZ, PZ, T, 1, true, true, true>(BufLd{fx, PZ}, BufSt{stg, PZ}, fo, fx, PZ, twz);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tma_store_3d(&a.tz, (int)rank * (NX / 2), y, 0, stg);
+        bulk_commit();
+        bulk_wait_all();   // the copy reads shared memory and must land before the CTA ends
+    }
 }
 
 }  // namespace ct

@@ -181,6 +181,12 @@ cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st);
 // Fused T_z + normal pass where instantiated (false: use the two passes).
 bool ct_zxnrm_available(int nx, int nz, int s);
 cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st);
+// Fused T_z + drive-axis forward where instantiated.
+bool ct_zxfwd_available(int nx, int nz, int s);
+cudaError_t run_zxfwd_ct(ZXArgs& a, const float* zin, cudaStream_t st);
+// Fused drive-axis adjoint + z correlation where instantiated (zout: its output).
+bool ct_xzadj_available(int nx, int nz, int s);
+cudaError_t run_xzadj_ct(ZXArgs& a, float* zout, cudaStream_t st);
 cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st);
 int xpass_blocks(int rows, int pairs);
 cudaError_t ops_set_attributes();
