@@ -196,62 +196,77 @@ bool ct_tpass_available(const TArgs& a)
 }
 bool ct_xpass_available(int nx, int s, int pairs) { return !force_generic() && pairs == kP && xpass_desc(nx, s, 0).fn; }
 
-// Fused T_z + normal pass (k_zxnrm_ct), per (nx, nz, s): the z schedule
-// of the T pass and the drive-axis schedule of the normal pass.
+// The y-slab cluster passes (k_zxnrm_ct, k_zxfwd_ct, k_xzadj_ct), per
+// (nx, nz, s) and cluster size C: C CTAs per y-slab, each with nz/C rows
+// of the drive-axis part and nx/C columns of the z part; 256 threads per CTA
+// for C = 2, 128 for C = 4.
 struct ZXDesc {
     void (*fn)(ZXArgs) = nullptr;
     size_t smem = 0;
+    int threads = 256;
+    int C = 2;
 };
-template <class LZ, class LF, int S>
+constexpr int zx_threads(int C) { return C == 2 ? 256 : 128; }
+
+// MH3D_ZX_CLUSTER=4: clusters of four CTAs (A/B checks); default two.
+static int zx_cluster()
+{
+    const char* e = std::getenv("MH3D_ZX_CLUSTER");
+    return (e && e[0] == '4') ? 4 : 2;
+}
+
+template <class LZ, class LF, int S, int C>
 ZXDesc zxdesc()
 {
-    constexpr int PZ = RInfo<LF>::n() / 4, PX = RInfo<LZ>::n() / 4;
-    return ZXDesc{k_zxnrm_ct<LZ, LF, S, PZ, PX, 256>, ZxGeom<LZ, LF, PZ, PX>::smem()};
+    constexpr int PZ = RInfo<LF>::n() / (2 * C), PX = RInfo<LZ>::n() / (2 * C), T = zx_threads(C);
+    return ZXDesc{k_zxnrm_ct<LZ, LF, S, C, PZ, PX, T>, ZxGeom<LZ, LF, C, PZ, PX>::smem(), T, C};
 }
-// Fused T_z + drive-axis forward (k_zxfwd_ct): the z schedule, the forward
-// kernel's length-nx forward and length-nx/s inverse schedules.
-template <class LZ, class LF, class LI, int S>
+template <class LZ, class LF, class LI, int S, int C>
 ZXDesc zxfdesc()
 {
-    constexpr int PZ = RInfo<LF>::n() / 4, PX = RInfo<LZ>::n() / 4;
-    return ZXDesc{k_zxfwd_ct<LZ, LF, LI, S, PZ, PX, 256>, ZxFwdGeom<LZ, LF, LI, PZ, PX>::smem()};
+    constexpr int PZ = RInfo<LF>::n() / (2 * C), PX = RInfo<LZ>::n() / (2 * C), T = zx_threads(C);
+    return ZXDesc{k_zxfwd_ct<LZ, LF, LI, S, C, PZ, PX, T>, ZxFwdGeom<LZ, LF, LI, C, PZ, PX>::smem(), T, C};
 }
-ZXDesc zxfwd_desc(int nx, int nz, int s)
-{
-    if (s != 2) return ZXDesc{};
-    if (nx == 128 && nz == 64) return zxfdesc<RList<8, 8>, RList<16, 8>, RList<4, 16>, 2>();
-    if (nx == 64 && nz == 64) return zxfdesc<RList<8, 8>, RList<8, 8>, RList<4, 8>, 2>();
-    if (nx == 96 && nz == 64) return zxfdesc<RList<8, 8>, RList<3, 4, 8>, RList<4, 4, 3>, 2>();
-    if (nx == 192 && nz == 96) return zxfdesc<RList<3, 4, 8>, RList<3, 8, 8>, RList<4, 8, 3>, 2>();
-    return ZXDesc{};
-}
-
-// Fused drive-axis adjoint + z correlation (k_xzadj_ct): the adjoint
-// kernel's length-nx/s forward and length-nx inverse schedules, the z one.
-template <class LF2, class LI, class LZ, int S>
+template <class LF2, class LI, class LZ, int S, int C>
 ZXDesc xzdesc()
 {
-    constexpr int PZ = RInfo<LI>::n() / 4, PX = RInfo<LZ>::n() / 4;
-    return ZXDesc{k_xzadj_ct<LF2, LI, LZ, S, PZ, PX, 256>, XzGeom<LF2, LI, LZ, PZ, PX>::smem()};
-}
-ZXDesc xzadj_desc(int nx, int nz, int s)
-{
-    if (s != 2) return ZXDesc{};
-    if (nx == 128 && nz == 64) return xzdesc<RList<8, 8>, RList<16, 8>, RList<8, 8>, 2>();
-    if (nx == 64 && nz == 64) return xzdesc<RList<4, 8>, RList<16, 4>, RList<8, 8>, 2>();
-    if (nx == 96 && nz == 64) return xzdesc<RList<3, 4, 4>, RList<8, 4, 3>, RList<8, 8>, 2>();
-    if (nx == 192 && nz == 96) return xzdesc<RList<3, 4, 8>, RList<16, 4, 3>, RList<3, 4, 8>, 2>();
-    return ZXDesc{};
+    constexpr int PZ = RInfo<LI>::n() / (2 * C), PX = RInfo<LZ>::n() / (2 * C), T = zx_threads(C);
+    return ZXDesc{k_xzadj_ct<LF2, LI, LZ, S, C, PZ, PX, T>, XzGeom<LF2, LI, LZ, C, PZ, PX>::smem(), T, C};
 }
 
-ZXDesc zxnrm_desc(int nx, int nz, int s)
+// which: 0 normal, 1 forward, 2 adjoint.  Schedules: the z one of the T
+// pass; the normal kernel's length-nx forward; the forward kernel's
+// length-nx forward and length-nx/s inverse; the adjoint kernel's
+// length-nx/s forward and length-nx inverse.
+template <int C>
+ZXDesc zx_desc_c(int which, int nx, int nz)
+{
+    if (nx == 128 && nz == 64) {
+        if (which == 0) return zxdesc<RList<8, 8>, RList<16, 8>, 2, C>();
+        if (which == 1) return zxfdesc<RList<8, 8>, RList<16, 8>, RList<4, 16>, 2, C>();
+        return xzdesc<RList<8, 8>, RList<16, 8>, RList<8, 8>, 2, C>();
+    }
+    if (nx == 64 && nz == 64) {
+        if (which == 0) return zxdesc<RList<8, 8>, RList<8, 8>, 2, C>();
+        if (which == 1) return zxfdesc<RList<8, 8>, RList<8, 8>, RList<4, 8>, 2, C>();
+        return xzdesc<RList<4, 8>, RList<16, 4>, RList<8, 8>, 2, C>();
+    }
+    if (nx == 96 && nz == 64) {
+        if (which == 0) return zxdesc<RList<8, 8>, RList<3, 4, 8>, 2, C>();
+        if (which == 1) return zxfdesc<RList<8, 8>, RList<3, 4, 8>, RList<4, 4, 3>, 2, C>();
+        return xzdesc<RList<3, 4, 4>, RList<8, 4, 3>, RList<8, 8>, 2, C>();
+    }
+    if (nx == 192 && nz == 96) {
+        if (which == 0) return zxdesc<RList<3, 4, 8>, RList<3, 8, 8>, 2, C>();
+        if (which == 1) return zxfdesc<RList<3, 4, 8>, RList<3, 8, 8>, RList<4, 8, 3>, 2, C>();
+        return xzdesc<RList<3, 4, 8>, RList<16, 4, 3>, RList<3, 4, 8>, 2, C>();
+    }
+    return ZXDesc{};
+}
+ZXDesc zx_desc(int which, int nx, int nz, int s, int C)
 {
     if (s != 2) return ZXDesc{};
-    if (nx == 128 && nz == 64) return zxdesc<RList<8, 8>, RList<16, 8>, 2>();
-    if (nx == 64 && nz == 64) return zxdesc<RList<8, 8>, RList<8, 8>, 2>();
-    if (nx == 96 && nz == 64) return zxdesc<RList<8, 8>, RList<3, 4, 8>, 2>();
-    if (nx == 192 && nz == 96) return zxdesc<RList<3, 4, 8>, RList<3, 8, 8>, 2>();
-    return ZXDesc{};
+    return C == 4 ? zx_desc_c<4>(which, nx, nz) : zx_desc_c<2>(which, nx, nz);
 }
 
 cudaError_t ct_set_attributes(int optin)
@@ -267,15 +282,13 @@ cudaError_t ct_set_attributes(int optin)
             if (e != cudaSuccess) return e;
         }
     static const int zx[][2] = {{128, 64}, {64, 64}, {96, 64}, {192, 96}};
-    for (const auto& p : zx) {
-        const ZXDesc d = zxnrm_desc(p[0], p[1], 2);
-        cudaError_t e = opt_in(d.fn, d.smem, optin);
-        if (e != cudaSuccess) return e;
-        const ZXDesc f = zxfwd_desc(p[0], p[1], 2);
-        if ((e = opt_in(f.fn, f.smem, optin)) != cudaSuccess) return e;
-        const ZXDesc g = xzadj_desc(p[0], p[1], 2);
-        if ((e = opt_in(g.fn, g.smem, optin)) != cudaSuccess) return e;
-    }
+    for (const auto& p : zx)
+        for (int which = 0; which < 3; ++which)
+            for (int C : {2, 4}) {
+                const ZXDesc d = zx_desc(which, p[0], p[1], 2, C);
+                cudaError_t e = opt_in(d.fn, d.smem, optin);
+                if (e != cudaSuccess) return e;
+            }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
         for (int w = 0; w < 8; ++w) {
@@ -381,54 +394,39 @@ static bool xnrm_small()
     return !(e && e[0] == '1' && e[1] == '6');
 }
 
-// The fused T_z + normal pass for the instantiated (nx, nz, s);
-// MH3D_FUSE_ZX=0 keeps the separate T_z and normal passes (A/B checks).
-bool ct_zxnrm_available(int nx, int nz, int s)
+// The cluster passes for the instantiated (nx, nz, s); MH3D_FUSE_ZX=0
+// keeps the separate passes (A/B checks).
+static bool zx_enabled(int which, int nx, int nz, int s)
 {
     const char* e = std::getenv("MH3D_FUSE_ZX");
     if (e && e[0] == '0') return false;
-    return !force_generic() && zxnrm_desc(nx, nz, s).fn && tensor_map_encoder();
+    return !force_generic() && zx_desc(which, nx, nz, s, zx_cluster()).fn && tensor_map_encoder();
 }
+bool ct_zxnrm_available(int nx, int nz, int s) { return zx_enabled(0, nx, nz, s); }
+bool ct_zxfwd_available(int nx, int nz, int s) { return zx_enabled(1, nx, nz, s); }
+bool ct_xzadj_available(int nx, int nz, int s) { return zx_enabled(2, nx, nz, s); }
 
-bool ct_zxfwd_available(int nx, int nz, int s)
-{
-    const char* e = std::getenv("MH3D_FUSE_ZX");
-    if (e && e[0] == '0') return false;
-    return !force_generic() && zxfwd_desc(nx, nz, s).fn && tensor_map_encoder();
-}
-
-// One cluster of two CTAs per y-slab; the z input's tensor map (box
-// nx/2 x 1 x nz, x coordinates 0 and nx/2: 16-byte multiples for nx % 8 == 0)
-// is encoded here.
-static cudaError_t run_zx(ZXArgs& a, const float* zin, const ZXDesc& d, cudaStream_t st)
+// C CTAs per y-slab; the z volume's tensor map (box nx/C x 1 x nz, x
+// coordinates multiples of nx/C: 16-byte multiples for nx % 4C == 0) is
+// encoded here.  zvol: the z pass's input (normal, forward) or output
+// (adjoint).
+static cudaError_t run_zx(ZXArgs& a, const void* zvol, int which, cudaStream_t st)
 {
     const int nx = a.x.nx;
-    if (!d.fn || nx % 8 != 0 || a.nz % 2 != 0 || !al16(zin)) return cudaErrorInvalidValue;
-    if (!encode_tile_map(&a.tz, zin, nx, a.ny, a.nz, 2, a.nz, nx / 2)) return cudaErrorInvalidValue;
-    d.fn<<<2 * a.ny, 256, d.smem, st>>>(a);
+    const ZXDesc d = zx_desc(which, nx, a.nz, a.x.s, zx_cluster());
+    if (!d.fn || nx % (4 * d.C) != 0 || a.nz % (2 * d.C) != 0 || !al16(zvol)) return cudaErrorInvalidValue;
+    if (!encode_tile_map(&a.tz, zvol, nx, a.ny, a.nz, 2, a.nz, nx / d.C)) return cudaErrorInvalidValue;
+    d.fn<<<d.C * a.ny, d.threads, d.smem, st>>>(a);
     return cudaGetLastError();
 }
-cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st)
-{
-    return run_zx(a, zin, zxnrm_desc(a.x.nx, a.nz, a.x.s), st);
-}
-cudaError_t run_zxfwd_ct(ZXArgs& a, const float* zin, cudaStream_t st)
-{
-    return run_zx(a, zin, zxfwd_desc(a.x.nx, a.nz, a.x.s), st);
-}
-
-// The adjoint's fused pass needs the pipelined adjoint's conditions (16-byte
-// aligned portraits, even mx and M); its tensor map is that of the output.
-bool ct_xzadj_available(int nx, int nz, int s)
-{
-    const char* e = std::getenv("MH3D_FUSE_ZX");
-    if (e && e[0] == '0') return false;
-    return !force_generic() && xzadj_desc(nx, nz, s).fn && tensor_map_encoder();
-}
+cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st) { return run_zx(a, zin, 0, st); }
+cudaError_t run_zxfwd_ct(ZXArgs& a, const float* zin, cudaStream_t st) { return run_zx(a, zin, 1, st); }
+// The adjoint's cluster pass also needs the pipelined adjoint's conditions
+// (16-byte aligned portraits, even mx and M).
 cudaError_t run_xzadj_ct(ZXArgs& a, float* zout, cudaStream_t st)
 {
     if (!al16(a.x.din) || (a.x.mx % 2) != 0 || (a.x.M % 2) != 0) return cudaErrorInvalidValue;
-    return run_zx(a, zout, xzadj_desc(a.x.nx, a.nz, a.x.s), st);
+    return run_zx(a, zout, 2, st);
 }
 
 cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st)

@@ -894,35 +894,38 @@ constexpr size_t xnrm_ct_smem()
 // ---------------------------------------------------------------------------
 // Fused T_z + drive-axis normal pass.  The normal operator's z and x steps
 // act on different axes, so one y-slab (nz rows of nx) carries all the data
-// both need.  A cluster of two CTAs takes one slab:
-//   phase 1: CTA c loads x-columns [c nx/2, (c+1) nx/2) of every z by one
+// both need.  A cluster of C CTAs (two or four) takes one slab:
+//   phase 1: CTA c loads x-columns [c nx/C, (c+1) nx/C) of every z by one
 //            TMA box and runs the z-axis convolution on them (the T pass's
-//            stages, nx/4 column-pair pencils); the last inverse stage stores
-//            each row z straight into the exchange buffer of the CTA that owns
-//            it (rows [c' nz/2, (c'+1) nz/2) belong to CTA c'), locally or
-//            through distributed shared memory;
+//            stages, nx/2C column-pair pencils); the last inverse stage
+//            stores each row z straight into the exchange buffer of the CTA
+//            that owns it (rows [c' nz/C, (c'+1) nz/C) belong to CTA c'),
+//            locally or through distributed shared memory;
 //   cluster barrier;
 //   phase 2: CTA c runs the drive-axis normal pass (alias blocks, then
-//            q = b w + lambda p and the dot products) on its nz/2 full rows.
+//            q = b w + lambda p and the dot products) on its nz/C full rows.
 // This removes the T_z launch and its round trip of the volume through L2.
 // Every CTA of a cluster passes both cluster barriers or neither (the
 // loop's done flag is the same for all), so no CTA waits on one that left.
-// Host conditions: R = I, 16-byte aligned vectors, nx % 8 == 0, nz even.
+// Host conditions: R = I, 16-byte aligned vectors, nx % 4C == 0,
+// nz % 2C == 0.
 
 // Stores of the z pass's last stage into the owners' exchange buffers:
-// element e = z, pencil p = columns x0 + 2p, x0 + 2p + 1.
+// element e = z (row e - owner ROWS of CTA owner = e / ROWS), pencil p =
+// columns x0 + 2p, x0 + 2p + 1.
+template <int ROWS>
 struct ZxExchangeSt {
-    float* xb;           // this CTA's exchange buffer [nz/2][nxp]
-    uint32_t peer;       // the other CTA's buffer (shared::cluster address)
-    int half, x0, rank, nxp;
+    float* xb;           // this CTA's exchange buffer [ROWS][nxp]
+    int x0, rank, nxp;
     __device__ __forceinline__ void operator()(int e, int p, float2 v) const
     {
-        const int owner = e >= half ? 1 : 0;
-        const int o = (e - owner * half) * nxp + x0 + 2 * p;
+        const int owner = e / ROWS;
+        const int o = (e - owner * ROWS) * nxp + x0 + 2 * p;
         if (owner == rank) {
             xb[o] = v.x;
             xb[o + 1] = v.y;
         } else {
+            const uint32_t peer = cluster_smem_addr(xb, (uint32_t)owner);
             st_cluster_f32(peer + 4u * (uint32_t)o, v.x);
             st_cluster_f32(peer + 4u * (uint32_t)(o + 1), v.y);
         }
@@ -938,14 +941,15 @@ struct XbPairLd {
     }
 };
 
-template <class LZ, class LF, int PZ, int PX>
+template <class LZ, class LF, int C, int PZ, int PX>
 struct ZxGeom {
     static constexpr int NZ = RInfo<LZ>::n(), NX = RInfo<LF>::n();
+    static_assert(NX == 2 * C * PZ && NZ == 2 * C * PX, "pencil counts: nx/2C column pairs, nz/2C row pairs");
     static constexpr int NXP = NX + 1;                  // exchange rows: odd stride, conflict-free pencil reads
     static constexpr int LD = xnrm_ld<LF, PX>();        // drive-axis transform buffers
     static constexpr int NXS = xnrm_nxs<LF, false, PX>();
     static constexpr int TAB = 2 * NZ + NX;             // float2: W_nz, z multiplier, W_nx
-    static constexpr int XB = (NZ / 2) * NXP;           // floats
+    static constexpr int XB = (NZ / C) * NXP;           // floats
     static constexpr int OFF = (TAB + (XB + 1) / 2 + 15) / 16 * 16;   // float2 offset of the union, 128-byte aligned
     static constexpr int P1 = 2 * NZ * PZ;              // float2: tile + second buffer of the z pass
     static constexpr int P2 = 2 * NX * LD;              // float2: the drive-axis buffers
@@ -954,15 +958,15 @@ struct ZxGeom {
 };
 
 // Phase 1 of the y-slab cluster passes: the z-axis convolution (multiplier
-// mu) of this CTA's column half, every result row stored into its owner's
+// mu) of this CTA's nx/C columns, every result row stored into its owner's
 // exchange buffer.  Loads the phase-2 twiddles (W_nx) while the TMA box is
 // in flight.  Returns whether the box landed; the caller takes the cluster
 // barrier either way.
-template <class LZ, int NX, int PZ, int T>
+template <class LZ, int NX, int C, int PZ, int T>
 __device__ __forceinline__ bool zx_zconv(const ZXArgs& a, const float2* __restrict__ mu_g, float2* twz, float2* muz,
                                          float2* twx, float* xb, float2* un, uint64_t* bar, int y, uint32_t rank)
 {
-    constexpr int NZ = RInfo<LZ>::n(), NSTZ = RInfo<LZ>::nst, RLZ = RInfo<LZ>::last(), HALF = NZ / 2, NXP = NX + 1;
+    constexpr int NZ = RInfo<LZ>::n(), NSTZ = RInfo<LZ>::nst, RLZ = RInfo<LZ>::last(), ROWS = NZ / C, NXP = NX + 1;
     using LZI = Reverse<LZ>;
     float2* tile = un;
     float2* zb = un + NZ * PZ;
@@ -973,7 +977,7 @@ __device__ __forceinline__ bool zx_zconv(const ZXArgs& a, const float2* __restri
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(bar, (uint32_t)(NZ * PZ * sizeof(float2)));
-        tma_load_3d(tile, &a.tz, (int)rank * (NX / 2), y, 0, bar);
+        tma_load_3d(tile, &a.tz, (int)rank * (NX / C), y, 0, bar);
     }
     for (int i = threadIdx.x; i < NZ; i += T) {
         twz[i] = a.twz[i];
@@ -990,24 +994,23 @@ __device__ __forceinline__ bool zx_zconv(const ZXArgs& a, const float2* __restri
         run_stages<LZ, 0, NSTZ - 1, PZ, T, 1, false, true, true>(BufLd{tile, PZ}, BufSt{fo, PZ}, zb, tile, PZ, twz);
         fused_conv_stage<NZ, RLZ, PZ, T>(BufLd{fo, PZ}, BufSt{fx, PZ}, muz, twz);
         __syncthreads();
-        const ZxExchangeSt xs{xb, cluster_smem_addr(xb, rank ^ 1u), HALF, (int)rank * (NX / 2), (int)rank, NXP};
+        const ZxExchangeSt<ROWS> xs{xb, (int)rank * (NX / C), (int)rank, NXP};
         run_stages<LZI, 1, NSTZ, PZ, T, 1, true, true, true>(BufLd{fx, PZ}, xs, fo, fx, PZ, twz);
     }
     return ok;
 }
 
-template <class LZ, class LF, int S, int PZ, int PX, int TT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const __grid_constant__ ZXArgs a)
+template <class LZ, class LF, int S, int C, int PZ, int PX, int TT>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const __grid_constant__ ZXArgs a)
 {
-    using G = ZxGeom<LZ, LF, PZ, PX>;
+    using G = ZxGeom<LZ, LF, C, PZ, PX>;
     constexpr int NZ = G::NZ, NX = G::NX, T = TT;
     using IF = RInfo<LF>;
     using LI = Reverse<LF>;
     constexpr int NSTX = IF::nst, R = IF::last(), R2 = R / S;
     constexpr int NBL = NX / R, ITERL = (NBL * PX + T - 1) / T;
-    constexpr int LD = G::LD, NXS = G::NXS, NXP = G::NXP, HALF = NZ / 2;
+    constexpr int LD = G::LD, NXS = G::NXS, NXP = G::NXP, ROWS = NZ / C;
     static_assert(R % S == 0, "alias blocks must sit in one butterfly");
-    static_assert(NX == 4 * PZ && NZ == 4 * PX, "pencil counts: nx/4 column pairs, nz/4 row pairs");
     static_assert(RInfo<LZ>::nst >= 2 && NSTX >= 2, "two stages at least on each axis");
     extern __shared__ __align__(128) float2 zx_raw[];
     __shared__ double red[34];
@@ -1019,19 +1022,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
     float* xb = reinterpret_cast<float*>(twx + NX);
     float2* un = sm + G::OFF;           // 128-byte aligned: the TMA box lands at its start
     const uint32_t rank = cluster_ctarank();
-    const int y = (int)blockIdx.x >> 1;
+    const int y = (int)blockIdx.x / C;
     // every CTA of the cluster is running before any of them stores remotely
     cluster_sync_all();
     float dummy;
     if (a.x.cg_active && !cg_enter(a.x.cg, false, &dummy, red)) return;
 
-    // ---- phase 1: z-axis convolution of this CTA's column half
-    const bool ok = zx_zconv<LZ, NX, PZ, T>(a, a.muz, twz, muz, twx, xb, un, &bar, y, rank);
-    // both halves of every owned row have landed (local and remote stores)
+    // ---- phase 1: z-axis convolution of this CTA's columns
+    const bool ok = zx_zconv<LZ, NX, C, PZ, T>(a, a.muz, twz, muz, twx, xb, un, &bar, y, rank);
+    // every part of every owned row has landed (local and remote stores)
     cluster_sync_all();
     if (!ok) return;
 
-    // ---- phase 2: drive-axis normal pass on rows z = rank nz/2 + rr
+    // ---- phase 2: drive-axis normal pass on rows z = rank nz/C + rr
     float2* b0 = un;
     float2* b1 = b0 + NX * LD;
     constexpr int pfx = result_parity<0, NSTX - 1>();
@@ -1071,7 +1074,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
     run_stages<LI, 1, NSTX, PX, T, 1, true, true, false>(BufLd{fx, LD}, RowStageSt{stg, NXS}, fo, fx, LD, twx);
 
     // epilogue over the 2 PX staged rows; volume row of staged row rr:
-    // (rank nz/2 + rr) ny + y
+    // (rank nz/C + rr) ny + y
     constexpr int V = NX / 4, TOTAL = 2 * PX * V, ITER = (TOTAL + T - 1) / T;
     const float* __restrict__ bp = a.x.b;
     const float* __restrict__ pp = a.x.pin;
@@ -1084,7 +1087,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
         const int idx = (int)threadIdx.x + it * T;
         if ((TOTAL % T) != 0 && idx >= TOTAL) continue;
         const int rr = idx / V, c = idx - rr * V;
-        const long long i = ((long long)((int)rank * HALF + rr) * a.ny + y) * NX + 4 * c;
+        const long long i = ((long long)((int)rank * ROWS + rr) * a.ny + y) * NX + 4 * c;
         W[it] = *reinterpret_cast<const float4*>(stg + rr * NXS + 4 * c);
         B[it] = bp ? __ldg(reinterpret_cast<const float4*>(bp + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
         Pv[it] = __ldg(reinterpret_cast<const float4*>(pp + i));
@@ -1094,7 +1097,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
         const int idx = (int)threadIdx.x + it * T;
         if ((TOTAL % T) != 0 && idx >= TOTAL) continue;
         const int rr = idx / V, c = idx - rr * V;
-        const long long i = ((long long)((int)rank * HALF + rr) * a.ny + y) * NX + 4 * c;
+        const long long i = ((long long)((int)rank * ROWS + rr) * a.ny + y) * NX + 4 * c;
         float4 q;
         q.x = fmaf(B[it].x, W[it].x, lam * Pv[it].x);
         q.y = fmaf(B[it].y, W[it].y, lam * Pv[it].y);
@@ -1126,24 +1129,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
 }
 
 // The forward operator's last two steps, T_z then the drive-axis forward
-// (fold by s, phase, portrait store), for one y-slab per cluster of two
+// (fold by s, phase, portrait store), for one y-slab per cluster of C
 // CTAs: phase 1 as in k_zxnrm_ct (multiplier Zhat), phase 2 the forward
-// pass on this CTA's nz/2 rows, whose portrait rows are ny apart.
-template <class LZ, class LF, class LI, int PZ, int PX>
+// pass on this CTA's nz/C rows, whose portrait rows are ny apart.
+template <class LZ, class LF, class LI, int C, int PZ, int PX>
 struct ZxFwdGeom {
-    using B = ZxGeom<LZ, LF, PZ, PX>;
+    using B = ZxGeom<LZ, LF, C, PZ, PX>;
     static constexpr int NX = RInfo<LF>::n(), MX = RInfo<LI>::n();
     static constexpr int F2 = 2 * NX * PX > 2 * MX * xfwd_ldc<LI, PX>() ? 2 * NX * PX : 2 * MX * xfwd_ldc<LI, PX>();
     static constexpr int UN = B::P1 > F2 ? B::P1 : F2;
     static constexpr size_t smem() { return sizeof(float2) * (size_t)(B::OFF + UN) + 128; }
 };
 
-template <class LZ, class LF, class LI, int S, int PZ, int PX, int TT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxfwd_ct(const __grid_constant__ ZXArgs a)
+template <class LZ, class LF, class LI, int S, int C, int PZ, int PX, int TT>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_zxfwd_ct(const __grid_constant__ ZXArgs a)
 {
-    using G = ZxGeom<LZ, LF, PZ, PX>;
-    constexpr int NZ = G::NZ, NX = G::NX, MX = RInfo<LI>::n(), T = TT, HALF = NZ / 2;
-    static_assert(NX == 4 * PZ && NZ == 4 * PX, "pencil counts: nx/4 column pairs, nz/4 row pairs");
+    using G = ZxGeom<LZ, LF, C, PZ, PX>;
+    constexpr int NZ = G::NZ, NX = G::NX, MX = RInfo<LI>::n(), T = TT, ROWS = NZ / C;
     extern __shared__ __align__(128) float2 zf_raw[];
     __shared__ __align__(8) uint64_t bar;
     float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(zf_raw) + 127) & ~uintptr_t(127));
@@ -1153,49 +1155,51 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_zxfwd_ct(const
     float* xb = reinterpret_cast<float*>(twx + NX);
     float2* un = sm + G::OFF;
     const uint32_t rank = cluster_ctarank();
-    const int y = (int)blockIdx.x >> 1;
+    const int y = (int)blockIdx.x / C;
     cluster_sync_all();   // every CTA of the cluster runs before any remote store
-    const bool ok = zx_zconv<LZ, NX, PZ, T>(a, a.muz, twz, muz, twx, xb, un, &bar, y, rank);
-    cluster_sync_all();   // both halves of every owned row have landed
+    const bool ok = zx_zconv<LZ, NX, C, PZ, T>(a, a.muz, twz, muz, twx, xb, un, &bar, y, rank);
+    cluster_sync_all();   // every part of every owned row has landed
     if (!ok) return;
-    const PortraitStK pst{nullptr, nullptr, a.x.M, MX, ((int)rank * HALF) * a.ny + y, a.x.rows, 0, PX, a.ny};
+    const PortraitStK pst{nullptr, nullptr, a.x.M, MX, ((int)rank * ROWS) * a.ny + y, a.x.rows, 0, PX, a.ny};
     xfwd_rows<LF, LI, S, PX, T>(XbPairLd{xb, G::NXP}, a.x, pst, 0, a.x.K, twx, un);
 }
 
 // The adjoint operator's first two steps, the drive-axis adjoint then the
-// z-axis correlation (T_z^T), for one y-slab per cluster of two CTAs:
+// z-axis correlation (T_z^T), for one y-slab per cluster of C CTAs:
 //   phase 1: CTA c runs the drive-axis adjoint of rows z in
-//            [c nz/2, (c+1) nz/2) (portrait rows z ny + y, staged by per-row
+//            [c nz/C, (c+1) nz/C) (portrait rows z ny + y, staged by per-row
 //            bulk copies); its last inverse stage stores each row's x-columns
 //            into the z-tile of the CTA that owns them (columns
-//            [c' nx/2, (c'+1) nx/2) belong to CTA c'), locally or through
+//            [c' nx/C, (c'+1) nx/C) belong to CTA c'), locally or through
 //            distributed shared memory;
 //   cluster barrier;
-//   phase 2: CTA c runs the z correlation on its nx/2 columns of every z and
+//   phase 2: CTA c runs the z correlation on its nx/C columns of every z and
 //            stores the result box with one TMA store.
 // Every CTA passes the cluster barrier, whether or not its copies landed.
+template <int QX>
 struct XzExchangeSt {
-    float* xt;           // this CTA's z-tile [nz][nx/2]
-    uint32_t peer;       // the other CTA's z-tile (shared::cluster address)
-    int half_x, z0, P, rank;
+    float* xt;           // this CTA's z-tile [nz][QX]; columns [c QX, (c+1) QX) belong to CTA c
+    int z0, P, rank;
     __device__ __forceinline__ void operator()(int e, int p, float2 v) const
     {
-        const int owner = e >= half_x ? 1 : 0;
-        const int col = e - owner * half_x;
-        const int o1 = (z0 + p) * half_x + col, o2 = (z0 + p + P) * half_x + col;
+        const int owner = e / QX;
+        const int col = e - owner * QX;
+        const int o1 = (z0 + p) * QX + col, o2 = (z0 + p + P) * QX + col;
         if (owner == rank) {
             xt[o1] = v.x;
             xt[o2] = v.y;
         } else {
+            const uint32_t peer = cluster_smem_addr(xt, (uint32_t)owner);
             st_cluster_f32(peer + 4u * (uint32_t)o1, v.x);
             st_cluster_f32(peer + 4u * (uint32_t)o2, v.y);
         }
     }
 };
 
-template <class LF2, class LI, class LZ, int PZ, int PX>
+template <class LF2, class LI, class LZ, int C, int PZ, int PX>
 struct XzGeom {
     static constexpr int NX = RInfo<LI>::n(), NZ = RInfo<LZ>::n();
+    static_assert(NX == 2 * C * PZ && NZ == 2 * C * PX, "pencil counts: nx/2C column pairs, nz/2C row pairs");
     static constexpr int TAB = NX + 2 * NZ;                       // float2: W_nx, W_nz, z multiplier
     static constexpr int TABR = (TAB + 15) / 16 * 16;             // 128-byte aligned z-tile
     static constexpr int XT = NZ * PZ;                            // float2: the z-tile
@@ -1204,15 +1208,14 @@ struct XzGeom {
     static constexpr size_t smem() { return sizeof(float2) * (size_t)(TABR + XT + UN) + 128; }
 };
 
-template <class LF2, class LI, class LZ, int S, int PZ, int PX, int TT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_xzadj_ct(const __grid_constant__ ZXArgs a)
+template <class LF2, class LI, class LZ, int S, int C, int PZ, int PX, int TT>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_xzadj_ct(const __grid_constant__ ZXArgs a)
 {
-    using G = XzGeom<LF2, LI, LZ, PZ, PX>;
-    constexpr int NX = G::NX, NZ = G::NZ, T = TT, HALF = NZ / 2;
+    using G = XzGeom<LF2, LI, LZ, C, PZ, PX>;
+    constexpr int NX = G::NX, NZ = G::NZ, T = TT, ROWS = NZ / C, QX = NX / C;
     constexpr int NSTZ = RInfo<LZ>::nst, RLZ = RInfo<LZ>::last();
     using LZI = Reverse<LZ>;
     constexpr int LD = xadj_ld<LI, PX>();
-    static_assert(NX == 4 * PZ && NZ == 4 * PX, "pencil counts: nx/4 column pairs, nz/4 row pairs");
     static_assert(NSTZ >= 2, "two stages at least along z");
     extern __shared__ __align__(128) float2 xz_raw[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -1223,19 +1226,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_xzadj_ct(const
     float2* xt = sm + G::TABR;          // the z-tile [NZ][PZ], written by both CTAs of the cluster
     float2* un = xt + G::XT;            // 128-byte aligned
     const uint32_t rank = cluster_ctarank();
-    const int y = (int)blockIdx.x >> 1;
+    const int y = (int)blockIdx.x / C;
     for (int i = threadIdx.x; i < NZ; i += T) {
         twz[i] = a.twz[i];
         muz[i] = a.muz[i];
     }
     cluster_sync_all();   // every CTA of the cluster runs before any remote store
-    // ---- phase 1: drive-axis adjoint of rows z = rank nz/2 + r
+    // ---- phase 1: drive-axis adjoint of rows z = rank nz/C + r
     float2* b0 = un;
     float2* b1 = b0 + NX * LD;
     float2* pb = b1 + NX * LD;
     float* xtf = reinterpret_cast<float*>(xt);
-    const XzExchangeSt st{xtf, cluster_smem_addr(xtf, rank ^ 1u), NX / 2, (int)rank * HALF, PX, (int)rank};
-    const bool ok = xadj_rows<LF2, LI, S, true, PX, T>(a.x, ((int)rank * HALF) * a.ny + y, a.ny, HALF, st, tw, b0,
+    const XzExchangeSt<QX> st{xtf, (int)rank * ROWS, PX, (int)rank};
+    const bool ok = xadj_rows<LF2, LI, S, true, PX, T>(a.x, ((int)rank * ROWS) * a.ny + y, a.ny, ROWS, st, tw, b0,
                                                        b1, pb, bars);
     cluster_sync_all();   // every column of this CTA's z-tile has landed
     if (!ok) return;
@@ -1253,7 +1256,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TT) k_xzadj_ct(const
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
-        tma_store_3d(&a.tz, (int)rank * (NX / 2), y, 0, stg);
+        tma_store_3d(&a.tz, (int)rank * QX, y, 0, stg);
         bulk_commit();
         bulk_wait_all();   // the copy reads shared memory and must land before the CTA ends
     }

@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 TOL = 1e-5
 
 
-@pytest.fixture(params=["specialised", "generic", "alternatives"])
+@pytest.fixture(params=["specialised", "generic", "alternatives", "cluster4"])
 def kernel_path(request, monkeypatch):
     """Run each operator test on the compile-time specialised kernels (the
     default for the common lengths: pipelined drive-axis adjoint, 16-row
@@ -25,10 +25,11 @@ def kernel_path(request, monkeypatch):
     kernels for every size, and on the measured alternatives of the
     specialised path: the bulk-copy normal pass, the adjoint without copy
     pipelining, the 16-row forward pass with uneven harmonic groups of
-    three per CTA, and the separate T_z and normal passes instead of the
-    fused cluster pass."""
+    three per CTA, and the separate T_z and drive-axis passes instead of the
+    y-slab cluster passes; and once more with those cluster passes on
+    clusters of four CTAs (MH3D_ZX_CLUSTER=4)."""
     for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS",
-              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX"):
+              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX", "MH3D_ZX_CLUSTER"):
         monkeypatch.delenv(v, raising=False)
     if request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
@@ -38,6 +39,8 @@ def kernel_path(request, monkeypatch):
         monkeypatch.setenv("MH3D_XFWD_KPC", "3")
         monkeypatch.setenv("MH3D_XFWD_PAIRS", "8")
         monkeypatch.setenv("MH3D_FUSE_ZX", "0")
+    elif request.param == "cluster4":
+        monkeypatch.setenv("MH3D_ZX_CLUSTER", "4")
     return request.param
 
 
