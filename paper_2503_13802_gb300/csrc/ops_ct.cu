@@ -74,6 +74,8 @@ XDesc xdesc(int which)
     if (which == 5) return XDesc{k_xadj_ct<LFA, LIA, S, true>, xadj_ct_smem<LFA, LIA, S, true>()};
     if (which == 7)
         return XDesc{k_xadj_ct<LFA, LIA, S, true, 8, 128>, xadj_ct_smem<LFA, LIA, S, true, 8>(), 128, 8};
+    if (which == 8)
+        return XDesc{k_xadj_ct<LFA, LIA, S, true, 8, 128, 2>, xadj_ct_smem<LFA, LIA, S, true, 8, 2>(), 128, 8};
     if (which == 3) return XDesc{k_xnrm_ct<LFN, S, true>, xnrm_ct_smem<LFN, S, true>(), kTN, kP};
     if (which == 4) return XDesc{k_xnrm_ct<LFN, S, false, 8, 128>, xnrm_ct_smem<LFN, S, false, 8>(), 128, 8};
     return XDesc{k_xnrm_ct<LFN, S, false>, xnrm_ct_smem<LFN, S, false>(), kTN, kP};
@@ -208,6 +210,17 @@ struct ZXDesc {
 };
 constexpr int zx_threads(int C) { return C == 2 ? 256 : 128; }
 
+// Harmonics per round of the pipelined adjoint: one by default.
+// MH3D_XADJ_KB=2 runs pairs (one first-stage run and one barrier per pair;
+// twice the staged rows): measured slower at 128x128x64, K = 8 -- the
+// cluster adjoint 61.5 us against 43.9 us (one CTA per SM instead of two),
+// the separate 16-row pass 47.0 us against 43.6-44.5 us for A^T.
+static int xadj_kb()
+{
+    const char* e = std::getenv("MH3D_XADJ_KB");
+    return (e && e[0] == '2') ? 2 : 1;
+}
+
 // MH3D_ZX_CLUSTER=4: clusters of four CTAs (A/B checks); default two.
 static int zx_cluster()
 {
@@ -227,11 +240,29 @@ ZXDesc zxfdesc()
     constexpr int PZ = RInfo<LF>::n() / (2 * C), PX = RInfo<LZ>::n() / (2 * C), T = zx_threads(C);
     return ZXDesc{k_zxfwd_ct<LZ, LF, LI, S, C, PZ, PX, T>, ZxFwdGeom<LZ, LF, LI, C, PZ, PX>::smem(), T, C};
 }
+template <class LF2, class LI, class LZ, int S, int C, int KB>
+ZXDesc xzdesc_kb()
+{
+    constexpr int PZ = RInfo<LI>::n() / (2 * C), PX = RInfo<LZ>::n() / (2 * C), T = zx_threads(C);
+    return ZXDesc{k_xzadj_ct<LF2, LI, LZ, S, C, PZ, PX, T, KB>, XzGeom<LF2, LI, LZ, C, PZ, PX, KB>::smem(), T, C};
+}
+// Clusters of two run the adjoint part in rounds of xadj_kb() harmonics
+// where the two rounds of row blocks fit in 227 KB of shared memory;
+// otherwise (and for clusters of four) in rounds of one.
+constexpr size_t kSmemOptinMax = 227 * 1024;
+template <class LF2, class LI, class LZ, int S, int C>
+constexpr bool xz_kb2_fits()
+{
+    constexpr int PZ = RInfo<LI>::n() / (2 * C), PX = RInfo<LZ>::n() / (2 * C);
+    return C == 2 && XzGeom<LF2, LI, LZ, C, PZ, PX, 2>::smem() <= kSmemOptinMax;
+}
 template <class LF2, class LI, class LZ, int S, int C>
 ZXDesc xzdesc()
 {
-    constexpr int PZ = RInfo<LI>::n() / (2 * C), PX = RInfo<LZ>::n() / (2 * C), T = zx_threads(C);
-    return ZXDesc{k_xzadj_ct<LF2, LI, LZ, S, C, PZ, PX, T>, XzGeom<LF2, LI, LZ, C, PZ, PX>::smem(), T, C};
+    if constexpr (xz_kb2_fits<LF2, LI, LZ, S, C>()) {
+        if (xadj_kb() == 2) return xzdesc_kb<LF2, LI, LZ, S, C, 2>();
+    }
+    return xzdesc_kb<LF2, LI, LZ, S, C, 1>();
 }
 
 // which: 0 normal, 1 forward, 2 adjoint.  Schedules: the z one of the T
@@ -289,9 +320,25 @@ cudaError_t ct_set_attributes(int optin)
                 cudaError_t e = opt_in(d.fn, d.smem, optin);
                 if (e != cudaSuccess) return e;
             }
+    // both round sizes of the clusters-of-two adjoint (xzdesc picks by MH3D_XADJ_KB)
+    {
+        const ZXDesc d[] = {
+            xzdesc_kb<RList<8, 8>, RList<16, 8>, RList<8, 8>, 2, 2, 1>(),
+            xzdesc_kb<RList<4, 8>, RList<16, 4>, RList<8, 8>, 2, 2, 1>(),
+            xzdesc_kb<RList<3, 4, 4>, RList<8, 4, 3>, RList<8, 8>, 2, 2, 1>(),
+            xzdesc_kb<RList<3, 4, 8>, RList<16, 4, 3>, RList<3, 4, 8>, 2, 2, 1>(),
+            xzdesc_kb<RList<8, 8>, RList<16, 8>, RList<8, 8>, 2, 2, 2>(),
+            xzdesc_kb<RList<4, 8>, RList<16, 4>, RList<8, 8>, 2, 2, 2>(),
+            xzdesc_kb<RList<3, 4, 4>, RList<8, 4, 3>, RList<8, 8>, 2, 2, 2>(),
+        };
+        for (const ZXDesc& x : d) {
+            cudaError_t e = opt_in(x.fn, x.smem, optin);
+            if (e != cudaSuccess) return e;
+        }
+    }
     static const int xs[][2] = {{32, 1}, {64, 2}, {96, 2}, {128, 1}, {128, 2}, {192, 2}, {256, 1}, {256, 2}};
     for (const auto& p : xs)
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < 9; ++w) {
             const XDesc d = xpass_desc(p[0], p[1], w);
             cudaError_t e = opt_in(d.fn, d.smem, optin);
             if (e != cudaSuccess) return e;
@@ -371,7 +418,9 @@ static bool xadj_small()
 
 cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st)
 {
-    return run_x_ct(a, xadj_bulk_ok(a) ? (xadj_small() ? 7 : 5) : 1, st);
+    if (!xadj_bulk_ok(a)) return run_x_ct(a, 1, st);
+    if (!xadj_small()) return run_x_ct(a, 5, st);
+    return run_x_ct(a, xadj_kb() == 2 ? 8 : 7, st);
 }
 // The bulk-copy normal pass (opt-in: MH3D_XNRM_BULK=1; measured 3 % slower
 // per CG iteration than the register-loading pass at 128x128x64) needs

@@ -477,20 +477,64 @@ constexpr int xadj_mxs()
     return RInfo<LF2>::n() + 2;
 }
 
-// BULK: each harmonic's 2P portrait rows go to a shared-memory block, one
-// 1D bulk copy per row (rows padded to mx + 2 float2); two such buffers with
-// one mbarrier each take the blocks of harmonics k and k + 1, and a buffer
-// is refilled with harmonic k + 2 as soon as harmonic k's first stage has
-// read it, so the copies run under the transforms.
+// Loader of the first stage of a round of KB harmonics (KB = 1 or 2) from
+// their staged row blocks (blk_stride float2 apart, rows mxs float2 apart):
+// pencil q = kk P + p packs Re(e^{-i theta} y) of rows p and p + P of
+// harmonic kk of the round; rows at or beyond nrow, and harmonics at or
+// beyond nk, read as zero.
+struct PortraitRoundLd {
+    const float2* blk;
+    float2 ph0, ph1;
+    int mxs, P, nrow, nk, blk_stride;
+    __device__ __forceinline__ float2 operator()(int m, int q) const
+    {
+        const int kk = q >= P ? 1 : 0;
+        const int p = q - kk * P;
+        float2 o = make_float2(0.f, 0.f);
+        if (kk >= nk) return o;
+        const float2 ph = kk ? ph1 : ph0;
+        const float2* b = blk + kk * blk_stride;
+        if (p < nrow) {
+            const float2 y = b[p * mxs + m];
+            o.x = fmaf(ph.x, y.x, ph.y * y.y);
+        }
+        if (p + P < nrow) {
+            const float2 y = b[(p + P) * mxs + m];
+            o.y = fmaf(ph.x, y.x, ph.y * y.y);
+        }
+        return o;
+    }
+};
+
+// Adjoint shared-memory geometry for P pencils and KB harmonics per round:
+// each of the two transform buffers holds max(nx ld, mx KB P) float2.
+template <class LF2, class LI, int P, int KB>
+constexpr int xadj_buf()
+{
+    constexpr int a = RInfo<LI>::n() * xadj_ld<LI, P>(), b = RInfo<LF2>::n() * KB * P;
+    return a > b ? a : b;
+}
+template <class LF2, int P, int KB>
+constexpr int xadj_pb()   // two rounds of KB row blocks
+{
+    return 2 * KB * 2 * P * xadj_mxs<LF2>();
+}
+
 // The drive-axis adjoint of 2P rows, portrait row rbase + r rstride for row
 // r of the CTA (r < nrow): per harmonic the length-mx forward transform of
 // Re(e^{-i theta_k} y_k), times conj(X_k) periodised to length nx, summed
 // over k in registers; then one length-nx inverse whose last stage goes to
-// `st` (element, pencil, value).  BULK pairs rows p and p + P in a pencil
-// (rows staged by 1D bulk copies); otherwise rows 2p and 2p + 1, read from
-// global memory (rstride 1).  Loads W_nx into tw.  Returns false if a bulk
-// copy's bounded wait gave up (MH3D_ERR_TIMEOUT recorded; the rest skipped).
-template <class LF2, class LI, int S, bool BULK, int P, int T, class ST>
+// `st` (element, pencil, value).
+// BULK: pencil p packs rows p and p + P; the harmonics go in rounds of KB,
+// one first-stage run over the round's KB P pencils and one CTA barrier per
+// round.  Each harmonic's rows reach a padded shared-memory block (rows of
+// mx + 2 float2) by one 1D bulk copy per row; two round buffers with one
+// mbarrier each take rounds t and t + 1, and a buffer is refilled with round
+// t + 2 once round t's first stage has read it, so the copies run under the
+// transforms.  Otherwise (KB = 1): rows 2p and 2p + 1, read from global
+// memory (rstride 1).  Loads W_nx into tw.  Returns false if a bulk copy's
+// bounded wait gave up (MH3D_ERR_TIMEOUT recorded; the rest skipped).
+template <class LF2, class LI, int S, bool BULK, int P, int T, int KB, class ST>
 __device__ __forceinline__ bool xadj_rows(const XArgs& a, int rbase, int rstride, int nrow, const ST& st, float2* tw,
                                           float2* b0, float2* b1, float2* pb, uint64_t* bars)
 {
@@ -498,20 +542,27 @@ __device__ __forceinline__ bool xadj_rows(const XArgs& a, int rbase, int rstride
     using II = RInfo<LI>;
     constexpr int MX = IF::n(), NX = II::n(), NST2 = IF::nst, NSTI = II::nst, R = IF::last(), RI = II::first();
     static_assert(NX == MX * S && RI == R * S, "inconsistent X adjoint schedules");
+    static_assert(KB == 1 || (KB == 2 && BULK), "rounds of two harmonics need the staged rows");
     constexpr int NBL = MX / R;    // = NX / RI
     constexpr int ITERL = (NBL * P + T - 1) / T;
     constexpr int LD = xadj_ld<LI, P>();
+    constexpr int PB = KB * P;     // first-stage pencils per round (pencil stride PB)
     constexpr int MXS = xadj_mxs<LF2>();
+    constexpr int BLK = 2 * P * MXS;
     constexpr uint32_t ROWB = (uint32_t)(MX * sizeof(float2));
     const uint32_t pbytes = (uint32_t)nrow * ROWB;
-    // warp 0 stages harmonic k's rows into buffer k & 1, one copy per row
-    auto stage_rows = [&](int k) {
-        if (threadIdx.x == 0) mbar_arrive_expect_tx(&bars[k & 1], pbytes);
+    const int nround = (a.K + KB - 1) / KB;
+    // warp 0 stages round t's rows into round buffer t & 1, one copy per row
+    auto stage_round = [&](int t) {
+        const int k0 = t * KB, nk = min(KB, a.K - k0);
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(&bars[t & 1], pbytes * (uint32_t)nk);
         __syncwarp();
-        const float2* src = a.din + (long long)k * a.M;
-        for (int r = (int)threadIdx.x; r < nrow; r += 32)
-            bulk_g2s(pb + (k & 1) * 2 * P * MXS + r * MXS, src + (long long)(rbase + r * rstride) * MX, ROWB,
-                     &bars[k & 1]);
+        for (int kk = 0; kk < nk; ++kk) {
+            const float2* src = a.din + (long long)(k0 + kk) * a.M;
+            float2* dst = pb + ((t & 1) * KB + kk) * BLK;
+            for (int r = (int)threadIdx.x; r < nrow; r += 32)
+                bulk_g2s(dst + r * MXS, src + (long long)(rbase + r * rstride) * MX, ROWB, &bars[t & 1]);
+        }
     };
     if constexpr (BULK) {
         if (threadIdx.x == 0) {
@@ -521,7 +572,7 @@ __device__ __forceinline__ bool xadj_rows(const XArgs& a, int rbase, int rstride
         }
         __syncthreads();
         if (threadIdx.x < 32)
-            for (int k = 0; k < a.K && k < 2; ++k) stage_rows(k);
+            for (int t = 0; t < nround && t < 2; ++t) stage_round(t);
     }
     for (int i = threadIdx.x; i < NX; i += T) tw[i] = a.twx[i];
     __syncthreads();
@@ -532,46 +583,53 @@ __device__ __forceinline__ bool xadj_rows(const XArgs& a, int rbase, int rstride
         for (int r = 0; r < RI; ++r) acc[it][r] = make_float2(0.f, 0.f);
     constexpr int pf = result_parity<0, NST2 - 1>();
     float2* fo = pf ? b1 : b0;
-    for (int k = 0; k < a.K; ++k) {
-        const int buf = k & 1;
+    for (int t = 0; t < nround; ++t) {
+        const int k0 = t * KB, nk = min(KB, a.K - k0);
         if constexpr (BULK) {
             // a copy that never lands would be a hardware fault: bounded wait
-            const bool ok = mbar_wait(&bars[buf], (uint32_t)((k >> 1) & 1), a.status);
+            const bool ok = mbar_wait(&bars[t & 1], (uint32_t)((t >> 1) & 1), a.status);
             if (!__syncthreads_and(ok)) return false;
         }
-        using LdT = typename std::conditional<BULK, PortraitSplitLd, PortraitLd>::type;
+        using LdT = typename std::conditional<BULK, PortraitRoundLd, PortraitLd>::type;
         LdT ld;
         if constexpr (BULK)
-            ld = PortraitSplitLd{pb + buf * 2 * P * MXS, __ldg(a.phase + k), MXS, P, nrow};
+            ld = PortraitRoundLd{pb + (t & 1) * KB * BLK, __ldg(a.phase + k0), __ldg(a.phase + k0 + (nk > 1 ? 1 : 0)),
+                                 MXS, P, nrow, nk, BLK};
         else
-            ld = PortraitLd{a.din + (long long)k * a.M, a.phase + k, a.M, MX, rbase, a.rows, P};
+            ld = PortraitLd{a.din + (long long)k0 * a.M, a.phase + k0, a.M, MX, rbase, a.rows, P};
         if constexpr (NST2 > 1)
-            run_stages<LF2, 0, NST2 - 1, P, T, S, false, false, true>(ld, BufSt{fo, LD}, b0, b1, LD, tw);
-        const float2* __restrict__ xk = a.Xhat + (long long)k * NX;
+            run_stages<LF2, 0, NST2 - 1, PB, T, S, false, false, true>(ld, BufSt{fo, PB}, b0, b1, PB, tw);
 #pragma unroll
-        for (int it = 0; it < ITERL; ++it) {
-            const int idx = (int)threadIdx.x + it * T;
-            const int p = idx % P, j = idx / P;
-            if ((NBL * P) % T != 0 && idx >= NBL * P) break;
-            float2 v[R];
+        for (int kk = 0; kk < KB; ++kk) {
+            if (kk >= nk) break;
+            const float2* __restrict__ xk = a.Xhat + (long long)(k0 + kk) * NX;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = (NST2 > 1) ? fo[(j + r * NBL) * LD + p] : ld(j + r * NBL, p);
-            if (NBL > 1) {
+            for (int it = 0; it < ITERL; ++it) {
+                const int idx = (int)threadIdx.x + it * T;
+                const int p = idx % P, j = idx / P;
+                if ((NBL * P) % T != 0 && idx >= NBL * P) break;
+                float2 v[R];
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw[r * j * S]);
+                for (int r = 0; r < R; ++r)
+                    v[r] = (NST2 > 1) ? fo[(j + r * NBL) * PB + kk * P + p] : ld(j + r * NBL, kk * P + p);
+                if (NBL > 1) {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw[r * j * S]);
+                }
+                dft<R, false>(v);
+#pragma unroll
+                for (int r = 0; r < RI; ++r)
+                    acc[it][r] = c_add(acc[it][r], c_mulc(v[r % R], __ldg(xk + j + r * NBL)));
             }
-            dft<R, false>(v);
-#pragma unroll
-            for (int r = 0; r < RI; ++r) acc[it][r] = c_add(acc[it][r], c_mulc(v[r % R], __ldg(xk + j + r * NBL)));
         }
         __syncthreads();
         if constexpr (BULK) {
-            // harmonic k's block has been read (barrier above): refill it
-            // with k + 2; each issuing lane orders the CTA's reads before
-            // its own async-proxy writes
-            if (threadIdx.x < 32 && k + 2 < a.K) {
+            // round t's blocks have been read (barrier above): refill the
+            // buffer with round t + 2; each issuing lane orders the CTA's
+            // reads before its own async-proxy writes
+            if (threadIdx.x < 32 && t + 2 < nround) {
                 fence_proxy_async_smem();
-                stage_rows(k + 2);
+                stage_round(t + 2);
             }
         }
     }
@@ -592,17 +650,17 @@ __device__ __forceinline__ bool xadj_rows(const XArgs& a, int rbase, int rstride
     return true;
 }
 
-template <class LF2, class LI, int S, bool BULK = false, int PP = kP, int TT = kT>
+template <class LF2, class LI, int S, bool BULK = false, int PP = kP, int TT = kT, int KB = 1>
 __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
 {
     constexpr int NX = RInfo<LI>::n(), P = PP;
-    constexpr int LD = xadj_ld<LI, PP>();
+    constexpr int BUF = xadj_buf<LF2, LI, PP, KB>();
     extern __shared__ __align__(16) float2 sm[];
     __shared__ __align__(8) uint64_t bars[2];
     float2* tw = sm;               // W_NX^t; W_MX^t = tw[t S]
     float2* b0 = tw + NX;
-    float2* b1 = b0 + NX * LD;
-    float2* pb = b1 + NX * LD;     // BULK: two [2P][MXS] portrait blocks
+    float2* b1 = b0 + BUF;
+    float2* pb = b1 + BUF;         // BULK: two rounds of KB [2P][MXS] portrait blocks
     const int row0 = blockIdx.x * 2 * P;
     const int nrow = min(2 * P, a.rows - row0);
     using StT = typename std::conditional<BULK, RowSplitSt, RowPairSt>::type;
@@ -611,14 +669,14 @@ __global__ void __launch_bounds__(TT) k_xadj_ct(const XArgs a)
         st = RowSplitSt{a.vout, NX, row0, a.rows, P};
     else
         st = RowPairSt{a.vout, NX, row0, a.rows};
-    xadj_rows<LF2, LI, S, BULK, P, TT>(a, row0, 1, nrow, st, tw, b0, b1, pb, bars);
+    xadj_rows<LF2, LI, S, BULK, P, TT, KB>(a, row0, 1, nrow, st, tw, b0, b1, pb, bars);
 }
 
-template <class LF2, class LI, int S, bool BULK = false, int PP = kP>
+template <class LF2, class LI, int S, bool BULK = false, int PP = kP, int KB = 1>
 constexpr size_t xadj_ct_smem()
 {
     constexpr size_t nx = RInfo<LI>::n();
-    return sizeof(float2) * (nx + 2 * nx * xadj_ld<LI, PP>() + (BULK ? 2 * 2 * PP * xadj_mxs<LF2>() : 0));
+    return sizeof(float2) * (nx + 2 * xadj_buf<LF2, LI, PP, KB>() + (BULK ? xadj_pb<LF2, PP, KB>() : 0));
 }
 
 // Storer into a row-major staging tile: pencil p's real part is tile row
@@ -1196,26 +1254,26 @@ struct XzExchangeSt {
     }
 };
 
-template <class LF2, class LI, class LZ, int C, int PZ, int PX>
+template <class LF2, class LI, class LZ, int C, int PZ, int PX, int KB>
 struct XzGeom {
     static constexpr int NX = RInfo<LI>::n(), NZ = RInfo<LZ>::n();
     static_assert(NX == 2 * C * PZ && NZ == 2 * C * PX, "pencil counts: nx/2C column pairs, nz/2C row pairs");
     static constexpr int TAB = NX + 2 * NZ;                       // float2: W_nx, W_nz, z multiplier
     static constexpr int TABR = (TAB + 15) / 16 * 16;             // 128-byte aligned z-tile
     static constexpr int XT = NZ * PZ;                            // float2: the z-tile
-    static constexpr int A1 = 2 * NX * xadj_ld<LI, PX>() + 2 * 2 * PX * xadj_mxs<LF2>();   // phase-1 buffers
+    static constexpr int A1 = 2 * xadj_buf<LF2, LI, PX, KB>() + xadj_pb<LF2, PX, KB>();   // phase-1 buffers
     static constexpr int UN = A1 > XT ? A1 : XT;                  // phase 2: the z pass's second buffer
     static constexpr size_t smem() { return sizeof(float2) * (size_t)(TABR + XT + UN) + 128; }
 };
 
-template <class LF2, class LI, class LZ, int S, int C, int PZ, int PX, int TT>
+template <class LF2, class LI, class LZ, int S, int C, int PZ, int PX, int TT, int KB>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_xzadj_ct(const __grid_constant__ ZXArgs a)
 {
-    using G = XzGeom<LF2, LI, LZ, C, PZ, PX>;
+    using G = XzGeom<LF2, LI, LZ, C, PZ, PX, KB>;
     constexpr int NX = G::NX, NZ = G::NZ, T = TT, ROWS = NZ / C, QX = NX / C;
     constexpr int NSTZ = RInfo<LZ>::nst, RLZ = RInfo<LZ>::last();
     using LZI = Reverse<LZ>;
-    constexpr int LD = xadj_ld<LI, PX>();
+    constexpr int BUF = xadj_buf<LF2, LI, PX, KB>();
     static_assert(NSTZ >= 2, "two stages at least along z");
     extern __shared__ __align__(128) float2 xz_raw[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -1234,12 +1292,12 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_xzadj_ct(const
     cluster_sync_all();   // every CTA of the cluster runs before any remote store
     // ---- phase 1: drive-axis adjoint of rows z = rank nz/C + r
     float2* b0 = un;
-    float2* b1 = b0 + NX * LD;
-    float2* pb = b1 + NX * LD;
+    float2* b1 = b0 + BUF;
+    float2* pb = b1 + BUF;
     float* xtf = reinterpret_cast<float*>(xt);
     const XzExchangeSt<QX> st{xtf, (int)rank * ROWS, PX, (int)rank};
-    const bool ok = xadj_rows<LF2, LI, S, true, PX, T>(a.x, ((int)rank * ROWS) * a.ny + y, a.ny, ROWS, st, tw, b0,
-                                                       b1, pb, bars);
+    const bool ok = xadj_rows<LF2, LI, S, true, PX, T, KB>(a.x, ((int)rank * ROWS) * a.ny + y, a.ny, ROWS, st, tw,
+                                                           b0, b1, pb, bars);
     cluster_sync_all();   // every column of this CTA's z-tile has landed
     if (!ok) return;
     // ---- phase 2: z correlation of this CTA's columns, one TMA store

@@ -27,9 +27,10 @@ def kernel_path(request, monkeypatch):
     pipelining, the 16-row forward pass with uneven harmonic groups of
     three per CTA, and the separate T_z and drive-axis passes instead of the
     y-slab cluster passes; and once more with those cluster passes on
-    clusters of four CTAs (MH3D_ZX_CLUSTER=4)."""
+    clusters of four CTAs (MH3D_ZX_CLUSTER=4) and the pipelined adjoint in
+    rounds of two harmonics (MH3D_XADJ_KB=2)."""
     for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS",
-              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX", "MH3D_ZX_CLUSTER"):
+              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX", "MH3D_ZX_CLUSTER", "MH3D_XADJ_KB"):
         monkeypatch.delenv(v, raising=False)
     if request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
@@ -41,6 +42,7 @@ def kernel_path(request, monkeypatch):
         monkeypatch.setenv("MH3D_FUSE_ZX", "0")
     elif request.param == "cluster4":
         monkeypatch.setenv("MH3D_ZX_CLUSTER", "4")
+        monkeypatch.setenv("MH3D_XADJ_KB", "2")
     return request.param
 
 
