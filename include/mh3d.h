@@ -58,14 +58,26 @@ typedef enum {
 
 /* Scanner/model geometry (Sec. 2; Sec. 3.3; Sec. 4.1).  Copied at plan time
  * except sensitivity_dev, which the plan keeps as a borrowed pointer: the
- * caller keeps that buffer alive and unchanged for the plan's lifetime. */
+ * caller keeps that buffer alive and unchanged for the plan's lifetime.
+ * Boundary padding: n is the field of view; the model grid is n + 2 pad on
+ * each axis (FFT-periodic there), and every image (rho, x0, the sensitivity)
+ * of the plan lives on that grid, [nz+2pz][ny+2py][nx+2px], the field of
+ * view at offsets (px, py, pz).  Portraits cover the field of view only:
+ * K*nz*ny*(nx/s) samples, row i' of the field of view's mesh being row
+ * px/s + i' of the padded one.  So A = C A_pad (C keeps the field of view's
+ * samples), A^T = A_pad^T C^T (zero padding), and the normal operator is
+ * A_pad^T C^T C A_pad, applied explicitly (normal_mode 1, whatever the
+ * options say).  lambda_relative scales by ||A_pad||_2^2.  The caller crops
+ * the field of view from the solution.  Padded plans are refused by
+ * mh3d_solve_batched, mh3d_mhad and mh3d_forward_noalloc. */
 typedef struct {
     int n[3];                    /* nx (drive axis), ny, nz                                 */
     double voxel_mm[3];          /* voxel size per axis, mm                                 */
     int drive_axis;              /* must be 0 (x, contiguous)                               */
     int ds_factor;               /* s >= 1: keep every s-th drive-axis row (Eq. dN, P)      */
     int ds_offset;               /* 0 <= r < s: kept rows are i = r (mod s)                 */
-    int pad[3];                  /* boundary padding voxels per axis; must be 0 here        */
+    int pad[3];                  /* boundary padding voxels per side per axis (Sec. 3.x,     */
+                                 /* boundary image padding); pad[0] a multiple of ds_factor  */
     int k_min, k_max;            /* harmonics k_min..k_max, 2 <= k_min <= k_max <= 32       */
     double gamma_per_mm;         /* gamma = beta G along the drive axis, 1/mm (> 0)         */
     double gammaA;               /* gamma * drive excursion A, |gamma A| < pi (Theorem 1)   */

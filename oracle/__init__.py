@@ -23,6 +23,10 @@ Functions and the passages they follow:
   subsection).
 * ``mhad``: the multi-harmonic anti-differentiation native image (appendix
   MHAD, Eq. mhadM); numpy's FFT is the library step.
+* ``padded_forward / padded_adjoint / padded_cg``: boundary image padding
+  (Sec. 3.x): the model on the field of view extended by ``pad`` voxels per
+  side, its portraits cropped to the field of view; the adjoint zero-pads;
+  CG on (A^T A + lambda I) x = A^T d with those two.
 """
 from __future__ import annotations
 
@@ -364,3 +368,69 @@ def mhad(d_list, ck_list, lam: float, axis: int = -1, k_min: int = 2) -> np.ndar
         num = num + np.conj(fk) * np.fft.fft(np.asarray(dk, dtype=np.float64), axis=axis) / c
         den = den + np.abs(fk) ** 2
     return np.real(np.fft.ifft(num / den, axis=axis))
+
+
+# ---------------------------------------------------------------------------
+# Boundary image padding (Sec. 3.x): the forward model runs on the field of
+# view extended by pad voxels on each side; the data cover the field of view
+# only, so the padded forward crops the extended portraits and its adjoint
+# zero-pads the field of view's portraits.
+# ---------------------------------------------------------------------------
+def padded_geometry(g_fov: Geometry, pad) -> Geometry:
+    """The geometry of the extended grid (pad = (px, py, pz) per side; px a
+    multiple of the downsampling factor)."""
+    px, py, pz = pad
+    nx, ny, nz = g_fov.n
+    assert px % g_fov.ds_factor == 0
+    return Geometry(n=(nx + 2 * px, ny + 2 * py, nz + 2 * pz), voxel_mm=g_fov.voxel_mm, ds_factor=g_fov.ds_factor,
+                    ds_offset=g_fov.ds_offset, k_min=g_fov.k_min, k_max=g_fov.k_max,
+                    gamma_per_mm=g_fov.gamma_per_mm, gammaA=g_fov.gammaA, transverse_ratio=g_fov.transverse_ratio,
+                    theta=g_fov.theta)
+
+
+def _fov_slices(g_fov: Geometry, pad):
+    px, py, pz = pad
+    _, nzf, nyf, mxf = g_fov.portrait_shape
+    pm = px // g_fov.ds_factor
+    return (slice(None), slice(pz, pz + nzf), slice(py, py + nyf), slice(pm, pm + mxf))
+
+
+def padded_forward(g_fov: Geometry, pad, rho_ext, b_ext=None, tables=None) -> np.ndarray:
+    """d = C A_ext rho on the field of view's portrait mesh."""
+    g = padded_geometry(g_fov, pad)
+    return forward(g, rho_ext, b_ext, tables)[_fov_slices(g_fov, pad)]
+
+
+def padded_adjoint(g_fov: Geometry, pad, d_fov, b_ext=None, tables=None) -> np.ndarray:
+    """rho_ext = A_ext^T C^T d (the field of view's portraits zero-padded)."""
+    g = padded_geometry(g_fov, pad)
+    y = np.zeros(g.portrait_shape, dtype=np.complex128)
+    y[_fov_slices(g_fov, pad)] = np.asarray(d_fov)
+    return adjoint(g, y, b_ext, tables)
+
+
+def padded_cg(g_fov: Geometry, pad, d_fov, b_ext, lam: float, iters: int, tables=None) -> np.ndarray:
+    """Plain CG on (A^T A + lam I) x = A^T d for the padded operator, from
+    x = 0, a fixed number of iterations (test sizes only)."""
+    g = padded_geometry(g_fov, pad)
+    tables = tables or psf_tables(g)
+
+    def nop(v):
+        return padded_adjoint(g_fov, pad, padded_forward(g_fov, pad, v, b_ext, tables), b_ext, tables) + lam * v
+
+    rhs = padded_adjoint(g_fov, pad, d_fov, b_ext, tables)
+    x = np.zeros(g.shape)
+    r = rhs.copy()
+    p = r.copy()
+    rr = float(np.sum(r * r))
+    for _ in range(iters):
+        if rr == 0.0:   # solved exactly (small systems): nothing left to do
+            break
+        q = nop(p)
+        a = rr / float(np.sum(p * q))
+        x += a * p
+        r -= a * q
+        rr_new = float(np.sum(r * r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x

@@ -162,6 +162,87 @@ static mh3d_status build_tables(Plan& P, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
+// Padded plans: the portraits of the field of view sit inside the extended
+// portrait mesh at rows z in [pz, pz + fnz), y in [py, py + fny) and samples
+// i' in [px/s, px/s + fmx) of each row (Sec. 3.x: the padding is part of
+// the model, not of the data).
+// ---------------------------------------------------------------------------
+struct PadGeom {
+    int K, nz, ny, mx;          // extended mesh
+    int fnz, fny, fmx;          // field of view
+    int pz, py, pm;             // offsets (pm = px / s)
+};
+static PadGeom pad_geom(const Plan& P)
+{
+    return PadGeom{P.K, P.nz, P.ny, P.mx, P.fnz, P.fny, P.fmx, P.pad[2], P.pad[1], P.pad[0] / P.s};
+}
+// d_ext = the field-of-view portraits, zero elsewhere
+__global__ void __launch_bounds__(256) k_pad_portraits(const float2* __restrict__ d, float2* __restrict__ e, PadGeom g)
+{
+    const long long n = (long long)g.K * g.nz * g.ny * g.mx;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        long long q = t;
+        const int i = (int)(q % g.mx);
+        q /= g.mx;
+        const int y = (int)(q % g.ny);
+        q /= g.ny;
+        const int z = (int)(q % g.nz);
+        const int k = (int)(q / g.nz);
+        const int fi = i - g.pm, fy = y - g.py, fz = z - g.pz;
+        float2 v = make_float2(0.f, 0.f);
+        if (fi >= 0 && fi < g.fmx && fy >= 0 && fy < g.fny && fz >= 0 && fz < g.fnz)
+            v = d[(((long long)k * g.fnz + fz) * g.fny + fy) * g.fmx + fi];
+        e[t] = v;
+    }
+}
+// d_fov = the field-of-view part of d_ext
+__global__ void __launch_bounds__(256) k_crop_portraits(const float2* __restrict__ e, float2* __restrict__ d, PadGeom g)
+{
+    const long long n = (long long)g.K * g.fnz * g.fny * g.fmx;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        long long q = t;
+        const int fi = (int)(q % g.fmx);
+        q /= g.fmx;
+        const int fy = (int)(q % g.fny);
+        q /= g.fny;
+        const int fz = (int)(q % g.fnz);
+        const int k = (int)(q / g.fnz);
+        d[t] = e[(((long long)k * g.nz + fz + g.pz) * g.ny + fy + g.py) * g.mx + fi + g.pm];
+    }
+}
+// zero the extended portraits outside the field of view (in place)
+__global__ void __launch_bounds__(256) k_mask_portraits(float2* __restrict__ e, PadGeom g)
+{
+    const long long n = (long long)g.K * g.nz * g.ny * g.mx;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        long long q = t;
+        const int i = (int)(q % g.mx);
+        q /= g.mx;
+        const int y = (int)(q % g.ny);
+        q /= g.ny;
+        const int z = (int)(q % g.nz);
+        const int fi = i - g.pm, fy = y - g.py, fz = z - g.pz;
+        if (!(fi >= 0 && fi < g.fmx && fy >= 0 && fy < g.fny && fz >= 0 && fz < g.fnz)) e[t] = make_float2(0.f, 0.f);
+    }
+}
+static int pad_blocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
+cudaError_t pad_portraits(const Plan& P, const float2* d_fov, float2* d_ext, cudaStream_t st)
+{
+    k_pad_portraits<<<pad_blocks((long long)P.K * P.M), 256, 0, st>>>(d_fov, d_ext, pad_geom(P));
+    return cudaGetLastError();
+}
+cudaError_t crop_portraits(const Plan& P, const float2* d_ext, float2* d_fov, cudaStream_t st)
+{
+    k_crop_portraits<<<pad_blocks((long long)P.K * P.Mf), 256, 0, st>>>(d_ext, d_fov, pad_geom(P));
+    return cudaGetLastError();
+}
+cudaError_t mask_portraits(const Plan& P, float2* d_ext, cudaStream_t st)
+{
+    k_mask_portraits<<<pad_blocks((long long)P.K * P.M), 256, 0, st>>>(d_ext, pad_geom(P));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Argument builders
 // ---------------------------------------------------------------------------
 TArgs tpass_args(const Plan& P, int axis /*1 = y, 2 = z*/, const float* in, float* out, const float2* mult)
@@ -379,6 +460,9 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
     xf.vin = t2;
     xf.dout = portrait;
     if ((e = run_xfwd(xf, st)) != cudaSuccess) return e;
+    // a padded plan's data cover the field of view only: A^T A becomes
+    // A^T M A with M the field-of-view mask of the portraits
+    if (P.padded && (e = mask_portraits(P, portrait, st)) != cudaSuccess) return e;
     XArgs xa = xpass_args(P);
     xa.din = portrait;
     xa.vout = t1;
@@ -441,10 +525,15 @@ mh3d_status mh3d_plan_create(const mh3d_geometry* g, void* stream, mh3d_plan* ou
     if (!out) return MH3D_ERR_INVALID_ARG;
     *out = nullptr;
     if (!g) return MH3D_ERR_INVALID_ARG;
-    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
     if (g->drive_axis != 0) return MH3D_ERR_UNSUPPORTED_SIZE;
-    if (g->pad[0] || g->pad[1] || g->pad[2]) return MH3D_ERR_UNSUPPORTED_SIZE;
     if (g->ds_factor < 1 || g->ds_offset < 0 || g->ds_offset >= g->ds_factor) return MH3D_ERR_INVALID_ARG;
+    // boundary padding: the model grid is the field of view extended by pad
+    // voxels per side; along the drive axis a multiple of s keeps the field
+    // of view's portrait mesh a sub-mesh of the extended one
+    for (int a = 0; a < 3; ++a)
+        if (g->pad[a] < 0 || g->n[a] < 1) return MH3D_ERR_INVALID_ARG;
+    if (g->pad[0] % g->ds_factor != 0) return MH3D_ERR_INVALID_ARG;
+    const int nx = g->n[0] + 2 * g->pad[0], ny = g->n[1] + 2 * g->pad[1], nz = g->n[2] + 2 * g->pad[2];
     if (g->k_min < 2 || g->k_max < g->k_min || g->k_max - g->k_min + 1 > kMaxK) return MH3D_ERR_INVALID_ARG;
     if (!(g->gamma_per_mm > 0) || !(std::fabs(g->gammaA) < 3.14159265358979) || !(g->transverse_ratio > 0))
         return MH3D_ERR_INVALID_ARG;
@@ -468,6 +557,17 @@ mh3d_status mh3d_plan_create(const mh3d_geometry* g, void* stream, mh3d_plan* ou
     P->mx = mx;
     P->N = (long long)nx * ny * nz;
     P->M = (long long)mx * ny * nz;
+    for (int a = 0; a < 3; ++a) P->pad[a] = g->pad[a];
+    P->padded = g->pad[0] || g->pad[1] || g->pad[2];
+    P->fnx = g->n[0];
+    P->fny = g->n[1];
+    P->fnz = g->n[2];
+    P->fmx = g->n[0] / g->ds_factor;
+    P->Mf = (long long)P->fmx * P->fny * P->fnz;
+    if (g->n[0] % g->ds_factor != 0) {
+        delete P;
+        return MH3D_ERR_UNSUPPORTED_SIZE;
+    }
     for (int a = 0; a < 3; ++a) P->vox[a] = g->voxel_mm[a];
     P->gamma = g->gamma_per_mm;
     P->gammaA = g->gammaA;
@@ -571,6 +671,13 @@ mh3d_status mh3d_forward(mh3d_plan P, const float* rho, void* d, void* stream)
         return MH3D_ERR_INVALID_ARG;
     }
     P->err.clear();
+    if (P->padded) {   // forward on the extended grid, then the field of view's portraits
+        mh3d_status s = ensure_portrait(*P);
+        if (s != MH3D_OK) return s;
+        MH3D_TRY(P, launch_forward(*P, rho, P->w.portrait, P->w.t1, P->w.t2, (cudaStream_t)stream));
+        MH3D_TRY(P, crop_portraits(*P, P->w.portrait, (float2*)d, (cudaStream_t)stream));
+        return MH3D_OK;
+    }
     MH3D_TRY(P, launch_forward(*P, rho, (float2*)d, P->w.t1, P->w.t2, (cudaStream_t)stream));
     return MH3D_OK;
 }
@@ -583,6 +690,13 @@ mh3d_status mh3d_adjoint(mh3d_plan P, const void* d, float* rho, void* stream)
         return MH3D_ERR_INVALID_ARG;
     }
     P->err.clear();
+    if (P->padded) {   // the field of view's portraits zero-padded, then the adjoint on the extended grid
+        mh3d_status s = ensure_portrait(*P);
+        if (s != MH3D_OK) return s;
+        MH3D_TRY(P, pad_portraits(*P, (const float2*)d, P->w.portrait, (cudaStream_t)stream));
+        MH3D_TRY(P, launch_adjoint(*P, P->w.portrait, rho, P->w.t1, P->w.t2, (cudaStream_t)stream));
+        return MH3D_OK;
+    }
     MH3D_TRY(P, launch_adjoint(*P, (const float2*)d, rho, P->w.t1, P->w.t2, (cudaStream_t)stream));
     return MH3D_OK;
 }
@@ -597,12 +711,14 @@ mh3d_status mh3d_normal(mh3d_plan P, const float* p, float* q, const mh3d_solve_
     mh3d_status v = validate_opts(*P, *o);
     if (v != MH3D_OK) return v;
     P->err.clear();
-    if (o->normal_mode == 1) {
+    // a padded plan's normal operator is the masked explicit one (mode 1)
+    const int mode = P->padded ? 1 : o->normal_mode;
+    if (mode == 1) {
         mh3d_status s = ensure_portrait(*P);
         if (s != MH3D_OK) return s;
     }
-    MH3D_TRY(P, launch_normal(*P, o->normal_mode, reg_args(*P, *o), p, q, P->w.t1, P->w.t2, P->w.portrait,
-                              nullptr, nullptr, nullptr, (cudaStream_t)stream));
+    MH3D_TRY(P, launch_normal(*P, mode, reg_args(*P, *o), p, q, P->w.t1, P->w.t2, P->w.portrait, nullptr, nullptr,
+                              nullptr, (cudaStream_t)stream));
     return MH3D_OK;
 }
 

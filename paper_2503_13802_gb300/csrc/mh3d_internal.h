@@ -52,6 +52,7 @@ struct SolveWork {
     float* rhs = nullptr;
     float* s = nullptr;           // A r (single-reduction CG)
     float2* portrait = nullptr;   // explicit mode only (allocated on first use)
+    float2* dstage = nullptr;     // padded plans: field-of-view portraits staged by mh3d_solve_host
     double* red = nullptr;        // reduction partials (see solve.cu)
     int* flags = nullptr;         // [done, iters, status, spare]
     double* hist = nullptr;       // per-iteration relative residual
@@ -104,6 +105,14 @@ struct Plan {
     int nx = 1, ny = 1, nz = 1, s = 1, r = 0, K = 1, kmin = 2, kmax = 2;
     int mx = 1;
     long long N = 1, M = 1;       // voxels; portrait samples per harmonic
+    // boundary padding (Sec. 3.x, boundary image padding): the model grid
+    // above is the field of view (fnx, fny, fnz) extended by pad voxels on
+    // each side; the portraits a caller passes cover the field of view only
+    // (fmx samples per row, Mf per harmonic)
+    int pad[3] = {0, 0, 0};
+    int fnx = 1, fny = 1, fnz = 1, fmx = 1;
+    long long Mf = 1;
+    bool padded = false;
     double vox[3] = {1, 1, 1};
     double gamma = 1, gammaA = 1, tratio = 0.5;
     std::vector<double> theta;
@@ -146,6 +155,13 @@ struct Plan {
 
 // mhad.cu
 void mhad_free(Plan& P);
+
+// Padded plans (capi.cu): field-of-view portraits <-> the extended portrait
+// mesh, and the mask of the explicit normal operator.
+cudaError_t pad_portraits(const Plan& P, const float2* d_fov, float2* d_ext, cudaStream_t st);
+cudaError_t crop_portraits(const Plan& P, const float2* d_ext, float2* d_fov, cudaStream_t st);
+cudaError_t mask_portraits(const Plan& P, float2* d_ext, cudaStream_t st);
+mh3d_status ensure_portrait(Plan& P);
 
 // psf_host.cpp
 double langevin_deriv_host(int k, double x);

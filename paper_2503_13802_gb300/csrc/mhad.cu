@@ -107,6 +107,7 @@ mh3d_status fail(Plan& P, const std::string& msg, mh3d_status s)
 
 mh3d_status mhad_run(Plan& P, const float2* d, double lambda, int upsample, float* out, cudaStream_t st)
 {
+    if (P.padded) return fail(P, "mh3d_mhad: padded plans are not supported", MH3D_ERR_INVALID_ARG);
     if (!(lambda > 0.0) || !std::isfinite(lambda))
         return fail(P, "mh3d_mhad: lambda must be finite and > 0", MH3D_ERR_INVALID_ARG);
     if (!P.mhad_tab)

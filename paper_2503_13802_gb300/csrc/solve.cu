@@ -258,6 +258,7 @@ void solve_free(Plan& P)
     P.graph_stream = nullptr;
     if (w.base) cudaFree(w.base);
     if (w.portrait) cudaFree(w.portrait);
+    if (w.dstage) cudaFree(w.dstage);
     if (w.flags) cudaFree(w.flags);
     if (w.hist) cudaFree(w.hist);
     if (w.flags_host) cudaFreeHost(w.flags_host);
@@ -938,6 +939,18 @@ mh3d_status mh3d_solve(mh3d_plan P, const void* d, const mh3d_solve_opts* o, flo
     mh3d_status v = validate_opts(*P, *o);
     if (v != MH3D_OK) return v;
     P->err.clear();
+    if (P->padded) {
+        // the field of view's portraits zero-padded into the portrait buffer
+        // (read once, by A^T d, before the explicit normal operator reuses
+        // it); the masked explicit normal operator throughout
+        mh3d_status s = ensure_portrait(*P);
+        if (s != MH3D_OK) return s;
+        MH3D_CK(*P, pad_portraits(*P, (const float2*)d, P->w.portrait, (cudaStream_t)stream));
+        mh3d_solve_opts op = *o;
+        op.normal_mode = 1;
+        if (o->solver == 1) return apg_solve(*P, P->w.portrait, op, rho, info, (cudaStream_t)stream);
+        return cg_solve(*P, P->w.portrait, op, rho, info, (cudaStream_t)stream);
+    }
     if (o->solver == 1) return apg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
     return cg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
 }
@@ -963,12 +976,27 @@ mh3d_status mh3d_solve_host(mh3d_plan P, const void* d_host, const mh3d_solve_op
     // device staging: the portrait buffer (allocated on demand) and the rhs slot
     mh3d_status s = ensure_portrait(*P);
     if (s != MH3D_OK) return s;
-    const size_t dbytes = sizeof(float2) * (size_t)P->K * P->M;
-    MH3D_CK(*P, cudaMemcpyAsync(P->w.portrait, d_host, dbytes, cudaMemcpyHostToDevice, st));
+    // a padded plan stages the field of view's portraits in their own buffer
+    // (the solve pads them into the portrait buffer)
+    float2* stage = P->w.portrait;
+    if (P->padded) {
+        if (!P->w.dstage) {
+            const size_t b = sizeof(float2) * (size_t)P->K * P->Mf;
+            if (dev_malloc(&P->w.dstage, b) != cudaSuccess) {
+                P->w.dstage = nullptr;
+                P->err = "cudaMalloc of the portrait staging buffer failed";
+                return MH3D_ERR_OOM;
+            }
+            P->work_bytes += b;
+        }
+        stage = P->w.dstage;
+    }
+    const size_t dbytes = sizeof(float2) * (size_t)P->K * P->Mf;
+    MH3D_CK(*P, cudaMemcpyAsync(stage, d_host, dbytes, cudaMemcpyHostToDevice, st));
     // The staged portraits are read once (A^T d) before the explicit normal
     // mode reuses the buffer as scratch; the image is copied back from the
     // solver's iterate.
-    s = mh3d_solve(P, P->w.portrait, o, P->w.t2, info, stream);
+    s = mh3d_solve(P, stage, o, P->w.t2, info, stream);
     if (s != MH3D_OK && s != MH3D_ERR_NOT_CONVERGED) return s;
     MH3D_CK(*P, cudaMemcpyAsync(rho_host, P->w.x, sizeof(float) * P->N, cudaMemcpyDeviceToHost, st));
     MH3D_CK(*P, cudaStreamSynchronize(st));
@@ -999,6 +1027,10 @@ mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* con
             }
         mh3d_status s = validate_opts(*ps[v], *o);
         if (s != MH3D_OK) return s;
+        if (ps[v]->padded) {
+            P0.err = "mh3d_solve_batched: volume " + std::to_string(v) + " has a padded plan (solve it with mh3d_solve)";
+            return MH3D_ERR_INVALID_ARG;
+        }
     }
     if (o->x0_dev) {
         P0.err = "mh3d_solve_batched: x0_dev must be NULL (one warm start cannot serve several volumes)";

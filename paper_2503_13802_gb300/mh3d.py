@@ -137,16 +137,21 @@ class Plan:
     def __init__(self, n: Sequence[int], voxel_mm=(1.0, 1.0, 1.0), ds_factor: int = 1, ds_offset: int = 0,
                  k_min: int = 2, k_max: int = 5, gamma_per_mm: float = 1.387016, gammaA: float = 2.0,
                  transverse_ratio: float = 0.5, theta: Optional[Sequence[float]] = None, sensitivity=None,
-                 stream=None):
+                 stream=None, pad: Sequence[int] = (0, 0, 0)):
+        """n: the field of view (nx, ny, nz); pad: boundary padding voxels per
+        side (px a multiple of ds_factor).  Images and the sensitivity live on
+        the padded grid (shape); portraits on the field of view's mesh."""
         import torch
 
         lib = load()
         self.n = tuple(int(v) for v in n)
+        self.pad = tuple(int(v) for v in pad)
         self.K = k_max - k_min + 1
         self.ds_factor = ds_factor
         nx, ny, nz = self.n
-        self.N = nx * ny * nz
-        self.shape = (nz, ny, nx)
+        px, py, pz = self.pad
+        self.N = (nx + 2 * px) * (ny + 2 * py) * (nz + 2 * pz)
+        self.shape = (nz + 2 * pz, ny + 2 * py, nx + 2 * px)
         self.portrait_shape = (self.K, nz, ny, nx // ds_factor)
         self.sensitivity = None
         if sensitivity is not None:
@@ -158,7 +163,7 @@ class Plan:
         g.voxel_mm[:] = list(voxel_mm)
         g.drive_axis = 0
         g.ds_factor, g.ds_offset = ds_factor, ds_offset
-        g.pad[:] = [0, 0, 0]
+        g.pad[:] = list(self.pad)
         g.k_min, g.k_max = k_min, k_max
         g.gamma_per_mm, g.gammaA, g.transverse_ratio = gamma_per_mm, gammaA, transverse_ratio
         self._theta = None
