@@ -231,6 +231,28 @@ mh3d_status mh3d_mhad(mh3d_plan plan, const void* d_dev, double lambda, int upsa
 mh3d_status mh3d_mhad_warm_start(mh3d_plan plan, const void* d_dev, double lambda, float* x0_dev, double* alpha_dev,
                                  void* stream);
 
+/* Portrait phase calibration (Sec. 4.4): estimates theta_k from portraits
+ * measured as e^{i theta_k} times a real field.
+ *   theta_k modulo pi: 1/2 arg of the sum of d_k^2 over the high-SNR samples
+ *   (|d_k| >= frac max |d_k|).  The remaining pi, when ds_factor = 1: the
+ *   single-harmonic back-projections A_k^T Re(e^{-i theta_k} d_k) correlate
+ *   positively for the true signs (along the drive axis their product is
+ *   non-negative at every frequency), which fixes every sign relative to
+ *   the strongest one; the common sign is the one whose 30-iteration CG
+ *   reconstruction (lambda 1e-2 relative) is positively skewed, as the
+ *   image of a non-negative density is.  With ds_factor > 1 theta_k is
+ *   returned modulo pi.
+ *   d_dev: the caller's portraits (K*nz*ny*(nx/s) complex64, device);
+ *   frac in (0, 1]; theta_out: K doubles (host) in (-pi, pi]; resolved_out:
+ *   K ints (host, may be NULL), 1 where the pi was decided, 0 where theta_k
+ *   is known modulo pi only.  Synchronises `stream`; allocates and frees its
+ *   scratch (K + 1 images and one portrait set); uses the plan's workspace
+ *   and runs a 30-iteration solve on it.
+ *   The paper picks high-SNR regions by hand and decides the pi with a trial
+ *   reconstruction; these rules are this library's automatic stand-ins. */
+mh3d_status mh3d_estimate_phase(mh3d_plan plan, const void* d_dev, double frac, double* theta_out, int* resolved_out,
+                                void* stream);
+
 /* Tile autotuning: times the fused normal operator (the CG loop's kernels)
  * for each transverse-pass tile width (16 and 8 columns) on the plan's
  * workspace and keeps the fastest for this plan.  The choice is remembered

@@ -434,3 +434,51 @@ def padded_cg(g_fov: Geometry, pad, d_fov, b_ext, lam: float, iters: int, tables
         p = r + (rr_new / rr) * p
         rr = rr_new
     return x
+
+
+# ---------------------------------------------------------------------------
+# Portrait phase calibration (Sec. 4.4).  The measured portrait of harmonic
+# k is e^{i theta_k} times a real field.
+#  * theta_k modulo pi: the direction of the high-SNR samples (|d_k| >= frac
+#    max |d_k|) in the complex plane, 1/2 arg sum d_k^2 (the samples are
+#    +-|d| e^{i theta}, so their squares all point along 2 theta);
+#  * the remaining pi, when the portraits are not downsampled (s = 1): the
+#    single-harmonic back-projections B_k = A_k^T Re(e^{-i theta_k} d_k)
+#    correlate positively for the true signs (along the drive axis
+#    <B_j, B_k> sums |X_j|^2 |X_k|^2 |U|^2 over the frequencies, U the
+#    filtered density), which fixes every sign relative to the harmonic with
+#    the largest ||B_k||; the common sign is the one whose short CG
+#    reconstruction (30 iterations, lambda = 1e-2 relative) is positively
+#    skewed (sum x^3 > 0), as the image of a sparse non-negative density is;
+#  * with s > 1 the row selector's aliases break the correlation argument
+#    and theta_k is returned modulo pi.
+# Returns (theta, resolved): theta in (-pi, pi]; resolved = 1 for every
+# harmonic when s = 1, else 0.
+# ---------------------------------------------------------------------------
+def estimate_phase(g: Geometry, d, frac: float = 0.5, b=None, tables=None):
+    d = np.asarray(d, dtype=np.complex128)
+    K = g.K
+    th = np.zeros(K)
+    for j in range(K):
+        a = np.abs(d[j])
+        sj = a >= frac * a.max() if a.max() > 0 else np.zeros(a.shape, dtype=bool)
+        th[j] = 0.5 * np.angle(np.sum(d[j][sj] ** 2))
+    resolved = np.zeros(K, dtype=np.int32)
+    if g.ds_factor == 1:
+        tables = tables or psf_tables(g)
+        g0 = Geometry(n=g.n, voxel_mm=g.voxel_mm, ds_factor=1, ds_offset=0, k_min=g.k_min, k_max=g.k_max,
+                      gamma_per_mm=g.gamma_per_mm, gammaA=g.gammaA, transverse_ratio=g.transverse_ratio)
+        B = []
+        for j in range(K):
+            y = np.zeros(g.portrait_shape, dtype=np.complex128)
+            y[j] = np.real(np.exp(-1j * th[j]) * d[j])
+            B.append(adjoint(g0, y, b, tables))
+        r = int(np.argmax([float(np.sum(x * x)) for x in B]))
+        sig = np.array([1.0 if j == r else (1.0 if float(np.sum(B[j] * B[r])) >= 0 else -1.0) for j in range(K)])
+        y = np.array([sig[j] * np.real(np.exp(-1j * th[j]) * d[j]) for j in range(K)]).astype(np.complex128)
+        x, _, _ = cg(g0, y, b, SolveOpts(lam=1e-2, lam_relative=True, rel_tol=0.0, max_iter=30), tables=tables)
+        if float(np.sum(x ** 3)) < 0:
+            sig = -sig
+        th = np.where(sig < 0, th + np.pi, th)
+        resolved[:] = 1
+    return np.angle(np.exp(1j * th)), resolved

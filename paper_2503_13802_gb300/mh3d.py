@@ -57,7 +57,7 @@ _lib = None
 EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoint", "mh3d_normal", "mh3d_solve",
            "mh3d_solve_host", "mh3d_solve_batched", "mh3d_forward_noalloc", "mh3d_operator_norm2", "mh3d_last_error",
            "mh3d_plan_workspace_bytes", "mh3d_version", "mh3d_plan_autotune", "mh3d_plan_spectra", "mh3d_mhad",
-           "mh3d_mhad_warm_start"]
+           "mh3d_mhad_warm_start", "mh3d_estimate_phase"]
 
 
 def library_path() -> str:
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
     lib.mh3d_forward_noalloc.argtypes = [POINTER(mh3d_geometry), P, P, P]
     lib.mh3d_mhad.argtypes = [P, P, c_double, c_int, P, P]
     lib.mh3d_mhad_warm_start.argtypes = [P, P, c_double, P, P, P]
+    lib.mh3d_estimate_phase.argtypes = [P, P, c_double, POINTER(c_double), POINTER(c_int), P]
     lib.mh3d_last_error.argtypes = [P]
     lib.mh3d_last_error.restype = c_char_p
     lib.mh3d_plan_workspace_bytes.argtypes = [P]
@@ -375,6 +376,23 @@ def mh3d_mhad_warm_start(plan: Plan, d, lam: float, x0, alpha=None, stream=None)
     _check(plan.handle, lib.mh3d_mhad_warm_start(plan.handle, c_void_p(p_d), c_double(lam), c_void_p(p_x),
                                                  c_void_p(p_a), c_void_p(_stream_ptr(stream))))
     return x0
+
+
+def mh3d_estimate_phase(plan: Plan, d, frac: float = 0.5, stream=None):
+    """(theta [K], resolved [K]) estimated from the portraits d (see
+    include/mh3d.h): numpy arrays; resolved[k] = 0 where theta_k is known
+    modulo pi only."""
+    import numpy as np
+    import torch
+
+    lib = load()
+    K, nz, ny, mx = plan.portrait_shape
+    p_d = _dev_ptr(d, torch.complex64, K * nz * ny * mx, "d")
+    th = (c_double * K)()
+    res = (c_int * K)()
+    _check(plan.handle, lib.mh3d_estimate_phase(plan.handle, c_void_p(p_d), c_double(frac), th, res,
+                                                c_void_p(_stream_ptr(stream))))
+    return np.array(th[:], dtype=np.float64), np.array(res[:], dtype=np.int32)
 
 
 def mh3d_operator_norm2(plan: Plan) -> float:

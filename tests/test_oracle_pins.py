@@ -562,3 +562,40 @@ def test_padded_cg_matches_dense_normal_equations():
     ref = np.linalg.solve(A.T @ A + lam * np.eye(n), rhs)
     x = oracle.padded_cg(g, pad, d, None, lam, 100)
     np.testing.assert_allclose(x.ravel(), ref, atol=1e-9 * np.abs(ref).max())
+
+
+# --------------------------------------------------------------------------
+# Portrait phase calibration (Sec. 4.4)
+# --------------------------------------------------------------------------
+
+def test_phase_modulo_pi_is_the_principal_axis():
+    """Samples e^{i theta} a_j with real a_j of both signs: the estimate is
+    theta modulo pi exactly (closed form: every a_j^2 e^{2 i theta} points
+    along 2 theta)."""
+    rng = np.random.default_rng(21)
+    for theta in (-2.9, -1.2, 0.0, 0.7, 1.5707, 3.1):
+        a = rng.standard_normal((1, 3, 4, 5))
+        d = np.exp(1j * theta) * a
+        g = _geom((5, 4, 3), kmin=2, kmax=2)
+        est, _ = oracle.estimate_phase(g, d, frac=1e-9)
+        diff = np.angle(np.exp(2j * (est[0] - theta))) / 2
+        assert abs(diff) <= 1e-12, (theta, est)
+
+
+@pytest.mark.parametrize("n,s,kmin,kmax", [((48, 16, 12), 1, 3, 6), ((32, 24, 16), 1, 2, 7), ((64, 12, 8), 2, 2, 9)])
+def test_phase_recovers_the_generating_phases(n, s, kmin, kmax):
+    """Noise-free portraits of a non-negative phantom made with known phases:
+    with s = 1 every theta_k is resolved and equals the generating one; with
+    s = 2 none is resolved and each equals it modulo pi."""
+    K = kmax - kmin + 1
+    theta = np.random.default_rng(kmin + K).uniform(-np.pi, np.pi, K)
+    g = _geom(n, s=s, kmin=kmin, kmax=kmax, theta=list(theta))
+    rho = W.phantom(n, (1.0, 1.0, 1.0), 3, 6, 1)
+    d = oracle.forward(g, rho)
+    est, res = oracle.estimate_phase(g, d)
+    assert res.all() if s == 1 else not res.any()
+    err = np.angle(np.exp(1j * (est - theta)))
+    err_pi = np.angle(np.exp(2j * (est - theta))) / 2
+    if res.any():
+        assert np.abs(err[res == 1]).max() <= 1e-10, err
+    assert np.abs(err_pi).max() <= 1e-10, err_pi
