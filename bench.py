@@ -76,7 +76,7 @@ def fused_zx(wl) -> bool:
     if os.environ.get("MH3D_FUSE_ZX", "1").startswith("0") or os.environ.get("MH3D_GENERIC", "0") not in ("", "0"):
         return False
     nx, _, nz = wl.n
-    return wl.ds_factor == 2 and (nx, nz) in ((128, 64), (64, 64), (96, 64), (192, 96))
+    return wl.ds_factor == 2 and (nx, nz) in ((128, 64), (64, 64), (96, 64))
 
 
 def dist_env():

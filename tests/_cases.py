@@ -61,7 +61,7 @@ OP_CASES = {
     "zx128": params((128, 6, 64), s=2, kmin=2, kmax=9, theta=[0.2, -0.4, 0.9, 1.3, -2.0, 2.6, 0.0, -1.1]),
     "zx64": params((64, 4, 64), s=2, kmin=2, kmax=5),
     "zx96": params((96, 3, 64), s=2, r=1, kmin=2, kmax=9),
-    "zx192": params((192, 2, 96), s=2, kmin=2, kmax=5),
+    "zx192": params((192, 2, 96), s=2, kmin=2, kmax=5),      # not fused (separate passes)
     # an odd harmonic count on the specialised drive-axis passes (the
     # adjoint's last round of two harmonics holds one)
     "oddk5": params((128, 6, 32), s=2, kmin=2, kmax=6, theta=[0.3, -1.2, 2.2, 0.7, -0.4]),
