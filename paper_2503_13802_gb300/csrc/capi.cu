@@ -329,7 +329,7 @@ cudaError_t launch_forward(const Plan& P, const float* rho, float2* d, float* t1
     ty.bin = P.sens;
     if ((e = run_tpass(ty, tpass_outer(P, 1), st)) != cudaSuccess) return e;
     if (ct_zxfwd_available(P.nx, P.nz, P.s) && ((uintptr_t)t1 & 15u) == 0) {
-        // T_z and the drive-axis forward in one launch (clusters of two CTAs per y-slab)
+        // T_z and the drive-axis forward in one launch (a cluster of CTAs per y-slab)
         ZXArgs z;
         z.x = xpass_args(P);
         z.x.dout = d;
@@ -353,7 +353,7 @@ cudaError_t launch_adjoint(const Plan& P, const float2* d, float* rho, float* t1
     const bool fused = ct_xzadj_available(P.nx, P.nz, P.s) && ((uintptr_t)d & 15u) == 0 &&
                        ((uintptr_t)t2 & 15u) == 0 && P.mx % 2 == 0 && P.M % 2 == 0;
     if (fused) {
-        // the drive-axis adjoint and T_z^T in one launch (clusters of two CTAs per y-slab)
+        // the drive-axis adjoint and T_z^T in one launch (a cluster of CTAs per y-slab)
         ZXArgs z;
         z.x = xpass_args(P);
         z.x.din = d;
@@ -404,7 +404,7 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
     if (mode == 0 && reg.kind == 0 && ct_zxnrm_available(P.nx, P.nz, P.s) && a16(t1) && a16(in) && a16(out) &&
         (!P.sens || a16(P.sens))) {
-        // T_z and the drive-axis normal pass in one launch (clusters of two CTAs per y-slab)
+        // T_z and the drive-axis normal pass in one launch (a cluster of CTAs per y-slab)
         ZXArgs z;
         z.x = xpass_args(P);
         z.x.b = P.sens;

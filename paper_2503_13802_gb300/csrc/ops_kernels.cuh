@@ -134,10 +134,10 @@ struct XArgs {
     int* status = nullptr;           // device status word for bounded-wait timeouts
 };
 
-// Fused T_z + drive-axis normal pass: one y-slab per cluster of two CTAs
-// (ops_ct.cuh, k_zxnrm_ct).
+// The y-slab cluster passes (ops_ct.cuh: k_zxnrm_ct, k_zxfwd_ct,
+// k_xzadj_ct): one y-slab per cluster of C CTAs.
 struct ZXArgs {
-    CUtensorMap tz;                  // the z-pass input (T_y output), box (nx/2 x 1 x nz)
+    CUtensorMap tz;                  // the z volume (input, or the adjoint's output), box (nx/C x 1 x nz)
     XArgs x;                         // the normal pass; x.vin unused (rows come through the cluster)
     const float2* twz = nullptr;     // W_nz^t
     const float2* muz = nullptr;     // z-axis normal multiplier [nz]
