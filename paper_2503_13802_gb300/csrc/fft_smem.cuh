@@ -279,6 +279,68 @@ __device__ __forceinline__ double block_sum_f64(double v, double* sh /* >= 32 do
     return t;
 }
 
+// Block-wide sums of one or two compensated FP32 accumulators (all threads
+// participate; results valid in thread 0).  The FP64 pipe is narrow on this
+// part, so the warp levels add the (hi, lo) pairs in FP32: the high words
+// by TwoSum (Knuth), whose exact rounding error joins the low words.  A
+// pair carries about 48 bits, as each thread's accumulator did.  Each warp's
+// total becomes one double, and thread 0 adds the warp totals in FP64 in
+// warp order, so the result does not depend on timing.
+__device__ __forceinline__ void warp_sum_acc(float& hi, float& lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = hi + h2;
+        const float bb = s - hi;
+        const float e = (hi - (s - bb)) + (h2 - bb);
+        hi = s;
+        lo = (lo + l2) + e;
+    }
+}
+
+__device__ __forceinline__ double block_sum_acc(const DotAcc& a, double* sh /* >= 32 doubles */)
+{
+    float hi = a.hi, lo = a.lo;
+    warp_sum_acc(hi, lo);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = (double)hi + (double)lo;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) t += sh[w];
+    }
+    return t;
+}
+
+__device__ __forceinline__ void block_sum_acc2(const DotAcc& a, const DotAcc& b, double* sh /* >= 32 doubles */,
+                                               double* ta, double* tb)
+{
+    float ha = a.hi, la = a.lo, hb = b.hi, lb = b.lo;
+    warp_sum_acc(ha, la);
+    warp_sum_acc(hb, lb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[wid] = (double)ha + (double)la;
+        sh[16 + wid] = (double)hb + (double)lb;
+    }
+    __syncthreads();
+    double s0 = 0.0, s1 = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; ++w) {
+            s0 += sh[w];
+            s1 += sh[16 + w];
+        }
+    }
+    *ta = s0;
+    *tb = s1;
+}
+
 // Deterministic FP64 sum of n partials, identical in every block (same
 // order): result returned to all threads of the block.
 __device__ __forceinline__ double sum_partials(const double* __restrict__ part, int n, double* sh)
@@ -296,9 +358,10 @@ __device__ __forceinline__ double sum_partials(const double* __restrict__ part, 
 
 // Grid-wide deterministic FP64 reduction.  Each block stores its partial
 // (v valid in thread 0) at part[bid]; the last block to arrive (atomic
-// ticket) sums part[0..nparts) in index order and stores the total in *out,
-// then re-arms the ticket counter for the next launch.  Consumers read the
-// single scalar.
+// ticket) sums part[0..nparts) in a fixed order (warp 0: lane l takes
+// l, l + 32, ..., then a butterfly over the lanes) and stores the total in
+// *out, then re-arms the ticket counter for the next launch.  Consumers
+// read the single scalar.
 __device__ __forceinline__ void grid_sum_finalize(double v, double* part, int bid, int nparts, unsigned int* counter,
                                                   double* out, double* sh)
 {
@@ -310,11 +373,14 @@ __device__ __forceinline__ void grid_sum_finalize(double v, double* part, int bi
         am_last = (t == (unsigned int)nparts - 1u);
     }
     __syncthreads();
-    if (am_last) {
+    // warp 0 alone: a strided FP64 sum per lane, then the lanes in a fixed
+    // butterfly (no block barrier on the last block's tail)
+    if (am_last && threadIdx.x < 32) {
         __threadfence();
         double acc = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += __ldcg(part + i);
-        acc = block_sum_f64(acc, sh);
+        for (int i = threadIdx.x; i < nparts; i += 32) acc += __ldcg(part + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (threadIdx.x == 0) {
             *out = acc;
             *counter = 0u;
@@ -337,15 +403,18 @@ __device__ __forceinline__ void grid_sum_finalize2(double v0, double v1, double*
         am_last2 = (t == (unsigned int)nparts - 1u);
     }
     __syncthreads();
-    if (am_last2) {
+    if (am_last2 && threadIdx.x < 32) {
         __threadfence();
         double a0 = 0.0, a1 = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nparts; i += 32) {
             a0 += __ldcg(part0 + i);
             a1 += __ldcg(part1 + i);
         }
-        a0 = block_sum_f64(a0, sh);
-        a1 = block_sum_f64(a1, sh);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        }
         if (threadIdx.x == 0) {
             *out0 = a0;
             *out1 = a1;

@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(256) k_mhad_dots(const float2* __restrict__ a,
         aa.add(x.x, x.x);
         aa.add(x.y, x.y);
     }
-    const double t1 = block_sum_f64(ad.value(), red);
-    const double t2 = block_sum_f64(aa.value(), red);
+    const double t1 = block_sum_acc(ad, red);
+    const double t2 = block_sum_acc(aa, red);
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = t1;
         part[2 * blockIdx.x + 1] = t2;

@@ -35,8 +35,9 @@ __global__ void __launch_bounds__(256) k_tpass(const TArgs a)
 {
     extern __shared__ float2 sm[];
     __shared__ double red[34];
+    __shared__ float cgs[3];
     float beta = 0.f, alpha = 0.f;
-    if (a.cg.flags && !cg_enter(a.cg, a.pupdate != 0, &beta, red, &alpha)) return;
+    if (a.cg.flags && !cg_enter_cta(a.cg, a.pupdate != 0, &beta, &alpha, cgs)) return;
     const int n = a.n, P = a.cols / 2, ld = P + 1;
     float2* tw = sm;
     float2* mu = tw + n;
@@ -57,10 +58,10 @@ __global__ void __launch_bounds__(256) k_tpass(const TArgs a)
     fft_run<true, true, true>(a.rp, MulLd{sr, ld, mu}, TStore{&a, base, x0, &acc, a.part2 ? &acc2 : nullptr}, so,
                               sr, ld, P, tw);
     if (a.epilogue && a.part) {
-        const double t = block_sum_f64(acc.value(), red);
+        const double t = block_sum_acc(acc, red);
         const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
         if (a.part2) {
-            const double t2 = block_sum_f64(acc2.value(), red);
+            const double t2 = block_sum_acc(acc2, red);
             grid_sum_finalize2(t, t2, a.part, a.part2, bid, nb, a.ticket, a.sum_out, a.sum_out2, red);
         } else {
             grid_sum_finalize(t, a.part, bid, nb, a.ticket, a.sum_out, red);
@@ -166,9 +167,9 @@ __global__ void __launch_bounds__(256) k_xnrm(const XArgs a)
     fft_run<true, true, false>(a.rpx, QLd{Ar, ldA, a.Q, a.mx, a.s},
                                NrmEpiSt{&a, row0, &dacc, a.part2 ? &dacc2 : nullptr}, Ao, Ar, ldA, P, twx);
     if (a.part) {
-        const double t = block_sum_f64(dacc.value(), red);
+        const double t = block_sum_acc(dacc, red);
         if (a.part2) {
-            const double t2 = block_sum_f64(dacc2.value(), red);
+            const double t2 = block_sum_acc(dacc2, red);
             grid_sum_finalize2(t, t2, a.part, a.part2, blockIdx.x, gridDim.x, a.ticket, a.sum_out, a.sum_out2, red);
         } else {
             grid_sum_finalize(t, a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out, red);

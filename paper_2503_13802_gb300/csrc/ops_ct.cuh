@@ -102,10 +102,11 @@ __global__ void __launch_bounds__(TT) k_tpass_ct(const __grid_constant__ TArgs a
     extern __shared__ __align__(128) float2 sm_raw[];
     __shared__ double red[34];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ float cgs[3];
     float beta = 0.f, alpha = 0.f;
     pdl_trigger();
     pdl_wait();   // no-ops unless launched with programmatic serialization
-    if (a.cg.flags && !cg_enter(a.cg, a.pupdate != 0, &beta, red, &alpha)) return;
+    if (a.cg.flags && !cg_enter_cta(a.cg, a.pupdate != 0, &beta, &alpha, cgs)) return;
     // 128-byte aligned start for the TMA boxes (the launcher adds the slack)
     float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
     float2* tw = sm;
@@ -272,13 +273,13 @@ __global__ void __launch_bounds__(TT) k_tpass_ct(const __grid_constant__ TArgs a
     }
 
     if (mode == 3 && a.part) {
-        const double t = block_sum_f64(acc.value(), red);
         const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
         if (a.part2) {
-            const double t2 = block_sum_f64(acc2.value(), red);
+            double t, t2;
+            block_sum_acc2(acc, acc2, red, &t, &t2);
             grid_sum_finalize2(t, t2, a.part, a.part2, bid, nb, a.ticket, a.sum_out, a.sum_out2, red);
         } else {
-            grid_sum_finalize(t, a.part, bid, nb, a.ticket, a.sum_out, red);
+            grid_sum_finalize(block_sum_acc(acc, red), a.part, bid, nb, a.ticket, a.sum_out, red);
         }
     }
     if (a.count_iter) cg_count_iteration(a.cg);
@@ -930,12 +931,12 @@ __global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
         nrm_epilogue<NX, 2 * P, T, NXS>(a, row0, stg, &dacc, a.part2 ? &dacc2 : nullptr);
     }
     if (a.part) {
-        const double t = block_sum_f64(dacc.value(), red);
         if (a.part2) {
-            const double t2 = block_sum_f64(dacc2.value(), red);
+            double t, t2;
+            block_sum_acc2(dacc, dacc2, red, &t, &t2);
             grid_sum_finalize2(t, t2, a.part, a.part2, blockIdx.x, gridDim.x, a.ticket, a.sum_out, a.sum_out2, red);
         } else {
-            grid_sum_finalize(t, a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out, red);
+            grid_sum_finalize(block_sum_acc(dacc, red), a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out, red);
         }
     }
     if (a.count_iter) cg_count_iteration(a.cg);
@@ -1174,13 +1175,14 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
         }
     }
     if (a.x.part) {
-        const double t = block_sum_f64(dacc.value(), red);
         if (a.x.part2) {
-            const double t2 = block_sum_f64(dacc2.value(), red);
+            double t, t2;
+            block_sum_acc2(dacc, dacc2, red, &t, &t2);
             grid_sum_finalize2(t, t2, a.x.part, a.x.part2, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out,
                                a.x.sum_out2, red);
         } else {
-            grid_sum_finalize(t, a.x.part, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out, red);
+            grid_sum_finalize(block_sum_acc(dacc, red), a.x.part, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out,
+                              red);
         }
     }
     if (a.x.count_iter) cg_count_iteration(a.x.cg);

@@ -117,6 +117,26 @@ __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, floa
     return true;
 }
 
+// cg_enter for a whole CTA (every thread calls it; c.flags set): thread 0
+// evaluates the loop control and shares beta, alpha and the decision through
+// shared memory, so the FP64 divides run once per CTA instead of once per
+// thread (the FP64 pipe is narrow on this part).
+__device__ __forceinline__ bool cg_enter_cta(const CgCtl& c, bool first_kernel, float* beta, float* alpha,
+                                             float* sh3)
+{
+    if (threadIdx.x == 0) {
+        float b = 0.f, al = 0.f;
+        const bool go = cg_enter(c, first_kernel, &b, nullptr, &al);
+        sh3[0] = b;
+        sh3[1] = al;
+        sh3[2] = go ? 1.f : 0.f;
+    }
+    __syncthreads();
+    *beta = sh3[0];
+    *alpha = sh3[1];
+    return sh3[2] != 0.f;
+}
+
 // End of a CG iteration whose last pass is this kernel: the lead thread
 // advances the completed-iteration counter (read only by later kernels).
 // The hard bound ends the graph loop even if the first kernel of the next

@@ -74,9 +74,9 @@ __global__ void __launch_bounds__(256) k_cg_init(const float* __restrict__ rhs, 
         ar.add(rv, rv);
         ab.add(b, b);
     }
-    double t = block_sum_f64(ar.value(), red);
+    double t = block_sum_acc(ar, red);
     grid_sum_finalize(t, rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out, red);
-    t = block_sum_f64(ab.value(), red);
+    t = block_sum_acc(ab, red);
     grid_sum_finalize(t, bn_part, blockIdx.x, gridDim.x, bn_tk, bn_out, red);
 }
 
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float*
         r[i] = rv;
         acc.add(rv, rv);
     }
-    const double t = block_sum_f64(acc.value(), red);
+    const double t = block_sum_acc(acc, red);
     grid_sum_finalize(t, rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out, red);
     if (lead) {
         const int it = c.flags[1] + 1;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_diff_norm2(const float* __restrict__ a,
         const float d = a[i] - (b ? b[i] : 0.f);
         acc.add(d, d);
     }
-    const double t = block_sum_f64(acc.value(), red);
+    const double t = block_sum_acc(acc, red);
     grid_sum_finalize(t, part, blockIdx.x, gridDim.x, tk, out, red);
 }
 
