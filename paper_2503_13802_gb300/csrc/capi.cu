@@ -427,7 +427,7 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
         z.muz = P.Znorm;
         z.ny = P.ny;
         z.nz = P.nz;
-        return run_zxnrm_ct(z, t1, st);
+        return run_zxnrm_ct(z, t1, st, P.w.shared_sms);
     }
     TArgs tz = tpass_args(P, 2, t1, t2, mode == 0 ? P.Znorm : P.Zhat);
     if (cg) tz.cg = cgp;

@@ -279,110 +279,147 @@ __device__ __forceinline__ double block_sum_f64(double v, double* sh /* >= 32 do
     return t;
 }
 
-// Block-wide sums of one or two compensated FP32 accumulators (all threads
-// participate; results valid in thread 0).  The FP64 pipe is narrow on this
-// part, so the warp levels add the (hi, lo) pairs in FP32: the high words
-// by TwoSum (Knuth), whose exact rounding error joins the low words.  A
-// pair carries about 48 bits, as each thread's accumulator did.  Each warp's
-// total becomes one double, and thread 0 adds the warp totals in FP64 in
-// warp order, so the result does not depend on timing.
+// x = m 2^e for a positive normal double x: m in [1, 2) as a float (the
+// leading 24 significand bits), e the unbiased exponent.  Integer operations
+// only.  Returns false for zero, negative, subnormal, infinite or NaN x.
+__device__ __forceinline__ bool dsplit(double x, float* m, int* e)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((b >> 52) & 0x7ffu);
+    *e = ef - 1023;
+    *m = __uint_as_float(0x3f800000u | (unsigned int)((b >> 29) & 0x7fffffu));
+    return (b >> 63) == 0 && ef != 0 && ef != 0x7ff;
+}
+
+// x / y as a float for doubles x, y: the leading significand bits are
+// divided in FP32 and the exponents subtracted.  Truncating each operand to
+// 24 bits and rounding the quotient leave a relative error below 3e-7; the
+// loop applies the quotient as a float anyway.  Falls back to the FP64
+// division when either operand is not a positive normal number.
+__device__ __forceinline__ float ddiv_to_float(double x, double y)
+{
+    float mx, my;
+    int ex, ey;
+    if (dsplit(x, &mx, &ex) && dsplit(y, &my, &ey)) return ldexpf(mx / my, ex - ey);
+    return (float)(x / y);
+}
+
+__device__ __forceinline__ bool dbits_finite(double x)
+{
+    return ((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ffu) != 0x7ffu;
+}
+
+__device__ __forceinline__ bool dbits_zero(double x)
+{
+    return (((unsigned long long)__double_as_longlong(x)) << 1) == 0ull;
+}
+
+// Sums of compensated FP32 accumulators.  The FP64 pipe is narrow on this
+// part (one FP64 warp instruction holds it for many cycles, whatever its
+// active lanes), so the whole reduction tree adds (hi, lo) pairs in FP32:
+// the high words by TwoSum (Knuth), whose exact rounding error joins the
+// low words.  A pair carries about 48 bits, as each thread's accumulator
+// did, and only the final total is converted to FP64.  The trees are fixed
+// (xor butterflies, lane order), so results do not depend on timing.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float h2, float l2)
+{
+    const float s = hi + h2;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (h2 - bb);
+    hi = s;
+    lo = (lo + l2) + e;
+}
+
 __device__ __forceinline__ void warp_sum_acc(float& hi, float& lo)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
         const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        const float s = hi + h2;
-        const float bb = s - hi;
-        const float e = (hi - (s - bb)) + (h2 - bb);
-        hi = s;
-        lo = (lo + l2) + e;
+        pair_add(hi, lo, h2, l2);
     }
 }
 
-__device__ __forceinline__ double block_sum_acc(const DotAcc& a, double* sh /* >= 32 doubles */)
+// Block-wide pair sums of one or two accumulators (all threads participate;
+// results valid in thread 0).  sh: at least 4 floats per warp of the block.
+__device__ __forceinline__ void block_pair_acc2(const DotAcc& a, const DotAcc* b, float* sh, float2* ta, float2* tb)
 {
-    float hi = a.hi, lo = a.lo;
-    warp_sum_acc(hi, lo);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float ha = a.hi, la = a.lo, hb = b ? b->hi : 0.f, lb = b ? b->lo : 0.f;
+    warp_sum_acc(ha, la);
+    if (b) warp_sum_acc(hb, lb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float* shb = sh + 2 * nw;
     __syncthreads();
-    if (lane == 0) sh[wid] = (double)hi + (double)lo;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int w = 0; w < nw; ++w) t += sh[w];
+    if (lane == 0) {
+        sh[2 * wid] = ha;
+        sh[2 * wid + 1] = la;
+        shb[2 * wid] = hb;
+        shb[2 * wid + 1] = lb;
     }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const bool in = (int)threadIdx.x < nw;
+        ha = in ? sh[2 * threadIdx.x] : 0.f;
+        la = in ? sh[2 * threadIdx.x + 1] : 0.f;
+        warp_sum_acc(ha, la);
+        *ta = make_float2(ha, la);
+        if (b) {
+            hb = in ? shb[2 * threadIdx.x] : 0.f;
+            lb = in ? shb[2 * threadIdx.x + 1] : 0.f;
+            warp_sum_acc(hb, lb);
+            *tb = make_float2(hb, lb);
+        }
+    }
+}
+
+__device__ __forceinline__ float2 block_pair_acc(const DotAcc& a, double* sh /* >= 2 doubles per warp */)
+{
+    float2 t = make_float2(0.f, 0.f), u;
+    block_pair_acc2(a, nullptr, reinterpret_cast<float*>(sh), &t, &u);
     return t;
 }
 
-__device__ __forceinline__ void block_sum_acc2(const DotAcc& a, const DotAcc& b, double* sh /* >= 32 doubles */,
-                                               double* ta, double* tb)
+// The block total as a double (valid in thread 0).
+__device__ __forceinline__ double block_sum_acc(const DotAcc& a, double* sh /* >= 2 doubles per warp */)
 {
-    float ha = a.hi, la = a.lo, hb = b.hi, lb = b.lo;
-    warp_sum_acc(ha, la);
-    warp_sum_acc(hb, lb);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) {
-        sh[wid] = (double)ha + (double)la;
-        sh[16 + wid] = (double)hb + (double)lb;
-    }
-    __syncthreads();
-    double s0 = 0.0, s1 = 0.0;
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int w = 0; w < nw; ++w) {
-            s0 += sh[w];
-            s1 += sh[16 + w];
-        }
-    }
-    *ta = s0;
-    *tb = s1;
+    const float2 t = block_pair_acc(a, sh);
+    return (double)t.x + (double)t.y;
 }
 
-// Deterministic FP64 sum of n partials, identical in every block (same
-// order): result returned to all threads of the block.
-__device__ __forceinline__ double sum_partials(const double* __restrict__ part, int n, double* sh)
+// Grid-wide deterministic reduction of the blocks' pair sums.  Each block
+// stores its pair (v valid in thread 0) in the 8-byte slot part[bid]; the
+// last block to arrive (atomic ticket) adds part[0..nparts) in a fixed
+// order (warp 0: lane l takes l, l + 32, ..., then a butterfly over the
+// lanes), stores the total in *out as a double, and re-arms the ticket
+// counter for the next launch.  Consumers read the single scalar.
+__device__ __forceinline__ float2 grid_pairs_sum(const double* part, int nparts)
 {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
-    v = block_sum_f64(v, sh);
-    __syncthreads();
-    if (threadIdx.x == 0) sh[32] = v;
-    __syncthreads();
-    const double r = sh[32];
-    __syncthreads();
-    return r;
+    const float2* pp = reinterpret_cast<const float2*>(part);
+    float hi = 0.f, lo = 0.f;
+    for (int i = threadIdx.x; i < nparts; i += 32) {
+        const float2 v = __ldcg(pp + i);
+        pair_add(hi, lo, v.x, v.y);
+    }
+    warp_sum_acc(hi, lo);
+    return make_float2(hi, lo);
 }
 
-// Grid-wide deterministic FP64 reduction.  Each block stores its partial
-// (v valid in thread 0) at part[bid]; the last block to arrive (atomic
-// ticket) sums part[0..nparts) in a fixed order (warp 0: lane l takes
-// l, l + 32, ..., then a butterfly over the lanes) and stores the total in
-// *out, then re-arms the ticket counter for the next launch.  Consumers
-// read the single scalar.
-__device__ __forceinline__ void grid_sum_finalize(double v, double* part, int bid, int nparts, unsigned int* counter,
-                                                  double* out, double* sh)
+__device__ __forceinline__ void grid_sum_finalize(float2 v, double* part, int bid, int nparts, unsigned int* counter,
+                                                  double* out)
 {
     __shared__ int am_last;
     if (threadIdx.x == 0) {
-        part[bid] = v;
+        reinterpret_cast<float2*>(part)[bid] = v;
         __threadfence();
         const unsigned int t = atomicAdd(counter, 1u);
         am_last = (t == (unsigned int)nparts - 1u);
     }
     __syncthreads();
-    // warp 0 alone: a strided FP64 sum per lane, then the lanes in a fixed
-    // butterfly (no block barrier on the last block's tail)
     if (am_last && threadIdx.x < 32) {
         __threadfence();
-        double acc = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += 32) acc += __ldcg(part + i);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const float2 t = grid_pairs_sum(part, nparts);
         if (threadIdx.x == 0) {
-            *out = acc;
+            *out = (double)t.x + (double)t.y;
             *counter = 0u;
             __threadfence();
         }
@@ -390,14 +427,13 @@ __device__ __forceinline__ void grid_sum_finalize(double v, double* part, int bi
 }
 
 // Two totals with one ticket: the last block sums both partial arrays.
-__device__ __forceinline__ void grid_sum_finalize2(double v0, double v1, double* part0, double* part1, int bid,
-                                                   int nparts, unsigned int* counter, double* out0, double* out1,
-                                                   double* sh)
+__device__ __forceinline__ void grid_sum_finalize2(float2 v0, float2 v1, double* part0, double* part1, int bid,
+                                                   int nparts, unsigned int* counter, double* out0, double* out1)
 {
     __shared__ int am_last2;
     if (threadIdx.x == 0) {
-        part0[bid] = v0;
-        part1[bid] = v1;
+        reinterpret_cast<float2*>(part0)[bid] = v0;
+        reinterpret_cast<float2*>(part1)[bid] = v1;
         __threadfence();
         const unsigned int t = atomicAdd(counter, 1u);
         am_last2 = (t == (unsigned int)nparts - 1u);
@@ -405,19 +441,11 @@ __device__ __forceinline__ void grid_sum_finalize2(double v0, double v1, double*
     __syncthreads();
     if (am_last2 && threadIdx.x < 32) {
         __threadfence();
-        double a0 = 0.0, a1 = 0.0;
-        for (int i = threadIdx.x; i < nparts; i += 32) {
-            a0 += __ldcg(part0 + i);
-            a1 += __ldcg(part1 + i);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        }
+        const float2 t0 = grid_pairs_sum(part0, nparts);
+        const float2 t1 = grid_pairs_sum(part1, nparts);
         if (threadIdx.x == 0) {
-            *out0 = a0;
-            *out1 = a1;
+            *out0 = (double)t0.x + (double)t0.y;
+            *out1 = (double)t1.x + (double)t1.y;
             *counter = 0u;
             __threadfence();
         }

@@ -43,6 +43,7 @@ struct TileChoice {
 
 // Solver workspace (device), sized at plan time.
 struct SolveWork {
+    bool shared_sms = false;      // set while a batched solve captures this plan's kernels
     float* x = nullptr;           // iterate (copied to the caller's buffer at the end)
     float* r = nullptr;
     float* p = nullptr;

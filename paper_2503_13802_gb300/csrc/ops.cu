@@ -58,14 +58,11 @@ __global__ void __launch_bounds__(256) k_tpass(const TArgs a)
     fft_run<true, true, true>(a.rp, MulLd{sr, ld, mu}, TStore{&a, base, x0, &acc, a.part2 ? &acc2 : nullptr}, so,
                               sr, ld, P, tw);
     if (a.epilogue && a.part) {
-        const double t = block_sum_acc(acc, red);
         const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
-        if (a.part2) {
-            const double t2 = block_sum_acc(acc2, red);
-            grid_sum_finalize2(t, t2, a.part, a.part2, bid, nb, a.ticket, a.sum_out, a.sum_out2, red);
-        } else {
-            grid_sum_finalize(t, a.part, bid, nb, a.ticket, a.sum_out, red);
-        }
+        float2 t, t2;
+        block_pair_acc2(acc, a.part2 ? &acc2 : nullptr, reinterpret_cast<float*>(red), &t, &t2);
+        if (a.part2) grid_sum_finalize2(t, t2, a.part, a.part2, bid, nb, a.ticket, a.sum_out, a.sum_out2);
+        else grid_sum_finalize(t, a.part, bid, nb, a.ticket, a.sum_out);
     }
     if (a.count_iter) cg_count_iteration(a.cg);
 }
@@ -167,13 +164,10 @@ __global__ void __launch_bounds__(256) k_xnrm(const XArgs a)
     fft_run<true, true, false>(a.rpx, QLd{Ar, ldA, a.Q, a.mx, a.s},
                                NrmEpiSt{&a, row0, &dacc, a.part2 ? &dacc2 : nullptr}, Ao, Ar, ldA, P, twx);
     if (a.part) {
-        const double t = block_sum_acc(dacc, red);
-        if (a.part2) {
-            const double t2 = block_sum_acc(dacc2, red);
-            grid_sum_finalize2(t, t2, a.part, a.part2, blockIdx.x, gridDim.x, a.ticket, a.sum_out, a.sum_out2, red);
-        } else {
-            grid_sum_finalize(t, a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out, red);
-        }
+        float2 t, t2;
+        block_pair_acc2(dacc, a.part2 ? &dacc2 : nullptr, reinterpret_cast<float*>(red), &t, &t2);
+        if (a.part2) grid_sum_finalize2(t, t2, a.part, a.part2, blockIdx.x, gridDim.x, a.ticket, a.sum_out, a.sum_out2);
+        else grid_sum_finalize(t, a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out);
     }
     if (a.count_iter) cg_count_iteration(a.cg);
 }

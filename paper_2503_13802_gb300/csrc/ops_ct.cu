@@ -228,11 +228,18 @@ static int zx_cluster()
     return (e && e[0] == '4') ? 4 : 2;
 }
 
-template <class LZ, class LF, int S, int C>
-ZXDesc zxdesc()
+template <class LZ, class LF, int S, int C, bool EARLY>
+ZXDesc zxdesc_e()
 {
     constexpr int PZ = RInfo<LF>::n() / (2 * C), PX = RInfo<LZ>::n() / (2 * C), T = zx_threads(C);
-    return ZXDesc{k_zxnrm_ct<LZ, LF, S, C, PZ, PX, T>, ZxGeom<LZ, LF, C, PZ, PX>::smem(), T, C};
+    return ZXDesc{k_zxnrm_ct<LZ, LF, S, C, PZ, PX, T, EARLY>, ZxGeom<LZ, LF, C, PZ, PX>::smem(), T, C};
+}
+// which 0: early epilogue loads (a solve on its own); 3: epilogue loads in
+// the epilogue (kernels that run beside other volumes' kernels)
+template <class LZ, class LF, int S, int C>
+ZXDesc zxdesc(int which)
+{
+    return which == 3 ? zxdesc_e<LZ, LF, S, C, false>() : zxdesc_e<LZ, LF, S, C, true>();
 }
 template <class LZ, class LF, class LI, int S, int C>
 ZXDesc zxfdesc()
@@ -265,7 +272,8 @@ ZXDesc xzdesc()
     return xzdesc_kb<LF2, LI, LZ, S, C, 1>();
 }
 
-// which: 0 normal, 1 forward, 2 adjoint.  Schedules: the z one of the T
+// which: 0 normal, 1 forward, 2 adjoint, 3 normal without early epilogue
+// loads.  Schedules: the z one of the T
 // pass; the normal kernel's length-nx forward; the forward kernel's
 // length-nx forward and length-nx/s inverse; the adjoint kernel's
 // length-nx/s forward and length-nx inverse.
@@ -273,17 +281,17 @@ template <int C>
 ZXDesc zx_desc_c(int which, int nx, int nz)
 {
     if (nx == 128 && nz == 64) {
-        if (which == 0) return zxdesc<RList<8, 8>, RList<16, 8>, 2, C>();
+        if (which == 0 || which == 3) return zxdesc<RList<8, 8>, RList<16, 8>, 2, C>(which);
         if (which == 1) return zxfdesc<RList<8, 8>, RList<16, 8>, RList<4, 16>, 2, C>();
         return xzdesc<RList<8, 8>, RList<16, 8>, RList<8, 8>, 2, C>();
     }
     if (nx == 64 && nz == 64) {
-        if (which == 0) return zxdesc<RList<8, 8>, RList<8, 8>, 2, C>();
+        if (which == 0 || which == 3) return zxdesc<RList<8, 8>, RList<8, 8>, 2, C>(which);
         if (which == 1) return zxfdesc<RList<8, 8>, RList<8, 8>, RList<4, 8>, 2, C>();
         return xzdesc<RList<4, 8>, RList<16, 4>, RList<8, 8>, 2, C>();
     }
     if (nx == 96 && nz == 64) {
-        if (which == 0) return zxdesc<RList<8, 8>, RList<3, 4, 8>, 2, C>();
+        if (which == 0 || which == 3) return zxdesc<RList<8, 8>, RList<3, 4, 8>, 2, C>(which);
         if (which == 1) return zxfdesc<RList<8, 8>, RList<3, 4, 8>, RList<4, 4, 3>, 2, C>();
         return xzdesc<RList<3, 4, 4>, RList<8, 4, 3>, RList<8, 8>, 2, C>();
     }
@@ -312,7 +320,7 @@ cudaError_t ct_set_attributes(int optin)
         }
     static const int zx[][2] = {{128, 64}, {64, 64}, {96, 64}};
     for (const auto& p : zx)
-        for (int which = 0; which < 3; ++which)
+        for (int which = 0; which < 4; ++which)
             for (int C : {2, 4}) {
                 const ZXDesc d = zx_desc(which, p[0], p[1], 2, C);
                 cudaError_t e = opt_in(d.fn, d.smem, optin);
@@ -465,7 +473,10 @@ static cudaError_t run_zx(ZXArgs& a, const void* zvol, int which, cudaStream_t s
     d.fn<<<d.C * a.ny, d.threads, d.smem, st>>>(a);
     return cudaGetLastError();
 }
-cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st) { return run_zx(a, zin, 0, st); }
+cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st, bool shared_sms)
+{
+    return run_zx(a, zin, shared_sms ? 3 : 0, st);
+}
 cudaError_t run_zxfwd_ct(ZXArgs& a, const float* zin, cudaStream_t st) { return run_zx(a, zin, 1, st); }
 // The adjoint's cluster pass also needs the pipelined adjoint's conditions
 // (16-byte aligned portraits, even mx and M).

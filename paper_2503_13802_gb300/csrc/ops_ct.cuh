@@ -274,13 +274,10 @@ __global__ void __launch_bounds__(TT) k_tpass_ct(const __grid_constant__ TArgs a
 
     if (mode == 3 && a.part) {
         const int bid = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
-        if (a.part2) {
-            double t, t2;
-            block_sum_acc2(acc, acc2, red, &t, &t2);
-            grid_sum_finalize2(t, t2, a.part, a.part2, bid, nb, a.ticket, a.sum_out, a.sum_out2, red);
-        } else {
-            grid_sum_finalize(block_sum_acc(acc, red), a.part, bid, nb, a.ticket, a.sum_out, red);
-        }
+        float2 t, t2;
+        block_pair_acc2(acc, a.part2 ? &acc2 : nullptr, reinterpret_cast<float*>(red), &t, &t2);
+        if (a.part2) grid_sum_finalize2(t, t2, a.part, a.part2, bid, nb, a.ticket, a.sum_out, a.sum_out2);
+        else grid_sum_finalize(t, a.part, bid, nb, a.ticket, a.sum_out);
     }
     if (a.count_iter) cg_count_iteration(a.cg);
 }
@@ -931,13 +928,10 @@ __global__ void __launch_bounds__(TT) k_xnrm_ct(const XArgs a)
         nrm_epilogue<NX, 2 * P, T, NXS>(a, row0, stg, &dacc, a.part2 ? &dacc2 : nullptr);
     }
     if (a.part) {
-        if (a.part2) {
-            double t, t2;
-            block_sum_acc2(dacc, dacc2, red, &t, &t2);
-            grid_sum_finalize2(t, t2, a.part, a.part2, blockIdx.x, gridDim.x, a.ticket, a.sum_out, a.sum_out2, red);
-        } else {
-            grid_sum_finalize(block_sum_acc(dacc, red), a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out, red);
-        }
+        float2 t, t2;
+        block_pair_acc2(dacc, a.part2 ? &dacc2 : nullptr, reinterpret_cast<float*>(red), &t, &t2);
+        if (a.part2) grid_sum_finalize2(t, t2, a.part, a.part2, blockIdx.x, gridDim.x, a.ticket, a.sum_out, a.sum_out2);
+        else grid_sum_finalize(t, a.part, blockIdx.x, gridDim.x, a.ticket, a.sum_out);
     }
     if (a.count_iter) cg_count_iteration(a.cg);
     (void)MX;
@@ -1059,7 +1053,7 @@ __device__ __forceinline__ bool zx_zconv(const ZXArgs& a, const float2* __restri
     return ok;
 }
 
-template <class LZ, class LF, int S, int C, int PZ, int PX, int TT>
+template <class LZ, class LF, int S, int C, int PZ, int PX, int TT, bool EARLY = true>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const __grid_constant__ ZXArgs a)
 {
     using G = ZxGeom<LZ, LF, C, PZ, PX>;
@@ -1094,6 +1088,30 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
     if (!ok) return;
 
     // ---- phase 2: drive-axis normal pass on rows z = rank nz/C + rr
+    // The epilogue's b and p values (2 PX rows, volume row of staged row rr:
+    // (rank nz/C + rr) ny + y).  With EARLY and a two-stage drive-axis
+    // transform they are loaded into registers now, so that their latency
+    // passes during the transform (64 -> 80 registers at n_x = 128).  Longer
+    // schedules need those registers, and kernels that share the SMs with
+    // other volumes' kernels (batched solves) keep the occupancy instead:
+    // both load in the epilogue.
+    constexpr int V = NX / 4, TOTAL = 2 * PX * V, ITER = (TOTAL + T - 1) / T;
+    constexpr bool kEarly = EARLY && NSTX <= 2;
+    const float* __restrict__ bp = a.x.b;
+    const float* __restrict__ pp = a.x.pin;
+    float4 B[ITER], Pv[ITER];
+    auto load_bp = [&]() {
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            const int idx = (int)threadIdx.x + it * T;
+            if ((TOTAL % T) != 0 && idx >= TOTAL) continue;
+            const int rr = idx / V, c = idx - rr * V;
+            const long long i = ((long long)((int)rank * ROWS + rr) * a.ny + y) * NX + 4 * c;
+            B[it] = bp ? __ldg(reinterpret_cast<const float4*>(bp + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
+            Pv[it] = __ldg(reinterpret_cast<const float4*>(pp + i));
+        }
+    };
+    if constexpr (kEarly) load_bp();
     float2* b0 = un;
     float2* b1 = b0 + NX * LD;
     constexpr int pfx = result_parity<0, NSTX - 1>();
@@ -1132,36 +1150,23 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
     float* stg = reinterpret_cast<float*>((NSTX % 2 == 0) ? fo : fx);
     run_stages<LI, 1, NSTX, PX, T, 1, true, true, false>(BufLd{fx, LD}, RowStageSt{stg, NXS}, fo, fx, LD, twx);
 
-    // epilogue over the 2 PX staged rows; volume row of staged row rr:
-    // (rank nz/C + rr) ny + y
-    constexpr int V = NX / 4, TOTAL = 2 * PX * V, ITER = (TOTAL + T - 1) / T;
-    const float* __restrict__ bp = a.x.b;
-    const float* __restrict__ pp = a.x.pin;
+    // epilogue over the 2 PX staged rows
+    if constexpr (!kEarly) load_bp();
     float* __restrict__ qp = a.x.qout;
     const float lam = a.x.reg.lambda;
     DotAcc dacc, dacc2;
-    float4 W[ITER], B[ITER], Pv[ITER];
 #pragma unroll
     for (int it = 0; it < ITER; ++it) {
         const int idx = (int)threadIdx.x + it * T;
         if ((TOTAL % T) != 0 && idx >= TOTAL) continue;
         const int rr = idx / V, c = idx - rr * V;
         const long long i = ((long long)((int)rank * ROWS + rr) * a.ny + y) * NX + 4 * c;
-        W[it] = *reinterpret_cast<const float4*>(stg + rr * NXS + 4 * c);
-        B[it] = bp ? __ldg(reinterpret_cast<const float4*>(bp + i)) : make_float4(1.f, 1.f, 1.f, 1.f);
-        Pv[it] = __ldg(reinterpret_cast<const float4*>(pp + i));
-    }
-#pragma unroll
-    for (int it = 0; it < ITER; ++it) {
-        const int idx = (int)threadIdx.x + it * T;
-        if ((TOTAL % T) != 0 && idx >= TOTAL) continue;
-        const int rr = idx / V, c = idx - rr * V;
-        const long long i = ((long long)((int)rank * ROWS + rr) * a.ny + y) * NX + 4 * c;
+        const float4 w = *reinterpret_cast<const float4*>(stg + rr * NXS + 4 * c);
         float4 q;
-        q.x = fmaf(B[it].x, W[it].x, lam * Pv[it].x);
-        q.y = fmaf(B[it].y, W[it].y, lam * Pv[it].y);
-        q.z = fmaf(B[it].z, W[it].z, lam * Pv[it].z);
-        q.w = fmaf(B[it].w, W[it].w, lam * Pv[it].w);
+        q.x = fmaf(B[it].x, w.x, lam * Pv[it].x);
+        q.y = fmaf(B[it].y, w.y, lam * Pv[it].y);
+        q.z = fmaf(B[it].z, w.z, lam * Pv[it].z);
+        q.w = fmaf(B[it].w, w.w, lam * Pv[it].w);
         *reinterpret_cast<float4*>(qp + i) = q;
         dacc.add(Pv[it].x, q.x);
         dacc.add(Pv[it].y, q.y);
@@ -1175,15 +1180,13 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
         }
     }
     if (a.x.part) {
-        if (a.x.part2) {
-            double t, t2;
-            block_sum_acc2(dacc, dacc2, red, &t, &t2);
+        float2 t, t2;
+        block_pair_acc2(dacc, a.x.part2 ? &dacc2 : nullptr, reinterpret_cast<float*>(red), &t, &t2);
+        if (a.x.part2)
             grid_sum_finalize2(t, t2, a.x.part, a.x.part2, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out,
-                               a.x.sum_out2, red);
-        } else {
-            grid_sum_finalize(block_sum_acc(dacc, red), a.x.part, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out,
-                              red);
-        }
+                               a.x.sum_out2);
+        else
+            grid_sum_finalize(t, a.x.part, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out);
     }
     if (a.x.count_iter) cg_count_iteration(a.x.cg);
 }

@@ -60,15 +60,31 @@ __device__ __forceinline__ float reg_term(const RegArgs& g, const float* __restr
 
 // CG loop control at the start of an iteration's kernels.  Returns false
 // when the loop is finished (every CTA of the kernel returns).  The first
-// kernel of an iteration also evaluates the stopping rule and the CG beta.
+// kernel of an iteration also evaluates the stopping rule and the CG beta
+// (and, in the single-reduction form, alpha).  Every control word and scalar
+// is read in one round of loads (values read before the done flag is tested
+// are simply unused once the loop has ended).  The FP64 pipe is narrow on
+// this part, so FP64 arithmetic is kept to the stopping test and to alpha's
+// denominator, where cancellation needs it; the divisions run in FP32 on the
+// split significands (ddiv_to_float) and deliver the float beta and alpha
+// the vector updates use.  Every CTA computes them with the same operations,
+// so all apply the same values.
 __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, float* beta, double* sh,
                                          float* alpha = nullptr)
 {
-    if (*(volatile int*)&c.flags[0]) return false;
-    if (!first_kernel) return true;
+    if (!first_kernel) return !*(volatile int*)&c.flags[0];
+    const int done = *(volatile int*)&c.flags[0];
     const int it = *(volatile int*)&c.flags[1];
-    if (*(volatile int*)&c.flags[3]) {   // a bounded wait gave up earlier: stop the loop
-        if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
+    const int gave_up = *(volatile int*)&c.flags[3];
+    const double g_new = __ldcg(c.rr_new);
+    const double bn = __ldcg(c.bn);
+    const double ro = c.rr_old ? __ldcg(c.rr_old) : 0.0;
+    const double dl = c.cgcg ? __ldcg(c.delta) : 0.0;
+    const double ap = c.cgcg ? __ldcg(c.alpha_prev) : 0.0;
+    if (done) return false;
+    const bool lead = threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0;
+    if (gave_up) {   // a bounded wait gave up earlier: stop the loop
+        if (lead) {
             c.flags[2] = MH3D_ERR_TIMEOUT;
             __threadfence();
             c.flags[0] = 1;
@@ -76,16 +92,12 @@ __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, floa
         }
         return false;
     }
-    const double g_new = __ldcg(c.rr_new);
-    const double bn = __ldcg(c.bn);
-    const double rel2 = (bn > 0.0) ? g_new / bn : 0.0;
     int status = -1;
-    if (!isfinite(g_new) || !isfinite(bn)) status = MH3D_ERR_NONFINITE;
-    else if (g_new == 0.0 || bn == 0.0) status = MH3D_OK;
-    else if (c.tol2 > 0.0 && rel2 <= c.tol2) status = MH3D_OK;
+    if (!dbits_finite(g_new) || !dbits_finite(bn)) status = MH3D_ERR_NONFINITE;
+    else if (dbits_zero(g_new) || dbits_zero(bn)) status = MH3D_OK;
+    else if (c.tol2 > 0.0 && g_new <= c.tol2 * bn) status = MH3D_OK;   // ||r||^2 / ||A^T d||^2 <= tol^2
     else if (it >= c.max_iter) status = (c.tol2 > 0.0) ? MH3D_ERR_NOT_CONVERGED : MH3D_OK;
-    const bool lead = threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0;
-    if (lead && it < c.hist_cap) c.hist[it] = sqrt(rel2);
+    if (lead && it < c.hist_cap) c.hist[it] = (bn > 0.0) ? sqrt(g_new / bn) : 0.0;
     if (status >= 0) {
         if (lead) {
             c.flags[2] = status;
@@ -95,14 +107,19 @@ __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, floa
         }
         return false;
     }
-    double b = 0.0;
-    if (it > 0) b = g_new / __ldcg(c.rr_old);
-    *beta = (float)b;
+    // beta_i = gamma_i / gamma_{i-1}
+    *beta = (it > 0) ? ddiv_to_float(g_new, ro) : 0.f;
     if (c.cgcg) {
         // alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
-        const double dl = __ldcg(c.delta);
-        const double a = (it == 0) ? g_new / dl : g_new / (dl - b * g_new / __ldcg(c.alpha_prev));
-        if (!isfinite(a) || !(a > 0.0)) {
+        //         = gamma_i u / (delta_i u - gamma_i^2),  u = gamma_{i-1} alpha_{i-1}
+        float a;
+        if (it == 0) {
+            a = ddiv_to_float(g_new, dl);
+        } else {
+            const double u = ro * ap;
+            a = ddiv_to_float(g_new * u, fma(dl, u, -g_new * g_new));
+        }
+        if (!isfinite(a) || !(a > 0.f)) {
             if (lead) {
                 c.flags[2] = MH3D_ERR_NONFINITE;
                 __threadfence();
@@ -111,8 +128,8 @@ __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, floa
             }
             return false;
         }
-        if (lead) *c.alpha_out = a;
-        if (alpha) *alpha = (float)a;
+        if (lead) *c.alpha_out = (double)a;
+        if (alpha) *alpha = a;
     }
     return true;
 }

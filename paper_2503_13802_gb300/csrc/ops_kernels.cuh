@@ -180,7 +180,9 @@ cudaError_t run_xfwd_ct(const XArgs& a, cudaStream_t st);
 cudaError_t run_xadj_ct(const XArgs& a, cudaStream_t st);
 // Fused T_z + normal pass where instantiated (false: use the two passes).
 bool ct_zxnrm_available(int nx, int nz, int s);
-cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st);
+// shared_sms: the pass runs beside other volumes' kernels (batched solves),
+// so it keeps its occupancy rather than loading the epilogue's operands early.
+cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st, bool shared_sms = false);
 // Fused T_z + drive-axis forward where instantiated.
 bool ct_zxfwd_available(int nx, int nz, int s);
 cudaError_t run_zxfwd_ct(ZXArgs& a, const float* zin, cudaStream_t st);

@@ -74,10 +74,11 @@ __global__ void __launch_bounds__(256) k_cg_init(const float* __restrict__ rhs, 
         ar.add(rv, rv);
         ab.add(b, b);
     }
-    double t = block_sum_acc(ar, red);
-    grid_sum_finalize(t, rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out, red);
-    t = block_sum_acc(ab, red);
-    grid_sum_finalize(t, bn_part, blockIdx.x, gridDim.x, bn_tk, bn_out, red);
+    float2 t, t2;
+    block_pair_acc2(ar, &ab, reinterpret_cast<float*>(red), &t, &t2);
+    grid_sum_finalize(t, rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out);
+    __syncthreads();   // every thread has read the first ticket's flag before thread 0 reuses it
+    grid_sum_finalize(t2, bn_part, blockIdx.x, gridDim.x, bn_tk, bn_out);
 }
 
 // Warm-start fallback: if r0^T r0 >= rhs^T rhs the initial iterate is no
@@ -119,8 +120,12 @@ __global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float*
     const bool lead = threadIdx.x == 0 && blockIdx.x == 0;
     const double g = __ldcg(c.rr_new);
     const double dl = __ldcg(pq);
-    const double al = g / dl;
-    if (!isfinite(al) || !(dl > 0.0)) {
+    // every thread takes alpha; the division runs in FP32 on the split
+    // significands (the FP64 pipe is narrow on this part)
+    const float a = ddiv_to_float(g, dl);
+    const unsigned long long db = (unsigned long long)__double_as_longlong(dl);
+    const bool dl_pos = (db >> 63) == 0 && (db << 1) != 0ull && !((db << 1) > 0xffe0000000000000ull);   // dl > 0
+    if (!isfinite(a) || !dl_pos) {
         if (lead) {
             c.flags[2] = MH3D_ERR_NONFINITE;
             __threadfence();
@@ -129,7 +134,6 @@ __global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float*
         }
         return;
     }
-    const float a = (float)al;
     DotAcc acc;
     // float4 body (vector buffers are 256-byte aligned), scalar tail
     const long long N4 = N >> 2;
@@ -154,8 +158,7 @@ __global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float*
         r[i] = rv;
         acc.add(rv, rv);
     }
-    const double t = block_sum_acc(acc, red);
-    grid_sum_finalize(t, rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out, red);
+    grid_sum_finalize(block_pair_acc(acc, red), rr_part, blockIdx.x, gridDim.x, rr_tk, rr_out);
     if (lead) {
         const int it = c.flags[1] + 1;
         c.flags[1] = it;
@@ -180,8 +183,7 @@ __global__ void __launch_bounds__(256) k_diff_norm2(const float* __restrict__ a,
         const float d = a[i] - (b ? b[i] : 0.f);
         acc.add(d, d);
     }
-    const double t = block_sum_acc(acc, red);
-    grid_sum_finalize(t, part, blockIdx.x, gridDim.x, tk, out, red);
+    grid_sum_finalize(block_pair_acc(acc, red), part, blockIdx.x, gridDim.x, tk, out);
 }
 
 // APG step (Sec. 4.3): given y and g = N y - rhs,
@@ -666,6 +668,7 @@ static mh3d_status build_batch_graph(const std::vector<Plan*>& ps, const mh3d_so
         Plan& P = *ps[v];
         e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) break;
+        P.w.shared_sms = true;   // the volumes' branches share the SMs
         st = cg_prefix(P, P.w.portrait, o, cs);
         if (st == MH3D_OK) {
             cudaStreamCaptureStatus cst;
@@ -681,6 +684,7 @@ static mh3d_status build_batch_graph(const std::vector<Plan*>& ps, const mh3d_so
                                                                           cudaStreamSetCaptureDependencies);
             if (e == cudaSuccess) st = cg_suffix(P, o, cs);
         }
+        P.w.shared_sms = false;
         cudaGraph_t captured = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
         if (e == cudaSuccess) e = e2;

@@ -3,7 +3,11 @@ per volume, volumes of different sizes.
 
 * Every volume of a batch must equal, bit for bit, the same volume solved
   alone by mh3d_solve: the branches launch the same kernels with the same
-  launch shapes, and every reduction has a fixed order.
+  launch shapes, and every reduction has a fixed order.  (In a batch the
+  fused T_z + drive-axis normal pass loads its epilogue operands late, to
+  keep its occupancy beside the other volumes' kernels; alone it loads
+  them before the transform.  The arithmetic is the same; the 64x32x64
+  volume takes that pass.)
 * One volume is compared with the FP64 oracle's CG at a fixed iteration
   count (rel. L2 <= 1e-4, as for single solves).
 * At the full size classes of the 64-volume workload (64^3, 96x96x64,
@@ -28,6 +32,7 @@ SMALL = [
     params((96, 96, 64), s=2, kmin=2, kmax=9),
     params((64, 64, 32), s=2, kmin=2, kmax=9),
     params((48, 32, 32), s=2, kmin=2, kmax=5),    # drive length 48: runtime-general X kernels
+    params((64, 32, 64), s=2, kmin=2, kmax=9),    # the fused cluster normal pass (n_x = 64, n_z = 64)
 ]
 
 
