@@ -23,6 +23,9 @@ Functions and the passages they follow:
   subsection).
 * ``mhad``: the multi-harmonic anti-differentiation native image (appendix
   MHAD, Eq. mhadM); numpy's FFT is the library step.
+* ``vector_model`` (its own module): the general model of Sec. 3.2 (Eq.
+  MH3Dcont, Eq. matrixModel) with the tensor PSF's harmonic PSFs (appendix,
+  Eq. PSF, Eq. skMD); numpy's FFT is the library step of its convolutions.
 * ``padded_forward / padded_adjoint / padded_cg``: boundary image padding
   (Sec. 3.x): the model on the field of view extended by ``pad`` voxels per
   side, its portraits cropped to the field of view; the adjoint zero-pads;
