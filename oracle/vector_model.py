@@ -233,3 +233,33 @@ def general_adjoint(g: "_orc.Geometry", d, bvec=None, H=None) -> np.ndarray:
     for j in range(3):
         out += b[j] * np.real(np.fft.ifftn(V[j]))
     return out
+
+
+def general_normal_apply(g: "_orc.Geometry", p, lam: float, bvec=None, H=None) -> np.ndarray:
+    """(A^T A + lambda I) p for the vector model."""
+    H = general_psf(g) if H is None else H
+    return general_adjoint(g, general_forward(g, p, bvec, H), bvec, H) + lam * np.asarray(p, dtype=np.float64)
+
+
+def general_cg(g: "_orc.Geometry", d, lam: float, iters: int, bvec=None, H=None, rel_tol: float = 0.0):
+    """Conjugate gradients on (A^T A + lambda I) x = A^T d from x = 0 (Hestenes-
+    Stiefel, the steps in the textbook order); stops after iters iterations or
+    when ||r|| <= rel_tol ||A^T d||.  Returns (x, iterations)."""
+    H = general_psf(g) if H is None else H
+    rhs = general_adjoint(g, d, bvec, H)
+    x = np.zeros(g.shape)
+    r = rhs.copy()
+    p = r.copy()
+    rr = float(np.vdot(r, r))
+    bn = rr
+    it = 0
+    while it < iters and rr > 0.0 and not (rel_tol > 0.0 and rr <= rel_tol ** 2 * bn):
+        q = general_normal_apply(g, p, lam, bvec, H)
+        alpha = rr / float(np.vdot(p, q))
+        x += alpha * p
+        r -= alpha * q
+        rr_new = float(np.vdot(r, r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it

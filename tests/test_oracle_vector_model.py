@@ -14,6 +14,9 @@ matrixModel; appendix, Eq. PSF and Eq. skMD).
   the drive component and b = (b, 0, 0), the FFT-based forward equals the
   pinned separable oracle (C, direct sums); on a tiny grid it equals a
   brute-force sum; and the adjoint satisfies Re<A x, y> = <x, A^T y>.
+* CG on the normal equations reaches the dense FP64 solution of
+  (A^T A + lambda I) x = A^T d, the matrix built column by column from the
+  forward operator on a tiny grid.
 """
 import math
 
@@ -138,3 +141,26 @@ def test_adjoint_identity():
     lhs = float(np.real(np.vdot(y, vm.general_forward(g, x, bvec, H))))
     rhs = float(np.dot(x.ravel(), vm.general_adjoint(g, y, bvec, H).ravel()))
     assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_cg_reaches_the_dense_normal_equations_solution():
+    g = _geom(n=(6, 4, 2), s=2, r=1, kmin=2, kmax=4, theta=[0.5, -0.3, 1.2])
+    H = vm.general_psf(g)
+    rng = np.random.default_rng(21)
+    bvec = 0.2 + rng.random((3,) + tuple(g.shape))
+    d = rng.standard_normal(g.portrait_shape) + 1j * rng.standard_normal(g.portrait_shape)
+    N = int(np.prod(g.shape))
+    # A as a real matrix on (Re d, Im d), one column per unit voxel
+    cols = []
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        f = vm.general_forward(g, e.reshape(g.shape), bvec, H).ravel()
+        cols.append(np.concatenate([f.real, f.imag]))
+    A = np.stack(cols, axis=1)
+    lam = 1e-2 * float(np.linalg.norm(A, 2) ** 2)
+    dv = np.concatenate([d.ravel().real, d.ravel().imag])
+    x_dense = np.linalg.solve(A.T @ A + lam * np.eye(N), A.T @ dv)
+    x, it = vm.general_cg(g, d, lam, 500, bvec, H, rel_tol=1e-13)
+    assert it < 500
+    np.testing.assert_allclose(x.ravel(), x_dense, rtol=1e-9, atol=1e-10 * np.abs(x_dense).max())
