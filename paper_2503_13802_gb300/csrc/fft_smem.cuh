@@ -242,8 +242,9 @@ __host__ __device__ __forceinline__ int fft_result_index(int nst) { return (nst 
 // ----------------------------------------------------------------------------
 // FP64-grade dot-product accumulation with FP32 arithmetic.
 // GB300's FP64 pipe is narrow, so each thread accumulates its products as an
-// unevaluated float pair (Dekker's exact product via fma, Knuth's TwoSum),
-// and only the per-thread totals are combined in FP64.
+// unevaluated float pair (Dekker's exact product via fma, Knuth's TwoSum);
+// the block and grid trees below add such pairs in FP32 too, and only a
+// final total becomes a double.
 // ----------------------------------------------------------------------------
 struct DotAcc {
     float hi = 0.f, lo = 0.f;

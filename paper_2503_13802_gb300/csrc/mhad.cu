@@ -19,7 +19,7 @@
 //
 // Warm start: u = upsampled image / b (b the sensitivity, where b > 0),
 // x0 = alpha u with alpha = Re<A u, d> / ||A u||^2, the least-squares scale
-// on the data, reduced in FP64 on the device.
+// on the data, reduced on the device (compensated float pairs, FP64 totals).
 #include <algorithm>
 #include <cmath>
 #include <complex>
