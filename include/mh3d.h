@@ -253,6 +253,31 @@ mh3d_status mh3d_mhad_warm_start(mh3d_plan plan, const void* d_dev, double lambd
 mh3d_status mh3d_estimate_phase(mh3d_plan plan, const void* d_dev, double frac, double* theta_out, int* resolved_out,
                                 void* stream);
 
+/* The general model (Sec. 3.2, Eq. MH3Dcont and Eq. matrixModel): three
+ * receive components with PSFs that need not be separable -- the harmonic
+ * PSFs of the tensor PSF (appendix, Eq. PSF, Eq. skMD) or simulated ones:
+ *   d_k[z][y][i'] = e^{i theta_k} sum_j (h_kj * (b_j rho))[z][y][s i' + r],
+ * * the 3D circular convolution on the plan's grid, theta_k, s and r the
+ * plan's.  Not for padded plans.
+ *
+ * mh3d_general_set_psf: h_host (host, float32, K*3*N values, layout
+ *   [k][j][z][y][x], component j = 0 drive axis, 1 y, 2 z) holds (h_k)_j at
+ *   the minimal-image offsets of the grid (index i along an axis of length
+ *   n is the offset i for 2i < n, else i - n, times the voxel size).  The
+ *   plan keeps their spectra on the device: K*3*N + 4*N complex64 values,
+ *   allocated on the first call and reused.  Synchronous.
+ * mh3d_general_forward: rho (device, N floats) -> d (device, complex64
+ *   K*nz*ny*(nx/s)).  bvec (device, 3*N floats [j][z][y][x]) or NULL for
+ *   b = (1, 0, 0).  Asynchronous on `stream`; uses the plan's work area, so
+ *   calls on one plan must not overlap.
+ * mh3d_general_adjoint: the adjoint for the real inner product,
+ *   Re<A x, d> = <x, A^T d>: d (device, complex64) -> out (device, N floats).
+ * Errors: MH3D_ERR_INVALID_ARG for null pointers, a padded plan, or no PSF
+ *   set; MH3D_ERR_CUDA with mh3d_last_error() text otherwise. */
+mh3d_status mh3d_general_set_psf(mh3d_plan plan, const float* h_host);
+mh3d_status mh3d_general_forward(mh3d_plan plan, const float* rho, const float* bvec, void* d, void* stream);
+mh3d_status mh3d_general_adjoint(mh3d_plan plan, const void* d, const float* bvec, float* out, void* stream);
+
 /* Tile autotuning: times the fused normal operator (the CG loop's kernels)
  * for each transverse-pass tile width (16 and 8 columns) on the plan's
  * workspace and keeps the fastest for this plan.  The choice is remembered

@@ -644,6 +644,7 @@ mh3d_status mh3d_plan_destroy(mh3d_plan P)
     batch_forget(*P);
     solve_free(*P);
     mhad_free(*P);
+    general_free(*P);
     if (P->table_mem) cudaFree(P->table_mem);
     delete P;
     return MH3D_OK;

@@ -148,6 +148,11 @@ struct Plan {
     float2* mhad_scratch = nullptr;
     double* mhad_red = nullptr;
 
+    // general model (general.cu): PSF spectra DFT(h_kj)/N [K][3][N] and a
+    // work area of 4N complex values, allocated by mh3d_general_set_psf
+    float2* gen_H = nullptr;
+    float2* gen_work = nullptr;
+
     // CUDA graph of the CG loop, cached per (mode, reg, fixed) key
     cudaGraphExec_t graph_exec = nullptr;
     unsigned long long graph_key = ~0ull;
@@ -156,6 +161,8 @@ struct Plan {
 
 // mhad.cu
 void mhad_free(Plan& P);
+// general.cu
+void general_free(Plan& P);
 
 // Padded plans (capi.cu): field-of-view portraits <-> the extended portrait
 // mesh, and the mask of the explicit normal operator.

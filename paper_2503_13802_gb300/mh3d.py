@@ -57,7 +57,8 @@ _lib = None
 EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoint", "mh3d_normal", "mh3d_solve",
            "mh3d_solve_host", "mh3d_solve_batched", "mh3d_forward_noalloc", "mh3d_operator_norm2", "mh3d_last_error",
            "mh3d_plan_workspace_bytes", "mh3d_version", "mh3d_plan_autotune", "mh3d_plan_spectra", "mh3d_mhad",
-           "mh3d_mhad_warm_start", "mh3d_estimate_phase"]
+           "mh3d_mhad_warm_start", "mh3d_estimate_phase", "mh3d_general_set_psf", "mh3d_general_forward",
+           "mh3d_general_adjoint"]
 
 
 def library_path() -> str:
@@ -92,6 +93,9 @@ def load(build_if_missing: bool = True):
     lib.mh3d_mhad.argtypes = [P, P, c_double, c_int, P, P]
     lib.mh3d_mhad_warm_start.argtypes = [P, P, c_double, P, P, P]
     lib.mh3d_estimate_phase.argtypes = [P, P, c_double, POINTER(c_double), POINTER(c_int), P]
+    lib.mh3d_general_set_psf.argtypes = [P, P]
+    lib.mh3d_general_forward.argtypes = [P, P, P, P, P]
+    lib.mh3d_general_adjoint.argtypes = [P, P, P, P, P]
     lib.mh3d_last_error.argtypes = [P]
     lib.mh3d_last_error.restype = c_char_p
     lib.mh3d_plan_workspace_bytes.argtypes = [P]
@@ -211,6 +215,54 @@ def mh3d_adjoint(plan: Plan, d, rho, stream=None):
     p_rho = _dev_ptr(rho, torch.float32, plan.N, "rho")
     _check(plan.handle, lib.mh3d_adjoint(plan.handle, c_void_p(p_d), c_void_p(p_rho), c_void_p(_stream_ptr(stream))))
     return rho
+
+
+def mh3d_general_set_psf(plan: Plan, h):
+    """PSF samples of the general model (include/mh3d.h): h is a float32
+    array of K*3*N values, layout [k][j][z][y][x], at the grid's minimal-image
+    offsets (a numpy array or a CPU tensor)."""
+    import numpy as np
+
+    lib = load()
+    a = np.ascontiguousarray(np.asarray(h, dtype=np.float32))
+    if a.size != plan.K * 3 * plan.N:
+        raise ValueError(f"h: need {plan.K * 3 * plan.N} float32 values, got {a.size}")
+    _check(plan.handle, lib.mh3d_general_set_psf(plan.handle, c_void_p(a.ctypes.data)))
+
+
+def _bvec_ptr(plan: Plan, bvec) -> Optional[int]:
+    import torch
+
+    return None if bvec is None else _dev_ptr(bvec, torch.float32, 3 * plan.N, "bvec")
+
+
+def mh3d_general_forward(plan: Plan, rho, d, bvec=None, stream=None):
+    """d = A rho for the general model; bvec: 3*N float32 on the device, or
+    None for b = (1, 0, 0)."""
+    import torch
+
+    lib = load()
+    p_rho = _dev_ptr(rho, torch.float32, plan.N, "rho")
+    n_d = plan.K * plan.portrait_shape[1] * plan.portrait_shape[2] * plan.portrait_shape[3]
+    p_d = _dev_ptr(d, torch.complex64, n_d, "d")
+    p_b = _bvec_ptr(plan, bvec)
+    _check(plan.handle, lib.mh3d_general_forward(plan.handle, c_void_p(p_rho), c_void_p(p_b), c_void_p(p_d),
+                                                 c_void_p(_stream_ptr(stream))))
+    return d
+
+
+def mh3d_general_adjoint(plan: Plan, d, out, bvec=None, stream=None):
+    """out = A^T d for the general model."""
+    import torch
+
+    lib = load()
+    n_d = plan.K * plan.portrait_shape[1] * plan.portrait_shape[2] * plan.portrait_shape[3]
+    p_d = _dev_ptr(d, torch.complex64, n_d, "d")
+    p_o = _dev_ptr(out, torch.float32, plan.N, "out")
+    p_b = _bvec_ptr(plan, bvec)
+    _check(plan.handle, lib.mh3d_general_adjoint(plan.handle, c_void_p(p_d), c_void_p(p_b), c_void_p(p_o),
+                                                 c_void_p(_stream_ptr(stream))))
+    return out
 
 
 def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: int = 2, solver: int = 0,
