@@ -3,9 +3,9 @@ convolution model with the tensor PSF (Sec. 3.2, Eq. MH3Dcont and Eq.
 matrixModel; appendix derivation, Eq. PSF and Eq. skMD).
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: imported by
-``tests/`` only; it shares no code with the CUDA path.  Parity of the CUDA
-path for this model is future work; these functions are pinned by
-``tests/test_oracle_vector_model.py``.
+``tests/`` only; it shares no code with the CUDA path (general.cu), which
+``tests/test_gpu_general.py`` compares with it.  These functions are pinned
+by ``tests/test_oracle_vector_model.py``.
 
 Axes follow the separable oracle: arrays are [nz][ny][nx], the drive axis is
 x (the paper's z, e_3), and components are ordered (drive, y, z).  With
