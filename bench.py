@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--mhad", action="store_true",
                     help="MHAD image timing and the MHAD warm start against the zero start (own JSON line)")
     ap.add_argument("--mhad-lambda", type=float, default=1e-2)
+    ap.add_argument("--general", action="store_true",
+                    help="the general (three-component, non-separable PSF) operators' timing (own JSON line)")
     ap.add_argument("--train-n", type=int, default=2000)
     ap.add_argument("--test-n", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=3)
@@ -784,6 +786,74 @@ def bench_mhad(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_general(args):
+    """The general model's forward and adjoint (mh3d_general_*) at the
+    128x128x64, K = 8, s = 2 size with three sensitivity components.  The PSF
+    samples are random (this leg times the operators; their parity with the
+    tensor PSF is tests/test_gpu_general.py).  CUDA events around each call,
+    L2 flushed before it; the K*3 spectra (201 MB) exceed the L2 as well.
+    Algorithmic bytes: forward = rho + b (3 components) + the spectra read
+    and the portraits written; adjoint = the portraits + spectra + b read and
+    the image written."""
+    import torch
+
+    from paper_2503_13802_gb300 import Plan, mh3d_general_adjoint, mh3d_general_forward, mh3d_general_set_psf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wl = W.WORKLOADS[WORKLOAD]
+    plan = Plan(wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max)
+    K, N = plan.K, plan.N
+    M = int(np.prod(plan.portrait_shape[1:]))
+    rng = np.random.default_rng(3)
+    mh3d_general_set_psf(plan, (1e-2 * rng.standard_normal(K * 3 * N)).astype(np.float32))
+    rho = torch.randn(plan.shape, dtype=torch.float32, device=dev)
+    bvec = (0.5 + torch.rand((3,) + tuple(plan.shape), dtype=torch.float32, device=dev)).contiguous()
+    d = torch.empty(plan.portrait_shape, dtype=torch.complex64, device=dev)
+    out = torch.empty(plan.shape, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return 1e3 * e0.elapsed_time(e1)
+
+    fwd = lambda: mh3d_general_forward(plan, rho, d, bvec)   # noqa: E731
+    adj = lambda: mh3d_general_adjoint(plan, d, out, bvec)   # noqa: E731
+    for _ in range(max(3, args.warmup)):
+        fwd()
+        adj()
+    steps = max(1, args.steps)
+    us_f = float(np.median([timed(fwd) for _ in range(steps)]))
+    us_a = float(np.median([timed(adj) for _ in range(steps)]))
+    spectra = K * 3 * N * 8
+    alg_f = N * 4 + 3 * N * 4 + spectra + K * M * 8
+    alg_a = K * M * 8 + spectra + 3 * N * 4 + N * 4
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+    except (OSError, ValueError):
+        peak = 6800.0
+    line = {
+        "metric": "general-model forward + adjoint pairs/s", "value": 1e6 / (us_f + us_a), "unit": "pairs/s",
+        "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": (us_f + us_a) / 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "general_128x128x64_k8_s2", "psf": "random samples (timing only)",
+                   "sensitivity": "three components", "l2": "flushed before each call"},
+        "forward": {"us": us_f, "alg_bytes": alg_f, "achieved_gbs": alg_f / us_f / 1e3,
+                    "frac": alg_f / us_f / 1e3 / peak, "launches": 1 + 9 + 5 * K},
+        "adjoint": {"us": us_a, "alg_bytes": alg_a, "achieved_gbs": alg_a / us_a / 1e3,
+                    "frac": alg_a / us_a / 1e3 / peak, "launches": 5 * K + 9 + 1},
+        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def bench_reference(args):
     """The FP64 oracle as the reference arm, rank 0 only."""
     ws, rank, _ = dist_env()
@@ -841,6 +911,8 @@ def main():
         bench_learned(args)
     elif args.mhad:
         bench_mhad(args)
+    elif args.general:
+        bench_general(args)
     else:
         bench_mh3d(args)
 
