@@ -17,7 +17,8 @@ Functions and the passages they follow:
 * ``adjoint``: A^T for the real inner product.
 * ``reg_apply``: R = I, or T^T T + alpha P_a^T P_a (Sec. 4.3, Eq. finalR).
 * ``normal_apply``: (A^T A + lambda R) p.
-* ``operator_norm2``: ||A||_2^2 with b = 1, the scale relative weights refer to.
+* ``operator_norm2``: ||A||_2^2 with b = 1, the scale relative weights refer to,
+  by Lanczos on the oracle's own A^T A.
 * ``cg``: conjugate gradients on the normal equations.
 * ``apg``: the paper's accelerated projected gradient (Sec. 4.3, runtime
   subsection).
@@ -89,6 +90,8 @@ def _load():
     lib.orc_cg.argtypes = [i, i, i, i, i, i, P, P, P, P, P, d, i, d, i, P, d, i, P, P]
     lib.orc_apg.restype = None
     lib.orc_apg.argtypes = [i, i, i, i, i, i, P, P, P, P, P, d, i, d, i, P, d, i, P]
+    lib.orc_normal_lambda_max.restype = d
+    lib.orc_normal_lambda_max.argtypes = [i, i, i, i, i, i, P, P, P, P, P, d, i, d, i, P, d, i, P]
     lib.orc_num_threads.restype = i
     lib.orc_set_threads.argtypes = [i]
     _lib = lib
@@ -262,29 +265,47 @@ def reg_apply(g: Geometry, p, kind: int = 0, alpha: float = 0.0, shell: int = 2)
     return out
 
 
-def operator_norm2(g: Geometry, tables=None) -> float:
+def operator_norm2(g: Geometry, tables=None, rel_tol: float = 1e-13, max_iter: int = 400) -> float:
     """||A||_2^2 for b = 1: the largest eigenvalue of A^T A.
 
-    The sampled PSF is separable, so A^T A = (X part) (x) (Y^T Y) (x) (Z^T Z);
-    the transverse factors are circulant (eigenvalues |DFT|^2, numpy's FFT as
-    the library step) and the drive factor sum_k X_k^T P^T P X_k couples
-    each frequency w only with its aliases w + j n/s.  With kernels shifted by
-    the kept-row offset r (X'_k[o] = X_k[o + r], P then keeps rows 0 mod s),
-    the alias block is B_m[a][b] = (1/s) sum_k conj(x_k[m + a M]) x_k[m + b M],
-    M = n/s, whose largest eigenvalue comes from numpy's eigvalsh."""
+    Plain Lanczos (FP64, in C) on the oracle's own normal operator with
+    lambda = 0 and uniform sensitivity: nothing about the operator's
+    structure is used.  The start vector is seeded normal noise; the process
+    stops once the largest Ritz value has changed by at most ``rel_tol``
+    (relative) in three successive steps.  The result is cached per grid,
+    offsets, phases and PSF tables, since relative regularisation weights
+    call it on every solve."""
+    tables = tables or psf_tables(g)
+    key = (tuple(g.n), g.ds_factor, g.ds_offset, tuple(np.round(g.theta_array(), 15)), rel_tol, max_iter,
+           b"".join(np.ascontiguousarray(t, dtype=np.float64).tobytes() for t in tables))
+    if key not in _NORM2_CACHE:
+        _NORM2_CACHE[key] = _lambda_max(g, None, 0.0, 0, 0.0, 1, tables, rel_tol, max_iter)
+    return _NORM2_CACHE[key]
+
+
+_NORM2_CACHE: dict = {}
+
+
+def _lambda_max(g: Geometry, b, lam: float, kind: int, alpha: float, shell: int, tables, rel_tol: float,
+                max_iter: int) -> float:
     X, Y, Z = tables or psf_tables(g)
-    nx = g.n[0]
-    s, r = g.ds_factor, g.ds_offset
-    M = nx // s
-    Xs = np.roll(X, -r, axis=1)                # X'_k[o] = X_k[o + r]
-    xh = np.fft.fft(Xs, axis=1)
-    lam_x = 0.0
-    for m in range(M):
-        idx = m + M * np.arange(s)
-        v = xh[:, idx]                         # [K, s]
-        B = (np.conj(v).T @ v) / s
-        lam_x = max(lam_x, float(np.linalg.eigvalsh(B).max()))
-    return lam_x * float(np.max(np.abs(np.fft.fft(Y)) ** 2)) * float(np.max(np.abs(np.fft.fft(Z)) ** 2))
+    nx, ny, nz = g.n
+    b = None if b is None else _f64(b).reshape(g.shape)
+    v0 = np.random.default_rng(20250317).standard_normal(g.shape)
+    it = ctypes.c_int(0)
+    return float(_load().orc_normal_lambda_max(nx, ny, nz, g.ds_factor, g.ds_offset, g.K, _ptr(X), _ptr(Y), _ptr(Z),
+                                               _ptr(g.theta_array()), _ptr(b), float(lam), int(kind), float(alpha),
+                                               int(shell), _ptr(v0), float(rel_tol), int(max_iter),
+                                               ctypes.byref(it)))
+
+
+def normal_lambda_max(g: Geometry, b=None, opts: "SolveOpts" = None, tables=None, rel_tol: float = 1e-13,
+                      max_iter: int = 400) -> float:
+    """lambda_max(A^T A + lambda R) with sensitivity b, by the same Lanczos
+    process: the reciprocal is the APG step of Sec. 4.3 (tau = 1 / ||M||^2)."""
+    opts = opts or SolveOpts()
+    return _lambda_max(g, b, opts.lam_eff(g, tables), opts.reg_kind, opts.alpha, opts.shell, tables, rel_tol,
+                       max_iter)
 
 
 @dataclass

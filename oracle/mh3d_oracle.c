@@ -17,7 +17,7 @@
  *   phase              d~_k = e^{i theta_k} d_k             (Sec. 4.4)
  *   regulariser        R = ||T rho||^2 + alpha ||P_a rho||^2 (Sec. 4.3, Eq. finalR)
  *
- * Readings taken where the paper is silent (each is listed in the design doc):
+ * Readings taken where the paper is silent:
  *   - the 3D PSF is separable: along the drive axis c_k L^(k)(gamma o_x);
  *     across it phi(o) = 3 L'(gamma_t o) on each transverse axis, with
  *     gamma_t = transverse_ratio * gamma (the transverse gradient is half the
@@ -497,6 +497,103 @@ void orc_normal_apply(int nx, int ny, int nz, int s, int r, int K,
     for (size_t i = 0; i < N; ++i) out[i] += lambda * rp[i];
     free(d);
     free(rp);
+}
+
+/* ------------------------------------------------------------------------ */
+/* ||A||_2^2: the largest eigenvalue of A^T A                               */
+/* ------------------------------------------------------------------------ */
+
+/* Number of eigenvalues below mu of the symmetric tridiagonal matrix with
+ * diagonal a[0..m) and off-diagonal b[0..m-1): the count of negative pivots
+ * of the LDL^T factorisation of T - mu I (Sylvester's law of inertia). */
+static int orc_tridiag_count_below(const double* a, const double* b, int m, double mu)
+{
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+        const double off = (i > 0) ? b[i - 1] * b[i - 1] : 0.0;
+        d = (a[i] - mu) - ((i > 0) ? off / d : 0.0);
+        if (d == 0.0) d = -1e-300;       /* mu hit an eigenvalue of a leading block: count it as below */
+        if (d < 0.0) ++c;
+    }
+    return c;
+}
+
+/* Largest eigenvalue of that tridiagonal matrix, by bisection between its
+ * Gershgorin bounds. */
+static double orc_tridiag_max_eig(const double* a, const double* b, int m)
+{
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < m; ++i) {
+        const double rad = ((i > 0) ? fabs(b[i - 1]) : 0.0) + ((i < m - 1) ? fabs(b[i]) : 0.0);
+        if (a[i] - rad < lo) lo = a[i] - rad;
+        if (a[i] + rad > hi) hi = a[i] + rad;
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-16 * (fabs(lo) + fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (orc_tridiag_count_below(a, b, m, mid) == m) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* The largest eigenvalue of the symmetric positive semi-definite normal
+ * operator A^T A + lambda R (sensitivity b, NULL = 1), applied by
+ * orc_normal_apply -- nothing about the operator's structure is used.  With
+ * b = NULL and lambda = 0 it is ||A||_2^2; the paper's APG step is its
+ * reciprocal (Sec. 4.3).  The Lanczos process (three-term recurrence, FP64)
+ * starts from v0 (N values, not all zero); after each step the largest
+ * eigenvalue of the Lanczos tridiagonal matrix (a lower bound that rises
+ * towards the answer) is taken by bisection.  Stops once that value has
+ * changed by at most rel_tol relative in three successive steps, when the
+ * Krylov space is exhausted, or after max_iter steps.  *iters_out (may be
+ * NULL) receives the number of steps. */
+double orc_normal_lambda_max(int nx, int ny, int nz, int s, int r, int K,
+                             const double* X, const double* Y, const double* Z, const double* theta,
+                             const double* b, double lambda, int kind, double alpha, int shell,
+                             const double* v0, double rel_tol, int max_iter, int* iters_out)
+{
+    const size_t N = (size_t)nx * ny * nz;
+    double* q = (double*)malloc(N * sizeof(double));
+    double* qp = (double*)calloc(N, sizeof(double));
+    double* w = (double*)malloc(N * sizeof(double));
+    double* al = (double*)malloc((size_t)(max_iter + 1) * sizeof(double));
+    double* be = (double*)malloc((size_t)(max_iter + 1) * sizeof(double));
+    double nv = 0.0;
+    for (size_t i = 0; i < N; ++i) nv += v0[i] * v0[i];
+    nv = sqrt(nv);
+    for (size_t i = 0; i < N; ++i) q[i] = v0[i] / nv;
+    double theta_max = 0.0, prev = 0.0;
+    int stable = 0, m = 0;
+    for (int j = 0; j < max_iter; ++j) {
+        orc_normal_apply(nx, ny, nz, s, r, K, X, Y, Z, theta, b, lambda, kind, alpha, shell, q, w);
+        double a = 0.0;
+        for (size_t i = 0; i < N; ++i) a += q[i] * w[i];
+        const double bprev = (j > 0) ? be[j - 1] : 0.0;
+        double bn = 0.0;
+        for (size_t i = 0; i < N; ++i) {
+            w[i] -= a * q[i] + bprev * qp[i];
+            bn += w[i] * w[i];
+        }
+        bn = sqrt(bn);
+        al[j] = a;
+        be[j] = bn;
+        m = j + 1;
+        theta_max = orc_tridiag_max_eig(al, be, m);
+        if (j > 0 && fabs(theta_max - prev) <= rel_tol * fabs(theta_max)) {
+            if (++stable >= 3) break;
+        } else {
+            stable = 0;
+        }
+        prev = theta_max;
+        if (!(bn > 1e-300)) break;        /* invariant subspace: T_m holds the answer */
+        for (size_t i = 0; i < N; ++i) {
+            qp[i] = q[i];
+            q[i] = w[i] / bn;
+        }
+    }
+    if (iters_out) *iters_out = m;
+    free(q); free(qp); free(w); free(al); free(be);
+    return theta_max;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -320,6 +320,18 @@ def test_cg_matches_dense_cholesky(kind, s):
     np.testing.assert_allclose(x.ravel(), ref, rtol=0, atol=1e-9 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("kind,s", [(0, 1), (1, 2)])
+def test_normal_lambda_max_matches_dense_eigenvalues(kind, s):
+    """lambda_max(A^T A + lambda R) with a non-uniform sensitivity, by the
+    oracle's Lanczos process, equals the largest eigenvalue of the dense
+    normal matrix assembled column by column (numpy eigvalsh)."""
+    g = _geom((8, 4, 6), s=s, r=s - 1, kmin=2, kmax=4, theta=[0.2, -0.5, 1.1])
+    b = 0.4 + np.abs(W.random_volume(g.shape, 34))
+    opts = oracle.SolveOpts(lam=3e-2, reg_kind=kind, alpha=4.0, shell=1)
+    ref = float(np.linalg.eigvalsh(_dense_normal(g, b, opts)).max())
+    assert oracle.normal_lambda_max(g, b, opts) == pytest.approx(ref, rel=1e-11)
+
+
 def test_cg_matches_fourier_closed_form():
     """b uniform, s = 1, R = I: the normal matrix is diagonal in Fourier and
     rho^ = sum_k conj(h^_k) D^_k / (sum_k |h^_k|^2 + lambda), D_k =
@@ -344,8 +356,8 @@ def test_cg_matches_fourier_closed_form():
 
 @pytest.mark.parametrize("n,s,r", [((12, 6, 4), 1, 0), ((12, 6, 4), 2, 1), ((18, 4, 3), 3, 2)])
 def test_operator_norm2_matches_power_iteration(n, s, r):
-    """||A||_2^2 (b = 1) from the Fourier/alias-block formula equals the
-    limit of a power iteration with the oracle's own A^T A (lambda = 0)."""
+    """||A||_2^2 (b = 1) by the oracle's Lanczos process equals the limit of
+    a plain power iteration with the oracle's own A^T A (lambda = 0)."""
     g = _geom(n, s=s, r=r, kmin=2, kmax=5, theta=[0.1, 0.2, 0.3, 0.4])
     v = W.random_volume(g.shape, 5)
     o = oracle.SolveOpts(lam=0.0)
@@ -355,6 +367,32 @@ def test_operator_norm2_matches_power_iteration(n, s, r):
         lam = float(np.sum(v * w) / np.sum(v * v))
         v = w / np.linalg.norm(w)
     assert oracle.operator_norm2(g) == pytest.approx(lam, rel=1e-9)
+
+
+def _norm2_alias_blocks(g):
+    """The closed form of ||A||_2^2 for a separable PSF and b = 1:
+    A^T A = (drive part) (x) Y^T Y (x) Z^T Z, the transverse factors are
+    circulant (eigenvalues |DFT|^2) and the drive part couples frequency m
+    only with its aliases m + a n/s: with the kernels shifted by the kept-row
+    offset r, the block is B_m[a][b] = (1/s) sum_k conj(x_k[m + aM]) x_k[m + bM]."""
+    X, Y, Z = oracle.psf_tables(g)
+    s, r = g.ds_factor, g.ds_offset
+    M = g.n[0] // s
+    xh = np.fft.fft(np.roll(X, -r, axis=1), axis=1)
+    lam_x = 0.0
+    for m in range(M):
+        v = xh[:, m + M * np.arange(s)]
+        lam_x = max(lam_x, float(np.linalg.eigvalsh((np.conj(v).T @ v) / s).max()))
+    return lam_x * float(np.max(np.abs(np.fft.fft(Y)) ** 2)) * float(np.max(np.abs(np.fft.fft(Z)) ** 2))
+
+
+@pytest.mark.parametrize("n,s,r,k", [((16, 8, 6), 1, 0, (2, 5)), ((24, 12, 8), 2, 1, (2, 9)),
+                                     ((18, 6, 4), 3, 2, (3, 6)), ((32, 16, 8), 2, 0, (2, 9))])
+def test_operator_norm2_matches_alias_block_closed_form(n, s, r, k):
+    """The Lanczos value equals the Fourier alias-block closed form (written
+    here, not in the oracle) to near FP64 precision."""
+    g = _geom(n, s=s, r=r, kmin=k[0], kmax=k[1], theta=list(np.linspace(0.1, 0.9, k[1] - k[0] + 1)))
+    assert oracle.operator_norm2(g) == pytest.approx(_norm2_alias_blocks(g), rel=1e-11)
 
 
 def test_relative_lambda_scales_regulariser():
