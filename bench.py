@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -30,11 +31,10 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "reconstructions/sec to rel. residual 1e-4"
+PRECISION = ("FP32 operator and vectors; inner products: exact FP32 products summed in float pairs (hi + lo), "
+             "FP64 totals; CG step lengths and stopping test FP64")
 UNIT = "reconstructions/s"
 WORKLOAD = "mh_128x128x64_k8_s2"
-# Iterations the FP64 oracle's CG takes to reach rel. residual 1e-4 on this
-# workload (seed 0); `python bench.py --impl reference --count-iters` recounts.
-ORACLE_CG_ITERS = 83
 # DRAM bytes (read + write) of one CG iteration's three kernels, summed from
 # one ncu capture with cold L2 (ncu's default cache flush between kernels).
 TRAFFIC_PER_ITER_FUSED = 37895680   # 25.24 MB T_y + 12.66 MB fused T_z + X normal (mean of two iterations)
@@ -119,11 +119,10 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"mh3d_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu),
@@ -146,6 +145,15 @@ class Clocks:
             self.f.close()
 
     def summary(self):
+        try:
+            return self._summary()
+        finally:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
+
+    def _summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         rows = []
@@ -235,8 +243,9 @@ def bench_mh3d(args):
     # loop runs inside a CUDA graph, so its per-iteration duration is measured
     # live with events on this stream as the difference of two solves with a
     # fixed iteration count (it_med and 2): set-up and exit work cancel.
-    def fixed_solve_seconds(n_it, reps=5):
-        of = make_opts(lam=wl.lam, lam_relative=True, max_iter=n_it, fixed_iters=1, normal_mode=args.mode)
+    def fixed_solve_seconds(n_it, reps=5, fp32_div=False):
+        of = make_opts(lam=wl.lam, lam_relative=True, max_iter=n_it, fixed_iters=1, normal_mode=args.mode,
+                       fp32_scalar_div=fp32_div)
         mh3d_solve(plan, d, of, x)
         ts = []
         for _ in range(reps):
@@ -252,12 +261,17 @@ def bench_mh3d(args):
 
     it_lo = 2
     it_s = (fixed_solve_seconds(it_med) - fixed_solve_seconds(it_lo)) / (it_med - it_lo)
-    # Algorithmic bytes of one single-reduction CG iteration with the fused
-    # normal operator: read r, s, p, q, x and b, write r, p, q, x and the new
-    # s = (A^T A + lambda I) r: 11 float32 vectors of N.  (The two
-    # intermediate volumes between the passes and the second reads of b and r
-    # are traffic of this design, not of the algorithm: 17 vectors in all.)
-    it_alg = 11 * 4 * N if args.mode == 0 else 11 * 4 * N + 2 * 8 * M
+    # the same with CG's beta and alpha as FP32 quotients (fp32_scalar_div),
+    # for the cost of the default FP64 quotients
+    it_s_f32 = (fixed_solve_seconds(it_med, fp32_div=True) - fixed_solve_seconds(it_lo, fp32_div=True)) / (
+        it_med - it_lo)
+    # Algorithmic bytes of one CG iteration: the CG vectors x, r and p read
+    # and written once each and b read once, 7 float32 vectors of N (28 N
+    # bytes); the operator's intermediates stay on chip in this count.  The
+    # single-reduction form this library runs also streams s and q (11
+    # vectors, `design_alg_bytes`), and its passes move two intermediate
+    # volumes and second reads of b and r (17 vectors, `design_bytes_per_iter`).
+    it_alg = 7 * 4 * N if args.mode == 0 else 7 * 4 * N + 2 * 8 * M
 
     # Roofline of the forward operator A (T_y + T_z + X_fwd), L2 flushed
     # before each application so rho and b come from HBM and d goes to HBM.
@@ -351,7 +365,7 @@ def bench_mh3d(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (FP64 reductions)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32", "precision": PRECISION, "data": "synthetic",
         "config": {"workload": wl.name, "grid": list(wl.n), "harmonics": [wl.k_min, wl.k_max],
                    "ds_factor": wl.ds_factor, "sensitivity": wl.sens, "phantom": f"{wl.n_blobs} blobs + {wl.n_lines} lines",
                    "snr_db": wl.snr_db, "lambda": wl.lam, "rel_tol": wl.rel_tol,
@@ -366,7 +380,10 @@ def bench_mh3d(args):
                      "traffic": (TRAFFIC_PER_ITER_FUSED if fused_zx(wl) else TRAFFIC_PER_ITER)
                                 if args.mode == 0 else None,
                      "alg_bytes_per_launch": it_alg, "us_per_launch": it_s * 1e6,
+                     "alg_bytes_note": "per CG iteration: x, r, p read + written and b read (28 N bytes)",
+                     "design_alg_bytes": 11 * 4 * N,
                      "design_bytes_per_iter": (15 if fused_zx(wl) else 17) * 4 * N,
+                     "fp32_scalar_div_us_per_iter": it_s_f32 * 1e6,
                      "forward_A": {"us": fwd_s * 1e6, "alg_bytes": alg_bytes, "achieved_gbs": alg_bytes / fwd_s / 1e9,
                                    "frac": alg_bytes / fwd_s / 1e9 / peak},
                      "adjoint_AT": {"us": adj_s * 1e6, "alg_bytes": alg_bytes,
@@ -384,7 +401,7 @@ def bench_mh3d(args):
     if other:
         line["explicit_mode"] = other
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, it_med)
+        line["cpu_baseline"] = cpu_baseline(wl)
     if ws > 1:
         import torch.distributed as dist
 
@@ -393,10 +410,10 @@ def bench_mh3d(args):
         print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(wl: W.Workload, gpu_iters: int, sample_iters: int = 2):
-    """The FP64 oracle as it stands on the host cores: A^T d plus
-    `sample_iters` CG iterations of the same workload, scaled to one full
-    reconstruction of `gpu_iters` iterations."""
+def oracle_case(wl: W.Workload):
+    """The bench workload's first volume for the FP64 oracle: geometry,
+    tables, sensitivity and noisy portraits (seed wl.seeds[0]); the relative
+    lambda's ||A||_2^2 (the oracle's own Lanczos) is computed here, as set-up."""
     import oracle
 
     g = oracle.Geometry(n=wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max)
@@ -406,28 +423,34 @@ def cpu_baseline(wl: W.Workload, gpu_iters: int, sample_iters: int = 2):
     clean = oracle.forward(g, rho, b, tables)
     sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
     d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, wl.seeds[0])
+    lam_abs = wl.lam * oracle.operator_norm2(g)
+    opts = oracle.SolveOpts(lam=lam_abs, rel_tol=wl.rel_tol, max_iter=wl.max_iter)
+    return g, tables, b, d, opts
+
+
+def oracle_reconstruction(g, tables, b, d, opts):
+    """One whole reconstruction by the oracle (A^T d, CG to the stopping
+    rule); returns (seconds, iterations)."""
+    import oracle
+
     t0 = time.perf_counter()
-    oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=sample_iters),
-              tables=tables)
-    t = time.perf_counter() - t0
-    # cg() costs A^T d + one normal application for r0 + sample_iters iterations
-    per_app = t / (sample_iters + 1.5)
-    est = per_app * (gpu_iters + 2.5)
+    _, it, _ = oracle.cg(g, d, b, opts, tables=tables)
+    return time.perf_counter() - t0, int(it)
+
+
+def cpu_baseline(wl: W.Workload):
+    """The FP64 oracle as it stands on all host cores: one whole
+    reconstruction of the bench workload (A^T d, CG to rel. residual 1e-4),
+    timed, nothing scaled."""
+    import oracle
+
+    case = oracle_case(wl)
+    t, it = oracle_reconstruction(*case)
     cores = oracle.num_threads()
-    # the same on one host thread, one iteration (bounded sample)
-    oracle.set_threads(1)
-    try:
-        t0 = time.perf_counter()
-        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=1), tables=tables)
-        t1 = time.perf_counter() - t0
-    finally:
-        oracle.set_threads(cores)
-    est1 = t1 / 2.5 * (gpu_iters + 2.5)
-    return {"value": 1.0 / est, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"oracle CG, {sample_iters} iterations at {wl.n} K={wl.k_max - wl.k_min + 1} "
-                      f"({t:.1f} s on {cores} threads), scaled to {gpu_iters} iterations + A^T d + true residual",
-            "one_thread": {"value": 1.0 / est1, "cores": 1,
-                           "sample": f"oracle CG, 1 iteration ({t1:.1f} s), scaled the same way"}}
+    return {"value": 1.0 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one whole reconstruction at {tuple(wl.n)} K={wl.k_max - wl.k_min + 1} s={wl.ds_factor}: "
+                      f"oracle A^T d + CG to rel. residual {wl.rel_tol:g} ({it} iterations, {t:.1f} s on "
+                      f"{cores} threads), not scaled"}
 
 
 class CufftOperators:
@@ -541,7 +564,7 @@ def bench_batched(args):
     line = {
         "metric": "batched reconstructions/sec to rel. residual 1e-4", "value": value, "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 reductions)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "precision": PRECISION,
         "data": "synthetic",
         "config": {"workload": "batch64_mixed_k8_s2", "volumes": len(plans),
                    "size_classes": [list(c) for c in W.BATCH_SIZE_CLASSES],
@@ -581,7 +604,9 @@ def batched_cpu_baseline(wl, sizes, iters):
         sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
         d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, 1000 + i)
         t0 = time.perf_counter()
-        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=1), tables=tables)
+        # one iteration's cost does not depend on lambda: an absolute weight
+        # spares the Lanczos run of the relative one
+        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, rel_tol=0.0, max_iter=1), tables=tables)
         t = time.perf_counter() - t0
         it = statistics.mean(iters[j] for j in idx)
         vol_s = t / 2.5 * (it + 2.5)
@@ -855,48 +880,43 @@ def bench_general(args):
 
 
 def bench_reference(args):
-    """The FP64 oracle as the reference arm, rank 0 only."""
+    """The FP64 oracle as the reference arm, rank 0 only: every timed step is
+    one whole reconstruction of the bench workload (A^T d and CG to rel.
+    residual 1e-4, about 17 s on 16 Arm cores), timed as it runs.  A warm-up
+    step is one application of the oracle's normal operator (it brings the
+    thread pool and the tables in; a whole reconstruction would only repeat a
+    timed step)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
 
     wl = W.WORKLOADS[args.workload]
-    g = oracle.Geometry(n=wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max)
-    rho = W.phantom(wl.n, wl.voxel_mm, wl.seeds[0], wl.n_blobs, wl.n_lines, wl.log_amplitudes)
-    b = W.sensitivity(wl.n, wl.voxel_mm, kind=wl.sens)
-    tables = oracle.psf_tables(g)
-    clean = oracle.forward(g, rho, b, tables)
-    sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
-    d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, wl.seeds[0])
+    g, tables, b, d, opts = oracle_case(wl)
     if args.count_iters:
-        t0 = time.perf_counter()
-        _, n_it, _ = oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol,
-                                                         max_iter=wl.max_iter), tables=tables)
-        print(json.dumps({"oracle_cg_iters": int(n_it), "seconds": time.perf_counter() - t0,
-                          "cores": oracle.num_threads()}), flush=True)
+        t, it = oracle_reconstruction(g, tables, b, d, opts)
+        print(json.dumps({"oracle_cg_iters": it, "seconds": t, "cores": oracle.num_threads()}), flush=True)
         return
-    ref_iters = ORACLE_CG_ITERS
-    sample = 1
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=sample),
-                  tables=tables)
-    times = []
+    for _ in range(args.warmup):
+        oracle.normal_apply(g, np.ones(g.shape), b, opts, tables)
+    times, iters = [], []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.cg(g, d, b, oracle.SolveOpts(lam=wl.lam, lam_relative=True, rel_tol=0.0, max_iter=sample),
-                  tables=tables)
-        times.append(time.perf_counter() - t0)
-    per_app = statistics.mean(times) / (sample + 1.5)
-    recon_s = per_app * (ref_iters + 2.5)
-    value = 1.0 / recon_s
+        t, it = oracle_reconstruction(g, tables, b, d, opts)
+        times.append(t)
+        iters.append(it)
+    total = sum(times)
+    value = args.steps / total
+    cores = oracle.num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * recon_s, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"per step: oracle CG with {sample} iteration at {wl.n}, scaled to "
-                                       f"{ref_iters} iterations + A^T d + true residual"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "grid": list(wl.n), "harmonics": [wl.k_min, wl.k_max],
+                       "ds_factor": wl.ds_factor, "rel_tol": wl.rel_tol, "cg_iters": int(statistics.median(iters))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"every step one whole oracle reconstruction (A^T d + CG to rel. residual "
+                                       f"{wl.rel_tol:g}, {int(statistics.median(iters))} iterations) on {cores} "
+                                       f"threads, timed, not scaled; warm-up steps: one normal-operator "
+                                       f"application each"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

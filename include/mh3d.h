@@ -33,8 +33,12 @@
  *     multiple of ds_factor; anything else is MH3D_ERR_UNSUPPORTED_SIZE at
  *     plan time.
  *   - All arithmetic on the operator path is FP32 (round to nearest, no fast
- *     math); CG inner products, norms and step lengths are accumulated in
- *     FP64 on the GPU.
+ *     math).  The solver's inner products and norms multiply FP32 values
+ *     exactly and sum them in float pairs (hi + lo, compensated: about 48
+ *     significand bits, error near FP64 summation's), each total becoming an
+ *     FP64 scalar; the CG step lengths and the stopping test are FP64 on the
+ *     GPU (see mh3d_solve_opts.fp32_scalar_div), rounded to FP32 only where
+ *     they scale the FP32 vectors.
  */
 #ifndef MH3D_H
 #define MH3D_H
@@ -106,7 +110,9 @@ typedef struct {
     const float* x0_dev;         /* device, N floats initial iterate; NULL = zero start     */
     int normal_mode;             /* 0 = fused normal operator (exact A^T A, Fourier blocks) */
                                  /* 1 = explicit A then A^T through a portrait buffer       */
-    double apg_tau;              /* APG step; <= 0 = 0.95 / ||M||^2 by power iteration      */
+    double apg_tau;              /* APG step; <= 0: 0.99 / lambda_max(A^T A + lambda R) from */
+                                 /*   a power iteration on the device (Rayleigh quotients,  */
+                                 /*   FP64, until they change by < 1e-6); info.tau has it   */
     int lambda_relative;         /* nonzero: the weight of R is lambda * ||A||_2^2, the     */
                                  /* squared spectral norm of A with b = 1 (see              */
                                  /* mh3d_operator_norm2); zero: lambda is absolute          */
@@ -119,6 +125,10 @@ typedef struct {
     int x0_fallback;             /* with x0_dev: if ||A^T d - N x0|| >= ||A^T d|| (the guess */
                                  /* is no better than zero) the solve restarts from x = 0;   */
                                  /* decided on the device, reported in info.x0_rejected      */
+    int fp32_scalar_div;         /* 0 (default): CG's beta and alpha are FP64 quotients of  */
+                                 /*   the FP64 scalars; nonzero: FP32 quotients of their    */
+                                 /*   leading 24 significand bits (relative error < 3e-7,   */
+                                 /*   no FP64 divide on the device)                         */
 } mh3d_solve_opts;
 
 typedef struct {
@@ -129,6 +139,7 @@ typedef struct {
                                  /* receives ||r_k||/||A^T d|| for k = 0..iters             */
     int status;                  /* mh3d_status of the solve                                */
     int x0_rejected;             /* 1 if x0_fallback replaced x0 by the zero start          */
+    double tau;                  /* APG: the step used (given or computed); CG: 0           */
 } mh3d_solve_info;
 
 /* Create a plan: validates the geometry, builds the PSF spectra in FP64 on
@@ -175,7 +186,8 @@ mh3d_status mh3d_solve_host(mh3d_plan plan, const void* d_host, const mh3d_solve
  *   plans[v], d_dev[v] (K*M complex64 on the device), rho_dev[v] (N floats
  *   on the device) for v < nvol; each plan at most once (the branches use
  *   the plans' workspaces); opts applies to every volume and opts->x0_dev
- *   must be NULL; infos (may be NULL) receives nvol records, and their
+ *   must be NULL (per-volume warm starts: mh3d_solve_batched_warm); infos
+ *   (may be NULL) receives nvol records, and their
  *   history pointers (may be NULL) are honoured.
  *   Returns the first non-OK volume status (MH3D_ERR_NOT_CONVERGED keeps
  *   the iterates); mh3d_last_error(plans[0]) names the volume.  Plans must
@@ -183,6 +195,19 @@ mh3d_status mh3d_solve_host(mh3d_plan plan, const void* d_host, const mh3d_solve
 mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* const* d_dev,
                                const mh3d_solve_opts* opts, float* const* rho_dev,
                                mh3d_solve_info* infos, void* stream);
+
+/* mh3d_solve_batched with a warm start per volume: x0_dev[v] (device, N_v
+ * floats) is volume v's initial iterate, as opts->x0_dev is for mh3d_solve
+ * (opts->x0_fallback applies to each volume; opts->x0_dev must be NULL).
+ * The call copies each x0 into its plan's iterate before the graph runs, so
+ * the cached graph serves any x0 pointers.  Each volume's result equals its
+ * single warm-started solve bit for bit.  The learned warm start of the
+ * batching pattern (a network's output per volume) goes through this call.
+ * MH3D_ERR_INVALID_ARG for a NULL x0_dev or x0_dev[v]; otherwise as
+ * mh3d_solve_batched. */
+mh3d_status mh3d_solve_batched_warm(const mh3d_plan* plans, int nvol, const void* const* d_dev,
+                                    const mh3d_solve_opts* opts, const float* const* x0_dev,
+                                    float* const* rho_dev, mh3d_solve_info* infos, void* stream);
 
 /* Copies the plan's FP32 spectral tables (device -> device, any pointer may
  * be NULL): X [K][nx] complex = c_k DFT_nx(L^(k)(gamma o dx) at o + ds_offset)
@@ -297,10 +322,17 @@ mh3d_status mh3d_plan_autotune(mh3d_plan plan, void* stream, int* tpass_cols);
  * counterpart; this is a deployment variant of the forward operator.
  *   Limits: nx*ny*nz <= 2,097,152 voxels and tables within 512 KiB, else
  *   MH3D_ERR_UNSUPPORTED_SIZE before any work is issued; other arguments as
- *   for mh3d_plan_create / mh3d_forward (geom->sensitivity_dev is read during
- *   the call only).
+ *   for mh3d_plan_create / mh3d_forward.  rho_dev, d_dev and
+ *   geom->sensitivity_dev must stay valid until the stream's work for this
+ *   call has completed (the kernels read them asynchronously).
  *   Set-up: the first call on each device (with that device current)
- *   resolves the array's address; make it before any stream capture.
+ *   resolves the array's address.
+ *   Capture: this entry point cannot be captured in a CUDA graph -- each call
+ *   uploads its tables from a host buffer freed on return -- and a call on a
+ *   capturing stream returns MH3D_ERR_INVALID_ARG without issuing work.
+ *   Device-side timeouts (a bounded wait of the passes giving up) are not
+ *   reported by this entry point, which has no status word; planned calls
+ *   report them as MH3D_ERR_TIMEOUT.
  *   Sharing: all calls on a device share the array; calls whose GPU work
  *   overlaps (other streams, other threads) race and corrupt each other's
  *   results -- serialise them.  Nothing in the array needs to start at zero.
@@ -316,6 +348,19 @@ mh3d_status mh3d_forward_noalloc(const mh3d_geometry* geom, const float* rho_dev
  * i 2 pi m f0 / Delta_t and the coil gain), so regularisation weights are
  * most meaningful relative to it. */
 mh3d_status mh3d_operator_norm2(mh3d_plan plan, double* norm2);
+
+/* *result = sum_i a_dev[i] b_dev[i] over n >= 0 FP32 device values, computed
+ * as every inner product and norm of the solvers (Sec. 4.3; the precision
+ * pattern of the CG reductions): each product split exactly into a float
+ * pair by FMA, the pairs summed per thread by TwoSum with the rounding
+ * errors carried in a low word, the per-thread pairs added as pairs through
+ * fixed warp, block and grid trees, and the final pair converted to one FP64
+ * value.  Deterministic (no atomics on values).  Uses the plan's reduction
+ * workspace, so it must not overlap a solve on the same plan; synchronises
+ * `stream`.  n = 0 gives 0 (the pointers may then be NULL);
+ * MH3D_ERR_INVALID_ARG for null pointers with n > 0, or n < 0. */
+mh3d_status mh3d_dot(mh3d_plan plan, const float* a_dev, const float* b_dev, long long n, double* result,
+                     void* stream);
 
 /* Message for the last failing call on `plan` ("" if none; never NULL).
  * With plan == NULL: the message of the calling thread's last failed

@@ -15,8 +15,11 @@ namespace mh3d {
 
 namespace {
 
+// Kernel attributes (dynamic shared-memory limits) belong to the current
+// device, so they are set once per device, not once per process.
+constexpr int kAttrMaxDevices = 64;
 std::mutex g_attr_mu;
-bool g_attr_done = false;
+bool g_attr_done[kAttrMaxDevices] = {};
 thread_local std::string g_create_err;   // message of the last failed mh3d_plan_create
 
 bool is_235(int n)
@@ -592,16 +595,19 @@ mh3d_status mh3d_plan_create(const mh3d_geometry* g, void* stream, mh3d_plan* ou
         return MH3D_ERR_UNSUPPORTED_SIZE;
     }
     {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess && (dev < 0 || dev >= kAttrMaxDevices)) e = cudaErrorInvalidDevice;
         std::lock_guard<std::mutex> lk(g_attr_mu);
-        if (!g_attr_done) {
-            cudaError_t e = ops_set_attributes();
+        if (e == cudaSuccess && !g_attr_done[dev]) {
+            e = ops_set_attributes();
             if (e == cudaSuccess) e = solve_set_attributes();
-            if (e != cudaSuccess) {
-                g_create_err = std::string("kernel attributes: ") + cudaGetErrorString(e);
-                delete P;
-                return MH3D_ERR_CUDA;
-            }
-            g_attr_done = true;
+            if (e == cudaSuccess) g_attr_done[dev] = true;
+        }
+        if (e != cudaSuccess) {
+            g_create_err = std::string("kernel attributes: ") + cudaGetErrorString(e);
+            delete P;
+            return MH3D_ERR_CUDA;
         }
     }
     cudaStream_t st = (cudaStream_t)stream;

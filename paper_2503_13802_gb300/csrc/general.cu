@@ -17,6 +17,7 @@
 // passes and sum_j b_j Re V_j finish.  Unnormalised transforms throughout;
 // the 1/N sits in the stored spectra.
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -194,6 +195,28 @@ mh3d_status gen_fail(Plan& P, const std::string& msg, mh3d_status s)
                                                MH3D_ERR_CUDA);                                         \
     } while (0)
 
+// The pencil kernels' dynamic shared-memory limit, raised once per device
+// (the attribute belongs to the current device) to what the longest
+// supported axis needs; the status is checked where it is set.
+constexpr int kGenMaxDevices = 64;
+std::mutex g_gen_attr_mu;
+bool g_gen_attr_done[kGenMaxDevices] = {};
+
+cudaError_t gen_set_attributes()
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kGenMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_gen_attr_mu);
+    if (g_gen_attr_done[dev]) return cudaSuccess;
+    const int smem = (int)(sizeof(float2) * 2 * (size_t)kMaxLen * kGP);
+    e = cudaFuncSetAttribute(k_gen_line<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gen_line<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) g_gen_attr_done[dev] = true;
+    return e;
+}
+
 // In-place transform of every pencil of `v` (rows of width W) along `axis`.
 cudaError_t gen_line(float2* v, int axis, int W, int ny, int nz, const AxisPlan& ap, bool inv, cudaStream_t st)
 {
@@ -201,13 +224,8 @@ cudaError_t gen_line(float2* v, int axis, int W, int ny, int nz, const AxisPlan&
     const long long np = g.count();
     const size_t smem = sizeof(float2) * 2 * (size_t)ap.n * kGP;
     const int grid = (int)((np + kGP - 1) / kGP);
-    if (inv) {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k_gen_line<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_gen_line<true><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
-    } else {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k_gen_line<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_gen_line<false><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
-    }
+    if (inv) k_gen_line<true><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
+    else k_gen_line<false><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
     return cudaGetLastError();
 }
 
@@ -227,6 +245,9 @@ cudaError_t gen_fft3(const Plan& P, float2* v, int count, const AxisPlan& axp, b
 
 mh3d_status gen_check(Plan& P, const char* who)
 {
+    const cudaError_t ea = gen_set_attributes();
+    if (ea != cudaSuccess)
+        return gen_fail(P, std::string(who) + ": kernel attributes: " + cudaGetErrorString(ea), MH3D_ERR_CUDA);
     if (P.padded) return gen_fail(P, std::string(who) + ": padded plans are not supported", MH3D_ERR_INVALID_ARG);
     if (!P.gen_H) return gen_fail(P, std::string(who) + ": no PSF spectra (call mh3d_general_set_psf)",
                                   MH3D_ERR_INVALID_ARG);
@@ -258,6 +279,7 @@ mh3d_status mh3d_general_set_psf(mh3d_plan Pp, const float* h_host)
     if (!h_host) return gen_fail(P, "mh3d_general_set_psf: null pointer", MH3D_ERR_INVALID_ARG);
     if (P.padded) return gen_fail(P, "mh3d_general_set_psf: padded plans are not supported", MH3D_ERR_INVALID_ARG);
     P.err.clear();
+    GEN_CK(P, gen_set_attributes());
     const long long N = P.N, n3 = 3LL * P.K * N;
     if (!P.gen_H) GEN_CK(P, dev_malloc(&P.gen_H, sizeof(float2) * (size_t)n3));
     if (!P.gen_work) GEN_CK(P, dev_malloc(&P.gen_work, sizeof(float2) * (size_t)(4 * N)));

@@ -29,8 +29,15 @@
 // Set-up: the first call on each device, with that device current, resolves
 // the array's device address with cudaGetSymbolAddress (the host-side name of
 // a __device__ array is only a stand-in, not a device address) and sets the
-// kernels' shared-memory limits.  Make that first call before any stream
-// capture on the device.
+// kernels' shared-memory limits.
+//
+// Not for stream capture: every call uploads its tables from a host buffer
+// that is freed when the call returns, so a call on a capturing stream
+// returns MH3D_ERR_INVALID_ARG without issuing work.
+//
+// Errors on the device: the passes' bounded waits have no status word here,
+// so a wait that gives up (which needs a broken copy engine, not bad input)
+// leaves partial portraits without a report; planned calls report it.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -143,6 +150,14 @@ extern "C" mh3d_status mh3d_forward_noalloc(const mh3d_geometry* g, const float*
         return MH3D_ERR_UNSUPPORTED_SIZE;
     P.tile = t;
 
+    // Each call uploads its tables from a host buffer that is gone when the
+    // call returns, so a captured call would replay a copy from freed memory:
+    // refuse capture.
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return MH3D_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return MH3D_ERR_INVALID_ARG;
+
     void* base = nullptr;
     cudaError_t e = na_setup(&base);
     if (e != cudaSuccess) return MH3D_ERR_CUDA;
@@ -174,7 +189,6 @@ extern "C" mh3d_status mh3d_forward_noalloc(const mh3d_geometry* g, const float*
     unsigned char* tb = static_cast<unsigned char*>(base);
     float* t1 = reinterpret_cast<float*>(tb + kNaTableBytes);
     float* t2 = t1 + P.N;
-    cudaStream_t st = (cudaStream_t)stream;
     // pageable source: the call returns once the data has been staged
     e = cudaMemcpyAsync(tb, h.data(), off, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return MH3D_ERR_CUDA;

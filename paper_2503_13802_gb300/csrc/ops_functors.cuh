@@ -63,12 +63,14 @@ __device__ __forceinline__ float reg_term(const RegArgs& g, const float* __restr
 // kernel of an iteration also evaluates the stopping rule and the CG beta
 // (and, in the single-reduction form, alpha).  Every control word and scalar
 // is read in one round of loads (values read before the done flag is tested
-// are simply unused once the loop has ended).  The FP64 pipe is narrow on
-// this part, so FP64 arithmetic is kept to the stopping test and to alpha's
-// denominator, where cancellation needs it; the divisions run in FP32 on the
-// split significands (ddiv_to_float) and deliver the float beta and alpha
-// the vector updates use.  Every CTA computes them with the same operations,
-// so all apply the same values.
+// are simply unused once the loop has ended).  The stopping test and
+// alpha's cancellation-prone denominator are FP64.  With c.fp64 (the
+// default) beta and alpha are FP64 quotients, rounded to FP32 only for the
+// FP32 vector updates, and the recurrence keeps the FP64 alpha; otherwise
+// the divisions run in FP32 on the split significands (ddiv_to_float,
+// relative error below 3e-7), which keeps the narrow FP64 pipe of this part
+// free of divides.  Every CTA computes them with the same operations, so all
+// apply the same values.
 __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, float* beta, double* sh,
                                          float* alpha = nullptr)
 {
@@ -108,16 +110,20 @@ __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, floa
         return false;
     }
     // beta_i = gamma_i / gamma_{i-1}
-    *beta = (it > 0) ? ddiv_to_float(g_new, ro) : 0.f;
+    *beta = (it > 0) ? (c.fp64 ? (float)(g_new / ro) : ddiv_to_float(g_new, ro)) : 0.f;
     if (c.cgcg) {
         // alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
         //         = gamma_i u / (delta_i u - gamma_i^2),  u = gamma_{i-1} alpha_{i-1}
+        const double an = (it == 0) ? g_new : g_new * (ro * ap);
+        const double ad = (it == 0) ? dl : fma(dl, ro * ap, -g_new * g_new);
+        double a64 = 0.0;
         float a;
-        if (it == 0) {
-            a = ddiv_to_float(g_new, dl);
+        if (c.fp64) {
+            a64 = an / ad;
+            a = (float)a64;
         } else {
-            const double u = ro * ap;
-            a = ddiv_to_float(g_new * u, fma(dl, u, -g_new * g_new));
+            a = ddiv_to_float(an, ad);
+            a64 = (double)a;
         }
         if (!isfinite(a) || !(a > 0.f)) {
             if (lead) {
@@ -128,7 +134,7 @@ __device__ __forceinline__ bool cg_enter(const CgCtl& c, bool first_kernel, floa
             }
             return false;
         }
-        if (lead) *c.alpha_out = (double)a;
+        if (lead) *c.alpha_out = a64;
         if (alpha) *alpha = a;
     }
     return true;

@@ -28,6 +28,9 @@ struct CgCtl {
     const double* delta = nullptr;
     const double* alpha_prev = nullptr;
     double* alpha_out = nullptr;
+    // 1: beta and alpha are FP64 quotients (rounded to FP32 only where the
+    // FP32 vectors are updated); 0: FP32 quotients of the split significands
+    int fp64 = 1;
 };
 
 // Destination of a grid-wide FP64 reduction: per-CTA partials, the ticket

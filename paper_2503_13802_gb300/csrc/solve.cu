@@ -120,9 +120,9 @@ __global__ void __launch_bounds__(256) k_cg_update(float* __restrict__ x, float*
     const bool lead = threadIdx.x == 0 && blockIdx.x == 0;
     const double g = __ldcg(c.rr_new);
     const double dl = __ldcg(pq);
-    // every thread takes alpha; the division runs in FP32 on the split
-    // significands (the FP64 pipe is narrow on this part)
-    const float a = ddiv_to_float(g, dl);
+    // every thread takes alpha: an FP64 quotient rounded to FP32, or (c.fp64
+    // off) an FP32 division of the split significands
+    const float a = c.fp64 ? (float)(g / dl) : ddiv_to_float(g, dl);
     const unsigned long long db = (unsigned long long)__double_as_longlong(dl);
     const bool dl_pos = (db >> 63) == 0 && (db << 1) != 0ull && !((db << 1) > 0xffe0000000000000ull);   // dl > 0
     if (!isfinite(a) || !dl_pos) {
@@ -184,6 +184,31 @@ __global__ void __launch_bounds__(256) k_diff_norm2(const float* __restrict__ a,
         acc.add(d, d);
     }
     grid_sum_finalize(block_pair_acc(acc, red), part, blockIdx.x, gridDim.x, tk, out);
+}
+
+// Partials of a^T b (float-pair accumulation, as every solver dot product).
+__global__ void __launch_bounds__(256) k_dot(const float* __restrict__ a, const float* __restrict__ b, long long N,
+                                             double* part, unsigned int* tk, double* out)
+{
+    __shared__ double red[34];
+    DotAcc acc;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        acc.add(a[i], b[i]);
+    grid_sum_finalize(block_pair_acc(acc, red), part, blockIdx.x, gridDim.x, tk, out);
+}
+
+// A fixed, index-hashed start vector in [-1, 1) for the power iteration
+// (never orthogonal to a given eigenvector in practice, unlike A^T d, which
+// vanishes for zero data).
+__global__ void __launch_bounds__(256) k_fill_hash(float* __restrict__ v, long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = (unsigned long long)i + 0x9e3779b97f4a7c15ull;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        v[i] = (float)((double)(z >> 40) * (1.0 / 8388608.0) - 1.0);
+    }
 }
 
 // APG step (Sec. 4.3): given y and g = N y - rhs,
@@ -310,6 +335,7 @@ static CgCtl base_ctl(const Plan& P, const mh3d_solve_opts& o)
     c.hist_cap = P.w.hist_cap;
     c.max_iter = o.max_iter;
     c.tol2 = o.fixed_iters ? 0.0 : o.rel_tol * o.rel_tol;
+    c.fp64 = o.fp32_scalar_div ? 0 : 1;
     return c;
 }
 
@@ -377,6 +403,7 @@ static unsigned long long opts_key(const mh3d_solve_opts& o)
     mix(&o.cg_variant, sizeof o.cg_variant);
     mix(&o.lambda_relative, sizeof o.lambda_relative);
     mix(&o.x0_fallback, sizeof o.x0_fallback);
+    mix(&o.fp32_scalar_div, sizeof o.fp32_scalar_div);
     return h;
 }
 
@@ -488,7 +515,9 @@ static mh3d_status cg_prefix(Plan& P, const float2* d, const mh3d_solve_opts& o,
     MH3D_CK(P, launch_adjoint(P, d, w.rhs, w.t1, w.t2, st));
     const float* qinit = nullptr;
     if (o.x0_dev) {
-        MH3D_CK(P, cudaMemcpyAsync(w.x, o.x0_dev, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+        // a batched warm start stages x0 in w.x before the graph runs
+        if (o.x0_dev != w.x)
+            MH3D_CK(P, cudaMemcpyAsync(w.x, o.x0_dev, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
         MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.x, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr,
                                  st));
         qinit = w.q;
@@ -572,6 +601,7 @@ static mh3d_status cg_report(Plan& P, double res2, double bn2, mh3d_solve_info* 
         info->rel_res_true = bn2 > 0 ? std::sqrt(res2 / bn2) : 0.0;
         info->status = status;
         info->x0_rejected = w.flags_host[4];
+        info->tau = 0.0;
     }
     if (w.flags_host[3] == MH3D_ERR_TIMEOUT) {
         P.err = "a bounded device wait (bulk copy) timed out";
@@ -655,7 +685,8 @@ void batch_forget(const Plan& P)
     }
 }
 
-static mh3d_status build_batch_graph(const std::vector<Plan*>& ps, const mh3d_solve_opts& o, cudaGraphExec_t* out)
+static mh3d_status build_batch_graph(const std::vector<Plan*>& ps, const mh3d_solve_opts& o, bool warm,
+                                     cudaGraphExec_t* out)
 {
     Plan& P0 = *ps[0];
     cudaStream_t cs = nullptr, cb = nullptr;
@@ -669,7 +700,9 @@ static mh3d_status build_batch_graph(const std::vector<Plan*>& ps, const mh3d_so
         e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) break;
         P.w.shared_sms = true;   // the volumes' branches share the SMs
-        st = cg_prefix(P, P.w.portrait, o, cs);
+        mh3d_solve_opts ov = o;
+        ov.x0_dev = warm ? P.w.x : nullptr;   // warm starts are staged in each plan's iterate
+        st = cg_prefix(P, P.w.portrait, ov, cs);
         if (st == MH3D_OK) {
             cudaStreamCaptureStatus cst;
             const cudaGraphNode_t* deps = nullptr;
@@ -682,7 +715,7 @@ static mh3d_status build_batch_graph(const std::vector<Plan*>& ps, const mh3d_so
             }
             if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &loop, nullptr, 1,
                                                                           cudaStreamSetCaptureDependencies);
-            if (e == cudaSuccess) st = cg_suffix(P, o, cs);
+            if (e == cudaSuccess) st = cg_suffix(P, ov, cs);
         }
         P.w.shared_sms = false;
         cudaGraph_t captured = nullptr;
@@ -703,11 +736,12 @@ static mh3d_status build_batch_graph(const std::vector<Plan*>& ps, const mh3d_so
     return MH3D_OK;
 }
 
-static mh3d_status batch_graph(const std::vector<Plan*>& ps, const mh3d_solve_opts& o, cudaGraphExec_t* exec)
+static mh3d_status batch_graph(const std::vector<Plan*>& ps, const mh3d_solve_opts& o, bool warm,
+                               cudaGraphExec_t* exec)
 {
     std::vector<unsigned long long> serials;
     for (const Plan* P : ps) serials.push_back(P->serial);
-    const unsigned long long key = batch_key(ps, o);
+    const unsigned long long key = batch_key(ps, o) ^ (warm ? 0x9e3779b97f4a7c15ull : 0ull);
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (size_t i = 0; i < g_batches.size(); ++i)
         if (g_batches[i].key == key && g_batches[i].serials == serials) {
@@ -720,7 +754,7 @@ static mh3d_status batch_graph(const std::vector<Plan*>& ps, const mh3d_solve_op
     BatchGraph b;
     b.serials = serials;
     b.key = key;
-    mh3d_status s = build_batch_graph(ps, o, &b.exec);
+    mh3d_status s = build_batch_graph(ps, o, warm, &b.exec);
     if (s != MH3D_OK) return s;
     if (g_batches.size() >= kMaxBatchGraphs) {
         cudaGraphExecDestroy(g_batches.front().exec);
@@ -732,7 +766,8 @@ static mh3d_status batch_graph(const std::vector<Plan*>& ps, const mh3d_solve_op
 }
 
 static mh3d_status cg_solve_batched(const std::vector<Plan*>& ps, const float2* const* d, const mh3d_solve_opts& o,
-                                    float* const* rho, mh3d_solve_info* infos, cudaStream_t st)
+                                    const float* const* x0, float* const* rho, mh3d_solve_info* infos,
+                                    cudaStream_t st)
 {
     Plan& P0 = *ps[0];
     for (Plan* P : ps) {
@@ -743,12 +778,17 @@ static mh3d_status cg_solve_batched(const std::vector<Plan*>& ps, const float2* 
             return s;
         }
     }
-    // stage the portraits in the plans' own buffers (the graph reads those)
-    for (size_t v = 0; v < ps.size(); ++v)
+    // stage the portraits (and warm starts) in the plans' own buffers (the
+    // graph reads those)
+    for (size_t v = 0; v < ps.size(); ++v) {
         MH3D_CK(P0, cudaMemcpyAsync(ps[v]->w.portrait, d[v], sizeof(float2) * (size_t)ps[v]->K * ps[v]->M,
                                     cudaMemcpyDeviceToDevice, st));
+        if (x0)
+            MH3D_CK(P0, cudaMemcpyAsync(ps[v]->w.x, x0[v], sizeof(float) * (size_t)ps[v]->N,
+                                        cudaMemcpyDeviceToDevice, st));
+    }
     cudaGraphExec_t exec = nullptr;
-    mh3d_status s = batch_graph(ps, o, &exec);
+    mh3d_status s = batch_graph(ps, o, x0 != nullptr, &exec);
     if (s != MH3D_OK) return s;
     MH3D_CK(P0, cudaGraphLaunch(exec, st));
     MH3D_CK(P0, cudaStreamSynchronize(st));
@@ -869,32 +909,47 @@ static mh3d_status apg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o,
     MH3D_CK(P, launch_adjoint(P, d, w.rhs, w.t1, w.t2, st));
     double tau = o.apg_tau;
     if (!(tau > 0)) {
-        // ||N||_2 by power iteration from the back-projection (30 steps), tau = 0.95 / ||N||.
-        MH3D_CK(P, cudaMemcpyAsync(w.p, w.rhs, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
-        double lam = 0;
+        // tau = 1 / ||M||^2 (Sec. 4.3), ||M||^2 = lambda_max(N), N = A^T A + lambda R
+        // with the plan's sensitivity: a power iteration on the device from a
+        // fixed hashed vector, v <- N v / ||N v||, with the Rayleigh quotient
+        // theta = v^T N v (v a unit vector) in FP64 after every step.  theta
+        // rises towards lambda_max; it stops once theta has changed by less
+        // than 1e-6 (relative) twice in a row, or after 2000 steps, and takes
+        // tau = 0.99 / theta (the margin covers what theta still lacks).
         MH3D_CK(P, cudaMemsetAsync(ticket(P, 0), 0, kNTk * sizeof(unsigned int), st));
-        for (int i = 0; i < 30; ++i) {
-            k_diff_norm2<<<nU, 256, 0, st>>>(w.p, nullptr, P.N, part_slot(P, kPartRES), ticket(P, kTkRES),
-                                             scal(P, kRES));
-            MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, kRES), sizeof(double), cudaMemcpyDeviceToHost, st));
-            MH3D_CK(P, cudaStreamSynchronize(st));
-            const double nrm = std::sqrt(w.red_host[0]);
-            if (!(nrm > 0)) break;
-            k_scale<<<nU, 256, 0, st>>>(w.p, w.p, (float)(1.0 / nrm), P.N);
-            MH3D_CK(P, launch_normal(P, o.normal_mode, reg, w.p, w.q, w.t1, w.t2, w.portrait, nullptr, nullptr,
+        k_fill_hash<<<nU, 256, 0, st>>>(w.p, P.N);
+        k_diff_norm2<<<nU, 256, 0, st>>>(w.p, nullptr, P.N, part_slot(P, kPartRES), ticket(P, kTkRES),
+                                         scal(P, kRES));
+        MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, kRES), sizeof(double), cudaMemcpyDeviceToHost, st));
+        MH3D_CK(P, cudaStreamSynchronize(st));
+        double nrm = std::sqrt(w.red_host[0]);
+        double theta = 0.0, prev = -1.0;
+        int calm = 0;
+        float* v = w.p;
+        float* nv = w.q;
+        for (int i = 0; i < 2000 && nrm > 0; ++i) {
+            k_scale<<<nU, 256, 0, st>>>(v, v, (float)(1.0 / nrm), P.N);
+            MH3D_CK(P, launch_normal(P, o.normal_mode, reg, v, nv, w.t1, w.t2, w.portrait, nullptr, nullptr,
                                      nullptr, st));
-            k_diff_norm2<<<nU, 256, 0, st>>>(w.q, nullptr, P.N, part_slot(P, kPartRES), ticket(P, kTkRES),
-                                             scal(P, kRES));
-            MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, kRES), sizeof(double), cudaMemcpyDeviceToHost, st));
+            k_dot<<<nU, 256, 0, st>>>(v, nv, P.N, part_slot(P, kPartRES), ticket(P, kTkRES), scal(P, kRES));
+            k_diff_norm2<<<nU, 256, 0, st>>>(nv, nullptr, P.N, part_slot(P, kPartPQ), ticket(P, kTkPQ),
+                                             scal(P, kPQ));
+            MH3D_CK(P, cudaGetLastError());
+            MH3D_CK(P, cudaMemcpyAsync(w.red_host, scal(P, 0), kNScal * sizeof(double), cudaMemcpyDeviceToHost, st));
             MH3D_CK(P, cudaStreamSynchronize(st));
-            lam = std::sqrt(w.red_host[0]);
-            MH3D_CK(P, cudaMemcpyAsync(w.p, w.q, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
+            theta = w.red_host[kRES];
+            nrm = std::sqrt(w.red_host[kPQ]);
+            std::swap(v, nv);
+            if (!std::isfinite(theta) || !std::isfinite(nrm)) break;
+            calm = (std::fabs(theta - prev) < 1e-6 * std::fabs(theta)) ? calm + 1 : 0;
+            prev = theta;
+            if (calm >= 2) break;
         }
-        if (!(lam > 0)) {
-            P.err = "power iteration failed";
+        if (!(theta > 0) || !std::isfinite(theta)) {
+            P.err = "APG step: the power iteration for ||M||^2 failed (non-finite or zero)";
             return MH3D_ERR_NONFINITE;
         }
-        tau = 0.95 / lam;
+        tau = 0.99 / theta;
     }
     // x = x0 or 0, x_prev = x, y = x
     if (o.x0_dev) MH3D_CK(P, cudaMemcpyAsync(w.x, o.x0_dev, sizeof(float) * P.N, cudaMemcpyDeviceToDevice, st));
@@ -920,6 +975,8 @@ static mh3d_status apg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o,
         info->rel_res_recurrence = 0.0;
         info->rel_res_true = bn2 > 0 ? std::sqrt(res2 / bn2) : 0.0;   // unconstrained gradient norm
         info->status = MH3D_OK;
+        info->x0_rejected = 0;
+        info->tau = tau;
     }
     return MH3D_OK;
 }
@@ -957,6 +1014,28 @@ mh3d_status mh3d_solve(mh3d_plan P, const void* d, const mh3d_solve_opts* o, flo
     }
     if (o->solver == 1) return apg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
     return cg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
+}
+
+mh3d_status mh3d_dot(mh3d_plan P, const float* a, const float* b, long long n, double* result, void* stream)
+{
+    if (!P) return MH3D_ERR_INVALID_ARG;
+    if (!result || n < 0 || (n > 0 && (!a || !b))) {
+        P->err = "mh3d_dot: null pointer or negative length";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    if (n == 0) {
+        *result = 0.0;
+        return MH3D_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = (int)std::min<long long>(update_blocks(std::max(n, 1LL)), (long long)P->w.red_cap);
+    MH3D_CK(*P, cudaMemsetAsync(ticket(*P, kTkRES), 0, sizeof(unsigned int), st));
+    k_dot<<<nb, 256, 0, st>>>(a, b, n, part_slot(*P, kPartRES), ticket(*P, kTkRES), scal(*P, kRES));
+    MH3D_CK(*P, cudaGetLastError());
+    MH3D_CK(*P, cudaMemcpyAsync(P->w.red_host, scal(*P, kRES), sizeof(double), cudaMemcpyDeviceToHost, st));
+    MH3D_CK(*P, cudaStreamSynchronize(st));
+    *result = P->w.red_host[0];
+    return MH3D_OK;
 }
 
 mh3d_status mh3d_plan_autotune(mh3d_plan P, void* stream, int* tpass_cols)
@@ -1007,8 +1086,9 @@ mh3d_status mh3d_solve_host(mh3d_plan P, const void* d_host, const mh3d_solve_op
     return s;
 }
 
-mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* const* d, const mh3d_solve_opts* o,
-                               float* const* rho, mh3d_solve_info* infos, void* stream)
+static mh3d_status solve_batched_impl(const mh3d_plan* plans, int nvol, const void* const* d,
+                                      const mh3d_solve_opts* o, const float* const* x0, float* const* rho,
+                                      mh3d_solve_info* infos, void* stream)
 {
     if (nvol == 0) return MH3D_OK;   // nothing to do; the arrays may be NULL
     if (!plans || nvol < 0 || !d || !o || !rho) return MH3D_ERR_INVALID_ARG;
@@ -1037,22 +1117,45 @@ mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* con
         }
     }
     if (o->x0_dev) {
-        P0.err = "mh3d_solve_batched: x0_dev must be NULL (one warm start cannot serve several volumes)";
+        P0.err = "mh3d_solve_batched: opts->x0_dev must be NULL (per-volume warm starts go through "
+                 "mh3d_solve_batched_warm)";
         return MH3D_ERR_INVALID_ARG;
     }
+    if (x0)
+        for (int v = 0; v < nvol; ++v)
+            if (!x0[v]) {
+                P0.err = "mh3d_solve_batched_warm: null x0 for volume " + std::to_string(v);
+                return MH3D_ERR_INVALID_ARG;
+            }
     cudaStream_t st = (cudaStream_t)stream;
     if (o->solver == 0 && !graphs_disabled()) {
         std::vector<const float2*> dv(nvol);
         for (int v = 0; v < nvol; ++v) dv[v] = (const float2*)d[v];
-        return cg_solve_batched(ps, dv.data(), *o, rho, infos, st);
+        return cg_solve_batched(ps, dv.data(), *o, x0, rho, infos, st);
     }
     // APG, or graphs switched off: one volume after another
     mh3d_status worst = MH3D_OK;
     for (int v = 0; v < nvol; ++v) {
-        mh3d_status s = mh3d_solve(plans[v], d[v], o, rho[v], infos ? &infos[v] : nullptr, stream);
+        mh3d_solve_opts ov = *o;
+        ov.x0_dev = x0 ? x0[v] : nullptr;
+        mh3d_status s = mh3d_solve(plans[v], d[v], &ov, rho[v], infos ? &infos[v] : nullptr, stream);
         if (s != MH3D_OK && worst == MH3D_OK) worst = s;
     }
     return worst;
+}
+
+mh3d_status mh3d_solve_batched(const mh3d_plan* plans, int nvol, const void* const* d, const mh3d_solve_opts* o,
+                               float* const* rho, mh3d_solve_info* infos, void* stream)
+{
+    return solve_batched_impl(plans, nvol, d, o, nullptr, rho, infos, stream);
+}
+
+mh3d_status mh3d_solve_batched_warm(const mh3d_plan* plans, int nvol, const void* const* d,
+                                    const mh3d_solve_opts* o, const float* const* x0_dev, float* const* rho,
+                                    mh3d_solve_info* infos, void* stream)
+{
+    if (nvol > 0 && !x0_dev) return MH3D_ERR_INVALID_ARG;
+    return solve_batched_impl(plans, nvol, d, o, x0_dev, rho, infos, stream);
 }
 
 }  // extern "C"

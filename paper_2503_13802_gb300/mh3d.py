@@ -38,12 +38,13 @@ class mh3d_solve_opts(ctypes.Structure):
     _fields_ = [("reg_kind", c_int), ("lambda_", c_double), ("alpha", c_double), ("shell", c_int),
                 ("solver", c_int), ("rel_tol", c_double), ("max_iter", c_int), ("fixed_iters", c_int),
                 ("x0_dev", c_void_p), ("normal_mode", c_int), ("apg_tau", c_double),
-                ("lambda_relative", c_int), ("cg_variant", c_int), ("x0_fallback", c_int)]
+                ("lambda_relative", c_int), ("cg_variant", c_int), ("x0_fallback", c_int),
+                ("fp32_scalar_div", c_int)]
 
 
 class mh3d_solve_info(ctypes.Structure):
     _fields_ = [("iters", c_int), ("rel_res_recurrence", c_double), ("rel_res_true", c_double),
-                ("history", POINTER(c_double)), ("status", c_int), ("x0_rejected", c_int)]
+                ("history", POINTER(c_double)), ("status", c_int), ("x0_rejected", c_int), ("tau", c_double)]
 
 
 class MH3DError(RuntimeError):
@@ -58,7 +59,7 @@ EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoin
            "mh3d_solve_host", "mh3d_solve_batched", "mh3d_forward_noalloc", "mh3d_operator_norm2", "mh3d_last_error",
            "mh3d_plan_workspace_bytes", "mh3d_version", "mh3d_plan_autotune", "mh3d_plan_spectra", "mh3d_mhad",
            "mh3d_mhad_warm_start", "mh3d_estimate_phase", "mh3d_general_set_psf", "mh3d_general_forward",
-           "mh3d_general_adjoint"]
+           "mh3d_general_adjoint", "mh3d_dot", "mh3d_solve_batched_warm"]
 
 
 def library_path() -> str:
@@ -96,6 +97,9 @@ def load(build_if_missing: bool = True):
     lib.mh3d_general_set_psf.argtypes = [P, P]
     lib.mh3d_general_forward.argtypes = [P, P, P, P, P]
     lib.mh3d_general_adjoint.argtypes = [P, P, P, P, P]
+    lib.mh3d_dot.argtypes = [P, P, P, ctypes.c_longlong, POINTER(c_double), P]
+    lib.mh3d_solve_batched_warm.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(mh3d_solve_opts),
+                                            POINTER(c_void_p), POINTER(c_void_p), POINTER(mh3d_solve_info), P]
     lib.mh3d_last_error.argtypes = [P]
     lib.mh3d_last_error.restype = c_char_p
     lib.mh3d_plan_workspace_bytes.argtypes = [P]
@@ -268,8 +272,9 @@ def mh3d_general_adjoint(plan: Plan, d, out, bvec=None, stream=None):
 def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: int = 2, solver: int = 0,
               rel_tol: float = 1e-4, max_iter: int = 1000, fixed_iters: bool = False, x0=None,
               normal_mode: int = 0, apg_tau: float = 0.0, lam_relative: bool = False,
-              cg_variant: int = 0, x0_fallback: bool = False) -> mh3d_solve_opts:
-    """lam_relative: lam multiplies ||A||_2^2 (b = 1), see mh3d_operator_norm2."""
+              cg_variant: int = 0, x0_fallback: bool = False, fp32_scalar_div: bool = False) -> mh3d_solve_opts:
+    """lam_relative: lam multiplies ||A||_2^2 (b = 1), see mh3d_operator_norm2.
+    fp32_scalar_div: CG's beta and alpha as FP32 quotients instead of FP64."""
     o = mh3d_solve_opts()
     o.reg_kind, o.lambda_, o.alpha, o.shell, o.solver = reg_kind, lam, alpha, shell, solver
     o.rel_tol, o.max_iter, o.fixed_iters = rel_tol, max_iter, int(bool(fixed_iters))
@@ -278,6 +283,7 @@ def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: i
     o.lambda_relative = int(bool(lam_relative))
     o.cg_variant = int(cg_variant)
     o.x0_fallback = int(bool(x0_fallback))
+    o.fp32_scalar_div = int(bool(fp32_scalar_div))
     o._x0_ref = x0
     return o
 
@@ -316,8 +322,23 @@ def mh3d_solve(plan: Plan, d, opts: mh3d_solve_opts, rho, stream=None, allow_not
     if st != MH3D_OK and not (allow_not_converged and st == MH3D_ERR_NOT_CONVERGED):
         _check(plan.handle, st)
     return {"iters": info.iters, "rel_res_recurrence": info.rel_res_recurrence, "rel_res_true": info.rel_res_true,
-            "status": info.status, "x0_rejected": info.x0_rejected,
+            "status": info.status, "x0_rejected": info.x0_rejected, "tau": info.tau,
             "history": [hist[i] for i in range(min(info.iters, opts.max_iter) + 1)]}
+
+
+def mh3d_dot(plan: Plan, a, b, stream=None) -> float:
+    """sum a_i b_i of two float32 CUDA tensors of equal length, as the
+    solvers' inner products are computed (float pairs, one FP64 total)."""
+    import torch
+
+    lib = load()
+    n = a.numel()
+    pa = _dev_ptr(a, torch.float32, n, "a")
+    pb = _dev_ptr(b, torch.float32, n, "b")
+    out = c_double(0.0)
+    _check(plan.handle, lib.mh3d_dot(plan.handle, c_void_p(pa), c_void_p(pb), n, ctypes.byref(out),
+                                     c_void_p(_stream_ptr(stream))))
+    return out.value
 
 
 def mh3d_solve_host(plan: Plan, d_host, opts: mh3d_solve_opts, rho_host, stream=None):
@@ -336,9 +357,10 @@ def mh3d_solve_host(plan: Plan, d_host, opts: mh3d_solve_opts, rho_host, stream=
     return {"iters": info.iters, "rel_res_true": info.rel_res_true, "status": info.status}
 
 
-def mh3d_solve_batched(plans: Sequence[Plan], ds, opts: mh3d_solve_opts, rhos, stream=None):
+def mh3d_solve_batched(plans: Sequence[Plan], ds, opts: mh3d_solve_opts, rhos, stream=None, x0s=None):
     """Solves every volume (its own plan, portraits ds[i], image rhos[i]) in
     one call: for CG, one CUDA graph with an independent branch per volume.
+    x0s (optional): one warm start per volume (mh3d_solve_batched_warm).
     Returns one info dict per volume."""
     import torch
 
@@ -347,16 +369,24 @@ def mh3d_solve_batched(plans: Sequence[Plan], ds, opts: mh3d_solve_opts, rhos, s
     hp = (c_void_p * n)(*[p.handle.value for p in plans])
     dp = (c_void_p * n)()
     rp = (c_void_p * n)()
+    xp = (c_void_p * n)()
     for i, (p, d, r) in enumerate(zip(plans, ds, rhos)):
         n_d = p.K * p.portrait_shape[1] * p.portrait_shape[2] * p.portrait_shape[3]
         dp[i] = _dev_ptr(d, torch.complex64, n_d, f"d[{i}]")
         rp[i] = _dev_ptr(r, torch.float32, p.N, f"rho[{i}]")
+        if x0s is not None:
+            xp[i] = _dev_ptr(x0s[i], torch.float32, p.N, f"x0[{i}]")
     infos = (mh3d_solve_info * n)()
-    st = lib.mh3d_solve_batched(hp, n, dp, ctypes.byref(opts), rp, infos, c_void_p(_stream_ptr(stream)))
+    if x0s is None:
+        st = lib.mh3d_solve_batched(hp, n, dp, ctypes.byref(opts), rp, infos, c_void_p(_stream_ptr(stream)))
+    else:
+        st = lib.mh3d_solve_batched_warm(hp, n, dp, ctypes.byref(opts), xp, rp, infos,
+                                         c_void_p(_stream_ptr(stream)))
     if st not in (MH3D_OK, MH3D_ERR_NOT_CONVERGED):
         _check(plans[0].handle if n else None, st)
     return [{"iters": infos[i].iters, "rel_res_recurrence": infos[i].rel_res_recurrence,
-             "rel_res_true": infos[i].rel_res_true, "status": infos[i].status} for i in range(n)]
+             "rel_res_true": infos[i].rel_res_true, "status": infos[i].status,
+             "x0_rejected": infos[i].x0_rejected} for i in range(n)]
 
 
 def mh3d_forward_noalloc(n, rho, d, voxel_mm=(1.0, 1.0, 1.0), ds_factor: int = 1, ds_offset: int = 0,
@@ -369,9 +399,11 @@ def mh3d_forward_noalloc(n, rho, d, voxel_mm=(1.0, 1.0, 1.0), ds_factor: int = 1
     real-time memory plan): the library keeps the tables and intermediate
     volumes in one fixed device array (grids up to 2,097,152 voxels).  Calls
     share that array, so calls that overlap on the GPU race; issue them on
-    one stream.  The first call on a device resolves the array's address and
-    should come before any stream capture.  `sensitivity` must already be a
-    float32 CUDA tensor (this call does not copy it to the device).
+    one stream.  The first call on a device resolves the array's address.  A
+    call on a capturing stream is refused (MH3D_ERR_INVALID_ARG): each call
+    uploads its tables from a host buffer freed on return.  `sensitivity`
+    must already be a float32 CUDA tensor (this call does not copy it to the
+    device).
     """
     import torch
 

@@ -66,8 +66,10 @@ def test_struct_layouts_match_c(tmp_path):
         "mh3d_geometry": ["n", "voxel_mm", "drive_axis", "ds_factor", "ds_offset", "pad", "k_min", "k_max",
                           "gamma_per_mm", "gammaA", "transverse_ratio", "theta", "sensitivity_dev"],
         "mh3d_solve_opts": ["reg_kind", "lambda", "alpha", "shell", "solver", "rel_tol", "max_iter", "fixed_iters",
-                            "x0_dev", "normal_mode", "apg_tau", "lambda_relative", "cg_variant", "x0_fallback"],
-        "mh3d_solve_info": ["iters", "rel_res_recurrence", "rel_res_true", "history", "status", "x0_rejected"],
+                            "x0_dev", "normal_mode", "apg_tau", "lambda_relative", "cg_variant", "x0_fallback",
+                            "fp32_scalar_div"],
+        "mh3d_solve_info": ["iters", "rel_res_recurrence", "rel_res_true", "history", "status", "x0_rejected",
+                            "tau"],
         "mh3d_unet_conv_desc": ["nx", "ny", "nz", "cin", "cout", "src_bf16", "skip_bf16", "src_f32", "up"],
     }
     src = ['#include <stdio.h>', '#include <stddef.h>'] + [f'#include "{h}"' for h in HEADERS] + ["int main(void){"]

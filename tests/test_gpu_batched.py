@@ -141,30 +141,64 @@ def test_batched_rejects_warm_start_and_repeated_plans():
     assert "INVALID_ARG" in str(e.value)
 
 
-def test_batched_full_size_classes_residual_property():
-    """Two volumes of each size class of the 64-volume workload, data made
-    by the GPU forward operator (the oracle cannot run these sizes whole):
-    every volume reaches rel. residual 1e-4 by its true residual, and one
-    of each class equals its single solve bit for bit."""
-    from paper_2503_13802_gb300 import Plan, mh3d_forward
+def test_batched_warm_starts_equal_single_warm_solves():
+    """mh3d_solve_batched_warm: a warm start per volume (here 0.8 times a
+    zero-start solution, and one deliberately bad guess that the fallback
+    rejects) gives, for every volume, the single warm-started solve bit for
+    bit, with fewer iterations than the zero start where the guess is good."""
+    from paper_2503_13802_gb300 import mh3d_solve, mh3d_solve_batched
 
+    plans, ds, _ = _small_batch(900)
+    opts = _opts(x0_fallback=True)
+    zero = _solve_each(plans, ds, opts)
+    x0s = [_dev(0.8 * xz, torch.float32) for xz, _ in zero]
+    x0s[1] = _dev(1e3 * W.random_volume(plans[1].shape, 5), torch.float32)   # rejected by the fallback
+    xs = [torch.empty(pl.shape, dtype=torch.float32, device="cuda") for pl in plans]
+    infos = mh3d_solve_batched(plans, ds, opts, xs, x0s=x0s)
+    for v, (pl, d, x0) in enumerate(zip(plans, ds, x0s)):
+        from paper_2503_13802_gb300 import make_opts
+
+        xa = torch.empty(pl.shape, dtype=torch.float32, device="cuda")
+        ia = mh3d_solve(pl, d, make_opts(lam=1e-3, lam_relative=True, rel_tol=1e-4, max_iter=400, x0=x0,
+                                         x0_fallback=True), xa)
+        assert infos[v]["iters"] == ia["iters"] and infos[v]["x0_rejected"] == ia["x0_rejected"], (v, infos[v], ia)
+        assert torch.equal(xs[v], xa), v
+        if v == 1:
+            assert infos[v]["x0_rejected"] == 1 and infos[v]["iters"] == zero[v][1]["iters"]
+        else:
+            assert infos[v]["x0_rejected"] == 0 and infos[v]["iters"] < zero[v][1]["iters"], (v, infos[v])
+
+
+def test_batched_full_size_classes_residual_property():
+    """Two volumes of each size class of the 64-volume workload, portraits
+    made by the FP64 oracle: every volume reaches rel. residual 1e-4 by its
+    true residual, which the oracle evaluates for the GPU solution in FP64
+    (||A^T d - (A^T A + lambda I) x|| / ||A^T d|| with the oracle's own
+    ||A||_2^2 for the relative lambda), and one of each class equals its
+    single solve bit for bit."""
     wl = W.WORKLOADS["mh_128x128x64_k8_s2"]
-    plans, ds = [], []
+    plans, ds, cases = [], [], []
     for i, n in enumerate([c for c in W.BATCH_SIZE_CLASSES for _ in range(2)]):
+        p = params(n, s=2, kmin=2, kmax=9)
+        g = oracle_geom(p)
+        b = sens_map(p)
+        tables = oracle.psf_tables(g)
         rho = W.phantom(n, (1.0, 1.0, 1.0), 1000 + i, wl.n_blobs, wl.n_lines)
-        b = W.sensitivity(n, (1.0, 1.0, 1.0), kind="gaussian")
-        pl = Plan(n, ds_factor=2, k_min=2, k_max=9, sensitivity=b)
-        d = torch.empty(pl.portrait_shape, dtype=torch.complex64, device="cuda")
-        mh3d_forward(pl, _dev(rho, torch.float32), d)
-        sig2 = float(torch.sum(torch.abs(d.to(torch.complex128)) ** 2)) / (d.numel() * 10 ** (wl.snr_db / 10))
-        noise = _dev(W.unit_complex_noise(tuple(d.shape), 1000 + i), torch.complex64)
-        plans.append(pl)
-        ds.append((d + math.sqrt(sig2) * noise).contiguous())
+        clean = oracle.forward(g, rho, b, tables)
+        sig2 = np.sum(np.abs(clean) ** 2) / (clean.size * 10 ** (wl.snr_db / 10))
+        d = clean + math.sqrt(sig2) * W.unit_complex_noise(clean.shape, 1000 + i)
+        plans.append(gpu_plan(p, b))
+        ds.append(_dev(d, torch.complex64))
+        cases.append((g, b, tables, d))
     opts = _opts(max_iter=wl.max_iter)
     xs, infos = _solve_batch(plans, ds, opts)
-    for v, inf in enumerate(infos):
+    for v, (inf, (g, b, tables, d)) in enumerate(zip(infos, cases)):
         assert inf["status"] == 0, (v, inf)
-        assert inf["rel_res_true"] <= 1.5e-4, (v, inf)
+        o = oracle.SolveOpts(lam=1e-3, lam_relative=True)
+        rhs = oracle.adjoint(g, d, b, tables)
+        res = rhs - oracle.normal_apply(g, xs[v].astype(np.float64), b, o, tables)
+        rel = float(np.linalg.norm(res) / np.linalg.norm(rhs))
+        assert rel <= 1.5e-4, (v, g.n, rel, inf)
     alone = _solve_each(plans[::2], ds[::2], opts)
     for (xa, ia), xb, ib in zip(alone, xs[::2], infos[::2]):
         assert ia["iters"] == ib["iters"]

@@ -108,3 +108,29 @@ def test_outputs_stay_inside_their_buffers(name):
     xbuf, xx, band = _banded(N, torch.float32, 12345.0)
     mh3d_solve(plan, d.view(g.portrait_shape), make_opts(lam=1e-2, lam_relative=True, max_iter=20), xx.view(g.shape))
     assert _bands_intact(xbuf, band, 12345.0)
+
+
+def test_noalloc_forward_refuses_stream_capture():
+    """mh3d_forward_noalloc uploads its tables from a host buffer freed when
+    the call returns, so a captured call would replay a copy from freed
+    memory: on a capturing stream it returns MH3D_ERR_INVALID_ARG and issues
+    nothing, and the capture itself ends normally."""
+    from paper_2503_13802_gb300 import MH3DError, mh3d_forward_noalloc
+
+    nx, ny, nz = 32, 16, 8
+    rho = torch.zeros((nz, ny, nx), dtype=torch.float32, device="cuda")
+    d = torch.empty((2, nz, ny, nx), dtype=torch.complex64, device="cuda")
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.graph(graph, stream=s):
+        d.zero_()
+        try:
+            mh3d_forward_noalloc((nx, ny, nz), rho, d, k_min=2, k_max=3, stream=s)
+        except MH3DError as e:
+            err = e
+    assert err is not None and "INVALID_ARG" in str(err)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(torch.abs(d).max()) == 0.0
