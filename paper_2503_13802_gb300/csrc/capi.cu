@@ -331,6 +331,15 @@ cudaError_t launch_forward(const Plan& P, const float* rho, float2* d, float* t1
     TArgs ty = tpass_args(P, 1, rho, t1, P.Yhat);
     ty.bin = P.sens;
     if ((e = run_tpass(ty, tpass_outer(P, 1), st)) != cudaSuccess) return e;
+    XArgs xw = xpass_args(P);
+    xw.vin = t2;
+    xw.dout = d;
+    if (xw_available(xw, true)) {
+        // T_z, then the warp-centric drive-axis forward
+        TArgs tz = tpass_args(P, 2, t1, t2, P.Zhat);
+        if ((e = run_tpass(tz, tpass_outer(P, 2), st)) != cudaSuccess) return e;
+        return run_xfwd_w(xw, st);
+    }
     if (ct_zxfwd_available(P.nx, P.nz, P.s) && ((uintptr_t)t1 & 15u) == 0) {
         // T_z and the drive-axis forward in one launch (a cluster of CTAs per y-slab)
         ZXArgs z;
@@ -353,9 +362,28 @@ cudaError_t launch_forward(const Plan& P, const float* rho, float2* d, float* t1
 cudaError_t launch_adjoint(const Plan& P, const float2* d, float* rho, float* t1, float* t2, cudaStream_t st)
 {
     cudaError_t e;
-    const bool fused = ct_xzadj_available(P.nx, P.nz, P.s) && ((uintptr_t)d & 15u) == 0 &&
+    XArgs xw = xpass_args(P);
+    xw.din = d;
+    xw.vout = t1;
+    const bool warp = xw_available(xw, false);
+    const bool fused = !warp && ct_xzadj_available(P.nx, P.nz, P.s) && ((uintptr_t)d & 15u) == 0 &&
                        ((uintptr_t)t2 & 15u) == 0 && P.mx % 2 == 0 && P.M % 2 == 0;
-    if (fused) {
+    if (warp && xzw_available(xw, P.nz) && ((uintptr_t)t2 & 15u) == 0) {
+        // the warp-centric drive-axis adjoint and T_z^T in one launch (a
+        // cluster of two CTAs per y-slab)
+        ZXArgs z;
+        z.x = xw;
+        z.twz = P.az.tw;
+        z.muz = P.Zhat_adj;
+        z.ny = P.ny;
+        z.nz = P.nz;
+        if ((e = run_xzadj_w(z, t2, st)) != cudaSuccess) return e;
+    } else if (warp) {
+        // the warp-centric drive-axis adjoint, then T_z^T
+        if ((e = run_xadj_w(xw, st)) != cudaSuccess) return e;
+        TArgs tz = tpass_args(P, 2, t1, t2, P.Zhat_adj);
+        if ((e = run_tpass(tz, tpass_outer(P, 2), st)) != cudaSuccess) return e;
+    } else if (fused) {
         // the drive-axis adjoint and T_z^T in one launch (a cluster of CTAs per y-slab)
         ZXArgs z;
         z.x = xpass_args(P);

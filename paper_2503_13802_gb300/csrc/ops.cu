@@ -214,6 +214,7 @@ cudaError_t ops_set_attributes()
     if ((e = opt_in_smem(k_xfwd, optin)) != cudaSuccess) return e;
     if ((e = opt_in_smem(k_xadj, optin)) != cudaSuccess) return e;
     if ((e = opt_in_smem(k_xnrm, optin)) != cudaSuccess) return e;
+    if ((e = xw_set_attributes()) != cudaSuccess) return e;
     return ct_set_attributes(optin);
 }
 

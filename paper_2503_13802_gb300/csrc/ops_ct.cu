@@ -473,6 +473,10 @@ static cudaError_t run_zx(ZXArgs& a, const void* zvol, int which, cudaStream_t s
     d.fn<<<d.C * a.ny, d.threads, d.smem, st>>>(a);
     return cudaGetLastError();
 }
+bool ct_encode_z_map(CUtensorMap* m, const void* zvol, int nx, int ny, int nz, int box_x)
+{
+    return al16(zvol) && encode_tile_map(m, zvol, nx, ny, nz, 2, nz, box_x);
+}
 cudaError_t run_zxnrm_ct(ZXArgs& a, const float* zin, cudaStream_t st, bool shared_sms)
 {
     return run_zx(a, zin, shared_sms ? 3 : 0, st);

@@ -195,5 +195,16 @@ cudaError_t run_xzadj_ct(ZXArgs& a, float* zout, cudaStream_t st);
 cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st);
 int xpass_blocks(int rows, int pairs);
 cudaError_t ops_set_attributes();
+// Warp-centric drive-axis passes for n_x = 128, s = 2 (xwarp.cu).
+bool xw_available(const XArgs& a, bool forward);
+cudaError_t xw_set_attributes();
+cudaError_t run_xfwd_w(const XArgs& a, cudaStream_t st);
+cudaError_t run_xadj_w(const XArgs& a, cudaStream_t st);
+// The warp adjoint with T_z^T fused (clusters of two CTAs per y-slab); zout:
+// the z pass's output volume.
+bool xzw_available(const XArgs& a, int nz);
+cudaError_t run_xzadj_w(ZXArgs& a, float* zout, cudaStream_t st);
+// The z volume's tensor map for the cluster passes (box box_x x 1 x nz).
+bool ct_encode_z_map(CUtensorMap* m, const void* zvol, int nx, int ny, int nz, int box_x);
 
 }  // namespace mh3d

@@ -65,4 +65,9 @@ OP_CASES = {
     # an odd harmonic count on the specialised drive-axis passes (the
     # adjoint's last round of two harmonics holds one)
     "oddk5": params((128, 6, 32), s=2, kmin=2, kmax=6, theta=[0.3, -1.2, 2.2, 0.7, -0.4]),
+    # the warp-centric drive-axis passes (n_x = 128, s = 2): an odd row count
+    # that leaves the last warp's last pencil with one row (27 rows), and the
+    # most harmonics a plan takes (31)
+    "warp_ragged27": params((128, 3, 9), s=2, r=1, kmin=2, kmax=4, theta=[0.9, -2.1, 0.4]),
+    "warp_k31": params((128, 4, 4), s=2, kmin=2, kmax=32, gammaA=1.0),
 }

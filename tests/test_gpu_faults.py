@@ -81,7 +81,7 @@ def _bands_intact(buf, band, sentinel):
     return bool((head == sentinel).all()) and bool((tail == sentinel).all())
 
 
-@pytest.mark.parametrize("name", ["ds2_theta", "spec96", "odd_nx27"])
+@pytest.mark.parametrize("name", ["ds2_theta", "spec96", "odd_nx27", "warp_ragged27", "zx128"])
 def test_outputs_stay_inside_their_buffers(name):
     from tests._cases import OP_CASES
     from paper_2503_13802_gb300 import make_opts, mh3d_adjoint, mh3d_forward, mh3d_normal, mh3d_solve

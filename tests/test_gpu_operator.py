@@ -17,30 +17,50 @@ torch = pytest.importorskip("torch")
 TOL = 1e-5
 
 
-@pytest.fixture(params=["specialised", "generic", "alternatives", "cluster4"])
+@pytest.fixture(params=["specialised", "warpsplit", "warp1", "ctalevel", "generic", "alternatives", "cluster4"])
 def kernel_path(request, monkeypatch):
-    """Run each operator test on the compile-time specialised kernels (the
-    default for the common lengths: pipelined drive-axis adjoint, 16-row
-    normal pass), again with MH3D_GENERIC=1, which forces the runtime-general
-    kernels for every size, and on the measured alternatives of the
-    specialised path: the bulk-copy normal pass, the adjoint without copy
-    pipelining, the 16-row forward pass with uneven harmonic groups of
+    """Run each operator test on the default kernels (the compile-time
+    specialised ones for the common lengths, with the warp-centric
+    drive-axis passes at n_x = 128, s = 2, the forward one opted in, two
+    warps per row group, the adjoint fused with T_z^T in y-slab clusters at
+    n_z = 64), again with four warps per row group and the adjoint's T_z^T
+    as a separate launch (MH3D_XWARP_KS=4, MH3D_XWARP_ZX=0), with one warp
+    per row group (MH3D_XWARP_KS=1), on the CTA-level drive-axis
+    passes those replace (MH3D_XWARP=0: y-slab cluster passes, pipelined
+    adjoint, 16-row normal pass), again with MH3D_GENERIC=1, which forces the
+    runtime-general kernels for every size, and on the measured alternatives
+    of the CTA-level path: the bulk-copy normal pass, the adjoint without
+    copy pipelining, the 16-row forward pass with uneven harmonic groups of
     three per CTA, and the separate T_z and drive-axis passes instead of the
     y-slab cluster passes; and once more with those cluster passes on
     clusters of four CTAs (MH3D_ZX_CLUSTER=4) and the pipelined adjoint in
     rounds of two harmonics (MH3D_XADJ_KB=2)."""
     for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS",
-              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX", "MH3D_ZX_CLUSTER", "MH3D_XADJ_KB"):
+              "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX", "MH3D_ZX_CLUSTER", "MH3D_XADJ_KB", "MH3D_XWARP",
+              "MH3D_XWARP_FWD", "MH3D_XWARP_KS", "MH3D_XWARP_ZX"):
         monkeypatch.delenv(v, raising=False)
-    if request.param == "generic":
+    if request.param == "specialised":
+        monkeypatch.setenv("MH3D_XWARP_FWD", "1")    # the opt-in warp forward too
+    elif request.param == "warpsplit":
+        monkeypatch.setenv("MH3D_XWARP_FWD", "1")
+        monkeypatch.setenv("MH3D_XWARP_KS", "4")
+        monkeypatch.setenv("MH3D_XWARP_ZX", "0")     # the warp adjoint and T_z^T as two launches
+    elif request.param == "warp1":
+        monkeypatch.setenv("MH3D_XWARP_FWD", "1")
+        monkeypatch.setenv("MH3D_XWARP_KS", "1")
+    elif request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
+    elif request.param == "ctalevel":
+        monkeypatch.setenv("MH3D_XWARP", "0")
     elif request.param == "alternatives":
+        monkeypatch.setenv("MH3D_XWARP", "0")
         monkeypatch.setenv("MH3D_XNRM_BULK", "1")
         monkeypatch.setenv("MH3D_XADJ_BULK", "0")
         monkeypatch.setenv("MH3D_XFWD_KPC", "3")
         monkeypatch.setenv("MH3D_XFWD_PAIRS", "8")
         monkeypatch.setenv("MH3D_FUSE_ZX", "0")
     elif request.param == "cluster4":
+        monkeypatch.setenv("MH3D_XWARP", "0")
         monkeypatch.setenv("MH3D_ZX_CLUSTER", "4")
         monkeypatch.setenv("MH3D_XADJ_KB", "2")
     return request.param
