@@ -433,8 +433,10 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
     CgCtl cgp;
     if (cg) cgp = *cg;   // later kernels only check the done flag
     auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
-    if (mode == 0 && reg.kind == 0 && ct_zxnrm_available(P.nx, P.nz, P.s) && a16(t1) && a16(in) && a16(out) &&
-        (!P.sens || a16(P.sens))) {
+    XArgs xq = xpass_args(P);
+    const bool zx_warp = mode == 0 && reg.kind == 0 && zxnw_available(xq, P.nz) && ct_zxnrm_available(P.nx, P.nz, P.s);
+    if (mode == 0 && reg.kind == 0 && (ct_zxnrm_available(P.nx, P.nz, P.s) || zx_warp) && a16(t1) && a16(in) &&
+        a16(out) && (!P.sens || a16(P.sens))) {
         // T_z and the drive-axis normal pass in one launch (a cluster of CTAs per y-slab)
         ZXArgs z;
         z.x = xpass_args(P);
@@ -458,6 +460,7 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
         z.muz = P.Znorm;
         z.ny = P.ny;
         z.nz = P.nz;
+        if (zx_warp) return run_zxnrm_w(z, t1, st, P.w.shared_sms);
         return run_zxnrm_ct(z, t1, st, P.w.shared_sms);
     }
     TArgs tz = tpass_args(P, 2, t1, t2, mode == 0 ? P.Znorm : P.Zhat);
@@ -497,7 +500,7 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
     XArgs xa = xpass_args(P);
     xa.din = portrait;
     xa.vout = t1;
-    if ((e = run_xadj(xa, st)) != cudaSuccess) return e;
+    if ((e = xw_available(xa, false) ? run_xadj_w(xa, st) : run_xadj(xa, st)) != cudaSuccess) return e;
     TArgs tz2 = tpass_args(P, 2, t1, t2, P.Zhat_adj);
     if (cg) tz2.cg = cgp;
     if ((e = run_tpass(tz2, tpass_outer(P, 2), st)) != cudaSuccess) return e;

@@ -204,6 +204,10 @@ cudaError_t run_xadj_w(const XArgs& a, cudaStream_t st);
 // the z pass's output volume.
 bool xzw_available(const XArgs& a, int nz);
 cudaError_t run_xzadj_w(ZXArgs& a, float* zout, cudaStream_t st);
+// The warp-centric cluster normal pass (T_z + drive-axis blocks + epilogue
+// + dots; zin: the z pass's input); shared_sms as for run_zxnrm_ct.
+bool zxnw_available(const XArgs& a, int nz);
+cudaError_t run_zxnrm_w(ZXArgs& a, const float* zin, cudaStream_t st, bool shared_sms);
 // The z volume's tensor map for the cluster passes (box box_x x 1 x nz).
 bool ct_encode_z_map(CUtensorMap* m, const void* zvol, int nx, int ny, int nz, int box_x);
 

@@ -60,8 +60,21 @@ bool xzw_available(const XArgs& a, int nz)
     return xw_available(a, false) && !env_off("MH3D_XWARP_ZX") && nz == 64;
 }
 
+// The warp-centric cluster normal pass (n_x = 128, s = 2, n_z = 64),
+// opt-in (MH3D_XWARP_NRM=1): in the CG loop at 128x128x64 it measured 25.8
+// us per iteration against 23.1 us for the CTA-level cluster pass (same
+// box), whose z part runs on 256 threads per CTA instead of 128.
+bool zxnw_available(const XArgs& a, int nz)
+{
+    return !env_on("MH3D_GENERIC") && !env_off("MH3D_XWARP") && env_on("MH3D_XWARP_NRM") && a.nx == xw::kNX &&
+           a.s == 2 && a.mx == xw::kMX && nz == 64;
+}
+
 cudaError_t xw_set_attributes()
 {
+    cudaError_t en = smem_attr(xw::k_zxnrm_w<LZ64, true>, xw::ZxwGeom<LZ64>::smem());
+    if (en == cudaSuccess) en = smem_attr(xw::k_zxnrm_w<LZ64, false>, xw::ZxwGeom<LZ64>::smem());
+    if (en != cudaSuccess) return en;
     cudaError_t e0 = smem_attr(xw::k_xzadj_w<LZ64, 1>, xw::XzwGeom<LZ64, 1>::smem(kMaxK));
     if (e0 == cudaSuccess) e0 = smem_attr(xw::k_xzadj_w<LZ64, 2>, xw::XzwGeom<LZ64, 2>::smem(kMaxK));
     if (e0 == cudaSuccess) e0 = smem_attr(xw::k_xzadj_w<LZ64, 4>, xw::XzwGeom<LZ64, 4>::smem(kMaxK));
@@ -123,6 +136,21 @@ cudaError_t run_xzadj_w(ZXArgs& a, float* zout, cudaStream_t st)
         xw::k_xzadj_w<LZ64, 2><<<grid, xw::XzwGeom<LZ64, 2>::T, xw::XzwGeom<LZ64, 2>::smem(a.x.K), st>>>(a);
     else
         xw::k_xzadj_w<LZ64, 4><<<grid, xw::XzwGeom<LZ64, 4>::T, xw::XzwGeom<LZ64, 4>::smem(a.x.K), st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mh3d
+
+namespace mh3d {
+
+cudaError_t run_zxnrm_w(ZXArgs& a, const float* zin, cudaStream_t st, bool shared_sms)
+{
+    using G = xw::ZxwGeom<LZ64>;
+    if (a.nz != 64 || !al(zin, 16) || !al(a.x.pin, 16) || !al(a.x.qout, 16)) return cudaErrorInvalidValue;
+    if (!ct_encode_z_map(&a.tz, zin, a.x.nx, a.ny, a.nz, a.x.nx / 2)) return cudaErrorInvalidValue;
+    const dim3 grid(2 * a.ny);
+    if (shared_sms) xw::k_zxnrm_w<LZ64, false><<<grid, G::T, G::smem(), st>>>(a);
+    else xw::k_zxnrm_w<LZ64, true><<<grid, G::T, G::smem(), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -75,6 +75,81 @@ __device__ __forceinline__ void load_tables(const XArgs& a, float2* tw, float2* 
     __syncthreads();
 }
 
+// Forward length-128 transform of a pencil on 8 lanes: xe[n2] and xo[n2]
+// hold x[2t + 16 n2] and x[2t + 1 + 16 n2]; X[j] receives the spectrum at
+// t + 8 j.  z: the pencil's scratch (8 x 18 float2 used); the caller makes
+// sure no lane still reads it.
+__device__ __forceinline__ void wfwd128(float2 (&xe)[8], float2 (&xo)[8], float2* z, const float2* tw, int t,
+                                        float2 (&X)[16])
+{
+    dft<8, false>(xe);
+    dft<8, false>(xo);
+    z[2 * t] = xe[0];
+    z[2 * t + 1] = xo[0];
+#pragma unroll
+    for (int f1 = 1; f1 < 8; ++f1) {
+        z[f1 * kRSF + 2 * t] = c_mul(xe[f1], tw[(2 * t) * f1]);
+        z[f1 * kRSF + 2 * t + 1] = c_mul(xo[f1], tw[(2 * t + 1) * f1]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) X[n1] = z[t * kRSF + n1];
+    dft<16, false>(X);
+}
+
+// Inverse length-128 transform of a pencil on 8 lanes: V[m] holds the
+// frequency t + 8 m; out[e][i] receives the sample t + 8 e + 16 i.  ub: the
+// pencil's scratch (16 x 17 float2 used); the caller makes sure no lane still
+// reads it.
+__device__ __forceinline__ void winv128(float2 (&V)[16], float2* ub, const float2* tw, int t, float2 (&out)[2][8])
+{
+    dft<16, true>(V);
+#pragma unroll
+    for (int j = 1; j < 16; ++j) V[j] = c_mulc(V[j], tw[t * j]);   // e^{+2 pi i t j / 128}
+#pragma unroll
+    for (int j = 0; j < 16; ++j) ub[j * kRSU + t] = V[j];
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int j = t + 8 * e;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) out[e][i] = ub[j * kRSU + i];
+        dft<8, true>(out[e]);
+    }
+}
+
+// One harmonic of the adjoint on a pencil: Re(e^{-i theta} y) of rows a
+// (ya) and b (yb), samples t + 8 n2, through the length-64 forward transform
+// (lane t ends with frequencies t + 8 k1), times conj(X^_k) at k1 and at its
+// alias + 64, added into V.  hb: the pencil's 8 x 9 scratch; the warp
+// barrier before it is written follows the first radix step, so the loads
+// a caller issues just before (a warp barrier waits for them) overlap that
+// step.
+__device__ __forceinline__ void wadj_harmonic(const float2 (&ya)[8], const float2 (&yb)[8], float2 ph, float2* hb,
+                                              const float2* tw, const float2* xk, int t, float2 (&V)[16])
+{
+    float2 w[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2)
+        w[n2] = make_float2(fmaf(ph.x, ya[n2].x, ph.y * ya[n2].y), fmaf(ph.x, yb[n2].x, ph.y * yb[n2].y));
+    dft<8, false>(w);
+#pragma unroll
+    for (int k2 = 1; k2 < 8; ++k2) w[k2] = c_mul(w[k2], tw[2 * t * k2]);   // W64^{t k2}
+    __syncwarp();   // the previous harmonic's reads of hb are done
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) hb[k2 * kRS8 + t] = w[k2];
+    __syncwarp();
+    float2 Y[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) Y[n1] = hb[t * kRS8 + n1];
+    dft<8, false>(Y);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        V[k1] = c_add(V[k1], c_mulc(Y[k1], xk[8 * k1]));
+        V[k1 + 8] = c_add(V[k1 + 8], c_mulc(Y[k1], xk[8 * k1 + 64]));
+    }
+}
+
 // d = Phi X_k (rows of a.vin): rows [rows][128] float -> portraits
 // [K][rows][64] complex.  KS warps share a row group: each runs the
 // length-128 transform of the group's rows and then the harmonics
@@ -112,22 +187,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_xfwd_w128(const XArgs a)
             xo[n2] = make_float2(u.y, v.y);
         }
     }
-    dft<8, false>(xe);
-    dft<8, false>(xo);
-    float2* z = sc + q * kQSF;
-    z[2 * t] = xe[0];
-    z[2 * t + 1] = xo[0];
-#pragma unroll
-    for (int f1 = 1; f1 < 8; ++f1) {
-        z[f1 * kRSF + 2 * t] = c_mul(xe[f1], tw[(2 * t) * f1]);
-        z[f1 * kRSF + 2 * t + 1] = c_mul(xo[f1], tw[(2 * t + 1) * f1]);
-    }
-    __syncwarp();
-    // second step: f1 = t, radix 16 over n1 -> X[j] = spectrum at t + 8 j
-    float2 X[16];
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) X[n1] = z[t * kRSF + n1];
-    dft<16, false>(X);
+    float2 X[16];   // spectrum at t + 8 j
+    wfwd128(xe, xo, sc + q * kQSF, tw, t, X);
 
     float2* hb = sc + q * kQS8;
     float2* dka = a.dout + (long long)ra * kMX + t;
@@ -212,32 +273,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_xadj_w128(const XArgs a)
             na[n2] = (more && va) ? __ldg(sa + off + 8 * n2) : zero;
             nb[n2] = (more && vb) ? __ldg(sb + off + 8 * n2) : zero;
         }
-        // Re(e^{-i theta_k} y) of both rows packed as one complex sequence;
-        // length-64 forward, first step (n1 = t)
-        const float2 p = ph[k];
-        float2 w[8];
-#pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2)
-            w[n2] = make_float2(fmaf(p.x, ya[n2].x, p.y * ya[n2].y), fmaf(p.x, yb[n2].x, p.y * yb[n2].y));
-        dft<8, false>(w);
-#pragma unroll
-        for (int k2 = 1; k2 < 8; ++k2) w[k2] = c_mul(w[k2], tw[2 * t * k2]);   // W64^{t k2}
-        __syncwarp();   // the previous harmonic's reads of this scratch are done
-#pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) hb[k2 * kRS8 + t] = w[k2];
-        __syncwarp();
-        // second step: k2 = t, radix 8 over n1 -> frequencies t + 8 k1
-        float2 Y[8];
-#pragma unroll
-        for (int n1 = 0; n1 < 8; ++n1) Y[n1] = hb[t * kRS8 + n1];
-        dft<8, false>(Y);
-        // times conj(X^_k), periodised to length 128, summed over k
-        const float2* xk = xh + k * kNX + t;
-#pragma unroll
-        for (int k1 = 0; k1 < 8; ++k1) {
-            V[k1] = c_add(V[k1], c_mulc(Y[k1], xk[8 * k1]));
-            V[k1 + 8] = c_add(V[k1 + 8], c_mulc(Y[k1], xk[8 * k1 + 64]));
-        }
+        // Re(e^{-i theta_k} y) of both rows packed as one complex sequence,
+        // its length-64 transform times conj(X^_k) periodised, into V
+        wadj_harmonic(ya, yb, ph[k], hb, tw, xh + k * kNX + t, t, V);
 #pragma unroll
         for (int n2 = 0; n2 < 8; ++n2) {
             ya[n2] = na[n2];
@@ -262,31 +300,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_xadj_w128(const XArgs a)
             for (int i = 0; i < 16; ++i) V[i] = c_add(V[i], o[i * 32 + lane]);
         }
     }
-    // length-128 inverse: lane t holds frequencies t + 8 m; radix 16 over m
-    dft<16, true>(V);
-#pragma unroll
-    for (int j = 1; j < 16; ++j) V[j] = c_mulc(V[j], tw[t * j]);   // e^{+2 pi i t j / 128}
-    float2* ub = sc + q * kQSU;
+    // length-128 inverse: lane t holds frequencies t + 8 m
     __syncwarp();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) ub[j * kRSU + t] = V[j];
-    __syncwarp();
-    // radix 8 over t for j = t and t + 8 -> samples j + 16 i
+    float2 g[2][8];   // samples t + 8 e + 16 i
+    winv128(V, sc + q * kQSU, tw, t, g);
     float* outa = a.vout + (long long)ra * kNX;
     float* outb = a.vout + (long long)rb * kNX;
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int j = t + 8 * e;
-        float2 g[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) g[i] = ub[j * kRSU + i];
-        dft<8, true>(g);
+    for (int e = 0; e < 2; ++e)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            if (va) outa[j + 16 * i] = g[i].x;
-            if (vb) outb[j + 16 * i] = g[i].y;
+            if (va) outa[t + 8 * e + 16 * i] = g[e][i].x;
+            if (vb) outb[t + 8 * e + 16 * i] = g[e][i].y;
         }
-    }
 }
 
 
@@ -311,7 +337,8 @@ struct XzwGeom {
     static constexpr int T = WARPS * 32;
     static constexpr int QX = kNX / 2, PZ = QX / 2;   // 64 columns (32 column pairs) per CTA
     static constexpr int XT = NZ * PZ;                  // float2: the z-tile
-    static constexpr int SCR = WARPS * kScrA;           // float2: phase-1 scratch
+    static constexpr int WS = kScrA;                    // float2 per warp
+    static constexpr int SCR = WARPS * WS;              // float2: phase-1 scratch
     static constexpr int UN = SCR > XT ? SCR : XT;      // phase 2: the z pass's second buffer
     static_assert(ROWS % kRowsW == 0 && T <= 1024 && GROUPS + 1 <= 16, "row groups of the slab");
     static __host__ __device__ int tab(int K) { return kNX + 2 * NZ + ((K + 1) & ~1) + K * kNX; }
@@ -352,11 +379,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XzwGeom<LZ, KS>::T)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = lane >> 3, t = lane & 7;
     const int gl = warp / KS, split = warp % KS;
-    float2* sc = un + warp * kScrA;
+    float2* sc = un + warp * G::WS;
     const int za = (int)rank * ROWS + gl * kRowsW + 2 * q, zb = za + 1;
     const float2* sa = a.x.din + ((long long)za * a.ny + y) * kMX + t;
     const float2* sb = a.x.din + ((long long)zb * a.ny + y) * kMX + t;
     const float2 zero = make_float2(0.f, 0.f);
+    float2 V[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) V[i] = zero;
+    float2* hb = sc + q * kQS8;
     float2 ya[8], yb[8];
     {
         const long long off = (long long)split * a.x.M;
@@ -367,10 +398,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XzwGeom<LZ, KS>::T)
             yb[n2] = any ? __ldg(sb + off + 8 * n2) : zero;
         }
     }
-    float2 V[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) V[i] = zero;
-    float2* hb = sc + q * kQS8;
     for (int k = split; k < K; k += KS) {
         float2 na[8], nb[8];
         const bool more = k + KS < K;
@@ -380,28 +407,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XzwGeom<LZ, KS>::T)
             na[n2] = more ? __ldg(sa + off + 8 * n2) : zero;
             nb[n2] = more ? __ldg(sb + off + 8 * n2) : zero;
         }
-        const float2 p = ph[k];
-        float2 w[8];
-#pragma unroll
-        for (int n2 = 0; n2 < 8; ++n2)
-            w[n2] = make_float2(fmaf(p.x, ya[n2].x, p.y * ya[n2].y), fmaf(p.x, yb[n2].x, p.y * yb[n2].y));
-        dft<8, false>(w);
-#pragma unroll
-        for (int k2 = 1; k2 < 8; ++k2) w[k2] = c_mul(w[k2], tw[2 * t * k2]);
-        __syncwarp();
-#pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) hb[k2 * kRS8 + t] = w[k2];
-        __syncwarp();
-        float2 Y[8];
-#pragma unroll
-        for (int n1 = 0; n1 < 8; ++n1) Y[n1] = hb[t * kRS8 + n1];
-        dft<8, false>(Y);
-        const float2* xk = xh + k * kNX + t;
-#pragma unroll
-        for (int k1 = 0; k1 < 8; ++k1) {
-            V[k1] = c_add(V[k1], c_mulc(Y[k1], xk[8 * k1]));
-            V[k1 + 8] = c_add(V[k1 + 8], c_mulc(Y[k1], xk[8 * k1 + 64]));
-        }
+        wadj_harmonic(ya, yb, ph[k], hb, tw, xh + k * kNX + t, t, V);
 #pragma unroll
         for (int n2 = 0; n2 < 8; ++n2) {
             ya[n2] = na[n2];
@@ -418,44 +424,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XzwGeom<LZ, KS>::T)
         if (split == 0) {
 #pragma unroll
             for (int w2 = 1; w2 < KS; ++w2) {
-                const float2* o = un + (warp + w2) * kScrA;
+                const float2* o = un + (warp + w2) * G::WS;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) V[i] = c_add(V[i], o[i * 32 + lane]);
             }
         }
     }
     if (split == 0) {
-        dft<16, true>(V);
-#pragma unroll
-        for (int j = 1; j < 16; ++j) V[j] = c_mulc(V[j], tw[t * j]);
-        float2* ub = sc + q * kQSU;
         __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) ub[j * kRSU + t] = V[j];
-        __syncwarp();
+        float2 g[2][8];   // samples t + 8 e + 16 i
+        winv128(V, sc + q * kQSU, tw, t, g);
         float* xtf = reinterpret_cast<float*>(xt);
         const uint32_t peer = cluster_smem_addr(xtf, rank ^ 1u);
+        // sample x = t + 8 e + 16 i: owner CTA i / 4, column t + 8 e + 16 (i % 4)
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int j = t + 8 * e;
-            float2 g[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) g[i] = ub[j * kRSU + i];
-            dft<8, true>(g);
-            // sample x = j + 16 i: owner CTA i / 4, column j + 16 (i % 4)
+        for (int e = 0; e < 2; ++e)
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int col = j + 16 * (i & 3);
+                const int col = t + 8 * e + 16 * (i & 3);
                 const int oa = za * QX + col, ob = zb * QX + col;
                 if ((uint32_t)(i >> 2) == rank) {
-                    xtf[oa] = g[i].x;
-                    xtf[ob] = g[i].y;
+                    xtf[oa] = g[e][i].x;
+                    xtf[ob] = g[e][i].y;
                 } else {
-                    st_cluster_f32(peer + 4u * (uint32_t)oa, g[i].x);
-                    st_cluster_f32(peer + 4u * (uint32_t)ob, g[i].y);
+                    st_cluster_f32(peer + 4u * (uint32_t)oa, g[e][i].x);
+                    st_cluster_f32(peer + 4u * (uint32_t)ob, g[e][i].y);
                 }
             }
-        }
     }
     cluster_sync_all();   // every column of this CTA's z-tile has landed
 
@@ -477,6 +472,145 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(XzwGeom<LZ, KS>::T)
         bulk_commit();
         bulk_wait_all();   // the copy reads shared memory and must land before the CTA ends
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// The normal operator's last two steps in one launch (the CG loop's second
+// kernel): T_z (multiplier |Z^|^2), then the drive-axis Fourier-block
+// product, q = b w + lambda p, and the dot products p^T q and p^T p, for one
+// y-slab per cluster of two CTAs (the structure of ct::k_zxnrm_ct, with the
+// CTA-level drive-axis part replaced by warp-centric transforms):
+//   phase 1: ct::zx_zconv -- CTA c convolves its 64 x-columns along z and
+//            stores each row into the exchange buffer of the CTA that owns
+//            it (rows [c nz/2, (c+1) nz/2));
+//   cluster barrier;
+//   phase 2: each warp takes 8 of the CTA's rows: the length-128 forward
+//            transform (lane t ends with frequencies t + 8 j, so a frequency
+//            and its alias + 64 sit in one lane), the s x s alias-block
+//            product Q(m) of the normal operator's drive-axis part (Sec. 4.3,
+//            the Fourier-block form of sum_k X_k^T P^T P X_k), the inverse,
+//            then the epilogue on the lane's 32 samples (b and p loaded
+//            before the transforms) and the CTA's pair-sum reduction.
+// Host conditions: n_x = 128, s = 2, R = I, 16-byte aligned vectors.
+template <class LZ>
+struct ZxwGeom {
+    static constexpr int NZ = ct::RInfo<LZ>::n(), ROWS = NZ / 2, WARPS = ROWS / kRowsW, T = WARPS * 32;
+    static constexpr int QX = kNX / 2, PZ = QX / 2, NXP = kNX + 1;
+    static_assert(ROWS % kRowsW == 0 && NZ % 2 == 0, "whole row groups per CTA");
+    static constexpr int TAB = 2 * NZ + kNX + kMX * 4;          // float2: W_nz, z multiplier, W_128, Q blocks
+    static constexpr int XB = ROWS * NXP;                        // floats: exchange rows
+    static constexpr int OFF = (TAB + (XB + 1) / 2 + 15) / 16 * 16;   // float2 offset of the union (128 B)
+    static constexpr int P1 = 2 * NZ * PZ;                       // phase 1: tile + second buffer
+    static constexpr int P2 = WARPS * kScrA;                     // phase 2: warp scratch
+    static constexpr int UN = P1 > P2 ? P1 : P2;
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)(OFF + UN) + 128; }
+};
+
+template <class LZ, bool EARLY>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(ZxwGeom<LZ>::T)
+    k_zxnrm_w(const __grid_constant__ ZXArgs a)
+{
+    using G = ZxwGeom<LZ>;
+    using namespace ct;
+    constexpr int NZ = G::NZ, ROWS = G::ROWS, T = G::T, NXP = G::NXP;
+    extern __shared__ __align__(128) float2 zxw_raw[];
+    __shared__ double red[34];
+    __shared__ __align__(8) uint64_t bar;
+    float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(zxw_raw) + 127) & ~uintptr_t(127));
+    float2* twz = sm;
+    float2* muz = twz + NZ;
+    float2* twx = muz + NZ;           // W_128 (zx_zconv loads it)
+    float2* qb = twx + kNX;           // [64][2][2] alias blocks
+    float* xb = reinterpret_cast<float*>(qb + kMX * 4);
+    float2* un = sm + G::OFF;         // 128-byte aligned: the TMA box lands at its start
+    const uint32_t rank = cluster_ctarank();
+    const int y = (int)blockIdx.x / 2;
+    for (int i = threadIdx.x; i < kMX * 4; i += T) qb[i] = a.x.Q[i];
+    cluster_sync_all();   // every CTA of the cluster runs before any remote store
+    float dummy;
+    if (a.x.cg_active && !cg_enter(a.x.cg, false, &dummy, red)) return;
+
+    // ---- phase 1: z-axis convolution of this CTA's columns (ends on a CTA barrier)
+    const bool ok = zx_zconv<LZ, kNX, 2, G::PZ, T>(a, a.muz, twz, muz, twx, xb, un, &bar, y, rank);
+    cluster_sync_all();   // every part of every owned row has landed (local and remote stores)
+    if (!ok) return;
+
+    // ---- phase 2: rows rr = 8 warp + 2q (+1) of this CTA, z = rank ROWS + rr
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane >> 3, t = lane & 7;
+    const int rra = warp * kRowsW + 2 * q, rrb = rra + 1;
+    const long long ia = ((long long)((int)rank * ROWS + rra) * a.ny + y) * kNX;
+    const long long ib = ((long long)((int)rank * ROWS + rrb) * a.ny + y) * kNX;
+    const float* __restrict__ bp = a.x.b;
+    const float* __restrict__ pp = a.x.pin;
+    // epilogue operands at the lane's samples x = t + 8 e + 16 i
+    float ba[2][8], bb[2][8], pa[2][8], pb[2][8];
+    auto load_bp = [&]() {
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int x = t + 8 * e + 16 * i;
+                ba[e][i] = bp ? __ldg(bp + ia + x) : 1.f;
+                bb[e][i] = bp ? __ldg(bp + ib + x) : 1.f;
+                pa[e][i] = __ldg(pp + ia + x);
+                pb[e][i] = __ldg(pp + ib + x);
+            }
+    };
+    if constexpr (EARLY) load_bp();
+    float2 xe[8], xo[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) {
+        const int c = 2 * t + 16 * n2;
+        xe[n2] = make_float2(xb[rra * NXP + c], xb[rrb * NXP + c]);
+        xo[n2] = make_float2(xb[rra * NXP + c + 1], xb[rrb * NXP + c + 1]);
+    }
+    float2* sc = un + warp * kScrA;   // the phase-1 buffers are dead after the cluster barrier
+    float2 X[16];   // spectrum at t + 8 j
+    wfwd128(xe, xo, sc + q * kQSF, twx, t, X);
+    // alias blocks: out(m + 64 a) = sum_b Q(m)[a][b] in(m + 64 b), m = t + 8 j
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float2* qm = qb + (t + 8 * j) * 4;
+        const float2 u0 = X[j], u1 = X[j + 8];
+        X[j] = c_add(c_mul(qm[0], u0), c_mul(qm[1], u1));
+        X[j + 8] = c_add(c_mul(qm[2], u0), c_mul(qm[3], u1));
+    }
+    __syncwarp();   // the forward's scratch reads are done
+    float2 g[2][8];
+    winv128(X, sc + q * kQSU, twx, t, g);
+    if constexpr (!EARLY) load_bp();
+    // epilogue: q = b w + lambda p, dots p^T q (and p^T p)
+    float* __restrict__ qo = a.x.qout;
+    const float lam = a.x.reg.lambda;
+    DotAcc dacc, dacc2;
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int x = t + 8 * e + 16 * i;
+            const float qa = fmaf(ba[e][i], g[e][i].x, lam * pa[e][i]);
+            const float qb2 = fmaf(bb[e][i], g[e][i].y, lam * pb[e][i]);
+            qo[ia + x] = qa;
+            qo[ib + x] = qb2;
+            dacc.add(pa[e][i], qa);
+            dacc.add(pb[e][i], qb2);
+            if (a.x.part2) {
+                dacc2.add(pa[e][i], pa[e][i]);
+                dacc2.add(pb[e][i], pb[e][i]);
+            }
+        }
+    if (a.x.part) {
+        float2 t0, t2;
+        block_pair_acc2(dacc, a.x.part2 ? &dacc2 : nullptr, reinterpret_cast<float*>(red), &t0, &t2);
+        if (a.x.part2)
+            grid_sum_finalize2(t0, t2, a.x.part, a.x.part2, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out,
+                               a.x.sum_out2);
+        else
+            grid_sum_finalize(t0, a.x.part, blockIdx.x, gridDim.x, a.x.ticket, a.x.sum_out);
+    }
+    if (a.x.count_iter) cg_count_iteration(a.x.cg);
 }
 
 }  // namespace xw

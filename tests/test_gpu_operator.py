@@ -21,7 +21,7 @@ TOL = 1e-5
 def kernel_path(request, monkeypatch):
     """Run each operator test on the default kernels (the compile-time
     specialised ones for the common lengths, with the warp-centric
-    drive-axis passes at n_x = 128, s = 2, the forward one opted in, two
+    drive-axis passes at n_x = 128, s = 2, the forward and normal ones opted in, two
     warps per row group, the adjoint fused with T_z^T in y-slab clusters at
     n_z = 64), again with four warps per row group and the adjoint's T_z^T
     as a separate launch (MH3D_XWARP_KS=4, MH3D_XWARP_ZX=0), with one warp
@@ -37,10 +37,11 @@ def kernel_path(request, monkeypatch):
     rounds of two harmonics (MH3D_XADJ_KB=2)."""
     for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS",
               "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX", "MH3D_ZX_CLUSTER", "MH3D_XADJ_KB", "MH3D_XWARP",
-              "MH3D_XWARP_FWD", "MH3D_XWARP_KS", "MH3D_XWARP_ZX"):
+              "MH3D_XWARP_FWD", "MH3D_XWARP_KS", "MH3D_XWARP_ZX", "MH3D_XWARP_NRM"):
         monkeypatch.delenv(v, raising=False)
     if request.param == "specialised":
-        monkeypatch.setenv("MH3D_XWARP_FWD", "1")    # the opt-in warp forward too
+        monkeypatch.setenv("MH3D_XWARP_FWD", "1")    # the opt-in warp forward and normal passes too
+        monkeypatch.setenv("MH3D_XWARP_NRM", "1")
     elif request.param == "warpsplit":
         monkeypatch.setenv("MH3D_XWARP_FWD", "1")
         monkeypatch.setenv("MH3D_XWARP_KS", "4")
@@ -139,7 +140,7 @@ def test_adjoint_matches_oracle(name, kernel_path):
     assert rel_l2(rho.cpu().numpy(), ref) <= TOL, rel_l2(rho.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("name", ["cube32_k4", "ds2_theta", "ds3_radix3", "odd_nx27", "tall_z"])
+@pytest.mark.parametrize("name", ["cube32_k4", "ds2_theta", "ds3_radix3", "odd_nx27", "tall_z", "zx128", "zx64"])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("reg_kind", [0, 1])
 def test_normal_matches_oracle(name, mode, reg_kind, kernel_path):

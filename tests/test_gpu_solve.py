@@ -158,6 +158,32 @@ def test_full_size_128x128x64_reconstruction_matches_oracle():
     assert rel_l2(xg4, same) <= 1e-4, rel_l2(xg4, same)
 
 
+@pytest.mark.parametrize("nrm", ["warp", "ctalevel"])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_cg_on_the_fused_slab_normal_pass_matches_oracle(nrm, variant, monkeypatch):
+    """128x8x64, k = 2..9, s = 2: the CG loop's fused T_z + drive-axis normal
+    pass with its dot products, CTA-level (default) or warp-centric
+    (MH3D_XWARP_NRM=1), against the oracle's CG at a fixed 40 iterations."""
+    if nrm == "warp":
+        monkeypatch.setenv("MH3D_XWARP_NRM", "1")
+    else:
+        monkeypatch.delenv("MH3D_XWARP_NRM", raising=False)
+    p = params((128, 8, 64), s=2, r=1, kmin=2, kmax=9, theta=list(np.linspace(-2.0, 2.5, 8)))
+    g = oracle_geom(p)
+    b = sens_map(p)
+    _, d = _data(p, g, b, 4, 25.0)
+    xo, it, hist = oracle.cg(g, d, b, oracle.SolveOpts(lam=1e-3, lam_relative=True, rel_tol=0.0, max_iter=40))
+    from paper_2503_13802_gb300 import make_opts, mh3d_solve
+
+    plan = gpu_plan(p, b)
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    info = mh3d_solve(plan, _dev(d, torch.complex64), make_opts(lam=1e-3, lam_relative=True, max_iter=40,
+                                                               fixed_iters=True, cg_variant=variant), x)
+    assert info["iters"] == 40 and info["status"] == 0, info
+    assert rel_l2(x.cpu().numpy(), xo) <= 1e-4, rel_l2(x.cpu().numpy(), xo)
+    np.testing.assert_allclose(info["history"][:15], hist[:15], rtol=1e-3)
+
+
 def test_fp32_scalar_division_variant_matches_oracle():
     """fp32_scalar_div (beta and alpha as FP32 quotients of split
     significands) against the default FP64 quotients: both reach the common
