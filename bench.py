@@ -61,6 +61,8 @@ def parse():
                     help="the general (three-component, non-separable PSF) operators' timing (own JSON line)")
     ap.add_argument("--train-n", type=int, default=2000)
     ap.add_argument("--test-n", type=int, default=200)
+    ap.add_argument("--batch-n", type=int, default=32,
+                    help="learned: volumes of the batched zero-start / warm-start comparison")
     ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
@@ -694,6 +696,44 @@ def bench_learned(args):
     ratio = np.array(t0) / np.array(t1)
     m, sd = float(ratio.mean()), float(ratio.std(ddof=1)) if len(ratio) > 1 else 0.0
     half = 1.972 * sd / math.sqrt(len(ratio))
+
+    # the learned + batched form: the first test volumes in one batched call,
+    # zero start (mh3d_solve_batched) against the network's x0 per volume
+    # (inference included) through mh3d_solve_batched_warm
+    from paper_2503_13802_gb300 import mh3d_solve_batched
+
+    nb = min(args.batch_n, len(tests))
+    bplans = [Plan(wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max,
+                   sensitivity=b) for _ in range(nb)]
+    bd = tests[:nb]
+    bx = [torch.empty(plan.shape, dtype=torch.float32, device=dev) for _ in range(nb)]
+    bx0 = [torch.empty(plan.shape, dtype=torch.float32, device=dev) for _ in range(nb)]
+    bopts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter, x0_fallback=True)
+
+    def batch_zero():
+        return mh3d_solve_batched(bplans, bd, bopts, bx)
+
+    def batch_warm():
+        for i in range(nb):
+            ws.predict(bd[i], bx0[i])
+        return mh3d_solve_batched(bplans, bd, bopts, bx, x0s=bx0)
+
+    for _ in range(2):   # warm-up (graph capture)
+        batch_zero()
+        batch_warm()
+    tb0, tb1, ib0, ib1 = [], [], [], []
+    for _ in range(3):
+        inf0, s0 = timed(batch_zero)
+        inf1, s1 = timed(batch_warm)
+        tb0.append(s0)
+        tb1.append(s1)
+        ib0.extend(v["iters"] for v in inf0)
+        ib1.extend(v["iters"] for v in inf1)
+    batched = {"volumes": nb, "zero_start_value": nb / float(np.mean(tb0)), "warm_start_value": nb / float(np.mean(tb1)),
+               "speedup": float(np.mean(tb0)) / float(np.mean(tb1)), "zero_mean_iters": float(np.mean(ib0)),
+               "warm_mean_iters": float(np.mean(ib1)),
+               "what": "one mh3d_solve_batched call over the first test volumes, zero start, against the "
+                       "network's x0 per volume (inference timed in) through mh3d_solve_batched_warm"}
     line = {
         "metric": "reconstructions/sec to rel. residual 1e-4 with learned warm start", "value": len(t1) / sum(t1),
         "unit": UNIT, "n_gpus": 1, "steps": len(t1), "warmup": 3, "ms_per_step": 1e3 * float(np.mean(t1)),
@@ -707,6 +747,7 @@ def bench_learned(args):
                        "fallback_rate": fb / len(t1),
                        "median_initial_rel_res": float(np.median(r0))},
         "speedup": {"mean": m, "ci95": [m - half, m + half], "per": "volume, zero-start time / warm-start time"},
+        "batched": batched,
         "train": {"loss_per_epoch": hist, "data_s": t_gen, "fit_s": t_fit},
     }
     print(json.dumps(line), flush=True)
@@ -795,6 +836,44 @@ def bench_mhad(args):
     ratio = np.array(t0) / np.array(t1)
     m, sd = float(ratio.mean()), float(ratio.std(ddof=1)) if len(ratio) > 1 else 0.0
     half = 1.972 * sd / math.sqrt(len(ratio))
+
+    # the learned + batched form: the first test volumes in one batched call,
+    # zero start (mh3d_solve_batched) against the network's x0 per volume
+    # (inference included) through mh3d_solve_batched_warm
+    from paper_2503_13802_gb300 import mh3d_solve_batched
+
+    nb = min(args.batch_n, len(tests))
+    bplans = [Plan(wl.n, voxel_mm=wl.voxel_mm, ds_factor=wl.ds_factor, k_min=wl.k_min, k_max=wl.k_max,
+                   sensitivity=b) for _ in range(nb)]
+    bd = tests[:nb]
+    bx = [torch.empty(plan.shape, dtype=torch.float32, device=dev) for _ in range(nb)]
+    bx0 = [torch.empty(plan.shape, dtype=torch.float32, device=dev) for _ in range(nb)]
+    bopts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter, x0_fallback=True)
+
+    def batch_zero():
+        return mh3d_solve_batched(bplans, bd, bopts, bx)
+
+    def batch_warm():
+        for i in range(nb):
+            ws.predict(bd[i], bx0[i])
+        return mh3d_solve_batched(bplans, bd, bopts, bx, x0s=bx0)
+
+    for _ in range(2):   # warm-up (graph capture)
+        batch_zero()
+        batch_warm()
+    tb0, tb1, ib0, ib1 = [], [], [], []
+    for _ in range(3):
+        inf0, s0 = timed(batch_zero)
+        inf1, s1 = timed(batch_warm)
+        tb0.append(s0)
+        tb1.append(s1)
+        ib0.extend(v["iters"] for v in inf0)
+        ib1.extend(v["iters"] for v in inf1)
+    batched = {"volumes": nb, "zero_start_value": nb / float(np.mean(tb0)), "warm_start_value": nb / float(np.mean(tb1)),
+               "speedup": float(np.mean(tb0)) / float(np.mean(tb1)), "zero_mean_iters": float(np.mean(ib0)),
+               "warm_mean_iters": float(np.mean(ib1)),
+               "what": "one mh3d_solve_batched call over the first test volumes, zero start, against the "
+                       "network's x0 per volume (inference timed in) through mh3d_solve_batched_warm"}
     line = {
         "metric": "reconstructions/sec to rel. residual 1e-4 with MHAD warm start", "value": len(t1) / sum(t1),
         "unit": UNIT, "n_gpus": 1, "steps": len(t1), "warmup": 3, "ms_per_step": 1e3 * float(np.mean(t1)),

@@ -303,6 +303,29 @@ mh3d_status mh3d_general_set_psf(mh3d_plan plan, const float* h_host);
 mh3d_status mh3d_general_forward(mh3d_plan plan, const float* rho, const float* bvec, void* d, void* stream);
 mh3d_status mh3d_general_adjoint(mh3d_plan plan, const void* d, const float* bvec, float* out, void* stream);
 
+/* The regularised reconstruction of Sec. 4.3 on the general model:
+ *   min ||A rho - d||^2 + lambda ||rho||^2,  A the forward of
+ *   mh3d_general_forward with the plan's PSF spectra and bvec,
+ * by conjugate gradients on (A^T A + lambda I) rho = A^T d (Hestenes-Stiefel).
+ * Each iteration applies A (into the plan's portrait buffer, allocated on
+ * first use) and A^T, two float-pair inner products (as mh3d_dot) and the
+ * vector updates; the scalars are FP64 on the host, which synchronises
+ * `stream` three times per iteration.
+ *   d_dev: portraits (device, complex64 K*nz*ny*(nx/s)); bvec_dev: as for
+ *   mh3d_general_forward (NULL = b = (1, 0, 0)); rho_dev: N floats (device,
+ *   written).  opts: solver 0, reg_kind 0, lambda absolute and > 0
+ *   (lambda_relative 0: the general model has no Fourier-block norm),
+ *   rel_tol (stopping rule ||r_k|| <= rel_tol ||A^T d||, recurrence
+ *   residual), max_iter, fixed_iters and x0_dev (device, or NULL) as for
+ *   mh3d_solve; other fields ignored.  info (may be NULL): iterations,
+ *   recurrence and recomputed true relative residuals, history (if its
+ *   pointer is set, max_iter + 1 doubles), status.
+ *   Errors: MH3D_ERR_INVALID_ARG (null pointers, unsupported options, no PSF
+ *   set), MH3D_ERR_NOT_CONVERGED (rho_dev holds the last iterate),
+ *   MH3D_ERR_NONFINITE, MH3D_ERR_CUDA. */
+mh3d_status mh3d_general_solve(mh3d_plan plan, const void* d_dev, const float* bvec_dev,
+                               const mh3d_solve_opts* opts, float* rho_dev, mh3d_solve_info* info, void* stream);
+
 /* Tile autotuning: times the fused normal operator (the CG loop's kernels)
  * for each transverse-pass tile width (16 and 8 columns) on the plan's
  * workspace and keeps the fastest for this plan.  The choice is remembered

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "solve_internal.h"
 
@@ -981,11 +982,156 @@ static mh3d_status apg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o,
     return MH3D_OK;
 }
 
+// ---------------------------------------------------------------------------
+// CG on the general three-component model (Sec. 3.2, Eq. matrixModel; the
+// solver of Sec. 4.3 applies to any A): (A^T A + lambda I) x = A^T d with A
+// the forward of mh3d_general_forward.  Classic CG (Hestenes-Stiefel) driven
+// from the host: the normal operator goes through the plan's portrait buffer
+// (A p, then A^T), the dot products are the solvers' float-pair sums, the
+// scalars are FP64 on the host, and the vector updates run on the device.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_axpy(float* __restrict__ y, const float* __restrict__ x, float a, long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fmaf(a, x[i], y[i]);
+}
+// x += a p; r -= a q
+__global__ void __launch_bounds__(256) k_cg_xr(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
+                                               const float* __restrict__ q, float a, long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fmaf(a, p[i], x[i]);
+        r[i] = fmaf(-a, q[i], r[i]);
+    }
+}
+// p = r + beta p
+__global__ void __launch_bounds__(256) k_xpby(float* __restrict__ p, const float* __restrict__ r, float beta,
+                                              long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        p[i] = fmaf(beta, p[i], r[i]);
+}
+// d = b - a (elementwise), for the residual
+__global__ void __launch_bounds__(256) k_sub(float* __restrict__ d, const float* __restrict__ b,
+                                             const float* __restrict__ a, long long N)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        d[i] = b[i] - a[i];
+}
+
+// a^T b on the device, returned to the host (synchronises `st`).
+static mh3d_status dot_host(Plan& P, const float* a, const float* b, cudaStream_t st, double* out)
+{
+    const int nb = (int)std::min<long long>(update_blocks(P.N), (long long)P.w.red_cap);
+    k_dot<<<nb, 256, 0, st>>>(a, b, P.N, part_slot(P, kPartRES), ticket(P, kTkRES), scal(P, kRES));
+    MH3D_CK(P, cudaGetLastError());
+    MH3D_CK(P, cudaMemcpyAsync(P.w.red_host, scal(P, kRES), sizeof(double), cudaMemcpyDeviceToHost, st));
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    *out = P.w.red_host[0];
+    return MH3D_OK;
+}
+
 }  // namespace mh3d
 
 using namespace mh3d;
 
 struct mh3d_plan_s : public Plan {};
+
+namespace mh3d {
+
+// q = (A^T A + lambda I) p for the general model.
+static mh3d_status general_normal(Plan& P, const float* p, const float* bvec, double lam, float* q, cudaStream_t st)
+{
+    mh3d_plan h = static_cast<mh3d_plan>(&P);
+    mh3d_status s = mh3d_general_forward(h, p, bvec, P.w.portrait, st);
+    if (s == MH3D_OK) s = mh3d_general_adjoint(h, P.w.portrait, bvec, q, st);
+    if (s != MH3D_OK) return s;
+    k_axpy<<<update_blocks(P.N), 256, 0, st>>>(q, p, (float)lam, P.N);
+    MH3D_CK(P, cudaGetLastError());
+    return MH3D_OK;
+}
+
+static mh3d_status general_cg(Plan& P, const void* d, const float* bvec, const mh3d_solve_opts& o, float* rho,
+                              mh3d_solve_info* info, cudaStream_t st)
+{
+    SolveWork& w = P.w;
+    mh3d_status s = ensure_portrait(P);
+    if (s != MH3D_OK) return s;
+    const int nU = update_blocks(P.N);
+    const size_t vb = sizeof(float) * (size_t)P.N;
+    mh3d_plan h = static_cast<mh3d_plan>(&P);
+    MH3D_CK(P, cudaMemsetAsync(ticket(P, 0), 0, kNTk * sizeof(unsigned int), st));
+    if ((s = mh3d_general_adjoint(h, d, bvec, w.rhs, st)) != MH3D_OK) return s;
+    if (o.x0_dev) {
+        MH3D_CK(P, cudaMemcpyAsync(w.x, o.x0_dev, vb, cudaMemcpyDeviceToDevice, st));
+        if ((s = general_normal(P, w.x, bvec, o.lambda, w.q, st)) != MH3D_OK) return s;
+        k_sub<<<nU, 256, 0, st>>>(w.r, w.rhs, w.q, P.N);
+        MH3D_CK(P, cudaGetLastError());
+    } else {
+        MH3D_CK(P, cudaMemsetAsync(w.x, 0, vb, st));
+        MH3D_CK(P, cudaMemcpyAsync(w.r, w.rhs, vb, cudaMemcpyDeviceToDevice, st));
+    }
+    MH3D_CK(P, cudaMemcpyAsync(w.p, w.r, vb, cudaMemcpyDeviceToDevice, st));
+    double bn = 0.0, rr = 0.0;
+    if ((s = dot_host(P, w.rhs, w.rhs, st, &bn)) != MH3D_OK) return s;
+    if ((s = dot_host(P, w.r, w.r, st, &rr)) != MH3D_OK) return s;
+    std::vector<double> hist;
+    hist.push_back(bn > 0 ? std::sqrt(rr / bn) : 0.0);
+    const double tol2 = o.fixed_iters ? 0.0 : o.rel_tol * o.rel_tol;
+    int it = 0;
+    mh3d_status status = MH3D_OK;
+    while (true) {
+        if (!std::isfinite(rr) || !std::isfinite(bn)) {
+            status = MH3D_ERR_NONFINITE;
+            break;
+        }
+        if (rr == 0.0 || bn == 0.0 || (tol2 > 0.0 && rr <= tol2 * bn)) break;
+        if (it >= o.max_iter) {
+            if (tol2 > 0.0) status = MH3D_ERR_NOT_CONVERGED;
+            break;
+        }
+        if ((s = general_normal(P, w.p, bvec, o.lambda, w.q, st)) != MH3D_OK) return s;
+        double pq = 0.0;
+        if ((s = dot_host(P, w.p, w.q, st, &pq)) != MH3D_OK) return s;
+        if (!(pq > 0.0) || !std::isfinite(pq)) {
+            status = MH3D_ERR_NONFINITE;
+            break;
+        }
+        const double alpha = rr / pq;
+        k_cg_xr<<<nU, 256, 0, st>>>(w.x, w.r, w.p, w.q, (float)alpha, P.N);
+        MH3D_CK(P, cudaGetLastError());
+        double rr_new = 0.0;
+        if ((s = dot_host(P, w.r, w.r, st, &rr_new)) != MH3D_OK) return s;
+        k_xpby<<<nU, 256, 0, st>>>(w.p, w.r, (float)(rr_new / rr), P.N);
+        MH3D_CK(P, cudaGetLastError());
+        rr = rr_new;
+        ++it;
+        hist.push_back(bn > 0 ? std::sqrt(rr / bn) : 0.0);
+    }
+    // true residual ||A^T d - (A^T A + lambda I) x|| / ||A^T d||
+    if ((s = general_normal(P, w.x, bvec, o.lambda, w.q, st)) != MH3D_OK) return s;
+    k_sub<<<nU, 256, 0, st>>>(w.q, w.rhs, w.q, P.N);
+    MH3D_CK(P, cudaGetLastError());
+    double res2 = 0.0;
+    if ((s = dot_host(P, w.q, w.q, st, &res2)) != MH3D_OK) return s;
+    MH3D_CK(P, cudaMemcpyAsync(rho, w.x, vb, cudaMemcpyDeviceToDevice, st));
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    if (info) {
+        info->iters = it;
+        info->rel_res_recurrence = hist.back();
+        info->rel_res_true = bn > 0 ? std::sqrt(res2 / bn) : 0.0;
+        info->status = status;
+        info->x0_rejected = 0;
+        info->tau = 0.0;
+        if (info->history)
+            for (size_t i = 0; i < hist.size() && (int)i <= o.max_iter; ++i) info->history[i] = hist[i];
+    }
+    if (status == MH3D_ERR_NOT_CONVERGED) P.err = "max_iter reached before rel_tol";
+    if (status == MH3D_ERR_NONFINITE) P.err = "non-finite value in a reduction of the general-model CG";
+    return status;
+}
+
+}  // namespace mh3d
 
 extern "C" {
 
@@ -1014,6 +1160,28 @@ mh3d_status mh3d_solve(mh3d_plan P, const void* d, const mh3d_solve_opts* o, flo
     }
     if (o->solver == 1) return apg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
     return cg_solve(*P, (const float2*)d, *o, rho, info, (cudaStream_t)stream);
+}
+
+mh3d_status mh3d_general_solve(mh3d_plan P, const void* d, const float* bvec, const mh3d_solve_opts* o, float* rho,
+                               mh3d_solve_info* info, void* stream)
+{
+    if (!P) return MH3D_ERR_INVALID_ARG;
+    if (!d || !o || !rho) {
+        P->err = "mh3d_general_solve: null pointer";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    if (!(o->lambda > 0) || !std::isfinite(o->lambda) || o->lambda_relative || o->solver != 0 || o->reg_kind != 0 ||
+        o->max_iter < 1 || o->max_iter > 1000000 || !(o->rel_tol >= 0)) {
+        P->err = "mh3d_general_solve: needs CG (solver 0), R = I (reg_kind 0), an absolute lambda > 0, "
+                 "1 <= max_iter <= 1e6 and rel_tol >= 0";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    if (!P->gen_H) {
+        P->err = "mh3d_general_solve: no PSF spectra (call mh3d_general_set_psf)";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    P->err.clear();
+    return general_cg(*P, d, bvec, *o, rho, info, (cudaStream_t)stream);
 }
 
 mh3d_status mh3d_dot(mh3d_plan P, const float* a, const float* b, long long n, double* result, void* stream)

@@ -59,7 +59,7 @@ EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoin
            "mh3d_solve_host", "mh3d_solve_batched", "mh3d_forward_noalloc", "mh3d_operator_norm2", "mh3d_last_error",
            "mh3d_plan_workspace_bytes", "mh3d_version", "mh3d_plan_autotune", "mh3d_plan_spectra", "mh3d_mhad",
            "mh3d_mhad_warm_start", "mh3d_estimate_phase", "mh3d_general_set_psf", "mh3d_general_forward",
-           "mh3d_general_adjoint", "mh3d_dot", "mh3d_solve_batched_warm"]
+           "mh3d_general_adjoint", "mh3d_dot", "mh3d_solve_batched_warm", "mh3d_general_solve"]
 
 
 def library_path() -> str:
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
     lib.mh3d_general_forward.argtypes = [P, P, P, P, P]
     lib.mh3d_general_adjoint.argtypes = [P, P, P, P, P]
     lib.mh3d_dot.argtypes = [P, P, P, ctypes.c_longlong, POINTER(c_double), P]
+    lib.mh3d_general_solve.argtypes = [P, P, P, POINTER(mh3d_solve_opts), P, POINTER(mh3d_solve_info), P]
     lib.mh3d_solve_batched_warm.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(mh3d_solve_opts),
                                             POINTER(c_void_p), POINTER(c_void_p), POINTER(mh3d_solve_info), P]
     lib.mh3d_last_error.argtypes = [P]
@@ -267,6 +268,28 @@ def mh3d_general_adjoint(plan: Plan, d, out, bvec=None, stream=None):
     _check(plan.handle, lib.mh3d_general_adjoint(plan.handle, c_void_p(p_d), c_void_p(p_b), c_void_p(p_o),
                                                  c_void_p(_stream_ptr(stream))))
     return out
+
+
+def mh3d_general_solve(plan: Plan, d, opts: mh3d_solve_opts, rho, bvec=None, stream=None,
+                       allow_not_converged: bool = True):
+    """CG on (A^T A + lambda I) rho = A^T d for the general model (absolute
+    lambda).  Returns a dict with iters, residuals, status and history."""
+    import torch
+
+    lib = load()
+    n_d = plan.K * plan.portrait_shape[1] * plan.portrait_shape[2] * plan.portrait_shape[3]
+    p_d = _dev_ptr(d, torch.complex64, n_d, "d")
+    p_r = _dev_ptr(rho, torch.float32, plan.N, "rho")
+    p_b = _bvec_ptr(plan, bvec)
+    if opts.x0_dev:
+        _dev_ptr(opts._x0_ref, torch.float32, plan.N, "x0")
+    info, hist = _info(opts.max_iter + 1)
+    st = lib.mh3d_general_solve(plan.handle, c_void_p(p_d), c_void_p(p_b), ctypes.byref(opts), c_void_p(p_r),
+                                ctypes.byref(info), c_void_p(_stream_ptr(stream)))
+    if st != MH3D_OK and not (allow_not_converged and st == MH3D_ERR_NOT_CONVERGED):
+        _check(plan.handle, st)
+    return {"iters": info.iters, "rel_res_recurrence": info.rel_res_recurrence, "rel_res_true": info.rel_res_true,
+            "status": info.status, "history": [hist[i] for i in range(min(info.iters, opts.max_iter) + 1)]}
 
 
 def make_opts(lam: float = 1e-3, reg_kind: int = 0, alpha: float = 0.0, shell: int = 2, solver: int = 0,

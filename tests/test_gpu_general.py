@@ -78,3 +78,96 @@ def test_general_argument_checks():
     with pytest.raises(MH3DError) as e:
         mh3d_general_set_psf(padded, np.zeros(padded.K * 3 * padded.N, dtype=np.float32))
     assert "INVALID_ARG" in str(e.value)
+
+
+def _lam_for(g, H, bvec, rel=1e-2):
+    """An absolute lambda of rel times ||A||_2^2 (power iteration with the
+    oracle's general normal operator, lambda = 0)."""
+    v = np.random.default_rng(3).standard_normal(g.shape)
+    lam = 0.0
+    for _ in range(60):
+        w = vm.general_normal_apply(g, v, 0.0, bvec, H)
+        lam = float(np.vdot(v, w) / np.vdot(v, v))
+        v = w / np.linalg.norm(w)
+    return rel * lam
+
+
+@pytest.mark.parametrize("name", ["s2_r1_vector_b", "s2_r0_vector_b"])
+def test_general_solve_matches_oracle_cg(name):
+    """CG on the general model (Sec. 4.3 with A of Eq. matrixModel), through
+    mh3d_general_solve, against the oracle's general CG (pinned against the
+    dense FP64 solve of the normal equations), with the comparisons of
+    reading r2 (FP32 and FP64 CG follow different rounding paths): (a) after
+    a fixed 10 iterations from zero, the residual histories agreeing while
+    far above FP32 resolution; (b) both to a common relative residual of
+    1e-6, against the oracle solved to 1e-11; (c) from a warm start that is
+    the solution, which stops at once."""
+    from paper_2503_13802_gb300 import make_opts, mh3d_general_set_psf, mh3d_general_solve
+
+    c, use_b = CASES[name]
+    theta = _theta(c, 11)
+    g = _geom(c, theta)
+    H = vm.general_psf(g).astype(np.float32)
+    H64 = H.astype(np.float64)
+    plan = _plan(c, theta)
+    mh3d_general_set_psf(plan, H)
+    rng = np.random.default_rng(23)
+    bvec = (0.3 + rng.random((3,) + tuple(g.shape))).astype(np.float32) if use_b else None
+    b64 = None if bvec is None else bvec.astype(np.float64)
+    rho = np.abs(rng.standard_normal(g.shape))
+    d = vm.general_forward(g, rho, b64, H64)
+    d = d + 0.05 * np.abs(d).max() * (rng.standard_normal(d.shape) + 1j * rng.standard_normal(d.shape))
+    lam = _lam_for(g, H64, b64)
+    bt = torch.as_tensor(bvec).cuda().contiguous() if use_b else None
+    dd = torch.as_tensor(d.astype(np.complex64)).cuda().contiguous()
+    x = torch.empty(g.shape, dtype=torch.float32, device="cuda")
+    # (a)
+    xo, it = vm.general_cg(g, d, lam, 10, b64, H64)
+    info = mh3d_general_solve(plan, dd, make_opts(lam=lam, max_iter=10, fixed_iters=True), x, bt)
+    assert info["iters"] == 10 and info["status"] == 0, info
+    assert rel_l2(x.cpu().numpy(), xo) <= 1e-4, rel_l2(x.cpu().numpy(), xo)
+    rhs = vm.general_adjoint(g, d, b64, H64)
+    r = rhs.copy()
+    p = r.copy()
+    hist = [1.0]
+    for _ in range(6):     # the oracle's own recurrence residuals, textbook CG
+        q = vm.general_normal_apply(g, p, lam, b64, H64)
+        a = float(np.vdot(r, r)) / float(np.vdot(p, q))
+        rn = r - a * q
+        p = rn + float(np.vdot(rn, rn)) / float(np.vdot(r, r)) * p
+        r = rn
+        hist.append(float(np.linalg.norm(r) / np.linalg.norm(rhs)))
+    np.testing.assert_allclose(info["history"][:7], hist, rtol=1e-4)
+    # (b)
+    tight, _ = vm.general_cg(g, d, lam, 5000, b64, H64, rel_tol=1e-11)
+    xo6, _ = vm.general_cg(g, d, lam, 5000, b64, H64, rel_tol=1e-6)
+    info = mh3d_general_solve(plan, dd, make_opts(lam=lam, rel_tol=1e-6, max_iter=5000), x, bt)
+    assert info["status"] == 0 and info["rel_res_true"] <= 1e-5, info
+    assert rel_l2(x.cpu().numpy(), tight) <= 1e-4, rel_l2(x.cpu().numpy(), tight)
+    assert rel_l2(x.cpu().numpy(), xo6) <= 1e-4, rel_l2(x.cpu().numpy(), xo6)
+    # (c)
+    x0 = torch.as_tensor(tight.astype(np.float32)).cuda().contiguous()
+    info = mh3d_general_solve(plan, dd, make_opts(lam=lam, rel_tol=1e-4, max_iter=100, x0=x0), x, bt)
+    assert info["status"] == 0 and info["iters"] <= 1, info
+
+
+def test_general_solve_rejects_unsupported_options():
+    from paper_2503_13802_gb300 import MH3DError, make_opts, mh3d_general_set_psf, mh3d_general_solve
+
+    c, _ = CASES["s1_drive_b"]
+    g = _geom(c, None)
+    plan = _plan(c, None)
+    d = torch.zeros(plan.portrait_shape, dtype=torch.complex64, device="cuda")
+    x = torch.empty(plan.shape, dtype=torch.float32, device="cuda")
+    with pytest.raises(MH3DError) as e:          # no PSF yet
+        mh3d_general_solve(plan, d, make_opts(lam=1e-2), x)
+    assert "INVALID_ARG" in str(e.value)
+    mh3d_general_set_psf(plan, vm.general_psf(g).astype(np.float32))
+    for bad in (make_opts(lam=1e-2, lam_relative=True), make_opts(lam=1e-2, solver=1),
+                make_opts(lam=1e-2, reg_kind=1), make_opts(lam=0.0)):
+        with pytest.raises(MH3DError) as e:
+            mh3d_general_solve(plan, d, bad, x)
+        assert "INVALID_ARG" in str(e.value)
+    info = mh3d_general_solve(plan, d, make_opts(lam=1e-2), x)    # zero data: zero at once
+    assert info["status"] == 0 and info["iters"] == 0
+    assert float(torch.abs(x).max()) == 0.0
