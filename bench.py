@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--mode", type=int, default=0, help="0 fused normal operator, 1 explicit A then A^T")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch variants instead of the autotuner's choice")
     ap.add_argument("--batched", action="store_true",
                     help="the 64-volume batched workload (one JSON line of its own)")
     ap.add_argument("--learned", action="store_true",
@@ -186,7 +188,8 @@ def bench_mh3d(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     else:
         torch.cuda.set_device(0)
-    from paper_2503_13802_gb300 import Plan, make_opts, mh3d_adjoint, mh3d_forward, mh3d_solve, mh3d_solve_host
+    from paper_2503_13802_gb300 import (Plan, make_opts, mh3d_adjoint, mh3d_forward, mh3d_plan_autotune,
+                                        mh3d_plan_tuning, mh3d_solve, mh3d_solve_host)
 
     wl = W.WORKLOADS[args.workload]
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -206,6 +209,11 @@ def bench_mh3d(args):
     x = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
     opts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter,
                      fixed_iters=wl.fixed_iters, normal_mode=args.mode)
+    # the library's autotuner picks the launch variants for this size (set-up, untimed)
+    tuning = None
+    if not args.no_autotune:
+        mh3d_plan_autotune(plan)
+        tuning = mh3d_plan_tuning(plan)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
 
@@ -373,7 +381,7 @@ def bench_mh3d(args):
                    "snr_db": wl.snr_db, "lambda": wl.lam, "rel_tol": wl.rel_tol,
                    "normal_mode": "fused Fourier-block A^T A" if args.mode == 0 else "explicit A then A^T",
                    "cg_iters": it_med, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}", "autotune": tuning},
         "roofline": {"kernel": ("CG iteration = graph body (k_tpass_ct T_y + CG update, k_zxnrm_ct T_z + "
                                 "drive-axis normal pass)" if fused_zx(wl) else
                                 "CG iteration = graph body (k_tpass_ct T_y + CG update, k_tpass_ct T_z, k_xnrm_ct)")
@@ -510,12 +518,14 @@ def bench_batched(args):
     mh3d_solve are reported beside it."""
     import torch
 
-    from paper_2503_13802_gb300 import Plan, make_opts, mh3d_forward, mh3d_solve, mh3d_solve_batched
+    from paper_2503_13802_gb300 import (Plan, make_opts, mh3d_forward, mh3d_plan_autotune, mh3d_plan_tuning,
+                                        mh3d_solve, mh3d_solve_batched)
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     wl = W.WORKLOADS[WORKLOAD]
     sizes = W.batch_sizes(64, 777)
+    tuning = {}
     plans, ds, xs = [], [], []
     for i, n in enumerate(sizes):
         rho = W.phantom(n, (1.0, 1.0, 1.0), 1000 + i, wl.n_blobs, wl.n_lines)
@@ -528,6 +538,10 @@ def bench_batched(args):
         plans.append(pl)
         ds.append((d + math.sqrt(sig2) * noise).contiguous())
         xs.append(torch.empty(pl.shape, dtype=torch.float32, device=dev))
+        if not args.no_autotune:
+            # the autotuner times each size class once; later plans of a class take its choice
+            mh3d_plan_autotune(pl)
+            tuning["x".join(map(str, n))] = mh3d_plan_tuning(pl)
     opts = make_opts(lam=wl.lam, lam_relative=True, rel_tol=wl.rel_tol, max_iter=wl.max_iter)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -573,7 +587,8 @@ def bench_batched(args):
                    "count_per_class": [sizes.count(c) for c in W.BATCH_SIZE_CLASSES],
                    "voxels_total": int(sum(p.N for p in plans)), "harmonics": [wl.k_min, wl.k_max],
                    "ds_factor": wl.ds_factor, "snr_db": wl.snr_db, "lambda": wl.lam, "rel_tol": wl.rel_tol,
-                   "launch": "one CUDA graph, one branch per volume", "l2": "flushed between steps (256 MB write)"},
+                   "launch": "one CUDA graph, one branch per volume", "l2": "flushed between steps (256 MB write)",
+                   "autotune": tuning or None},
         "cg_iters": {"min": min(iters), "max": max(iters), "mean": statistics.mean(iters)},
         "worst_rel_res_true": worst,
         "one_after_another": {"value": len(plans) / statistics.mean(seq), "unit": UNIT,

@@ -326,13 +326,39 @@ mh3d_status mh3d_general_adjoint(mh3d_plan plan, const void* d, const float* bve
 mh3d_status mh3d_general_solve(mh3d_plan plan, const void* d_dev, const float* bvec_dev,
                                const mh3d_solve_opts* opts, float* rho_dev, mh3d_solve_info* info, void* stream);
 
-/* Tile autotuning: times the fused normal operator (the CG loop's kernels)
- * for each transverse-pass tile width (16 and 8 columns) on the plan's
- * workspace and keeps the fastest for this plan.  The choice is remembered
- * for the process per (grid, ds_factor, K, weighted or not), so later plans
- * of a tuned size take it without timing.  Synchronises `stream`; drops the
- * plan's cached graphs.  tpass_cols (may be NULL) receives the width. */
+/* Autotuning (the batching pattern's per-size-class schedule choice; the
+ * paper has no counterpart): times, on the plan's own workspace, the launch
+ * variants of the three operators and keeps the fastest of each --
+ *   the normal operator (the CG loop's kernels): transverse-pass tile width
+ *   (16 or 8 columns) x its radix schedule (the default or the alternative
+ *   one, e.g. 8 x 16 instead of 16 x 8 at length 128) x CTAs per y-slab of
+ *   the fused cluster pass (2 or 4);
+ *   the adjoint's drive-axis part: warp-centric fused with T_z^T, or
+ *   followed by T_z^T, with 1, 2 or 4 warps per row group, or CTA-level;
+ *   the forward's drive-axis part: the cluster pass fusing T_z or the
+ *   warp-centric pass (1, 2 or 4 warps per row group).
+ * The choice applies to this plan and is remembered for the process per
+ * (grid, ds_factor, K, weighted or not), so later plans of a tuned size take
+ * it without timing.  With the environment variable MH3D_TUNE_CACHE set to
+ * a file path the choice is also read from and written to that JSON file
+ * (a JSON object with one size class per line, the layout it writes), so a later
+ * process takes it without timing.
+ * The normal operator is timed back to back (in the CG loop its working
+ * set stays in L2); the adjoint and forward, which a solve runs once on
+ * data not in L2, are timed launch by launch after a write of a temporary
+ * buffer twice the L2 size (allocated and freed by the call).
+ * The radix and path choices change the FP32 rounding path (results agree
+ * within the operators' tolerance, not bit for bit); the tile width alone
+ * does not.  Synchronises `stream`; allocates the plan's portrait buffer
+ * (K*M complex64) if it has none; drops the plan's cached graphs.
+ * tpass_cols (may be NULL) receives the tile width. */
 mh3d_status mh3d_plan_autotune(mh3d_plan plan, void* stream, int* tpass_cols);
+
+/* The plan's current launch choices as a JSON object (the fields the
+ * autotuner sets: tpass_cols, tpass_radix, zx_c, adj_path, xw_ks, fwd_path,
+ * xw_ks_fwd; 0 = the library's default) written into buf (host, buflen
+ * bytes, NUL-terminated).  MH3D_ERR_INVALID_ARG if buf is too small. */
+mh3d_status mh3d_plan_tuning(mh3d_plan plan, char* buf, int buflen);
 
 /* d_dev = A rho_dev like mh3d_forward, for callers that cannot allocate
  * device memory (a fixed device-memory budget owned by another framework's

@@ -256,6 +256,8 @@ TArgs tpass_args(const Plan& P, int axis /*1 = y, 2 = z*/, const float* in, floa
     a.mult = mult;
     a.nx = P.nx;
     a.cols = P.tile.tpass_cols;
+    a.radix_alt = P.tile.tpass_radix;
+    if (const char* e = std::getenv("MH3D_TPASS_RADIX")) a.radix_alt = (e[0] == '1') ? 1 : 0;   // A/B checks
     a.vec2 = (P.nx % 2 == 0) ? 1 : 0;
     a.vec4 = (P.nx % 4 == 0 && ((uintptr_t)P.sens % 16) == 0) ? 1 : 0;
     a.status = P.w.flags ? P.w.flags + 3 : nullptr;
@@ -309,6 +311,7 @@ XArgs xpass_args(const Plan& P)
     a.reg.ny = P.ny;
     a.reg.nz = P.nz;
     a.status = P.w.flags ? P.w.flags + 3 : nullptr;
+    a.ks = P.tile.xw_ks;
     return a;
 }
 
@@ -334,7 +337,8 @@ cudaError_t launch_forward(const Plan& P, const float* rho, float2* d, float* t1
     XArgs xw = xpass_args(P);
     xw.vin = t2;
     xw.dout = d;
-    if (xw_available(xw, true)) {
+    xw.ks = P.tile.xw_ks_fwd;
+    if (xw_available(xw, true, P.tile.fwd_path == 2)) {
         // T_z, then the warp-centric drive-axis forward
         TArgs tz = tpass_args(P, 2, t1, t2, P.Zhat);
         if ((e = run_tpass(tz, tpass_outer(P, 2), st)) != cudaSuccess) return e;
@@ -349,6 +353,7 @@ cudaError_t launch_forward(const Plan& P, const float* rho, float2* d, float* t1
         z.muz = P.Zhat;
         z.ny = P.ny;
         z.nz = P.nz;
+        z.C = P.tile.zx_c;
         return run_zxfwd_ct(z, t1, st);
     }
     TArgs tz = tpass_args(P, 2, t1, t2, P.Zhat);
@@ -365,10 +370,11 @@ cudaError_t launch_adjoint(const Plan& P, const float2* d, float* rho, float* t1
     XArgs xw = xpass_args(P);
     xw.din = d;
     xw.vout = t1;
-    const bool warp = xw_available(xw, false);
+    // the plan's tuned path (adj_path: 1 warp fused, 2 warp then T_z^T, 3 CTA-level; 0 the default)
+    const bool warp = P.tile.adj_path != 3 && xw_available(xw, false);
     const bool fused = !warp && ct_xzadj_available(P.nx, P.nz, P.s) && ((uintptr_t)d & 15u) == 0 &&
                        ((uintptr_t)t2 & 15u) == 0 && P.mx % 2 == 0 && P.M % 2 == 0;
-    if (warp && xzw_available(xw, P.nz) && ((uintptr_t)t2 & 15u) == 0) {
+    if (warp && P.tile.adj_path != 2 && xzw_available(xw, P.nz) && ((uintptr_t)t2 & 15u) == 0) {
         // the warp-centric drive-axis adjoint and T_z^T in one launch (a
         // cluster of two CTAs per y-slab)
         ZXArgs z;
@@ -377,6 +383,7 @@ cudaError_t launch_adjoint(const Plan& P, const float2* d, float* rho, float* t1
         z.muz = P.Zhat_adj;
         z.ny = P.ny;
         z.nz = P.nz;
+        z.C = P.tile.zx_c;
         if ((e = run_xzadj_w(z, t2, st)) != cudaSuccess) return e;
     } else if (warp) {
         // the warp-centric drive-axis adjoint, then T_z^T
@@ -392,6 +399,7 @@ cudaError_t launch_adjoint(const Plan& P, const float2* d, float* rho, float* t1
         z.muz = P.Zhat_adj;
         z.ny = P.ny;
         z.nz = P.nz;
+        z.C = P.tile.zx_c;
         if ((e = run_xzadj_ct(z, t2, st)) != cudaSuccess) return e;
     } else {
         XArgs x = xpass_args(P);
@@ -460,6 +468,7 @@ cudaError_t launch_normal(const Plan& P, int mode, const RegArgs& reg, const flo
         z.muz = P.Znorm;
         z.ny = P.ny;
         z.nz = P.nz;
+        z.C = P.tile.zx_c;
         if (zx_warp) return run_zxnrm_w(z, t1, st, P.w.shared_sms);
         return run_zxnrm_ct(z, t1, st, P.w.shared_sms);
     }

@@ -39,6 +39,14 @@ struct TileChoice {
     int xpass_pairs = 16;         // row pairs per X-pass CTA
     int xpass_kgroup = 4;         // harmonics transformed together in the X pass
     int threads = 256;
+    // chosen by mh3d_plan_autotune (0 = the library's default; environment
+    // switches of the same name still take precedence for A/B checks)
+    int tpass_radix = 0;          // T pass schedule: 0 the default, 1 the alternative (n = 64: 4x16, 128: 8x16)
+    int zx_c = 0;                 // CTAs per y-slab of the cluster passes (2 or 4)
+    int xw_ks = 0;                // warps per row group of the warp-centric adjoint (1, 2 or 4)
+    int adj_path = 0;             // adjoint's drive-axis part: 1 warp + T_z^T fused, 2 warp then T_z^T, 3 CTA-level
+    int fwd_path = 0;             // forward's drive-axis part: 1 cluster pass fusing T_z, 2 warp-centric
+    int xw_ks_fwd = 0;            // warps per row group of the warp-centric forward
 };
 
 // Solver workspace (device), sized at plan time.

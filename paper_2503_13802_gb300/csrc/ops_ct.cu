@@ -49,8 +49,11 @@ TDesc tdesc(int P)
     return TDesc{};
 }
 
-TDesc tpass_desc(int n, int P)
+// alt = 1: the alternative schedule the autotuner may pick (n = 64, 128).
+TDesc tpass_desc(int n, int P, int alt = 0)
 {
+    if (alt == 1 && n == 64) return tdesc<RList<4, 16>>(P);
+    if (alt == 1 && n == 128) return tdesc<RList<8, 16>>(P);
     switch (n) {
         case 32: return tdesc<RList<4, 8>>(P);
         case 64: return tdesc<RList<8, 8>>(P);
@@ -313,11 +316,12 @@ cudaError_t ct_set_attributes(int optin)
     tensor_map_encoder();
     static const int tn[] = {32, 64, 96, 128, 192, 256};
     for (int n : tn)
-        for (int P : {4, 8}) {
-            const TDesc d = tpass_desc(n, P);
-            cudaError_t e = opt_in(d.fn, d.smem, optin);
-            if (e != cudaSuccess) return e;
-        }
+        for (int P : {4, 8})
+            for (int alt : {0, 1}) {
+                const TDesc d = tpass_desc(n, P, alt);
+                cudaError_t e = opt_in(d.fn, d.smem, optin);
+                if (e != cudaSuccess) return e;
+            }
     static const int zx[][2] = {{128, 64}, {64, 64}, {96, 64}};
     for (const auto& p : zx)
         for (int which = 0; which < 4; ++which)
@@ -362,7 +366,7 @@ cudaError_t run_tpass_ct(const TArgs& a0, int nouter, cudaStream_t st)
                     enc(kTmS, a.svec) && enc(kTmP, a.pvec) && enc(kTmQ, a.qdir) && enc(kTmX, a.xvec) &&
                     enc(kTmOut, a.epilogue ? a.qvec : a.out) && enc(kTmPin, a.pin);
     if (!ok) return cudaErrorInvalidValue;
-    const TDesc d = tpass_desc(a.n, a.cols / 2);
+    const TDesc d = tpass_desc(a.n, a.cols / 2, a.radix_alt);
     dim3 grid((a.nx + a.cols - 1) / a.cols, nouter);
     return launch_pdl(d.fn, grid, d.threads, d.smem, st, a);
 }
@@ -467,7 +471,9 @@ bool ct_xzadj_available(int nx, int nz, int s) { return zx_enabled(2, nx, nz, s)
 static cudaError_t run_zx(ZXArgs& a, const void* zvol, int which, cudaStream_t st)
 {
     const int nx = a.x.nx;
-    const ZXDesc d = zx_desc(which, nx, a.nz, a.x.s, zx_cluster());
+    const char* ev = std::getenv("MH3D_ZX_CLUSTER");
+    const int C = (ev && ev[0]) ? zx_cluster() : (a.C == 4 ? 4 : 2);
+    const ZXDesc d = zx_desc(which, nx, a.nz, a.x.s, C);
     if (!d.fn || nx % (4 * d.C) != 0 || a.nz % (2 * d.C) != 0 || !al16(zvol)) return cudaErrorInvalidValue;
     if (!encode_tile_map(&a.tz, zvol, nx, a.ny, a.nz, 2, a.nz, nx / d.C)) return cudaErrorInvalidValue;
     d.fn<<<d.C * a.ny, d.threads, d.smem, st>>>(a);

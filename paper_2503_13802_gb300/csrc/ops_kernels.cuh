@@ -79,6 +79,7 @@ struct TArgs {
     int vec4 = 0;                    // nx % 4 == 0 and every vector 16-byte aligned: float4 access
     int* status = nullptr;           // device status word (bounded waits record timeouts here)
     unsigned debug_extra_tx = 0;     // fault test only: bytes the tile barrier waits for that never arrive
+    int radix_alt = 0;               // 1: the alternative radix schedule (where instantiated)
     // CG fusions
     int pupdate = 0;                 // loader: 1 = p = r + beta p (written back), value = b p;
                                      //         2 = p = r + beta p, q = s + beta q, x += alpha p,
@@ -135,6 +136,7 @@ struct XArgs {
     CgCtl cg{};
     int cg_active = 0;
     int* status = nullptr;           // device status word for bounded-wait timeouts
+    int ks = 0;                      // warp-centric passes: warps per row group (0: default)
 };
 
 // The y-slab cluster passes (ops_ct.cuh: k_zxnrm_ct, k_zxfwd_ct,
@@ -145,6 +147,7 @@ struct ZXArgs {
     const float2* twz = nullptr;     // W_nz^t
     const float2* muz = nullptr;     // z-axis normal multiplier [nz]
     int ny = 1, nz = 1;
+    int C = 0;                       // CTAs per y-slab (2 or 4; 0: default)
 };
 
 // Shared-memory sizes in bytes.
@@ -196,7 +199,9 @@ cudaError_t run_xnrm_ct(const XArgs& a, cudaStream_t st);
 int xpass_blocks(int rows, int pairs);
 cudaError_t ops_set_attributes();
 // Warp-centric drive-axis passes for n_x = 128, s = 2 (xwarp.cu).
-bool xw_available(const XArgs& a, bool forward);
+// forward: the warp forward's opt-in (MH3D_XWARP_FWD=1 or a plan's tuned
+// choice, `want`); the adjoint's is on by default.
+bool xw_available(const XArgs& a, bool forward, bool want = false);
 cudaError_t xw_set_attributes();
 cudaError_t run_xfwd_w(const XArgs& a, cudaStream_t st);
 cudaError_t run_xadj_w(const XArgs& a, cudaStream_t st);

@@ -14,6 +14,7 @@
 // (Sec. 4.3), runs the same normal operator with a fixed iteration count.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -815,15 +816,24 @@ static mh3d_status cg_solve_batched(const std::vector<Plan*>& ps, const float2* 
 }
 
 // ---------------------------------------------------------------------------
-// Tile autotuning
+// Autotuning
 // ---------------------------------------------------------------------------
-// Times the fused normal operator (the kernels of the CG loop) for each
-// transverse-pass tile width on the plan's own workspace and keeps the
-// fastest; the choice is remembered per (grid, s, K, weighting) for the
-// process, so plans of an already tuned size take it without timing.
+// Times, on the plan's own workspace, the launch variants of the three
+// operators and keeps the fastest of each, per size class (grid, s, K,
+// weighted or not):
+//   1. the normal operator (the CG loop's kernels): T-pass tile width (16 or
+//      8 columns) x T-pass radix schedule (default or the alternative, where
+//      instantiated) x CTAs per y-slab of the cluster pass (2 or 4);
+//   2. the adjoint's drive-axis part: warp-centric fused with T_z^T, or then
+//      T_z^T, with 1, 2 or 4 warps per row group, or the CTA-level pass;
+//   3. the forward's drive-axis part: the cluster pass fusing T_z, or the
+//      warp-centric pass with 1, 2 or 4 warps per row group.
+// The choice is remembered for the process, and with MH3D_TUNE_CACHE set to
+// a file path it is read from and written to that JSON file, so a later
+// process takes it without timing.
 namespace {
 std::mutex g_tune_mu;
-std::vector<std::pair<std::vector<long long>, int>> g_tuned;
+std::vector<std::pair<std::string, TileChoice>> g_tuned;
 }  // namespace
 
 static void drop_graphs(Plan& P)
@@ -835,65 +845,272 @@ static void drop_graphs(Plan& P)
     batch_forget(P);
 }
 
-static mh3d_status autotune(Plan& P, cudaStream_t st, int* chosen)
+static std::string tune_key(const Plan& P)
 {
-    const std::vector<long long> key = {P.nx, P.ny, P.nz, P.s, P.K, P.sens ? 1 : 0};
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        for (const auto& e : g_tuned)
-            if (e.first == key) {
-                if (P.tile.tpass_cols != e.second) {
-                    P.tile.tpass_cols = e.second;
-                    drop_graphs(P);
-                }
-                *chosen = e.second;
-                return MH3D_OK;
-            }
+    char b[96];
+    std::snprintf(b, sizeof b, "%dx%dx%d/s%d/K%d/b%d", P.nx, P.ny, P.nz, P.s, P.K, P.sens ? 1 : 0);
+    return b;
+}
+
+static std::string tile_json(const TileChoice& t)
+{
+    char b[256];
+    std::snprintf(b, sizeof b,
+                  "{\"tpass_cols\": %d, \"tpass_radix\": %d, \"zx_c\": %d, \"adj_path\": %d, \"xw_ks\": %d, "
+                  "\"fwd_path\": %d, \"xw_ks_fwd\": %d}",
+                  t.tpass_cols, t.tpass_radix, t.zx_c, t.adj_path, t.xw_ks, t.fwd_path, t.xw_ks_fwd);
+    return b;
+}
+
+// The integer after "name": in obj, or false.
+static bool json_int(const std::string& obj, const char* name, int* v)
+{
+    const std::string k = std::string("\"") + name + "\":";
+    const size_t i = obj.find(k);
+    return i != std::string::npos && std::sscanf(obj.c_str() + i + k.size(), "%d", v) == 1;
+}
+
+// The cache file's entries: one line per key, "<key>": {<choices>}.
+static std::vector<std::pair<std::string, TileChoice>> cache_read(const char* path)
+{
+    std::vector<std::pair<std::string, TileChoice>> out;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return out;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        const std::string l(line);
+        const size_t q0 = l.find('"'), q1 = (q0 == std::string::npos) ? q0 : l.find('"', q0 + 1);
+        const size_t b0 = l.find('{', q1 == std::string::npos ? 0 : q1);
+        if (q0 == std::string::npos || q1 == std::string::npos || b0 == std::string::npos) continue;
+        const std::string key = l.substr(q0 + 1, q1 - q0 - 1), obj = l.substr(b0);
+        TileChoice t;
+        if (json_int(obj, "tpass_cols", &t.tpass_cols) && json_int(obj, "tpass_radix", &t.tpass_radix) &&
+            json_int(obj, "zx_c", &t.zx_c) && json_int(obj, "adj_path", &t.adj_path) &&
+            json_int(obj, "xw_ks", &t.xw_ks) && json_int(obj, "fwd_path", &t.fwd_path) &&
+            json_int(obj, "xw_ks_fwd", &t.xw_ks_fwd) && (t.tpass_cols == 8 || t.tpass_cols == 16))
+            out.push_back({key, t});
     }
+    std::fclose(f);
+    return out;
+}
+
+static void cache_write(const char* path, const std::vector<std::pair<std::string, TileChoice>>& e)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "{\n");
+    for (size_t i = 0; i < e.size(); ++i)
+        std::fprintf(f, "  \"%s\": %s%s\n", e[i].first.c_str(), tile_json(e[i].second).c_str(),
+                     i + 1 < e.size() ? "," : "");
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    std::rename(tmp.c_str(), path);
+}
+
+static void apply_choice(Plan& P, const TileChoice& c)
+{
+    TileChoice& t = P.tile;
+    t.tpass_cols = c.tpass_cols;
+    t.tpass_radix = c.tpass_radix;
+    t.zx_c = c.zx_c;
+    t.adj_path = c.adj_path;
+    t.xw_ks = c.xw_ks;
+    t.fwd_path = c.fwd_path;
+    t.xw_ks_fwd = c.xw_ks_fwd;
+    drop_graphs(P);
+}
+
+// Mean time (us) of one application of operator `which` (0 normal, 1
+// adjoint, 2 forward) over 20 launches after 3 warm-ups.  The normal
+// operator runs back to back, as in the CG loop, whose working set stays in
+// L2; the adjoint and forward run once per solve on data that is not in L2,
+// so with a flush buffer each of their launches is timed alone after the
+// buffer has been written (10 launches).
+static mh3d_status time_op(Plan& P, int which, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float* flush,
+                           size_t flush_n, float* us)
+{
     mh3d_solve_opts o{};
     o.lambda = 1e-3;
     o.lambda_relative = 1;
     const RegArgs reg = reg_args(P, o);
     SolveWork& w = P.w;
+    auto one = [&]() -> cudaError_t {
+        if (which == 0) return launch_normal(P, 0, reg, w.r, w.s, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr, st);
+        if (which == 1) return launch_adjoint(P, w.portrait, w.x, w.t1, w.t2, st);
+        return launch_forward(P, w.r, w.portrait, w.t1, w.t2, st);
+    };
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = one();
+    float total = 0.f;
+    int reps = 20;
+    if (which != 0 && flush) {
+        reps = 10;
+        for (int i = 0; i < reps && e == cudaSuccess; ++i) {
+            e = cudaMemsetAsync(flush, i & 1, sizeof(float) * flush_n, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = one();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            total += ms;
+        }
+    } else {
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int i = 0; i < reps && e == cudaSuccess; ++i) e = one();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
+    }
+    if (e != cudaSuccess) {
+        P.err = std::string("autotune: ") + cudaGetErrorString(e);
+        return MH3D_ERR_CUDA;
+    }
+    *us = 1e3f * total / (float)reps;
+    return MH3D_OK;
+}
+
+static mh3d_status tune_all(Plan& P, cudaStream_t st)
+{
+    mh3d_status s = ensure_portrait(P);
+    if (s != MH3D_OK) return s;
+    SolveWork& w = P.w;
+    MH3D_CK(P, cudaMemsetAsync(w.r, 0, sizeof(float) * P.N, st));
+    MH3D_CK(P, cudaMemsetAsync(w.portrait, 0, sizeof(float2) * (size_t)P.K * P.M, st));
     cudaEvent_t e0, e1;
     MH3D_CK(P, cudaEventCreate(&e0));
     MH3D_CK(P, cudaEventCreate(&e1));
-    MH3D_CK(P, cudaMemsetAsync(w.r, 0, sizeof(float) * P.N, st));
-    const int cand[2] = {16, 8};
-    float best = 1e30f;
-    int pick = P.tile.tpass_cols;
-    for (int c : cand) {
-        P.tile.tpass_cols = c;
-        cudaError_t e = cudaSuccess;
-        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
-            e = launch_normal(P, 0, reg, w.r, w.s, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr, st);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        for (int i = 0; i < 20 && e == cudaSuccess; ++i)
-            e = launch_normal(P, 0, reg, w.r, w.s, w.t1, w.t2, w.portrait, nullptr, nullptr, nullptr, st);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            P.err = std::string("autotune: ") + cudaGetErrorString(e);
-            return MH3D_ERR_CUDA;
+    // a buffer twice the L2 size, written before each timed adjoint and
+    // forward launch (freed at the end; without it those are timed warm)
+    float* flush = nullptr;
+    size_t flush_n = 0;
+    {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
+            l2 > 0) {
+            flush_n = 2 * (size_t)l2 / sizeof(float);
+            if (dev_malloc(&flush, sizeof(float) * flush_n) != cudaSuccess) {
+                cudaGetLastError();
+                flush = nullptr;
+                flush_n = 0;
+            }
         }
-        if (ms < best) {
-            best = ms;
-            pick = c;
+    }
+    const TileChoice keep = P.tile;
+    TileChoice best = P.tile;
+    auto trial = [&](const TileChoice& c, int which, float* us) {
+        apply_choice(P, c);
+        return time_op(P, which, st, e0, e1, flush, flush_n, us);
+    };
+    // 1. the normal operator
+    const bool alt = (P.ny == 64 || P.ny == 128 || P.nz == 64 || P.nz == 128);
+    const bool zx = ct_zxnrm_available(P.nx, P.nz, P.s);
+    float bt = 1e30f;
+    for (int cols : {16, 8})
+        for (int radix = 0; radix <= (alt ? 1 : 0); ++radix)
+            for (int zc : {2, 4}) {
+                if (!zx && zc == 4) continue;
+                TileChoice c = best;
+                c.tpass_cols = cols;
+                c.tpass_radix = radix;
+                c.zx_c = zx ? zc : 0;
+                float us = 0.f;
+                if ((s = trial(c, 0, &us)) != MH3D_OK) break;
+                if (us < bt) {
+                    bt = us;
+                    best.tpass_cols = cols;
+                    best.tpass_radix = radix;
+                    best.zx_c = c.zx_c;
+                }
+            }
+    // 2. the adjoint, 3. the forward
+    XArgs xa = xpass_args(P);
+    const bool warp = s == MH3D_OK && xw_available(xa, false);
+    const bool wfused = warp && xzw_available(xa, P.nz);
+    if (s == MH3D_OK) {
+        std::vector<std::pair<int, int>> cand = {{3, 0}};
+        if (warp)
+            for (int ks : {1, 2, 4}) {
+                if (wfused) cand.push_back({1, ks});
+                cand.push_back({2, ks});
+            }
+        float ba = 1e30f;
+        for (const auto& pk : cand) {
+            TileChoice c = best;
+            c.adj_path = pk.first;
+            c.xw_ks = pk.second;
+            float us = 0.f;
+            if ((s = trial(c, 1, &us)) != MH3D_OK) break;
+            if (us < ba) {
+                ba = us;
+                best.adj_path = pk.first;
+                best.xw_ks = pk.second;
+            }
+        }
+    }
+    if (s == MH3D_OK) {
+        std::vector<std::pair<int, int>> cand = {{1, 0}};
+        if (xw_available(xa, true, true))
+            for (int ks : {1, 2, 4}) cand.push_back({2, ks});
+        float bf = 1e30f;
+        for (const auto& pk : cand) {
+            TileChoice c = best;
+            c.fwd_path = pk.first;
+            c.xw_ks_fwd = pk.second;
+            float us = 0.f;
+            if ((s = trial(c, 2, &us)) != MH3D_OK) break;
+            if (us < bf) {
+                bf = us;
+                best.fwd_path = pk.first;
+                best.xw_ks_fwd = pk.second;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    P.tile.tpass_cols = pick;
-    drop_graphs(P);
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned.push_back({key, pick});
+    if (flush) {
+        cudaStreamSynchronize(st);
+        cudaFree(flush);
     }
-    *chosen = pick;
+    apply_choice(P, s == MH3D_OK ? best : keep);
+    return s;
+}
+
+static mh3d_status autotune(Plan& P, cudaStream_t st, int* chosen)
+{
+    const std::string key = tune_key(P);
+    const char* path = std::getenv("MH3D_TUNE_CACHE");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& e : g_tuned)
+        if (e.first == key) {
+            apply_choice(P, e.second);
+            *chosen = P.tile.tpass_cols;
+            return MH3D_OK;
+        }
+    if (path && path[0])
+        for (const auto& e : cache_read(path))
+            if (e.first == key) {
+                apply_choice(P, e.second);
+                g_tuned.push_back(e);
+                *chosen = P.tile.tpass_cols;
+                return MH3D_OK;
+            }
+    mh3d_status s = tune_all(P, st);
+    if (s != MH3D_OK) return s;
+    g_tuned.push_back({key, P.tile});
+    if (path && path[0]) {
+        auto all = cache_read(path);
+        bool found = false;
+        for (auto& e : all)
+            if (e.first == key) {
+                e.second = P.tile;
+                found = true;
+            }
+        if (!found) all.push_back({key, P.tile});
+        cache_write(path, all);
+    }
+    *chosen = P.tile.tpass_cols;
     return MH3D_OK;
 }
 
@@ -1203,6 +1420,18 @@ mh3d_status mh3d_dot(mh3d_plan P, const float* a, const float* b, long long n, d
     MH3D_CK(*P, cudaMemcpyAsync(P->w.red_host, scal(*P, kRES), sizeof(double), cudaMemcpyDeviceToHost, st));
     MH3D_CK(*P, cudaStreamSynchronize(st));
     *result = P->w.red_host[0];
+    return MH3D_OK;
+}
+
+mh3d_status mh3d_plan_tuning(mh3d_plan P, char* buf, int buflen)
+{
+    if (!P || !buf || buflen < 1) return MH3D_ERR_INVALID_ARG;
+    const std::string j = tile_json(P->tile);
+    if ((int)j.size() + 1 > buflen) {
+        P->err = "mh3d_plan_tuning: buffer too small";
+        return MH3D_ERR_INVALID_ARG;
+    }
+    std::memcpy(buf, j.c_str(), j.size() + 1);
     return MH3D_OK;
 }
 

@@ -29,21 +29,21 @@ bool al(const void* p, uintptr_t m) { return ((uintptr_t)p & (m - 1)) == 0; }
 // CTA-level passes); the forward A = T_y + T_z + warp pass took 34.4 us
 // against 30.2 us with the cluster pass that fuses T_z, so the warp
 // forward is opt-in (MH3D_XWARP_FWD=1).  MH3D_GENERIC=1 turns both off.
-bool xw_available(const XArgs& a, bool forward)
+bool xw_available(const XArgs& a, bool forward, bool want)
 {
     if (env_on("MH3D_GENERIC") || env_off("MH3D_XWARP")) return false;
-    if (forward && !env_on("MH3D_XWARP_FWD")) return false;
+    if (forward && !(env_on("MH3D_XWARP_FWD") || (want && !env_off("MH3D_XWARP_FWD")))) return false;
     return a.nx == xw::kNX && a.s == 2 && a.mx == xw::kMX && a.K >= 1 && a.K <= kMaxK && a.rows >= 1;
 }
 
 // Warps per row group (harmonics split over them): MH3D_XWARP_KS = 1, 2 or
 // 4.  Default 2 (same workload: A^T 35.4 us with 1, 33.2 us with 2,
 // 36.3 us with 4).
-int xw_ks()
+int xw_ks(int plan_ks = 0)
 {
     const char* v = std::getenv("MH3D_XWARP_KS");
-    if (v && (v[0] == '1' || v[0] == '4')) return v[0] - '0';
-    return 2;
+    if (v && (v[0] == '1' || v[0] == '2' || v[0] == '4')) return v[0] - '0';
+    return (plan_ks == 1 || plan_ks == 4) ? plan_ks : 2;
 }
 
 template <class F>
@@ -99,7 +99,7 @@ static int xw_grid(int rows, int ks)
 cudaError_t run_xfwd_w(const XArgs& a, cudaStream_t st)
 {
     if (!al(a.vin, 8) || !al(a.dout, 8)) return cudaErrorMisalignedAddress;
-    const int ks = xw_ks();
+    const int ks = xw_ks(a.ks);
     const dim3 grid(xw_grid(a.rows, ks));
     const size_t smem = xw::fwd_smem(a.K);
     if (ks == 1) xw::k_xfwd_w128<1><<<grid, xw::kWarps * 32, smem, st>>>(a);
@@ -111,7 +111,7 @@ cudaError_t run_xfwd_w(const XArgs& a, cudaStream_t st)
 cudaError_t run_xadj_w(const XArgs& a, cudaStream_t st)
 {
     if (!al(a.din, 8) || !al(a.vout, 4)) return cudaErrorMisalignedAddress;
-    const int ks = xw_ks();
+    const int ks = xw_ks(a.ks);
     const dim3 grid(xw_grid(a.rows, ks));
     const size_t smem = xw::adj_smem(a.K);
     if (ks == 1) xw::k_xadj_w128<1><<<grid, xw::kWarps * 32, smem, st>>>(a);
@@ -128,7 +128,7 @@ cudaError_t run_xzadj_w(ZXArgs& a, float* zout, cudaStream_t st)
 {
     if (!al(a.x.din, 8) || !al(zout, 16) || a.nz != 64) return cudaErrorInvalidValue;
     if (!ct_encode_z_map(&a.tz, zout, a.x.nx, a.ny, a.nz, a.x.nx / 2)) return cudaErrorInvalidValue;
-    const int ks = xw_ks();
+    const int ks = xw_ks(a.x.ks);
     const dim3 grid(2 * a.ny);
     if (ks == 1)
         xw::k_xzadj_w<LZ64, 1><<<grid, xw::XzwGeom<LZ64, 1>::T, xw::XzwGeom<LZ64, 1>::smem(a.x.K), st>>>(a);

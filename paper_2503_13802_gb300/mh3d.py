@@ -59,7 +59,7 @@ EXPORTS = ["mh3d_plan_create", "mh3d_plan_destroy", "mh3d_forward", "mh3d_adjoin
            "mh3d_solve_host", "mh3d_solve_batched", "mh3d_forward_noalloc", "mh3d_operator_norm2", "mh3d_last_error",
            "mh3d_plan_workspace_bytes", "mh3d_version", "mh3d_plan_autotune", "mh3d_plan_spectra", "mh3d_mhad",
            "mh3d_mhad_warm_start", "mh3d_estimate_phase", "mh3d_general_set_psf", "mh3d_general_forward",
-           "mh3d_general_adjoint", "mh3d_dot", "mh3d_solve_batched_warm", "mh3d_general_solve"]
+           "mh3d_general_adjoint", "mh3d_dot", "mh3d_solve_batched_warm", "mh3d_general_solve", "mh3d_plan_tuning"]
 
 
 def library_path() -> str:
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
     lib.mh3d_general_adjoint.argtypes = [P, P, P, P, P]
     lib.mh3d_dot.argtypes = [P, P, P, ctypes.c_longlong, POINTER(c_double), P]
     lib.mh3d_general_solve.argtypes = [P, P, P, POINTER(mh3d_solve_opts), P, POINTER(mh3d_solve_info), P]
+    lib.mh3d_plan_tuning.argtypes = [P, ctypes.c_char_p, c_int]
     lib.mh3d_solve_batched_warm.argtypes = [POINTER(c_void_p), c_int, POINTER(c_void_p), POINTER(mh3d_solve_opts),
                                             POINTER(c_void_p), POINTER(c_void_p), POINTER(mh3d_solve_info), P]
     lib.mh3d_last_error.argtypes = [P]
@@ -509,10 +510,20 @@ def mh3d_operator_norm2(plan: Plan) -> float:
 
 
 def mh3d_plan_autotune(plan: Plan, stream=None) -> int:
-    """Picks the transverse-pass tile width by timing; returns it."""
+    """Times the operators' launch variants and keeps the fastest for this
+    plan (see mh3d_plan_tuning for the choices); returns the tile width."""
     c = c_int(0)
     _check(plan.handle, load().mh3d_plan_autotune(plan.handle, c_void_p(_stream_ptr(stream)), ctypes.byref(c)))
     return c.value
+
+
+def mh3d_plan_tuning(plan: Plan) -> dict:
+    """The plan's current launch choices (0 = the library's default)."""
+    import json
+
+    buf = ctypes.create_string_buffer(512)
+    _check(plan.handle, load().mh3d_plan_tuning(plan.handle, buf, 512))
+    return json.loads(buf.value.decode())
 
 
 def mh3d_plan_spectra(plan: Plan, stream=None):

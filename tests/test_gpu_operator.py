@@ -25,7 +25,8 @@ def kernel_path(request, monkeypatch):
     warps per row group, the adjoint fused with T_z^T in y-slab clusters at
     n_z = 64), again with four warps per row group and the adjoint's T_z^T
     as a separate launch (MH3D_XWARP_KS=4, MH3D_XWARP_ZX=0), with one warp
-    per row group (MH3D_XWARP_KS=1), on the CTA-level drive-axis
+    per row group and the alternative T-pass radix schedules the autotuner
+    may pick (MH3D_XWARP_KS=1, MH3D_TPASS_RADIX=1), on the CTA-level drive-axis
     passes those replace (MH3D_XWARP=0: y-slab cluster passes, pipelined
     adjoint, 16-row normal pass), again with MH3D_GENERIC=1, which forces the
     runtime-general kernels for every size, and on the measured alternatives
@@ -37,7 +38,7 @@ def kernel_path(request, monkeypatch):
     rounds of two harmonics (MH3D_XADJ_KB=2)."""
     for v in ("MH3D_GENERIC", "MH3D_XNRM_BULK", "MH3D_XADJ_BULK", "MH3D_XNRM_PAIRS", "MH3D_XADJ_PAIRS",
               "MH3D_XFWD_KPC", "MH3D_XFWD_PAIRS", "MH3D_FUSE_ZX", "MH3D_ZX_CLUSTER", "MH3D_XADJ_KB", "MH3D_XWARP",
-              "MH3D_XWARP_FWD", "MH3D_XWARP_KS", "MH3D_XWARP_ZX", "MH3D_XWARP_NRM"):
+              "MH3D_XWARP_FWD", "MH3D_XWARP_KS", "MH3D_XWARP_ZX", "MH3D_XWARP_NRM", "MH3D_TPASS_RADIX"):
         monkeypatch.delenv(v, raising=False)
     if request.param == "specialised":
         monkeypatch.setenv("MH3D_XWARP_FWD", "1")    # the opt-in warp forward and normal passes too
@@ -49,6 +50,7 @@ def kernel_path(request, monkeypatch):
     elif request.param == "warp1":
         monkeypatch.setenv("MH3D_XWARP_FWD", "1")
         monkeypatch.setenv("MH3D_XWARP_KS", "1")
+        monkeypatch.setenv("MH3D_TPASS_RADIX", "1")  # the alternative T-pass schedules (64: 4x16, 128: 8x16)
     elif request.param == "generic":
         monkeypatch.setenv("MH3D_GENERIC", "1")
     elif request.param == "ctalevel":

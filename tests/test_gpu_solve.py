@@ -354,16 +354,20 @@ def test_solve_host_buffers_match_device_solve():
     np.testing.assert_array_equal(xh.numpy(), x.cpu().numpy())
 
 
-def test_tile_width_and_autotune_keep_results_bit_identical(monkeypatch):
+def test_tile_width_keeps_results_bit_identical_and_autotune_keeps_parity(monkeypatch):
     """The transverse-pass tile width (8 or 16 columns per CTA) only groups
     columns into CTAs: every column's transform and every reduction is the
-    same, so solves agree bit for bit, before and after autotuning."""
-    from paper_2503_13802_gb300 import make_opts, mh3d_plan_autotune, mh3d_solve
+    same, so solves agree bit for bit.  The autotuner also picks radix
+    schedules and drive-axis launch variants, which change the FP32 rounding
+    path: the tuned plan's solve agrees with the untuned one and with the
+    oracle's to 1e-4 at a common rel. residual of 1e-6."""
+    from paper_2503_13802_gb300 import make_opts, mh3d_plan_autotune, mh3d_plan_tuning, mh3d_solve
 
     p = params((64, 32, 32), s=2, kmin=2, kmax=9)
     g = oracle_geom(p)
     b = sens_map(p)
-    d = _dev(W.random_portraits(g.portrait_shape, 17), torch.complex64)
+    dn = W.random_portraits(g.portrait_shape, 17)
+    d = _dev(dn, torch.complex64)
     opts = make_opts(lam=1e-3, lam_relative=True, rel_tol=1e-4, max_iter=300)
     monkeypatch.delenv("MH3D_TPASS_COLS", raising=False)
     plan16 = gpu_plan(p, b)
@@ -375,11 +379,42 @@ def test_tile_width_and_autotune_keep_results_bit_identical(monkeypatch):
     i16 = mh3d_solve(plan16, d, opts, x16)
     i8 = mh3d_solve(plan8, d, opts, x8)
     assert i16["iters"] == i8["iters"] and torch.equal(x16, x8)
+    o6 = make_opts(lam=1e-3, lam_relative=True, rel_tol=1e-6, max_iter=3000)
+    xu = torch.empty_like(x16)
+    mh3d_solve(plan16, d, o6, xu)
     cols = mh3d_plan_autotune(plan16)
-    assert cols in (8, 16)
+    t = mh3d_plan_tuning(plan16)
+    assert cols in (8, 16) and t["tpass_cols"] == cols, t
+    assert t["tpass_radix"] in (0, 1) and t["adj_path"] in (1, 2, 3) and t["fwd_path"] in (1, 2), t
     xt = torch.empty_like(x16)
-    mh3d_solve(plan16, d, opts, xt)
-    assert torch.equal(xt, x16)
+    it = mh3d_solve(plan16, d, o6, xt)
+    assert it["status"] == 0
+    assert rel_l2(xt.cpu().numpy(), xu.cpu().numpy()) <= 1e-4
+    xo, _, _ = oracle.cg(g, dn, b, oracle.SolveOpts(lam=1e-3, lam_relative=True, rel_tol=1e-6, max_iter=5000))
+    assert rel_l2(xt.cpu().numpy(), xo) <= 1e-4, rel_l2(xt.cpu().numpy(), xo)
+
+
+def test_autotune_choices_persist_in_the_json_cache(tmp_path, monkeypatch):
+    """MH3D_TUNE_CACHE: a size class found in the file takes the file's
+    choices without timing; a new one is timed and appended to the file."""
+    import json
+
+    from paper_2503_13802_gb300 import mh3d_plan_autotune, mh3d_plan_tuning
+
+    path = tmp_path / "tune.json"
+    stored = {"tpass_cols": 8, "tpass_radix": 1, "zx_c": 4, "adj_path": 3, "xw_ks": 0, "fwd_path": 1,
+              "xw_ks_fwd": 0}
+    # the library's layout: a JSON object with one size class per line
+    path.write_text('{\n  "128x12x64/s2/K8/b0": ' + json.dumps(stored) + "\n}\n")
+    monkeypatch.setenv("MH3D_TUNE_CACHE", str(path))
+    pa = gpu_plan(params((128, 12, 64), s=2, kmin=2, kmax=9), None)
+    assert mh3d_plan_autotune(pa) == 8
+    assert mh3d_plan_tuning(pa) == stored
+    pb = gpu_plan(params((64, 12, 64), s=2, kmin=2, kmax=9), None)
+    mh3d_plan_autotune(pb)
+    saved = json.loads(path.read_text())
+    assert saved["128x12x64/s2/K8/b0"] == stored
+    assert saved["64x12x64/s2/K8/b0"] == mh3d_plan_tuning(pb)
 
 
 def test_zero_data_converges_at_once_to_zero():
