@@ -63,7 +63,8 @@ bool xzw_available(const XArgs& a, int nz)
 // The warp-centric cluster normal pass (n_x = 128, s = 2, n_z = 64),
 // opt-in (MH3D_XWARP_NRM=1): in the CG loop at 128x128x64 it measured 25.8
 // us per iteration against 23.1 us for the CTA-level cluster pass (same
-// box), whose z part runs on 256 threads per CTA instead of 128.
+// box).  Not for want of threads in its z part: with 256 threads per CTA
+// (the drive-axis part on half of them) it measured 25.5 against 23.3 us.
 bool zxnw_available(const XArgs& a, int nz)
 {
     return !env_on("MH3D_GENERIC") && !env_off("MH3D_XWARP") && env_on("MH3D_XWARP_NRM") && a.nx == xw::kNX &&
