@@ -7,15 +7,17 @@
 //
 // Forward: the weighted volumes b_j rho go through complex pencil passes
 // along x, y and z (the Stockham engine of fft_smem.cuh, no spectral step);
-// per harmonic, one pointwise kernel forms the portrait-grid spectrum
-//   D(w') = sum_{a < s} e^{2 pi i (w' + a m_x) r / n_x} sum_j H_kj W_j (w' + a m_x)
+// one pointwise kernel forms every harmonic's portrait-grid spectrum
+//   D_k(w') = sum_{a < s} e^{2 pi i (w' + a m_x) r / n_x} sum_j H_kj W_j (w' + a m_x)
 // (the row selector x = s i' + r is exactly this alias sum with the offset
-// phase), and inverse passes along x (length m_x), y and z return
-// c_k[z][y][s i' + r]; d_k = e^{i theta_k} Re c.  Adjoint: per harmonic the
-// real parts Re(e^{-i theta_k} d_k) are inserted at x = s i' + r, the volume
-// is transformed, V_j += conj(H_kj) E accumulates over k, and the inverse
-// passes and sum_j b_j Re V_j finish.  Unnormalised transforms throughout;
-// the 1/N sits in the stored spectra.
+// phase) in the output buffer, and inverse passes along x (length m_x), y and
+// z over all K portraits return c_k[z][y][s i' + r]; d_k = e^{i theta_k} Re c
+// in place.  Adjoint: the real parts Re(e^{-i theta_k} d_k) of every
+// harmonic are inserted at x = s i' + r into K volumes, the K volumes are
+// transformed together, V_j = sum_k conj(H_kj) E_k, and the inverse passes
+// and sum_j b_j Re V_j finish.  Each pass covers every harmonic (or
+// component) in one launch: 9 launches a call, whatever K.  Unnormalised
+// transforms throughout; the 1/N sits in the stored spectra.
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -31,19 +33,25 @@ constexpr int kGP = 8;      // pencils per CTA
 constexpr int kGT = 128;    // threads per CTA
 constexpr int kGB = 256;    // threads per CTA of the pointwise kernels
 
-// Pencils of a complex volume [nz][ny][W] (x fastest): axis 0 walks x
-// (pencil p = row z ny + y), 1 walks y (p = z W + x), 2 walks z (p = y W + x).
+// Pencils of `vols` complex volumes [nz][ny][W] (x fastest), vstride
+// float2 apart: axis 0 walks x (pencil p = row z ny + y), 1 walks y
+// (p = z W + x), 2 walks z (p = y W + x); pencil p of the whole set is
+// pencil p % per_vol() of volume p / per_vol().
 struct Pencils {
     int axis, W, ny, nz;
-    __host__ __device__ long long count() const
+    int vols = 1;
+    long long vstride = 0;
+    __host__ __device__ long long per_vol() const
     {
         return axis == 0 ? (long long)ny * nz : (axis == 1 ? (long long)W * nz : (long long)W * ny);
     }
-    __device__ __forceinline__ long long base(long long p) const
+    __host__ __device__ long long count() const { return per_vol() * vols; }
+    __device__ __forceinline__ long long base(long long pg) const
     {
-        if (axis == 0) return p * W;
+        const long long pv = per_vol(), c = pg / pv, p = pg - c * pv;
+        if (axis == 0) return c * vstride + p * W;
         const long long x = p % W, q = p / W;
-        return axis == 1 ? q * ny * W + x : q * W + x;
+        return c * vstride + (axis == 1 ? q * ny * W + x : q * W + x);
     }
     __device__ __forceinline__ long long stride() const
     {
@@ -109,13 +117,18 @@ __global__ void k_gen_weight(const float* __restrict__ rho, const float* __restr
     }
 }
 
-// Portrait-grid spectrum of harmonic k: q over [nz][ny][mx].
-__global__ void k_gen_fold(const float2* __restrict__ Hk, const float2* __restrict__ W, float2* __restrict__ D,
-                           int nx, int ny, int nz, int mx, int s, int r, int nc, long long N,
+// Portrait-grid spectra of every harmonic: D[k][q], q over [nz][ny][mx]:
+// D_k(w) = sum_a e^{2 pi i f r / nx} sum_j H_kj(f) W_j(f), f = w + a mx (the
+// row selector x = s i' + r as an alias sum).
+__global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restrict__ W, float2* __restrict__ D,
+                           int nx, int ny, int nz, int mx, int s, int r, int nc, int K, long long N,
                            const float2* __restrict__ twx)
 {
     const long long Q = (long long)nz * ny * mx;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (long long)gridDim.x * blockDim.x) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < Q * K;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long k = g / Q, q = g - k * Q;
+        const float2* __restrict__ Hk = H + k * 3 * N;
         const int w = (int)(q % mx);
         const long long row = q / mx;   // z ny + y
         float2 acc = make_float2(0.f, 0.f);
@@ -128,44 +141,52 @@ __global__ void k_gen_fold(const float2* __restrict__ Hk, const float2* __restri
             const float2 tw = twx[(int)(((long long)f * r) % nx)];
             acc = c_add(acc, c_mul(t, make_float2(tw.x, -tw.y)));
         }
-        D[q] = acc;
+        D[g] = acc;
     }
 }
 
-// d_k = e^{i theta_k} Re(c)
-__global__ void k_gen_phase(const float2* __restrict__ D, float2* __restrict__ dk, long long Q, float2 ph)
+// d_k = e^{i theta_k} Re(D_k) for every harmonic (ph[k] = e^{i theta_k})
+__global__ void k_gen_phase(const float2* D, float2* d, long long Q, int K,
+                            const float2* __restrict__ ph)
 {
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (long long)gridDim.x * blockDim.x) {
-        const float c = D[q].x;
-        dk[q] = make_float2(ph.x * c, ph.y * c);
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < Q * K; g += (long long)gridDim.x * blockDim.x) {
+        const float2 p = ph[g / Q];
+        const float c = D[g].x;
+        d[g] = make_float2(p.x * c, p.y * c);
     }
 }
 
-// E = Re(e^{-i theta_k} d_k) at x = s i' + r, zero elsewhere
-__global__ void k_gen_insert(const float2* __restrict__ dk, float2* __restrict__ E, int nx, int mx, int s, int r,
-                             long long N, float2 ph)
+// E_k = Re(e^{-i theta_k} d_k) at x = s i' + r, zero elsewhere, every harmonic
+__global__ void k_gen_insert(const float2* __restrict__ d, float2* __restrict__ E, int nx, int mx, int s, int r,
+                             long long N, long long Q, int K, const float2* __restrict__ ph)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N * K; g += (long long)gridDim.x * blockDim.x) {
+        const long long k = g / N, i = g - k * N;
         const int x = (int)(i % nx);
         const long long row = i / nx;
         float v = 0.f;
         if (x >= r && (x - r) % s == 0) {
-            const float2 d = dk[row * mx + (x - r) / s];
-            v = ph.x * d.x + ph.y * d.y;
+            const float2 dv = d[k * Q + row * mx + (x - r) / s];
+            const float2 p = ph[k];
+            v = p.x * dv.x + p.y * dv.y;
         }
-        E[i] = make_float2(v, 0.f);
+        E[g] = make_float2(v, 0.f);
     }
 }
 
-// V_j (+)= conj(H_kj) E
-__global__ void k_gen_acc(const float2* __restrict__ Hk, const float2* __restrict__ E, float2* __restrict__ V,
-                          long long N, int nc, int first)
+// V_j = sum_k conj(H_kj) E_k
+__global__ void k_gen_acc(const float2* __restrict__ H, const float2* __restrict__ E, float2* __restrict__ V,
+                          long long N, int nc, int K)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N * nc;
          i += (long long)gridDim.x * blockDim.x) {
-        const float2 h = Hk[i];
-        const float2 t = c_mul(make_float2(h.x, -h.y), E[i % N]);
-        V[i] = first ? t : c_add(V[i], t);
+        const long long j = i / N, v = i - j * N;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int k = 0; k < K; ++k) {
+            const float2 h = H[((long long)k * 3 + j) * N + v];
+            acc = c_add(acc, c_mul(make_float2(h.x, -h.y), E[(long long)k * N + v]));
+        }
+        V[i] = acc;
     }
 }
 
@@ -217,10 +238,14 @@ cudaError_t gen_set_attributes()
     return e;
 }
 
-// In-place transform of every pencil of `v` (rows of width W) along `axis`.
-cudaError_t gen_line(float2* v, int axis, int W, int ny, int nz, const AxisPlan& ap, bool inv, cudaStream_t st)
+// In-place transform of every pencil of `vols` volumes (rows of width W,
+// vstride float2 apart) along `axis`.
+cudaError_t gen_line(float2* v, int axis, int W, int ny, int nz, int vols, long long vstride, const AxisPlan& ap,
+                     bool inv, cudaStream_t st)
 {
-    const Pencils g{axis, W, ny, nz};
+    Pencils g{axis, W, ny, nz};
+    g.vols = vols;
+    g.vstride = vstride;
     const long long np = g.count();
     const size_t smem = sizeof(float2) * 2 * (size_t)ap.n * kGP;
     const int grid = (int)((np + kGP - 1) / kGP);
@@ -229,18 +254,15 @@ cudaError_t gen_line(float2* v, int axis, int W, int ny, int nz, const AxisPlan&
     return cudaGetLastError();
 }
 
-// 3D transform of `count` volumes [nz][ny][W], W = the x length of `axp`.
+// 3D transform of `count` consecutive volumes [nz][ny][W], W = the x length
+// of `axp`: three launches, each over every volume's pencils.
 cudaError_t gen_fft3(const Plan& P, float2* v, int count, const AxisPlan& axp, bool inv, cudaStream_t st)
 {
     const long long vol = (long long)axp.n * P.ny * P.nz;
-    for (int c = 0; c < count; ++c) {
-        float2* u = v + c * vol;
-        cudaError_t e;
-        if ((e = gen_line(u, 0, axp.n, P.ny, P.nz, axp, inv, st)) != cudaSuccess) return e;
-        if ((e = gen_line(u, 1, axp.n, P.ny, P.nz, P.ay, inv, st)) != cudaSuccess) return e;
-        if ((e = gen_line(u, 2, axp.n, P.ny, P.nz, P.az, inv, st)) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    cudaError_t e;
+    if ((e = gen_line(v, 0, axp.n, P.ny, P.nz, count, vol, axp, inv, st)) != cudaSuccess) return e;
+    if ((e = gen_line(v, 1, axp.n, P.ny, P.nz, count, vol, P.ay, inv, st)) != cudaSuccess) return e;
+    return gen_line(v, 2, axp.n, P.ny, P.nz, count, vol, P.az, inv, st);
 }
 
 mh3d_status gen_check(Plan& P, const char* who)
@@ -282,8 +304,9 @@ mh3d_status mh3d_general_set_psf(mh3d_plan Pp, const float* h_host)
     GEN_CK(P, gen_set_attributes());
     const long long N = P.N, n3 = 3LL * P.K * N;
     if (!P.gen_H) GEN_CK(P, dev_malloc(&P.gen_H, sizeof(float2) * (size_t)n3));
-    if (!P.gen_work) GEN_CK(P, dev_malloc(&P.gen_work, sizeof(float2) * (size_t)(4 * N)));
-    // the real samples are staged in the work area (4N float2 >= 3N floats per harmonic)
+    // work area: 3 component volumes + one inserted volume per harmonic
+    if (!P.gen_work) GEN_CK(P, dev_malloc(&P.gen_work, sizeof(float2) * (size_t)((3 + P.K) * N)));
+    // the real samples are staged in the work area (>= 4N float2 >= 3N floats per harmonic)
     float* stage = reinterpret_cast<float*>(P.gen_work);
     const cudaStream_t st = 0;
     for (int k = 0; k < P.K; ++k) {
@@ -312,21 +335,17 @@ mh3d_status mh3d_general_forward(mh3d_plan Pp, const float* rho, const float* bv
     const cudaStream_t st = (cudaStream_t)stream;
     const long long N = P.N, Q = (long long)P.nz * P.ny * P.mx;
     const int nc = bvec ? 3 : 1;
-    float2* W = P.gen_work;          // nc volumes
-    float2* D = P.gen_work + 3 * N;  // the portrait-grid spectrum
-    std::vector<float2> ph(P.K);
-    for (int k = 0; k < P.K; ++k) ph[k] = make_float2((float)std::cos(P.theta[k]), (float)std::sin(P.theta[k]));
+    float2* W = P.gen_work;   // nc volumes
+    float2* D = (float2*)d;   // the portrait-grid spectra, transformed and phased in place
     k_gen_weight<<<gen_blocks(N * nc), kGB, 0, st>>>(rho, bvec, W, N, nc);
     GEN_CK(P, cudaGetLastError());
     GEN_CK(P, gen_fft3(P, W, nc, P.ax, false, st));
-    for (int k = 0; k < P.K; ++k) {
-        const float2* Hk = P.gen_H + (long long)k * 3 * N;
-        k_gen_fold<<<gen_blocks(Q), kGB, 0, st>>>(Hk, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, N, P.ax.tw);
-        GEN_CK(P, cudaGetLastError());
-        GEN_CK(P, gen_fft3(P, D, 1, P.am, true, st));
-        k_gen_phase<<<gen_blocks(Q), kGB, 0, st>>>(D, (float2*)d + (long long)k * Q, Q, ph[k]);
-        GEN_CK(P, cudaGetLastError());
-    }
+    k_gen_fold<<<gen_blocks(Q * P.K), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N,
+                                                    P.ax.tw);
+    GEN_CK(P, cudaGetLastError());
+    GEN_CK(P, gen_fft3(P, D, P.K, P.am, true, st));
+    k_gen_phase<<<gen_blocks(Q * P.K), kGB, 0, st>>>(D, D, Q, P.K, P.phase);
+    GEN_CK(P, cudaGetLastError());
     return MH3D_OK;
 }
 
@@ -342,16 +361,12 @@ mh3d_status mh3d_general_adjoint(mh3d_plan Pp, const void* d, const float* bvec,
     const long long N = P.N, Q = (long long)P.nz * P.ny * P.mx;
     const int nc = bvec ? 3 : 1;
     float2* V = P.gen_work;          // nc accumulators
-    float2* E = P.gen_work + 3 * N;  // one harmonic's inserted volume
-    for (int k = 0; k < P.K; ++k) {
-        const float2 ph = make_float2((float)std::cos(P.theta[k]), (float)std::sin(P.theta[k]));
-        k_gen_insert<<<gen_blocks(N), kGB, 0, st>>>((const float2*)d + (long long)k * Q, E, P.nx, P.mx, P.s, P.r, N,
-                                                      ph);
-        GEN_CK(P, cudaGetLastError());
-        GEN_CK(P, gen_fft3(P, E, 1, P.ax, false, st));
-        k_gen_acc<<<gen_blocks(N * nc), kGB, 0, st>>>(P.gen_H + (long long)k * 3 * N, E, V, N, nc, k == 0);
-        GEN_CK(P, cudaGetLastError());
-    }
+    float2* E = P.gen_work + 3 * N;  // the harmonics' inserted volumes
+    k_gen_insert<<<gen_blocks(N * P.K), kGB, 0, st>>>((const float2*)d, E, P.nx, P.mx, P.s, P.r, N, Q, P.K, P.phase);
+    GEN_CK(P, cudaGetLastError());
+    GEN_CK(P, gen_fft3(P, E, P.K, P.ax, false, st));
+    k_gen_acc<<<gen_blocks(N * nc), kGB, 0, st>>>(P.gen_H, E, V, N, nc, P.K);
+    GEN_CK(P, cudaGetLastError());
     GEN_CK(P, gen_fft3(P, V, nc, P.ax, true, st));
     k_gen_out<<<gen_blocks(N), kGB, 0, st>>>(V, bvec, out, N, nc);
     GEN_CK(P, cudaGetLastError());
