@@ -59,36 +59,46 @@ struct Pencils {
     }
 };
 
+// Element e of the CTA's pencil p: base[p] + e * stride (base < 0: a pencil
+// past the end, read as zero and not written).  The bases are computed once
+// per CTA, so the per-element address is one multiply-add.
 struct GenLd {
     const float2* v;
-    Pencils g;
-    long long p0, np;
+    const long long* base;
+    long long stride;
     __device__ __forceinline__ float2 operator()(int e, int p) const
     {
-        if (p0 + p >= np) return make_float2(0.f, 0.f);
-        return v[g.base(p0 + p) + (long long)e * g.stride()];
+        const long long b = base[p];
+        return b < 0 ? make_float2(0.f, 0.f) : v[b + e * stride];
     }
 };
 struct GenSt {
     float2* v;
-    Pencils g;
-    long long p0, np;
+    const long long* base;
+    long long stride;
     __device__ __forceinline__ void operator()(int e, int p, float2 x) const
     {
-        if (p0 + p < np) v[g.base(p0 + p) + (long long)e * g.stride()] = x;
+        const long long b = base[p];
+        if (b >= 0) v[b + e * stride] = x;
     }
 };
 
 // One transform along an axis, in place: every CTA owns kGP whole pencils;
-// the first stage reads all of them before the last stage writes.
-template <bool INV>
+// the first stage reads all of them before the last stage writes.  PF: the
+// first and last stages walk pencils fastest (axes y and z, where the kGP
+// pencils are neighbours in memory); along x they walk elements fastest.
+template <bool INV, bool PF>
 __global__ void __launch_bounds__(kGT) k_gen_line(float2* v, Pencils g, RadixPlan pl, const float2* __restrict__ tw)
 {
     extern __shared__ float2 gsm[];
+    __shared__ long long sbase[kGP];
     float2* s0 = gsm;
     float2* s1 = gsm + (size_t)pl.n * kGP;
     const long long p0 = (long long)blockIdx.x * kGP, np = g.count();
-    fft_run<INV, true, true>(pl, GenLd{v, g, p0, np}, GenSt{v, g, p0, np}, s0, s1, kGP, kGP, tw);
+    if (threadIdx.x < kGP) sbase[threadIdx.x] = p0 + threadIdx.x < np ? g.base(p0 + threadIdx.x) : -1;
+    __syncthreads();
+    const long long sd = g.stride();
+    fft_run<INV, PF, PF>(pl, GenLd{v, sbase, sd}, GenSt{v, sbase, sd}, s0, s1, kGP, kGP, tw);
 }
 
 __global__ void k_gen_spectra_in(const float* __restrict__ h, float2* __restrict__ H, long long n)
@@ -232,8 +242,13 @@ cudaError_t gen_set_attributes()
     std::lock_guard<std::mutex> lk(g_gen_attr_mu);
     if (g_gen_attr_done[dev]) return cudaSuccess;
     const int smem = (int)(sizeof(float2) * 2 * (size_t)kMaxLen * kGP);
-    e = cudaFuncSetAttribute(k_gen_line<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gen_line<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_gen_line<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gen_line<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gen_line<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gen_line<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) g_gen_attr_done[dev] = true;
     return e;
 }
@@ -249,8 +264,11 @@ cudaError_t gen_line(float2* v, int axis, int W, int ny, int nz, int vols, long 
     const long long np = g.count();
     const size_t smem = sizeof(float2) * 2 * (size_t)ap.n * kGP;
     const int grid = (int)((np + kGP - 1) / kGP);
-    if (inv) k_gen_line<true><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
-    else k_gen_line<false><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
+    const bool pf = axis != 0;
+    if (inv && pf) k_gen_line<true, true><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
+    else if (inv) k_gen_line<true, false><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
+    else if (pf) k_gen_line<false, true><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
+    else k_gen_line<false, false><<<grid, kGT, smem, st>>>(v, g, ap.rp, ap.tw);
     return cudaGetLastError();
 }
 
