@@ -12,17 +12,23 @@
 // (the row selector x = s i' + r is exactly this alias sum with the offset
 // phase) in the output buffer, and inverse passes along x (length m_x), y and
 // z over all K portraits return c_k[z][y][s i' + r]; d_k = e^{i theta_k} Re c
-// in place.  Adjoint: the real parts Re(e^{-i theta_k} d_k) of every
-// harmonic are inserted at x = s i' + r into K volumes, the K volumes are
-// transformed together, V_j = sum_k conj(H_kj) E_k, and the inverse passes
-// and sum_j b_j Re V_j finish.  Each pass covers every harmonic (or
-// component) in one launch: 9 launches a call, whatever K.  Unnormalised
+// in place.  Adjoint: the real parts u_k = Re(e^{-i theta_k} d_k) are
+// transformed on the portrait grid, the unfold kernel forms
+// V_j(f) = e^{-2 pi i f r / n_x} sum_k conj(H_kj(f)) U_k(f mod m_x) (the
+// spectrum of u_k inserted at x = s i' + r, periodic in m_x), and the
+// inverse passes and sum_j b_j Re V_j finish.  Each pass covers every
+// harmonic (or component) in one launch, whatever K: 9 launches a call, or,
+// where the pencil passes run the compile-time kernel (lengths 64 and 128)
+// and carry the weighting b_j rho, the phase and the unphasing in their
+// loads and stores, 7 for the forward and 8 for the adjoint.  Unnormalised
 // transforms throughout; the 1/N sits in the stored spectra.
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
 
+#include "fft_ct.cuh"
 #include "fft_smem.cuh"
 #include "mh3d_internal.h"
 
@@ -101,6 +107,98 @@ __global__ void __launch_bounds__(kGT) k_gen_line(float2* v, Pencils g, RadixPla
     fft_run<INV, PF, PF>(pl, GenLd{v, sbase, sd}, GenSt{v, sbase, sd}, s0, s1, kGP, kGP, tw);
 }
 
+// Fused pre- and post-steps of the compile-time pencil kernel (MODE):
+//   0  in place;
+//   1  load W_j = b_j rho (rho real [N], b [nc][N] or null: 1) -- the x pass
+//      of the forward's component volumes, written to v;
+//   2  store d_k = e^{i theta_k} Re(c_k) (ph[k]) -- the z pass of the
+//      forward's inverse, in place;
+//   3  load u_k = Re(e^{-i theta_k} d_k) (src = the portraits, ph[k]) --
+//      the x pass of the adjoint's portrait transform, written to v.
+// The volume of pencil p (a component or a harmonic) is p / per_vol.
+struct GenIO {
+    const float* rho = nullptr;
+    const float* b = nullptr;
+    const float2* src = nullptr;
+    const float2* ph = nullptr;
+};
+
+// The same transform for the common lengths (64, 128) with a compile-time
+// radix schedule L and kGPC pencils per CTA.  The pencils are staged through
+// shared memory with the coalesced mapping of their axis (elements fastest
+// along x, where a pencil is a contiguous row; pencils fastest along y and
+// z, where the CTA's pencils are neighbours in memory), every stage runs
+// pencil-fast from shared memory, and the result leaves the same way.  The
+// pencil stride kGPC + 1 keeps the element-fast staging conflict-free.
+constexpr int kGPC = 16;
+template <class L, bool INV, bool X, int MODE>
+__global__ void __launch_bounds__(kGT) k_gen_line_ct(float2* v, Pencils g, const float2* __restrict__ tw, GenIO io)
+{
+    constexpr int N = ct::RInfo<L>::n(), NST = ct::RInfo<L>::nst, P = kGPC, LD = P + 1;
+    constexpr int IT = N * P / kGT;
+    static_assert((N * P) % kGT == 0, "whole staging rounds");
+    __shared__ __align__(16) float2 b0[N * LD];
+    __shared__ __align__(16) float2 b1[N * LD];
+    __shared__ long long sbase[P], svol[P];
+    __shared__ float2 sph[P];
+    const long long p0 = (long long)blockIdx.x * P, np = g.count();
+    if (threadIdx.x < P) {
+        const long long pg = p0 + threadIdx.x;
+        const long long c = pg < np ? pg / g.per_vol() : 0;
+        sbase[threadIdx.x] = pg < np ? g.base(pg) : -1;
+        svol[threadIdx.x] = c;
+        if (MODE == 2 || MODE == 3) sph[threadIdx.x] = io.ph[c];
+    }
+    __syncthreads();
+    const long long sd = g.stride();
+    float2 t[IT];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int idx = (int)threadIdx.x + i * kGT;
+        const int e = X ? idx % N : idx / P, p = X ? idx / N : idx % P;
+        const long long b = sbase[p];
+        if (b < 0) {
+            t[i] = make_float2(0.f, 0.f);
+        } else if (MODE == 1) {
+            const long long a = b + e * sd;
+            float x = io.rho[a - svol[p] * g.vstride];
+            if (io.b) x *= io.b[a];
+            t[i] = make_float2(x, 0.f);
+        } else if (MODE == 3) {
+            const float2 dv = io.src[b + e * sd], ph = sph[p];
+            t[i] = make_float2(ph.x * dv.x + ph.y * dv.y, 0.f);
+        } else {
+            t[i] = v[b + e * sd];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int idx = (int)threadIdx.x + i * kGT;
+        const int e = X ? idx % N : idx / P, p = X ? idx / N : idx % P;
+        b1[e * LD + p] = t[i];
+    }
+    __syncthreads();
+    // stage 0 reads b1 and writes b0; the last stage writes the buffer it
+    // does not read
+    float2* out = ((NST - 1) & 1) ? b1 : b0;
+    ct::run_stages<L, 0, NST, P, kGT, 1, INV, true, true>(BufLd{b1, LD}, BufSt{out, LD}, b0, b1, LD, tw);
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int idx = (int)threadIdx.x + i * kGT;
+        const int e = X ? idx % N : idx / P, p = X ? idx / N : idx % P;
+        const long long b = sbase[p];
+        if (b >= 0) {
+            const float2 o = out[e * LD + p];
+            if (MODE == 2) {
+                const float2 ph = sph[p];
+                v[b + e * sd] = make_float2(ph.x * o.x, ph.y * o.x);
+            } else {
+                v[b + e * sd] = o;
+            }
+        }
+    }
+}
+
 __global__ void k_gen_spectra_in(const float* __restrict__ h, float2* __restrict__ H, long long n)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -129,29 +227,61 @@ __global__ void k_gen_weight(const float* __restrict__ rho, const float* __restr
 
 // Portrait-grid spectra of every harmonic: D[k][q], q over [nz][ny][mx]:
 // D_k(w) = sum_a e^{2 pi i f r / nx} sum_j H_kj(f) W_j(f), f = w + a mx (the
-// row selector x = s i' + r as an alias sum).
+// row selector x = s i' + r as an alias sum).  One thread per q walks the
+// harmonics.  SR > 0 (s <= SR): the thread keeps W_j(f) and the offset
+// phases of its s frequencies in registers; SR = 0: any s, re-read per k.
+template <int SR>
 __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restrict__ W, float2* __restrict__ D,
-                           int nx, int ny, int nz, int mx, int s, int r, int nc, int K, long long N,
+                           int nx, int mx, int s, int r, int nc, int K, long long N, long long Q,
                            const float2* __restrict__ twx)
 {
-    const long long Q = (long long)nz * ny * mx;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < Q * K;
-         g += (long long)gridDim.x * blockDim.x) {
-        const long long k = g / Q, q = g - k * Q;
-        const float2* __restrict__ Hk = H + k * 3 * N;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (long long)gridDim.x * blockDim.x) {
         const int w = (int)(q % mx);
-        const long long row = q / mx;   // z ny + y
-        float2 acc = make_float2(0.f, 0.f);
-        for (int a = 0; a < s; ++a) {
-            const int f = w + a * mx;
-            const long long i = row * nx + f;
-            float2 t = make_float2(0.f, 0.f);
-            for (int j = 0; j < nc; ++j) t = c_add(t, c_mul(Hk[(long long)j * N + i], W[(long long)j * N + i]));
-            // e^{+2 pi i f r / nx} = conj(W_nx^{f r mod nx})
-            const float2 tw = twx[(int)(((long long)f * r) % nx)];
-            acc = c_add(acc, c_mul(t, make_float2(tw.x, -tw.y)));
+        const long long row = (q - w) / mx * nx;   // (z ny + y) nx
+        if constexpr (SR > 0) {
+            float2 wv[SR][3], ph[SR];
+#pragma unroll
+            for (int a = 0; a < SR; ++a) {
+                const int f = w + a * mx;
+                const long long i = row + f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    wv[a][j] = (a < s && j < nc) ? W[(long long)j * N + i] : make_float2(0.f, 0.f);
+                // e^{+2 pi i f r / nx} = conj(W_nx^{f r mod nx})
+                const float2 tw = a < s ? twx[(int)(((long long)f * r) % nx)] : make_float2(0.f, 0.f);
+                ph[a] = make_float2(tw.x, -tw.y);
+            }
+#pragma unroll 2
+            for (int k = 0; k < K; ++k) {
+                const float2* __restrict__ Hk = H + (long long)k * 3 * N + row + w;
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int a = 0; a < SR; ++a) {
+                    if (a < s) {
+                        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            if (j < nc) t = c_add(t, c_mul(Hk[(long long)j * N + a * mx], wv[a][j]));
+                        acc = c_add(acc, c_mul(t, ph[a]));
+                    }
+                }
+                D[(long long)k * Q + q] = acc;
+            }
+        } else {
+            for (int k = 0; k < K; ++k) {
+                const float2* __restrict__ Hk = H + (long long)k * 3 * N;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int a = 0; a < s; ++a) {
+                    const int f = w + a * mx;
+                    const long long i = row + f;
+                    float2 t = make_float2(0.f, 0.f);
+                    for (int j = 0; j < nc; ++j) t = c_add(t, c_mul(Hk[(long long)j * N + i], W[(long long)j * N + i]));
+                    const float2 tw = twx[(int)(((long long)f * r) % nx)];
+                    acc = c_add(acc, c_mul(t, make_float2(tw.x, -tw.y)));
+                }
+                D[(long long)k * Q + q] = acc;
+            }
         }
-        D[g] = acc;
     }
 }
 
@@ -166,37 +296,45 @@ __global__ void k_gen_phase(const float2* D, float2* d, long long Q, int K,
     }
 }
 
-// E_k = Re(e^{-i theta_k} d_k) at x = s i' + r, zero elsewhere, every harmonic
-__global__ void k_gen_insert(const float2* __restrict__ d, float2* __restrict__ E, int nx, int mx, int s, int r,
-                             long long N, long long Q, int K, const float2* __restrict__ ph)
+// u_k = Re(e^{-i theta_k} d_k) on the portrait grid, every harmonic, as
+// complex values with zero imaginary part
+__global__ void k_gen_unphase(const float2* __restrict__ d, float2* __restrict__ U, long long Q, int K,
+                              const float2* __restrict__ ph)
 {
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N * K; g += (long long)gridDim.x * blockDim.x) {
-        const long long k = g / N, i = g - k * N;
-        const int x = (int)(i % nx);
-        const long long row = i / nx;
-        float v = 0.f;
-        if (x >= r && (x - r) % s == 0) {
-            const float2 dv = d[k * Q + row * mx + (x - r) / s];
-            const float2 p = ph[k];
-            v = p.x * dv.x + p.y * dv.y;
-        }
-        E[g] = make_float2(v, 0.f);
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < Q * K; g += (long long)gridDim.x * blockDim.x) {
+        const float2 p = ph[g / Q], v = d[g];
+        U[g] = make_float2(p.x * v.x + p.y * v.y, 0.f);
     }
 }
 
-// V_j = sum_k conj(H_kj) E_k
-__global__ void k_gen_acc(const float2* __restrict__ H, const float2* __restrict__ E, float2* __restrict__ V,
-                          long long N, int nc, int K)
+// The adjoint of the fold.  u_k inserted at x = s i' + r (zero elsewhere)
+// has the spectrum e^{-2 pi i f r / nx} U_k(f mod mx) along x, U_k the
+// transform of u_k over the portrait grid (s / nx = 1 / mx), so
+//   V_j(f) = e^{-2 pi i f r / nx} sum_k conj(H_kj(f)) U_k(f mod mx).
+// One thread per frequency f walks the harmonics.
+__global__ void k_gen_unfold(const float2* __restrict__ H, const float2* __restrict__ U, float2* __restrict__ V,
+                             int nx, int mx, int r, int nc, int K, long long N, long long Q,
+                             const float2* __restrict__ twx)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N * nc;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long j = i / N, v = i - j * N;
-        float2 acc = make_float2(0.f, 0.f);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i % nx);
+        const long long qi = (i - f) / nx * mx + f % mx;
+        float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         for (int k = 0; k < K; ++k) {
-            const float2 h = H[((long long)k * 3 + j) * N + v];
-            acc = c_add(acc, c_mul(make_float2(h.x, -h.y), E[(long long)k * N + v]));
+            const float2 u = U[(long long)k * Q + qi];
+            const float2* __restrict__ Hk = H + (long long)k * 3 * N + i;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j < nc) {
+                    const float2 h = Hk[(long long)j * N];
+                    acc[j] = c_add(acc[j], c_mul(make_float2(h.x, -h.y), u));
+                }
+            }
         }
-        V[i] = acc;
+        const float2 tw = twx[(int)(((long long)f * r) % nx)];   // e^{-2 pi i f r / nx}
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (j < nc) V[(long long)j * N + i] = c_mul(acc[j], tw);
     }
 }
 
@@ -253,15 +391,54 @@ cudaError_t gen_set_attributes()
     return e;
 }
 
-// In-place transform of every pencil of `vols` volumes (rows of width W,
-// vstride float2 apart) along `axis`.
+// MH3D_GEN_RUNTIME=1 keeps every length on the runtime-schedule kernel.
+bool gen_runtime_only()
+{
+    const char* e = std::getenv("MH3D_GEN_RUNTIME");
+    return e && e[0] && e[0] != '0';
+}
+
+// Lengths served by the compile-time pencil kernel (and its fused modes).
+bool gen_ct_length(int n) { return (n == 128 || n == 64) && !gen_runtime_only(); }
+
+template <class L, bool INV, bool X>
+void gen_line_ct_launch(int grid, float2* v, const Pencils& g, const float2* tw, int mode, const GenIO& io,
+                        cudaStream_t st)
+{
+    if (mode == 1) k_gen_line_ct<L, INV, X, 1><<<grid, kGT, 0, st>>>(v, g, tw, io);
+    else if (mode == 2) k_gen_line_ct<L, INV, X, 2><<<grid, kGT, 0, st>>>(v, g, tw, io);
+    else if (mode == 3) k_gen_line_ct<L, INV, X, 3><<<grid, kGT, 0, st>>>(v, g, tw, io);
+    else k_gen_line_ct<L, INV, X, 0><<<grid, kGT, 0, st>>>(v, g, tw, io);
+}
+
+template <class L>
+void gen_line_ct(int grid, float2* v, const Pencils& g, const float2* tw, bool inv, int mode, const GenIO& io,
+                 cudaStream_t st)
+{
+    const bool x = g.axis == 0;
+    if (inv && x) gen_line_ct_launch<L, true, true>(grid, v, g, tw, mode, io, st);
+    else if (inv) gen_line_ct_launch<L, true, false>(grid, v, g, tw, mode, io, st);
+    else if (x) gen_line_ct_launch<L, false, true>(grid, v, g, tw, mode, io, st);
+    else gen_line_ct_launch<L, false, false>(grid, v, g, tw, mode, io, st);
+}
+
+// Transform of every pencil of `vols` volumes (rows of width W, vstride
+// float2 apart) along `axis`, in place, or with a fused step (mode, io: see
+// GenIO; modes other than 0 need gen_ct_length(ap.n)).
 cudaError_t gen_line(float2* v, int axis, int W, int ny, int nz, int vols, long long vstride, const AxisPlan& ap,
-                     bool inv, cudaStream_t st)
+                     bool inv, cudaStream_t st, int mode = 0, const GenIO& io = GenIO{})
 {
     Pencils g{axis, W, ny, nz};
     g.vols = vols;
     g.vstride = vstride;
     const long long np = g.count();
+    if (gen_ct_length(ap.n)) {
+        const int gc = (int)((np + kGPC - 1) / kGPC);
+        if (ap.n == 128) gen_line_ct<ct::RList<16, 8>>(gc, v, g, ap.tw, inv, mode, io, st);
+        else gen_line_ct<ct::RList<8, 8>>(gc, v, g, ap.tw, inv, mode, io, st);
+        return cudaGetLastError();
+    }
+    if (mode != 0) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float2) * 2 * (size_t)ap.n * kGP;
     const int grid = (int)((np + kGP - 1) / kGP);
     const bool pf = axis != 0;
@@ -273,14 +450,16 @@ cudaError_t gen_line(float2* v, int axis, int W, int ny, int nz, int vols, long 
 }
 
 // 3D transform of `count` consecutive volumes [nz][ny][W], W = the x length
-// of `axp`: three launches, each over every volume's pencils.
-cudaError_t gen_fft3(const Plan& P, float2* v, int count, const AxisPlan& axp, bool inv, cudaStream_t st)
+// of `axp`: three launches, each over every volume's pencils.  mode_x /
+// io_x fuse a load step into the x pass, mode_z a store step into the z pass.
+cudaError_t gen_fft3(const Plan& P, float2* v, int count, const AxisPlan& axp, bool inv, cudaStream_t st,
+                     int mode_x = 0, int mode_z = 0, const GenIO& io = GenIO{})
 {
     const long long vol = (long long)axp.n * P.ny * P.nz;
     cudaError_t e;
-    if ((e = gen_line(v, 0, axp.n, P.ny, P.nz, count, vol, axp, inv, st)) != cudaSuccess) return e;
+    if ((e = gen_line(v, 0, axp.n, P.ny, P.nz, count, vol, axp, inv, st, mode_x, io)) != cudaSuccess) return e;
     if ((e = gen_line(v, 1, axp.n, P.ny, P.nz, count, vol, P.ay, inv, st)) != cudaSuccess) return e;
-    return gen_line(v, 2, axp.n, P.ny, P.nz, count, vol, P.az, inv, st);
+    return gen_line(v, 2, axp.n, P.ny, P.nz, count, vol, P.az, inv, st, mode_z, io);
 }
 
 mh3d_status gen_check(Plan& P, const char* who)
@@ -322,9 +501,10 @@ mh3d_status mh3d_general_set_psf(mh3d_plan Pp, const float* h_host)
     GEN_CK(P, gen_set_attributes());
     const long long N = P.N, n3 = 3LL * P.K * N;
     if (!P.gen_H) GEN_CK(P, dev_malloc(&P.gen_H, sizeof(float2) * (size_t)n3));
-    // work area: 3 component volumes + one inserted volume per harmonic
-    if (!P.gen_work) GEN_CK(P, dev_malloc(&P.gen_work, sizeof(float2) * (size_t)((3 + P.K) * N)));
-    // the real samples are staged in the work area (>= 4N float2 >= 3N floats per harmonic)
+    // work area: 3 component volumes + one portrait-grid volume per harmonic
+    const long long Q = (long long)P.nz * P.ny * P.mx;
+    if (!P.gen_work) GEN_CK(P, dev_malloc(&P.gen_work, sizeof(float2) * (size_t)(3 * N + P.K * Q)));
+    // the real samples are staged in the work area (>= 3N float2 >= 3N floats per harmonic)
     float* stage = reinterpret_cast<float*>(P.gen_work);
     const cudaStream_t st = 0;
     for (int k = 0; k < P.K; ++k) {
@@ -355,15 +535,31 @@ mh3d_status mh3d_general_forward(mh3d_plan Pp, const float* rho, const float* bv
     const int nc = bvec ? 3 : 1;
     float2* W = P.gen_work;   // nc volumes
     float2* D = (float2*)d;   // the portrait-grid spectra, transformed and phased in place
-    k_gen_weight<<<gen_blocks(N * nc), kGB, 0, st>>>(rho, bvec, W, N, nc);
+    GenIO io;
+    io.rho = rho;
+    io.b = bvec;
+    io.ph = P.phase;
+    if (gen_ct_length(P.ax.n)) {   // b_j rho formed in the x pass's load
+        GEN_CK(P, gen_fft3(P, W, nc, P.ax, false, st, 1, 0, io));
+    } else {
+        k_gen_weight<<<gen_blocks(N * nc), kGB, 0, st>>>(rho, bvec, W, N, nc);
+        GEN_CK(P, cudaGetLastError());
+        GEN_CK(P, gen_fft3(P, W, nc, P.ax, false, st));
+    }
+    if (P.s <= 2)
+        k_gen_fold<2><<<gen_blocks(Q), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.mx, P.s, P.r, nc, P.K, N, Q, P.ax.tw);
+    else if (P.s <= 4)
+        k_gen_fold<4><<<gen_blocks(Q), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.mx, P.s, P.r, nc, P.K, N, Q, P.ax.tw);
+    else
+        k_gen_fold<0><<<gen_blocks(Q), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.mx, P.s, P.r, nc, P.K, N, Q, P.ax.tw);
     GEN_CK(P, cudaGetLastError());
-    GEN_CK(P, gen_fft3(P, W, nc, P.ax, false, st));
-    k_gen_fold<<<gen_blocks(Q * P.K), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N,
-                                                    P.ax.tw);
-    GEN_CK(P, cudaGetLastError());
-    GEN_CK(P, gen_fft3(P, D, P.K, P.am, true, st));
-    k_gen_phase<<<gen_blocks(Q * P.K), kGB, 0, st>>>(D, D, Q, P.K, P.phase);
-    GEN_CK(P, cudaGetLastError());
+    if (gen_ct_length(P.az.n)) {   // the phase applied in the z pass's store
+        GEN_CK(P, gen_fft3(P, D, P.K, P.am, true, st, 0, 2, io));
+    } else {
+        GEN_CK(P, gen_fft3(P, D, P.K, P.am, true, st));
+        k_gen_phase<<<gen_blocks(Q * P.K), kGB, 0, st>>>(D, D, Q, P.K, P.phase);
+        GEN_CK(P, cudaGetLastError());
+    }
     return MH3D_OK;
 }
 
@@ -379,11 +575,18 @@ mh3d_status mh3d_general_adjoint(mh3d_plan Pp, const void* d, const float* bvec,
     const long long N = P.N, Q = (long long)P.nz * P.ny * P.mx;
     const int nc = bvec ? 3 : 1;
     float2* V = P.gen_work;          // nc accumulators
-    float2* E = P.gen_work + 3 * N;  // the harmonics' inserted volumes
-    k_gen_insert<<<gen_blocks(N * P.K), kGB, 0, st>>>((const float2*)d, E, P.nx, P.mx, P.s, P.r, N, Q, P.K, P.phase);
-    GEN_CK(P, cudaGetLastError());
-    GEN_CK(P, gen_fft3(P, E, P.K, P.ax, false, st));
-    k_gen_acc<<<gen_blocks(N * nc), kGB, 0, st>>>(P.gen_H, E, V, N, nc, P.K);
+    float2* U = P.gen_work + 3 * N;  // the harmonics' real portrait images, then their spectra
+    if (gen_ct_length(P.am.n)) {   // u_k formed in the x pass's load
+        GenIO io;
+        io.src = (const float2*)d;
+        io.ph = P.phase;
+        GEN_CK(P, gen_fft3(P, U, P.K, P.am, false, st, 3, 0, io));
+    } else {
+        k_gen_unphase<<<gen_blocks(Q * P.K), kGB, 0, st>>>((const float2*)d, U, Q, P.K, P.phase);
+        GEN_CK(P, cudaGetLastError());
+        GEN_CK(P, gen_fft3(P, U, P.K, P.am, false, st));
+    }
+    k_gen_unfold<<<gen_blocks(N), kGB, 0, st>>>(P.gen_H, U, V, P.nx, P.mx, P.r, nc, P.K, N, Q, P.ax.tw);
     GEN_CK(P, cudaGetLastError());
     GEN_CK(P, gen_fft3(P, V, nc, P.ax, true, st));
     k_gen_out<<<gen_blocks(N), kGB, 0, st>>>(V, bvec, out, N, nc);

@@ -19,6 +19,14 @@ CASES = {
     "s2_r1_vector_b": (dict(n=(16, 8, 8), s=2, r=1, kmin=2, kmax=5), True),
     "s1_drive_b": (dict(n=(24, 12, 8), s=1, r=0, kmin=2, kmax=4), False),
     "s2_r0_vector_b": (dict(n=(32, 16, 8), s=2, r=0, kmin=2, kmax=6), True),
+    # s = 3 (the fold's s <= 4 register form) and s = 6 (its any-s form)
+    "s3_r2_vector_b": (dict(n=(24, 8, 6), s=3, r=2, kmin=2, kmax=4), True),
+    "s6_r5_drive_b": (dict(n=(36, 8, 4), s=6, r=5, kmin=2, kmax=3), False),
+    # lengths 128 and 64 on the compile-time pencil kernel: x (b_j rho fused
+    # in its load), y and the portrait x (the unphasing fused); then z (the
+    # phase fused in its store)
+    "ct_lengths_vector_b": (dict(n=(128, 64, 8), s=2, r=1, kmin=2, kmax=5), True),
+    "ct_z64_drive_b": (dict(n=(16, 8, 64), s=2, r=0, kmin=2, kmax=4), False),
 }
 
 
