@@ -157,7 +157,8 @@ struct Plan {
     double* mhad_red = nullptr;
 
     // general model (general.cu): PSF spectra DFT(h_kj)/N [K][3][N] and a
-    // work area of (3 + K) N complex values, allocated by mh3d_general_set_psf
+    // work area of 3 N + K n_z n_y m_x complex values, allocated by
+    // mh3d_general_set_psf
     float2* gen_H = nullptr;
     float2* gen_work = nullptr;
 

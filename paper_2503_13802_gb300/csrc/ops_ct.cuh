@@ -104,8 +104,7 @@ __global__ void __launch_bounds__(TT) k_tpass_ct(const __grid_constant__ TArgs a
     __shared__ __align__(8) uint64_t bar;
     __shared__ float cgs[3];
     float beta = 0.f, alpha = 0.f;
-    pdl_trigger();
-    pdl_wait();   // no-ops unless launched with programmatic serialization
+    pdl_wait();   // a no-op unless launched with programmatic serialization
     if (a.cg.flags && !cg_enter_cta(a.cg, a.pupdate != 0, &beta, &alpha, cgs)) return;
     // 128-byte aligned start for the TMA boxes (the launcher adds the slack)
     float2* sm = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
@@ -266,6 +265,9 @@ __global__ void __launch_bounds__(TT) k_tpass_ct(const __grid_constant__ TArgs a
     }
     fence_proxy_async_smem();
     __syncthreads();
+    // a dependent launch may now be scheduled; it reads nothing of this
+    // kernel's before its griddepcontrol.wait (the whole grid's completion)
+    pdl_trigger();
     if (threadIdx.x == 0) {
         tma_store_3d(&a.tm.m[kTmOut], x0, cy, cz, stg);
         bulk_commit();
@@ -1076,6 +1078,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(TT) k_zxnrm_ct(const
     float2* un = sm + G::OFF;           // 128-byte aligned: the TMA box lands at its start
     const uint32_t rank = cluster_ctarank();
     const int y = (int)blockIdx.x / C;
+    pdl_wait();   // a no-op unless launched with programmatic serialization
     // every CTA of the cluster is running before any of them stores remotely
     cluster_sync_all();
     float dummy;
