@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/mh3d_unet.h"
+#include "umma_conv.cuh"
 #include "unet_kernels.cuh"
 
 namespace mh3d {
@@ -27,8 +28,17 @@ bool tiles_disabled()
 int tile_n(int n) { return n <= 16 ? 16 : (n <= 32 ? 32 : 64); }
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Weights of one convolution in the tcgen05 kernel's B-operand layout
+// ([27][c8p][np][8] bfloat16, umma_conv.cuh); w null: that kernel is not
+// used for it.
+struct UmmaW {
+    __nv_bfloat16* w = nullptr;
+    int c8p = 0, np = 0;
+};
+
 struct Layer {
     int cin = 0, cout = 0;
+    UmmaW uf, ub;                   // forward and input-gradient operands of the tcgen05 kernel
     long long woff = 0, boff = 0;   // offsets of W [cout][27][cin] and b [cout] in theta
     int Kf = 0, Nf = 0;             // forward matrix [Kf][Nf]
     int Kb = 0, Nb = 0;             // input-gradient matrix [Kb][Nb]
@@ -59,6 +69,7 @@ struct Net {
     __nv_bfloat16 *gd1 = nullptr, *gs1 = nullptr, *gupb = nullptr, *ge1 = nullptr, *ge1a = nullptr, *gp0 = nullptr;
     __nv_bfloat16 *gb = nullptr, *gba = nullptr, *gp1 = nullptr, *scratch = nullptr;
     float *wpart = nullptr, *bpart = nullptr;
+    int* status = nullptr;           // device word: MH3D_ERR_TIMEOUT from a bounded wait, else 0
     double* lpart = nullptr;
     double* lhost = nullptr;
     size_t wpart_n = 0, bpart_n = 0;
@@ -166,11 +177,142 @@ bool tile_conv_n(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, 
     return tile_conv<C, 64>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, err);
 }
 
+// ---- the tcgen05 convolution (umma_conv.cuh) --------------------------------
+
+// Chunk planes (8 channels each, padded to an even count) of a source the
+// tcgen05 kernel takes: the FP32 single-channel input, or 8..32 bfloat16
+// channels in multiples of 8; 0 otherwise.
+int umma_c8p(int Cs, bool f32)
+{
+    if (f32) return Cs == 1 ? 2 : 0;
+    if (Cs < 8 || Cs > 32 || Cs % 8 != 0) return 0;
+    return (Cs / 8 + 1) / 2 * 2;
+}
+// Accumulator columns for N output channels (a multiple of 16), 0 past 64.
+int umma_np(int N) { return N <= 16 ? 16 : (N <= 32 ? 32 : (N <= 64 ? 64 : 0)); }
+
+// Which convolutions run on the tcgen05 kernel.  By default those with a
+// bfloat16 source whose rows fill most of a 128-voxel tile (W >= 96): per
+// launch at 128x128x64, channels (8, 16, 32), L2 flushed, it takes the
+// full-resolution layers in 69 (8 -> 8), 69 (upsampled 16 -> 8), 93 (skip
+// sum 8 -> 8) and 62 us (8 -> 1, FP32 out) against 90, 158, 99 and 89 us on
+// the mma.sync tiles, while the half- and quarter-resolution layers (rows
+// of 64 and 32 voxels in a 128-lane accumulator: 22-29 against 10-23 us)
+// and the single-channel FP32 input layer (70 against 62 us, where the
+// mma.sync kernel packs the 27 taps into K) stay on mma.sync.
+// MH3D_UNET_UMMA=1 sends every convolution it can take to the tcgen05
+// kernel, 0 none.
+int umma_mode()
+{
+    const char* e = std::getenv("MH3D_UNET_UMMA");
+    if (e && e[0] == '0') return 0;
+    if (e && e[0] == '1') return 2;
+    return 1;
+}
+bool umma_enabled() { return umma_mode() != 0; }
+bool umma_prefers(const ConvSrc& s) { return umma_mode() == 2 || (!s.f32 && s.W >= 96); }
+
+template <int C8P, int NP, int NB, class OutT>
+cudaError_t launch_umma_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, const float* bias, int relu,
+                          const float* oscale, OutT* out, int* status, cudaStream_t st)
+{
+    using G = umma::Geom<C8P, NP, NB>;
+    auto* fn = umma::k_conv_umma<C8P, NP, NB, OutT>;
+    const size_t smem = G::smem();
+    if (smem > (size_t)smem_optin()) return cudaErrorInvalidValue;
+    static int occ = 0;   // resident CTAs per SM, with the attributes set (once)
+    if (occ == 0) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // the whole carveout to shared memory, so that several CTAs fit
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        // resident CTAs per SM from the shared memory (each CTA also reserves
+        // 1 KB), the registers and the threads; every resident CTA holds
+        // G::kCols of the SM's 512 TMEM columns
+        int dev = 0, smem_sm = 0, regs_sm = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+            return cudaErrorInvalidValue;
+        const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+        const int by_regs = regs_sm / std::max(1, fa.numRegs * umma::kT);
+        occ = std::max(1, std::min(std::min(by_smem, by_regs), std::min(2048 / umma::kT, 512 / G::kCols)));
+    }
+    const long long tiles = (long long)((s.W + umma::kM - 1) / umma::kM) * s.H * s.D;
+    if (tiles > (1LL << 30)) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long long>(tiles, (long long)num_sms() * occ);
+    fn<<<grid, umma::kT, smem, st>>>(s, Wu, N, bias, relu, oscale, out, (int)tiles, status);
+    return cudaGetLastError();
+}
+
+// One halo buffer and accumulator per CTA, several CTAs per SM (the
+// default), or two per CTA with the next tile staged during this tile's
+// MMAs (MH3D_UMMA_NB=2, where it fits).  Measured at 128x128x64 (network
+// forward, channels (8, 16, 32)): 0.576 ms with one, 0.847 ms with two
+// (half the resident CTAs).
+template <int C8P, int NP, class OutT>
+cudaError_t launch_umma_nb(const ConvSrc& s, const UmmaW& u, int N, const float* bias, int relu, const float* oscale,
+                           OutT* out, int* status, cudaStream_t st)
+{
+    const char* e = std::getenv("MH3D_UMMA_NB");
+    const bool two = e && e[0] == '2';
+    if (two && umma::Geom<C8P, NP, 2>::smem() <= (size_t)smem_optin())
+        return launch_umma_t<C8P, NP, 2>(s, u.w, N, bias, relu, oscale, out, status, st);
+    return launch_umma_t<C8P, NP, 1>(s, u.w, N, bias, relu, oscale, out, status, st);
+}
+
+template <int C8P, class OutT>
+cudaError_t launch_umma_np(const ConvSrc& s, const UmmaW& u, int N, const float* bias, int relu, const float* oscale,
+                           OutT* out, int* status, cudaStream_t st)
+{
+    if (u.np == 16) return launch_umma_nb<C8P, 16>(s, u, N, bias, relu, oscale, out, status, st);
+    if (u.np == 32) return launch_umma_nb<C8P, 32>(s, u, N, bias, relu, oscale, out, status, st);
+    return launch_umma_nb<C8P, 64>(s, u, N, bias, relu, oscale, out, status, st);
+}
+
+// Whether the tcgen05 kernel runs this convolution (its operands prepared,
+// the source of a form it stages, not switched off).
+bool umma_takes(const ConvSrc& s, const UmmaW* u, int N)
+{
+    return u && u->w && umma_enabled() && umma_prefers(s) && u->c8p == umma_c8p(s.C, s.f32 != nullptr) &&
+           u->np == umma_np(N) && u->np > 0 && !(s.b && s.up);
+}
+
+template <class OutT>
+cudaError_t launch_umma(const ConvSrc& s, const UmmaW& u, int N, const float* bias, int relu, const float* oscale,
+                        OutT* out, int* status, cudaStream_t st)
+{
+    if (u.c8p == 2) return launch_umma_np<2>(s, u, N, bias, relu, oscale, out, status, st);
+    return launch_umma_np<4>(s, u, N, bias, relu, oscale, out, status, st);
+}
+
+// Builds the tcgen05 operand of a convolution from its implicit-GEMM
+// matrix Wt [Kpad][Npad] (source channels Cs, N outputs); allocates u.w
+// unless given.
+cudaError_t prep_umma(const __nv_bfloat16* Wt, int Npad, int Cs, bool f32, int N, UmmaW& u, cudaStream_t st)
+{
+    u.c8p = umma_c8p(Cs, f32);
+    u.np = umma_np(N);
+    if (!u.c8p || !u.np || !u.w) return cudaSuccess;
+    const int total = 27 * u.c8p * u.np * 8;
+    umma::k_prep_umma<<<blocks_for(total, 256), 256, 0, st>>>(Wt, Npad, Cs, N, u.c8p, u.np, u.w);
+    return cudaGetLastError();
+}
+size_t umma_elems(int Cs, bool f32, int N)
+{
+    const int c = umma_c8p(Cs, f32), np = umma_np(N);
+    return (c && np) ? (size_t)27 * c * np * 8 : 0;
+}
+
 template <class OutT>
 cudaError_t launch_conv(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, int N, const float* bias,
-                        int relu, OutT* out, cudaStream_t st, const float* oscale = nullptr)
+                        int relu, OutT* out, cudaStream_t st, const float* oscale = nullptr,
+                        const UmmaW* uw = nullptr, int* status = nullptr)
 {
     cudaError_t e = cudaSuccess;
+    if (umma_takes(s, uw, N)) return launch_umma(s, *uw, N, bias, relu, oscale, out, status, st);
     bool done = false;
     if (!tiles_disabled()) {
         if (s.C == 1)
@@ -246,6 +388,9 @@ mh3d_status prep_weights(Net& n, cudaStream_t st)
                                                                                 l.Kf, l.Nf, 0, l.Wf);
         k_prep_weights<<<blocks_for((long long)l.Kb * l.Nb, 256), 256, 0, st>>>(n.theta + l.woff, l.cin, l.cout,
                                                                                 l.Kb, l.Nb, 1, l.Wb);
+        const bool f32in = &l == &n.L[0];   // the network input: one FP32 channel
+        UN_CK(n, prep_umma(l.Wf, l.Nf, l.cin, f32in, l.cout, l.uf, st));
+        UN_CK(n, prep_umma(l.Wb, l.Nb, l.cout, false, l.cin, l.ub, st));
     }
     UN_CK(n, cudaGetLastError());
     n.weights_ready = true;
@@ -257,7 +402,7 @@ cudaError_t fwd(const Net& n, int li, const ConvSrc& s, int relu, OutT* out, cud
                 const float* oscale = nullptr)
 {
     const Layer& l = n.L[li];
-    return launch_conv(s, l.Wf, l.Kf, l.Nf, l.cout, n.theta + l.boff, relu, out, st, oscale);
+    return launch_conv(s, l.Wf, l.Kf, l.Nf, l.cout, n.theta + l.boff, relu, out, st, oscale, &l.uf, n.status);
 }
 
 // iscale / oscale: device scalars multiplying the input and the output
@@ -308,7 +453,8 @@ mh3d_status back_layer(Net& n, int li, const ConvSrc& s, const __nv_bfloat16* g,
     if (gin) {
         ConvSrc sg = src_of(g, s.D, s.H, s.W, l.cout);
         sg.flip = 1;
-        UN_CK(n, launch_conv(sg, l.Wb, l.Kb, l.Nb, l.cin, (const float*)nullptr, 0, gin, st));
+        UN_CK(n, launch_conv(sg, l.Wb, l.Kb, l.Nb, l.cin, (const float*)nullptr, 0, gin, st, nullptr, &l.ub,
+                             n.status));
     }
     return MH3D_OK;
 }
@@ -421,7 +567,13 @@ mh3d_status mh3d_unet_create(int nx, int ny, int nz, int c0, int c1, int c2, mh3
     for (Layer& l : n->L) {
         A(&l.Wf, (size_t)l.Kf * l.Nf);
         A(&l.Wb, (size_t)l.Kb * l.Nb);
+        const bool f32in = &l == &n->L[0];
+        const size_t ef = umma_elems(l.cin, f32in, l.cout), eb = umma_elems(l.cout, false, l.cin);
+        if (ef) A(&l.uf.w, ef);
+        if (eb) A(&l.ub.w, eb);
     }
+    A(&n->status, 1);
+    if (ok && cudaMemset(n->status, 0, sizeof(int)) != cudaSuccess) ok = false;
     const size_t V0 = n->V0, V1 = n->V1, V2 = n->V2;
     A(&n->e0a, V0 * c0);
     A(&n->e0, V0 * c0);
@@ -528,6 +680,12 @@ static mh3d_status loss_grad_impl(mh3d_unet n, const float* in, const float* tar
         double L = 0.0;
         for (int i = 0; i < n->lblocks; ++i) L += n->lhost[i];
         *loss = L;
+        int dst = 0;   // a bounded wait of the tcgen05 convolutions that ran out
+        UN_CK(*n, cudaMemcpy(&dst, n->status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (dst != 0) {
+            n->err = "tensor-core convolution: bounded wait expired";
+            return MH3D_ERR_TIMEOUT;
+        }
     }
     return MH3D_OK;
 }
@@ -631,11 +789,19 @@ struct Tmp {
     ~Tmp() { if (p) cudaFree(p); }
 };
 
-mh3d_status finish(cudaStream_t st)
+// Synchronises; with a device status word, reports a bounded wait that
+// ran out (MH3D_ERR_TIMEOUT).
+mh3d_status finish(cudaStream_t st, const int* status = nullptr)
 {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? MH3D_OK : MH3D_ERR_CUDA;
+    if (e != cudaSuccess) return MH3D_ERR_CUDA;
+    if (status) {
+        int h = 0;
+        if (cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MH3D_ERR_CUDA;
+        if (h != 0) return MH3D_ERR_TIMEOUT;
+    }
+    return MH3D_OK;
 }
 
 }  // namespace
@@ -652,9 +818,19 @@ mh3d_status mh3d_unet_conv_forward(const mh3d_unet_conv_desc* c, const float* W,
     if (!wt.p) return MH3D_ERR_OOM;
     k_prep_weights<<<blocks_for((long long)K * Np, 256), 256, 0, st>>>(W, c->cin, c->cout, K, Np, 0,
                                                                        (__nv_bfloat16*)wt.p);
-    if (launch_conv(src_from(c), (const __nv_bfloat16*)wt.p, K, Np, c->cout, b, relu, out, st) != cudaSuccess)
+    const ConvSrc s = src_from(c);
+    const size_t ue = umma_elems(s.C, s.f32 != nullptr, c->cout);
+    Tmp uw(sizeof(__nv_bfloat16) * std::max<size_t>(ue, 1)), stat(sizeof(int));
+    if (!uw.p || !stat.p) return MH3D_ERR_OOM;
+    UmmaW u;
+    u.w = ue ? (__nv_bfloat16*)uw.p : nullptr;
+    if (prep_umma((const __nv_bfloat16*)wt.p, Np, s.C, s.f32 != nullptr, c->cout, u, st) != cudaSuccess ||
+        cudaMemsetAsync(stat.p, 0, sizeof(int), st) != cudaSuccess)
         return MH3D_ERR_CUDA;
-    return finish(st);
+    if (launch_conv(s, (const __nv_bfloat16*)wt.p, K, Np, c->cout, b, relu, out, st, nullptr, &u, (int*)stat.p) !=
+        cudaSuccess)
+        return MH3D_ERR_CUDA;
+    return finish(st, (int*)stat.p);
 }
 
 mh3d_status mh3d_unet_conv_input_grad(const mh3d_unet_conv_desc* c, const void* g, const float* W, float* gin,
@@ -676,9 +852,18 @@ mh3d_status mh3d_unet_conv_input_grad(const mh3d_unet_conv_desc* c, const void* 
     s.W = c->nx;
     s.C = c->cout;
     s.flip = 1;
-    if (launch_conv(s, (const __nv_bfloat16*)wt.p, K, Np, c->cin, (const float*)nullptr, 0, gin, st) != cudaSuccess)
+    const size_t ue = umma_elems(s.C, false, c->cin);
+    Tmp uw(sizeof(__nv_bfloat16) * std::max<size_t>(ue, 1)), stat(sizeof(int));
+    if (!uw.p || !stat.p) return MH3D_ERR_OOM;
+    UmmaW u;
+    u.w = ue ? (__nv_bfloat16*)uw.p : nullptr;
+    if (prep_umma((const __nv_bfloat16*)wt.p, Np, s.C, false, c->cin, u, st) != cudaSuccess ||
+        cudaMemsetAsync(stat.p, 0, sizeof(int), st) != cudaSuccess)
         return MH3D_ERR_CUDA;
-    return finish(st);
+    if (launch_conv(s, (const __nv_bfloat16*)wt.p, K, Np, c->cin, (const float*)nullptr, 0, gin, st, nullptr, &u,
+                    (int*)stat.p) != cudaSuccess)
+        return MH3D_ERR_CUDA;
+    return finish(st, (int*)stat.p);
 }
 
 mh3d_status mh3d_unet_conv_weight_grad(const mh3d_unet_conv_desc* c, const void* g, float* gW, float* gb,

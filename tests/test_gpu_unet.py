@@ -27,14 +27,25 @@ torch = pytest.importorskip("torch")
 N_SMALL = (14, 10, 6)   # nx, ny, nz: V = 840, not a multiple of the 128-voxel tile; partial 8x4x4 blocks
 
 
-@pytest.fixture(params=["tiled", "gather"], autouse=True)
+@pytest.fixture(params=["umma", "umma_nb2", "default", "tiled", "gather"], autouse=True)
 def conv_path(request, monkeypatch):
-    """Every test runs on the halo-tiled convolution (the default) and again
-    with MH3D_UNET_GATHER=1, which forces the gather kernel."""
-    if request.param == "gather":
-        monkeypatch.setenv("MH3D_UNET_GATHER", "1")
-    else:
-        monkeypatch.delenv("MH3D_UNET_GATHER", raising=False)
+    """Every test runs with every convolution the tcgen05/TMEM kernel takes
+    on it (MH3D_UNET_UMMA=1: the FP32 input, 8..32 bfloat16 channels in
+    multiples of 8, up to 64 outputs; the others go to the mma.sync
+    kernels), on its double-buffered form (MH3D_UMMA_NB=2), with the default
+    choice (tcgen05 for bfloat16 sources with rows of 96 voxels or more), on
+    the halo-tiled mma.sync kernel alone (MH3D_UNET_UMMA=0) and on the
+    gather kernel (MH3D_UNET_UMMA=0, MH3D_UNET_GATHER=1)."""
+    for v in ("MH3D_UNET_GATHER", "MH3D_UNET_UMMA", "MH3D_UMMA_NB"):
+        monkeypatch.delenv(v, raising=False)
+    if request.param in ("umma", "umma_nb2"):
+        monkeypatch.setenv("MH3D_UNET_UMMA", "1")
+        if request.param == "umma_nb2":
+            monkeypatch.setenv("MH3D_UMMA_NB", "2")
+    elif request.param in ("tiled", "gather"):
+        monkeypatch.setenv("MH3D_UNET_UMMA", "0")
+        if request.param == "gather":
+            monkeypatch.setenv("MH3D_UNET_GATHER", "1")
     return request.param
 
 
@@ -102,7 +113,26 @@ def test_conv_forward_matches_oracle(cin, cout, mode, relu):
     assert rel_l2(got, ref) <= 1e-5, rel_l2(got, ref)
 
 
-@pytest.mark.parametrize("cin,cout", [(1, 16), (16, 16), (16, 32), (64, 32), (16, 1), (12, 16)])
+@pytest.mark.parametrize("n,cin,cout,mode", [
+    ((136, 6, 4), 16, 16, "plain"),   # two 128-voxel x tiles, the second ragged
+    ((130, 4, 4), 32, 48, "skip"),    # 48 outputs in 64 accumulator columns
+    ((128, 6, 4), 1, 16, "f32"),
+    ((260, 4, 2), 8, 8, "up"),        # three x tiles, upsampled source
+])
+def test_conv_forward_multi_tile_rows(n, cin, cout, mode):
+    """Rows longer than one 128-voxel tile, with ragged last tiles."""
+    from paper_2503_13802_gb300.unet import mh3d_unet_conv_forward
+
+    kw, x = _sources(n, cin, mode, 3 * cin + cout)
+    W, b = _w(cout, cin, cin * 5 + cout)
+    out = torch.empty(n[2] * n[1] * n[0] * cout, dtype=torch.float32, device="cuda")
+    mh3d_unet_conv_forward(n, cin, cout, W.cuda(), b.cuda(), out, relu=True, **kw)
+    ref = U.relu(U.conv(x, _np(W).reshape(cout, 3, 3, 3, cin), _np(b)))
+    got = out.cpu().numpy().reshape(ref.shape)
+    assert rel_l2(got, ref) <= 1e-5, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("cin,cout", [(1, 16), (16, 16), (16, 32), (64, 32), (16, 1), (12, 16), (32, 8)])
 def test_conv_input_grad_matches_oracle(cin, cout):
     from paper_2503_13802_gb300.unet import mh3d_unet_conv_input_grad
 
