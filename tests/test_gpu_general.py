@@ -45,8 +45,16 @@ def _plan(c, theta):
     return Plan(c["n"], ds_factor=c["s"], ds_offset=c["r"], k_min=c["kmin"], k_max=c["kmax"], theta=theta)
 
 
+@pytest.mark.parametrize("kernels", ["default", "runtime"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_general_forward_and_adjoint_match_oracle(name):
+def test_general_forward_and_adjoint_match_oracle(name, kernels, monkeypatch):
+    """kernels = runtime: every pencil pass on the runtime-schedule kernel
+    (MH3D_GEN_RUNTIME=1), the weighting, phase and unphasing as separate
+    kernels."""
+    if kernels == "runtime":
+        monkeypatch.setenv("MH3D_GEN_RUNTIME", "1")
+    else:
+        monkeypatch.delenv("MH3D_GEN_RUNTIME", raising=False)
     from paper_2503_13802_gb300 import mh3d_general_adjoint, mh3d_general_forward, mh3d_general_set_psf
 
     c, use_b = CASES[name]
