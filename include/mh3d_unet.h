@@ -8,24 +8,36 @@
  * which CG starts (mh3d_solve_opts.x0_dev).  The paper has no counterpart;
  * its architecture, loss and training recipe are this library's.
  *
- * Network (channels c0, c1, c2 at full, half and quarter resolution):
+ * Network (L levels, channels C_0 .. C_{L-1}; level l at 1 / 2^l of the
+ * resolution).  For L = 3 (c0, c1, c2):
  *   e0a = relu(conv(in, W0a)); e0 = relu(conv(e0a, W0b))
  *   e1a = relu(conv(pool(e0), W1a)); e1 = relu(conv(e1a, W1b))
  *   ba = relu(conv(pool(e1), W2a)); b = relu(conv(ba, W2b))
  *   u1 = relu(conv(up(b), W3a)); d1 = relu(conv(u1 + e1, W3b))
  *   u0 = relu(conv(up(d1), W4a)); d0 = relu(conv(u0 + e0, W4b))
  *   out = conv(d0, W5)
+ * In general: encoder levels l = 0 .. L-1 (W{l}a on the input, or on
+ * pool(e_{l-1}); W{l}b), the last one the bottleneck; decoder levels
+ * l = L-2 .. 0 (W{2L-2-l}a on up(d_{l+1}), W{2L-2-l}b on u_l + e_l; the
+ * bottleneck's e is its d); out = conv(d0, W{2L-1}): 4 L - 1 convolutions.
  * conv: 3x3x3 cross-correlation, zero padding, bias; pool: 2x2x2 mean;
  * up: nearest x2.  Arithmetic: bfloat16 operands on the tensor cores with
  * FP32 accumulation; activations stored as bfloat16 (channels last); the
  * input and the output are FP32.
  *
  * Parameters: one flat FP32 vector; per layer in the order above
- * (W0a, W0b, W1a, W1b, W2a, W2b, W3a, W3b, W4a, W4b, W5): W as
+ * (L = 3: W0a, W0b, W1a, W1b, W2a, W2b, W3a, W3b, W4a, W4b, W5): W as
  * [cout][3][3][3][cin] (taps dz, dy, dx), then b [cout].
  * Loss of mh3d_unet_loss_grad: sum((out - target)^2) / (2 V).
  *
- * Sizes: nx, ny, nz multiples of 4; c0, c1, c2 in 1..64.  Volumes are
+ * The convolutions run on the tcgen05 tensor cores (accumulators in tensor
+ * memory) where the source is bfloat16 with 8..32 channels in multiples of
+ * 8, at most 64 outputs, and rows of 96 voxels or more; on mma.sync tiles
+ * otherwise.  MH3D_UNET_UMMA=0 / 1 sends none / every convolution it can
+ * take to the tcgen05 kernel.
+ *
+ * Sizes: nx, ny, nz multiples of 2^(L-1) (4 for mh3d_unet_create); channels
+ * in 1..64 (mh3d_unet_create) or 1..128 (mh3d_unet_create_levels).  Volumes are
  * C-order [nz][ny][nx].  All pointers are device pointers unless stated;
  * calls are asynchronous on `stream` unless stated.  Errors are status
  * codes (mh3d.h) with text from mh3d_unet_last_error.
@@ -41,13 +53,19 @@ extern "C" {
 
 typedef struct mh3d_unet_s* mh3d_unet;
 
-/* Number of parameters of a network with channels c0, c1, c2. */
+/* Number of parameters of a network with channels c0, c1, c2 (three
+ * levels), or with `levels` levels (2..5) of channels[0 .. levels-1]
+ * (-1 for a bad level count or a null pointer). */
 long long mh3d_unet_param_count(int c0, int c1, int c2);
+long long mh3d_unet_param_count_levels(int levels, const int* channels);
 
 /* Allocates a network for volumes of nx x ny x nz voxels: parameters (set
  * them with mh3d_unet_set_params before use), Adam state, activations and
  * gradient buffers.  MH3D_ERR_INVALID_ARG for bad sizes, MH3D_ERR_OOM. */
 mh3d_status mh3d_unet_create(int nx, int ny, int nz, int c0, int c1, int c2, mh3d_unet* out);
+/* The same for `levels` levels (2..5) with channels[0 .. levels-1] (host
+ * array, 1..128 each); nx, ny, nz multiples of 2^(levels-1). */
+mh3d_status mh3d_unet_create_levels(int nx, int ny, int nz, int levels, const int* channels, mh3d_unet* out);
 mh3d_status mh3d_unet_destroy(mh3d_unet net);
 
 /* Copies param_count floats in (and resets the Adam state) / out. */

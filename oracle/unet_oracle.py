@@ -3,8 +3,9 @@ infrastructure only: imported by tests/ and the benchmark's CPU leg, never
 by the product library).
 
 The network maps the normalised back-projection A^T d (one channel) to a
-warm start for CG.  It is a small 3D U-Net with additive skips, written out
-layer by layer with numpy so a reader can check it by eye:
+warm start for CG.  It is a small 3D U-Net with additive skips of L levels
+(channels C_0 .. C_{L-1}, L >= 2), written out layer by layer with numpy so
+a reader can check it by eye.  For L = 3:
 
     e0a = relu(conv(in,        W0a))      C0 channels, full resolution
     e0  = relu(conv(e0a,       W0b))      C0            (skip 0)
@@ -17,6 +18,11 @@ layer by layer with numpy so a reader can check it by eye:
     u0  = relu(conv(up(d1),    W4a))      C0, full
     d0  = relu(conv(u0 + e0,   W4b))      C0
     out = conv(d0, W5)                    1 channel, no activation
+
+In general: encoder levels l = 0 .. L-1 (W{l}a, W{l}b; the input of level
+l > 0 is pool(e_{l-1}), the last level is the bottleneck), decoder levels
+l = L-2 .. 0 (W{2L-2-l}a on up(d_{l+1}), d_{L-1} = the bottleneck output,
+and W{2L-2-l}b on u_l + e_l), then W{2L-1} to one channel.
 
 conv: 3x3x3 cross-correlation with zero padding ("same"), weights
 [Cout][3][3][3][Cin] (taps ordered dz, dy, dx), plus a bias per output
@@ -36,22 +42,30 @@ import numpy as np
 LAYERS = ("W0a", "W0b", "W1a", "W1b", "W2a", "W2b", "W3a", "W3b", "W4a", "W4b", "W5")
 
 
-def layer_shapes(c0: int, c1: int, c2: int):
-    """(name, Cin, Cout) of every convolution, in parameter order."""
-    return [("W0a", 1, c0), ("W0b", c0, c0), ("W1a", c0, c1), ("W1b", c1, c1), ("W2a", c1, c2),
-            ("W2b", c2, c2), ("W3a", c2, c1), ("W3b", c1, c1), ("W4a", c1, c0), ("W4b", c0, c0),
-            ("W5", c0, 1)]
+def layer_shapes(*ch: int):
+    """(name, Cin, Cout) of every convolution, in parameter order, for the
+    network with channels ch = (C_0, .., C_{L-1})."""
+    L = len(ch)
+    assert L >= 2
+    out = []
+    for l in range(L):
+        out += [(f"W{l}a", 1 if l == 0 else ch[l - 1], ch[l]), (f"W{l}b", ch[l], ch[l])]
+    for l in range(L - 2, -1, -1):
+        i = 2 * L - 2 - l
+        out += [(f"W{i}a", ch[l + 1], ch[l]), (f"W{i}b", ch[l], ch[l])]
+    out.append((f"W{2 * L - 1}", ch[0], 1))
+    return out
 
 
-def param_count(c0: int, c1: int, c2: int) -> int:
-    return sum(co * 27 * ci + co for _, ci, co in layer_shapes(c0, c1, c2))
+def param_count(*ch: int) -> int:
+    return sum(co * 27 * ci + co for _, ci, co in layer_shapes(*ch))
 
 
-def unflatten(theta: np.ndarray, c0: int, c1: int, c2: int) -> dict:
+def unflatten(theta: np.ndarray, *ch: int) -> dict:
     """Flat parameter vector -> {name: (W [Cout,3,3,3,Cin], b [Cout])}.
     Layout: per layer in order, W row-major then b."""
     out, o = {}, 0
-    for name, ci, co in layer_shapes(c0, c1, c2):
+    for name, ci, co in layer_shapes(*ch):
         n = co * 27 * ci
         W = np.asarray(theta[o:o + n], dtype=np.float64).reshape(co, 3, 3, 3, ci)
         o += n
@@ -62,9 +76,9 @@ def unflatten(theta: np.ndarray, c0: int, c1: int, c2: int) -> dict:
     return out
 
 
-def flatten(grads: dict, c0: int, c1: int, c2: int) -> np.ndarray:
+def flatten(grads: dict, *ch: int) -> np.ndarray:
     parts = []
-    for name, _, _ in layer_shapes(c0, c1, c2):
+    for name, _, _ in layer_shapes(*ch):
         gW, gb = grads[name]
         parts += [gW.ravel(), gb.ravel()]
     return np.concatenate(parts)
@@ -142,29 +156,35 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def _levels(params: dict) -> int:
+    """L from the parameter names: 4 L - 1 convolutions."""
+    n = len(params)
+    assert (n + 1) % 4 == 0, n
+    return (n + 1) // 4
+
+
 def forward(params: dict, inp: np.ndarray, bf16: bool = False):
-    """inp: [D, H, W] float.  Returns (out [D, H, W], cache of activations)."""
+    """inp: [D, H, W] float.  Returns (out [D, H, W], cache of activations).
+    The number of levels follows from the parameters."""
     r = bf16_round if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     P = {k: (r(W), np.asarray(b, dtype=np.float64)) for k, (W, b) in params.items()}
-    c = {}
-    c["in"] = r(inp)[..., None]
-    c["e0a"] = r(relu(conv(c["in"], *P["W0a"])))
-    c["e0"] = r(relu(conv(c["e0a"], *P["W0b"])))
-    c["p0"] = r(pool(c["e0"]))
-    c["e1a"] = r(relu(conv(c["p0"], *P["W1a"])))
-    c["e1"] = r(relu(conv(c["e1a"], *P["W1b"])))
-    c["p1"] = r(pool(c["e1"]))
-    c["ba"] = r(relu(conv(c["p1"], *P["W2a"])))
-    c["b"] = r(relu(conv(c["ba"], *P["W2b"])))
-    c["ub"] = up(c["b"])
-    c["u1"] = r(relu(conv(c["ub"], *P["W3a"])))
-    c["s1"] = r(c["u1"] + c["e1"])
-    c["d1"] = r(relu(conv(c["s1"], *P["W3b"])))
-    c["ud1"] = up(c["d1"])
-    c["u0"] = r(relu(conv(c["ud1"], *P["W4a"])))
-    c["s0"] = r(c["u0"] + c["e0"])
-    c["d0"] = r(relu(conv(c["s0"], *P["W4b"])))
-    out = conv(c["d0"], *P["W5"])[..., 0]
+    L = _levels(P)
+    c = {"in": r(inp)[..., None]}
+    x = c["in"]
+    for l in range(L):                       # encoder; level L-1 is the bottleneck
+        if l > 0:
+            x = c[f"p{l - 1}"] = r(pool(c[f"e{l - 1}"]))
+        c[f"x{l}"] = x
+        c[f"e{l}a"] = r(relu(conv(x, *P[f"W{l}a"])))
+        c[f"e{l}"] = r(relu(conv(c[f"e{l}a"], *P[f"W{l}b"])))
+    c[f"d{L - 1}"] = c[f"e{L - 1}"]
+    for l in range(L - 2, -1, -1):           # decoder
+        i = 2 * L - 2 - l
+        c[f"ud{l}"] = up(c[f"d{l + 1}"])
+        c[f"u{l}"] = r(relu(conv(c[f"ud{l}"], *P[f"W{i}a"])))
+        c[f"s{l}"] = r(c[f"u{l}"] + c[f"e{l}"])
+        c[f"d{l}"] = r(relu(conv(c[f"s{l}"], *P[f"W{i}b"])))
+    out = conv(c["d0"], *P[f"W{2 * L - 1}"])[..., 0]
     c["P"] = P
     return out, c
 
@@ -174,9 +194,10 @@ def loss_and_grad(params: dict, inp: np.ndarray, target: np.ndarray, bf16: bool 
     through the forward's stored values)."""
     out, c = forward(params, inp, bf16)
     P = c["P"]
+    L = _levels(P)
     V = out.size
     diff = out - target
-    L = float(np.sum(diff * diff) / (2 * V))
+    loss = float(np.sum(diff * diff) / (2 * V))
     G = {}
 
     def back_conv(name, x, g):
@@ -187,19 +208,17 @@ def loss_and_grad(params: dict, inp: np.ndarray, target: np.ndarray, bf16: bool 
         return g * (y > 0)
 
     g = (diff / V)[..., None]
-    g = back_conv("W5", c["d0"], g)
-    g_s0 = back_conv("W4b", c["s0"], mask(g, c["d0"]))
-    g = back_conv("W4a", c["ud1"], mask(g_s0, c["u0"]))
-    g_d1 = up_grad(g)
-    g_s1 = back_conv("W3b", c["s1"], mask(g_d1, c["d1"]))
-    g = back_conv("W3a", c["ub"], mask(g_s1, c["u1"]))
-    g_b = up_grad(g)
-    g = back_conv("W2b", c["ba"], mask(g_b, c["b"]))
-    g_p1 = back_conv("W2a", c["p1"], mask(g, c["ba"]))
-    g_e1 = g_s1 + pool_grad(g_p1)
-    g = back_conv("W1b", c["e1a"], mask(g_e1, c["e1"]))
-    g_p0 = back_conv("W1a", c["p0"], mask(g, c["e1a"]))
-    g_e0 = g_s0 + pool_grad(g_p0)
-    g = back_conv("W0b", c["e0a"], mask(g_e0, c["e0"]))
-    back_conv("W0a", c["in"], mask(g, c["e0a"]))
-    return L, G, out
+    g_d = back_conv(f"W{2 * L - 1}", c["d0"], g)       # gradient w.r.t. d0
+    g_s = {}
+    for l in range(L - 1):                             # decoder, top to bottom
+        i = 2 * L - 2 - l
+        g_s[l] = back_conv(f"W{i}b", c[f"s{l}"], mask(g_d, c[f"d{l}"]))
+        g = back_conv(f"W{i}a", c[f"ud{l}"], mask(g_s[l], c[f"u{l}"]))
+        g_d = up_grad(g)                               # gradient w.r.t. d_{l+1}
+    g_e = g_d                                          # the bottleneck: e_{L-1} = d_{L-1}
+    for l in range(L - 1, -1, -1):                     # encoder, bottom to top
+        g = back_conv(f"W{l}b", c[f"e{l}a"], mask(g_e, c[f"e{l}"]))
+        g_x = back_conv(f"W{l}a", c[f"x{l}"], mask(g, c[f"e{l}a"]))
+        if l > 0:
+            g_e = g_s[l - 1] + pool_grad(g_x)          # e_{l-1}: skip and pool paths
+    return loss, G, out

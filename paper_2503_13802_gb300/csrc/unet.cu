@@ -48,26 +48,38 @@ struct Layer {
 
 }  // namespace
 
+constexpr int kMaxLevels = 5;
+constexpr int kMaxChannels = 128;
+constexpr int kMaxLayers = 4 * kMaxLevels - 1;
+
 struct Net {
-    int D = 0, H = 0, W = 0, c0 = 0, c1 = 0, c2 = 0;
-    long long V0 = 0, V1 = 0, V2 = 0;
+    int D = 0, H = 0, W = 0;
+    int levels = 0;
+    int ch[kMaxLevels] = {};          // channels per level
+    long long V[kMaxLevels] = {};     // voxels per level (V[l] = V[0] / 8^l)
+    int dims[kMaxLevels][3] = {};     // (D, H, W) per level
+    int nlayers = 0;
     long long nparam = 0;
     int adam_t = 0;
-    Layer L[11];
+    Layer L[kMaxLayers];
     std::vector<void*> allocs;
     float *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
-    // forward activations (bfloat16, channels last) and the FP32 output
-    __nv_bfloat16 *e0a = nullptr, *e0 = nullptr, *p0 = nullptr, *e1a = nullptr, *e1 = nullptr, *p1 = nullptr;
-    __nv_bfloat16 *ba = nullptr, *b = nullptr, *u1 = nullptr, *d1 = nullptr, *u0 = nullptr, *d0 = nullptr;
+    // forward activations (bfloat16, channels last) per level, and the FP32
+    // output.  Encoder: ea, e (level l), p[l] = pool(e[l]) (level l + 1);
+    // decoder (l < levels - 1): u, d; the bottleneck's d is its e.
+    __nv_bfloat16 *ea[kMaxLevels] = {}, *e[kMaxLevels] = {}, *p[kMaxLevels] = {};
+    __nv_bfloat16 *u[kMaxLevels] = {}, *d[kMaxLevels] = {};
     float* out = nullptr;
     const float* in = nullptr;       // the last forward's input (borrowed)
     const float* iscale = nullptr;   // the last forward's input scale (device scalar) or null
     float* scales = nullptr;         // {1 / r, r gain, 1 / (r gain)} of the scaled calls
     double* spart = nullptr;
-    // gradients
-    __nv_bfloat16 *gout = nullptr, *gd0 = nullptr, *gs0 = nullptr, *gup = nullptr, *ge0 = nullptr, *ge0a = nullptr;
-    __nv_bfloat16 *gd1 = nullptr, *gs1 = nullptr, *gupb = nullptr, *ge1 = nullptr, *ge1a = nullptr, *gp0 = nullptr;
-    __nv_bfloat16 *gb = nullptr, *gba = nullptr, *gp1 = nullptr, *scratch = nullptr;
+    // gradients (w.r.t. the named activations): gd (d; the bottleneck's e),
+    // gs (u + e), gup (up(d[l + 1]) at level l), ge (e), gea (ea), gp (p)
+    __nv_bfloat16* gout = nullptr;
+    __nv_bfloat16 *gd[kMaxLevels] = {}, *gs[kMaxLevels] = {}, *gup[kMaxLevels] = {};
+    __nv_bfloat16 *ge[kMaxLevels] = {}, *gea[kMaxLevels] = {}, *gp[kMaxLevels] = {};
+    __nv_bfloat16* scratch = nullptr;
     float *wpart = nullptr, *bpart = nullptr;
     int* status = nullptr;           // device word: MH3D_ERR_TIMEOUT from a bounded wait, else 0
     double* lpart = nullptr;
@@ -349,8 +361,8 @@ cudaError_t launch_wgrad(const ConvSrc& s, const __nv_bfloat16* g, int N, float*
     const long long V = (long long)s.D * s.H * s.W;
     const int Kpad = round_up(27 * s.C, kBK);
     const unsigned chunks = blocks_for(V, kWChunk);
-    dim3 grid(blocks_for(Kpad, kBM), chunks);
     const int bn = tile_n(N);
+    dim3 grid(blocks_for(Kpad, kBM), chunks, (unsigned)((N + bn - 1) / bn));
     if (bn == 16)
         k_conv_wgrad<16><<<grid, kThreads, 0, st>>>(s, g, N, Kpad, wpart);
     else if (bn == 32)
@@ -383,7 +395,8 @@ namespace {
 
 mh3d_status prep_weights(Net& n, cudaStream_t st)
 {
-    for (Layer& l : n.L) {
+    for (int i = 0; i < n.nlayers; ++i) {
+        Layer& l = n.L[i];
         k_prep_weights<<<blocks_for((long long)l.Kf * l.Nf, 256), 256, 0, st>>>(n.theta + l.woff, l.cin, l.cout,
                                                                                 l.Kf, l.Nf, 0, l.Wf);
         k_prep_weights<<<blocks_for((long long)l.Kb * l.Nb, 256), 256, 0, st>>>(n.theta + l.woff, l.cin, l.cout,
@@ -405,34 +418,46 @@ cudaError_t fwd(const Net& n, int li, const ConvSrc& s, int relu, OutT* out, cud
     return launch_conv(s, l.Wf, l.Kf, l.Nf, l.cout, n.theta + l.boff, relu, out, st, oscale, &l.uf, n.status);
 }
 
+// Layer indices: encoder level l: 2 l (a), 2 l + 1 (b); decoder level l
+// (levels - 2 .. 0): 2 levels + 2 (levels - 2 - l) (a, on up(d[l + 1])) and
+// the next (b, on u[l] + e[l]); the output convolution last.
+inline int dec_layer(const Net& n, int l) { return 2 * n.levels + 2 * (n.levels - 2 - l); }
+
+ConvSrc src_at(const Net& n, const __nv_bfloat16* a, int l, int C, const __nv_bfloat16* skip = nullptr, int up = 0)
+{
+    return src_of(a, n.dims[l][0], n.dims[l][1], n.dims[l][2], C, skip, up);
+}
+
 // iscale / oscale: device scalars multiplying the input and the output
 // (null: 1).
 mh3d_status forward_pass(Net& n, const float* in, cudaStream_t st, const float* iscale = nullptr,
                          const float* oscale = nullptr)
 {
-    const int D = n.D, H = n.H, W = n.W, D1 = D / 2, H1 = H / 2, W1 = W / 2, D2 = D / 4, H2 = H / 4, W2 = W / 4;
+    const int Lv = n.levels;
     ConvSrc s0;
     s0.f32 = in;
-    s0.D = D;
-    s0.H = H;
-    s0.W = W;
+    s0.D = n.D;
+    s0.H = n.H;
+    s0.W = n.W;
     s0.C = 1;
     s0.f32_scale = iscale;
     n.in = in;
     n.iscale = iscale;
-    UN_CK(n, fwd(n, 0, s0, 1, n.e0a, st));
-    UN_CK(n, fwd(n, 1, src_of(n.e0a, D, H, W, n.c0), 1, n.e0, st));
-    k_pool<<<blocks_for(n.V1 * n.c0, 256), 256, 0, st>>>(n.e0, D, H, W, n.c0, n.p0);
-    UN_CK(n, fwd(n, 2, src_of(n.p0, D1, H1, W1, n.c0), 1, n.e1a, st));
-    UN_CK(n, fwd(n, 3, src_of(n.e1a, D1, H1, W1, n.c1), 1, n.e1, st));
-    k_pool<<<blocks_for(n.V2 * n.c1, 256), 256, 0, st>>>(n.e1, D1, H1, W1, n.c1, n.p1);
-    UN_CK(n, fwd(n, 4, src_of(n.p1, D2, H2, W2, n.c1), 1, n.ba, st));
-    UN_CK(n, fwd(n, 5, src_of(n.ba, D2, H2, W2, n.c2), 1, n.b, st));
-    UN_CK(n, fwd(n, 6, src_of(n.b, D1, H1, W1, n.c2, nullptr, 1), 1, n.u1, st));
-    UN_CK(n, fwd(n, 7, src_of(n.u1, D1, H1, W1, n.c1, n.e1), 1, n.d1, st));
-    UN_CK(n, fwd(n, 8, src_of(n.d1, D, H, W, n.c1, nullptr, 1), 1, n.u0, st));
-    UN_CK(n, fwd(n, 9, src_of(n.u0, D, H, W, n.c0, n.e0), 1, n.d0, st));
-    UN_CK(n, fwd(n, 10, src_of(n.d0, D, H, W, n.c0), 0, n.out, st, oscale));
+    for (int l = 0; l < Lv; ++l) {
+        const ConvSrc x = l == 0 ? s0 : src_at(n, n.p[l - 1], l, n.ch[l - 1]);
+        UN_CK(n, fwd(n, 2 * l, x, 1, n.ea[l], st));
+        UN_CK(n, fwd(n, 2 * l + 1, src_at(n, n.ea[l], l, n.ch[l]), 1, n.e[l], st));
+        if (l + 1 < Lv)
+            k_pool<<<blocks_for(n.V[l + 1] * n.ch[l], 256), 256, 0, st>>>(n.e[l], n.dims[l][0], n.dims[l][1],
+                                                                          n.dims[l][2], n.ch[l], n.p[l]);
+    }
+    for (int l = Lv - 2; l >= 0; --l) {
+        const __nv_bfloat16* below = l + 1 == Lv - 1 ? n.e[l + 1] : n.d[l + 1];
+        const int li = dec_layer(n, l);
+        UN_CK(n, fwd(n, li, src_at(n, below, l, n.ch[l + 1], nullptr, 1), 1, n.u[l], st));
+        UN_CK(n, fwd(n, li + 1, src_at(n, n.u[l], l, n.ch[l], n.e[l]), 1, n.d[l], st));
+    }
+    UN_CK(n, fwd(n, n.nlayers - 1, src_at(n, n.d[0], 0, n.ch[0]), 0, n.out, st, oscale));
     return MH3D_OK;
 }
 
@@ -461,32 +486,39 @@ mh3d_status back_layer(Net& n, int li, const ConvSrc& s, const __nv_bfloat16* g,
 
 mh3d_status backward_pass(Net& n, cudaStream_t st)
 {
-    const int D = n.D, H = n.H, W = n.W, D1 = D / 2, H1 = H / 2, W1 = W / 2, D2 = D / 4, H2 = H / 4, W2 = W / 4;
+    const int Lv = n.levels;
     mh3d_status s;
 #define UN_BACK(...)                                             \
     if ((s = back_layer(n, __VA_ARGS__, st)) != MH3D_OK) return s
-    UN_BACK(10, src_of(n.d0, D, H, W, n.c0), n.gout, nullptr, n.gd0);
-    UN_BACK(9, src_of(n.u0, D, H, W, n.c0, n.e0), n.gd0, n.d0, n.gs0);
-    UN_BACK(8, src_of(n.d1, D, H, W, n.c1, nullptr, 1), n.gs0, n.u0, n.gup);
-    k_up_grad<<<blocks_for(n.V1 * n.c1, 256), 256, 0, st>>>(n.gup, D1, H1, W1, n.c1, n.gd1);
-    UN_BACK(7, src_of(n.u1, D1, H1, W1, n.c1, n.e1), n.gd1, n.d1, n.gs1);
-    UN_BACK(6, src_of(n.b, D1, H1, W1, n.c2, nullptr, 1), n.gs1, n.u1, n.gupb);
-    k_up_grad<<<blocks_for(n.V2 * n.c2, 256), 256, 0, st>>>(n.gupb, D2, H2, W2, n.c2, n.gb);
-    UN_BACK(5, src_of(n.ba, D2, H2, W2, n.c2), n.gb, n.b, n.gba);
-    UN_BACK(4, src_of(n.p1, D2, H2, W2, n.c1), n.gba, n.ba, n.gp1);
-    k_pool_grad_add<<<blocks_for(n.V1 * n.c1, 256), 256, 0, st>>>(n.gs1, n.gp1, D1, H1, W1, n.c1, n.ge1);
-    UN_BACK(3, src_of(n.e1a, D1, H1, W1, n.c1), n.ge1, n.e1, n.ge1a);
-    UN_BACK(2, src_of(n.p0, D1, H1, W1, n.c0), n.ge1a, n.e1a, n.gp0);
-    k_pool_grad_add<<<blocks_for(n.V0 * n.c0, 256), 256, 0, st>>>(n.gs0, n.gp0, D, H, W, n.c0, n.ge0);
-    UN_BACK(1, src_of(n.e0a, D, H, W, n.c0), n.ge0, n.e0, n.ge0a);
+    // output convolution: gradient w.r.t. d[0]
+    UN_BACK(n.nlayers - 1, src_at(n, n.d[0], 0, n.ch[0]), n.gout, nullptr, n.gd[0]);
+    for (int l = 0; l + 1 < Lv; ++l) {   // decoder, top to bottom
+        const int li = dec_layer(n, l);
+        const __nv_bfloat16* below = l + 1 == Lv - 1 ? n.e[l + 1] : n.d[l + 1];
+        UN_BACK(li + 1, src_at(n, n.u[l], l, n.ch[l], n.e[l]), n.gd[l], n.d[l], n.gs[l]);
+        UN_BACK(li, src_at(n, below, l, n.ch[l + 1], nullptr, 1), n.gs[l], n.u[l], n.gup[l]);
+        const int* dn = n.dims[l + 1];
+        k_up_grad<<<blocks_for(n.V[l + 1] * n.ch[l + 1], 256), 256, 0, st>>>(n.gup[l], dn[0], dn[1], dn[2],
+                                                                              n.ch[l + 1], n.gd[l + 1]);
+    }
     ConvSrc s0;
     s0.f32 = n.in;
     s0.f32_scale = n.iscale;
-    s0.D = D;
-    s0.H = H;
-    s0.W = W;
+    s0.D = n.D;
+    s0.H = n.H;
+    s0.W = n.W;
     s0.C = 1;
-    UN_BACK(0, s0, n.ge0a, n.e0a, nullptr);
+    for (int l = Lv - 1; l >= 0; --l) {   // encoder, bottom to top
+        const __nv_bfloat16* ge = l == Lv - 1 ? n.gd[l] : n.ge[l];   // the bottleneck's e is its d
+        UN_BACK(2 * l + 1, src_at(n, n.ea[l], l, n.ch[l]), ge, n.e[l], n.gea[l]);
+        const ConvSrc x = l == 0 ? s0 : src_at(n, n.p[l - 1], l, n.ch[l - 1]);
+        UN_BACK(2 * l, x, n.gea[l], n.ea[l], l == 0 ? nullptr : n.gp[l - 1]);
+        if (l > 0) {
+            const int* dm = n.dims[l - 1];
+            k_pool_grad_add<<<blocks_for(n.V[l - 1] * n.ch[l - 1], 256), 256, 0, st>>>(
+                n.gs[l - 1], n.gp[l - 1], dm[0], dm[1], dm[2], n.ch[l - 1], n.ge[l - 1]);
+        }
+    }
 #undef UN_BACK
     UN_CK(n, cudaGetLastError());
     return MH3D_OK;
@@ -494,7 +526,22 @@ mh3d_status backward_pass(Net& n, cudaStream_t st)
 
 constexpr int kScaleBlocks = 304;   // partial sums of the RMS (2 per SM)
 
-const int kLayerIO[11][2] = {{-1, 0}, {0, 0}, {0, 1}, {1, 1}, {1, 2}, {2, 2}, {2, 1}, {1, 1}, {1, 0}, {0, 0}, {0, -1}};
+// (cin, cout) of layer i of a network with channels ch[0 .. levels - 1].
+void layer_io(int levels, const int* ch, int i, int* cin, int* cout)
+{
+    if (i < 2 * levels) {   // encoder
+        const int l = i / 2;
+        *cin = i % 2 == 0 ? (l == 0 ? 1 : ch[l - 1]) : ch[l];
+        *cout = ch[l];
+    } else if (i < 4 * levels - 2) {   // decoder level l = levels - 2 - (i - 2 levels) / 2
+        const int l = levels - 2 - (i - 2 * levels) / 2;
+        *cin = (i - 2 * levels) % 2 == 0 ? ch[l + 1] : ch[l];
+        *cout = ch[l];
+    } else {
+        *cin = ch[0];
+        *cout = 1;
+    }
+}
 
 }  // namespace
 }  // namespace unet
@@ -505,43 +552,55 @@ struct mh3d_unet_s : public Net {};
 
 extern "C" {
 
-long long mh3d_unet_param_count(int c0, int c1, int c2)
+long long mh3d_unet_param_count_levels(int levels, const int* channels)
 {
-    const int ch[3] = {c0, c1, c2};
+    if (levels < 2 || levels > mh3d::unet::kMaxLevels || !channels) return -1;
     long long n = 0;
-    for (const auto& io : mh3d::unet::kLayerIO) {
-        const int ci = io[0] < 0 ? 1 : ch[io[0]], co = io[1] < 0 ? 1 : ch[io[1]];
+    for (int i = 0; i < 4 * levels - 1; ++i) {
+        int ci = 0, co = 0;
+        mh3d::unet::layer_io(levels, channels, i, &ci, &co);
         n += (long long)co * 27 * ci + co;
     }
     return n;
 }
 
-mh3d_status mh3d_unet_create(int nx, int ny, int nz, int c0, int c1, int c2, mh3d_unet* out)
+long long mh3d_unet_param_count(int c0, int c1, int c2)
+{
+    const int ch[3] = {c0, c1, c2};
+    return mh3d_unet_param_count_levels(3, ch);
+}
+
+mh3d_status mh3d_unet_create_levels(int nx, int ny, int nz, int levels, const int* channels, mh3d_unet* out)
 {
     using namespace mh3d::unet;
     if (!out) return MH3D_ERR_INVALID_ARG;
     *out = nullptr;
-    if (nx < 4 || ny < 4 || nz < 4 || nx % 4 || ny % 4 || nz % 4 || c0 < 1 || c1 < 1 || c2 < 1 || c0 > 64 ||
-        c1 > 64 || c2 > 64)
-        return MH3D_ERR_INVALID_ARG;
+    if (levels < 2 || levels > kMaxLevels || !channels) return MH3D_ERR_INVALID_ARG;
+    const int q = 1 << (levels - 1);   // every level's grid halves the previous one
+    if (nx < q || ny < q || nz < q || nx % q || ny % q || nz % q) return MH3D_ERR_INVALID_ARG;
+    for (int l = 0; l < levels; ++l)
+        if (channels[l] < 1 || channels[l] > kMaxChannels) return MH3D_ERR_INVALID_ARG;
     mh3d_unet n = new mh3d_unet_s();
     n->W = nx;
     n->H = ny;
     n->D = nz;
-    n->c0 = c0;
-    n->c1 = c1;
-    n->c2 = c2;
-    n->V0 = (long long)nx * ny * nz;
-    n->V1 = n->V0 / 8;
-    n->V2 = n->V1 / 8;
-    const int ch[3] = {c0, c1, c2};
+    n->levels = levels;
+    n->nlayers = 4 * levels - 1;
+    for (int l = 0; l < levels; ++l) {
+        n->ch[l] = channels[l];
+        n->dims[l][0] = nz >> l;
+        n->dims[l][1] = ny >> l;
+        n->dims[l][2] = nx >> l;
+        n->V[l] = (long long)n->dims[l][0] * n->dims[l][1] * n->dims[l][2];
+    }
     long long off = 0;
     size_t wp = 0, bp = 0;
-    const long long Vl[11] = {n->V0, n->V0, n->V1, n->V1, n->V2, n->V2, n->V1, n->V1, n->V0, n->V0, n->V0};
-    for (int i = 0; i < 11; ++i) {
+    int cm = 1;
+    for (int i = 0; i < n->nlayers; ++i) {
         Layer& l = n->L[i];
-        l.cin = kLayerIO[i][0] < 0 ? 1 : ch[kLayerIO[i][0]];
-        l.cout = kLayerIO[i][1] < 0 ? 1 : ch[kLayerIO[i][1]];
+        layer_io(levels, channels, i, &l.cin, &l.cout);
+        // the level the layer's output lives at
+        const int lv = i < 2 * levels ? i / 2 : (i < 4 * levels - 2 ? levels - 2 - (i - 2 * levels) / 2 : 0);
         l.woff = off;
         off += (long long)l.cout * 27 * l.cin;
         l.boff = off;
@@ -550,60 +609,52 @@ mh3d_status mh3d_unet_create(int nx, int ny, int nz, int c0, int c1, int c2, mh3
         l.Nf = round_up(l.cout, tile_n(l.cout));
         l.Kb = round_up(27 * l.cout, kBK);
         l.Nb = round_up(l.cin, tile_n(l.cin));
-        wp = std::max(wp, wpart_floats(Vl[i], l.Kf, l.cout));
-        bp = std::max(bp, (size_t)blocks_for(Vl[i], kWChunk) * l.cout);
+        wp = std::max(wp, wpart_floats(n->V[lv], l.Kf, l.cout));
+        bp = std::max(bp, (size_t)blocks_for(n->V[lv], kWChunk) * l.cout);
+        cm = std::max(cm, std::max(l.cin, l.cout));
     }
     n->nparam = off;
     n->wpart_n = wp;
     n->bpart_n = bp;
-    n->lblocks = (int)blocks_for(n->V0, kThreads);
-    const int cm = std::max(c0, std::max(c1, c2));
+    n->lblocks = (int)blocks_for(n->V[0], kThreads);
     bool ok = true;
     auto A = [&](auto** p, size_t count) { ok = ok && dalloc(*n, p, count) == cudaSuccess; };
     A(&n->theta, off);
     A(&n->grad, off);
     A(&n->am, off);
     A(&n->av, off);
-    for (Layer& l : n->L) {
+    for (int i = 0; i < n->nlayers; ++i) {
+        Layer& l = n->L[i];
         A(&l.Wf, (size_t)l.Kf * l.Nf);
         A(&l.Wb, (size_t)l.Kb * l.Nb);
-        const bool f32in = &l == &n->L[0];
-        const size_t ef = umma_elems(l.cin, f32in, l.cout), eb = umma_elems(l.cout, false, l.cin);
+        const size_t ef = umma_elems(l.cin, i == 0, l.cout), eb = umma_elems(l.cout, false, l.cin);
         if (ef) A(&l.uf.w, ef);
         if (eb) A(&l.ub.w, eb);
     }
     A(&n->status, 1);
     if (ok && cudaMemset(n->status, 0, sizeof(int)) != cudaSuccess) ok = false;
-    const size_t V0 = n->V0, V1 = n->V1, V2 = n->V2;
-    A(&n->e0a, V0 * c0);
-    A(&n->e0, V0 * c0);
-    A(&n->p0, V1 * c0);
-    A(&n->e1a, V1 * c1);
-    A(&n->e1, V1 * c1);
-    A(&n->p1, V2 * c1);
-    A(&n->ba, V2 * c2);
-    A(&n->b, V2 * c2);
-    A(&n->u1, V1 * c1);
-    A(&n->d1, V1 * c1);
-    A(&n->u0, V0 * c0);
-    A(&n->d0, V0 * c0);
-    A(&n->out, V0);
-    A(&n->gout, V0);
-    A(&n->gd0, V0 * c0);
-    A(&n->gs0, V0 * c0);
-    A(&n->gup, V0 * c1);
-    A(&n->ge0, V0 * c0);
-    A(&n->ge0a, V0 * c0);
-    A(&n->gd1, V1 * c1);
-    A(&n->gs1, V1 * c1);
-    A(&n->gupb, V1 * c2);
-    A(&n->ge1, V1 * c1);
-    A(&n->ge1a, V1 * c1);
-    A(&n->gp0, V1 * c0);
-    A(&n->gb, V2 * c2);
-    A(&n->gba, V2 * c2);
-    A(&n->gp1, V2 * c1);
-    A(&n->scratch, V0 * cm);
+    size_t smax = 0;   // the largest level volume x channels (the mask scratch)
+    for (int l = 0; l < levels; ++l) {
+        const size_t Vl = n->V[l], c = n->ch[l];
+        A(&n->ea[l], Vl * c);
+        A(&n->e[l], Vl * c);
+        A(&n->gd[l], Vl * c);
+        A(&n->ge[l], Vl * c);
+        A(&n->gea[l], Vl * c);
+        smax = std::max(smax, Vl * c);
+        if (l + 1 < levels) {
+            const size_t cn = n->ch[l + 1];
+            A(&n->p[l], n->V[l + 1] * c);
+            A(&n->gp[l], n->V[l + 1] * c);
+            A(&n->u[l], Vl * c);
+            A(&n->d[l], Vl * c);
+            A(&n->gs[l], Vl * c);
+            A(&n->gup[l], Vl * cn);
+        }
+    }
+    A(&n->out, n->V[0]);
+    A(&n->gout, n->V[0]);
+    A(&n->scratch, std::max(smax, (size_t)n->V[0] * cm));
     A(&n->wpart, wp);
     A(&n->bpart, bp);
     A(&n->lpart, (size_t)n->lblocks);
@@ -621,6 +672,16 @@ mh3d_status mh3d_unet_create(int nx, int ny, int nz, int c0, int c1, int c2, mh3
     }
     *out = n;
     return MH3D_OK;
+}
+
+mh3d_status mh3d_unet_create(int nx, int ny, int nz, int c0, int c1, int c2, mh3d_unet* out)
+{
+    using namespace mh3d::unet;
+    if (!out) return MH3D_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (c0 > 64 || c1 > 64 || c2 > 64) return MH3D_ERR_INVALID_ARG;
+    const int ch[3] = {c0, c1, c2};
+    return mh3d_unet_create_levels(nx, ny, nz, 3, ch, out);
 }
 
 mh3d_status mh3d_unet_destroy(mh3d_unet n)
@@ -661,7 +722,7 @@ mh3d_status mh3d_unet_forward(mh3d_unet n, const float* in, float* out, void* st
     cudaStream_t st = (cudaStream_t)stream;
     mh3d_status s = mh3d::unet::forward_pass(*n, in, st);
     if (s != MH3D_OK) return s;
-    UN_CK(*n, cudaMemcpyAsync(out, n->out, sizeof(float) * n->V0, cudaMemcpyDeviceToDevice, st));
+    UN_CK(*n, cudaMemcpyAsync(out, n->out, sizeof(float) * n->V[0], cudaMemcpyDeviceToDevice, st));
     return MH3D_OK;
 }
 
@@ -671,7 +732,7 @@ static mh3d_status loss_grad_impl(mh3d_unet n, const float* in, const float* tar
     using namespace mh3d::unet;
     mh3d_status s = forward_pass(*n, in, st, iscale, nullptr);
     if (s != MH3D_OK) return s;
-    k_mse<<<n->lblocks, kThreads, 0, st>>>(n->out, target, tscale, n->V0, n->gout, n->lpart);
+    k_mse<<<n->lblocks, kThreads, 0, st>>>(n->out, target, tscale, n->V[0], n->gout, n->lpart);
     if ((s = backward_pass(*n, st)) != MH3D_OK) return s;
     if (grad) UN_CK(*n, cudaMemcpyAsync(grad, n->grad, sizeof(float) * n->nparam, cudaMemcpyDeviceToDevice, st));
     if (loss) {
@@ -700,8 +761,8 @@ static bool ready(mh3d_unet n)
 static void launch_scales(mh3d_unet n, const float* in, float gain, cudaStream_t st)
 {
     using namespace mh3d::unet;
-    k_sumsq_part<<<kScaleBlocks, kThreads, 0, st>>>(in, n->V0, n->spart);
-    k_scales<<<1, 32, 0, st>>>(n->spart, kScaleBlocks, n->V0, gain, n->scales);
+    k_sumsq_part<<<kScaleBlocks, kThreads, 0, st>>>(in, n->V[0], n->spart);
+    k_scales<<<1, 32, 0, st>>>(n->spart, kScaleBlocks, n->V[0], gain, n->scales);
 }
 
 mh3d_status mh3d_unet_loss_grad(mh3d_unet n, const float* in, const float* target, float* grad, double* loss,
@@ -720,7 +781,7 @@ mh3d_status mh3d_unet_forward_scaled(mh3d_unet n, const float* in, float gain, f
     launch_scales(n, in, gain, st);
     mh3d_status s = mh3d::unet::forward_pass(*n, in, st, n->scales, n->scales + 1);
     if (s != MH3D_OK) return s;
-    UN_CK(*n, cudaMemcpyAsync(out, n->out, sizeof(float) * n->V0, cudaMemcpyDeviceToDevice, st));
+    UN_CK(*n, cudaMemcpyAsync(out, n->out, sizeof(float) * n->V[0], cudaMemcpyDeviceToDevice, st));
     return MH3D_OK;
 }
 

@@ -474,7 +474,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tile(ConvSrc src, const __
 
 // Weight gradient, split over voxel chunks: part[chunk][k][n] =
 // sum over the chunk's voxels of A[v][k] dY[v][n] (k < Kpad, n < N, dY is
-// [V][N] bfloat16).  Grid (Kpad / kBM rounded up, chunks).
+// [V][N] bfloat16).  Grid (Kpad / kBM rounded up, chunks, N / BN rounded
+// up): blockIdx.z takes outputs n0 = BN blockIdx.z .. n0 + BN - 1.
 template <int BN>
 __global__ void __launch_bounds__(kThreads) k_conv_wgrad(ConvSrc src, const __nv_bfloat16* __restrict__ dY, int N,
                                                          int Kpad, float* __restrict__ part)
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_wgrad(ConvSrc src, const __nv
     __shared__ __align__(16) __nv_bfloat16 sB[kBK * (BN + 8)];    // [v][n]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long V = (long long)src.D * src.H * src.W;
-    const int k0 = blockIdx.x * kBM;
+    const int k0 = blockIdx.x * kBM, n0 = blockIdx.z * BN;
     const long long v0 = (long long)blockIdx.y * kWChunk;
     const long long v1 = v0 + kWChunk < V ? v0 + kWChunk : V;
     const int Kvalid = 27 * src.C;
@@ -523,14 +524,14 @@ __global__ void __launch_bounds__(kThreads) k_conv_wgrad(ConvSrc src, const __nv
                 const int r = i / (BN / 8), c = i % (BN / 8);
                 const long long v = vb + r;
                 uint4 val = make_uint4(0, 0, 0, 0);
-                if (v < v1 && c * 8 < N) val = *reinterpret_cast<const uint4*>(dY + v * N + c * 8);
+                if (v < v1 && n0 + c * 8 < N) val = *reinterpret_cast<const uint4*>(dY + v * N + n0 + c * 8);
                 *reinterpret_cast<uint4*>(sB + r * (BN + 8) + c * 8) = val;
             }
         } else {
             for (int i = threadIdx.x; i < kBK * BN; i += kThreads) {
                 const int r = i / BN, c = i % BN;
                 const long long v = vb + r;
-                sB[r * (BN + 8) + c] = (v < v1 && c < N) ? dY[v * N + c] : __float2bfloat16(0.f);
+                sB[r * (BN + 8) + c] = (v < v1 && n0 + c < N) ? dY[v * N + n0 + c] : __float2bfloat16(0.f);
             }
         }
         __syncthreads();
@@ -546,7 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_wgrad(ConvSrc src, const __nv
             if (k >= Kpad) continue;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const int n = t * 8 + 2 * (lane & 3) + e;
+                const int n = n0 + t * 8 + 2 * (lane & 3) + e;
                 if (n < N) P[(size_t)k * N + n] = acc[t][2 * h + e];
             }
         }

@@ -12,7 +12,8 @@ from typing import Sequence
 
 from .mh3d import MH3DError, _dev_ptr, _stream_ptr, load as _load_base
 
-EXPORTS = ["mh3d_unet_param_count", "mh3d_unet_create", "mh3d_unet_destroy", "mh3d_unet_set_params",
+EXPORTS = ["mh3d_unet_param_count", "mh3d_unet_param_count_levels", "mh3d_unet_create",
+           "mh3d_unet_create_levels", "mh3d_unet_destroy", "mh3d_unet_set_params",
            "mh3d_unet_get_params", "mh3d_unet_forward", "mh3d_unet_loss_grad", "mh3d_unet_forward_scaled",
            "mh3d_unet_loss_grad_scaled", "mh3d_unet_adam_step",
            "mh3d_unet_conv_forward", "mh3d_unet_conv_input_grad", "mh3d_unet_conv_weight_grad",
@@ -35,7 +36,10 @@ def load():
     P = c_void_p
     lib.mh3d_unet_param_count.argtypes = [c_int, c_int, c_int]
     lib.mh3d_unet_param_count.restype = c_longlong
+    lib.mh3d_unet_param_count_levels.argtypes = [c_int, POINTER(c_int)]
+    lib.mh3d_unet_param_count_levels.restype = c_longlong
     lib.mh3d_unet_create.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, POINTER(c_void_p)]
+    lib.mh3d_unet_create_levels.argtypes = [c_int, c_int, c_int, c_int, POINTER(c_int), POINTER(c_void_p)]
     lib.mh3d_unet_destroy.argtypes = [P]
     lib.mh3d_unet_set_params.argtypes = [P, P, P]
     lib.mh3d_unet_get_params.argtypes = [P, P, P]
@@ -50,31 +54,40 @@ def load():
     lib.mh3d_unet_last_error.argtypes = [P]
     lib.mh3d_unet_last_error.restype = c_char_p
     for name in EXPORTS:
-        if name not in ("mh3d_unet_param_count", "mh3d_unet_last_error"):
+        if name not in ("mh3d_unet_param_count", "mh3d_unet_param_count_levels", "mh3d_unet_last_error"):
             getattr(lib, name).restype = c_int
     _ready = True
     return lib
 
 
-def mh3d_unet_param_count(c0: int, c1: int, c2: int) -> int:
-    return int(load().mh3d_unet_param_count(c0, c1, c2))
+def mh3d_unet_param_count(*channels: int) -> int:
+    """Parameters of the network with these channels per level (2..5
+    levels)."""
+    ch = (c_int * len(channels))(*channels)
+    n = int(load().mh3d_unet_param_count_levels(len(channels), ch))
+    if n < 0:
+        raise ValueError(f"bad channel list {channels}")
+    return n
 
 
 class UNet:
     """The warm-start network for volumes of n = (nx, ny, nz) voxels."""
 
-    def __init__(self, n: Sequence[int], c0: int = 16, c1: int = 32, c2: int = 64):
+    def __init__(self, n: Sequence[int], *channels: int):
+        """channels per level, full resolution first (2..5 levels; default
+        (16, 32, 64))."""
         lib = load()
         self.n = tuple(int(v) for v in n)
-        self.channels = (c0, c1, c2)
+        self.channels = tuple(int(c) for c in channels) if channels else (16, 32, 64)
         nx, ny, nz = self.n
         self.shape = (nz, ny, nx)
         self.V = nx * ny * nz
-        self.nparam = mh3d_unet_param_count(c0, c1, c2)
+        self.nparam = mh3d_unet_param_count(*self.channels)
         self.handle = c_void_p()
-        st = lib.mh3d_unet_create(nx, ny, nz, c0, c1, c2, ctypes.byref(self.handle))
+        ch = (c_int * len(self.channels))(*self.channels)
+        st = lib.mh3d_unet_create_levels(nx, ny, nz, len(self.channels), ch, ctypes.byref(self.handle))
         if st != 0:
-            raise MH3DError(st, "mh3d_unet_create")
+            raise MH3DError(st, "mh3d_unet_create_levels")
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -24,7 +24,18 @@ from typing import Iterable, Optional, Sequence, Tuple
 from .mh3d import Plan, make_opts, mh3d_adjoint, mh3d_operator_norm2, mh3d_solve
 from .unet import UNet
 
-LAYER_IO = ((None, 0), (0, 0), (0, 1), (1, 1), (1, 2), (2, 2), (2, 1), (1, 1), (1, 0), (0, 0), (0, None))
+def layer_io(levels: int):
+    """(input level, output level) of every convolution in parameter order
+    (None: the one-channel input or output): the encoder's two per level,
+    the decoder's two per level from the bottom up, the output
+    convolution."""
+    io = []
+    for l in range(levels):
+        io += [(None if l == 0 else l - 1, l), (l, l)]
+    for l in range(levels - 2, -1, -1):
+        io += [(l + 1, l), (l, l)]
+    io.append((0, None))
+    return tuple(io)
 
 
 class WarmStart:
@@ -48,7 +59,7 @@ class WarmStart:
 
         g = torch.Generator().manual_seed(int(seed))
         parts = []
-        for ci, co in LAYER_IO:
+        for ci, co in layer_io(len(self.channels)):
             cin = 1 if ci is None else self.channels[ci]
             cout = 1 if co is None else self.channels[co]
             parts.append(torch.randn(cout * 27 * cin, generator=g) * (2.0 / (27 * cin)) ** 0.5)

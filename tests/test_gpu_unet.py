@@ -242,6 +242,44 @@ def test_network_gradient_matches_oracle():
         o += nW + co
 
 
+CH4 = (8, 16, 32, 128)   # four levels; the bottleneck's 128 channels: gather kernels, two output tiles
+N_NET4 = (32, 32, 16)
+
+
+def test_four_level_network_forward_and_gradient_match_oracle():
+    """The network with four levels (encoder and decoder loops of any
+    depth) against the oracle: forward to 5e-3, the gradient to cosine
+    0.999 and every layer's weight gradient to 5e-2, as for three levels."""
+    from paper_2503_13802_gb300.unet import UNet
+
+    theta = _theta(11, CH4)
+    nx, ny, nz = N_NET4
+    rng = np.random.default_rng(12)
+    inp = rng.standard_normal((nz, ny, nx)).astype(np.float32).astype(np.float64)
+    tgt = rng.standard_normal((nz, ny, nx)).astype(np.float32).astype(np.float64)
+    net = UNet(N_NET4, *CH4)
+    assert net.nparam == theta.size == U.param_count(*CH4)
+    net.set_params(_gpu(theta))
+    out = torch.empty(net.V, dtype=torch.float32, device="cuda")
+    net.forward(_gpu(inp), out)
+    ref, _ = U.forward(U.unflatten(theta, *CH4), inp, bf16=True)
+    got = out.cpu().numpy().reshape(ref.shape)
+    assert rel_l2(got, ref) <= 5e-3, rel_l2(got, ref)
+    grad = torch.empty(net.nparam, dtype=torch.float32, device="cuda")
+    loss = net.loss_grad(_gpu(inp), _gpu(tgt), grad)
+    Lr, G, _ = U.loss_and_grad(U.unflatten(theta, *CH4), inp, tgt, bf16=True)
+    assert abs(loss - Lr) <= 1e-3 * Lr, (loss, Lr)
+    g = grad.cpu().numpy().astype(np.float64)
+    gr = U.flatten(G, *CH4)
+    cos = float(np.dot(g, gr) / (np.linalg.norm(g) * np.linalg.norm(gr)))
+    assert cos >= 0.999, cos
+    o = 0
+    for name, ci, co in U.layer_shapes(*CH4):
+        nW = co * 27 * ci
+        assert rel_l2(g[o:o + nW], gr[o:o + nW]) <= 5e-2, (name, rel_l2(g[o:o + nW], gr[o:o + nW]))
+        o += nW + co
+
+
 def test_training_steps_reduce_the_loss():
     from paper_2503_13802_gb300.unet import UNet
 

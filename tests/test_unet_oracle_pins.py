@@ -120,3 +120,31 @@ def test_bf16_round_matches_torch():
     assert np.array_equal(U.bf16_round(x32), ref)
     assert U.bf16_round(np.float32(1.0 + 2.0 ** -8)) == 1.0          # tie -> even
     assert U.bf16_round(np.float32(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6
+
+
+@pytest.mark.parametrize("ch,shape", [((2, 3, 4, 5), (8, 8, 8)), ((2, 3), (4, 6, 2))])
+def test_loss_gradient_matches_central_differences_other_depths(ch, shape):
+    """Four levels (and two): the generic encoder/decoder loops against
+    central differences of the loss."""
+    r = _rng(16)
+    n = U.param_count(*ch)
+    theta = r.standard_normal(n) * 0.4
+    inp = r.standard_normal(shape)
+    tgt = r.standard_normal(shape)
+    _, G, _ = U.loss_and_grad(U.unflatten(theta, *ch), inp, tgt)
+    g = U.flatten(G, *ch)
+    h = 1e-6
+    for i in r.choice(n, 40, replace=False):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (U.loss_and_grad(U.unflatten(tp, *ch), inp, tgt)[0] - U.loss_and_grad(U.unflatten(tm, *ch), inp, tgt)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (i, fd, g[i])
+
+
+def test_four_level_layout():
+    """(16, 32, 64, 128): 15 convolutions, the bottleneck at 128 channels,
+    1,314,849 parameters."""
+    sh = U.layer_shapes(16, 32, 64, 128)
+    assert len(sh) == 15 and sh[7] == ("W3b", 128, 128) and sh[8] == ("W4a", 128, 64) and sh[-1] == ("W7", 16, 1)
+    assert U.param_count(16, 32, 64, 128) == sum(co * 27 * ci + co for _, ci, co in sh) == 1314849
