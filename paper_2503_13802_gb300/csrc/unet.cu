@@ -36,6 +36,13 @@ struct UmmaW {
     int c8p = 0, np = 0;
 };
 
+// FP32 workspace of the split-K partial sums of the gather kernel (owned
+// by the network).
+struct SplitWS {
+    float* p = nullptr;
+    size_t cap = 0;   // floats
+};
+
 struct Layer {
     int cin = 0, cout = 0;
     UmmaW uf, ub;                   // forward and input-gradient operands of the tcgen05 kernel
@@ -82,6 +89,7 @@ struct Net {
     __nv_bfloat16* scratch = nullptr;
     float *wpart = nullptr, *bpart = nullptr;
     int* status = nullptr;           // device word: MH3D_ERR_TIMEOUT from a bounded wait, else 0
+    SplitWS skws;                    // split-K partial sums of the coarse gather convolutions
     double* lpart = nullptr;
     double* lhost = nullptr;
     size_t wpart_n = 0, bpart_n = 0;
@@ -183,7 +191,14 @@ template <int C, class OutT>
 bool tile_conv_n(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, int N, const float* bias, int relu,
                  const float* oscale, OutT* out, cudaStream_t st, cudaError_t* err)
 {
+    // output tiles of tile_n(N) columns; 32 outputs whose weights do not fit
+    // in shared memory (64 input channels: 27 x 64 weight rows) take two
+    // tiles of 16 (upsampled 64 -> 32 at 64x64x32: 228 us, 250 us on the
+    // gather kernel).  For 64 outputs, narrower tiles lose to the split-K
+    // gather kernel (64 -> 64 at 32x32x16: 79 against 62 us), which takes them.
     const int bn = tile_n(N);
+    if (bn == 32 && tile_smem<C, 32>(Kpad) > (size_t)smem_optin())
+        return tile_conv<C, 16>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, err);
     if (bn == 16) return tile_conv<C, 16>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, err);
     if (bn == 32) return tile_conv<C, 32>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, err);
     return tile_conv<C, 64>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, st, err);
@@ -318,10 +333,33 @@ size_t umma_elems(int Cs, bool f32, int N)
     return (c && np) ? (size_t)27 * c * np * 8 : 0;
 }
 
+// ---- split K for the gather kernel ------------------------------------------
+
+// Splits of the K loop that bring a gather launch of few CTAs (the coarse
+// levels: a few thousand voxels, up to 128 channels) to about two per SM,
+// each split at least two K steps; 1 when the launch fills the GPU.
+// Measured at 128x128x64, channels (16, 32, 64, 128): the 128 -> 128
+// bottleneck convolution (2048 voxels, 32 CTAs) took 215 us unsplit.
+int splitk_parts(long long V, int Npad, int bn, int Kpad)
+{
+    const long long ctas = (long long)blocks_for(V, kBM) * (Npad / bn);
+    const long long want = 2LL * num_sms();
+    if (ctas >= want) return 1;
+    const int steps = Kpad / kBK;
+    const int S = (int)std::min<long long>((want + ctas - 1) / ctas, std::max(1, steps / 2));
+    const int kl = (steps + S - 1) / S;   // K steps per split
+    return (steps + kl - 1) / kl;
+}
+size_t splitk_floats(long long V, int Npad, int N, int Kpad)
+{
+    const int S = splitk_parts(V, Npad, tile_n(N), Kpad);
+    return S > 1 ? (size_t)S * V * N : 0;
+}
+
 template <class OutT>
 cudaError_t launch_conv(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, int N, const float* bias,
                         int relu, OutT* out, cudaStream_t st, const float* oscale = nullptr,
-                        const UmmaW* uw = nullptr, int* status = nullptr)
+                        const UmmaW* uw = nullptr, int* status = nullptr, const SplitWS* ws = nullptr)
 {
     cudaError_t e = cudaSuccess;
     if (umma_takes(s, uw, N)) return launch_umma(s, *uw, N, bias, relu, oscale, out, status, st);
@@ -341,13 +379,19 @@ cudaError_t launch_conv(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int
     if (done) return e;
     const long long V = (long long)s.D * s.H * s.W;
     const int bn = tile_n(N);
-    dim3 grid(blocks_for(V, kBM), (unsigned)(Npad / bn));
+    int S = ws ? splitk_parts(V, Npad, bn, Kpad) : 1;
+    if (S > 1 && (size_t)S * V * N > ws->cap) S = 1;
+    const int steps = Kpad / kBK, kl = (steps + S - 1) / S * kBK;
+    float* part = S > 1 ? ws->p : nullptr;
+    dim3 grid(blocks_for(V, kBM), (unsigned)(Npad / bn), (unsigned)S);
     if (bn == 16)
-        k_conv<16, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out);
+        k_conv<16, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, kl, part);
     else if (bn == 32)
-        k_conv<32, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out);
+        k_conv<32, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, kl, part);
     else
-        k_conv<64, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out);
+        k_conv<64, OutT><<<grid, kThreads, 0, st>>>(s, Wt, Kpad, Npad, N, bias, relu, oscale, out, kl, part);
+    if (part)
+        k_splitk_finish<OutT><<<blocks_for(V * N, 256), 256, 0, st>>>(part, S, V * N, N, bias, relu, oscale, out);
     return cudaGetLastError();
 }
 
@@ -415,7 +459,8 @@ cudaError_t fwd(const Net& n, int li, const ConvSrc& s, int relu, OutT* out, cud
                 const float* oscale = nullptr)
 {
     const Layer& l = n.L[li];
-    return launch_conv(s, l.Wf, l.Kf, l.Nf, l.cout, n.theta + l.boff, relu, out, st, oscale, &l.uf, n.status);
+    return launch_conv(s, l.Wf, l.Kf, l.Nf, l.cout, n.theta + l.boff, relu, out, st, oscale, &l.uf, n.status,
+                       &n.skws);
 }
 
 // Layer indices: encoder level l: 2 l (a), 2 l + 1 (b); decoder level l
@@ -479,7 +524,7 @@ mh3d_status back_layer(Net& n, int li, const ConvSrc& s, const __nv_bfloat16* g,
         ConvSrc sg = src_of(g, s.D, s.H, s.W, l.cout);
         sg.flip = 1;
         UN_CK(n, launch_conv(sg, l.Wb, l.Kb, l.Nb, l.cin, (const float*)nullptr, 0, gin, st, nullptr, &l.ub,
-                             n.status));
+                             n.status, &n.skws));
     }
     return MH3D_OK;
 }
@@ -594,7 +639,7 @@ mh3d_status mh3d_unet_create_levels(int nx, int ny, int nz, int levels, const in
         n->V[l] = (long long)n->dims[l][0] * n->dims[l][1] * n->dims[l][2];
     }
     long long off = 0;
-    size_t wp = 0, bp = 0;
+    size_t wp = 0, bp = 0, skn = 0;
     int cm = 1;
     for (int i = 0; i < n->nlayers; ++i) {
         Layer& l = n->L[i];
@@ -610,6 +655,8 @@ mh3d_status mh3d_unet_create_levels(int nx, int ny, int nz, int levels, const in
         l.Kb = round_up(27 * l.cout, kBK);
         l.Nb = round_up(l.cin, tile_n(l.cin));
         wp = std::max(wp, wpart_floats(n->V[lv], l.Kf, l.cout));
+        skn = std::max(skn, std::max(splitk_floats(n->V[lv], l.Nf, l.cout, l.Kf),
+                                     splitk_floats(n->V[lv], l.Nb, l.cin, l.Kb)));
         bp = std::max(bp, (size_t)blocks_for(n->V[lv], kWChunk) * l.cout);
         cm = std::max(cm, std::max(l.cin, l.cout));
     }
@@ -657,6 +704,10 @@ mh3d_status mh3d_unet_create_levels(int nx, int ny, int nz, int levels, const in
     A(&n->scratch, std::max(smax, (size_t)n->V[0] * cm));
     A(&n->wpart, wp);
     A(&n->bpart, bp);
+    if (skn) {
+        A(&n->skws.p, skn);
+        n->skws.cap = skn;
+    }
     A(&n->lpart, (size_t)n->lblocks);
     A(&n->spart, (size_t)kScaleBlocks);
     A(&n->scales, 4);

@@ -174,11 +174,14 @@ __device__ __forceinline__ void load_weights(__nv_bfloat16* sB, const __nv_bfloa
 // Convolution as GEMM: out[v][n] (n < N) = sum_k A[v][k] Wt[k][n] (+ bias,
 // times the device scalar *oscale when given, ReLU).  Kvalid = 27 C; Wt is
 // [Kpad][Npad] with zero rows k >= Kvalid.  OutT = __nv_bfloat16 (stored
-// activations) or float.
+// activations) or float.  Split K (part != null): blockIdx.z takes
+// k in [z kl, (z + 1) kl) and writes its FP32 sums to part[z][v][n], which
+// k_splitk_finish adds in split order before the epilogue.
 template <int BN, class OutT>
 __global__ void __launch_bounds__(kThreads) k_conv(ConvSrc src, const __nv_bfloat16* __restrict__ Wt, int Kpad,
                                                    int Npad, int N, const float* __restrict__ bias, int relu,
-                                                   const float* __restrict__ oscale, OutT* __restrict__ out)
+                                                   const float* __restrict__ oscale, OutT* __restrict__ out,
+                                                   int kl, float* __restrict__ part)
 {
     __shared__ __align__(16) __nv_bfloat16 sA[kBM * (kBK + 8)];
     __shared__ __align__(16) __nv_bfloat16 sB[kBK * (BN + 8)];
@@ -191,7 +194,8 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvSrc src, const __nv_bfloa
     float acc[BN / 8][4];
 #pragma unroll
     for (int t = 0; t < BN / 8; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-    for (int k0 = 0; k0 < Kpad; k0 += kBK) {
+    const int kbeg = blockIdx.z * kl, kend = kbeg + kl < Kpad ? kbeg + kl : Kpad;
+    for (int k0 = kbeg; k0 < kend; k0 += kBK) {
         if (vec) {
             for (int i = threadIdx.x; i < kBM * (kBK / 8); i += kThreads) {
                 const int r = i / (kBK / 8), c = i % (kBK / 8);
@@ -223,6 +227,22 @@ __global__ void __launch_bounds__(kThreads) k_conv(ConvSrc src, const __nv_bfloa
         __syncthreads();
     }
     // epilogue: fragment (row lane/4 [+8], columns 2 (lane%4) + {0, 1})
+    if (part) {
+        float* P = part + (size_t)blockIdx.z * V * N;
+#pragma unroll
+        for (int t = 0; t < BN / 8; ++t)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long v = m0 + 16 * warp + (lane >> 2) + 8 * h;
+                if (v >= V) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int n = n0 + t * 8 + 2 * (lane & 3) + e;
+                    if (n < N) P[v * N + n] = acc[t][2 * h + e];
+                }
+            }
+        return;
+    }
     const float osc = oscale ? *oscale : 1.f;
 #pragma unroll
     for (int t = 0; t < BN / 8; ++t) {
@@ -470,6 +490,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_tile(ConvSrc src, const __
         y0 = ny0;
         z0 = nz0;
     }
+}
+
+// out[v][n] = epilogue(sum over the S splits, in order, of part[z][v][n]).
+template <class OutT>
+__global__ void k_splitk_finish(const float* __restrict__ part, int S, long long VN, int N,
+                                const float* __restrict__ bias, int relu, const float* __restrict__ oscale,
+                                OutT* __restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= VN) return;
+    float a = 0.f;
+    for (int z = 0; z < S; ++z) a += part[(size_t)z * VN + i];
+    const int n = (int)(i % N);
+    float val = (a + (bias ? bias[n] : 0.f)) * (oscale ? *oscale : 1.f);
+    if (relu) val = fmaxf(val, 0.f);
+    if constexpr (sizeof(OutT) == 2)
+        out[i] = __float2bfloat16(val);
+    else
+        out[i] = val;
 }
 
 // Weight gradient, split over voxel chunks: part[chunk][k][n] =
