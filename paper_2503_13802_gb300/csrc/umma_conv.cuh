@@ -47,17 +47,22 @@ namespace umma {
 
 constexpr int kM = 128;       // voxels per tile (TMEM lanes)
 constexpr int kHP = 136;      // voxels per staged plane (130 used; 136 x 16 B = 17 x 128 B)
-constexpr int kPlanes = 9;    // (dz, dy) neighbour rows
+// R output rows per tile (y0 .. y0 + R - 1) share the staged planes: 3 dz
+// x (R + 2) dy neighbour rows.
+template <int R>
+constexpr int planes() { return 3 * (R + 2); }
 constexpr int kT = 128;       // threads per CTA
 
 // NB halo buffers and accumulators (2: the next tile's halo is staged and
 // the previous tile's epilogue runs while this tile's MMAs execute).
-template <int C8P, int NP, int NB>
+template <int C8P, int NP, int NB, int R = 1>
 struct Geom {
     static_assert(C8P % 2 == 0 && NP % 16 == 0 && NP >= 16 && NP <= 128 && (NB == 1 || NB == 2), "operand shape");
+    static_assert(R == 1 || (NB == 1 && (R == 2 || R == 4)), "rows per tile");
+    static constexpr int kPl = planes<R>();
     static constexpr int kWBytes = 27 * C8P * NP * 16;
-    static constexpr int kHBytes = C8P * kPlanes * kHP * 16;   // one halo buffer
-    static constexpr int kAcc = NB * NP;                       // TMEM columns used
+    static constexpr int kHBytes = C8P * kPl * kHP * 16;       // one halo buffer
+    static constexpr int kAcc = NB * R * NP;                   // TMEM columns used
     static constexpr int kCols = kAcc <= 32 ? 32 : (kAcc <= 64 ? 64 : (kAcc <= 128 ? 128 : 256));   // allocated
     static constexpr size_t smem() { return 1024 + (size_t)kWBytes + (size_t)NB * kHBytes; }
 };
@@ -155,14 +160,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // upsampled) and the FP32 input (rounded to bfloat16, channel 0) need
 // arithmetic: their units are loaded into registers in batches (all loads
 // of a batch in flight), combined and stored.
-template <int C8P>
+template <int C8P, int R>
 __device__ __forceinline__ void stage_halo(const ConvSrc& src, unsigned char* sH, int z, int y, int x0, int cv)
 {
-    constexpr int NV = kPlanes * 130;
-    constexpr size_t CST = (size_t)kPlanes * kHP * 16;   // bytes between chunk planes
+    constexpr int PL = planes<R>();
+    constexpr int NV = PL * 130;
+    constexpr size_t CST = (size_t)PL * kHP * 16;   // bytes between chunk planes
     auto voxel = [&](int vi, unsigned char*& d, long long& off) {
         const int plane = vi / 130, xi = vi - plane * 130;
-        const int zz = z + plane / 3 - 1, yy = y + plane % 3 - 1, xx = x0 + xi - 1;
+        const int zz = z + plane / (R + 2) - 1, yy = y + plane % (R + 2) - 1, xx = x0 + xi - 1;
         d = sH + ((size_t)plane * kHP + xi) * 16;
         const bool in = zz >= 0 && zz < src.D && yy >= 0 && yy < src.H && xx >= 0 && xx < src.W;
         if (!in) {
@@ -264,7 +270,7 @@ __device__ __forceinline__ void epilogue(const ConvSrc& src, uint32_t acc, int z
         float a[16];
         tmem_ld16(acc + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, a);
         tmem_ld_wait();
-        if (x >= src.W) continue;
+        if (x >= src.W || y >= src.H) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int n = c0 + j;
@@ -297,35 +303,39 @@ __device__ __forceinline__ void epilogue(const ConvSrc& src, uint32_t acc, int z
     }
 }
 
-// The 27 x C8P / 2 MMAs of one tile into the accumulator at column acc,
-// committed to `bar` (one thread).
-template <int C8P, int NP>
+// The R x 27 x C8P / 2 MMAs of one tile (row r into the accumulator at
+// column acc + r NP), committed to `bar` (one thread).
+template <int C8P, int NP, int R>
 __device__ __forceinline__ void issue_mmas(uint32_t acc, uint32_t sH_a, uint32_t sW_a, int sgn, uint64_t* bar)
 {
     constexpr uint32_t kIdesc = idesc_bf16(kM, NP);
-    uint32_t accumulate = 0;
-    for (int tap = 0; tap < 27; ++tap) {
-        const int dz = sgn * (tap / 9 - 1), dy = sgn * ((tap / 3) % 3 - 1), dx = sgn * (tap % 3 - 1);
-        const int plane = (dz + 1) * 3 + (dy + 1);
+    constexpr int PL = planes<R>();
+    for (int r = 0; r < R; ++r) {
+        uint32_t accumulate = 0;
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = sgn * (tap / 9 - 1), dy = sgn * ((tap / 3) % 3 - 1), dx = sgn * (tap % 3 - 1);
+            const int plane = (dz + 1) * (R + 2) + (r + dy + 1);
 #pragma unroll
-        for (int ks = 0; ks < C8P / 2; ++ks) {
-            const uint32_t a = sH_a + (uint32_t)(((2 * ks * kPlanes + plane) * kHP + dx + 1) * 16);
-            const uint32_t b = sW_a + (uint32_t)((tap * C8P + 2 * ks) * NP * 16);
-            mma_f16(acc, smem_desc(a, kPlanes * kHP * 16, 128), smem_desc(b, NP * 16, 128), kIdesc, accumulate);
-            accumulate = 1;
+            for (int ks = 0; ks < C8P / 2; ++ks) {
+                const uint32_t a = sH_a + (uint32_t)(((2 * ks * PL + plane) * kHP + dx + 1) * 16);
+                const uint32_t b = sW_a + (uint32_t)((tap * C8P + 2 * ks) * NP * 16);
+                mma_f16(acc + (uint32_t)(r * NP), smem_desc(a, PL * kHP * 16, 128), smem_desc(b, NP * 16, 128),
+                        kIdesc, accumulate);
+                accumulate = 1;
+            }
         }
     }
     mma_commit(bar);
 }
 
 // Wu: [27][C8P][NP][8] bfloat16 (k_prep_umma); out: [V][N] channels last.
-template <int C8P, int NP, int NB, class OutT>
+template <int C8P, int NP, int NB, int R, class OutT>
 __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat16* __restrict__ Wu, int N,
                                                   const float* __restrict__ bias, int relu,
                                                   const float* __restrict__ oscale, OutT* __restrict__ out,
                                                   int ntiles, int* status)
 {
-    using G = Geom<C8P, NP, NB>;
+    using G = Geom<C8P, NP, NB, R>;
     extern __shared__ unsigned char umma_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base_s;
@@ -355,8 +365,8 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
     // zeroed once and never staged
     const int cv = src.f32 ? 1 : (src.C + 7) / 8;
     for (int nb = 0; nb < NB; ++nb) {
-        uint4* h4 = reinterpret_cast<uint4*>(sH + (size_t)nb * G::kHBytes + (size_t)cv * kPlanes * kHP * 16);
-        const int n16 = (C8P - cv) * kPlanes * kHP;
+        uint4* h4 = reinterpret_cast<uint4*>(sH + (size_t)nb * G::kHBytes + (size_t)cv * G::kPl * kHP * 16);
+        const int n16 = (C8P - cv) * G::kPl * kHP;
         for (int i = threadIdx.x; i < n16; i += kT) h4[i] = make_uint4(0, 0, 0, 0);
     }
     fence_proxy_async_smem();   // generic-proxy writes -> visible to the tensor core
@@ -366,10 +376,11 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
     const uint32_t tmem = tmem_base_s;
     const uint32_t sW_a = smem_u32(sW), sH_a = smem_u32(sH);
     const float osc = oscale ? *oscale : 1.f;
+    const int nyb = (src.H + R - 1) / R;   // row groups per z slice
     auto origin = [&](int tile, int& z, int& y, int& x0) {
         const int tx = tile % ntx, row = tile / ntx;
-        y = row % src.H;
-        z = row / src.H;
+        y = (row % nyb) * R;
+        z = row / nyb;
         x0 = tx * kM;
     };
 
@@ -378,14 +389,14 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             int z, y, x0;
             origin(tile, z, y, x0);
-            stage_halo<C8P>(src, sH, z, y, x0, cv);
+            stage_halo<C8P, R>(src, sH, z, y, x0, cv);
             cp_async_wait_all();
             fence_proxy_async_smem();
             tc_fence_before();
             __syncthreads();
             if (threadIdx.x == 0) {
                 tc_fence_after();
-                issue_mmas<C8P, NP>(tmem, sH_a, sW_a, sgn, &mbar[0]);
+                issue_mmas<C8P, NP, R>(tmem, sH_a, sW_a, sgn, &mbar[0]);
             }
             // one thread waits on the MMAs' mbarrier; the block barrier
             // releases the others (no spinning warps taking issue slots)
@@ -393,7 +404,8 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
             phase ^= 1;
             if (!ok) break;
             tc_fence_after();
-            epilogue<NP>(src, tmem, z, y, x0, N, bias, relu, osc, out);
+#pragma unroll
+            for (int r = 0; r < R; ++r) epilogue<NP>(src, tmem + (uint32_t)(r * NP), z, y + r, x0, N, bias, relu, osc, out);
             tc_fence_before();
             __syncthreads();   // TMEM read and halo consumed before the next tile reuses both
         }
@@ -404,7 +416,7 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
         if (tile < ntiles) {
             int z, y, x0;
             origin(tile, z, y, x0);
-            stage_halo<C8P>(src, sH, z, y, x0, cv);
+            stage_halo<C8P, 1>(src, sH, z, y, x0, cv);
         }
         for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
             const int b = i & 1;
@@ -416,8 +428,8 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
             __syncthreads();
             if (threadIdx.x == 0) {
                 tc_fence_after();
-                issue_mmas<C8P, NP>(tmem + (uint32_t)(b * NP), sH_a + (uint32_t)(b * G::kHBytes), sW_a, sgn,
-                                    &mbar[b]);
+                issue_mmas<C8P, NP, 1>(tmem + (uint32_t)(b * NP), sH_a + (uint32_t)(b * G::kHBytes), sW_a, sgn,
+                                       &mbar[b]);
             }
             if (i > 0) {   // tile i - 1's MMAs: done before its halo buffer is refilled
                 if (!__syncthreads_and(threadIdx.x != 0 || mbar_wait(&mbar[b ^ 1], ((i - 1) >> 1) & 1, status)))
@@ -428,7 +440,7 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
             if (next < ntiles) {
                 int nz, ny, nx0;
                 origin(next, nz, ny, nx0);
-                stage_halo<C8P>(src, sH + (size_t)(b ^ 1) * G::kHBytes, nz, ny, nx0, cv);
+                stage_halo<C8P, 1>(src, sH + (size_t)(b ^ 1) * G::kHBytes, nz, ny, nx0, cv);
             }
             if (i > 0) {
                 epilogue<NP>(src, tmem + (uint32_t)((b ^ 1) * NP), pz, py, px0, N, bias, relu, osc, out);

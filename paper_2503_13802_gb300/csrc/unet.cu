@@ -239,12 +239,12 @@ int umma_mode()
 bool umma_enabled() { return umma_mode() != 0; }
 bool umma_prefers(const ConvSrc& s) { return umma_mode() == 2 || (!s.f32 && s.W >= 96); }
 
-template <int C8P, int NP, int NB, class OutT>
+template <int C8P, int NP, int NB, int R, class OutT>
 cudaError_t launch_umma_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, const float* bias, int relu,
                           const float* oscale, OutT* out, int* status, cudaStream_t st)
 {
-    using G = umma::Geom<C8P, NP, NB>;
-    auto* fn = umma::k_conv_umma<C8P, NP, NB, OutT>;
+    using G = umma::Geom<C8P, NP, NB, R>;
+    auto* fn = umma::k_conv_umma<C8P, NP, NB, R, OutT>;
     const size_t smem = G::smem();
     if (smem > (size_t)smem_optin()) return cudaErrorInvalidValue;
     static int occ = 0;   // resident CTAs per SM, with the attributes set (once)
@@ -267,11 +267,19 @@ cudaError_t launch_umma_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, cons
         const int by_regs = regs_sm / std::max(1, fa.numRegs * umma::kT);
         occ = std::max(1, std::min(std::min(by_smem, by_regs), std::min(2048 / umma::kT, 512 / G::kCols)));
     }
-    const long long tiles = (long long)((s.W + umma::kM - 1) / umma::kM) * s.H * s.D;
+    const long long tiles = (long long)((s.W + umma::kM - 1) / umma::kM) * ((s.H + R - 1) / R) * s.D;
     if (tiles > (1LL << 30)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long long>(tiles, (long long)num_sms() * occ);
     fn<<<grid, umma::kT, smem, st>>>(s, Wu, N, bias, relu, oscale, out, (int)tiles, status);
     return cudaGetLastError();
+}
+
+// Output rows per tile of the tcgen05 kernel (MH3D_UMMA_ROWS = 1, 2 or 4).
+int umma_rows()
+{
+    const char* e = std::getenv("MH3D_UMMA_ROWS");
+    if (e && (e[0] == '1' || e[0] == '2' || e[0] == '4')) return e[0] - '0';
+    return 2;
 }
 
 // One halo buffer and accumulator per CTA, several CTAs per SM (the
@@ -286,8 +294,13 @@ cudaError_t launch_umma_nb(const ConvSrc& s, const UmmaW& u, int N, const float*
     const char* e = std::getenv("MH3D_UMMA_NB");
     const bool two = e && e[0] == '2';
     if (two && umma::Geom<C8P, NP, 2>::smem() <= (size_t)smem_optin())
-        return launch_umma_t<C8P, NP, 2>(s, u.w, N, bias, relu, oscale, out, status, st);
-    return launch_umma_t<C8P, NP, 1>(s, u.w, N, bias, relu, oscale, out, status, st);
+        return launch_umma_t<C8P, NP, 2, 1>(s, u.w, N, bias, relu, oscale, out, status, st);
+    const int R = umma_rows();
+    if (R == 4 && umma::Geom<C8P, NP, 1, 4>::smem() <= (size_t)smem_optin())
+        return launch_umma_t<C8P, NP, 1, 4>(s, u.w, N, bias, relu, oscale, out, status, st);
+    if (R >= 2 && umma::Geom<C8P, NP, 1, 2>::smem() <= (size_t)smem_optin())
+        return launch_umma_t<C8P, NP, 1, 2>(s, u.w, N, bias, relu, oscale, out, status, st);
+    return launch_umma_t<C8P, NP, 1, 1>(s, u.w, N, bias, relu, oscale, out, status, st);
 }
 
 template <int C8P, class OutT>

@@ -27,21 +27,24 @@ torch = pytest.importorskip("torch")
 N_SMALL = (14, 10, 6)   # nx, ny, nz: V = 840, not a multiple of the 128-voxel tile; partial 8x4x4 blocks
 
 
-@pytest.fixture(params=["umma", "umma_nb2", "default", "tiled", "gather"], autouse=True)
+@pytest.fixture(params=["umma", "umma_r1", "umma_r4", "umma_nb2", "default", "tiled", "gather"], autouse=True)
 def conv_path(request, monkeypatch):
     """Every test runs with every convolution the tcgen05/TMEM kernel takes
     on it (MH3D_UNET_UMMA=1: the FP32 input, 8..32 bfloat16 channels in
     multiples of 8, up to 64 outputs; the others go to the mma.sync
-    kernels), on its double-buffered form (MH3D_UMMA_NB=2), with the default
-    choice (tcgen05 for bfloat16 sources with rows of 96 voxels or more), on
-    the halo-tiled mma.sync kernel alone (MH3D_UNET_UMMA=0) and on the
-    gather kernel (MH3D_UNET_UMMA=0, MH3D_UNET_GATHER=1)."""
-    for v in ("MH3D_UNET_GATHER", "MH3D_UNET_UMMA", "MH3D_UMMA_NB"):
+    kernels) with two output rows per tile (the default), one and four
+    (MH3D_UMMA_ROWS), on its double-buffered form (MH3D_UMMA_NB=2), with
+    the default choice (tcgen05 for bfloat16 sources with rows of 96 voxels
+    or more), on the halo-tiled mma.sync kernel alone (MH3D_UNET_UMMA=0)
+    and on the gather kernel (MH3D_UNET_UMMA=0, MH3D_UNET_GATHER=1)."""
+    for v in ("MH3D_UNET_GATHER", "MH3D_UNET_UMMA", "MH3D_UMMA_NB", "MH3D_UMMA_ROWS"):
         monkeypatch.delenv(v, raising=False)
-    if request.param in ("umma", "umma_nb2"):
+    if request.param.startswith("umma"):
         monkeypatch.setenv("MH3D_UNET_UMMA", "1")
         if request.param == "umma_nb2":
             monkeypatch.setenv("MH3D_UMMA_NB", "2")
+        elif request.param in ("umma_r1", "umma_r4"):
+            monkeypatch.setenv("MH3D_UMMA_ROWS", request.param[-1])
     elif request.param in ("tiled", "gather"):
         monkeypatch.setenv("MH3D_UNET_UMMA", "0")
         if request.param == "gather":
