@@ -162,12 +162,19 @@ bool tile_conv(const ConvSrc& s, const __nv_bfloat16* Wt, int Kpad, int Npad, in
 {
     const size_t smem = tile_smem<C, BN>(Kpad);
     if (smem > (size_t)smem_optin()) return false;
-    static bool attr = false;
-    if (!attr && smem > 48 * 1024) {
+    // the attribute belongs to the current device: set once per device
+    static bool attr_dev[64] = {};
+    int dev = 0;
+    if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return true;
+    if (dev < 0 || dev >= 64) {
+        *err = cudaErrorInvalidDevice;
+        return true;
+    }
+    if (!attr_dev[dev] && smem > 48 * 1024) {
         if ((*err = cudaFuncSetAttribute(k_conv_tile<C, BN, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem_optin())) != cudaSuccess)
             return true;
-        attr = true;
+        attr_dev[dev] = true;
     }
     // persistent grid: resident CTAs per SM (cached per shared-memory size) x SMs
     static size_t occ_smem = 0;
@@ -247,7 +254,13 @@ cudaError_t launch_umma_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, cons
     auto* fn = umma::k_conv_umma<C8P, NP, NB, R, OutT>;
     const size_t smem = G::smem();
     if (smem > (size_t)smem_optin()) return cudaErrorInvalidValue;
-    static int occ = 0;   // resident CTAs per SM, with the attributes set (once)
+    // resident CTAs per SM, with the attributes set, once per device (the
+    // attributes belong to the current device)
+    constexpr int kDevs = 64;
+    static int occ_dev[kDevs] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
+    int& occ = occ_dev[dev];
     if (occ == 0) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         // the whole carveout to shared memory, so that several CTAs fit
@@ -256,10 +269,9 @@ cudaError_t launch_umma_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, cons
         // resident CTAs per SM from the shared memory (each CTA also reserves
         // 1 KB), the registers and the threads; every resident CTA holds
         // G::kCols of the SM's 512 TMEM columns
-        int dev = 0, smem_sm = 0, regs_sm = 0;
+        int smem_sm = 0, regs_sm = 0;
         cudaFuncAttributes fa{};
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
             cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
             return cudaErrorInvalidValue;

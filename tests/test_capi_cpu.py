@@ -52,6 +52,23 @@ def test_binding_covers_every_declared_symbol():
     assert sorted(mh3d.EXPORTS + unet.EXPORTS) == _declared_functions()
 
 
+@pytest.mark.parametrize("ch", [(2, 3), (8, 16, 32), (16, 32, 64, 128), (2, 3, 4, 5, 6)])
+def test_network_layer_tables_match_the_oracle(lib, ch):
+    """The library's parameter count (its C layer table, a host function
+    callable without a GPU) and the warm start's initialisation table agree
+    with the oracle's layer shapes at every depth."""
+    from oracle import unet_oracle as U
+    from paper_2503_13802_gb300.warmstart import layer_io
+
+    lib.mh3d_unet_param_count_levels.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.mh3d_unet_param_count_levels.restype = ctypes.c_longlong
+    arr = (ctypes.c_int * len(ch))(*ch)
+    assert lib.mh3d_unet_param_count_levels(len(ch), arr) == U.param_count(*ch)
+    io = [(1 if ci is None else ch[ci], 1 if co is None else ch[co]) for ci, co in layer_io(len(ch))]
+    assert io == [(ci, co) for _, ci, co in U.layer_shapes(*ch)]
+    assert lib.mh3d_unet_param_count_levels(1, arr) == -1
+
+
 def test_version_without_gpu(lib):
     lib.mh3d_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.mh3d_version()
