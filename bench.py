@@ -37,7 +37,7 @@ UNIT = "reconstructions/s"
 WORKLOAD = "mh_128x128x64_k8_s2"
 # DRAM bytes (read + write) of one CG iteration's three kernels, summed from
 # one ncu capture with cold L2 (ncu's default cache flush between kernels).
-TRAFFIC_PER_ITER_FUSED = 37889536   # 25.24 MB T_y + 12.65 MB fused T_z + X normal (mean of two iterations)
+TRAFFIC_PER_ITER_FUSED = 37891584   # 25.23 MB T_y + 12.66 MB fused T_z + X normal (mean of four iterations)
 TRAFFIC_PER_ITER = 42103808   # 25.22 MB T_y + 4.24 MB T_z + 12.64 MB X normal (mean of two iterations), writes stay in L2
 
 

@@ -232,12 +232,21 @@ __global__ void k_gen_weight(const float* __restrict__ rho, const float* __restr
 // phases of its s frequencies in registers; SR = 0: any s, re-read per k.
 template <int SR>
 __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restrict__ W, float2* __restrict__ D,
-                           int nx, int mx, int s, int r, int nc, int K, long long N, long long Q,
+                           int nx, int ny, int nz, int mx, int s, int r, int nc, int K, long long N, long long Q,
                            const float2* __restrict__ twx)
 {
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (long long)gridDim.x * blockDim.x) {
+    // D_k is the spectrum of a real portrait image: D_k(-q) = conj(D_k(q)).
+    // Threads cover the planes z <= nz / 2 and write the mirror of every q
+    // off the planes z = 0 and 2 z = nz (which hold their own mirrors and
+    // are computed in full), so each spectrum sample is read for one of
+    // f and -f only.
+    const long long Qh = (long long)(nz / 2 + 1) * ny * mx;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Qh; q += (long long)gridDim.x * blockDim.x) {
         const int w = (int)(q % mx);
         const long long row = (q - w) / mx * nx;   // (z ny + y) nx
+        const int yz = (int)((q - w) / mx), y = yz % ny, z = yz / ny;
+        const bool mirror = z != 0 && 2 * z != nz;
+        const long long qm = ((long long)(nz - z) * ny + (ny - y) % ny) * mx + (mx - w) % mx;
         if constexpr (SR > 0) {
             float2 wv[SR][3], ph[SR];
 #pragma unroll
@@ -266,6 +275,7 @@ __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restric
                     }
                 }
                 D[(long long)k * Q + q] = acc;
+                if (mirror) D[(long long)k * Q + qm] = make_float2(acc.x, -acc.y);
             }
         } else {
             for (int k = 0; k < K; ++k) {
@@ -280,6 +290,7 @@ __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restric
                     acc = c_add(acc, c_mul(t, make_float2(tw.x, -tw.y)));
                 }
                 D[(long long)k * Q + q] = acc;
+                if (mirror) D[(long long)k * Q + qm] = make_float2(acc.x, -acc.y);
             }
         }
     }
@@ -311,14 +322,21 @@ __global__ void k_gen_unphase(const float2* __restrict__ d, float2* __restrict__
 // has the spectrum e^{-2 pi i f r / nx} U_k(f mod mx) along x, U_k the
 // transform of u_k over the portrait grid (s / nx = 1 / mx), so
 //   V_j(f) = e^{-2 pi i f r / nx} sum_k conj(H_kj(f)) U_k(f mod mx).
-// One thread per frequency f walks the harmonics.
+// One thread per frequency f walks the harmonics.  V_j is the spectrum of
+// a real image (H, U real images' spectra): V_j(-f) = conj(V_j(f)), so the
+// threads cover the planes z <= nz / 2 and write the mirrors off the planes
+// z = 0 and 2 z = nz, as the fold does.
 __global__ void k_gen_unfold(const float2* __restrict__ H, const float2* __restrict__ U, float2* __restrict__ V,
-                             int nx, int mx, int r, int nc, int K, long long N, long long Q,
+                             int nx, int ny, int nz, int mx, int r, int nc, int K, long long N, long long Q,
                              const float2* __restrict__ twx)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const long long Nh = (long long)(nz / 2 + 1) * ny * nx;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Nh; i += (long long)gridDim.x * blockDim.x) {
         const int f = (int)(i % nx);
-        const long long qi = (i - f) / nx * mx + f % mx;
+        const int yz = (int)((i - f) / nx), y = yz % ny, z = yz / ny;
+        const bool mirror = z != 0 && 2 * z != nz;
+        const long long im = ((long long)(nz - z) * ny + (ny - y) % ny) * nx + (nx - f) % nx;
+        const long long qi = (long long)yz * mx + f % mx;
         float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         for (int k = 0; k < K; ++k) {
             const float2 u = U[(long long)k * Q + qi];
@@ -334,7 +352,11 @@ __global__ void k_gen_unfold(const float2* __restrict__ H, const float2* __restr
         const float2 tw = twx[(int)(((long long)f * r) % nx)];   // e^{-2 pi i f r / nx}
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-            if (j < nc) V[(long long)j * N + i] = c_mul(acc[j], tw);
+            if (j < nc) {
+                const float2 v = c_mul(acc[j], tw);
+                V[(long long)j * N + i] = v;
+                if (mirror) V[(long long)j * N + im] = make_float2(v.x, -v.y);
+            }
     }
 }
 
@@ -546,12 +568,16 @@ mh3d_status mh3d_general_forward(mh3d_plan Pp, const float* rho, const float* bv
         GEN_CK(P, cudaGetLastError());
         GEN_CK(P, gen_fft3(P, W, nc, P.ax, false, st));
     }
+    const long long Qh = (long long)(P.nz / 2 + 1) * P.ny * P.mx;   // the planes the fold's threads cover
     if (P.s <= 2)
-        k_gen_fold<2><<<gen_blocks(Q), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.mx, P.s, P.r, nc, P.K, N, Q, P.ax.tw);
+        k_gen_fold<2><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
+                                                      P.ax.tw);
     else if (P.s <= 4)
-        k_gen_fold<4><<<gen_blocks(Q), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.mx, P.s, P.r, nc, P.K, N, Q, P.ax.tw);
+        k_gen_fold<4><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
+                                                      P.ax.tw);
     else
-        k_gen_fold<0><<<gen_blocks(Q), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.mx, P.s, P.r, nc, P.K, N, Q, P.ax.tw);
+        k_gen_fold<0><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
+                                                      P.ax.tw);
     GEN_CK(P, cudaGetLastError());
     if (gen_ct_length(P.az.n)) {   // the phase applied in the z pass's store
         GEN_CK(P, gen_fft3(P, D, P.K, P.am, true, st, 0, 2, io));
@@ -586,7 +612,8 @@ mh3d_status mh3d_general_adjoint(mh3d_plan Pp, const void* d, const float* bvec,
         GEN_CK(P, cudaGetLastError());
         GEN_CK(P, gen_fft3(P, U, P.K, P.am, false, st));
     }
-    k_gen_unfold<<<gen_blocks(N), kGB, 0, st>>>(P.gen_H, U, V, P.nx, P.mx, P.r, nc, P.K, N, Q, P.ax.tw);
+    const long long Nh = (long long)(P.nz / 2 + 1) * P.ny * P.nx;   // the planes the unfold's threads cover
+    k_gen_unfold<<<gen_blocks(Nh), kGB, 0, st>>>(P.gen_H, U, V, P.nx, P.ny, P.nz, P.mx, P.r, nc, P.K, N, Q, P.ax.tw);
     GEN_CK(P, cudaGetLastError());
     GEN_CK(P, gen_fft3(P, V, nc, P.ax, true, st));
     k_gen_out<<<gen_blocks(N), kGB, 0, st>>>(V, bvec, out, N, nc);

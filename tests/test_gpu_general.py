@@ -27,6 +27,8 @@ CASES = {
     # phase fused in its store)
     "ct_lengths_vector_b": (dict(n=(128, 64, 8), s=2, r=1, kmin=2, kmax=5), True),
     "ct_z64_drive_b": (dict(n=(16, 8, 64), s=2, r=0, kmin=2, kmax=4), False),
+    # odd n_z and n_y: the half-spectrum fold's mirror planes without a middle plane
+    "odd_nz9_vector_b": (dict(n=(16, 9, 9), s=2, r=1, kmin=2, kmax=4), True),
 }
 
 
