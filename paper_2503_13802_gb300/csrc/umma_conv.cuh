@@ -4,21 +4,23 @@
 // descriptors and accumulating in tensor memory (TMEM); the epilogue reads
 // the accumulators back with tcgen05.ld.
 //
-// The GEMM of one output tile.  A tile is 128 consecutive voxels of one x
-// row (z, y, x0 .. x0 + 127); its accumulator D[128][NP] (FP32, NP >= N
-// output channels, a multiple of 16) lives in NP TMEM columns, lane m =
-// voxel x0 + m.  For every tap (dz, dy, dx) and every 16 input channels
-//     D[m][n] += sum_{c < 16} in[z + dz][y + dy][x0 + m + dx][c] W[n][tap][c]
+// The GEMM of one output tile.  A tile is R x rows of 128 consecutive
+// voxels (z, y0 + r, x0 .. x0 + 127), r < R; row r's accumulator
+// D_r[128][NP] (FP32, NP >= N output channels, a multiple of 16) lives in
+// TMEM columns r NP .. r NP + NP - 1, lane m = voxel x0 + m.  For every row,
+// tap (dz, dy, dx) and 16 input channels
+//     D_r[m][n] += sum_{c < 16} in[z + dz][y0 + r + dy][x0 + m + dx][c] W[n][tap][c]
 // is one tcgen05.mma with M = 128, N = NP, K = 16.
 //
 // Operand layout (no swizzle, K-major canonical layout: 8 rows x 16 bytes
 // per core matrix, rows 16 bytes apart, core matrices along M 128 bytes
 // apart, along K `LBO` bytes apart):
-//   halo: the tile's 3 x 3 neighbouring x rows, x0 - 1 .. x0 + 128, staged
-//         as planes [chunk of 8 channels][dz][dy][kHP voxels][8]: a plane
-//         is 136 x 16 bytes, so the A operand of tap (dz, dy, dx) is the
-//         plane (dz, dy) started dx + 1 rows in -- a descriptor offset, no
-//         data movement -- and the tap's second 8 channels sit 9 planes on;
+//   halo: the tile's 3 x (R + 2) neighbouring x rows, x0 - 1 .. x0 + 128,
+//         staged as planes [chunk of 8 channels][dz][dy][kHP voxels][8]: a
+//         plane is 136 x 16 bytes, so the A operand of tap (dz, dy, dx) for
+//         row r is the plane (dz, r + dy) started dx + 1 rows in -- a
+//         descriptor offset, no data movement -- and the tap's second 8
+//         channels sit 3 (R + 2) planes on;
 //   weights: [tap][chunk][NP][8], the B operand of (tap, chunk pair) one
 //         descriptor, its second 8 channels NP rows on.
 // Chunks are padded to an even count with zeros (8 channels: one zero
