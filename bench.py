@@ -976,6 +976,15 @@ def bench_general(args):
     spectra = K * 3 * N * 8
     alg_f = N * 4 + 3 * N * 4 + spectra + K * M * 8
     alg_a = K * M * 8 + spectra + 3 * N * 4 + N * 4
+    # the general model's CG (mh3d_general_solve), a fixed number of
+    # iterations on the portraits of rho: time per solve / iterations
+    from paper_2503_13802_gb300 import make_opts, mh3d_general_solve
+    fwd()
+    x = torch.empty(plan.shape, dtype=torch.float32, device=dev)
+    it = 20
+    go = make_opts(lam=1e-3, max_iter=it, fixed_iters=True)
+    mh3d_general_solve(plan, d, go, x, bvec)
+    sol_us = float(np.median([timed(lambda: mh3d_general_solve(plan, d, go, x, bvec)) for _ in range(3)]))
     try:
         peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
     except (OSError, ValueError):
@@ -991,6 +1000,9 @@ def bench_general(args):
         "adjoint": {"us": us_a, "alg_bytes": alg_a, "achieved_gbs": alg_a / us_a / 1e3,
                     "frac": alg_a / us_a / 1e3 / peak, "launches": 8},
         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+        "general_cg": {"iterations": it, "us_per_solve": sol_us, "us_per_iteration": sol_us / it,
+                       "what": "mh3d_general_solve, lambda 1e-3, fixed iterations (A^T d, the CG set-up and "
+                               "one forward + adjoint per iteration through the portrait buffer)"},
     }
     print(json.dumps(line), flush=True)
 
