@@ -501,8 +501,11 @@ void general_free(Plan& P)
 {
     if (P.gen_H) cudaFree(P.gen_H);
     if (P.gen_work) cudaFree(P.gen_work);
+    if (P.gen_cg) cudaFree(P.gen_cg);
     P.gen_H = nullptr;
     P.gen_work = nullptr;
+    P.gen_cg = nullptr;
+    P.gen_cg_cap = 0;
 }
 
 }  // namespace mh3d

@@ -161,6 +161,10 @@ struct Plan {
     // mh3d_general_set_psf
     float2* gen_H = nullptr;
     float2* gen_work = nullptr;
+    // the general CG's device scalars and residual history (solve.cu),
+    // grown on demand: gen_cg_cap doubles
+    double* gen_cg = nullptr;
+    size_t gen_cg_cap = 0;
 
     // CUDA graph of the CG loop, cached per (mode, reg, fixed) key
     cudaGraphExec_t graph_exec = nullptr;

@@ -1202,10 +1202,11 @@ static mh3d_status apg_solve(Plan& P, const float2* d, const mh3d_solve_opts& o,
 // ---------------------------------------------------------------------------
 // CG on the general three-component model (Sec. 3.2, Eq. matrixModel; the
 // solver of Sec. 4.3 applies to any A): (A^T A + lambda I) x = A^T d with A
-// the forward of mh3d_general_forward.  Classic CG (Hestenes-Stiefel) driven
-// from the host: the normal operator goes through the plan's portrait buffer
-// (A p, then A^T), the dot products are the solvers' float-pair sums, the
-// scalars are FP64 on the host, and the vector updates run on the device.
+// the forward of mh3d_general_forward.  Classic CG (Hestenes-Stiefel) on the
+// device: the normal operator goes through the plan's portrait buffer (A p,
+// then A^T), the dot products are the solvers' float-pair sums into device
+// FP64 scalars, the step lengths are formed from them per CTA (FP64), and a
+// one-thread kernel keeps the count, the history and the stopping rule.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_axpy(float* __restrict__ y, const float* __restrict__ x, float a, long long N)
 {
@@ -1234,6 +1235,85 @@ __global__ void __launch_bounds__(256) k_sub(float* __restrict__ d, const float*
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
         d[i] = b[i] - a[i];
+}
+
+// The general CG's device state: g[kGB..] scalars, then the history.
+enum GenCg { kGBn = 0, kGRr = 1, kGPq = 2, kGRn = 3, kGDone = 4, kGIt = 5, kGBad = 6, kGHist = 8 };
+
+// x += alpha p, r -= alpha q with alpha = rr / pq (FP64, once per CTA), unless
+// the loop is done or pq is not positive (recorded by k_gcg_step).
+__global__ void __launch_bounds__(256) k_gcg_xr(float* __restrict__ x, float* __restrict__ r,
+                                                const float* __restrict__ p, const float* __restrict__ q,
+                                                const double* __restrict__ g, long long N)
+{
+    __shared__ float a_s;
+    if (threadIdx.x == 0) {
+        const double pq = g[kGPq];
+        a_s = (g[kGDone] != 0.0 || !(pq > 0.0)) ? 0.f : (float)(g[kGRr] / pq);
+    }
+    __syncthreads();
+    const float a = a_s;
+    if (a == 0.f) return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fmaf(a, p[i], x[i]);
+        r[i] = fmaf(-a, q[i], r[i]);
+    }
+}
+
+// p = r + beta p with beta = rr_new / rr, unless the loop is done.
+__global__ void __launch_bounds__(256) k_gcg_p(float* __restrict__ p, const float* __restrict__ r,
+                                               const double* __restrict__ g, long long N)
+{
+    __shared__ float b_s;
+    __shared__ int skip;
+    if (threadIdx.x == 0) {
+        const double pq = g[kGPq];
+        skip = g[kGDone] != 0.0 || !(pq > 0.0);
+        b_s = skip ? 0.f : (float)(g[kGRn] / g[kGRr]);
+    }
+    __syncthreads();
+    if (skip) return;
+    const float beta = b_s;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        p[i] = fmaf(beta, p[i], r[i]);
+}
+
+// The step's scalars (one thread): rr = rr_new, the iteration count, the
+// history, and the stopping rule (converged, max_iter, or a non-finite or
+// non-positive value: recorded in kGBad).
+__global__ void k_gcg_step(double* __restrict__ g, double tol2, int max_iter)
+{
+    if (g[kGDone] != 0.0) return;
+    const double pq = g[kGPq], rn = g[kGRn], bn = g[kGBn];
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rn)) {
+        g[kGBad] = 1.0;
+        g[kGDone] = 1.0;
+        return;
+    }
+    const int it = (int)g[kGIt] + 1;
+    g[kGRr] = rn;
+    g[kGIt] = (double)it;
+    g[kGHist + it] = bn > 0.0 ? sqrt(rn / bn) : 0.0;
+    if (rn == 0.0 || (tol2 > 0.0 && rn <= tol2 * bn) || it >= max_iter) g[kGDone] = 1.0;
+}
+
+// The loop's initial state from bn and rr in g (one thread).
+__global__ void k_gcg_init(double* __restrict__ g, double tol2, int max_iter)
+{
+    const double bn = g[kGBn], rr = g[kGRr];
+    g[kGIt] = 0.0;
+    g[kGBad] = (isfinite(bn) && isfinite(rr)) ? 0.0 : 1.0;
+    g[kGHist] = bn > 0.0 ? sqrt(rr / bn) : 0.0;
+    g[kGDone] = (g[kGBad] != 0.0 || rr == 0.0 || bn == 0.0 || (tol2 > 0.0 && rr <= tol2 * bn) || max_iter <= 0)
+                    ? 1.0 : 0.0;
+}
+
+// a^T b on the device into *out (no host synchronisation).
+static cudaError_t dot_dev(Plan& P, const float* a, const float* b, double* out, cudaStream_t st)
+{
+    const int nb = (int)std::min<long long>(update_blocks(P.N), (long long)P.w.red_cap);
+    k_dot<<<nb, 256, 0, st>>>(a, b, P.N, part_slot(P, kPartRES), ticket(P, kTkRES), out);
+    return cudaGetLastError();
 }
 
 // a^T b on the device, returned to the host (synchronises `st`).
@@ -1289,42 +1369,51 @@ static mh3d_status general_cg(Plan& P, const void* d, const float* bvec, const m
         MH3D_CK(P, cudaMemcpyAsync(w.r, w.rhs, vb, cudaMemcpyDeviceToDevice, st));
     }
     MH3D_CK(P, cudaMemcpyAsync(w.p, w.r, vb, cudaMemcpyDeviceToDevice, st));
-    double bn = 0.0, rr = 0.0;
-    if ((s = dot_host(P, w.rhs, w.rhs, st, &bn)) != MH3D_OK) return s;
-    if ((s = dot_host(P, w.r, w.r, st, &rr)) != MH3D_OK) return s;
-    std::vector<double> hist;
-    hist.push_back(bn > 0 ? std::sqrt(rr / bn) : 0.0);
-    const double tol2 = o.fixed_iters ? 0.0 : o.rel_tol * o.rel_tol;
-    int it = 0;
-    mh3d_status status = MH3D_OK;
-    while (true) {
-        if (!std::isfinite(rr) || !std::isfinite(bn)) {
-            status = MH3D_ERR_NONFINITE;
-            break;
-        }
-        if (rr == 0.0 || bn == 0.0 || (tol2 > 0.0 && rr <= tol2 * bn)) break;
-        if (it >= o.max_iter) {
-            if (tol2 > 0.0) status = MH3D_ERR_NOT_CONVERGED;
-            break;
-        }
-        if ((s = general_normal(P, w.p, bvec, o.lambda, w.q, st)) != MH3D_OK) return s;
-        double pq = 0.0;
-        if ((s = dot_host(P, w.p, w.q, st, &pq)) != MH3D_OK) return s;
-        if (!(pq > 0.0) || !std::isfinite(pq)) {
-            status = MH3D_ERR_NONFINITE;
-            break;
-        }
-        const double alpha = rr / pq;
-        k_cg_xr<<<nU, 256, 0, st>>>(w.x, w.r, w.p, w.q, (float)alpha, P.N);
-        MH3D_CK(P, cudaGetLastError());
-        double rr_new = 0.0;
-        if ((s = dot_host(P, w.r, w.r, st, &rr_new)) != MH3D_OK) return s;
-        k_xpby<<<nU, 256, 0, st>>>(w.p, w.r, (float)(rr_new / rr), P.N);
-        MH3D_CK(P, cudaGetLastError());
-        rr = rr_new;
-        ++it;
-        hist.push_back(bn > 0 ? std::sqrt(rr / bn) : 0.0);
+    // the scalars and the history live on the device; the host looks at the
+    // done flag every kChunk iterations (kernels of iterations launched after
+    // the stop return at once, so x and the count are exact)
+    const size_t need = (size_t)kGHist + (size_t)std::max(o.max_iter, 0) + 1;
+    if (P.gen_cg_cap < need) {
+        if (P.gen_cg) cudaFree(P.gen_cg);
+        P.gen_cg = nullptr;
+        P.gen_cg_cap = 0;
+        MH3D_CK(P, dev_malloc(&P.gen_cg, sizeof(double) * need));
+        P.gen_cg_cap = need;
     }
+    double* g = P.gen_cg;
+    const double tol2 = o.fixed_iters ? 0.0 : o.rel_tol * o.rel_tol;
+    MH3D_CK(P, dot_dev(P, w.rhs, w.rhs, g + kGBn, st));
+    MH3D_CK(P, dot_dev(P, w.r, w.r, g + kGRr, st));
+    k_gcg_init<<<1, 1, 0, st>>>(g, tol2, o.max_iter);
+    MH3D_CK(P, cudaGetLastError());
+    constexpr int kChunk = 8;
+    int launched = 0;
+    while (launched < o.max_iter) {
+        MH3D_CK(P, cudaMemcpyAsync(P.w.red_host, g + kGDone, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MH3D_CK(P, cudaStreamSynchronize(st));
+        if (P.w.red_host[0] != 0.0) break;
+        for (int c = 0; c < kChunk && launched < o.max_iter; ++c, ++launched) {
+            if ((s = general_normal(P, w.p, bvec, o.lambda, w.q, st)) != MH3D_OK) return s;
+            MH3D_CK(P, dot_dev(P, w.p, w.q, g + kGPq, st));
+            k_gcg_xr<<<nU, 256, 0, st>>>(w.x, w.r, w.p, w.q, g, P.N);
+            MH3D_CK(P, cudaGetLastError());
+            MH3D_CK(P, dot_dev(P, w.r, w.r, g + kGRn, st));
+            k_gcg_p<<<nU, 256, 0, st>>>(w.p, w.r, g, P.N);
+            k_gcg_step<<<1, 1, 0, st>>>(g, tol2, o.max_iter);
+            MH3D_CK(P, cudaGetLastError());
+        }
+    }
+    std::vector<double> gh(need);
+    MH3D_CK(P, cudaMemcpyAsync(gh.data(), g, sizeof(double) * need, cudaMemcpyDeviceToHost, st));
+    MH3D_CK(P, cudaStreamSynchronize(st));
+    const double bn = gh[kGBn], rr = gh[kGRr];
+    const int it = (int)gh[kGIt];
+    std::vector<double> hist(gh.begin() + kGHist, gh.begin() + kGHist + it + 1);
+    mh3d_status status = MH3D_OK;
+    if (gh[kGBad] != 0.0 || !std::isfinite(rr) || !std::isfinite(bn))
+        status = MH3D_ERR_NONFINITE;
+    else if (tol2 > 0.0 && rr > tol2 * bn && bn > 0.0 && rr > 0.0)
+        status = MH3D_ERR_NOT_CONVERGED;
     // true residual ||A^T d - (A^T A + lambda I) x|| / ||A^T d||
     if ((s = general_normal(P, w.x, bvec, o.lambda, w.q, st)) != MH3D_OK) return s;
     k_sub<<<nU, 256, 0, st>>>(w.q, w.rhs, w.q, P.N);
