@@ -135,6 +135,27 @@ def test_conv_forward_multi_tile_rows(n, cin, cout, mode):
     assert rel_l2(got, ref) <= 1e-5, rel_l2(got, ref)
 
 
+@pytest.mark.parametrize("cin,cout,mode", [(8, 8, "plain"), (16, 8, "up"), (8, 8, "skip"), (8, 1, "plain")])
+def test_conv_forward_at_the_bench_size(cin, cout, mode, conv_path):
+    """The warm-start network's full-resolution layers at 128x128x64 (the
+    size the learned benchmark runs), element by element against the
+    oracle, on the tcgen05 kernel (default and forced) and the mma.sync
+    tiles."""
+    from paper_2503_13802_gb300.unet import mh3d_unet_conv_forward
+
+    if conv_path not in ("default", "umma", "tiled"):
+        pytest.skip("the full-size layers run on the default, tcgen05 and tiled paths")
+
+    n = (128, 128, 64)
+    kw, x = _sources(n, cin, mode, 40 * cin + cout)
+    W, b = _w(cout, cin, cin * 3 + cout)
+    out = torch.empty(n[2] * n[1] * n[0] * cout, dtype=torch.float32, device="cuda")
+    mh3d_unet_conv_forward(n, cin, cout, W.cuda(), b.cuda(), out, relu=True, **kw)
+    ref = U.relu(U.conv(x, _np(W).reshape(cout, 3, 3, 3, cin), _np(b)))
+    got = out.cpu().numpy().reshape(ref.shape)
+    assert rel_l2(got, ref) <= 1e-5, rel_l2(got, ref)
+
+
 @pytest.mark.parametrize("cin,cout", [(1, 16), (16, 16), (16, 32), (64, 32), (16, 1), (12, 16), (32, 8)])
 def test_conv_input_grad_matches_oracle(cin, cout):
     from paper_2503_13802_gb300.unet import mh3d_unet_conv_input_grad
