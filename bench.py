@@ -68,8 +68,9 @@ def parse():
     ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--channels", type=int, nargs="+", default=[16, 32, 64],
-                    help="learned: channels per level of the warm-start network (2..5 levels)")
+    ap.add_argument("--channels", type=int, nargs="+", default=[16, 32, 64, 128],
+                    help="learned: channels per level of the warm-start network (2..5 levels; default the "
+                         "four-level 16-128 network)")
     ap.add_argument("--count-iters", action="store_true",
                     help="reference arm: run the oracle's CG to the tolerance once and print its iteration count")
     return ap.parse_args()
