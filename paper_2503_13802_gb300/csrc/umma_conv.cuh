@@ -163,7 +163,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // arithmetic: their units are loaded into registers in batches (all loads
 // of a batch in flight), combined and stored.
 template <int C8P, int R>
-__device__ __forceinline__ void stage_halo(const ConvSrc& src, unsigned char* sH, int z, int y, int x0, int cv)
+__device__ __forceinline__ void stage_halo(const ConvSrc& src, unsigned char* sH, int z, int y, int x0, int cv,
+                                           int tid = threadIdx.x, int nthr = kT)
 {
     constexpr int PL = planes<R>();
     constexpr int NV = PL * 130;
@@ -182,7 +183,7 @@ __device__ __forceinline__ void stage_halo(const ConvSrc& src, unsigned char* sH
         }
     };
     if (!src.b && !src.f32) {
-        for (int vi = threadIdx.x; vi < NV; vi += kT) {
+        for (int vi = tid; vi < NV; vi += nthr) {
             unsigned char* d;
             long long off;
             voxel(vi, d, off);
@@ -196,13 +197,13 @@ __device__ __forceinline__ void stage_halo(const ConvSrc& src, unsigned char* sH
     if (src.f32) {
         constexpr int kB = 8;
         const float fsc = src.f32_scale ? *src.f32_scale : 1.f;
-        for (int v0 = threadIdx.x; v0 < NV; v0 += kB * kT) {
+        for (int v0 = tid; v0 < NV; v0 += kB * nthr) {
             unsigned char* d[kB];
             long long off[kB];
             float f[kB];
 #pragma unroll
             for (int i = 0; i < kB; ++i) {
-                const int vi = v0 + i * kT;
+                const int vi = v0 + i * nthr;
                 if (vi < NV) voxel(vi, d[i], off[i]);
                 else off[i] = -2;
             }
@@ -219,13 +220,13 @@ __device__ __forceinline__ void stage_halo(const ConvSrc& src, unsigned char* sH
         return;
     }
     constexpr int kB = 8 / C8P > 0 ? 8 / C8P : 1;   // voxels per batch: 8 chunk units
-    for (int v0 = threadIdx.x; v0 < NV; v0 += kB * kT) {
+    for (int v0 = tid; v0 < NV; v0 += kB * nthr) {
         unsigned char* d[kB];
         long long off[kB];
         uint4 va[kB][C8P], vb[kB][C8P];
 #pragma unroll
         for (int i = 0; i < kB; ++i) {
-            const int vi = v0 + i * kT;
+            const int vi = v0 + i * nthr;
             if (vi < NV) voxel(vi, d[i], off[i]);
             else off[i] = -2;
         }
@@ -307,23 +308,52 @@ __device__ __forceinline__ void epilogue(const ConvSrc& src, uint32_t acc, int z
 
 // The R x 27 x C8P / 2 MMAs of one tile (row r into the accumulator at
 // column acc + r NP), committed to `bar` (one thread).
+// The rows' MMAs are interleaved (tap by tap, each row in turn): an MMA's
+// successor accumulates into another row's columns, so R chains of
+// dependent MMAs are in flight instead of one.
+//
+// Paired taps (pair != 0; sources of at most 8 channels, whose second chunk
+// is zero padding): one MMA takes two taps of the same (dz, dx) whose planes
+// are neighbours -- plane offsets 0 and 1, the second chunk LBO = one plane
+// on -- and a second MMA the third plane with a zero second chunk: 18 MMAs a
+// row instead of 27.  The paired weights ([3 pz][3 px][2 g][2 c][NP][8],
+// k_prep_umma_pair) are indexed by plane offsets, the flip folded in.
 template <int C8P, int NP, int R>
-__device__ __forceinline__ void issue_mmas(uint32_t acc, uint32_t sH_a, uint32_t sW_a, int sgn, uint64_t* bar)
+__device__ __forceinline__ void issue_mmas(uint32_t acc, uint32_t sH_a, uint32_t sW_a, int sgn, uint64_t* bar,
+                                           int pair = 0)
 {
     constexpr uint32_t kIdesc = idesc_bf16(kM, NP);
     constexpr int PL = planes<R>();
-    for (int r = 0; r < R; ++r) {
-        uint32_t accumulate = 0;
-        for (int tap = 0; tap < 27; ++tap) {
-            const int dz = sgn * (tap / 9 - 1), dy = sgn * ((tap / 3) % 3 - 1), dx = sgn * (tap % 3 - 1);
-            const int plane = (dz + 1) * (R + 2) + (r + dy + 1);
+    if (pair) {
+        for (int pz = 0; pz < 3; ++pz)
+            for (int px = 0; px < 3; ++px)
 #pragma unroll
-            for (int ks = 0; ks < C8P / 2; ++ks) {
+                for (int g = 0; g < 2; ++g) {
+                    const uint32_t b = sW_a + (uint32_t)((((pz * 3 + px) * 2 + g) * 2) * NP * 16);
+                    const uint64_t bdesc = smem_desc(b, NP * 16, 128);
+                    const uint32_t accumulate = (pz | px | g) != 0;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int plane = pz * (R + 2) + r + 2 * g;
+                        const uint32_t a = sH_a + (uint32_t)((plane * kHP + px) * 16);
+                        mma_f16(acc + (uint32_t)(r * NP), smem_desc(a, kHP * 16, 128), bdesc, kIdesc, accumulate);
+                    }
+                }
+        mma_commit(bar);
+        return;
+    }
+    for (int tap = 0; tap < 27; ++tap) {
+        const int dz = sgn * (tap / 9 - 1), dy = sgn * ((tap / 3) % 3 - 1), dx = sgn * (tap % 3 - 1);
+#pragma unroll
+        for (int ks = 0; ks < C8P / 2; ++ks) {
+            const uint32_t b = sW_a + (uint32_t)((tap * C8P + 2 * ks) * NP * 16);
+            const uint64_t bdesc = smem_desc(b, NP * 16, 128);
+            const uint32_t accumulate = (tap | ks) != 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int plane = (dz + 1) * (R + 2) + (r + dy + 1);
                 const uint32_t a = sH_a + (uint32_t)(((2 * ks * PL + plane) * kHP + dx + 1) * 16);
-                const uint32_t b = sW_a + (uint32_t)((tap * C8P + 2 * ks) * NP * 16);
-                mma_f16(acc + (uint32_t)(r * NP), smem_desc(a, PL * kHP * 16, 128), smem_desc(b, NP * 16, 128),
-                        kIdesc, accumulate);
-                accumulate = 1;
+                mma_f16(acc + (uint32_t)(r * NP), smem_desc(a, PL * kHP * 16, 128), bdesc, kIdesc, accumulate);
             }
         }
     }
@@ -335,8 +365,9 @@ template <int C8P, int NP, int NB, int R, class OutT>
 __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat16* __restrict__ Wu, int N,
                                                   const float* __restrict__ bias, int relu,
                                                   const float* __restrict__ oscale, OutT* __restrict__ out,
-                                                  int ntiles, int* status)
+                                                  int ntiles, int* status, const __nv_bfloat16* __restrict__ Wpair)
 {
+    const int pair = (Wpair != nullptr && NB == 1) ? 1 : 0;   // paired taps (NB == 1 form only)
     using G = Geom<C8P, NP, NB, R>;
     extern __shared__ unsigned char umma_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
@@ -359,9 +390,10 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
         fence_barrier_init();
     }
     {
-        const uint4* w4 = reinterpret_cast<const uint4*>(Wu);
+        const uint4* w4 = reinterpret_cast<const uint4*>(pair ? Wpair : Wu);
         uint4* s4 = reinterpret_cast<uint4*>(sW);
-        for (int i = threadIdx.x; i < G::kWBytes / 16; i += kT) s4[i] = w4[i];
+        const int n16 = pair ? 9 * 2 * 2 * NP : G::kWBytes / 16;   // the paired layout is smaller
+        for (int i = threadIdx.x; i < n16; i += kT) s4[i] = w4[i];
     }
     // chunks carrying channels; the padding chunks of every halo buffer are
     // zeroed once and never staged
@@ -398,7 +430,7 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
             __syncthreads();
             if (threadIdx.x == 0) {
                 tc_fence_after();
-                issue_mmas<C8P, NP, R>(tmem, sH_a, sW_a, sgn, &mbar[0]);
+                issue_mmas<C8P, NP, R>(tmem, sH_a, sW_a, sgn, &mbar[0], pair);
             }
             // one thread waits on the MMAs' mbarrier; the block barrier
             // releases the others (no spinning warps taking issue slots)
@@ -466,6 +498,228 @@ __global__ void __launch_bounds__(kT) k_conv_umma(ConvSrc src, const __nv_bfloat
         tc_fence_after();
         tmem_dealloc(tmem, G::kCols);
     }
+}
+
+// ---- the warp-specialised form ---------------------------------------------
+//
+// One persistent CTA per SM, three roles over the same tile sequence
+// (tiles of one x row), linked by mbarriers:
+//   warps 4-7 (producers) stage tile i's halo into ring slot i % NS, after
+//     slot i % NS is released (empty: the MMAs of tile i - NS completed),
+//     keeping NS - 1 tiles of cp.async copies in flight; when a tile's copies
+//     have landed each producer thread fences them for the async proxy and
+//     arrives on full[slot] (128 arrivals);
+//   warp 8, lane 0 (MMA) waits for full[slot] and for the accumulator i % 2
+//     to be drained (acce), issues the tile's MMAs and commits them to
+//     empty[slot] and accf[i % 2];
+//   warps 0-3 (epilogue) wait for accf, read their 32 TMEM lanes, store and
+//     arrive on acce (one arrival per warp).
+// So the staging of the next tiles, this tile's MMAs and the previous
+// tile's epilogue overlap inside the CTA.  Every wait is bounded; a timeout
+// records MH3D_ERR_TIMEOUT, sets the CTA's abort flag, and every role leaves
+// its loop (at the latest after its own bounded wait) before TMEM is freed.
+constexpr int kWsT = 288;   // 4 epilogue warps, 4 producer warps, 1 MMA warp
+
+template <int C8P, int NP, int NS>
+struct GeomWs {
+    static_assert(C8P % 2 == 0 && NP % 16 == 0 && NP >= 16 && NP <= 64 && NS >= 2 && NS <= 4, "operand shape");
+    static constexpr int kWBytes = 27 * C8P * NP * 16;
+    static constexpr int kHBytes = C8P * planes<1>() * kHP * 16;
+    static constexpr int kCols = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : 128);
+    static constexpr size_t smem() { return 1024 + (size_t)kWBytes + (size_t)NS * kHBytes; }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_commit_wait()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The 27 x C8P / 2 MMAs of one row tile into the accumulator at column acc
+// (no commit).
+template <int C8P, int NP>
+__device__ __forceinline__ void issue_mmas_row(uint32_t acc, uint32_t sH_a, uint32_t sW_a, int sgn)
+{
+    constexpr uint32_t kIdesc = idesc_bf16(kM, NP);
+    constexpr int PL = planes<1>();
+    uint32_t accumulate = 0;
+    for (int tap = 0; tap < 27; ++tap) {
+        const int dz = sgn * (tap / 9 - 1), dy = sgn * ((tap / 3) % 3 - 1), dx = sgn * (tap % 3 - 1);
+        const int plane = (dz + 1) * 3 + (dy + 1);
+#pragma unroll
+        for (int ks = 0; ks < C8P / 2; ++ks) {
+            const uint32_t a = sH_a + (uint32_t)(((2 * ks * PL + plane) * kHP + dx + 1) * 16);
+            const uint32_t b = sW_a + (uint32_t)((tap * C8P + 2 * ks) * NP * 16);
+            mma_f16(acc, smem_desc(a, PL * kHP * 16, 128), smem_desc(b, NP * 16, 128), kIdesc, accumulate);
+            accumulate = 1;
+        }
+    }
+}
+
+template <int C8P, int NP, int NS, class OutT>
+__global__ void __launch_bounds__(kWsT, 1) k_conv_umma_ws(ConvSrc src, const __nv_bfloat16* __restrict__ Wu, int N,
+                                                          const float* __restrict__ bias, int relu,
+                                                          const float* __restrict__ oscale, OutT* __restrict__ out,
+                                                          int ntiles, int* status)
+{
+    using G = GeomWs<C8P, NP, NS>;
+    extern __shared__ unsigned char umma_raw[];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], accf[2], acce[2];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_s;
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(umma_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sW = base;
+    unsigned char* sH = base + G::kWBytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = (src.W + kM - 1) / kM;
+    const int sgn = src.flip ? -1 : 1;
+    const bool async_src = !src.b && !src.f32;   // staged by cp.async
+    const int cv = src.f32 ? 1 : (src.C + 7) / 8;
+
+    if (warp == 8) {
+        tmem_alloc(&tmem_base_s, G::kCols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 128);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 4);
+        }
+        abort_s = 0;
+        fence_barrier_init();
+    }
+    {
+        const uint4* w4 = reinterpret_cast<const uint4*>(Wu);
+        uint4* s4 = reinterpret_cast<uint4*>(sW);
+        for (int i = tid; i < G::kWBytes / 16; i += kWsT) s4[i] = w4[i];
+        for (int nb = 0; nb < NS; ++nb) {   // padding chunks: zero once, never staged
+            uint4* h4 = reinterpret_cast<uint4*>(sH + (size_t)nb * G::kHBytes + (size_t)cv * planes<1>() * kHP * 16);
+            const int n16 = (C8P - cv) * planes<1>() * kHP;
+            for (int i = tid; i < n16; i += kWsT) h4[i] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+    const uint32_t sW_a = smem_u32(sW), sH_a = smem_u32(sH);
+    auto origin = [&](int tile, int& z, int& y, int& x0) {
+        const int tx = tile % ntx, row = tile / ntx;
+        y = row % src.H;
+        z = row / src.H;
+        x0 = tx * kM;
+    };
+
+    if (warp >= 4 && warp < 8) {
+        // producers: slot of tile i is i % NS; its full arrival comes NS - 1
+        // tiles later (async sources) or at once (register-staged sources)
+        const int pt = tid - 128;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            const int sl = i % NS, k = i / NS;
+            if (k > 0 && !mbar_wait(&empty[sl], (k - 1) & 1, status)) abort_s = 1;
+            if (abort_s) break;
+            int z, y, x0;
+            origin(tile, z, y, x0);
+            stage_halo<C8P, 1>(src, sH + (size_t)sl * G::kHBytes, z, y, x0, cv, pt, 128);
+            if (async_src) {
+                cp_async_commit();
+                if (i >= NS - 1) {   // tile i - (NS - 1) has landed
+                    cp_async_wait_group<NS - 1>();
+                    fence_proxy_async_smem();
+                    mbar_arrive(&full[(i - (NS - 1)) % NS]);
+                }
+            } else {
+                fence_proxy_async_smem();
+                mbar_arrive(&full[sl]);
+            }
+        }
+        // the copies still in flight: land them and arrive for their tiles
+        cp_async_wait_all();
+        if (async_src && !abort_s) {
+            fence_proxy_async_smem();
+            for (int j = i - (NS - 1) > 0 ? i - (NS - 1) : 0; j < i; ++j) mbar_arrive(&full[j % NS]);
+        }
+    } else if (warp == 8) {
+        if (lane == 0) {
+            int i = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                const int sl = i % NS, k = i / NS, a = i & 1, ka = i >> 1;
+                if (!mbar_wait(&full[sl], k & 1, status) ||
+                    (ka > 0 && !mbar_wait(&acce[a], (ka - 1) & 1, status)))
+                    abort_s = 1;
+                if (abort_s) break;
+                tc_fence_after();
+                issue_mmas_row<C8P, NP>(tmem + (uint32_t)(a * NP), sH_a + (uint32_t)(sl * G::kHBytes), sW_a, sgn);
+                mma_commit(&empty[sl]);
+                mma_commit(&accf[a]);
+            }
+        }
+        __syncwarp();
+    } else {
+        const float osc = oscale ? *oscale : 1.f;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            const int a = i & 1, ka = i >> 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&accf[a], ka & 1, status) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) abort_s = 1;
+            if (abort_s) break;
+            tc_fence_after();
+            int z, y, x0;
+            origin(tile, z, y, x0);
+            epilogue<NP>(src, tmem + (uint32_t)(a * NP), z, y, x0, N, bias, relu, osc, out);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[a]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        tmem_dealloc(tmem, G::kCols);
+    }
+}
+
+// The paired-tap weights of a source of at most 8 channels:
+// Wp[pz][px][g][c][n][j], plane offsets (pz, p, px) of the halo, p = 0 and 1
+// for g = 0 (c = 0, 1) and p = 2 for g = 1 (c = 0; c = 1 zero); the tap is
+// the one applied at offset (pz - 1, p - 1, px - 1) = sgn (dz, dy, dx).
+__global__ void k_prep_umma_pair(const __nv_bfloat16* __restrict__ Wt, int Npad, int Cs, int N, int NP, int sgn,
+                                 __nv_bfloat16* __restrict__ Wp)
+{
+    const int total = 9 * 2 * 2 * NP * 8;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int j = i % 8, n = (i / 8) % NP, c = (i / (8 * NP)) % 2, g = (i / (16 * NP)) % 2, pzx = i / (32 * NP);
+    const int pz = pzx / 3, px = pzx % 3;
+    const int p = g == 0 ? c : (c == 0 ? 2 : -1);
+    __nv_bfloat16 v = __float2bfloat16(0.f);
+    if (p >= 0 && j < Cs && n < N) {
+        const int dz = sgn * (pz - 1), dy = sgn * (p - 1), dx = sgn * (px - 1);
+        const int tap = 9 * (dz + 1) + 3 * (dy + 1) + (dx + 1);
+        v = Wt[(size_t)(tap * Cs + j) * Npad + n];
+    }
+    Wp[i] = v;
 }
 
 // Wu[tap][c][n][j] = Wt[(tap * Cs + 8 c + j) * Npad + n] (zero past Cs

@@ -33,7 +33,9 @@ unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 // used for it.
 struct UmmaW {
     __nv_bfloat16* w = nullptr;
+    __nv_bfloat16* wp = nullptr;   // paired-tap layout (sources of at most 8 channels), or null
     int c8p = 0, np = 0;
+    int sgn = 1;                   // -1: the input-gradient (flipped) operand
 };
 
 // FP32 workspace of the split-K partial sums of the gather kernel (owned
@@ -248,7 +250,8 @@ bool umma_prefers(const ConvSrc& s) { return umma_mode() == 2 || (!s.f32 && s.W 
 
 template <int C8P, int NP, int NB, int R, class OutT>
 cudaError_t launch_umma_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, const float* bias, int relu,
-                          const float* oscale, OutT* out, int* status, cudaStream_t st)
+                          const float* oscale, OutT* out, int* status, cudaStream_t st,
+                          const __nv_bfloat16* Wpair = nullptr)
 {
     using G = umma::Geom<C8P, NP, NB, R>;
     auto* fn = umma::k_conv_umma<C8P, NP, NB, R, OutT>;
@@ -282,8 +285,63 @@ cudaError_t launch_umma_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, cons
     const long long tiles = (long long)((s.W + umma::kM - 1) / umma::kM) * ((s.H + R - 1) / R) * s.D;
     if (tiles > (1LL << 30)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long long>(tiles, (long long)num_sms() * occ);
-    fn<<<grid, umma::kT, smem, st>>>(s, Wu, N, bias, relu, oscale, out, (int)tiles, status);
+    fn<<<grid, umma::kT, smem, st>>>(s, Wu, N, bias, relu, oscale, out, (int)tiles, status, Wpair);
     return cudaGetLastError();
+}
+
+// The warp-specialised form (umma_conv.cuh: producer, MMA and epilogue
+// warps, one persistent CTA per SM, NS halo slots): MH3D_UMMA_WS=1.
+bool umma_ws()
+{
+    const char* e = std::getenv("MH3D_UMMA_WS");
+    return e && e[0] == '1';
+}
+
+template <int C8P, int NP, int NS, class OutT>
+cudaError_t launch_umma_ws_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, const float* bias, int relu,
+                             const float* oscale, OutT* out, int* status, cudaStream_t st)
+{
+    using G = umma::GeomWs<C8P, NP, NS>;
+    auto* fn = umma::k_conv_umma_ws<C8P, NP, NS, OutT>;
+    const size_t smem = G::smem();
+    constexpr int kDevs = 64;
+    static bool attr_dev[kDevs] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
+    if (!attr_dev[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_dev[dev] = true;
+    }
+    const long long tiles = (long long)((s.W + umma::kM - 1) / umma::kM) * s.H * s.D;
+    if (tiles > (1LL << 30)) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long long>(tiles, (long long)num_sms());   // one CTA per SM
+    fn<<<grid, umma::kWsT, smem, st>>>(s, Wu, N, bias, relu, oscale, out, (int)tiles, status);
+    return cudaGetLastError();
+}
+
+// The deepest halo ring that fits (4, 3 or 2 slots); false if none does.
+template <int C8P, int NP, class OutT>
+bool launch_umma_ws(const ConvSrc& s, const __nv_bfloat16* Wu, int N, const float* bias, int relu,
+                    const float* oscale, OutT* out, int* status, cudaStream_t st, cudaError_t* err)
+{
+    const size_t lim = (size_t)smem_optin();
+    if (umma::GeomWs<C8P, NP, 4>::smem() <= lim)
+        *err = launch_umma_ws_t<C8P, NP, 4>(s, Wu, N, bias, relu, oscale, out, status, st);
+    else if (umma::GeomWs<C8P, NP, 3>::smem() <= lim)
+        *err = launch_umma_ws_t<C8P, NP, 3>(s, Wu, N, bias, relu, oscale, out, status, st);
+    else if (umma::GeomWs<C8P, NP, 2>::smem() <= lim)
+        *err = launch_umma_ws_t<C8P, NP, 2>(s, Wu, N, bias, relu, oscale, out, status, st);
+    else
+        return false;
+    return true;
+}
+
+// Paired taps for sources of at most 8 channels (MH3D_UMMA_PAIR=0: off).
+bool umma_pair()
+{
+    const char* e = std::getenv("MH3D_UMMA_PAIR");
+    return !(e && e[0] == '0');
 }
 
 // Output rows per tile of the tcgen05 kernel (MH3D_UMMA_ROWS = 1, 2 or 4).
@@ -303,16 +361,21 @@ template <int C8P, int NP, class OutT>
 cudaError_t launch_umma_nb(const ConvSrc& s, const UmmaW& u, int N, const float* bias, int relu, const float* oscale,
                            OutT* out, int* status, cudaStream_t st)
 {
+    if (umma_ws()) {
+        cudaError_t err = cudaSuccess;
+        if (launch_umma_ws<C8P, NP>(s, u.w, N, bias, relu, oscale, out, status, st, &err)) return err;
+    }
     const char* e = std::getenv("MH3D_UMMA_NB");
     const bool two = e && e[0] == '2';
     if (two && umma::Geom<C8P, NP, 2>::smem() <= (size_t)smem_optin())
         return launch_umma_t<C8P, NP, 2, 1>(s, u.w, N, bias, relu, oscale, out, status, st);
     const int R = umma_rows();
+    const __nv_bfloat16* wp = umma_pair() ? u.wp : nullptr;
     if (R == 4 && umma::Geom<C8P, NP, 1, 4>::smem() <= (size_t)smem_optin())
-        return launch_umma_t<C8P, NP, 1, 4>(s, u.w, N, bias, relu, oscale, out, status, st);
+        return launch_umma_t<C8P, NP, 1, 4>(s, u.w, N, bias, relu, oscale, out, status, st, wp);
     if (R >= 2 && umma::Geom<C8P, NP, 1, 2>::smem() <= (size_t)smem_optin())
-        return launch_umma_t<C8P, NP, 1, 2>(s, u.w, N, bias, relu, oscale, out, status, st);
-    return launch_umma_t<C8P, NP, 1, 1>(s, u.w, N, bias, relu, oscale, out, status, st);
+        return launch_umma_t<C8P, NP, 1, 2>(s, u.w, N, bias, relu, oscale, out, status, st, wp);
+    return launch_umma_t<C8P, NP, 1, 1>(s, u.w, N, bias, relu, oscale, out, status, st, wp);
 }
 
 template <int C8P, class OutT>
@@ -350,12 +413,22 @@ cudaError_t prep_umma(const __nv_bfloat16* Wt, int Npad, int Cs, bool f32, int N
     if (!u.c8p || !u.np || !u.w) return cudaSuccess;
     const int total = 27 * u.c8p * u.np * 8;
     umma::k_prep_umma<<<blocks_for(total, 256), 256, 0, st>>>(Wt, Npad, Cs, N, u.c8p, u.np, u.w);
+    if (u.wp) {
+        const int tp = 9 * 2 * 2 * u.np * 8;
+        umma::k_prep_umma_pair<<<blocks_for(tp, 256), 256, 0, st>>>(Wt, Npad, Cs, N, u.np, u.sgn, u.wp);
+    }
     return cudaGetLastError();
 }
 size_t umma_elems(int Cs, bool f32, int N)
 {
     const int c = umma_c8p(Cs, f32), np = umma_np(N);
     return (c && np) ? (size_t)27 * c * np * 8 : 0;
+}
+// The paired-tap layout, for sources of at most 8 channels (one chunk).
+size_t umma_pair_elems(int Cs, bool f32, int N)
+{
+    const int np = umma_np(N);
+    return (umma_c8p(Cs, f32) && np && (f32 || Cs <= 8)) ? (size_t)9 * 2 * 2 * np * 8 : 0;
 }
 
 // ---- split K for the gather kernel ------------------------------------------
@@ -702,6 +775,10 @@ mh3d_status mh3d_unet_create_levels(int nx, int ny, int nz, int levels, const in
         const size_t ef = umma_elems(l.cin, i == 0, l.cout), eb = umma_elems(l.cout, false, l.cin);
         if (ef) A(&l.uf.w, ef);
         if (eb) A(&l.ub.w, eb);
+        const size_t pf = umma_pair_elems(l.cin, i == 0, l.cout), pb = umma_pair_elems(l.cout, false, l.cin);
+        if (pf) A(&l.uf.wp, pf);
+        if (pb) A(&l.ub.wp, pb);
+        l.ub.sgn = -1;
     }
     A(&n->status, 1);
     if (ok && cudaMemset(n->status, 0, sizeof(int)) != cudaSuccess) ok = false;
@@ -959,8 +1036,12 @@ mh3d_status mh3d_unet_conv_forward(const mh3d_unet_conv_desc* c, const float* W,
     const size_t ue = umma_elems(s.C, s.f32 != nullptr, c->cout);
     Tmp uw(sizeof(__nv_bfloat16) * std::max<size_t>(ue, 1)), stat(sizeof(int));
     if (!uw.p || !stat.p) return MH3D_ERR_OOM;
+    const size_t pe = umma_pair_elems(s.C, s.f32 != nullptr, c->cout);
+    Tmp pw(sizeof(__nv_bfloat16) * std::max<size_t>(pe, 1));
+    if (!pw.p) return MH3D_ERR_OOM;
     UmmaW u;
     u.w = ue ? (__nv_bfloat16*)uw.p : nullptr;
+    u.wp = pe ? (__nv_bfloat16*)pw.p : nullptr;
     if (prep_umma((const __nv_bfloat16*)wt.p, Np, s.C, s.f32 != nullptr, c->cout, u, st) != cudaSuccess ||
         cudaMemsetAsync(stat.p, 0, sizeof(int), st) != cudaSuccess)
         return MH3D_ERR_CUDA;
@@ -992,8 +1073,13 @@ mh3d_status mh3d_unet_conv_input_grad(const mh3d_unet_conv_desc* c, const void* 
     const size_t ue = umma_elems(s.C, false, c->cin);
     Tmp uw(sizeof(__nv_bfloat16) * std::max<size_t>(ue, 1)), stat(sizeof(int));
     if (!uw.p || !stat.p) return MH3D_ERR_OOM;
+    const size_t pe = umma_pair_elems(s.C, false, c->cin);
+    Tmp pw(sizeof(__nv_bfloat16) * std::max<size_t>(pe, 1));
+    if (!pw.p) return MH3D_ERR_OOM;
     UmmaW u;
     u.w = ue ? (__nv_bfloat16*)uw.p : nullptr;
+    u.wp = pe ? (__nv_bfloat16*)pw.p : nullptr;
+    u.sgn = -1;
     if (prep_umma((const __nv_bfloat16*)wt.p, Np, s.C, false, c->cin, u, st) != cudaSuccess ||
         cudaMemsetAsync(stat.p, 0, sizeof(int), st) != cudaSuccess)
         return MH3D_ERR_CUDA;

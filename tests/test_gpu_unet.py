@@ -27,22 +27,30 @@ torch = pytest.importorskip("torch")
 N_SMALL = (14, 10, 6)   # nx, ny, nz: V = 840, not a multiple of the 128-voxel tile; partial 8x4x4 blocks
 
 
-@pytest.fixture(params=["umma", "umma_r1", "umma_r4", "umma_nb2", "default", "tiled", "gather"], autouse=True)
+@pytest.fixture(params=["umma", "umma_r1", "umma_r4", "umma_nopair", "umma_nb2", "umma_ws", "default", "tiled",
+                        "gather"], autouse=True)
 def conv_path(request, monkeypatch):
     """Every test runs with every convolution the tcgen05/TMEM kernel takes
     on it (MH3D_UNET_UMMA=1: the FP32 input, 8..32 bfloat16 channels in
     multiples of 8, up to 64 outputs; the others go to the mma.sync
     kernels) with two output rows per tile (the default), one and four
-    (MH3D_UMMA_ROWS), on its double-buffered form (MH3D_UMMA_NB=2), with
+    (MH3D_UMMA_ROWS), without the paired taps of 8-channel sources
+    (MH3D_UMMA_PAIR=0), on its double-buffered form (MH3D_UMMA_NB=2), on its
+    warp-specialised pipelined form (MH3D_UMMA_WS=1), with
     the default choice (tcgen05 for bfloat16 sources with rows of 96 voxels
     or more), on the halo-tiled mma.sync kernel alone (MH3D_UNET_UMMA=0)
     and on the gather kernel (MH3D_UNET_UMMA=0, MH3D_UNET_GATHER=1)."""
-    for v in ("MH3D_UNET_GATHER", "MH3D_UNET_UMMA", "MH3D_UMMA_NB", "MH3D_UMMA_ROWS"):
+    for v in ("MH3D_UNET_GATHER", "MH3D_UNET_UMMA", "MH3D_UMMA_NB", "MH3D_UMMA_ROWS", "MH3D_UMMA_WS",
+              "MH3D_UMMA_PAIR"):
         monkeypatch.delenv(v, raising=False)
     if request.param.startswith("umma"):
         monkeypatch.setenv("MH3D_UNET_UMMA", "1")
         if request.param == "umma_nb2":
             monkeypatch.setenv("MH3D_UMMA_NB", "2")
+        elif request.param == "umma_ws":
+            monkeypatch.setenv("MH3D_UMMA_WS", "1")
+        elif request.param == "umma_nopair":
+            monkeypatch.setenv("MH3D_UMMA_PAIR", "0")
         elif request.param in ("umma_r1", "umma_r4"):
             monkeypatch.setenv("MH3D_UMMA_ROWS", request.param[-1])
     elif request.param in ("tiled", "gather"):
@@ -143,7 +151,7 @@ def test_conv_forward_at_the_bench_size(cin, cout, mode, conv_path):
     tiles."""
     from paper_2503_13802_gb300.unet import mh3d_unet_conv_forward
 
-    if conv_path not in ("default", "umma", "tiled"):
+    if conv_path not in ("default", "umma", "umma_ws", "tiled"):
         pytest.skip("the full-size layers run on the default, tcgen05 and tiled paths")
 
     n = (128, 128, 64)
