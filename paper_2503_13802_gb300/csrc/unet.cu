@@ -227,15 +227,15 @@ int umma_c8p(int Cs, bool f32)
 // Accumulator columns for N output channels (a multiple of 16), 0 past 64.
 int umma_np(int N) { return N <= 16 ? 16 : (N <= 32 ? 32 : (N <= 64 ? 64 : 0)); }
 
-// Which convolutions run on the tcgen05 kernel.  By default those with a
-// bfloat16 source whose rows fill most of a 128-voxel tile (W >= 96): per
-// launch at 128x128x64, channels (8, 16, 32), L2 flushed, it takes the
-// full-resolution layers in 69 (8 -> 8), 69 (upsampled 16 -> 8), 93 (skip
-// sum 8 -> 8) and 62 us (8 -> 1, FP32 out) against 90, 158, 99 and 89 us on
-// the mma.sync tiles, while the half- and quarter-resolution layers (rows
-// of 64 and 32 voxels in a 128-lane accumulator: 22-29 against 10-23 us)
-// and the single-channel FP32 input layer (70 against 62 us, where the
-// mma.sync kernel packs the 27 taps into K) stay on mma.sync.
+// Which convolutions run on the tcgen05 kernel.  By default those whose
+// rows fill most of a 128-voxel tile (W >= 96; the FP32 single-channel
+// input only with paired taps): per launch at 128x128x64, channels
+// (8, 16, 32), L2 flushed, it takes the full-resolution layers in 58 (FP32
+// input 1 -> 8), 52 (8 -> 8), 68 (upsampled 16 -> 8), 71 (skip sum 8 -> 8)
+// and 51 us (8 -> 1, FP32 out) against 62, 90, 158, 99 and 89 us on the
+// mma.sync tiles, while the half- and quarter-resolution layers (rows of 64
+// and 32 voxels in a 128-lane accumulator: 22-29 against 10-23 us) stay on
+// mma.sync.
 // MH3D_UNET_UMMA=1 sends every convolution it can take to the tcgen05
 // kernel, 0 none.
 int umma_mode()
@@ -246,7 +246,8 @@ int umma_mode()
     return 1;
 }
 bool umma_enabled() { return umma_mode() != 0; }
-bool umma_prefers(const ConvSrc& s) { return umma_mode() == 2 || (!s.f32 && s.W >= 96); }
+bool umma_pair();
+bool umma_prefers(const ConvSrc& s) { return umma_mode() == 2 || (s.W >= 96 && (!s.f32 || umma_pair())); }
 
 template <int C8P, int NP, int NB, int R, class OutT>
 cudaError_t launch_umma_t(const ConvSrc& s, const __nv_bfloat16* Wu, int N, const float* bias, int relu,
