@@ -32,9 +32,9 @@
  *
  * The convolutions run on the tcgen05 tensor cores (accumulators in tensor
  * memory) where the source is bfloat16 with 8..32 channels in multiples of
- * 8, at most 64 outputs, and rows of 96 voxels or more; on mma.sync tiles
- * otherwise.  MH3D_UNET_UMMA=0 / 1 sends none / every convolution it can
- * take to the tcgen05 kernel.
+ * 8 or the FP32 input, at most 64 outputs, and rows of 96 voxels or more;
+ * on mma.sync tiles otherwise.  MH3D_UNET_UMMA=0 / 1 sends none / every
+ * convolution it can take to the tcgen05 kernel.
  *
  * Sizes: nx, ny, nz multiples of 2^(L-1) (4 for mh3d_unet_create); channels
  * in 1..64 (mh3d_unet_create) or 1..128 (mh3d_unet_create_levels).  Volumes are

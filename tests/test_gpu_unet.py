@@ -37,7 +37,7 @@ def conv_path(request, monkeypatch):
     (MH3D_UMMA_ROWS), without the paired taps of 8-channel sources
     (MH3D_UMMA_PAIR=0), on its double-buffered form (MH3D_UMMA_NB=2), on its
     warp-specialised pipelined form (MH3D_UMMA_WS=1), with
-    the default choice (tcgen05 for bfloat16 sources with rows of 96 voxels
+    the default choice (tcgen05 for sources with rows of 96 voxels
     or more), on the halo-tiled mma.sync kernel alone (MH3D_UNET_UMMA=0)
     and on the gather kernel (MH3D_UNET_UMMA=0, MH3D_UNET_GATHER=1)."""
     for v in ("MH3D_UNET_GATHER", "MH3D_UNET_UMMA", "MH3D_UMMA_NB", "MH3D_UMMA_ROWS", "MH3D_UMMA_WS",
