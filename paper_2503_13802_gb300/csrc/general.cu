@@ -10,10 +10,12 @@
 // one pointwise kernel forms every harmonic's portrait-grid spectrum
 //   D_k(w') = sum_{a < s} e^{2 pi i (w' + a m_x) r / n_x} sum_j H_kj W_j (w' + a m_x)
 // (the row selector x = s i' + r is exactly this alias sum with the offset
-// phase) in the output buffer, and inverse passes along x (length m_x), y and
-// z over all K portraits return c_k[z][y][s i' + r]; d_k = e^{i theta_k} Re c
-// in place.  Adjoint: the real parts u_k = Re(e^{-i theta_k} d_k) are
-// transformed on the portrait grid, the unfold kernel forms
+// phase), packed in harmonic pairs D_{2c} + i D_{2c+1} (two real images per
+// complex transform), and inverse passes along x (length m_x), y and z over
+// the pairs return c_k[z][y][s i' + r]; d_k = e^{i theta_k} Re c for each of
+// the pair.  Adjoint: the real parts u_k = Re(e^{-i theta_k} d_k), packed in
+// pairs, are transformed on the portrait grid, the unfold kernel separates
+// each pair's spectra by their symmetry and forms
 // V_j(f) = e^{-2 pi i f r / n_x} sum_k conj(H_kj(f)) U_k(f mod m_x) (the
 // spectrum of u_k inserted at x = s i' + r, periodic in m_x), and the
 // inverse passes and sum_j b_j Re V_j finish.  Each pass covers every
@@ -111,16 +113,22 @@ __global__ void __launch_bounds__(kGT) k_gen_line(float2* v, Pencils g, RadixPla
 //   0  in place;
 //   1  load W_j = b_j rho (rho real [N], b [nc][N] or null: 1) -- the x pass
 //      of the forward's component volumes, written to v;
-//   2  store d_k = e^{i theta_k} Re(c_k) (ph[k]) -- the z pass of the
-//      forward's inverse, in place;
-//   3  load u_k = Re(e^{-i theta_k} d_k) (src = the portraits, ph[k]) --
-//      the x pass of the adjoint's portrait transform, written to v.
-// The volume of pencil p (a component or a harmonic) is p / per_vol.
+//   2  store the pair c of portraits: volume c holds z_c = c_{2c} + i c_{2c+1}
+//      (two real images in one complex transform), so d_{2c} =
+//      e^{i theta_2c} Re(z_c) and d_{2c+1} = e^{i theta_2c+1} Im(z_c) -- the
+//      z pass of the forward's inverse, written to dst (K portraits);
+//   3  load z_c = u_{2c} + i u_{2c+1}, u_k = Re(e^{-i theta_k} d_k) (src =
+//      the K portraits) -- the x pass of the adjoint's portrait transform,
+//      written to v.
+// The volume of pencil p (a component or a harmonic pair) is p / per_vol.
 struct GenIO {
     const float* rho = nullptr;
     const float* b = nullptr;
     const float2* src = nullptr;
+    float2* dst = nullptr;
     const float2* ph = nullptr;
+    int K = 0;              // harmonics (modes 2, 3)
+    long long Q = 0;        // portrait samples per harmonic (modes 2, 3)
 };
 
 // The same transform for the common lengths (64, 128) with a compile-time
@@ -140,14 +148,17 @@ __global__ void __launch_bounds__(kGT) k_gen_line_ct(float2* v, Pencils g, const
     __shared__ __align__(16) float2 b0[N * LD];
     __shared__ __align__(16) float2 b1[N * LD];
     __shared__ long long sbase[P], svol[P];
-    __shared__ float2 sph[P];
+    __shared__ float2 sph[P], sph2[P];   // modes 2, 3: the pair's phases (the second zero past K)
     const long long p0 = (long long)blockIdx.x * P, np = g.count();
     if (threadIdx.x < P) {
         const long long pg = p0 + threadIdx.x;
         const long long c = pg < np ? pg / g.per_vol() : 0;
         sbase[threadIdx.x] = pg < np ? g.base(pg) : -1;
         svol[threadIdx.x] = c;
-        if (MODE == 2 || MODE == 3) sph[threadIdx.x] = io.ph[c];
+        if (MODE == 2 || MODE == 3) {
+            sph[threadIdx.x] = io.ph[2 * c];
+            sph2[threadIdx.x] = 2 * c + 1 < io.K ? io.ph[2 * c + 1] : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     const long long sd = g.stride();
@@ -165,8 +176,11 @@ __global__ void __launch_bounds__(kGT) k_gen_line_ct(float2* v, Pencils g, const
             if (io.b) x *= io.b[a];
             t[i] = make_float2(x, 0.f);
         } else if (MODE == 3) {
-            const float2 dv = io.src[b + e * sd], ph = sph[p];
-            t[i] = make_float2(ph.x * dv.x + ph.y * dv.y, 0.f);
+            // in-volume offset of the element, then the pair's two portraits
+            const long long c = svol[p], o = b + e * sd - c * g.vstride;
+            const float2 da = io.src[2 * c * io.Q + o], pa = sph[p], pb = sph2[p];
+            const float2 db = 2 * c + 1 < io.K ? io.src[(2 * c + 1) * io.Q + o] : make_float2(0.f, 0.f);
+            t[i] = make_float2(pa.x * da.x + pa.y * da.y, pb.x * db.x + pb.y * db.y);
         } else {
             t[i] = v[b + e * sd];
         }
@@ -190,8 +204,10 @@ __global__ void __launch_bounds__(kGT) k_gen_line_ct(float2* v, Pencils g, const
         if (b >= 0) {
             const float2 o = out[e * LD + p];
             if (MODE == 2) {
-                const float2 ph = sph[p];
-                v[b + e * sd] = make_float2(ph.x * o.x, ph.y * o.x);
+                const long long c = svol[p], off = b + e * sd - c * g.vstride;
+                const float2 pa = sph[p], pb = sph2[p];
+                io.dst[2 * c * io.Q + off] = make_float2(pa.x * o.x, pa.y * o.x);
+                if (2 * c + 1 < io.K) io.dst[(2 * c + 1) * io.Q + off] = make_float2(pb.x * o.y, pb.y * o.y);
             } else {
                 v[b + e * sd] = o;
             }
@@ -225,21 +241,25 @@ __global__ void k_gen_weight(const float* __restrict__ rho, const float* __restr
     }
 }
 
-// Portrait-grid spectra of every harmonic: D[k][q], q over [nz][ny][mx]:
-// D_k(w) = sum_a e^{2 pi i f r / nx} sum_j H_kj(f) W_j(f), f = w + a mx (the
-// row selector x = s i' + r as an alias sum).  One thread per q walks the
-// harmonics.  SR > 0 (s <= SR): the thread keeps W_j(f) and the offset
-// phases of its s frequencies in registers; SR = 0: any s, re-read per k.
+// Portrait-grid spectra of every harmonic, D_k(w) = sum_a e^{2 pi i f r / nx}
+// sum_j H_kj(f) W_j(f), f = w + a mx (the row selector x = s i' + r as an
+// alias sum), q over [nz][ny][mx], written in harmonic pairs: Z_c = D_{2c} +
+// i D_{2c+1} (D_K = 0), the spectrum of the complex image c_{2c} + i c_{2c+1}
+// of two real portrait images, so that one inverse transform serves two
+// harmonics.  One thread per q walks the harmonics.  SR > 0 (s <= SR): the
+// thread keeps W_j(f) and the offset phases of its s frequencies in
+// registers; SR = 0: any s, re-read per k.
+//
+// Each D_k is the spectrum of a real image: D_k(-q) = conj(D_k(q)), so
+// Z_c(-q) = conj(D_{2c}(q)) + i conj(D_{2c+1}(q)).  Threads cover the planes
+// z <= nz / 2 and write the mirror of every q off the planes z = 0 and
+// 2 z = nz (which hold their own mirrors and are computed in full): each
+// spectrum sample is read for one of f and -f only.
 template <int SR>
-__global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restrict__ W, float2* __restrict__ D,
+__global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restrict__ W, float2* __restrict__ Z,
                            int nx, int ny, int nz, int mx, int s, int r, int nc, int K, long long N, long long Q,
                            const float2* __restrict__ twx)
 {
-    // D_k is the spectrum of a real portrait image: D_k(-q) = conj(D_k(q)).
-    // Threads cover the planes z <= nz / 2 and write the mirror of every q
-    // off the planes z = 0 and 2 z = nz (which hold their own mirrors and
-    // are computed in full), so each spectrum sample is read for one of
-    // f and -f only.
     const long long Qh = (long long)(nz / 2 + 1) * ny * mx;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Qh; q += (long long)gridDim.x * blockDim.x) {
         const int w = (int)(q % mx);
@@ -247,6 +267,10 @@ __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restric
         const int yz = (int)((q - w) / mx), y = yz % ny, z = yz / ny;
         const bool mirror = z != 0 && 2 * z != nz;
         const long long qm = ((long long)(nz - z) * ny + (ny - y) % ny) * mx + (mx - w) % mx;
+        auto put = [&](int c, float2 da, float2 db) {
+            Z[(long long)c * Q + q] = make_float2(da.x - db.y, da.y + db.x);
+            if (mirror) Z[(long long)c * Q + qm] = make_float2(da.x + db.y, db.x - da.y);
+        };
         if constexpr (SR > 0) {
             float2 wv[SR][3], ph[SR];
 #pragma unroll
@@ -260,8 +284,7 @@ __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restric
                 const float2 tw = a < s ? twx[(int)(((long long)f * r) % nx)] : make_float2(0.f, 0.f);
                 ph[a] = make_float2(tw.x, -tw.y);
             }
-#pragma unroll 2
-            for (int k = 0; k < K; ++k) {
+            auto fold_k = [&](int k) {
                 const float2* __restrict__ Hk = H + (long long)k * 3 * N + row + w;
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -274,11 +297,12 @@ __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restric
                         acc = c_add(acc, c_mul(t, ph[a]));
                     }
                 }
-                D[(long long)k * Q + q] = acc;
-                if (mirror) D[(long long)k * Q + qm] = make_float2(acc.x, -acc.y);
-            }
+                return acc;
+            };
+            for (int c = 0; 2 * c < K; ++c)
+                put(c, fold_k(2 * c), 2 * c + 1 < K ? fold_k(2 * c + 1) : make_float2(0.f, 0.f));
         } else {
-            for (int k = 0; k < K; ++k) {
+            auto fold_k = [&](int k) {
                 const float2* __restrict__ Hk = H + (long long)k * 3 * N;
                 float2 acc = make_float2(0.f, 0.f);
                 for (int a = 0; a < s; ++a) {
@@ -289,32 +313,48 @@ __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restric
                     const float2 tw = twx[(int)(((long long)f * r) % nx)];
                     acc = c_add(acc, c_mul(t, make_float2(tw.x, -tw.y)));
                 }
-                D[(long long)k * Q + q] = acc;
-                if (mirror) D[(long long)k * Q + qm] = make_float2(acc.x, -acc.y);
-            }
+                return acc;
+            };
+            for (int c = 0; 2 * c < K; ++c)
+                put(c, fold_k(2 * c), 2 * c + 1 < K ? fold_k(2 * c + 1) : make_float2(0.f, 0.f));
         }
     }
 }
 
-// d_k = e^{i theta_k} Re(D_k) for every harmonic (ph[k] = e^{i theta_k})
-__global__ void k_gen_phase(const float2* D, float2* d, long long Q, int K,
+// d_{2c} = e^{i theta_2c} Re(z_c), d_{2c+1} = e^{i theta_2c+1} Im(z_c): the
+// harmonic pairs' images unpacked into the K portraits (ph[k] = e^{i theta_k})
+__global__ void k_gen_phase(const float2* __restrict__ Zi, float2* __restrict__ d, long long Q, int K,
                             const float2* __restrict__ ph)
 {
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < Q * K; g += (long long)gridDim.x * blockDim.x) {
-        const float2 p = ph[g / Q];
-        const float c = D[g].x;
-        d[g] = make_float2(p.x * c, p.y * c);
+    const int Kh = (K + 1) / 2;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < Q * Kh;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long c = g / Q, o = g - c * Q;
+        const float2 z = Zi[g], pa = ph[2 * c];
+        d[2 * c * Q + o] = make_float2(pa.x * z.x, pa.y * z.x);
+        if (2 * c + 1 < K) {
+            const float2 pb = ph[2 * c + 1];
+            d[(2 * c + 1) * Q + o] = make_float2(pb.x * z.y, pb.y * z.y);
+        }
     }
 }
 
-// u_k = Re(e^{-i theta_k} d_k) on the portrait grid, every harmonic, as
-// complex values with zero imaginary part
+// z_c = u_{2c} + i u_{2c+1}, u_k = Re(e^{-i theta_k} d_k): the harmonic
+// pairs of real portrait images packed for one complex transform each
 __global__ void k_gen_unphase(const float2* __restrict__ d, float2* __restrict__ U, long long Q, int K,
                               const float2* __restrict__ ph)
 {
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < Q * K; g += (long long)gridDim.x * blockDim.x) {
-        const float2 p = ph[g / Q], v = d[g];
-        U[g] = make_float2(p.x * v.x + p.y * v.y, 0.f);
+    const int Kh = (K + 1) / 2;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < Q * Kh;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long c = g / Q, o = g - c * Q;
+        const float2 pa = ph[2 * c], va = d[2 * c * Q + o];
+        float ub = 0.f;
+        if (2 * c + 1 < K) {
+            const float2 pb = ph[2 * c + 1], vb = d[(2 * c + 1) * Q + o];
+            ub = pb.x * vb.x + pb.y * vb.y;
+        }
+        U[g] = make_float2(pa.x * va.x + pa.y * va.y, ub);
     }
 }
 
@@ -336,16 +376,30 @@ __global__ void k_gen_unfold(const float2* __restrict__ H, const float2* __restr
         const int yz = (int)((i - f) / nx), y = yz % ny, z = yz / ny;
         const bool mirror = z != 0 && 2 * z != nz;
         const long long im = ((long long)(nz - z) * ny + (ny - y) % ny) * nx + (nx - f) % nx;
-        const long long qi = (long long)yz * mx + f % mx;
+        const int w = f % mx;
+        const long long qi = (long long)yz * mx + w;
+        // the portrait-grid mirror -g of g = (w, y, z)
+        const long long qim = ((long long)((nz - z) % nz) * ny + (ny - y) % ny) * mx + (mx - w) % mx;
         float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        for (int k = 0; k < K; ++k) {
-            const float2 u = U[(long long)k * Q + qi];
-            const float2* __restrict__ Hk = H + (long long)k * 3 * N + i;
+        for (int c = 0; 2 * c < K; ++c) {
+            // U holds z_c = u_{2c} + i u_{2c+1} transformed: with A = Z(g) and
+            // B = conj(Z(-g)), U_{2c}(g) = (A + B) / 2, U_{2c+1}(g) = (A - B) / 2i
+            const float2 A = U[(long long)c * Q + qi], Bm = U[(long long)c * Q + qim];
+            const float2 B = make_float2(Bm.x, -Bm.y);
+            const float2 ua = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
+            const float2 ub = make_float2(0.5f * (A.y - B.y), -0.5f * (A.x - B.x));
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (j < nc) {
-                    const float2 h = Hk[(long long)j * N];
-                    acc[j] = c_add(acc[j], c_mul(make_float2(h.x, -h.y), u));
+            for (int h = 0; h < 2; ++h) {
+                const int k = 2 * c + h;
+                if (k >= K) break;
+                const float2 u = h == 0 ? ua : ub;
+                const float2* __restrict__ Hk = H + (long long)k * 3 * N + i;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (j < nc) {
+                        const float2 hv = Hk[(long long)j * N];
+                        acc[j] = c_add(acc[j], c_mul(make_float2(hv.x, -hv.y), u));
+                    }
                 }
             }
         }
@@ -558,12 +612,16 @@ mh3d_status mh3d_general_forward(mh3d_plan Pp, const float* rho, const float* bv
     const cudaStream_t st = (cudaStream_t)stream;
     const long long N = P.N, Q = (long long)P.nz * P.ny * P.mx;
     const int nc = bvec ? 3 : 1;
-    float2* W = P.gen_work;   // nc volumes
-    float2* D = (float2*)d;   // the portrait-grid spectra, transformed and phased in place
+    float2* W = P.gen_work;           // nc volumes
+    float2* Z = P.gen_work + 3 * N;   // the harmonic pairs' portrait-grid spectra, then images
+    const int Kh = (P.K + 1) / 2;
     GenIO io;
     io.rho = rho;
     io.b = bvec;
     io.ph = P.phase;
+    io.dst = (float2*)d;
+    io.K = P.K;
+    io.Q = Q;
     if (gen_ct_length(P.ax.n)) {   // b_j rho formed in the x pass's load
         GEN_CK(P, gen_fft3(P, W, nc, P.ax, false, st, 1, 0, io));
     } else {
@@ -573,20 +631,20 @@ mh3d_status mh3d_general_forward(mh3d_plan Pp, const float* rho, const float* bv
     }
     const long long Qh = (long long)(P.nz / 2 + 1) * P.ny * P.mx;   // the planes the fold's threads cover
     if (P.s <= 2)
-        k_gen_fold<2><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
+        k_gen_fold<2><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, Z, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
                                                       P.ax.tw);
     else if (P.s <= 4)
-        k_gen_fold<4><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
+        k_gen_fold<4><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, Z, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
                                                       P.ax.tw);
     else
-        k_gen_fold<0><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, D, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
+        k_gen_fold<0><<<gen_blocks(Qh), kGB, 0, st>>>(P.gen_H, W, Z, P.nx, P.ny, P.nz, P.mx, P.s, P.r, nc, P.K, N, Q,
                                                       P.ax.tw);
     GEN_CK(P, cudaGetLastError());
-    if (gen_ct_length(P.az.n)) {   // the phase applied in the z pass's store
-        GEN_CK(P, gen_fft3(P, D, P.K, P.am, true, st, 0, 2, io));
+    if (gen_ct_length(P.az.n)) {   // the pairs unpacked and phased in the z pass's store
+        GEN_CK(P, gen_fft3(P, Z, Kh, P.am, true, st, 0, 2, io));
     } else {
-        GEN_CK(P, gen_fft3(P, D, P.K, P.am, true, st));
-        k_gen_phase<<<gen_blocks(Q * P.K), kGB, 0, st>>>(D, D, Q, P.K, P.phase);
+        GEN_CK(P, gen_fft3(P, Z, Kh, P.am, true, st));
+        k_gen_phase<<<gen_blocks(Q * Kh), kGB, 0, st>>>(Z, (float2*)d, Q, P.K, P.phase);
         GEN_CK(P, cudaGetLastError());
     }
     return MH3D_OK;
@@ -604,16 +662,19 @@ mh3d_status mh3d_general_adjoint(mh3d_plan Pp, const void* d, const float* bvec,
     const long long N = P.N, Q = (long long)P.nz * P.ny * P.mx;
     const int nc = bvec ? 3 : 1;
     float2* V = P.gen_work;          // nc accumulators
-    float2* U = P.gen_work + 3 * N;  // the harmonics' real portrait images, then their spectra
-    if (gen_ct_length(P.am.n)) {   // u_k formed in the x pass's load
+    float2* U = P.gen_work + 3 * N;  // the harmonic pairs of real portrait images, then their spectra
+    const int Kh = (P.K + 1) / 2;
+    if (gen_ct_length(P.am.n)) {   // the pairs formed in the x pass's load
         GenIO io;
         io.src = (const float2*)d;
         io.ph = P.phase;
-        GEN_CK(P, gen_fft3(P, U, P.K, P.am, false, st, 3, 0, io));
+        io.K = P.K;
+        io.Q = Q;
+        GEN_CK(P, gen_fft3(P, U, Kh, P.am, false, st, 3, 0, io));
     } else {
-        k_gen_unphase<<<gen_blocks(Q * P.K), kGB, 0, st>>>((const float2*)d, U, Q, P.K, P.phase);
+        k_gen_unphase<<<gen_blocks(Q * Kh), kGB, 0, st>>>((const float2*)d, U, Q, P.K, P.phase);
         GEN_CK(P, cudaGetLastError());
-        GEN_CK(P, gen_fft3(P, U, P.K, P.am, false, st));
+        GEN_CK(P, gen_fft3(P, U, Kh, P.am, false, st));
     }
     const long long Nh = (long long)(P.nz / 2 + 1) * P.ny * P.nx;   // the planes the unfold's threads cover
     k_gen_unfold<<<gen_blocks(Nh), kGB, 0, st>>>(P.gen_H, U, V, P.nx, P.ny, P.nz, P.mx, P.r, nc, P.K, N, Q, P.ax.tw);
