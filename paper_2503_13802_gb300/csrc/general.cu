@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(kGT) k_gen_line(float2* v, Pencils g, RadixPla
 
 // Fused pre- and post-steps of the compile-time pencil kernel (MODE):
 //   0  in place;
-//   1  load W_j = b_j rho (rho real [N], b [nc][N] or null: 1) -- the x pass
-//      of the forward's component volumes, written to v;
+//   1  load the component pair c: b_{2c} rho + i b_{2c+1} rho (rho real
+//      [N], b [nc][N] or null: one component, b = 1; b_nc = 0) -- the x pass
+//      of the forward's packed component volumes, written to v;
 //   2  store the pair c of portraits: volume c holds z_c = c_{2c} + i c_{2c+1}
 //      (two real images in one complex transform), so d_{2c} =
 //      e^{i theta_2c} Re(z_c) and d_{2c+1} = e^{i theta_2c+1} Im(z_c) -- the
@@ -129,6 +130,7 @@ struct GenIO {
     const float2* ph = nullptr;
     int K = 0;              // harmonics (modes 2, 3)
     long long Q = 0;        // portrait samples per harmonic (modes 2, 3)
+    int nc = 1;             // sensitivity components (mode 1)
 };
 
 // The same transform for the common lengths (64, 128) with a compile-time
@@ -171,10 +173,11 @@ __global__ void __launch_bounds__(kGT) k_gen_line_ct(float2* v, Pencils g, const
         if (b < 0) {
             t[i] = make_float2(0.f, 0.f);
         } else if (MODE == 1) {
-            const long long a = b + e * sd;
-            float x = io.rho[a - svol[p] * g.vstride];
-            if (io.b) x *= io.b[a];
-            t[i] = make_float2(x, 0.f);
+            const long long c = svol[p], off = b + e * sd - c * g.vstride;
+            const float x = io.rho[off];
+            const float re = io.b ? x * io.b[2 * c * g.vstride + off] : x;
+            const float im = (io.b && 2 * c + 1 < io.nc) ? x * io.b[(2 * c + 1) * g.vstride + off] : 0.f;
+            t[i] = make_float2(re, im);
         } else if (MODE == 3) {
             // in-volume offset of the element, then the pair's two portraits
             const long long c = svol[p], o = b + e * sd - c * g.vstride;
@@ -233,11 +236,15 @@ __global__ void k_gen_scale(float2* __restrict__ H, long long n, float sc)
 __global__ void k_gen_weight(const float* __restrict__ rho, const float* __restrict__ bvec, float2* __restrict__ W,
                              long long N, int nc)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N * nc;
+    // the component pairs: W[c] = b_{2c} rho + i b_{2c+1} rho (b = 1 without bvec; b_nc = 0)
+    const int nv = (nc + 1) / 2;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N * nv;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long v = i % N;
-        const float b = bvec ? bvec[i] : 1.f;
-        W[i] = make_float2(b * rho[v], 0.f);
+        const long long c = i / N, v = i - c * N;
+        const float x = rho[v];
+        const float re = bvec ? x * bvec[2 * c * N + v] : x;
+        const float im = (bvec && 2 * c + 1 < nc) ? x * bvec[(2 * c + 1) * N + v] : 0.f;
+        W[i] = make_float2(re, im);
     }
 }
 
@@ -271,15 +278,32 @@ __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restric
             Z[(long long)c * Q + q] = make_float2(da.x - db.y, da.y + db.x);
             if (mirror) Z[(long long)c * Q + qm] = make_float2(da.x + db.y, db.x - da.y);
         };
+        // W holds the component pairs b_{2c} rho + i b_{2c+1} rho transformed:
+        // with A = P_c(f) and B = conj(P_c(-f)), W_{2c} = (A + B) / 2 and
+        // W_{2c+1} = (A - B) / 2i; a lone last component is P_c(f) itself
+        const int zm = (nz - z) % nz, ym = (ny - y) % ny;
+        auto wcomp = [&](int f, float2* out) {
+            const long long i = row + f, im = ((long long)zm * ny + ym) * nx + (nx - f) % nx;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (2 * c >= nc) break;
+                const float2 A = W[(long long)c * N + i];
+                if (2 * c + 1 < nc) {
+                    const float2 Bm = W[(long long)c * N + im];
+                    out[2 * c] = make_float2(0.5f * (A.x + Bm.x), 0.5f * (A.y - Bm.y));
+                    out[2 * c + 1] = make_float2(0.5f * (A.y + Bm.y), -0.5f * (A.x - Bm.x));
+                } else {
+                    out[2 * c] = A;
+                }
+            }
+        };
         if constexpr (SR > 0) {
             float2 wv[SR][3], ph[SR];
 #pragma unroll
             for (int a = 0; a < SR; ++a) {
                 const int f = w + a * mx;
-                const long long i = row + f;
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    wv[a][j] = (a < s && j < nc) ? W[(long long)j * N + i] : make_float2(0.f, 0.f);
+                wv[a][0] = wv[a][1] = wv[a][2] = make_float2(0.f, 0.f);
+                if (a < s) wcomp(f, wv[a]);
                 // e^{+2 pi i f r / nx} = conj(W_nx^{f r mod nx})
                 const float2 tw = a < s ? twx[(int)(((long long)f * r) % nx)] : make_float2(0.f, 0.f);
                 ph[a] = make_float2(tw.x, -tw.y);
@@ -308,8 +332,10 @@ __global__ void k_gen_fold(const float2* __restrict__ H, const float2* __restric
                 for (int a = 0; a < s; ++a) {
                     const int f = w + a * mx;
                     const long long i = row + f;
+                    float2 wj[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    wcomp(f, wj);
                     float2 t = make_float2(0.f, 0.f);
-                    for (int j = 0; j < nc; ++j) t = c_add(t, c_mul(Hk[(long long)j * N + i], W[(long long)j * N + i]));
+                    for (int j = 0; j < nc; ++j) t = c_add(t, c_mul(Hk[(long long)j * N + i], wj[j]));
                     const float2 tw = twx[(int)(((long long)f * r) % nx)];
                     acc = c_add(acc, c_mul(t, make_float2(tw.x, -tw.y)));
                 }
@@ -612,8 +638,9 @@ mh3d_status mh3d_general_forward(mh3d_plan Pp, const float* rho, const float* bv
     const cudaStream_t st = (cudaStream_t)stream;
     const long long N = P.N, Q = (long long)P.nz * P.ny * P.mx;
     const int nc = bvec ? 3 : 1;
-    float2* W = P.gen_work;           // nc volumes
+    float2* W = P.gen_work;           // the component pairs (nc + 1) / 2 volumes
     float2* Z = P.gen_work + 3 * N;   // the harmonic pairs' portrait-grid spectra, then images
+    const int nv = (nc + 1) / 2;
     const int Kh = (P.K + 1) / 2;
     GenIO io;
     io.rho = rho;
@@ -622,12 +649,13 @@ mh3d_status mh3d_general_forward(mh3d_plan Pp, const float* rho, const float* bv
     io.dst = (float2*)d;
     io.K = P.K;
     io.Q = Q;
-    if (gen_ct_length(P.ax.n)) {   // b_j rho formed in the x pass's load
-        GEN_CK(P, gen_fft3(P, W, nc, P.ax, false, st, 1, 0, io));
+    io.nc = nc;
+    if (gen_ct_length(P.ax.n)) {   // the pairs b_j rho formed in the x pass's load
+        GEN_CK(P, gen_fft3(P, W, nv, P.ax, false, st, 1, 0, io));
     } else {
-        k_gen_weight<<<gen_blocks(N * nc), kGB, 0, st>>>(rho, bvec, W, N, nc);
+        k_gen_weight<<<gen_blocks(N * nv), kGB, 0, st>>>(rho, bvec, W, N, nc);
         GEN_CK(P, cudaGetLastError());
-        GEN_CK(P, gen_fft3(P, W, nc, P.ax, false, st));
+        GEN_CK(P, gen_fft3(P, W, nv, P.ax, false, st));
     }
     const long long Qh = (long long)(P.nz / 2 + 1) * P.ny * P.mx;   // the planes the fold's threads cover
     if (P.s <= 2)
