@@ -5,9 +5,11 @@
 // The caller supplies the PSF samples (h_k)_j at the grid's minimal-image
 // offsets; the plan keeps their spectra, DFT(h)/N, as K * 3 complex volumes.
 //
-// Forward: the weighted volumes b_j rho go through complex pencil passes
-// along x, y and z (the Stockham engine of fft_smem.cuh, no spectral step);
-// one pointwise kernel forms every harmonic's portrait-grid spectrum
+// Forward: the weighted volumes b_j rho, packed in pairs b_0 rho + i b_1 rho
+// and b_2 rho (real images, two per complex transform), go through complex
+// pencil passes along x, y and z (no spectral step); one pointwise kernel
+// separates the pairs' spectra by their symmetry and forms every harmonic's
+// portrait-grid spectrum
 //   D_k(w') = sum_{a < s} e^{2 pi i (w' + a m_x) r / n_x} sum_j H_kj W_j (w' + a m_x)
 // (the row selector x = s i' + r is exactly this alias sum with the offset
 // phase), packed in harmonic pairs D_{2c} + i D_{2c+1} (two real images per
