@@ -175,11 +175,18 @@ __global__ void __launch_bounds__(kGT) k_gen_line_ct(float2* v, Pencils g, const
         if (b < 0) {
             t[i] = make_float2(0.f, 0.f);
         } else if (MODE == 1) {
+            // unconditional loads (the lone last component reads its own b
+            // twice and zeroes the second), so the loads of the unrolled
+            // rounds issue together
             const long long c = svol[p], off = b + e * sd - c * g.vstride;
             const float x = io.rho[off];
-            const float re = io.b ? x * io.b[2 * c * g.vstride + off] : x;
-            const float im = (io.b && 2 * c + 1 < io.nc) ? x * io.b[(2 * c + 1) * g.vstride + off] : 0.f;
-            t[i] = make_float2(re, im);
+            if (io.b) {
+                const long long c1 = 2 * c + 1 < io.nc ? 2 * c + 1 : 2 * c;
+                const float w1 = 2 * c + 1 < io.nc ? 1.f : 0.f;
+                t[i] = make_float2(x * io.b[2 * c * g.vstride + off], w1 * x * io.b[c1 * g.vstride + off]);
+            } else {
+                t[i] = make_float2(x, 0.f);
+            }
         } else if (MODE == 3) {
             // in-volume offset of the element, then the pair's two portraits
             const long long c = svol[p], o = b + e * sd - c * g.vstride;
